@@ -1,0 +1,1044 @@
+/*
+ * vof_oracle.c -- plain FP64 CPU oracle of the unsplit geometric VoF advection
+ * step of Maric, Marschall & Bothe (2013).  TEST INFRASTRUCTURE ONLY: it is the
+ * reference that the CUDA path is checked against and is never called by it.
+ *
+ * Slow on purpose.  Geometry is done the way the paper describes it:
+ *  - convex polyhedra are clipped face by face and capped with a cap polygon
+ *    whose points are ordered by an angle insertion sort (Sec. 2.1);
+ *  - intersections of two convex polyhedra are repeated plane clips (Sec. 2.1);
+ *  - the NAG gradient follows Sec. 2.2.1 step by step;
+ *  - interface positioning is the secant iteration with a bisection fallback
+ *    of Alg. 1 (Sec. 2.2.2);
+ *  - flux polyhedra come from the face sweep of Eq. sweep, their volume from a
+ *    tetrahedral decomposition (Eq. V_fS), and the sweep is corrected by a
+ *    secant iteration until Eq. VF holds (Sec. 2.3);
+ *  - phase volumes are the intersections of Eqs. S'_f and S''_f, and the update
+ *    is Eq. alpha-discrete in the owner/neighbour form of Eq. own-nei.
+ * Readings where the paper is silent (cell solids, stencil, tolerances, the
+ * narrow band, the bounding pass) are stated where they are used.
+ * Compiled with -ffp-contract=off so no fused multiply-add changes rounding.
+ */
+#include "vof_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- vectors */
+typedef struct { double x, y, z; } v3;
+
+static v3 mk(double x, double y, double z) { v3 r; r.x = x; r.y = y; r.z = z; return r; }
+static v3 add(v3 a, v3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static v3 sub(v3 a, v3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static v3 scl(v3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 cross(v3 a, v3 b)
+{
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double norm(v3 a) { return sqrt(dot(a, a)); }
+/* signed volume of tetrahedron (a,b,c,d): (b-a).((c-a)x(d-a))/6 */
+static double tetvol(v3 a, v3 b, v3 c, v3 d)
+{
+    return dot(sub(b, a), cross(sub(c, a), sub(d, a))) / 6.0;
+}
+
+/* ------------------------------------------------------------------ mesh */
+struct vo_mesh {
+    int np, nf, ni, nc;
+    v3 *P;
+    int *fptr, *fpts, *own, *nei;
+    int *cptr, *cface;   /* cell -> faces, ascending face index */
+    int *cpptr, *cpt;    /* cell -> its distinct points, ascending */
+    int *pptr, *pcell;   /* point -> cells, ascending */
+    double *w;           /* inverse-distance weight of each (point, cell) entry */
+    v3 *cf, *sf, *cc;
+    double *vc;
+    unsigned char *wall; /* per boundary face: 1 = wall */
+    int *pwn;            /* per point: number of distinct wall normals (0..3) */
+    v3 *pwv;             /* per point: up to two wall normals */
+};
+
+static int cmp_int(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+int vo_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+static int fn(const vo_mesh *m, int f) { return m->fptr[f + 1] - m->fptr[f]; }
+static v3 fp(const vo_mesh *m, int f, int i) { return m->P[m->fpts[m->fptr[f] + i]]; }
+/* R1: a face with three points is its own triangle; a face with more points is
+ * the fan of triangles (c_f, p_i, p_i+1) about the mean point c_f, the
+ * triangulation the paper uses for the NAG face values (Sec. 2.2.1). */
+static int ntri(const vo_mesh *m, int f) { int n = fn(m, f); return n == 3 ? 1 : n; }
+static void face_tri(const vo_mesh *m, int f, int t, v3 o[3])
+{
+    int n = fn(m, f);
+    if (n == 3) { o[0] = fp(m, f, 0); o[1] = fp(m, f, 1); o[2] = fp(m, f, 2); }
+    else { o[0] = m->cf[f]; o[1] = fp(m, f, t); o[2] = fp(m, f, (t + 1) % n); }
+}
+
+vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
+                        const double *px, const double *py, const double *pz,
+                        const int *face_ptr, const int *face_pts, const int *owner,
+                        const int *neighbour, const unsigned char *wall)
+{
+    vo_mesh *m = (vo_mesh *)calloc(1, sizeof(vo_mesh));
+    int i, f, c;
+    m->np = n_points; m->nf = n_faces; m->ni = n_internal; m->nc = n_cells;
+    m->P = (v3 *)malloc(sizeof(v3) * (size_t)n_points);
+    for (i = 0; i < n_points; i++) m->P[i] = mk(px[i], py[i], pz[i]);
+    m->fptr = (int *)malloc(sizeof(int) * (size_t)(n_faces + 1));
+    memcpy(m->fptr, face_ptr, sizeof(int) * (size_t)(n_faces + 1));
+    m->fpts = (int *)malloc(sizeof(int) * (size_t)face_ptr[n_faces]);
+    memcpy(m->fpts, face_pts, sizeof(int) * (size_t)face_ptr[n_faces]);
+    m->own = (int *)malloc(sizeof(int) * (size_t)n_faces);
+    memcpy(m->own, owner, sizeof(int) * (size_t)n_faces);
+    m->nei = (int *)malloc(sizeof(int) * (size_t)(n_internal > 0 ? n_internal : 1));
+    if (n_internal > 0) memcpy(m->nei, neighbour, sizeof(int) * (size_t)n_internal);
+
+    /* cell -> faces */
+    m->cptr = (int *)calloc((size_t)n_cells + 1, sizeof(int));
+    for (f = 0; f < n_faces; f++) {
+        m->cptr[owner[f] + 1]++;
+        if (f < n_internal) m->cptr[neighbour[f] + 1]++;
+    }
+    for (c = 0; c < n_cells; c++) m->cptr[c + 1] += m->cptr[c];
+    m->cface = (int *)malloc(sizeof(int) * (size_t)m->cptr[n_cells]);
+    {
+        int *fill = (int *)calloc((size_t)n_cells, sizeof(int));
+        for (f = 0; f < n_faces; f++) {
+            c = owner[f]; m->cface[m->cptr[c] + fill[c]++] = f;
+            if (f < n_internal) { c = neighbour[f]; m->cface[m->cptr[c] + fill[c]++] = f; }
+        }
+        free(fill);
+    }
+    /* cell -> distinct points */
+    {
+        int total = 0, *tmp, cap = 0;
+        m->cpptr = (int *)calloc((size_t)n_cells + 1, sizeof(int));
+        for (c = 0; c < n_cells; c++) {
+            int k = 0;
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) k += fn(m, m->cface[i]);
+            if (k > cap) cap = k;
+            total += k;
+        }
+        m->cpt = (int *)malloc(sizeof(int) * (size_t)total);
+        tmp = (int *)malloc(sizeof(int) * (size_t)(cap > 0 ? cap : 1));
+        total = 0;
+        for (c = 0; c < n_cells; c++) {
+            int k = 0, u = 0, j;
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+                int g = m->cface[i];
+                for (j = m->fptr[g]; j < m->fptr[g + 1]; j++) tmp[k++] = m->fpts[j];
+            }
+            qsort(tmp, (size_t)k, sizeof(int), cmp_int);
+            for (j = 0; j < k; j++)
+                if (j == 0 || tmp[j] != tmp[j - 1]) m->cpt[total + u++] = tmp[j];
+            total += u;
+            m->cpptr[c + 1] = total;
+        }
+        free(tmp);
+    }
+    /* point -> cells */
+    m->pptr = (int *)calloc((size_t)n_points + 1, sizeof(int));
+    for (i = 0; i < m->cpptr[n_cells]; i++) m->pptr[m->cpt[i] + 1]++;
+    for (i = 0; i < n_points; i++) m->pptr[i + 1] += m->pptr[i];
+    m->pcell = (int *)malloc(sizeof(int) * (size_t)(m->pptr[n_points] > 0 ? m->pptr[n_points] : 1));
+    {
+        int *fill = (int *)calloc((size_t)n_points, sizeof(int));
+        for (c = 0; c < n_cells; c++)
+            for (i = m->cpptr[c]; i < m->cpptr[c + 1]; i++) {
+                int p = m->cpt[i];
+                m->pcell[m->pptr[p] + fill[p]++] = c;
+            }
+        free(fill);
+    }
+    /* R1 geometry */
+    m->cf = (v3 *)malloc(sizeof(v3) * (size_t)n_faces);
+    m->sf = (v3 *)malloc(sizeof(v3) * (size_t)n_faces);
+    for (f = 0; f < n_faces; f++) {
+        int n = fn(m, f), t;
+        v3 s = mk(0, 0, 0);
+        for (i = 0; i < n; i++) s = add(s, fp(m, f, i));
+        m->cf[f] = scl(s, 1.0 / n);
+        s = mk(0, 0, 0);
+        for (t = 0; t < ntri(m, f); t++) {
+            v3 T[3];
+            face_tri(m, f, t, T);
+            s = add(s, scl(cross(sub(T[1], T[0]), sub(T[2], T[0])), 0.5));
+        }
+        m->sf[f] = s;
+    }
+    m->cc = (v3 *)malloc(sizeof(v3) * (size_t)n_cells);
+    m->vc = (double *)malloc(sizeof(double) * (size_t)n_cells);
+    for (c = 0; c < n_cells; c++) {
+        v3 s = mk(0, 0, 0);
+        double V = 0.0;
+        int k = m->cpptr[c + 1] - m->cpptr[c];
+        for (i = m->cpptr[c]; i < m->cpptr[c + 1]; i++) s = add(s, m->P[m->cpt[i]]);
+        m->cc[c] = scl(s, 1.0 / k);
+        for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+            int g = m->cface[i], t;
+            for (t = 0; t < ntri(m, g); t++) {
+                v3 T[3];
+                face_tri(m, g, t, T);
+                if (m->own[g] == c) V += tetvol(m->cc[c], T[0], T[1], T[2]);
+                else V += tetvol(m->cc[c], T[0], T[2], T[1]);
+            }
+        }
+        m->vc[c] = V;
+    }
+    /* reading R2: wall faces allow no normal flow, so the point velocity at a wall
+     * point keeps only its component tangent to every wall through the point */
+    m->wall = (unsigned char *)malloc((size_t)(n_faces - n_internal > 0 ? n_faces - n_internal : 1));
+    for (f = n_internal; f < n_faces; f++) m->wall[f - n_internal] = wall ? wall[f - n_internal] : 1;
+    m->pwn = (int *)calloc((size_t)n_points, sizeof(int));
+    m->pwv = (v3 *)calloc(2 * (size_t)n_points, sizeof(v3));
+    for (f = n_internal; f < n_faces; f++) {
+        v3 u;
+        if (!m->wall[f - n_internal]) continue;
+        u = scl(m->sf[f], 1.0 / norm(m->sf[f]));
+        for (i = m->fptr[f]; i < m->fptr[f + 1]; i++) {
+            int p = m->fpts[i], k, dup = 0;
+            for (k = 0; k < m->pwn[p] && k < 2; k++)
+                if (fabs(dot(u, m->pwv[2 * p + k])) > 1.0 - 1e-12) dup = 1;
+            if (dup || m->pwn[p] >= 3) continue;
+            if (m->pwn[p] < 2) m->pwv[2 * p + m->pwn[p]] = u;
+            m->pwn[p]++;
+        }
+    }
+    /* Eq. w_pc: inverse distance between the point and the point-cell centre */
+    m->w = (double *)malloc(sizeof(double) * (size_t)(m->pptr[n_points] > 0 ? m->pptr[n_points] : 1));
+    for (i = 0; i < n_points; i++) {
+        double s = 0.0;
+        int j;
+        for (j = m->pptr[i]; j < m->pptr[i + 1]; j++) s += 1.0 / norm(sub(m->P[i], m->cc[m->pcell[j]]));
+        for (j = m->pptr[i]; j < m->pptr[i + 1]; j++)
+            m->w[j] = (1.0 / norm(sub(m->P[i], m->cc[m->pcell[j]]))) / s;
+    }
+    return m;
+}
+
+void vo_mesh_destroy(vo_mesh *m)
+{
+    if (!m) return;
+    free(m->P); free(m->fptr); free(m->fpts); free(m->own); free(m->nei);
+    free(m->cptr); free(m->cface); free(m->cpptr); free(m->cpt); free(m->pptr);
+    free(m->pcell); free(m->w); free(m->cf); free(m->sf); free(m->cc); free(m->vc);
+    free(m->wall); free(m->pwn); free(m->pwv);
+    free(m);
+}
+
+void vo_geometry(const vo_mesh *m, double *cc, double *vc, double *cf, double *sf)
+{
+    int i;
+    for (i = 0; i < m->nc; i++) {
+        if (cc) { cc[i] = m->cc[i].x; cc[m->nc + i] = m->cc[i].y; cc[2 * m->nc + i] = m->cc[i].z; }
+        if (vc) vc[i] = m->vc[i];
+    }
+    for (i = 0; i < m->nf; i++) {
+        if (cf) { cf[i] = m->cf[i].x; cf[m->nf + i] = m->cf[i].y; cf[2 * m->nf + i] = m->cf[i].z; }
+        if (sf) { sf[i] = m->sf[i].x; sf[m->nf + i] = m->sf[i].y; sf[2 * m->nf + i] = m->sf[i].z; }
+    }
+}
+
+/* R7: the flux stencil of a face is every cell that shares a point with it
+ * (point and edge neighbours, Sec. 2.3), listed in ascending order. */
+int vo_stencil(const vo_mesh *m, int f, int *out, int cap)
+{
+    int k = 0, i, j, u = 0;
+    int buf[1024];
+    for (i = m->fptr[f]; i < m->fptr[f + 1]; i++) {
+        int p = m->fpts[i];
+        for (j = m->pptr[p]; j < m->pptr[p + 1]; j++)
+            if (k < 1024) buf[k++] = m->pcell[j];
+    }
+    qsort(buf, (size_t)k, sizeof(int), cmp_int);
+    for (i = 0; i < k; i++)
+        if (i == 0 || buf[i] != buf[i - 1]) {
+            if (u < cap) out[u] = buf[i];
+            u++;
+        }
+    return u;
+}
+
+/* ---------------------------------------------------- A1: NAG gradient */
+static double point_value(const vo_mesh *m, int p, const double *phi_c)
+{
+    double s = 0.0;
+    int j;
+    for (j = m->pptr[p]; j < m->pptr[p + 1]; j++) s += m->w[j] * phi_c[m->pcell[j]];
+    return s; /* Eq. idwpointphi */
+}
+
+void vo_point_interp(const vo_mesh *m, const double *phi_c, double *phi_p)
+{
+    int p;
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < m->np; p++) phi_p[p] = point_value(m, p, phi_c);
+}
+
+static v3 nag_gradient_cell(const vo_mesh *m, int c, const double *alpha)
+{
+    v3 g = mk(0, 0, 0);
+    int i;
+    for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+        int f = m->cface[i], n = fn(m, f), k;
+        double phi1 = 0.0, sa = 0.0, sp = 0.0;
+        double val[64];
+        for (k = 0; k < n; k++) val[k] = point_value(m, m->fpts[m->fptr[f] + k], alpha);
+        for (k = 0; k < n; k++) phi1 += val[k];
+        phi1 /= n; /* initial face value: algebraic mean of the face points */
+        for (k = 0; k < n; k++) {
+            /* triangle (c_f, p_k, p_k+1): area weight and averaged value */
+            v3 a = sub(fp(m, f, k), m->cf[f]), b = sub(fp(m, f, (k + 1) % n), m->cf[f]);
+            double At = 0.5 * norm(cross(a, b));
+            double pt = (phi1 + val[k] + val[(k + 1) % n]) / 3.0;
+            sa += At;
+            sp += At * pt;
+        }
+        /* Gauss theorem: owner faces add, neighbour faces subtract (Eq. own-nei) */
+        if (m->own[f] == c) g = add(g, scl(m->sf[f], sp / sa));
+        else g = sub(g, scl(m->sf[f], sp / sa));
+    }
+    return scl(g, 1.0 / m->vc[c]);
+}
+
+void vo_nag_gradient(const vo_mesh *m, const double *alpha, int n_sel, const int *sel, double *grad)
+{
+    int k, nn = sel ? n_sel : m->nc;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (k = 0; k < nn; k++) {
+        int c = sel ? sel[k] : k;
+        v3 g = nag_gradient_cell(m, c, alpha);
+        grad[c] = g.x; grad[m->nc + c] = g.y; grad[2 * m->nc + c] = g.z;
+    }
+}
+
+/* ---------------------------------------- clipping and capping (Sec. 2.1) */
+#define MAXF 12
+#define MAXV 16
+typedef struct {
+    int nf;
+    int nv[MAXF];
+    v3 v[MAXF][MAXV];
+} poly;
+
+static void poly_tet(poly *P, v3 a, v3 b, v3 c, v3 d)
+{
+    if (tetvol(a, b, c, d) < 0) { v3 t = b; b = c; c = t; }
+    /* faces oriented counter-clockwise seen from outside */
+    P->nf = 4;
+    P->nv[0] = 3; P->v[0][0] = a; P->v[0][1] = c; P->v[0][2] = b;
+    P->nv[1] = 3; P->v[1][0] = a; P->v[1][1] = b; P->v[1][2] = d;
+    P->nv[2] = 3; P->v[2][0] = a; P->v[2][1] = d; P->v[2][2] = c;
+    P->nv[3] = 3; P->v[3][0] = b; P->v[3][1] = c; P->v[3][2] = d;
+}
+
+static double poly_volume(const poly *P)
+{
+    double V = 0.0;
+    int f, i;
+    v3 o;
+    if (P->nf == 0) return 0.0;
+    o = P->v[0][0];
+    for (f = 0; f < P->nf; f++)
+        for (i = 1; i + 1 < P->nv[f]; i++) V += tetvol(o, P->v[f][0], P->v[f][i], P->v[f][i + 1]);
+    return V;
+}
+
+static int same(v3 a, v3 b) { return a.x == b.x && a.y == b.y && a.z == b.z; }
+
+/* Keep the part of P with n.x <= d.  Each face is clipped; the cut points
+ * (edge crossings and vertices lying on the plane) are gathered, duplicates
+ * dropped, and the cap face is added with its points ordered by the angle they
+ * make about the cap centre (insertion sort).  Returns 0 with the result in Q,
+ * 1 when no point of P is outside (P is the result), -1 on overflow. */
+static int poly_clip(const poly *P, poly *Q, v3 n, double d)
+{
+    v3 cap[4 * MAXV];
+    double sv[MAXF][MAXV], vmax = 0.0, tol;
+    int ncap = 0, f, i, any_out = 0, any_in = 0;
+    /* special cases (Sec. 2.1): a signed distance within a few rounding units of
+     * zero is taken as exactly zero, so that faces lying in the clipping plane
+     * are recognised as such instead of being cut into slivers */
+    for (f = 0; f < P->nf; f++)
+        for (i = 0; i < P->nv[f]; i++) {
+            v3 v = P->v[f][i];
+            if (fabs(v.x) > vmax) vmax = fabs(v.x);
+            if (fabs(v.y) > vmax) vmax = fabs(v.y);
+            if (fabs(v.z) > vmax) vmax = fabs(v.z);
+        }
+    tol = 1e-14 * (2.0 * norm(n) * vmax + fabs(d));
+    for (f = 0; f < P->nf; f++)
+        for (i = 0; i < P->nv[f]; i++) {
+            double s = dot(n, P->v[f][i]) - d;
+            if (fabs(s) <= tol) s = 0.0;
+            sv[f][i] = s;
+            if (s > 0) any_out = 1; else any_in = 1;
+        }
+    if (!any_out) return 1; /* nothing outside: P is unchanged */
+    Q->nf = 0;
+    if (!any_in) return 0;
+    for (f = 0; f < P->nf; f++) {
+        int k = P->nv[f], o = 0;
+        v3 buf[MAXV];
+        for (i = 0; i < k; i++) {
+            v3 a = P->v[f][i], b = P->v[f][(i + 1) % k];
+            double sa = sv[f][i], sb = sv[f][(i + 1) % k];
+            if (sa <= 0) {
+                if (o >= MAXV) return -1;
+                buf[o++] = a;
+                if (sa == 0) { if (ncap >= 4 * MAXV) return -1; cap[ncap++] = a; }
+            }
+            if ((sa < 0 && sb > 0) || (sa > 0 && sb < 0)) {
+                /* interpolate from the inside end so both faces of an edge agree */
+                v3 pi = sa < 0 ? a : b, po = sa < 0 ? b : a;
+                double si = sa < 0 ? sa : sb, so = sa < 0 ? sb : sa;
+                v3 x = add(pi, scl(sub(po, pi), si / (si - so)));
+                if (o >= MAXV || ncap >= 4 * MAXV) return -1;
+                buf[o++] = x;
+                cap[ncap++] = x;
+            }
+        }
+        if (o >= 3) {
+            if (Q->nf >= MAXF) return -1;
+            Q->nv[Q->nf] = o;
+            for (i = 0; i < o; i++) Q->v[Q->nf][i] = buf[i];
+            Q->nf++;
+        }
+    }
+    {
+        v3 u[4 * MAXV], c = mk(0, 0, 0), e1, e2;
+        double ang[4 * MAXV];
+        int nu = 0, j;
+        for (i = 0; i < ncap; i++) {
+            int dup = 0;
+            for (j = 0; j < nu; j++) if (same(u[j], cap[i])) { dup = 1; break; }
+            if (!dup) u[nu++] = cap[i];
+        }
+        if (nu >= 3) {
+            for (i = 0; i < nu; i++) c = add(c, u[i]);
+            c = scl(c, 1.0 / nu);
+            e1 = sub(u[0], c);
+            if (norm(e1) == 0.0) e1 = sub(u[1], c);
+            e2 = cross(n, e1);
+            for (i = 0; i < nu; i++) {
+                v3 r = sub(u[i], c);
+                ang[i] = atan2(dot(r, e2), dot(r, e1));
+            }
+            for (i = 1; i < nu; i++) { /* insertion sort by angle */
+                double a = ang[i];
+                v3 p = u[i];
+                j = i - 1;
+                while (j >= 0 && ang[j] > a) { ang[j + 1] = ang[j]; u[j + 1] = u[j]; j--; }
+                ang[j + 1] = a; u[j + 1] = p;
+            }
+            if (Q->nf >= MAXF || nu > MAXV) return -1;
+            Q->nv[Q->nf] = nu;
+            for (i = 0; i < nu; i++) Q->v[Q->nf][i] = u[i];
+            Q->nf++;
+        }
+    }
+    return 0;
+}
+
+/* |tet ^ {x : n_k.x <= d_k, k < n_planes}| by repeated clipping (Sec. 2.1) */
+static double tet_clip(v3 a, v3 b, v3 c, v3 d, int np, const v3 *n, const double *dd, int *st)
+{
+    poly A, B;
+    poly *src = &A, *dst = &B, *t;
+    int k;
+    poly_tet(&A, a, b, c, d);
+    for (k = 0; k < np; k++) {
+        int r = poly_clip(src, dst, n[k], dd[k]);
+        if (r < 0) { if (st) *st |= VO_ST_CLIP_OVERFLOW; return 0.0; }
+        if (r == 1) continue;
+        t = src; src = dst; dst = t;
+        if (src->nf == 0) return 0.0;
+    }
+    return poly_volume(src);
+}
+
+double vo_tet_clip_volume(const double *t, int n_planes, const double *pl)
+{
+    v3 n[16];
+    double dd[16];
+    int k;
+    for (k = 0; k < n_planes && k < 16; k++) { n[k] = mk(pl[4 * k], pl[4 * k + 1], pl[4 * k + 2]); dd[k] = pl[4 * k + 3]; }
+    return tet_clip(mk(t[0], t[1], t[2]), mk(t[3], t[4], t[5]), mk(t[6], t[7], t[8]),
+                    mk(t[9], t[10], t[11]), n_planes, n, dd, NULL);
+}
+
+double vo_signed_tet_volume(const double *t)
+{
+    return tetvol(mk(t[0], t[1], t[2]), mk(t[3], t[4], t[5]), mk(t[6], t[7], t[8]), mk(t[9], t[10], t[11]));
+}
+
+/* R1: cell c is the union of the tetrahedra (c_c, outward face triangle). */
+static int cell_tets(const vo_mesh *m, int c, v3 (*K)[4], int cap)
+{
+    int i, k = 0;
+    for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+        int f = m->cface[i], t;
+        for (t = 0; t < ntri(m, f); t++) {
+            v3 T[3];
+            face_tri(m, f, t, T);
+            if (k >= cap) return -1;
+            K[k][0] = m->cc[c];
+            K[k][1] = T[0];
+            if (m->own[f] == c) { K[k][2] = T[1]; K[k][3] = T[2]; }
+            else { K[k][2] = T[2]; K[k][3] = T[1]; }
+            k++;
+        }
+    }
+    return k;
+}
+
+/* outward face planes of a positively oriented tetrahedron: n.x <= d inside */
+static void tet_planes(v3 *K, v3 *n, double *d)
+{
+    v3 a = K[0], b = K[1], c = K[2], e = K[3];
+    if (tetvol(a, b, c, e) < 0) { v3 t = b; b = c; c = t; }
+    n[0] = cross(sub(c, a), sub(b, a)); d[0] = dot(n[0], a);
+    n[1] = cross(sub(b, a), sub(e, a)); d[1] = dot(n[1], a);
+    n[2] = cross(sub(e, a), sub(c, a)); d[2] = dot(n[2], a);
+    n[3] = cross(sub(c, b), sub(e, b)); d[3] = dot(n[3], b);
+}
+
+#define MAXK 256
+
+double vo_cut_volume(const vo_mesh *m, int c, const double nn[3], double d)
+{
+    v3 K[MAXK][4], n = mk(nn[0], nn[1], nn[2]);
+    int nk = cell_tets(m, c, K, MAXK), k;
+    double V = 0.0;
+    for (k = 0; k < nk; k++) V += tet_clip(K[k][0], K[k][1], K[k][2], K[k][3], 1, &n, &d, NULL);
+    return V;
+}
+
+/* ------------------------------------ A2 + A3: reconstruction (Alg. 1) */
+#define POS_TOL 1e-13
+#define POS_MAXIT 100
+
+static int position_cell(const vo_mesh *m, int c, double alpha, v3 n, double *dout)
+{
+    /* fill level g(d) = |C ^ {n.x <= d}|/V - alpha rises monotonically from -alpha
+     * at d_min to 1-alpha at d_max (Sec. 2.2.2) */
+    double dmin = 1e300, dmax = -1e300, a, b, x0, g0, x1, g1, x = 0.0, gx = 0.0;
+    double nn[3] = {n.x, n.y, n.z};
+    int i, it = 0, bisect = 0;
+    for (i = m->cpptr[c]; i < m->cpptr[c + 1]; i++) {
+        double s = dot(n, m->P[m->cpt[i]]);
+        if (s < dmin) dmin = s;
+        if (s > dmax) dmax = s;
+    }
+    a = dmin; b = dmax;
+    x0 = a; g0 = -alpha; x1 = b; g1 = 1.0 - alpha;
+    while (it < POS_MAXIT) {
+        if (!bisect) {
+            /* secant through the last two arguments; it has diverged when the new
+             * argument leaves the search interval -> bisection from then on */
+            x = x1 - g1 * (x1 - x0) / (g1 - g0);
+            if (!(x > a && x < b)) bisect = 1;
+        }
+        if (bisect) x = 0.5 * (a + b);
+        gx = vo_cut_volume(m, c, nn, x) / m->vc[c] - alpha;
+        it++;
+        if (gx < 0) a = x; else b = x;
+        x0 = x1; g0 = g1; x1 = x; g1 = gx;
+        if (fabs(gx) <= POS_TOL) break;
+        if (b - a <= 1e-15 * (dmax - dmin)) break;
+    }
+    *dout = x;
+    return it;
+}
+
+int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel, const int *sel,
+                   double *nout, double *dout, unsigned char *flags, int *iters)
+{
+    int k, nn = sel ? n_sel : m->nc, st = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : st)
+    for (k = 0; k < nn; k++) {
+        int c = sel ? sel[k] : k, it = 0;
+        double a = alpha[c], d = 0.0;
+        unsigned char fl = 0;
+        v3 n = mk(0, 0, 0);
+        if (a >= 1.0 - eps) fl = VO_FULL;
+        else if (a > eps) {
+            v3 g = nag_gradient_cell(m, c, alpha);
+            double gm = norm(g), hc = cbrt(m->vc[c]);
+            fl = VO_INTERFACE;
+            /* R4: a vanishing gradient leaves the cell unoriented */
+            if (gm * hc > 1e-12) {
+                n = scl(g, -1.0 / gm); /* R11: points out of the phase */
+                fl |= VO_ORIENTED;
+                it = position_cell(m, c, a, n, &d);
+                if (it >= POS_MAXIT) st |= VO_ST_POS_NOT_CONVERGED;
+            }
+        }
+        if (nout) { nout[c] = n.x; nout[m->nc + c] = n.y; nout[2 * m->nc + c] = n.z; }
+        if (dout) dout[c] = d;
+        if (flags) flags[c] = fl;
+        if (iters) iters[c] = it;
+    }
+    return st;
+}
+
+/* ------------------------------------------- A4: point velocity + sweep */
+void vo_point_velocity(const vo_mesh *m, const double *Uc, double *Up)
+{
+    int p;
+#pragma omp parallel for schedule(static)
+    for (p = 0; p < m->np; p++) {
+        v3 u = mk(point_value(m, p, Uc), point_value(m, p, Uc + m->nc),
+                  point_value(m, p, Uc + 2 * m->nc));
+        if (m->pwn[p] == 1) {
+            v3 n = m->pwv[2 * p];
+            u = sub(u, scl(n, dot(u, n)));
+        } else if (m->pwn[p] == 2) {
+            v3 t = cross(m->pwv[2 * p], m->pwv[2 * p + 1]);
+            t = scl(t, 1.0 / norm(t));
+            u = scl(t, dot(u, t));
+        } else if (m->pwn[p] >= 3) {
+            u = mk(0, 0, 0);
+        }
+        Up[p] = u.x; Up[m->np + p] = u.y; Up[2 * m->np + p] = u.z;
+    }
+}
+
+/* ----------------------------------------------- A5: flux polyhedra */
+/* Tetrahedral decomposition of the flux polyhedron (reading R5): every face
+ * triangle (a0,a1,a2) is swept to (b0,b1,b2), b = a - w (Eq. sweep).  With a
+ * sweep factor lambda >= 0 the displacement is w = lambda*U_p*dt, the swept face
+ * centre moving with the mean of the point displacements.  lambda < 0 marks the
+ * normal-sweep fallback: every point moves by w = -lambda*(F_f/|S_f|^2) S_f dt,
+ * a uniform translation whose swept volume is exactly -lambda*F_f*dt.
+ * The triangular prism is split into three tetrahedra after ordering its
+ * vertices by key (face centre first, then global point index), so that a side
+ * quad shared by two prisms is split along the same diagonal in both.  Each
+ * tetrahedron carries the sign that makes the sum the signed swept volume,
+ * positive for a sweep against S_f (flux from owner to neighbour). */
+typedef struct { v3 v[4]; double s; } stet;
+
+static v3 point_disp(const vo_mesh *m, int p, const double *Up, double dt, double lambda, v3 wn)
+{
+    if (lambda < 0) return wn;
+    return scl(mk(Up[p], Up[m->np + p], Up[2 * m->np + p]), dt * lambda);
+}
+
+static int face_prism_tets(const vo_mesh *m, int f, const double *Up, double F, double dt,
+                           double lambda, stet *out)
+{
+    int n = fn(m, f), t, q = 0, i;
+    v3 wc = mk(0, 0, 0), wn = mk(0, 0, 0);
+    const int *p = m->fpts + m->fptr[f];
+    if (lambda < 0) wn = scl(m->sf[f], -lambda * F * dt / dot(m->sf[f], m->sf[f]));
+    for (i = 0; i < n; i++) wc = add(wc, point_disp(m, p[i], Up, dt, lambda, wn));
+    wc = scl(wc, 1.0 / n);
+    for (t = 0; t < ntri(m, f); t++) {
+        v3 a[3], w[3], b[3];
+        long key[3];
+        int id[3] = {0, 1, 2}, parity = 1, j, k;
+        if (n == 3) {
+            for (j = 0; j < 3; j++) {
+                a[j] = m->P[p[j]];
+                w[j] = point_disp(m, p[j], Up, dt, lambda, wn);
+                key[j] = p[j];
+            }
+        } else {
+            int j0 = p[t], j1 = p[(t + 1) % n];
+            a[0] = m->cf[f]; w[0] = wc; key[0] = -1;
+            a[1] = m->P[j0]; w[1] = point_disp(m, j0, Up, dt, lambda, wn); key[1] = j0;
+            a[2] = m->P[j1]; w[2] = point_disp(m, j1, Up, dt, lambda, wn); key[2] = j1;
+        }
+        for (j = 0; j < 3; j++) b[j] = sub(a[j], w[j]);
+        for (j = 1; j < 3; j++) /* sort vertex ids by key, tracking permutation parity */
+            for (k = j; k > 0 && key[id[k]] < key[id[k - 1]]; k--) {
+                int tmp = id[k]; id[k] = id[k - 1]; id[k - 1] = tmp; parity = -parity;
+            }
+        {
+            v3 A0 = a[id[0]], A1 = a[id[1]], A2 = a[id[2]];
+            v3 B0 = b[id[0]], B1 = b[id[1]], B2 = b[id[2]];
+            stet *o = out + q;
+            o[0].v[0] = A0; o[0].v[1] = A1; o[0].v[2] = A2; o[0].v[3] = B2;
+            o[1].v[0] = A0; o[1].v[1] = A1; o[1].v[2] = B2; o[1].v[3] = B1;
+            o[2].v[0] = A0; o[2].v[1] = B0; o[2].v[2] = B1; o[2].v[3] = B2;
+            for (j = 0; j < 3; j++) o[j].s = -parity * tetvol(o[j].v[0], o[j].v[1], o[j].v[2], o[j].v[3]);
+            q += 3;
+        }
+    }
+    return q;
+}
+
+double vo_swept_volume(const vo_mesh *m, int f, const double *Up, double F, double dt, double lambda)
+{
+    stet T[3 * 64];
+    int q = face_prism_tets(m, f, Up, F, dt, lambda, T), i;
+    double V = 0.0;
+    for (i = 0; i < q; i++) V += T[i].s; /* Eq. V_fS */
+    return V;
+}
+
+static double swept_abs(const vo_mesh *m, int f, const double *Up, double dt, double lambda)
+{
+    stet T[3 * 64];
+    int q = face_prism_tets(m, f, Up, 0.0, dt, lambda, T), i;
+    double V = 0.0;
+    for (i = 0; i < q; i++) V += fabs(T[i].s);
+    return V;
+}
+
+#define CORR_TOL 1e-14
+#define CORR_MAXIT 100
+#define CORR_LMAX 2.0
+#define CORR_NSAMP 16
+
+/* Reading R5: the swept end points move along their stream vectors by a common
+ * factor lambda, and the secant method drives r(lambda) = V_f(lambda) - F_f dt
+ * to zero (Eq. VF, Sec. 2.3).  The root taken is the one in the first of the
+ * intervals [k, k+1]*LMAX/NSAMP (k = 0..NSAMP-1) at whose ends r changes sign;
+ * inside it the secant starts from the interval ends, and an iterate that
+ * leaves the current bracket is replaced by bisection (the safeguard of
+ * Alg. 1).  When no interval brackets a root (point velocities nearly
+ * tangential to the face disagree with F_f) the face takes the normal-sweep
+ * fallback, returned as lambda = -1.  Returns the secant iterations. */
+static int correct_face(const vo_mesh *m, int f, const double *Up, double F, double dt, double *lam)
+{
+    double tau = F * dt, lo = 0.0, hi = 0.0, rlo = -tau, rhi = 0.0, x0, r0, x1, r1, x, r, scale;
+    int it = 0, k, bisect = 0, found = 0;
+    if (tau == 0.0) { *lam = 0.0; return 0; }
+    for (k = 1; k <= CORR_NSAMP; k++) {
+        double lk = k * (CORR_LMAX / CORR_NSAMP);
+        double rk = vo_swept_volume(m, f, Up, F, dt, lk) - tau;
+        if (rk == 0.0) { *lam = lk; return 0; }
+        if ((rk > 0) != (rlo > 0)) { hi = lk; rhi = rk; found = 1; break; }
+        lo = lk; rlo = rk;
+    }
+    if (!found) { *lam = -1.0; return 0; }
+    x0 = lo; r0 = rlo; x1 = hi; r1 = rhi; x = hi;
+    while (it < CORR_MAXIT) {
+        if (!bisect) {
+            x = x1 - r1 * (x1 - x0) / (r1 - r0);
+            if (!(x > lo && x < hi)) bisect = 1;
+        }
+        if (bisect) x = 0.5 * (lo + hi);
+        r = vo_swept_volume(m, f, Up, F, dt, x) - tau;
+        scale = swept_abs(m, f, Up, dt, x);
+        if (fabs(tau) > scale) scale = fabs(tau);
+        it++;
+        if ((r > 0) == (rhi > 0)) { hi = x; rhi = r; } else { lo = x; rlo = r; }
+        x0 = x1; r0 = r1; x1 = x; r1 = r;
+        if (fabs(r) <= CORR_TOL * scale) break;
+        if (hi - lo <= 1e-15 * hi) break;
+    }
+    *lam = x;
+    return it;
+}
+
+int vo_correct_flux(const vo_mesh *m, const double *Up, const double *F, double dt, int n_sel,
+                    const int *sel, double *lambda, int *iters)
+{
+    int k, nn = sel ? n_sel : m->nf, st = 0;
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : st)
+    for (k = 0; k < nn; k++) {
+        int f = sel ? sel[k] : k;
+        double l = 0.0;
+        int it = correct_face(m, f, Up, F[f], dt, &l);
+        if (it >= CORR_MAXIT) st |= VO_ST_CORR_NOT_CONVERGED;
+        lambda[f] = l;
+        if (iters) iters[f] = it;
+    }
+    return st;
+}
+
+/* ---------------------------------------------------- A6: phase flux */
+static void aabb_tet(v3 *v, v3 *lo, v3 *hi)
+{
+    int i;
+    *lo = v[0]; *hi = v[0];
+    for (i = 1; i < 4; i++) {
+        if (v[i].x < lo->x) lo->x = v[i].x;
+        if (v[i].y < lo->y) lo->y = v[i].y;
+        if (v[i].z < lo->z) lo->z = v[i].z;
+        if (v[i].x > hi->x) hi->x = v[i].x;
+        if (v[i].y > hi->y) hi->y = v[i].y;
+        if (v[i].z > hi->z) hi->z = v[i].z;
+    }
+}
+static int disjoint(v3 alo, v3 ahi, v3 blo, v3 bhi)
+{
+    return ahi.x < blo.x || bhi.x < alo.x || ahi.y < blo.y || bhi.y < alo.y || ahi.z < blo.z || bhi.z < alo.z;
+}
+
+/* R9: a face is trivial when every stencil cell is empty (alpha <= eps) or
+ * every stencil cell is full (alpha >= 1-eps). */
+void vo_classify_faces(const vo_mesh *m, const double *alpha, double eps, unsigned char *cls)
+{
+    int f;
+#pragma omp parallel for schedule(dynamic, 1024)
+    for (f = 0; f < m->nf; f++) {
+        int all_e = 1, all_f = 1, i, j;
+        for (i = m->fptr[f]; i < m->fptr[f + 1]; i++) {
+            int p = m->fpts[i];
+            for (j = m->pptr[p]; j < m->pptr[p + 1]; j++) {
+                double a = alpha[m->pcell[j]];
+                if (!(a <= eps)) all_e = 0;
+                if (!(a >= 1.0 - eps)) all_f = 0;
+            }
+        }
+        cls[f] = all_e ? 0 : (all_f ? 1 : 2);
+    }
+}
+
+/* sum over the stencil of the signed |T ^ K ^ H| pieces (Eqs. S'_f, S''_f) */
+static double face_phase_volume(const vo_mesh *m, int f, const double *alpha, double eps,
+                                const double *nrm, const double *dd, const unsigned char *flags,
+                                const double *Up, double F, double dt, double lambda, int coverage,
+                                int *st)
+{
+    stet T[3 * 64];
+    int sten[1024];
+    v3 K[MAXK][4];
+    int q = face_prism_tets(m, f, Up, F, dt, lambda, T);
+    int ns = vo_stencil(m, f, sten, 1024), t, s, k;
+    double acc = 0.0;
+    for (t = 0; t < q; t++) {
+        v3 tlo, thi;
+        double sg;
+        if (T[t].s == 0.0) continue;
+        sg = T[t].s > 0 ? 1.0 : -1.0;
+        aabb_tet(T[t].v, &tlo, &thi);
+        for (s = 0; s < ns; s++) {
+            int c = sten[s], nk;
+            double a = coverage ? 1.0 : alpha[c], wgt = 1.0;
+            int use_h = 0;
+            v3 hn = mk(0, 0, 0);
+            double hd = 0.0;
+            if (!coverage) {
+                if (a <= eps) continue; /* empty cell carries no phase */
+                if (flags[c] & VO_INTERFACE) {
+                    if (flags[c] & VO_ORIENTED) {
+                        use_h = 1;
+                        hn = mk(nrm[c], nrm[m->nc + c], nrm[2 * m->nc + c]);
+                        hd = dd[c];
+                    } else wgt = a; /* R4: unoriented mixed cell is homogeneous */
+                }
+            }
+            nk = cell_tets(m, c, K, MAXK);
+            for (k = 0; k < nk; k++) {
+                v3 klo, khi, pn[5];
+                double pd[5], v;
+                aabb_tet(K[k], &klo, &khi);
+                if (disjoint(tlo, thi, klo, khi)) continue;
+                tet_planes(K[k], pn, pd);
+                if (use_h) { pn[4] = hn; pd[4] = hd; }
+                v = tet_clip(T[t].v[0], T[t].v[1], T[t].v[2], T[t].v[3], use_h ? 5 : 4, pn, pd, st);
+                acc += sg * wgt * v;
+            }
+        }
+    }
+    return acc;
+}
+
+double vo_stencil_coverage(const vo_mesh *m, int f, const double *Up, double F, double dt,
+                           double lambda)
+{
+    int st = 0;
+    return face_phase_volume(m, f, NULL, 0.0, NULL, NULL, NULL, Up, F, dt, lambda, 1, &st);
+}
+
+static double phase_flux_face(const vo_mesh *m, int f, const unsigned char *cls, const double *alpha,
+                              double eps, const double *n, const double *d,
+                              const unsigned char *flags, const double *Up, const double *F,
+                              const double *lambda, double dt, int *st)
+{
+    if (F[f] == 0.0) return 0.0;
+    /* R2: a boundary face with inflow brings in the empty exterior */
+    if (f >= m->ni && F[f] < 0.0) return 0.0;
+    if (cls[f] == 0) return 0.0;
+    if (cls[f] == 1) return F[f] * dt; /* Eq. vol-phase-flux with alpha_f = 1 */
+    return face_phase_volume(m, f, alpha, eps, n, d, flags, Up, F[f], dt, lambda[f], 0, st);
+}
+
+int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const double *n,
+                  const double *d, const unsigned char *flags, const double *Up, const double *F,
+                  const double *lambda, double dt, int n_sel, const int *sel, double *Valpha)
+{
+    int k, nn = sel ? n_sel : m->nf, st = 0;
+    unsigned char *cls = (unsigned char *)malloc((size_t)m->nf);
+    vo_classify_faces(m, alpha, eps, cls);
+#pragma omp parallel for schedule(dynamic, 16) reduction(| : st)
+    for (k = 0; k < nn; k++) {
+        int f = sel ? sel[k] : k, s1 = 0;
+        Valpha[f] = phase_flux_face(m, f, cls, alpha, eps, n, d, flags, Up, F, lambda, dt, &s1);
+        st |= s1;
+    }
+    free(cls);
+    return st;
+}
+
+/* ---------------------------------------------------------- A7: update */
+#define BOUND_PASSES 8
+#define BOUND_TOL 1e-15   /* violations at round-off scale are left alone */
+#define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
+
+/* Reading R10: a conservative bounding pass.  Excess above 1 (deficit below 0)
+ * is handed to face neighbours in proportion to their free (filled) volume;
+ * each receiver offers its capacity divided by its number of sources, so no
+ * receiver can be pushed out of [0,1].  Written as gathers, repeated a fixed
+ * number of passes at most. */
+static int bound_pass(const vo_mesh *m, double *alpha)
+{
+    int nc = m->nc, c, any = 0;
+    double *e = (double *)calloc((size_t)nc, sizeof(double)), *u = (double *)calloc((size_t)nc, sizeof(double));
+    double *op = (double *)calloc((size_t)nc, sizeof(double)), *om = (double *)calloc((size_t)nc, sizeof(double));
+    double *Cp = (double *)calloc((size_t)nc, sizeof(double)), *Cm = (double *)calloc((size_t)nc, sizeof(double));
+    double *give = (double *)calloc((size_t)nc, sizeof(double)), *take = (double *)calloc((size_t)nc, sizeof(double));
+    for (c = 0; c < nc; c++) {
+        double a = alpha[c];
+        if (a > 1.0 + BOUND_TOL) { e[c] = (a - 1.0) * m->vc[c]; any = 1; }
+        if (a < -BOUND_TOL) { u[c] = -a * m->vc[c]; any = 1; }
+    }
+    if (any) {
+#pragma omp parallel for schedule(static)
+        for (c = 0; c < nc; c++) {
+            int i, sp = 0, sm = 0;
+            double a = alpha[c];
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+                int f = m->cface[i], nb;
+                if (f >= m->ni) continue;
+                nb = m->own[f] == c ? m->nei[f] : m->own[f];
+                if (e[nb] > 0) sp++;
+                if (u[nb] > 0) sm++;
+            }
+            op[c] = (a >= 0.0 && a < 1.0) ? (1.0 - a) * m->vc[c] / (sp > 0 ? sp : 1) : 0.0;
+            om[c] = (a > 0.0 && a <= 1.0) ? a * m->vc[c] / (sm > 0 ? sm : 1) : 0.0;
+        }
+#pragma omp parallel for schedule(static)
+        for (c = 0; c < nc; c++) {
+            int i;
+            double sp = 0.0, sm = 0.0;
+            if (e[c] == 0.0 && u[c] == 0.0) continue;
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+                int f = m->cface[i], nb;
+                if (f >= m->ni) continue;
+                nb = m->own[f] == c ? m->nei[f] : m->own[f];
+                sp += op[nb];
+                sm += om[nb];
+            }
+            Cp[c] = sp; Cm[c] = sm;
+            give[c] = e[c] < sp ? e[c] : sp;
+            take[c] = u[c] < sm ? u[c] : sm;
+        }
+#pragma omp parallel for schedule(static)
+        for (c = 0; c < nc; c++) {
+            int i;
+            double rec = 0.0, out = 0.0;
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+                int f = m->cface[i], nb;
+                if (f >= m->ni) continue;
+                nb = m->own[f] == c ? m->nei[f] : m->own[f];
+                if (give[nb] > 0.0) rec += give[nb] * (op[c] / Cp[nb]);
+                if (take[nb] > 0.0) out += take[nb] * (om[c] / Cm[nb]);
+            }
+            if (give[c] != 0.0 || take[c] != 0.0 || rec != 0.0 || out != 0.0)
+                alpha[c] = (alpha[c] * m->vc[c] - give[c] + take[c] + rec - out) / m->vc[c];
+        }
+    }
+    free(e); free(u); free(op); free(om); free(Cp); free(Cm); free(give); free(take);
+    return any;
+}
+
+int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, double *stats)
+{
+    int c, st = 0, f;
+    double mb = 0.0, ma = 0.0, mn = 1e300, mx = -1e300, bo = 0.0;
+    for (c = 0; c < m->nc; c++) mb += m->vc[c] * alpha[c];
+#pragma omp parallel for schedule(static)
+    for (c = 0; c < m->nc; c++) {
+        double s = 0.0;
+        int i;
+        for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+            int g = m->cface[i];
+            if (m->own[g] == c) s += Va[g]; else s -= Va[g];
+        }
+        alpha[c] = alpha[c] - s / m->vc[c];
+    }
+    for (c = 0; c < m->nc; c++) {
+        if (alpha[c] < mn) mn = alpha[c];
+        if (alpha[c] > mx) mx = alpha[c];
+    }
+    if (stats) { stats[VO_S_MIN_PRE] = mn; stats[VO_S_MAX_PRE] = mx; }
+    if (bound) {
+        int p;
+        for (p = 0; p < BOUND_PASSES; p++)
+            if (!bound_pass(m, alpha)) break;
+        for (c = 0; c < m->nc; c++)
+            if (alpha[c] < -BOUND_FLAG || alpha[c] > 1.0 + BOUND_FLAG) { st |= VO_ST_BOUND_RESIDUAL; break; }
+    }
+    mn = 1e300; mx = -1e300;
+    for (c = 0; c < m->nc; c++) {
+        ma += m->vc[c] * alpha[c];
+        if (alpha[c] < mn) mn = alpha[c];
+        if (alpha[c] > mx) mx = alpha[c];
+    }
+    for (f = m->ni; f < m->nf; f++) bo += Va[f];
+    if (stats) {
+        stats[VO_S_MASS_BEFORE] = mb; stats[VO_S_MASS_AFTER] = ma;
+        stats[VO_S_MIN_POST] = mn; stats[VO_S_MAX_POST] = mx; stats[VO_S_BOUNDARY_OUT] = bo;
+    }
+    return st;
+}
+
+int vo_advect(const vo_mesh *m, double *alpha, const double *Uc, const double *F, double dt,
+              double eps, int bound, double *stats)
+{
+    int nc = m->nc, nf = m->nf, st = 0, f, c, nb = 0, ni = 0, *band, *it, maxit = 0;
+    unsigned char *cls = (unsigned char *)malloc((size_t)nf), *flags = (unsigned char *)malloc((size_t)nc);
+    double *n = (double *)calloc(3 * (size_t)nc, sizeof(double)), *d = (double *)calloc((size_t)nc, sizeof(double));
+    double *Up = (double *)malloc(sizeof(double) * 3 * (size_t)m->np);
+    double *lam = (double *)calloc((size_t)nf, sizeof(double)), *Va = (double *)calloc((size_t)nf, sizeof(double));
+    int *pit = (int *)calloc((size_t)nc, sizeof(int));
+    band = (int *)malloc(sizeof(int) * (size_t)(nf > 0 ? nf : 1));
+    it = (int *)calloc((size_t)(nf > 0 ? nf : 1), sizeof(int));
+    vo_classify_faces(m, alpha, eps, cls);
+    for (f = 0; f < nf; f++)
+        if (cls[f] == 2 && F[f] != 0.0 && !(f >= m->ni && F[f] < 0.0)) band[nb++] = f;
+    st |= vo_reconstruct(m, alpha, eps, 0, NULL, n, d, flags, pit);
+    vo_point_velocity(m, Uc, Up);
+    st |= vo_correct_flux(m, Up, F, dt, nb, band, lam, it);
+    st |= vo_phase_flux(m, alpha, eps, n, d, flags, Up, F, lam, dt, 0, NULL, Va);
+    st |= vo_update(m, alpha, Va, bound, stats);
+    if (stats) {
+        int mp = 0;
+        for (c = 0; c < nc; c++) {
+            if (flags[c] & VO_INTERFACE) ni++;
+            if (pit[c] > mp) mp = pit[c];
+        }
+        for (f = 0; f < nb; f++) if (it[band[f]] > maxit) maxit = it[band[f]];
+        stats[VO_S_N_INTERFACE] = ni;
+        stats[VO_S_N_BAND] = nb;
+        stats[VO_S_MAX_POS_IT] = mp;
+        stats[VO_S_MAX_CORR_IT] = maxit;
+        stats[VO_S_STATUS] = st;
+    }
+    free(cls); free(flags); free(n); free(d); free(Up); free(lam); free(Va); free(pit); free(band); free(it);
+    return st;
+}

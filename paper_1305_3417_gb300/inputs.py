@@ -1,0 +1,552 @@
+"""Seeded synthetic inputs for the geometric VoF advection step.
+
+This module builds the data that the method consumes; it computes no step of
+the method itself.  Both the CUDA path and the CPU oracle receive the arrays
+made here, and neither is imported by this module.
+
+* Meshes in the unstructured face-based form the paper describes (Sec. 2: points
+  stored once, a face is an ordered list of point indices whose right-hand
+  normal points from the owner to the neighbour, owner/neighbour per face,
+  internal faces first, then boundary faces with outward normals):
+  uniform and jittered hexahedral boxes, and the Kuhn six-tetrahedra split of
+  a hexahedral lattice.
+* Initial volume fractions: exact disc/rectangle areas on uniform 2D meshes,
+  otherwise a Jacobian-weighted midpoint rule over each cell's trilinear
+  (hexahedron) or affine (tetrahedron) parametrisation.
+* Volumetric face fluxes that are discretely divergence-free (Eq.
+  discretedivergence) by construction: F_f is the circulation of a vector
+  potential around the face's edge loop (Stokes), with one Gauss-Legendre
+  integral per unique edge, so that every edge term enters its two faces with
+  opposite signs.
+* Cell-centred velocities of the analytic fields of the paper's test cases
+  (Sec. 5.2: translation, deformation Eq. deformation-test-case) and of the
+  2D single vortex and solid-body rotation.
+
+Random numbers come from numpy's PCG64 generator seeded per workload.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Callable
+
+import numpy as np
+
+__all__ = [
+    "Mesh", "hex_mesh", "kuhn_tet_mesh", "disc_rect_area", "disc_fraction_2d",
+    "sampled_fraction", "sphere_sdf", "cylinder_sdf", "Field", "translation_field",
+    "deformation_field", "single_vortex_field", "rotation_field",
+    "face_flux_stokes", "cell_velocity", "Workload", "make_workload",
+]
+
+
+@dataclasses.dataclass
+class Mesh:
+    points: np.ndarray      # (n_points, 3) float64
+    face_ptr: np.ndarray    # (n_faces + 1,) int32
+    face_pts: np.ndarray    # (face_ptr[-1],) int32
+    owner: np.ndarray       # (n_faces,) int32
+    neighbour: np.ndarray   # (n_internal,) int32
+    n_cells: int
+    cell_verts: np.ndarray  # (n_cells, 8 or 4) int32 -- generator's own record
+    h: float                # nominal lattice spacing
+    dim: int
+    kind: str
+    shape: tuple = ()
+    wall: np.ndarray | None = None   # (n_faces - n_internal,) uint8: 1 = wall (no normal flow)
+
+    @property
+    def n_points(self) -> int:
+        return int(self.points.shape[0])
+
+    @property
+    def n_faces(self) -> int:
+        return int(self.owner.shape[0])
+
+    @property
+    def n_internal(self) -> int:
+        return int(self.neighbour.shape[0])
+
+    def wall_flags(self) -> np.ndarray:
+        if self.wall is None:
+            return np.ones(self.n_faces - self.n_internal, np.uint8)
+        return np.ascontiguousarray(self.wall, np.uint8)
+
+    def soa_points(self):
+        p = np.ascontiguousarray(self.points.T)
+        return p[0].copy(), p[1].copy(), p[2].copy()
+
+
+# --------------------------------------------------------------------------
+# Hexahedral boxes
+# --------------------------------------------------------------------------
+
+def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = None,
+             dim: int = 3, open_sides: tuple = ()) -> Mesh:
+    """Box [0,lx]x[0,ly]x[0,lz] split into nx*ny*nz hexahedra.
+
+    Boundary faces are walls (no normal flow) except on the sides listed in
+    ``open_sides`` (any of "x-", "x+", "y-", "y+", "z-", "z+").
+
+    ``jitter`` moves every point that lies on no boundary plane by an
+    independent uniform offset in [-jitter*h, jitter*h] per coordinate
+    (h = lx/nx), drawn from PCG64(seed).  With dim=2 the mesh is one cell
+    thick and only x, y of points off the x/y boundary planes are moved.
+    """
+    nx, ny, nz = (int(v) for v in n)
+    lx, ly, lz = (float(v) for v in length)
+    h = lx / nx
+    xs = np.linspace(0.0, lx, nx + 1)
+    ys = np.linspace(0.0, ly, ny + 1)
+    zs = np.linspace(0.0, lz, nz + 1)
+    # point id p(i,j,k) = i + (nx+1)*(j + (ny+1)*k)
+    I, J, K = np.meshgrid(np.arange(nx + 1), np.arange(ny + 1), np.arange(nz + 1), indexing="ij")
+    pid = (I + (nx + 1) * (J + (ny + 1) * K)).astype(np.int64)
+    npts = (nx + 1) * (ny + 1) * (nz + 1)
+    pts = np.empty((npts, 3))
+    pts[pid.ravel(), 0] = xs[I.ravel()]
+    pts[pid.ravel(), 1] = ys[J.ravel()]
+    pts[pid.ravel(), 2] = zs[K.ravel()]
+    if jitter > 0.0:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        if dim == 3:
+            inner = (I > 0) & (I < nx) & (J > 0) & (J < ny) & (K > 0) & (K < nz)
+            ids = np.sort(pid[inner])
+            pts[ids] += rng.uniform(-jitter * h, jitter * h, size=(ids.size, 3))
+        else:
+            inner = (I > 0) & (I < nx) & (J > 0) & (J < ny)
+            ids = np.sort(pid[inner])
+            pts[ids, :2] += rng.uniform(-jitter * h, jitter * h, size=(ids.size, 2))
+
+    def P(i, j, k):
+        return (i + (nx + 1) * (j + (ny + 1) * k)).astype(np.int64)
+
+    def C(i, j, k):
+        return (i + nx * (j + ny * k)).astype(np.int64)
+
+    ci, cj, ck = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    ci, cj, ck = ci.ravel(), cj.ravel(), ck.ravel()
+
+    def xface(i, j, k):      # +x normal at x-plane index i
+        return np.stack([P(i, j, k), P(i, j + 1, k), P(i, j + 1, k + 1), P(i, j, k + 1)], 1)
+
+    def yface(i, j, k):      # +y normal at y-plane index j
+        return np.stack([P(i, j, k), P(i, j, k + 1), P(i + 1, j, k + 1), P(i + 1, j, k)], 1)
+
+    def zface(i, j, k):      # +z normal at z-plane index k
+        return np.stack([P(i, j, k), P(i + 1, j, k), P(i + 1, j + 1, k), P(i, j + 1, k)], 1)
+
+    own, nei, fps = [], [], []
+    m = ci < nx - 1
+    own.append(C(ci[m], cj[m], ck[m])); nei.append(C(ci[m] + 1, cj[m], ck[m]))
+    fps.append(xface(ci[m] + 1, cj[m], ck[m]))
+    m = cj < ny - 1
+    own.append(C(ci[m], cj[m], ck[m])); nei.append(C(ci[m], cj[m] + 1, ck[m]))
+    fps.append(yface(ci[m], cj[m] + 1, ck[m]))
+    m = ck < nz - 1
+    own.append(C(ci[m], cj[m], ck[m])); nei.append(C(ci[m], cj[m], ck[m] + 1))
+    fps.append(zface(ci[m], cj[m], ck[m] + 1))
+    own_i = np.concatenate(own); nei_i = np.concatenate(nei); fp_i = np.concatenate(fps)
+    order = np.lexsort((nei_i, own_i))          # upper-triangular (owner, neighbour) order
+    own_i, nei_i, fp_i = own_i[order], nei_i[order], fp_i[order]
+
+    bown, bfp = [], []
+    # x-, x+, y-, y+, z-, z+ ; reversed point order gives the outward normal on the low side
+    m = ci == 0
+    bown.append(C(ci[m], cj[m], ck[m])); bfp.append(xface(ci[m], cj[m], ck[m])[:, ::-1])
+    m = ci == nx - 1
+    bown.append(C(ci[m], cj[m], ck[m])); bfp.append(xface(ci[m] + 1, cj[m], ck[m]))
+    m = cj == 0
+    bown.append(C(ci[m], cj[m], ck[m])); bfp.append(yface(ci[m], cj[m], ck[m])[:, ::-1])
+    m = cj == ny - 1
+    bown.append(C(ci[m], cj[m], ck[m])); bfp.append(yface(ci[m], cj[m] + 1, ck[m]))
+    m = ck == 0
+    bown.append(C(ci[m], cj[m], ck[m])); bfp.append(zface(ci[m], cj[m], ck[m])[:, ::-1])
+    m = ck == nz - 1
+    bown.append(C(ci[m], cj[m], ck[m])); bfp.append(zface(ci[m], cj[m], ck[m] + 1))
+    bsorted = []
+    wall = []
+    for side, o, f in zip(("x-", "x+", "y-", "y+", "z-", "z+"), bown, bfp):
+        s = np.argsort(o, kind="stable")
+        bsorted.append((o[s], f[s]))
+        wall.append(np.full(o.size, 0 if side in open_sides else 1, np.uint8))
+    b_own = np.concatenate([b[0] for b in bsorted])
+    b_fp = np.concatenate([b[1] for b in bsorted])
+
+    owner = np.concatenate([own_i, b_own]).astype(np.int32)
+    face_pts = np.concatenate([fp_i, b_fp]).reshape(-1).astype(np.int32)
+    face_ptr = (4 * np.arange(owner.size + 1)).astype(np.int32)
+    cell_ids = C(ci, cj, ck)
+    cv = np.empty((nx * ny * nz, 8), np.int64)
+    for t, (a, b, c) in enumerate([(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0),
+                                   (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]):
+        cv[cell_ids, t] = P(ci + a, cj + b, ck + c)
+    return Mesh(pts, face_ptr, face_pts, owner, nei_i.astype(np.int32), nx * ny * nz,
+                cv.astype(np.int32), h, dim, "hex", (nx, ny, nz), np.concatenate(wall))
+
+
+# --------------------------------------------------------------------------
+# Kuhn split of a hexahedral lattice into tetrahedra
+# --------------------------------------------------------------------------
+
+def _tet_signed6(p, t):
+    a, b, c, d = (p[t[:, i]] for i in range(4))
+    return np.einsum("ij,ij->i", b - a, np.cross(c - a, d - a))
+
+
+def kuhn_tet_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0,
+                  seed: int | None = None) -> Mesh:
+    """Each hexahedron of an n^3 lattice split into the six tetrahedra that share
+    its (0,0,0)-(1,1,1) diagonal; the split is conforming across hexahedra.
+    Interior points are jittered as in :func:`hex_mesh`."""
+    base = hex_mesh(n, length, jitter, seed, dim=3)
+    nx, ny, nz = base.shape
+    pts = base.points
+    cv = base.cell_verts.astype(np.int64)       # corners (000,100,110,010,001,101,111,011)
+    corner = {(0, 0, 0): 0, (1, 0, 0): 1, (1, 1, 0): 2, (0, 1, 0): 3,
+              (0, 0, 1): 4, (1, 0, 1): 5, (1, 1, 1): 6, (0, 1, 1): 7}
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+    tets = []
+    for pa in perms:
+        v = [0, 0, 0]
+        path = [corner[tuple(v)]]
+        for ax in pa:
+            v[ax] = 1
+            path.append(corner[tuple(v)])
+        tets.append(cv[:, path])
+    tet = np.stack(tets, 1).reshape(-1, 4)      # hexahedron-major, then permutation
+    vol6 = _tet_signed6(pts, tet)
+    neg = vol6 < 0
+    tet[neg] = tet[neg][:, [0, 2, 1, 3]]
+    if np.any(np.abs(vol6) <= 0):
+        raise ValueError("degenerate tetrahedron in Kuhn split")
+    nt = tet.shape[0]
+    # outward faces of a positively oriented tet (a,b,c,d)
+    loc = np.array([[0, 2, 1], [0, 1, 3], [0, 3, 2], [1, 2, 3]])
+    inst = tet[:, loc].reshape(-1, 3)           # (4*nt, 3)
+    cell_of = np.repeat(np.arange(nt, dtype=np.int64), 4)
+    s = np.sort(inst, axis=1)
+    N = np.int64(pts.shape[0])
+    key = s[:, 0] + N * (s[:, 1] + N * s[:, 2])
+    order = np.argsort(key, kind="stable")
+    ks = key[order]
+    start = np.flatnonzero(np.r_[True, ks[1:] != ks[:-1]])
+    cnt = np.diff(np.r_[start, ks.size])
+    if np.any(cnt > 2):
+        raise ValueError("non-manifold face in tetrahedral mesh")
+    pair = start[cnt == 2]
+    i0, i1 = order[pair], order[pair + 1]
+    c0, c1 = cell_of[i0], cell_of[i1]
+    own_inst = np.where(c0 < c1, i0, i1)
+    own = np.minimum(c0, c1)
+    nei = np.maximum(c0, c1)
+    o = np.lexsort((nei, own))
+    own, nei, own_inst = own[o], nei[o], own_inst[o]
+    single = order[start[cnt == 1]]
+    b_own = cell_of[single]
+    o = np.argsort(b_own, kind="stable")
+    single, b_own = single[o], b_own[o]
+    owner = np.concatenate([own, b_own]).astype(np.int32)
+    face_pts = np.concatenate([inst[own_inst], inst[single]]).reshape(-1).astype(np.int32)
+    face_ptr = (3 * np.arange(owner.size + 1)).astype(np.int32)
+    return Mesh(pts, face_ptr, face_pts, owner, nei.astype(np.int32), nt,
+                tet.astype(np.int32), base.h, 3, "tet", base.shape)
+
+
+# --------------------------------------------------------------------------
+# Initial volume fractions
+# --------------------------------------------------------------------------
+
+def _circle_prim(x, R):
+    """Antiderivative of sqrt(R^2 - x^2) on [-R, R]."""
+    x = np.clip(x, -R, R)
+    return 0.5 * (x * np.sqrt(np.maximum(R * R - x * x, 0.0)) + R * R * np.arcsin(x / R))
+
+
+def disc_rect_area(cx, cy, R, x0, x1, y0, y1):
+    """Exact area of disc((cx,cy),R) intersected with [x0,x1]x[y0,y1].
+
+    The chord length L(X) = |[y0,y1] ^ [cy-s, cy+s]|, s = sqrt(R^2-(X-cx)^2), is a
+    piecewise combination of constants and +-s between the abscissae where
+    cy +- s crosses y0 or y1; each piece is integrated with the circle's
+    antiderivative.  Scalar arguments."""
+    a, b = max(x0, cx - R), min(x1, cx + R)
+    if b <= a or y1 <= cy - R or y0 >= cy + R:
+        return 0.0
+    br = [a, b]
+    for y in (y0, y1):
+        dy = abs(y - cy)
+        if dy < R:
+            xb = math.sqrt(R * R - dy * dy)
+            for xv in (cx - xb, cx + xb):
+                if a < xv < b:
+                    br.append(xv)
+    br = sorted(br)
+    area = 0.0
+    for u, v in zip(br[:-1], br[1:]):
+        if v <= u:
+            continue
+        xm = 0.5 * (u + v) - cx
+        sm = math.sqrt(max(R * R - xm * xm, 0.0))
+        top_is_circle = (cy + sm) < y1
+        bot_is_circle = (cy - sm) > y0
+        if (min(y1, cy + sm) - max(y0, cy - sm)) <= 0.0:
+            continue
+        S = float(_circle_prim(v - cx, R) - _circle_prim(u - cx, R))
+        w = v - u
+        top = S + cy * w if top_is_circle else y1 * w
+        bot = (cy * w - S) if bot_is_circle else y0 * w
+        area += top - bot
+    return area
+
+
+def disc_fraction_2d(mesh: Mesh, cx: float, cy: float, R: float) -> np.ndarray:
+    """Exact cell fractions of a disc on a uniform one-cell-thick hex mesh."""
+    nx, ny, _ = mesh.shape
+    h = mesh.h
+    out = np.zeros(mesh.n_cells)
+    for j in range(ny):
+        for i in range(nx):
+            out[i + nx * j] = disc_rect_area(cx, cy, R, i * h, (i + 1) * h, j * h, (j + 1) * h) / (h * h)
+    return out
+
+
+def sphere_sdf(c, R):
+    c = np.asarray(c, float)
+    return lambda x: np.sqrt(((x - c) ** 2).sum(-1)) - R
+
+
+def cylinder_sdf(cx, cy, R):
+    return lambda x: np.sqrt((x[..., 0] - cx) ** 2 + (x[..., 1] - cy) ** 2) - R
+
+
+def _hex_shape(xi):
+    """Trilinear shape functions and their derivatives at reference points xi (m,3),
+    corner order (000,100,110,010,001,101,111,011)."""
+    u, v, w = xi[:, 0], xi[:, 1], xi[:, 2]
+    cs = np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 1, 0],
+                   [0, 0, 1], [1, 0, 1], [1, 1, 1], [0, 1, 1]], float)
+    fu = np.where(cs[None, :, 0] == 1, u[:, None], 1 - u[:, None])
+    fv = np.where(cs[None, :, 1] == 1, v[:, None], 1 - v[:, None])
+    fw = np.where(cs[None, :, 2] == 1, w[:, None], 1 - w[:, None])
+    du = np.where(cs[None, :, 0] == 1, 1.0, -1.0)
+    dv = np.where(cs[None, :, 1] == 1, 1.0, -1.0)
+    dw = np.where(cs[None, :, 2] == 1, 1.0, -1.0)
+    N = fu * fv * fw
+    dN = np.stack([du * fv * fw, fu * dv * fw, fu * fv * dw], -1)   # (m,8,3)
+    return N, dN
+
+
+def sampled_fraction(mesh: Mesh, sdf: Callable, m: int = 8, chunk: int = 4096) -> np.ndarray:
+    """Initial fraction by a midpoint rule: m^3 reference points per cell mapped
+    through the cell's trilinear (hex) or affine (tet) parametrisation, each
+    weighted by the map's Jacobian; a point counts if sdf < 0.  Cells whose
+    centroid is farther from the surface than their circumradius are set to 0/1
+    without sampling."""
+    P = mesh.points
+    cv = mesh.cell_verts
+    X = P[cv]                                    # (nc, k, 3)
+    cen = X.mean(1)
+    rad = np.sqrt(((X - cen[:, None, :]) ** 2).sum(-1)).max(1)
+    dc = sdf(cen)
+    out = np.where(dc < 0, 1.0, 0.0)
+    near = np.flatnonzero(np.abs(dc) <= rad * 1.0001)
+    g = (np.arange(m) + 0.5) / m
+    xi = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    if mesh.kind == "hex":
+        N, dN = _hex_shape(xi)
+        for s in range(0, near.size, chunk):
+            ids = near[s:s + chunk]
+            Xc = X[ids]                              # (b,8,3)
+            x = np.einsum("qk,bkd->bqd", N, Xc)
+            Jm = np.einsum("qke,bkd->bqde", dN, Xc)   # (b,q,3,3)
+            det = np.linalg.det(Jm)
+            ins = (sdf(x) < 0).astype(float)
+            out[ids] = (det * ins).sum(1) / det.sum(1)
+    else:
+        srt = -np.sort(-xi, axis=1)                  # s1 >= s2 >= s3 in the unit simplex
+        lam = np.stack([1 - srt[:, 0], srt[:, 0] - srt[:, 1], srt[:, 1] - srt[:, 2], srt[:, 2]], 1)
+        for s in range(0, near.size, chunk):
+            ids = near[s:s + chunk]
+            x = np.einsum("qk,bkd->bqd", lam, X[ids])
+            out[ids] = (sdf(x) < 0).mean(1)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Velocity fields with vector potentials (u = curl A)
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Field:
+    name: str
+    u: Callable            # x (...,3) -> (...,3), spatial part
+    A: Callable            # x (...,3) -> (...,3), vector potential of u
+    tau: Callable          # time factor tau(t)
+    tau_int: Callable      # antiderivative of tau
+
+
+def translation_field(U):
+    U = np.asarray(U, float)
+    return Field("translation", lambda x: np.broadcast_to(U, x.shape).copy(),
+                 lambda x: 0.5 * np.cross(np.broadcast_to(U, x.shape), x),
+                 lambda t: 1.0, lambda t: t)
+
+
+def deformation_field(T: float = 3.0):
+    """Eq. deformation-test-case; A = (0, -(1/pi) s2x sin2y s2z, (1/pi) s2x s2y sin2z)."""
+    pi = math.pi
+
+    def u(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return np.stack([2 * np.sin(pi * X) ** 2 * np.sin(2 * pi * Y) * np.sin(2 * pi * Z),
+                         -np.sin(2 * pi * X) * np.sin(pi * Y) ** 2 * np.sin(2 * pi * Z),
+                         -np.sin(2 * pi * X) * np.sin(2 * pi * Y) * np.sin(pi * Z) ** 2], -1)
+
+    def A(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        s2x = np.sin(pi * X) ** 2
+        return np.stack([np.zeros_like(X),
+                         -(1 / pi) * s2x * np.sin(2 * pi * Y) * np.sin(pi * Z) ** 2,
+                         (1 / pi) * s2x * np.sin(pi * Y) ** 2 * np.sin(2 * pi * Z)], -1)
+
+    return Field("deformation", u, A, lambda t: math.cos(pi * t / T),
+                 lambda t: (T / pi) * math.sin(pi * t / T))
+
+
+def single_vortex_field(T: float = 8.0):
+    pi = math.pi
+
+    def u(x):
+        X, Y = x[..., 0], x[..., 1]
+        return np.stack([-np.sin(pi * X) ** 2 * np.sin(2 * pi * Y),
+                         np.sin(2 * pi * X) * np.sin(pi * Y) ** 2, np.zeros_like(X)], -1)
+
+    def A(x):
+        X, Y = x[..., 0], x[..., 1]
+        return np.stack([np.zeros_like(X), np.zeros_like(X),
+                         -(1 / pi) * np.sin(pi * X) ** 2 * np.sin(pi * Y) ** 2], -1)
+
+    return Field("single_vortex", u, A, lambda t: math.cos(pi * t / T),
+                 lambda t: (T / pi) * math.sin(pi * t / T))
+
+
+def rotation_field(omega, x0=(0.5, 0.5, 0.5)):
+    om = np.asarray(omega, float)
+    c = np.asarray(x0, float)
+    return Field("rotation", lambda x: np.cross(np.broadcast_to(om, x.shape), x - c),
+                 lambda x: -0.5 * ((x - c) ** 2).sum(-1)[..., None] * om,
+                 lambda t: 1.0, lambda t: t)
+
+
+_GL_X, _GL_W = np.polynomial.legendre.leggauss(8)
+_GL_X = 0.5 * (_GL_X + 1.0)
+_GL_W = 0.5 * _GL_W
+
+
+def face_flux_stokes(mesh: Mesh, A: Callable, chunk: int = 1 << 20) -> np.ndarray:
+    """F_f = circulation of A around face f (Stokes), signed along the face normal.
+    One 8-point Gauss-Legendre integral per unique edge (low -> high point id);
+    each face sums its edges with +-1, so per-cell sums cancel to round-off."""
+    ptr = mesh.face_ptr.astype(np.int64)
+    fp = mesh.face_pts.astype(np.int64)
+    nf = mesh.n_faces
+    cnt = np.diff(ptr)
+    face_of = np.repeat(np.arange(nf), cnt)
+    nxt = np.arange(fp.size) + 1
+    nxt[ptr[1:] - 1] = ptr[:-1]
+    a, b = fp, fp[nxt]
+    lo, hi = np.minimum(a, b), np.maximum(a, b)
+    sign = np.where(a < b, 1.0, -1.0)
+    N = np.int64(mesh.n_points)
+    key = lo * N + hi
+    uk, inv = np.unique(key, return_inverse=True)
+    e0, e1 = uk // N, uk % N
+    P = mesh.points
+    I = np.empty(uk.size)
+    for s in range(0, uk.size, chunk):
+        x0 = P[e0[s:s + chunk]]
+        dx = P[e1[s:s + chunk]] - x0
+        acc = np.zeros(x0.shape[0])
+        for t, w in zip(_GL_X, _GL_W):
+            acc += w * np.einsum("ij,ij->i", A(x0 + t * dx), dx)
+        I[s:s + chunk] = acc
+    return np.bincount(face_of, weights=sign * I[inv.reshape(-1)], minlength=nf)
+
+
+def cell_velocity(mesh: Mesh, u: Callable) -> np.ndarray:
+    """Analytic velocity at the mean of each cell's vertices, SoA (3, n_cells)."""
+    cen = mesh.points[mesh.cell_verts].mean(1)
+    return np.ascontiguousarray(u(cen).T)
+
+
+# --------------------------------------------------------------------------
+# Workloads
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    mesh: Mesh
+    alpha0: np.ndarray
+    field: Field
+    F_spatial: np.ndarray      # circulation of the spatial potential per face
+    U_spatial: np.ndarray      # (3, n_cells)
+    dt: float
+    n_steps: int
+    t_end: float
+    exact: Callable | None = None   # t -> exact fractions (if known)
+
+    def step_inputs(self, n: int, dt: float | None = None):
+        """(F, U_c, dt) for step n: F averaged over [t_n, t_n+dt] (exact time
+        integral of the field's time factor), U_c at the step midpoint."""
+        dt = self.dt if dt is None else dt
+        t0 = n * self.dt
+        f = self.field
+        tf = (f.tau_int(t0 + dt) - f.tau_int(t0)) / dt
+        return self.F_spatial * tf, self.U_spatial * f.tau(t0 + 0.5 * dt), dt
+
+
+def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | None = None) -> Workload:
+    """Named workloads.
+
+    disc2d:       uniform 32x32x1 hex on [0,1]^2 x [0,1/32], disc R=0.15 at (0.5,0.75),
+                  exact fractions, translation (1,1,0), Co 0.5, 20 steps; the four
+                  sides are open (empty inflow, geometric outflow), front/back walls.
+    deform3d:     jittered (+-0.2h, seed 1302) n^3 hex (n=128), sphere R=0.15 at
+                  (0.35,0.35,0.35), deformation field T=3, Co 0.5 to t=3.
+    vortex_tet:   jittered (+-0.15h, seed 1303) Kuhn split of n^3 (n=96), cylinder
+                  R=0.15 at (0.5,0.75), single vortex T=8, Co 0.5 to t=8.
+    """
+    if name == "disc2d":
+        n = 32 if n is None else n
+        mesh = hex_mesh((n, n, 1), (1.0, 1.0, 1.0 / n), dim=2, open_sides=("x-", "x+", "y-", "y+"))
+        a0 = disc_fraction_2d(mesh, 0.5, 0.75, 0.15)
+        fld = translation_field((1.0, 1.0, 0.0))
+        steps = 20
+    elif name == "deform3d":
+        n = 128 if n is None else n
+        mesh = hex_mesh((n, n, n), jitter=0.2, seed=1302 if seed is None else seed)
+        a0 = sampled_fraction(mesh, sphere_sdf((0.35, 0.35, 0.35), 0.15))
+        fld = deformation_field(3.0)
+        steps = None
+    elif name == "vortex_tet":
+        n = 96 if n is None else n
+        mesh = kuhn_tet_mesh((n, n, n), jitter=0.15, seed=1303 if seed is None else seed)
+        a0 = sampled_fraction(mesh, cylinder_sdf(0.5, 0.75, 0.15))
+        fld = single_vortex_field(8.0)
+        steps = None
+    else:
+        raise ValueError(name)
+    Us = cell_velocity(mesh, fld.u)
+    umax = float(np.sqrt((Us ** 2).sum(0)).max())
+    dt = co * mesh.h / umax
+    Fs = face_flux_stokes(mesh, fld.A)
+    t_end = {"disc2d": steps * dt if steps else None, "deform3d": 3.0, "vortex_tet": 8.0}[name]
+    if steps is None:
+        steps = int(math.ceil(t_end / dt - 1e-12))
+    exact = None
+    if name == "disc2d":
+        def exact(t, _m=mesh):
+            return disc_fraction_2d(_m, 0.5 + t, 0.75 + t, 0.15)
+    return Workload(name, mesh, a0, fld, Fs, Us, dt, steps, t_end, exact)
