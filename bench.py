@@ -1,0 +1,312 @@
+#!/usr/bin/env python3
+"""Benchmark of the geometric VoF advection step (one JSON line on rank 0).
+
+Workload (default): 128^3 hexahedral mesh on [0,1]^3 with interior points
+jittered by +-0.2h (seed 1302), sphere R=0.15 at (0.35,0.35,0.35), deformation
+field (T=3), Courant number 0.5.  A step is one full vof_advect call (band
+classification, reconstruction, point velocities, flux correction, phase
+fluxes, update and bounding) with the step's flux F and cell velocity U_c
+already resident in HBM.  Metric: internal face fluxes with final phase volume
+per second (millions), whole job.
+
+--impl reference times the CPU oracle (test infrastructure) on the host cores
+on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "geometric VoF face fluxes/s (M/s), mixed vs plain FP64 GPU, at stated L1 error"
+UNIT = "M face fluxes/s"
+# algorithmic flop cost model of the phase-flux kernel (primitive costs: signed
+# distance 6, edge intersection 10, tetrahedron volume 17, plane from 3 points 20)
+FLOPS_PER_PAIR = 16 * 6 + 4 * 20     # 4 planes of the cell tetrahedron, 4x4 distances
+FLOPS_PER_CUT = 4 * 10 + 3 * 17      # edge intersections + resulting tetrahedra volumes
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, idx):
+        self.idx = idx
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        for line in (self.out or "").strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(args):
+    from paper_1305_3417_gb300 import inputs as I
+    return I.make_workload(args.workload, n=args.n)
+
+
+def cpu_baseline(w, steps=1):
+    """The oracle as it stands, timed on the host cores on full steps of the
+    same workload."""
+    from oracle import oracle as O
+    threads = O.set_threads(os.cpu_count() or 1)
+    om = O.OracleMesh(w.mesh)
+    a = w.alpha0.copy()
+    t_total = 0.0
+    for k in range(steps):
+        F, U, dt = w.step_inputs(k)
+        t0 = time.perf_counter()
+        a, st, s = om.advect(a, U, F, dt)
+        t_total += time.perf_counter() - t0
+    v = steps * w.mesh.n_internal / t_total / 1e6
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} full oracle step(s) of the {args_workload_name(w)} workload from t=0 "
+                      f"({w.mesh.n_internal} internal faces each), {t_total:.1f} s"}, st
+
+
+def args_workload_name(w):
+    return f"{w.name} {w.mesh.shape}"
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    w = workload(args)
+    t0 = time.perf_counter()
+    base, st = cpu_baseline(w, steps=max(1, args.steps))
+    elapsed = time.perf_counter() - t0
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": max(1, args.steps), "warmup": 0, "ms_per_step": 1e3 * elapsed / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(args, w),
+            "cpu_baseline": {**base, "value": base["value"]},
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config(args, w):
+    m = w.mesh
+    return {"workload": f"{w.name}: {m.shape[0]}x{m.shape[1]}x{m.shape[2]} {m.kind} mesh "
+                        f"({m.n_cells} cells, {m.n_internal} internal faces), jitter, {w.field.name} field, Co 0.5",
+            "n_cells": m.n_cells, "n_internal_faces": m.n_internal, "precision": args.precision,
+            "skip_steps": args.skip, "dt": w.dt,
+            "l2": "inputs larger than L2 (mesh, fluxes and per-step arrays > 129 MB)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default="deform3d")
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--skip", type=int, default=0, help="untimed steps advanced before warm-up")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_1305_3417_gb300 import build, vof
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = workload(args)
+    m = w.mesh
+    prec = vof.MIXED if args.precision == "mixed" else vof.FP64
+    ctx = vof.VofContext(m, precision=prec, device=local)
+    total = args.skip + args.warmup + args.steps
+    # per-step inputs resident in HBM before the timed region
+    Fs = torch.from_numpy(w.F_spatial).to(dev)
+    Us = torch.from_numpy(np.ascontiguousarray(w.U_spatial).reshape(-1)).to(dev)
+    fac = []
+    for k in range(total):
+        t0 = k * w.dt
+        tf = (w.field.tau_int(t0 + w.dt) - w.field.tau_int(t0)) / w.dt
+        fac.append((tf, w.field.tau(t0 + 0.5 * w.dt)))
+    Fk = [Fs * f for f, _ in fac]
+    Uk = [Us * u for _, u in fac]
+    alpha = torch.from_numpy(w.alpha0.copy()).to(dev)
+    stats = torch.zeros(vof.S_LEN, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    for k in range(args.skip + args.warmup):
+        ctx.advect(alpha, Uk[k], Fk[k], w.dt, stats)
+    torch.cuda.synchronize()
+    st0 = ctx.status()
+    vof.vof_work_counts(ctx.h, reset=True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_stats = torch.zeros((args.steps, vof.S_LEN), dtype=torch.float64, device=dev)
+    vof.vof_profile_begin(ctx.h, args.steps)
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for j in range(args.steps):
+            k = args.skip + args.warmup + j
+            ctx.advect(alpha, Uk[k], Fk[k], w.dt, step_stats[j])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    group_ms, nprof = vof.vof_profile_end(ctx.h)
+    work = vof.vof_work_counts(ctx.h, reset=True)
+    launches = vof.vof_last_launch_count(ctx.h) * args.steps
+    st1 = ctx.status()
+    ms_max = max_over_ranks(ms, world, dev)
+    faces = world * args.steps * m.n_internal
+    value = faces / (ms_max * 1e-3) / 1e6
+    S = step_stats.cpu().numpy()
+    drift = np.abs((S[:, 1] + S[:, 10] - S[:, 0]) / S[:, 0]).max()
+
+    # ---- end to end through the C ABI with host buffers (copies in the timed region)
+    ha = torch.from_numpy(w.alpha0.copy()).pin_memory()
+    hstat = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
+    hF = [Fk[args.skip + args.warmup + j].cpu().pin_memory() for j in range(args.steps)]
+    hU = [Uk[args.skip + args.warmup + j].cpu().pin_memory() for j in range(args.steps)]
+    for k in range(args.skip + args.warmup):
+        vof.vof_advect_host(ctx.h, ha, Uk[k].cpu(), Fk[k].cpu(), w.dt, hstat)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for j in range(args.steps):
+        vof.vof_advect_host(ctx.h, ha, hU[j], hF[j], w.dt, hstat)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), world, dev)
+    e2e = faces / (ms_e2e * 1e-3) / 1e6
+    h2d = 8 * m.n_cells + 24 * m.n_cells + 8 * m.n_faces
+    d2h = 8 * m.n_cells + 8 * vof.S_LEN
+
+    # ---- roofline of the dominant kernel group
+    pk, pk_src = peaks()
+    per_launch = {g: v / max(nprof, 1) for g, v in group_ms.items()}
+    dom = max(per_launch, key=per_launch.get)
+    if dom == "phase_flux":
+        fl = (work["pairs"] * FLOPS_PER_PAIR + work["cuts"] * FLOPS_PER_CUT) / max(nprof, 1)
+        alu = vof.vof_probe_fma(local, prec)
+        achieved = fl / (per_launch[dom] * 1e-3) / 1e12
+        roof = {"kernel": "k_phase_flux", "bound": "alu", "achieved": achieved, "peak": alu / 1e12,
+                "unit": "TFLOP/s", "frac": achieved * 1e12 / alu, "traffic": None,
+                "peak_source": f"measured {'FP64' if prec == vof.FP64 else 'FP32'} FMA probe (vof_probe_fma)",
+                "work_per_launch": {"pairs": work["pairs"] / max(nprof, 1), "cuts": work["cuts"] / max(nprof, 1),
+                                    "band_faces": work["faces"] / max(nprof, 1)}}
+    else:
+        # HBM-bound groups: algorithmic bytes per internal face
+        byts = 72.0 * m.n_internal
+        achieved = byts / (per_launch[dom] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_src}
+    roof["group_ms_per_step"] = per_launch
+
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base, _ = cpu_baseline(w, steps=args.cpu_steps)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if prec == vof.FP64 else "f32+f64",
+                "data": "synthetic", "config": config(args, w),
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": base,
+                "clocks": clk.summary(),
+                "quality": {"max_rel_volume_drift": float(drift), "alpha_min": float(S[:, 4].min()),
+                            "alpha_max": float(S[:, 5].max()), "alpha_min_pre_bound": float(S[:, 2].min()),
+                            "alpha_max_pre_bound": float(S[:, 3].max()),
+                            "band_faces_per_step": float(S[:, 7].mean()),
+                            "interface_cells_per_step": float(S[:, 6].mean()),
+                            "status_bits": int(st0 | st1)}}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,212 @@
+/*
+ * vof.h -- C ABI of libvof, the GB300 (sm_103a) implementation of the unsplit
+ * geometric Volume-of-Fluid advection step of Maric, Marschall & Bothe (2013):
+ * PLIC reconstruction, flux polyhedra, flux correction, phase fluxes and the
+ * conservative volume-fraction update.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Return value: VOF_OK (0) or a negative VOF_ERR_* code; vof_error_string()
+ *   names it.  Argument errors are detected on the host before anything is
+ *   enqueued.  Conditions found on the device (an iteration cap reached, a
+ *   clip buffer exhausted, a bounding residual) set bits of a per-context
+ *   status word and never trap; vof_status() reads and clears it.
+ * - Per-step arrays are DEVICE pointers owned by the caller (for example
+ *   PyTorch tensors).  They must stay valid until `stream` reaches the call.
+ *   Every per-step call is asynchronous on `stream` (a cudaStream_t; NULL is
+ *   the legacy default stream) and allocates no memory: the context allocates
+ *   all of its scratch in vof_create.
+ * - Vectors are structure-of-arrays: x block, then y block, then z block.
+ * - Face f of the mesh has points face_pts[face_ptr[f] .. face_ptr[f+1]),
+ *   ordered so that the right-hand area vector S_f points from owner[f] to
+ *   neighbour[f] (internal faces 0 .. n_internal-1) or out of the domain
+ *   (boundary faces n_internal .. n_faces-1).  This is the owner/neighbour
+ *   addressing of Sec. 2 (Eq. own-nei).  A volumetric flux F_f is positive
+ *   from owner to neighbour; phase volumes V_alpha are signed the same way.
+ * - Cell solids (reading of Sec. 2.1 for non-planar faces): a face with more
+ *   than three points is the fan of triangles (c_f, p_i, p_i+1) about the mean
+ *   of its points c_f; a cell is the union of the tetrahedra (c_c, outward face
+ *   triangle), c_c the mean of the cell's points.
+ */
+#ifndef VOF_H
+#define VOF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    VOF_OK = 0,
+    VOF_ERR_INVALID_ARG = -1, /* NULL or inconsistent argument */
+    VOF_ERR_CUDA = -2,        /* a CUDA runtime call failed */
+    VOF_ERR_BAD_MESH = -3,    /* index out of range, cell of non-positive volume, ... */
+    VOF_ERR_NOT_CONVERGED = -4,
+    VOF_ERR_STENCIL = -5,
+    VOF_ERR_TIMEOUT = -6,
+    VOF_ERR_NO_DEVICE = -7,   /* no CUDA device, or not a compute capability 10.3 part */
+};
+
+/* status bits accumulated on the device (vof_status) */
+enum {
+    VOF_ST_POS_NOT_CONVERGED = 1u << 0,  /* plane positioning hit its iteration cap */
+    VOF_ST_CORR_NOT_CONVERGED = 1u << 1, /* flux correction hit its iteration cap */
+    VOF_ST_CLIP_OVERFLOW = 1u << 2,      /* clipping stack exhausted (volume dropped) */
+    VOF_ST_BOUND_RESIDUAL = 1u << 3,     /* |alpha - clamp(alpha)| > 1e-12 after bounding */
+    VOF_ST_INDEX = 1u << 4,              /* an index check failed inside a kernel */
+    VOF_ST_CAPACITY = 1u << 5,           /* a per-step list exceeded its capacity */
+};
+
+/* precision of the geometric kernels */
+enum { VOF_FP64 = 0, VOF_MIXED = 1 };
+
+/* cell flags written by vof_reconstruct */
+enum { VOF_INTERFACE = 1, VOF_ORIENTED = 2, VOF_FULL = 4 };
+
+/* Mesh description.  All pointers are HOST pointers, read during vof_create
+ * only (the context keeps device copies). */
+typedef struct {
+    int32_t n_points, n_faces, n_internal, n_cells;
+    const double *px, *py, *pz;  /* [n_points] point coordinates */
+    const int32_t *face_ptr;     /* [n_faces + 1] CSR offsets into face_pts */
+    const int32_t *face_pts;     /* [face_ptr[n_faces]] ordered point indices */
+    const int32_t *owner;        /* [n_faces] */
+    const int32_t *neighbour;    /* [n_internal] */
+    const uint8_t *wall;         /* [n_faces - n_internal]: 1 = wall (no normal
+                                    flow), 0 = open; NULL makes all walls */
+} vof_mesh;
+
+typedef struct {
+    double eps;     /* interface tolerance: eps < alpha < 1-eps is an interface
+                       cell (reading of Sec. 5.2's reconstruction tolerance);
+                       <= 0 selects 1e-9 */
+    int precision;  /* VOF_FP64 or VOF_MIXED */
+    int bound;      /* 1: conservative bounding pass after the update */
+    int device;     /* CUDA device ordinal */
+} vof_options;
+
+/* stats[] layout (doubles, device memory) written by vof_update / vof_advect */
+enum {
+    VOF_S_MASS_BEFORE = 0, VOF_S_MASS_AFTER, VOF_S_MIN_PRE, VOF_S_MAX_PRE, VOF_S_MIN_POST,
+    VOF_S_MAX_POST, VOF_S_N_INTERFACE, VOF_S_N_BAND, VOF_S_MAX_POS_IT, VOF_S_MAX_CORR_IT,
+    VOF_S_BOUNDARY_OUT, VOF_S_N_FALLBACK, VOF_S_LEN = 16
+};
+
+typedef struct vof_ctx vof_ctx;
+
+/* Builds the derived topology (cell->face, cell->point, point->cell, face
+ * stencils: every cell sharing a point with the face, Sec. 2.3) on the host,
+ * copies it to the device, computes the geometry (face centres and area
+ * vectors, cell centres, volumes and bounding boxes, inverse-distance weights
+ * of Eq. w_pc, NAG face weights of Sec. 2.2.1) in kernels, and allocates all
+ * per-step scratch.  Synchronous.  Fails with VOF_ERR_BAD_MESH on an index out
+ * of range or a cell tetrahedron of non-positive volume.  *out receives a
+ * context the caller releases with vof_destroy. */
+int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out);
+void vof_destroy(vof_ctx *ctx);
+
+/* Geometry computed by vof_create, copied to caller DEVICE arrays (any may be
+ * NULL): cell centres [3*n_cells], volumes [n_cells], face centres and area
+ * vectors [3*n_faces]. */
+int vof_geometry(vof_ctx *ctx, double *cell_centre, double *cell_vol, double *face_centre,
+                 double *face_area, void *stream);
+
+/* A4, Eq. idwpointphi: point velocity Up [3*n_points] from the cell velocity
+ * Uc [3*n_cells] by inverse-distance weighting over the point's cells; at a
+ * point on wall faces only the component tangent to the walls is kept. */
+int vof_point_velocity(vof_ctx *ctx, const double *Uc, double *Up, void *stream);
+
+/* A1-A3, Alg. 1 and Sec. 2.2: for every cell with eps < alpha < 1-eps, the NAG
+ * gradient (Sec. 2.2.1), the unit normal n = -grad/|grad| (pointing out of the
+ * phase), and the plane offset d with |C ^ {x : n.x <= d}| = alpha |C| found by
+ * the secant iteration with bisection fallback (Sec. 2.2.2; stops at a fill
+ * residual of 1e-13 or a bracket of 1e-15 of the cell's extent, at most 100
+ * iterations).  Outputs (device): n [3*n_cells], d [n_cells], flags [n_cells]
+ * (VOF_INTERFACE / VOF_ORIENTED / VOF_FULL), iters [n_cells] or NULL.  Cells
+ * that are not oriented interface cells get n = 0, d = 0. */
+int vof_reconstruct(vof_ctx *ctx, const double *alpha, double *n, double *d, uint8_t *flags,
+                    int32_t *iters, void *stream);
+
+/* A4-A5, Eqs. sweep and V_fS: signed volume Vswept [n_faces] of the flux
+ * polyhedron of every face, each face triangle swept to b = a - lambda*Up*dt
+ * and split into three tetrahedra (positive for a sweep against S_f).  lambda
+ * [n_faces] may be NULL (lambda = 1); a negative lambda selects the normal
+ * sweep -lambda*(F_f/|S_f|^2) S_f dt, which needs F (else F may be NULL). */
+int vof_flux_polyhedra(vof_ctx *ctx, const double *Up, const double *F, const double *lambda,
+                       double dt, double *Vswept, void *stream);
+
+/* A5, Eq. VF: per face the sweep factor lambda with V_f(lambda) = F_f dt, the
+ * root in the first of the sixteen intervals of (0, 2] across which
+ * V_f - F_f dt changes sign (V_f is a cubic in lambda, solved by a bracketed
+ * Newton iteration); lambda = -1 where no interval brackets a root (normal-sweep
+ * fallback), 0 where F_f = 0.  iters [n_faces] or NULL. */
+int vof_correct_flux(vof_ctx *ctx, const double *Up, const double *F, double dt, double *lambda,
+                     int32_t *iters, void *stream);
+
+/* A6, Eqs. S'_f, S''_f and vol-phase-flux: fluxed phase volume Valpha
+ * [n_faces].  A face whose stencil cells all have alpha <= eps carries 0, all
+ * >= 1-eps carries F_f dt; a boundary face with inflow carries 0 (empty
+ * exterior); every other face sums, over its stencil cells s and the
+ * tetrahedra T of its flux polyhedron and K of cell s, sign(T) |T ^ K ^ H_s|,
+ * H_s the phase half-space {n_s.x <= d_s} of an oriented interface cell, all
+ * of K for a full cell, alpha_s |T ^ K| for an unoriented one. */
+int vof_phase_flux(vof_ctx *ctx, const double *alpha, const double *n, const double *d,
+                   const uint8_t *flags, const double *Up, const double *F, const double *lambda,
+                   double dt, double *Valpha, void *stream);
+
+/* A7, Eq. alpha-discrete with Eq. own-nei: alpha_c -= (sum over owner faces of
+ * Valpha - sum over neighbour faces) / |C_c|, in place, then the optional
+ * conservative bounding pass; stats (device, VOF_S_LEN doubles) or NULL. */
+int vof_update(vof_ctx *ctx, double *alpha, const double *Valpha, double *stats, void *stream);
+
+/* One full advection step A1-A7 over the narrow band: band classification,
+ * reconstruction of interface cells, point velocities and flux correction of
+ * band faces, phase fluxes, update.  alpha [n_cells] in/out, Uc [3*n_cells]
+ * cell velocity at the step midpoint, F [n_faces] volumetric flux averaged over
+ * the step (discretely divergence-free, Eq. discretedivergence), dt > 0. */
+int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
+               double *stats, void *stream);
+
+/* vof_advect with HOST arrays (pinned memory gives full copy speed): copies
+ * alpha, Uc, F to the context's device buffers, runs the step, copies alpha
+ * (and stats, VOF_S_LEN doubles, if not NULL) back.  Asynchronous on `stream`;
+ * the host arrays must stay valid until the stream reaches the end of it. */
+int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
+                    double *stats, void *stream);
+
+/* Kernel-group timing with CUDA events recorded on the launching stream.
+ * vof_profile_begin arms recording for up to max_steps subsequent vof_advect
+ * calls (creating events, no device memory); vof_profile_end synchronises on
+ * the last event and returns, per group, the summed milliseconds over the
+ * recorded steps: [0] band classification, [1] reconstruction, [2] flux
+ * correction, [3] phase flux, [4] update, bounding and statistics; *steps
+ * receives the number of steps recorded.  Recording stops at max_steps. */
+enum { VOF_PROF_GROUPS = 5 };
+int vof_profile_begin(vof_ctx *ctx, int max_steps);
+int vof_profile_end(vof_ctx *ctx, double *group_ms, int *steps);
+
+/* Algorithmic work counted by the phase-flux kernel since the last reset:
+ * counts[0] (tetrahedron, cell-tetrahedron) pairs whose bounding boxes overlap,
+ * counts[1] plane cuts that split a tetrahedron, counts[2] band faces.  Reading
+ * synchronises `stream`; reset zeroes the counters. */
+int vof_work_counts(vof_ctx *ctx, unsigned long long counts[3], int reset, void *stream);
+
+/* Measurement helper with no counterpart in the paper: sustained fused
+ * multiply-add rate (FLOP/s, 2 per FMA) of the plain FP64 (VOF_FP64) or FP32
+ * (VOF_MIXED) pipes of `device`, the roofline peak of arithmetic-bound kernels.
+ * Synchronous; allocates and frees one scalar of device memory. */
+int vof_probe_fma(int device, int precision, double *flops_per_s, void *stream);
+
+/* Reads (synchronising `stream`) and clears the device status word. */
+int vof_status(vof_ctx *ctx, uint32_t *bits, void *stream);
+
+/* Number of kernel launches the last vof_advect enqueued. */
+int vof_last_launch_count(vof_ctx *ctx);
+
+const char *vof_error_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,489 @@
+// C-ABI entry points of libvof and the host-side topology builder.
+//
+// vof_create derives the integer topology on the host (cell->face,
+// cell->point, point->cell, face stencils, wall-point lists), copies it to the
+// device, and computes every geometric quantity in kernels.  Per-step entry
+// points only validate arguments and enqueue kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "vof_internal.h"
+
+int launch_wall_table(vof_ctx *c, const int *wptr, const int *wface, int nrows, cudaStream_t s);
+
+namespace {
+
+template <class F>
+void parallel_for(long n, F fn)
+{
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    if (n < 4096) nt = 1;
+    std::vector<std::thread> th;
+    long chunk = (n + nt - 1) / nt;
+    for (unsigned t = 0; t < nt; ++t) {
+        long a = t * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([=, &fn] { for (long i = a; i < b; ++i) fn(i); });
+    }
+    for (auto &x : th) x.join();
+}
+
+template <class T>
+T *dev_alloc(vof_ctx *c, size_t n, int *err)
+{
+    if (*err) return nullptr;
+    if (c->nbufs >= 64) { *err = VOF_ERR_CUDA; return nullptr; }
+    void *p = nullptr;
+    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) { *err = VOF_ERR_CUDA; return nullptr; }
+    c->bufs[c->nbufs++] = p;
+    return (T *)p;
+}
+
+template <class T>
+T *dev_copy(vof_ctx *c, const T *h, size_t n, int *err)
+{
+    T *d = dev_alloc<T>(c, n, err);
+    if (*err) return nullptr;
+    if (n && cudaMemcpy(d, h, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) *err = VOF_ERR_CUDA;
+    return d;
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+
+extern "C" {
+
+const char *vof_error_string(int code)
+{
+    switch (code) {
+    case VOF_OK: return "ok";
+    case VOF_ERR_INVALID_ARG: return "invalid argument";
+    case VOF_ERR_CUDA: return "CUDA runtime error";
+    case VOF_ERR_BAD_MESH: return "bad mesh (index out of range or non-positive cell volume)";
+    case VOF_ERR_NOT_CONVERGED: return "iteration did not converge";
+    case VOF_ERR_STENCIL: return "flux stencil does not cover the flux polyhedron";
+    case VOF_ERR_TIMEOUT: return "device wait timed out";
+    case VOF_ERR_NO_DEVICE: return "no compute capability 10.3 CUDA device";
+    default: return "unknown error";
+    }
+}
+
+static void free_profile(vof_ctx *c)
+{
+    if (!c->prof_ev) return;
+    for (int i = 0; i < c->prof_max * (VOF_PROF_GROUPS + 1); ++i) cudaEventDestroy(c->prof_ev[i]);
+    delete[] c->prof_ev;
+    c->prof_ev = nullptr;
+    c->prof_max = c->prof_steps = 0;
+}
+
+void vof_destroy(vof_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    free_profile(c);
+    for (int i = 0; i < c->nbufs; ++i) cudaFree(c->bufs[i]);
+    delete c;
+}
+
+int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
+{
+    if (!mesh || !out) return VOF_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int np = mesh->n_points, nf = mesh->n_faces, ni = mesh->n_internal, nc = mesh->n_cells;
+    if (np <= 0 || nf <= 0 || nc <= 0 || ni < 0 || ni > nf) return VOF_ERR_INVALID_ARG;
+    if (!mesh->px || !mesh->py || !mesh->pz || !mesh->face_ptr || !mesh->face_pts || !mesh->owner ||
+        (ni > 0 && !mesh->neighbour))
+        return VOF_ERR_INVALID_ARG;
+    int device = opt ? opt->device : 0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return VOF_ERR_NO_DEVICE;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return VOF_ERR_NO_DEVICE;
+    if (!(prop.major == 10 && prop.minor == 3)) return VOF_ERR_NO_DEVICE;
+    if (cudaSetDevice(device) != cudaSuccess) return VOF_ERR_NO_DEVICE;
+
+    // ---------------------------------------------------------- validation
+    const int *fptr = mesh->face_ptr, *fpts = mesh->face_pts, *own = mesh->owner, *nei = mesh->neighbour;
+    if (fptr[0] != 0) return VOF_ERR_BAD_MESH;
+    for (int f = 0; f < nf; ++f) {
+        int n = fptr[f + 1] - fptr[f];
+        if (n < 3 || n > VOF_MAXFP) return VOF_ERR_BAD_MESH;
+        if (own[f] < 0 || own[f] >= nc) return VOF_ERR_BAD_MESH;
+        if (f < ni && (nei[f] < 0 || nei[f] >= nc || nei[f] == own[f])) return VOF_ERR_BAD_MESH;
+    }
+    const long nfp = fptr[nf];
+    for (long k = 0; k < nfp; ++k)
+        if (fpts[k] < 0 || fpts[k] >= np) return VOF_ERR_BAD_MESH;
+
+    // ------------------------------------------------------ host topology
+    std::vector<int> cptr(nc + 1, 0), cface;
+    for (int f = 0; f < nf; ++f) {
+        cptr[own[f] + 1]++;
+        if (f < ni) cptr[nei[f] + 1]++;
+    }
+    for (int c = 0; c < nc; ++c) cptr[c + 1] += cptr[c];
+    cface.resize(cptr[nc]);
+    {
+        std::vector<int> fill(nc, 0);
+        for (int f = 0; f < nf; ++f) {
+            cface[cptr[own[f]] + fill[own[f]]++] = 2 * f;
+            if (f < ni) cface[cptr[nei[f]] + fill[nei[f]]++] = 2 * f + 1;
+        }
+    }
+    // cell -> distinct points, and the tetrahedron count per cell
+    std::vector<int> cpcount(nc);
+    std::vector<int> ktet(nc);
+    parallel_for(nc, [&](long c) {
+        int k = 0, kt = 0;
+        for (int i = cptr[c]; i < cptr[c + 1]; ++i) {
+            int f = cface[i] >> 1, n = fptr[f + 1] - fptr[f];
+            k += n;
+            kt += n == 3 ? 1 : n;
+        }
+        cpcount[c] = k;
+        ktet[c] = kt;
+    });
+    for (int c = 0; c < nc; ++c)
+        if (ktet[c] > 32 * VOF_MAXK_LANE || ktet[c] < 4) return VOF_ERR_BAD_MESH;
+    std::vector<int> cpptr(nc + 1, 0);
+    {
+        std::vector<int> uniq(nc);
+        std::vector<long> off(nc + 1, 0);
+        for (int c = 0; c < nc; ++c) off[c + 1] = off[c] + cpcount[c];
+        std::vector<int> tmp(off[nc]);
+        parallel_for(nc, [&](long c) {
+            long o = off[c];
+            int k = 0;
+            for (int i = cptr[c]; i < cptr[c + 1]; ++i) {
+                int f = cface[i] >> 1;
+                for (int j = fptr[f]; j < fptr[f + 1]; ++j) tmp[o + k++] = fpts[j];
+            }
+            std::sort(tmp.begin() + o, tmp.begin() + o + k);
+            uniq[c] = (int)(std::unique(tmp.begin() + o, tmp.begin() + o + k) - (tmp.begin() + o));
+        });
+        for (int c = 0; c < nc; ++c) cpptr[c + 1] = cpptr[c] + uniq[c];
+        std::vector<int> cpts(cpptr[nc]);
+        parallel_for(nc, [&](long c) {
+            std::copy(tmp.begin() + off[c], tmp.begin() + off[c] + uniq[c], cpts.begin() + cpptr[c]);
+        });
+        tmp.clear();
+        tmp.shrink_to_fit();
+        cpcount.swap(cpts);  // reuse: cpcount now holds the flattened cell points
+    }
+    const std::vector<int> &cpts = cpcount;
+    // point -> cells (ascending cell index)
+    std::vector<int> pptr(np + 1, 0), pcell(cpptr[nc]);
+    for (int c = 0; c < nc; ++c)
+        for (int i = cpptr[c]; i < cpptr[c + 1]; ++i) pptr[cpts[i] + 1]++;
+    for (int p = 0; p < np; ++p) pptr[p + 1] += pptr[p];
+    {
+        std::vector<int> fill(np, 0);
+        for (int c = 0; c < nc; ++c)
+            for (int i = cpptr[c]; i < cpptr[c + 1]; ++i) {
+                int p = cpts[i];
+                pcell[pptr[p] + fill[p]++] = c;
+            }
+    }
+    for (int p = 0; p < np; ++p)
+        if (pptr[p + 1] == pptr[p]) return VOF_ERR_BAD_MESH;  // point used by no cell
+    // face stencils: every cell sharing a point with the face, ascending
+    std::vector<int> scount(nf);
+    std::vector<long> soff(nf + 1, 0);
+    for (int f = 0; f < nf; ++f) {
+        long k = 0;
+        for (int j = fptr[f]; j < fptr[f + 1]; ++j) k += pptr[fpts[j] + 1] - pptr[fpts[j]];
+        soff[f + 1] = soff[f] + k;
+    }
+    std::vector<int> stmp(soff[nf]);
+    parallel_for(nf, [&](long f) {
+        long o = soff[f];
+        int k = 0;
+        for (int j = fptr[f]; j < fptr[f + 1]; ++j)
+            for (int q = pptr[fpts[j]]; q < pptr[fpts[j] + 1]; ++q) stmp[o + k++] = pcell[q];
+        std::sort(stmp.begin() + o, stmp.begin() + o + k);
+        scount[f] = (int)(std::unique(stmp.begin() + o, stmp.begin() + o + k) - (stmp.begin() + o));
+    });
+    std::vector<int> sptr(nf + 1, 0);
+    for (int f = 0; f < nf; ++f) {
+        long v = (long)sptr[f] + scount[f];
+        if (v > 0x7fffffffL) return VOF_ERR_BAD_MESH;
+        sptr[f + 1] = (int)v;
+    }
+    std::vector<int> scell(sptr[nf]);
+    parallel_for(nf, [&](long f) {
+        std::copy(stmp.begin() + soff[f], stmp.begin() + soff[f] + scount[f], scell.begin() + sptr[f]);
+    });
+    stmp.clear();
+    stmp.shrink_to_fit();
+    // wall points and the wall faces through them (reading R2)
+    std::vector<int> pwall(np, -1), wptr(1, 0), wface;
+    {
+        std::vector<std::vector<int>> lists;
+        for (int f = ni; f < nf; ++f) {
+            bool w = mesh->wall ? mesh->wall[f - ni] != 0 : true;
+            if (!w) continue;
+            for (int j = fptr[f]; j < fptr[f + 1]; ++j) {
+                int p = fpts[j];
+                if (pwall[p] < 0) { pwall[p] = (int)lists.size(); lists.emplace_back(); }
+                lists[pwall[p]].push_back(f);
+            }
+        }
+        for (auto &l : lists) {
+            wface.insert(wface.end(), l.begin(), l.end());
+            wptr.push_back((int)wface.size());
+        }
+    }
+    const int nwrows = (int)wptr.size() - 1;
+
+    // ------------------------------------------------------------- device
+    vof_ctx *c = new vof_ctx();
+    std::memset(c->bufs, 0, sizeof(c->bufs));
+    c->nbufs = 0;
+    c->device = device;
+    c->np = np; c->nf = nf; c->ni = ni; c->nc = nc;
+    c->eps = (opt && opt->eps > 0.0) ? opt->eps : 1e-9;
+    c->precision = opt ? opt->precision : VOF_FP64;
+    c->bound = opt ? (opt->bound != 0) : 1;
+    int err = 0;
+    DevMesh &m = c->m;
+    m.np = np; m.nf = nf; m.ni = ni; m.nc = nc; m.eps = c->eps;
+    m.px = dev_copy(c, mesh->px, np, &err);
+    m.py = dev_copy(c, mesh->py, np, &err);
+    m.pz = dev_copy(c, mesh->pz, np, &err);
+    m.fptr = dev_copy(c, fptr, nf + 1, &err);
+    m.fpts = dev_copy(c, fpts, nfp, &err);
+    m.own = dev_copy(c, own, nf, &err);
+    m.nei = dev_copy(c, ni > 0 ? nei : own, std::max(ni, 1), &err);
+    m.cptr = dev_copy(c, cptr.data(), cptr.size(), &err);
+    m.cface = dev_copy(c, cface.data(), cface.size(), &err);
+    m.cpptr = dev_copy(c, cpptr.data(), cpptr.size(), &err);
+    m.cpts = dev_copy(c, cpts.data(), cpts.size(), &err);
+    m.pptr = dev_copy(c, pptr.data(), pptr.size(), &err);
+    m.pcell = dev_copy(c, pcell.data(), pcell.size(), &err);
+    m.pw = dev_alloc<double>(c, pcell.size(), &err);
+    m.sptr = dev_copy(c, sptr.data(), sptr.size(), &err);
+    m.scell = dev_copy(c, scell.data(), scell.size(), &err);
+    m.pwall = dev_copy(c, pwall.data(), pwall.size(), &err);
+    m.wallt = dev_alloc<double>(c, 7 * (size_t)std::max(nwrows, 1), &err);
+    int *d_wptr = dev_copy(c, wptr.data(), wptr.size(), &err);
+    int *d_wface = dev_copy(c, wface.empty() ? wptr.data() : wface.data(), std::max<size_t>(wface.size(), 1), &err);
+    m.cf = dev_alloc<double>(c, 3 * (size_t)nf, &err);
+    m.sf = dev_alloc<double>(c, 3 * (size_t)nf, &err);
+    m.cc = dev_alloc<double>(c, 3 * (size_t)nc, &err);
+    m.vc = dev_alloc<double>(c, nc, &err);
+    m.cbox = dev_alloc<double>(c, 6 * (size_t)nc, &err);
+    m.nagc = dev_alloc<double>(c, nfp, &err);
+    m.cf32 = nullptr;
+    m.cc32 = nullptr;
+    // per-step scratch
+    c->pstate = dev_alloc<uint8_t>(c, np, &err);
+    c->band = dev_alloc<int>(c, nf, &err);
+    c->icell = dev_alloc<int>(c, nc, &err);
+    c->viol[0] = dev_alloc<int>(c, nc, &err);
+    c->viol[1] = dev_alloc<int>(c, nc, &err);
+    c->pend_c = dev_alloc<int>(c, 8 * (size_t)nc, &err);
+    c->pend_a = dev_alloc<double>(c, 8 * (size_t)nc, &err);
+    c->counters = dev_alloc<int>(c, 16, &err);
+    c->lam_b = dev_alloc<double>(c, nf, &err);
+    c->disp_b = dev_alloc<double>(c, (size_t)nf * (VOF_MAXFP + 1) * 3, &err);
+    c->it_b = dev_alloc<int>(c, nf, &err);
+    c->n = dev_alloc<double>(c, 3 * (size_t)nc, &err);
+    c->d = dev_alloc<double>(c, nc, &err);
+    c->flags = dev_alloc<uint8_t>(c, nc, &err);
+    c->pit = dev_alloc<int>(c, nc, &err);
+    c->Va = dev_alloc<double>(c, nf, &err);
+    c->gv = dev_alloc<double>(c, nc, &err);
+    c->Cc = dev_alloc<double>(c, nc, &err);
+    c->partial = dev_alloc<double>(c, 10 * 1024, &err);
+    c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
+    c->status = dev_alloc<unsigned>(c, 1, &err);
+    c->h_alpha = dev_alloc<double>(c, nc, &err);
+    c->h_Uc = dev_alloc<double>(c, 3 * (size_t)nc, &err);
+    c->h_F = dev_alloc<double>(c, nf, &err);
+    c->work = dev_alloc<unsigned long long>(c, 4, &err);
+    if (err) { vof_destroy(c); return err; }
+    cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
+    cudaMemset(c->gv, 0, sizeof(double) * nc);
+    cudaMemset(c->Cc, 0, sizeof(double) * nc);
+    cudaMemset(c->counters, 0, sizeof(int) * 16);
+    cudaMemset(c->status, 0, sizeof(unsigned));
+    cudaMemset(c->n, 0, sizeof(double) * 3 * nc);
+    cudaMemset(c->d, 0, sizeof(double) * nc);
+    cudaMemset(c->flags, 0, nc);
+    int r = launch_setup_geometry(c, 0);
+    if (!r) r = launch_wall_table(c, d_wptr, d_wface, nwrows, 0);
+    if (r) { vof_destroy(c); return r; }
+    unsigned bad = 0;
+    if (cudaMemcpy(&bad, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        vof_destroy(c);
+        return VOF_ERR_CUDA;
+    }
+    if (bad) { vof_destroy(c); return VOF_ERR_BAD_MESH; }
+    *out = c;
+    return VOF_OK;
+}
+
+int vof_geometry(vof_ctx *c, double *cc, double *vc, double *cf, double *sf, void *stream)
+{
+    if (!c) return VOF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaSetDevice(c->device);
+    if (cc && cudaMemcpyAsync(cc, c->m.cc, 3 * sizeof(double) * c->nc, cudaMemcpyDeviceToDevice, s)) return VOF_ERR_CUDA;
+    if (vc && cudaMemcpyAsync(vc, c->m.vc, sizeof(double) * c->nc, cudaMemcpyDeviceToDevice, s)) return VOF_ERR_CUDA;
+    if (cf && cudaMemcpyAsync(cf, c->m.cf, 3 * sizeof(double) * c->nf, cudaMemcpyDeviceToDevice, s)) return VOF_ERR_CUDA;
+    if (sf && cudaMemcpyAsync(sf, c->m.sf, 3 * sizeof(double) * c->nf, cudaMemcpyDeviceToDevice, s)) return VOF_ERR_CUDA;
+    return VOF_OK;
+}
+
+int vof_point_velocity(vof_ctx *c, const double *Uc, double *Up, void *stream)
+{
+    if (!c || !Uc || !Up) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_point_velocity(c, Uc, Up, (cudaStream_t)stream);
+}
+
+int vof_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8_t *flags, int32_t *iters,
+                    void *stream)
+{
+    if (!c || !alpha || !n || !d || !flags) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_reconstruct(c, alpha, n, d, flags, iters, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+int vof_flux_polyhedra(vof_ctx *c, const double *Up, const double *F, const double *lambda, double dt,
+                       double *V, void *stream)
+{
+    if (!c || !Up || !V || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_flux_polyhedra(c, Up, F, lambda, dt, V, (cudaStream_t)stream);
+}
+
+int vof_correct_flux(vof_ctx *c, const double *Up, const double *F, double dt, double *lambda, int32_t *iters,
+                     void *stream)
+{
+    if (!c || !Up || !F || !lambda || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_correct_all(c, Up, F, dt, lambda, iters, (cudaStream_t)stream);
+}
+
+int vof_phase_flux(vof_ctx *c, const double *alpha, const double *n, const double *d, const uint8_t *flags,
+                   const double *Up, const double *F, const double *lambda, double dt, double *Va, void *stream)
+{
+    if (!c || !alpha || !n || !d || !flags || !Up || !F || !lambda || !Va || !finite_pos(dt))
+        return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_phase_flux_all(c, alpha, n, d, flags, Up, F, lambda, dt, Va, (cudaStream_t)stream);
+}
+
+int vof_update(vof_ctx *c, double *alpha, const double *Va, double *stats, void *stream)
+{
+    if (!c || !alpha || !Va) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_update(c, alpha, Va, stats, (cudaStream_t)stream);
+}
+
+int vof_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt, double *stats,
+               void *stream)
+{
+    if (!c || !alpha || !Uc || !F || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_advect(c, alpha, Uc, F, dt, stats, (cudaStream_t)stream);
+}
+
+int vof_advect_host(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt, double *stats,
+                    void *stream)
+{
+    if (!c || !alpha || !Uc || !F || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(c->h_Uc, Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
+        cudaMemcpyAsync(c->h_F, F, sizeof(double) * c->nf, cudaMemcpyHostToDevice, s))
+        return VOF_ERR_CUDA;
+    int r = launch_advect(c, c->h_alpha, c->h_Uc, c->h_F, dt, c->stats_dev, s);
+    if (r) return r;
+    if (cudaMemcpyAsync(alpha, c->h_alpha, sizeof(double) * c->nc, cudaMemcpyDeviceToHost, s)) return VOF_ERR_CUDA;
+    if (stats && cudaMemcpyAsync(stats, c->stats_dev, sizeof(double) * VOF_S_LEN, cudaMemcpyDeviceToHost, s))
+        return VOF_ERR_CUDA;
+    return VOF_OK;
+}
+
+int vof_status(vof_ctx *c, uint32_t *bits, void *stream)
+{
+    if (!c || !bits) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned v = 0;
+    if (cudaMemcpyAsync(&v, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOF_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VOF_ERR_CUDA;
+    if (cudaMemsetAsync(c->status, 0, sizeof(unsigned), s) != cudaSuccess) return VOF_ERR_CUDA;
+    *bits = v;
+    return VOF_OK;
+}
+
+int vof_last_launch_count(vof_ctx *c) { return c ? c->launches : 0; }
+
+int vof_profile_begin(vof_ctx *c, int max_steps)
+{
+    if (!c || max_steps <= 0) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    free_profile(c);
+    int n = max_steps * (VOF_PROF_GROUPS + 1);
+    c->prof_ev = new cudaEvent_t[n];
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) {
+            for (int j = 0; j < i; ++j) cudaEventDestroy(c->prof_ev[j]);
+            delete[] c->prof_ev;
+            c->prof_ev = nullptr;
+            return VOF_ERR_CUDA;
+        }
+    c->prof_max = max_steps;
+    c->prof_steps = 0;
+    return VOF_OK;
+}
+
+int vof_profile_end(vof_ctx *c, double *group_ms, int *steps)
+{
+    if (!c || !group_ms) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    for (int g = 0; g < VOF_PROF_GROUPS; ++g) group_ms[g] = 0.0;
+    int ns = c->prof_ev ? c->prof_steps : 0;
+    if (ns > 0 && cudaEventSynchronize(c->prof_ev[(size_t)(ns - 1) * (VOF_PROF_GROUPS + 1) + VOF_PROF_GROUPS]) != cudaSuccess)
+        return VOF_ERR_CUDA;
+    for (int k = 0; k < ns; ++k)
+        for (int g = 0; g < VOF_PROF_GROUPS; ++g) {
+            float ms = 0.f;
+            cudaEvent_t *e = c->prof_ev + (size_t)k * (VOF_PROF_GROUPS + 1);
+            if (cudaEventElapsedTime(&ms, e[g], e[g + 1]) != cudaSuccess) return VOF_ERR_CUDA;
+            group_ms[g] += ms;
+        }
+    if (steps) *steps = ns;
+    free_profile(c);
+    return VOF_OK;
+}
+
+int vof_work_counts(vof_ctx *c, unsigned long long counts[3], int reset, void *stream)
+{
+    if (!c || !counts) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long v[4] = {0, 0, 0, 0};
+    if (cudaMemcpyAsync(v, c->work, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOF_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return VOF_ERR_CUDA;
+    if (reset && cudaMemsetAsync(c->work, 0, sizeof(v), s) != cudaSuccess) return VOF_ERR_CUDA;
+    counts[0] = v[0]; counts[1] = v[1]; counts[2] = v[2];
+    return VOF_OK;
+}
+
+}  // extern "C"

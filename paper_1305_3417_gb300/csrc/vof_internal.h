@@ -1,0 +1,80 @@
+// Internal declarations of libvof: the context, the device-side mesh view
+// passed by value to kernels, and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/vof.h"
+
+#define VOF_MAXFP 8       // points per face handled by the per-face kernels
+#define VOF_MAXK_LANE 2   // cell tetrahedra per lane in the reconstruction warp (64 per cell)
+
+// Device view of the mesh, its derived topology and its geometry.  All
+// pointers are device pointers owned by the context.
+struct DevMesh {
+    int np, nf, ni, nc;
+    double eps;
+    const double *px, *py, *pz;
+    const int *fptr, *fpts, *own, *nei;
+    const int *cptr, *cface;     // cell -> face codes, code = 2*f + (cell is neighbour)
+    const int *cpptr, *cpts;     // cell -> distinct points (ascending)
+    const int *pptr, *pcell;     // point -> cells (ascending)
+    const double *pw;            // inverse-distance weight per (point, cell) entry
+    const int *sptr, *scell;     // face stencil: cells sharing a point with the face
+    const int *pwall;            // per point: wall-table row or -1
+    const double *wallt;         // wall table rows: count, n1 (3), n2 (3)
+    const double *cf, *sf;       // face centre, area vector [3*nf]
+    const double *cc, *vc, *cbox;  // cell centre [3*nc], volume [nc], box [6*nc]
+    const double *nagc;          // NAG face-value weight per face-point entry
+    const float *cf32, *cc32;    // single-precision copies for the mixed kernels
+};
+
+struct vof_ctx {
+    int device;
+    int np, nf, ni, nc;
+    double eps;
+    int precision, bound;
+    DevMesh m;
+    // owned device buffers (freed in vof_destroy)
+    void *bufs[64];
+    int nbufs;
+    // per-step scratch
+    uint8_t *pstate;
+    int *band, *icell, *viol[2], *pend_c;
+    double *pend_a;
+    int *counters;               // see CNT_* in vof_kernels.cu
+    double *lam_b, *disp_b;      // per band slot
+    int *it_b;
+    double *n, *d;
+    uint8_t *flags;
+    int *pit;
+    double *Va;
+    double *gv, *Cc;             // bounding scratch per cell
+    double *partial;             // reduction partials
+    double *stats_dev;           // internal stats buffer
+    unsigned *status;
+    double *h_alpha, *h_Uc, *h_F;  // device staging for vof_advect_host
+    int launches;
+    unsigned long long *work;    // [3] phase-flux work counters
+    // kernel-group timing (vof_profile_begin / _end)
+    cudaEvent_t *prof_ev;
+    int prof_max, prof_steps;
+};
+
+// ---- launchers (vof_kernels.cu) ----
+int launch_setup_geometry(vof_ctx *c, cudaStream_t s);
+int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t s);
+int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8_t *flags,
+                       int *iters, const int *list, const int *count, cudaStream_t s);
+int launch_flux_polyhedra(vof_ctx *c, const double *Up, const double *F, const double *lambda,
+                          double dt, double *V, cudaStream_t s);
+int launch_correct_all(vof_ctx *c, const double *Up, const double *F, double dt, double *lambda,
+                       int *iters, cudaStream_t s);
+int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
+                          const uint8_t *flags, const double *Up, const double *F,
+                          const double *lambda, double dt, double *Va, cudaStream_t s);
+int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cudaStream_t s);
+int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt,
+                  double *stats, cudaStream_t s);
+int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad);

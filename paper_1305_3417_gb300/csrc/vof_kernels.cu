@@ -1,0 +1,1302 @@
+// FP64 kernels of libvof: geometry set-up, reconstruction (NAG gradient + Alg. 1
+// positioning), point velocities, flux-polyhedron construction and correction,
+// phase fluxes by tetrahedral clipping, the conservative update and the
+// bounding pass.  Every kernel bounds its loops and reports problems through
+// the context status word; none traps.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "vof_internal.h"
+
+namespace {
+
+enum { CNT_BAND = 0, CNT_ICELL, CNT_VIOL0, CNT_VIOL1, CNT_PEND, CNT_MAXPOS, CNT_MAXCORR,
+       CNT_FALLBACK, CNT_LEN = 16 };
+
+constexpr int POS_MAXIT = 100;
+constexpr double POS_TOL = 1e-13;
+constexpr int CORR_MAXIT = 100;
+constexpr double CORR_TOL = 1e-14;
+constexpr double CORR_LMAX = 2.0;
+constexpr int CORR_NSAMP = 16;
+constexpr double BOUND_TOL = 1e-15;
+constexpr double BOUND_FLAG = 1e-12;
+constexpr int BOUND_PASSES = 8;
+constexpr int CLIP_STACK = 12;
+constexpr int DISP_STRIDE = (VOF_MAXFP + 1) * 3;
+
+// ------------------------------------------------------------------ vectors
+struct V3 { double x, y, z; };
+__device__ __forceinline__ V3 mk(double x, double y, double z) { return V3{x, y, z}; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ V3 operator*(V3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b)
+{
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double det3(V3 a, V3 b, V3 c) { return dot(a, cross(b, c)); }
+__device__ __forceinline__ double norm3(V3 a) { return sqrt(dot(a, a)); }
+// signed volume of tetrahedron (a,b,c,d)
+__device__ __forceinline__ double tvol(V3 a, V3 b, V3 c, V3 d) { return det3(b - a, c - a, d - a) / 6.0; }
+
+__device__ __forceinline__ V3 ldP(const DevMesh &m, int p)
+{
+    return mk(__ldg(m.px + p), __ldg(m.py + p), __ldg(m.pz + p));
+}
+__device__ __forceinline__ V3 ld3(const double *a, int n, int i)
+{
+    return mk(__ldg(a + i), __ldg(a + n + i), __ldg(a + 2 * n + i));
+}
+__device__ __forceinline__ void st3(double *a, int n, int i, V3 v)
+{
+    a[i] = v.x; a[n + i] = v.y; a[2 * n + i] = v.z;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// append with one atomic per warp
+__device__ __forceinline__ void warp_append(bool pred, int val, int *list, int *count, int cap,
+                                            unsigned *status)
+{
+    unsigned mask = __ballot_sync(0xffffffffu, pred);
+    if (!mask) return;
+    int lane = threadIdx.x & 31;
+    int leader = __ffs(mask) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(count, __popc(mask));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) {
+        int pos = base + __popc(mask & ((1u << lane) - 1u));
+        if (pos < cap) list[pos] = val;
+        else atomicOr(status, VOF_ST_CAPACITY);
+    }
+}
+
+// fraction of a tetrahedron below the level d of a linear function whose sorted
+// vertex values are h0 <= h1 <= h2 <= h3.  One/three vertices below: product of
+// edge fractions; two below: the wedge split into three tetrahedra, whose
+// barycentric volumes are ab, a(1-b)e and (1-a)ce -- all terms non-negative.
+__device__ __forceinline__ double frac_below(double h0, double h1, double h2, double h3, double d)
+{
+    if (d <= h0) return 0.0;
+    if (d >= h3) return 1.0;
+    if (d <= h1) {
+        double x = d - h0;
+        return (x / (h1 - h0)) * (x / (h2 - h0)) * (x / (h3 - h0));
+    }
+    if (d >= h2) {
+        double y = h3 - d;
+        return 1.0 - (y / (h3 - h0)) * (y / (h3 - h1)) * (y / (h3 - h2));
+    }
+    double a = (d - h0) / (h2 - h0), b = (d - h0) / (h3 - h0);
+    double c = (d - h1) / (h2 - h1), e = (d - h1) / (h3 - h1);
+    return a * b + a * (1.0 - b) * e + (1.0 - a) * c * e;
+}
+
+__device__ __forceinline__ void sort4(double &a, double &b, double &c, double &d)
+{
+    double t;
+#define CS(p, q) if (p > q) { t = p; p = q; q = t; }
+    CS(a, b) CS(c, d) CS(a, c) CS(b, d) CS(b, c)
+#undef CS
+}
+
+// i-th triangle of face f oriented along S_f (flip for the neighbour side)
+__device__ __forceinline__ void face_tri(const DevMesh &m, int f, int t, bool flip, V3 &t0, V3 &t1,
+                                         V3 &t2)
+{
+    int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
+    if (n == 3) {
+        t0 = ldP(m, __ldg(m.fpts + b)); t1 = ldP(m, __ldg(m.fpts + b + 1)); t2 = ldP(m, __ldg(m.fpts + b + 2));
+    } else {
+        t0 = ld3(m.cf, m.nf, f);
+        t1 = ldP(m, __ldg(m.fpts + b + t));
+        t2 = ldP(m, __ldg(m.fpts + b + (t + 1 == n ? 0 : t + 1)));
+    }
+    if (flip) { V3 s = t1; t1 = t2; t2 = s; }
+}
+
+// =========================================================== set-up kernels
+__global__ void k_face_geom(DevMesh m, double *cf, double *sf, double *nagc)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.nf) return;
+    int b = m.fptr[f], n = m.fptr[f + 1] - b;
+    V3 c = mk(0, 0, 0);
+    for (int i = 0; i < n; ++i) c = c + ldP(m, m.fpts[b + i]);
+    c = c * (1.0 / n);
+    V3 S = mk(0, 0, 0);
+    if (n == 3) {
+        V3 p0 = ldP(m, m.fpts[b]), p1 = ldP(m, m.fpts[b + 1]), p2 = ldP(m, m.fpts[b + 2]);
+        S = cross(p1 - p0, p2 - p0) * 0.5;
+    } else {
+        for (int t = 0; t < n; ++t) {
+            V3 a = ldP(m, m.fpts[b + t]) - c, e = ldP(m, m.fpts[b + (t + 1) % n]) - c;
+            S = S + cross(a, e) * 0.5;
+        }
+    }
+    // NAG face value (Sec. 2.2.1) as a weighted sum of the point values:
+    // phi_f = sum_t w_t (phi' + phi_t + phi_t+1)/3, phi' the point mean, w_t the
+    // area share of fan triangle t, so point k weighs (1/n + w_k + w_k-1)/3.
+    double A[VOF_MAXFP], sa = 0.0;
+    for (int t = 0; t < n; ++t) {
+        V3 a = ldP(m, m.fpts[b + t]) - c, e = ldP(m, m.fpts[b + (t + 1) % n]) - c;
+        A[t] = 0.5 * norm3(cross(a, e));
+        sa += A[t];
+    }
+    for (int k = 0; k < n; ++k)
+        nagc[b + k] = (1.0 / n + A[k] / sa + A[(k + n - 1) % n] / sa) / 3.0;
+    st3(cf, m.nf, f, c);
+    st3(sf, m.nf, f, S);
+}
+
+__global__ void k_cell_geom(DevMesh m, double *cc, double *vc, double *cbox, unsigned *bad)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    int p0 = m.cpptr[c], p1 = m.cpptr[c + 1];
+    V3 s = mk(0, 0, 0), lo = mk(1e300, 1e300, 1e300), hi = mk(-1e300, -1e300, -1e300);
+    for (int i = p0; i < p1; ++i) {
+        V3 p = ldP(m, m.cpts[i]);
+        s = s + p;
+        lo = mk(fmin(lo.x, p.x), fmin(lo.y, p.y), fmin(lo.z, p.z));
+        hi = mk(fmax(hi.x, p.x), fmax(hi.y, p.y), fmax(hi.z, p.z));
+    }
+    V3 ctr = s * (1.0 / (p1 - p0));
+    double V = 0.0;
+    for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+        int code = m.cface[k], f = code >> 1;
+        int n = m.fptr[f + 1] - m.fptr[f], nt = n == 3 ? 1 : n;
+        for (int t = 0; t < nt; ++t) {
+            V3 a, b, e;
+            face_tri(m, f, t, code & 1, a, b, e);
+            double v = tvol(ctr, a, b, e);
+            if (!(v > 0.0)) atomicOr(bad, 1u);
+            V += v;
+        }
+    }
+    st3(cc, m.nc, c, ctr);
+    vc[c] = V;
+    cbox[6 * c + 0] = lo.x; cbox[6 * c + 1] = lo.y; cbox[6 * c + 2] = lo.z;
+    cbox[6 * c + 3] = hi.x; cbox[6 * c + 4] = hi.y; cbox[6 * c + 5] = hi.z;
+}
+
+// Eq. w_pc: inverse distance from the point to each point-cell centre, normalised
+__global__ void k_point_weights(DevMesh m, double *pw)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.np) return;
+    V3 x = ldP(m, p);
+    double s = 0.0;
+    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) s += 1.0 / norm3(x - ld3(m.cc, m.nc, m.pcell[j]));
+    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j)
+        pw[j] = (1.0 / norm3(x - ld3(m.cc, m.nc, m.pcell[j]))) / s;
+}
+
+// wall table: distinct unit normals of the wall faces through each wall point
+__global__ void k_wall_table(DevMesh m, const int *wptr, const int *wface, int nrows, double *wallt)
+{
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrows) return;
+    int cnt = 0;
+    V3 v[2] = {mk(0, 0, 0), mk(0, 0, 0)};
+    for (int j = wptr[r]; j < wptr[r + 1]; ++j) {
+        int f = wface[j];
+        V3 S = ld3(m.sf, m.nf, f);
+        V3 u = S * (1.0 / norm3(S));
+        bool dup = false;
+        for (int k = 0; k < cnt && k < 2; ++k)
+            if (fabs(dot(u, v[k])) > 1.0 - 1e-12) dup = true;
+        if (dup || cnt >= 3) continue;
+        if (cnt < 2) v[cnt] = u;
+        ++cnt;
+    }
+    double *o = wallt + 7 * r;
+    o[0] = cnt;
+    o[1] = v[0].x; o[2] = v[0].y; o[3] = v[0].z;
+    o[4] = v[1].x; o[5] = v[1].y; o[6] = v[1].z;
+}
+
+// ====================================================== point velocity (A4)
+__device__ __forceinline__ V3 point_velocity(const DevMesh &m, int p, const double *__restrict__ Uc)
+{
+    V3 u = mk(0, 0, 0);
+    for (int j = __ldg(m.pptr + p); j < __ldg(m.pptr + p + 1); ++j) {
+        int c = __ldg(m.pcell + j);
+        u = u + ld3(Uc, m.nc, c) * __ldg(m.pw + j);
+    }
+    int r = __ldg(m.pwall + p);
+    if (r >= 0) {
+        const double *w = m.wallt + 7 * r;
+        int cnt = (int)w[0];
+        V3 n1 = mk(w[1], w[2], w[3]), n2 = mk(w[4], w[5], w[6]);
+        if (cnt == 1) u = u - n1 * dot(u, n1);
+        else if (cnt == 2) {
+            V3 t = cross(n1, n2);
+            t = t * (1.0 / norm3(t));
+            u = t * dot(u, t);
+        } else if (cnt >= 3) u = mk(0, 0, 0);
+    }
+    return u;
+}
+
+__global__ void k_point_velocity(DevMesh m, const double *__restrict__ Uc, double *Up)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.np) return;
+    st3(Up, m.np, p, point_velocity(m, p, Uc));
+}
+
+// ===================================================== reconstruction (A1-A3)
+// one warp per cell: NAG gradient over the (face, point) entries of the cell,
+// then Alg. 1 with the fill function summed over the cell tetrahedra, one or
+// two per lane, each a closed-form cut fraction of its sorted projections.
+template <bool LIST>
+__global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
+                                                     const int *list, const int *count, double *nout,
+                                                     double *dout, uint8_t *fout, int *itout,
+                                                     int *maxit, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int total = LIST ? *count : m.nc;
+    const double eps = m.eps;
+    for (int item = warp; item < total; item += nwarps) {
+        const int c = LIST ? list[item] : item;
+        const double a = alpha[c];
+        uint8_t fl = 0;
+        V3 nn = mk(0, 0, 0);
+        double dd = 0.0;
+        int it = 0;
+        if (a >= 1.0 - eps) fl = VOF_FULL;
+        else if (a > eps) {
+            fl = VOF_INTERFACE;
+            const int f0 = m.cptr[c], f1 = m.cptr[c + 1];
+            const double V = m.vc[c];
+            // ---- NAG gradient: lane j handles the j-th (face, point) entry
+            V3 g = mk(0, 0, 0);
+            for (int j = lane;; j += 32) {
+                int off = j, k = f0, code = 0, base = 0;
+                bool found = false;
+                for (; k < f1; ++k) {
+                    code = __ldg(m.cface + k);
+                    int f = code >> 1;
+                    base = __ldg(m.fptr + f);
+                    int n = __ldg(m.fptr + f + 1) - base;
+                    if (off < n) { found = true; break; }
+                    off -= n;
+                }
+                if (!found) break;
+                int f = code >> 1;
+                int p = __ldg(m.fpts + base + off);
+                double ap = 0.0;  // Eq. idwpointphi
+                for (int q = __ldg(m.pptr + p); q < __ldg(m.pptr + p + 1); ++q)
+                    ap += __ldg(m.pw + q) * __ldg(alpha + __ldg(m.pcell + q));
+                double w = __ldg(m.nagc + base + off) * ap;
+                if (code & 1) w = -w;  // Eq. own-nei: the neighbour sees -S_f
+                g = g + ld3(m.sf, m.nf, f) * w;
+            }
+            g = mk(warp_sum(g.x), warp_sum(g.y), warp_sum(g.z)) * (1.0 / V);
+            double gm = norm3(g);
+            if (gm * cbrt(V) > 1e-12) {
+                nn = g * (-1.0 / gm);  // points out of the phase
+                fl |= VOF_ORIENTED;
+                // ---- cell tetrahedra (c_c, outward face triangle), lanes j, j+32
+                const V3 ctr = ld3(m.cc, m.nc, c);
+                double h[VOF_MAXK_LANE][4], vk[VOF_MAXK_LANE];
+                double lo = 1e300, hi = -1e300;
+#pragma unroll
+                for (int s = 0; s < VOF_MAXK_LANE; ++s) {
+                    vk[s] = 0.0;
+                    h[s][0] = h[s][1] = h[s][2] = h[s][3] = 0.0;
+                    int off = lane + 32 * s, k = f0, code = 0, nt = 0;
+                    bool found = false;
+                    for (; k < f1; ++k) {
+                        code = __ldg(m.cface + k);
+                        int f = code >> 1;
+                        int n = __ldg(m.fptr + f + 1) - __ldg(m.fptr + f);
+                        nt = n == 3 ? 1 : n;
+                        if (off < nt) { found = true; break; }
+                        off -= nt;
+                    }
+                    if (!found) continue;
+                    V3 t0, t1, t2;
+                    face_tri(m, code >> 1, off, code & 1, t0, t1, t2);
+                    vk[s] = fabs(tvol(ctr, t0, t1, t2));
+                    double e0 = dot(nn, ctr), e1 = dot(nn, t0), e2 = dot(nn, t1), e3 = dot(nn, t2);
+                    sort4(e0, e1, e2, e3);
+                    h[s][0] = e0; h[s][1] = e1; h[s][2] = e2; h[s][3] = e3;
+                    lo = fmin(lo, e0);
+                    hi = fmax(hi, e3);
+                }
+                const double dmin = warp_min(lo), dmax = warp_max(hi);
+                // ---- Alg. 1: secant, bisection once the secant leaves the bracket
+                double A = dmin, B = dmax, x0 = A, g0 = -a, x1 = B, g1 = 1.0 - a, x = 0.0, gx = 0.0;
+                bool bisect = false;
+                while (it < POS_MAXIT) {
+                    if (!bisect) {
+                        x = x1 - g1 * (x1 - x0) / (g1 - g0);
+                        if (!(x > A && x < B)) bisect = true;
+                    }
+                    if (bisect) x = 0.5 * (A + B);
+                    double part = 0.0;
+#pragma unroll
+                    for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                        if (vk[s] > 0.0) part += vk[s] * frac_below(h[s][0], h[s][1], h[s][2], h[s][3], x);
+                    gx = warp_sum(part) / V - a;
+                    ++it;
+                    if (gx < 0) A = x; else B = x;
+                    x0 = x1; g0 = g1; x1 = x; g1 = gx;
+                    if (fabs(gx) <= POS_TOL) break;
+                    if (B - A <= 1e-15 * (dmax - dmin)) break;
+                }
+                if (it >= POS_MAXIT && lane == 0) atomicOr(status, VOF_ST_POS_NOT_CONVERGED);
+                dd = x;
+            }
+        }
+        if (lane == 0) {
+            if (nout) st3(nout, m.nc, c, nn);
+            if (dout) dout[c] = dd;
+            if (fout) fout[c] = fl;
+            if (itout) itout[c] = it;
+            if (maxit && it > 0) atomicMax(maxit, it);
+        }
+    }
+}
+
+// ======================================== flux polyhedra and correction (A5)
+// Cubic V(lambda) = C1 lambda + C2 lambda^2 + C3 lambda^3 of the signed swept
+// volume.  Each face triangle (a0,a1,a2), ordered by key (face centre first,
+// then global point index, parity par), sweeps to b_k = a_k - lambda w_k and is
+// split into the tetrahedra (a0,a1,a2,b2), (a0,a1,b2,b1), (a0,b0,b1,b2), whose
+// signed volumes -par*det/6 expand, with E1 = a1-a0, E2 = a2-a0, into
+//   k1 = -det(E1,E2,w0+w1+w2),  k2 = det(E1,w2,w1)+det(w0,w1,E2)+det(w0,E1,w2),
+//   k3 = -det(w0,w1,w2).
+struct Cubic { double c1, c2, c3, s1, s2, s3; };
+
+__device__ __forceinline__ void prism_cubic(V3 a0, V3 a1, V3 a2, V3 w0, V3 w1, V3 w2, long k0,
+                                            long k1, long k2, Cubic &q)
+{
+    int par = 1;
+    // sort (a,w,k) triples by key, tracking permutation parity
+    if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long u = k0; k0 = k1; k1 = u; par = -par; }
+    if (k2 < k1) { V3 t = a1; a1 = a2; a2 = t; t = w1; w1 = w2; w2 = t; long u = k1; k1 = k2; k2 = u; par = -par; }
+    if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long u = k0; k0 = k1; k1 = u; par = -par; }
+    V3 E1 = a1 - a0, E2 = a2 - a0;
+    double f = -par / 6.0;
+    double t1 = -det3(E1, E2, w0 + w1 + w2) * f;
+    double t2 = (det3(E1, w2, w1) + det3(w0, w1, E2) + det3(w0, E1, w2)) * f;
+    double t3 = -det3(w0, w1, w2) * f;
+    q.c1 += t1; q.c2 += t2; q.c3 += t3;
+    q.s1 += fabs(t1); q.s2 += fabs(t2); q.s3 += fabs(t3);
+}
+
+// loads the face's points and per-point displacements w = U_p dt
+template <bool IDW>
+__device__ __forceinline__ int face_points(const DevMesh &m, int f, const double *__restrict__ U,
+                                           double dt, V3 *A, V3 *W, int *id)
+{
+    int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
+    for (int i = 0; i < n; ++i) {
+        int p = __ldg(m.fpts + b + i);
+        id[i] = p;
+        A[i] = ldP(m, p);
+        V3 u = IDW ? point_velocity(m, p, U) : ld3(U, m.np, p);
+        W[i] = u * dt;
+    }
+    return n;
+}
+
+__device__ __forceinline__ Cubic face_cubic(const DevMesh &m, int f, int n, const V3 *A, const V3 *W,
+                                            const int *id)
+{
+    Cubic q = {0, 0, 0, 0, 0, 0};
+    if (n == 3) {
+        prism_cubic(A[0], A[1], A[2], W[0], W[1], W[2], id[0], id[1], id[2], q);
+    } else {
+        V3 c = ld3(m.cf, m.nf, f), wc = mk(0, 0, 0);
+        for (int i = 0; i < n; ++i) wc = wc + W[i];
+        wc = wc * (1.0 / n);
+        for (int t = 0; t < n; ++t) {
+            int u = t + 1 == n ? 0 : t + 1;
+            prism_cubic(c, A[t], A[u], wc, W[t], W[u], -1, id[t], id[u], q);
+        }
+    }
+    return q;
+}
+
+__device__ __forceinline__ double cubic_at(const Cubic &q, double x) { return ((q.c3 * x + q.c2) * x + q.c1) * x; }
+
+// Root of V(lambda) = tau in the first sign-changing interval of the grid
+// k*LMAX/NSAMP (the bracket is the same one the secant oracle uses), refined by
+// Newton steps that fall back to bisection when they leave the bracket.
+// Returns lambda, or -1 (normal-sweep fallback) when no interval brackets a root.
+__device__ double solve_lambda(const Cubic &q, double tau, int &its)
+{
+    its = 0;
+    if (tau == 0.0) return 0.0;
+    double lo = 0.0, rlo = -tau, hi = 0.0, rhi = 0.0;
+    bool found = false;
+    for (int k = 1; k <= CORR_NSAMP; ++k) {
+        double lk = k * (CORR_LMAX / CORR_NSAMP);
+        double rk = cubic_at(q, lk) - tau;
+        if (rk == 0.0) return lk;
+        if ((rk > 0) != (rlo > 0)) { hi = lk; rhi = rk; found = true; break; }
+        lo = lk; rlo = rk;
+    }
+    if (!found) return -1.0;
+    double x = lo - rlo * (hi - lo) / (rhi - rlo);
+    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+    while (its < CORR_MAXIT) {
+        double r = cubic_at(q, x) - tau;
+        double ax = fabs(x);
+        double scale = fmax(fabs(tau), ((q.s3 * ax + q.s2) * ax + q.s1) * ax);
+        ++its;
+        if ((r > 0) == (rhi > 0)) { hi = x; rhi = r; } else { lo = x; rlo = r; }
+        if (fabs(r) <= CORR_TOL * scale) break;
+        if (hi - lo <= 1e-15 * hi) break;
+        double dr = (3.0 * q.c3 * x + 2.0 * q.c2) * x + q.c1;
+        double xn = x - r / dr;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        x = xn;
+    }
+    return x;
+}
+
+__global__ void k_flux_polyhedra(DevMesh m, const double *__restrict__ Up, const double *F,
+                                 const double *lambda, double dt, double *V)
+{
+    int f = blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= m.nf) return;
+    V3 A[VOF_MAXFP], W[VOF_MAXFP];
+    int id[VOF_MAXFP];
+    int n = face_points<false>(m, f, Up, dt, A, W, id);
+    double lam = lambda ? lambda[f] : 1.0;
+    if (lam < 0.0) {  // normal sweep: uniform translation along S_f
+        V3 S = ld3(m.sf, m.nf, f);
+        V3 wn = S * (-lam * F[f] * dt / dot(S, S));
+        for (int i = 0; i < n; ++i) W[i] = wn;
+        lam = 1.0;
+    }
+    Cubic q = face_cubic(m, f, n, A, W, id);
+    V[f] = cubic_at(q, lam);
+}
+
+template <bool IDW, bool LIST>
+__global__ void k_correct(DevMesh m, const double *__restrict__ U, const double *__restrict__ F,
+                          double dt, const int *list, const int *count, double *lam_out,
+                          int *it_out, double *disp_out, int *maxit, int *nfallback)
+{
+    const int total = LIST ? *count : m.nf;
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+        const int f = LIST ? list[item] : item;
+        V3 A[VOF_MAXFP], W[VOF_MAXFP];
+        int id[VOF_MAXFP];
+        int n = face_points<IDW>(m, f, U, dt, A, W, id);
+        double tau = F[f] * dt;
+        Cubic q = face_cubic(m, f, n, A, W, id);
+        int its = 0;
+        double lam = solve_lambda(q, tau, its);
+        lam_out[item] = lam;
+        if (it_out) it_out[item] = its;
+        if (maxit && its > 0) atomicMax(maxit, its);
+        if (lam < 0.0 && nfallback) atomicAdd(nfallback, 1);
+        if (disp_out) {
+            double *o = disp_out + (size_t)item * DISP_STRIDE;
+            V3 wc = mk(0, 0, 0);
+            if (lam < 0.0) {
+                V3 S = ld3(m.sf, m.nf, f);
+                wc = S * (-lam * F[f] * dt / dot(S, S));
+                for (int i = 0; i < n; ++i) W[i] = wc;
+            } else {
+                for (int i = 0; i < n; ++i) { W[i] = W[i] * lam; wc = wc + W[i]; }
+                wc = wc * (1.0 / n);
+            }
+            o[0] = wc.x; o[1] = wc.y; o[2] = wc.z;
+            for (int i = 0; i < n; ++i) { o[3 + 3 * i] = W[i].x; o[4 + 3 * i] = W[i].y; o[5 + 3 * i] = W[i].z; }
+        }
+    }
+}
+
+// ========================================================= phase flux (A6)
+struct Tet { V3 v[4]; };
+
+// |T ^ {n_k.x <= d_k, k < np}| by depth-first splitting of T into the
+// tetrahedra of its inside parts (1 or 3 per plane); the last plane is applied
+// with the closed-form cut fraction.  Bounded stack: 1 + 2(np-1) entries.
+__device__ double clip_tet(const Tet &T, const V3 *pn, const double *pd, int np, unsigned *status,
+                          unsigned &cuts)
+{
+    if (np == 0) return fabs(tvol(T.v[0], T.v[1], T.v[2], T.v[3]));
+    Tet st[CLIP_STACK];
+    unsigned char lv[CLIP_STACK];
+    int sp = 1;
+    st[0] = T;
+    lv[0] = 0;
+    double vol = 0.0;
+    while (sp > 0) {
+        --sp;
+        Tet t = st[sp];
+        int k = lv[sp];
+        double s[4];
+        int nin = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { s[i] = dot(pn[k], t.v[i]) - pd[k]; nin += s[i] <= 0.0; }
+        if (nin == 0) continue;
+        if (nin == 4) {
+            if (k + 1 == np) vol += fabs(tvol(t.v[0], t.v[1], t.v[2], t.v[3]));
+            else if (sp < CLIP_STACK) { st[sp] = t; lv[sp] = k + 1; ++sp; }
+            else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
+            continue;
+        }
+        ++cuts;
+        if (k + 1 == np) {
+            double h0 = s[0], h1 = s[1], h2 = s[2], h3 = s[3];
+            sort4(h0, h1, h2, h3);
+            vol += fabs(tvol(t.v[0], t.v[1], t.v[2], t.v[3])) * frac_below(h0, h1, h2, h3, 0.0);
+            continue;
+        }
+        // order vertices: inside ones first
+        int ord[4], a = 0, b = 3;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { if (s[i] <= 0.0) ord[a++] = i; else ord[b--] = i; }
+        V3 P[4];
+        double S[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) { P[i] = t.v[ord[i]]; S[i] = s[ord[i]]; }
+        // point on edge (inside i, outside o), interpolated from the inside end
+        auto ep = [&](int i, int o) { return P[i] + (P[o] - P[i]) * (S[i] / (S[i] - S[o])); };
+        Tet out[3];
+        int nout;
+        if (nin == 1) {
+            out[0] = Tet{{P[0], ep(0, 1), ep(0, 2), ep(0, 3)}};
+            nout = 1;
+        } else if (nin == 2) {
+            // wedge (P0, p02, p03) -> (P1, p12, p13)
+            V3 a0 = P[0], a1 = ep(0, 2), a2 = ep(0, 3), b0 = P[1], b1 = ep(1, 2), b2 = ep(1, 3);
+            out[0] = Tet{{a0, a1, a2, b2}};
+            out[1] = Tet{{a0, a1, b2, b1}};
+            out[2] = Tet{{a0, b0, b1, b2}};
+            nout = 3;
+        } else {
+            // prism (P0, P1, P2) -> (p03, p13, p23)
+            V3 a0 = P[0], a1 = P[1], a2 = P[2], b0 = ep(0, 3), b1 = ep(1, 3), b2 = ep(2, 3);
+            out[0] = Tet{{a0, a1, a2, b2}};
+            out[1] = Tet{{a0, a1, b2, b1}};
+            out[2] = Tet{{a0, b0, b1, b2}};
+            nout = 3;
+        }
+        for (int i = 0; i < nout; ++i) {
+            if (sp < CLIP_STACK) { st[sp] = out[i]; lv[sp] = k + 1; ++sp; }
+            else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
+        }
+    }
+    return vol;
+}
+
+struct PFArgs {
+    const double *alpha, *n, *d;
+    const uint8_t *flags;
+    const double *Up, *F, *lambda;
+    double dt;
+    double *Va;
+    const int *list, *count;
+    const double *disp;   // per list slot displacements (LIST mode)
+    unsigned *status;
+    unsigned long long *work;  // [pairs, cuts, faces]
+};
+
+constexpr int PF_WARPS = 4;
+constexpr int PF_MAXT = 3 * VOF_MAXFP;
+
+template <bool LIST>
+__global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs a)
+{
+    __shared__ Tet sT[PF_WARPS][PF_MAXT];
+    __shared__ double sSg[PF_WARPS][PF_MAXT];
+    __shared__ double sBox[PF_WARPS][PF_MAXT][6];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int total = LIST ? *a.count : m.nf;
+    const double eps = m.eps;
+    for (int item = warp; item < total; item += nwarps) {
+        const int f = LIST ? a.list[item] : item;
+        const int s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
+        if (!LIST) {
+            // trivial faces (reading R9) and boundary inflow
+            double Ff = a.F[f];
+            bool all_e = true, all_f = true;
+            for (int s = s0 + lane; s < s1; s += 32) {
+                double al = a.alpha[__ldg(m.scell + s)];
+                all_e &= al <= eps;
+                all_f &= al >= 1.0 - eps;
+            }
+            all_e = __all_sync(0xffffffffu, all_e);
+            all_f = __all_sync(0xffffffffu, all_f);
+            double triv = 0.0;
+            bool done = true;
+            if (Ff == 0.0 || (f >= m.ni && Ff < 0.0) || all_e) triv = 0.0;
+            else if (all_f) triv = Ff * a.dt;
+            else done = false;
+            if (done) {
+                if (lane == 0) a.Va[f] = triv;
+                continue;
+            }
+        }
+        // ---- flux polyhedron tetrahedra, one per lane
+        const int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
+        const int nt = n == 3 ? 3 : 3 * n;
+        if (lane < nt) {
+            int pr = lane / 3, j = lane % 3;
+            V3 a0, a1, a2, w0, w1, w2;
+            long k0, k1, k2;
+            auto disp = [&](int i) -> V3 {  // i < 0: face centre
+                if (LIST) {
+                    const double *o = a.disp + (size_t)item * DISP_STRIDE + (i < 0 ? 0 : 3 + 3 * i);
+                    return mk(o[0], o[1], o[2]);
+                }
+                double lam = a.lambda[f];
+                if (lam < 0.0) {
+                    V3 S = ld3(m.sf, m.nf, f);
+                    return S * (-lam * a.F[f] * a.dt / dot(S, S));
+                }
+                if (i >= 0) return ld3(a.Up, m.np, __ldg(m.fpts + b + i)) * (a.dt * lam);
+                V3 wc = mk(0, 0, 0);
+                for (int q = 0; q < n; ++q) wc = wc + ld3(a.Up, m.np, __ldg(m.fpts + b + q)) * (a.dt * lam);
+                return wc * (1.0 / n);
+            };
+            if (n == 3) {
+                k0 = __ldg(m.fpts + b); k1 = __ldg(m.fpts + b + 1); k2 = __ldg(m.fpts + b + 2);
+                a0 = ldP(m, (int)k0); a1 = ldP(m, (int)k1); a2 = ldP(m, (int)k2);
+                w0 = disp(0); w1 = disp(1); w2 = disp(2);
+            } else {
+                int u = pr + 1 == n ? 0 : pr + 1;
+                k0 = -1; k1 = __ldg(m.fpts + b + pr); k2 = __ldg(m.fpts + b + u);
+                a0 = ld3(m.cf, m.nf, f); a1 = ldP(m, (int)k1); a2 = ldP(m, (int)k2);
+                w0 = disp(-1); w1 = disp(pr); w2 = disp(u);
+            }
+            int par = 1;
+            if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
+            if (k2 < k1) { V3 t = a1; a1 = a2; a2 = t; t = w1; w1 = w2; w2 = t; long q = k1; k1 = k2; k2 = q; par = -par; }
+            if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
+            V3 b0 = a0 - w0, b1 = a1 - w1, b2 = a2 - w2;
+            Tet T;
+            if (j == 0) T = Tet{{a0, a1, a2, b2}};
+            else if (j == 1) T = Tet{{a0, a1, b2, b1}};
+            else T = Tet{{a0, b0, b1, b2}};
+            double sv = -par * tvol(T.v[0], T.v[1], T.v[2], T.v[3]);
+            sT[wib][lane] = T;
+            sSg[wib][lane] = sv > 0.0 ? 1.0 : (sv < 0.0 ? -1.0 : 0.0);
+            double *bx = sBox[wib][lane];
+            bx[0] = fmin(fmin(T.v[0].x, T.v[1].x), fmin(T.v[2].x, T.v[3].x));
+            bx[1] = fmin(fmin(T.v[0].y, T.v[1].y), fmin(T.v[2].y, T.v[3].y));
+            bx[2] = fmin(fmin(T.v[0].z, T.v[1].z), fmin(T.v[2].z, T.v[3].z));
+            bx[3] = fmax(fmax(T.v[0].x, T.v[1].x), fmax(T.v[2].x, T.v[3].x));
+            bx[4] = fmax(fmax(T.v[0].y, T.v[1].y), fmax(T.v[2].y, T.v[3].y));
+            bx[5] = fmax(fmax(T.v[0].z, T.v[1].z), fmax(T.v[2].z, T.v[3].z));
+        }
+        __syncwarp();
+        // ---- (tetrahedron, stencil cell) pairs over the lanes
+        double acc = 0.0;
+        unsigned npairs = 0, ncuts = 0;
+        const int ns = s1 - s0, nitems = nt * ns;
+        for (int w = lane; w < nitems; w += 32) {
+            const int t = w % nt, c = __ldg(m.scell + s0 + w / nt);
+            const double sg = sSg[wib][t];
+            if (sg == 0.0) continue;
+            const double al = a.alpha[c];
+            if (al <= eps) continue;  // empty cell carries no phase
+            const double *bx = sBox[wib][t];
+            const double *cb = m.cbox + 6 * (size_t)c;
+            if (bx[3] < cb[0] || cb[3] < bx[0] || bx[4] < cb[1] || cb[4] < bx[1] || bx[5] < cb[2] || cb[5] < bx[2])
+                continue;
+            const Tet &T = sT[wib][t];
+            double wgt = 1.0;
+            bool useH = false;
+            V3 hn = mk(0, 0, 0);
+            double hd = 0.0;
+            if (al < 1.0 - eps) {
+                if (a.flags[c] & VOF_ORIENTED) {
+                    hn = ld3(a.n, m.nc, c);
+                    hd = a.d[c];
+                    int nin = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) nin += dot(hn, T.v[i]) - hd <= 0.0;
+                    if (nin == 0) continue;
+                    useH = nin < 4;
+                } else wgt = al;  // unoriented mixed cell: homogeneous
+            }
+            const V3 ctr = ld3(m.cc, m.nc, c);
+            double vsum = 0.0;
+            for (int k = __ldg(m.cptr + c); k < __ldg(m.cptr + c + 1); ++k) {
+                const int code = __ldg(m.cface + k), g = code >> 1;
+                const int gn = __ldg(m.fptr + g + 1) - __ldg(m.fptr + g);
+                const int gt = gn == 3 ? 1 : gn;
+                for (int tt = 0; tt < gt; ++tt) {
+                    V3 k1, k2, k3;
+                    face_tri(m, g, tt, code & 1, k1, k2, k3);
+                    // K = (ctr, k1, k2, k3), positively oriented
+                    double lx = fmin(fmin(ctr.x, k1.x), fmin(k2.x, k3.x)), hx = fmax(fmax(ctr.x, k1.x), fmax(k2.x, k3.x));
+                    if (hx < bx[0] || bx[3] < lx) continue;
+                    double ly = fmin(fmin(ctr.y, k1.y), fmin(k2.y, k3.y)), hy = fmax(fmax(ctr.y, k1.y), fmax(k2.y, k3.y));
+                    if (hy < bx[1] || bx[4] < ly) continue;
+                    double lz = fmin(fmin(ctr.z, k1.z), fmin(k2.z, k3.z)), hz = fmax(fmax(ctr.z, k1.z), fmax(k2.z, k3.z));
+                    if (hz < bx[2] || bx[5] < lz) continue;
+                    ++npairs;
+                    V3 pn[5];
+                    double pd[5];
+                    // outward planes of (ctr,k1,k2,k3): faces (ctr,k2,k1),(ctr,k1,k3),(ctr,k3,k2),(k1,k2,k3)
+                    pn[0] = cross(k2 - ctr, k1 - ctr); pd[0] = dot(pn[0], ctr);
+                    pn[1] = cross(k1 - ctr, k3 - ctr); pd[1] = dot(pn[1], ctr);
+                    pn[2] = cross(k3 - ctr, k2 - ctr); pd[2] = dot(pn[2], ctr);
+                    pn[3] = cross(k2 - k1, k3 - k1);   pd[3] = dot(pn[3], k1);
+                    int np = 0;
+                    V3 an[5];
+                    double ad[5];
+                    bool outside = false;
+                    for (int q = 0; q < 4; ++q) {
+                        int nin = 0;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) nin += dot(pn[q], T.v[i]) - pd[q] <= 0.0;
+                        if (nin == 0) { outside = true; break; }
+                        if (nin < 4) { an[np] = pn[q]; ad[np] = pd[q]; ++np; }
+                    }
+                    if (outside) continue;
+                    if (useH) { an[np] = hn; ad[np] = hd; ++np; }
+                    vsum += clip_tet(T, an, ad, np, a.status, ncuts);
+                }
+            }
+            acc += sg * wgt * vsum;
+        }
+        acc = warp_sum(acc);
+        if (a.work) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
+                ncuts += __shfl_xor_sync(0xffffffffu, ncuts, o);
+            }
+            if (lane == 0) {
+                atomicAdd(a.work, (unsigned long long)npairs);
+                atomicAdd(a.work + 1, (unsigned long long)ncuts);
+                atomicAdd(a.work + 2, 1ull);
+            }
+        }
+        if (lane == 0) a.Va[f] = acc;
+        __syncwarp();
+    }
+}
+
+// ============================================================ update (A7)
+constexpr int UPD_THREADS = 256;
+constexpr int UPD_BLOCKS = 1024;
+// partial layout per block: [mass_before, mass_after, min, max, boundary_out]
+
+__device__ __forceinline__ void block_reduce5(double v[5], double *out)
+{
+    __shared__ double sh[5][UPD_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        v[1] += __shfl_xor_sync(0xffffffffu, v[1], o);
+        v[2] = fmin(v[2], __shfl_xor_sync(0xffffffffu, v[2], o));
+        v[3] = fmax(v[3], __shfl_xor_sync(0xffffffffu, v[3], o));
+        v[4] += __shfl_xor_sync(0xffffffffu, v[4], o);
+    }
+    if (lane == 0) for (int i = 0; i < 5; ++i) sh[i][w] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+        for (int k = 0; k < UPD_THREADS / 32; ++k) {
+            r[0] += sh[0][k]; r[1] += sh[1][k];
+            r[2] = fmin(r[2], sh[2][k]); r[3] = fmax(r[3], sh[3][k]);
+            r[4] += sh[4][k];
+        }
+        for (int i = 0; i < 5; ++i) out[i] = r[i];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha, const double *__restrict__ Va,
+                                                        double *partial, int *viol, int *nviol, int cap,
+                                                        unsigned *status)
+{
+    double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    const int nb = m.nf - m.ni;
+    const int stride = gridDim.x * blockDim.x;
+    const int lim = m.nc > nb ? m.nc : nb;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < lim; i0 += stride) {
+        int c = i0 + threadIdx.x;
+        bool bad = false;
+        if (c < m.nc) {
+            double s = 0.0;
+            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+                int code = m.cface[k];
+                double x = Va[code >> 1];
+                s += (code & 1) ? -x : x;
+            }
+            double a0 = alpha[c], V = m.vc[c];
+            double a1 = a0 - s / V;
+            alpha[c] = a1;
+            v[0] += V * a0;
+            v[1] += V * a1;
+            v[2] = fmin(v[2], a1);
+            v[3] = fmax(v[3], a1);
+            bad = a1 > 1.0 + BOUND_TOL || a1 < -BOUND_TOL;
+        }
+        if (c < nb) v[4] += Va[m.ni + c];
+        if (viol) warp_append(bad, c, viol, nviol, cap, status);
+    }
+    block_reduce5(v, partial + 5 * blockIdx.x);
+}
+
+// final fixed-order reduction of the per-block partials into stats
+__global__ void k_stats(const double *partial, int nblk, const int *counters, double *stats, int post,
+                        double *bound_partial)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double r[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    for (int k = 0; k < nblk; ++k) {
+        r[0] += partial[5 * k]; r[1] += partial[5 * k + 1];
+        r[2] = fmin(r[2], partial[5 * k + 2]); r[3] = fmax(r[3], partial[5 * k + 3]);
+        r[4] += partial[5 * k + 4];
+    }
+    stats[VOF_S_MASS_BEFORE] = r[0];
+    stats[VOF_S_MIN_PRE] = r[2];
+    stats[VOF_S_MAX_PRE] = r[3];
+    stats[VOF_S_BOUNDARY_OUT] = r[4];
+    if (!post) {
+        stats[VOF_S_MASS_AFTER] = r[1];
+        stats[VOF_S_MIN_POST] = r[2];
+        stats[VOF_S_MAX_POST] = r[3];
+    } else {
+        double q[3] = {0.0, 1e300, -1e300};
+        for (int k = 0; k < nblk; ++k) {
+            q[0] += bound_partial[5 * k + 1];
+            q[1] = fmin(q[1], bound_partial[5 * k + 2]);
+            q[2] = fmax(q[2], bound_partial[5 * k + 3]);
+        }
+        stats[VOF_S_MASS_AFTER] = q[0];
+        stats[VOF_S_MIN_POST] = q[1];
+        stats[VOF_S_MAX_POST] = q[2];
+    }
+    if (counters) {
+        stats[VOF_S_N_INTERFACE] = counters[CNT_ICELL];
+        stats[VOF_S_N_BAND] = counters[CNT_BAND];
+        stats[VOF_S_MAX_POS_IT] = counters[CNT_MAXPOS];
+        stats[VOF_S_MAX_CORR_IT] = counters[CNT_MAXCORR];
+        stats[VOF_S_N_FALLBACK] = counters[CNT_FALLBACK];
+    }
+}
+
+// post-bounding mass / extrema
+__global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *alpha, double *partial)
+{
+    double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
+        double a = alpha[c];
+        v[1] += m.vc[c] * a;
+        v[2] = fmin(v[2], a);
+        v[3] = fmax(v[3], a);
+    }
+    block_reduce5(v, partial + 5 * blockIdx.x);
+}
+
+// ------------------------------------------------- bounding pass (reading R10)
+// Excess above 1 (deficit below 0) of a source cell is handed to its face
+// neighbours in proportion to their free (filled) volume; a receiver offers its
+// capacity divided by its number of sources.  Three kernels per pass over the
+// list of violating cells: (1) per source the sum of its neighbours' offers and
+// the amount it gives or takes, (2) per receiver -- visited once, by its
+// lowest-index source -- the new value from all its sources, (3) apply.
+__device__ __forceinline__ int nbr_of(const DevMesh &m, int c, int k)
+{
+    int code = m.cface[k], f = code >> 1;
+    if (f >= m.ni) return -1;
+    return (code & 1) ? m.own[f] : m.nei[f];
+}
+__device__ __forceinline__ bool is_exc(double a) { return a > 1.0 + BOUND_TOL; }
+__device__ __forceinline__ bool is_def(double a) { return a < -BOUND_TOL; }
+
+// offers of cell c: excess offer (free volume) and deficit offer (phase volume)
+__device__ __forceinline__ void offers(const DevMesh &m, const double *alpha, int c, double &op, double &om)
+{
+    int sp = 0, sm = 0;
+    for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+        int nb = nbr_of(m, c, k);
+        if (nb < 0) continue;
+        double a = alpha[nb];
+        sp += is_exc(a);
+        sm += is_def(a);
+    }
+    double a = alpha[c], V = m.vc[c];
+    op = (a >= 0.0 && a < 1.0) ? (1.0 - a) * V / (sp > 0 ? sp : 1) : 0.0;
+    om = (a > 0.0 && a <= 1.0) ? a * V / (sm > 0 ? sm : 1) : 0.0;
+}
+
+__global__ void k_bound_sources(DevMesh m, const double *alpha, const int *src, const int *nsrc,
+                                double *gv, double *Cc)
+{
+    int n = *nsrc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = src[i];
+        double a = alpha[c], V = m.vc[c], sp = 0.0, sm = 0.0;
+        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+            int nb = nbr_of(m, c, k);
+            if (nb < 0) continue;
+            double op, om;
+            offers(m, alpha, nb, op, om);
+            sp += op;
+            sm += om;
+        }
+        if (a > 1.0) { double e = (a - 1.0) * V; gv[c] = fmin(e, sp); Cc[c] = sp; }
+        else { double u = -a * V; gv[c] = -fmin(u, sm); Cc[c] = sm; }
+    }
+}
+
+__global__ void k_bound_receivers(DevMesh m, const double *alpha, const int *src, const int *nsrc,
+                                  const double *gv, const double *Cc, int *pc, double *pa, int *npend,
+                                  int cap, unsigned *status)
+{
+    int n = *nsrc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = src[i];
+        double V = m.vc[c];
+        double g = gv[c];
+        // the source itself: gives its excess away or takes its deficit back
+        if (g != 0.0) {
+            double na = (alpha[c] * V - (g > 0.0 ? g : 0.0) + (g < 0.0 ? -g : 0.0)) / V;
+            int pos = atomicAdd(npend, 1);
+            if (pos < cap) { pc[pos] = c; pa[pos] = na; } else atomicOr(status, VOF_ST_CAPACITY);
+        }
+        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+            int nb = nbr_of(m, c, k);
+            if (nb < 0) continue;
+            double anb = alpha[nb];
+            if (is_exc(anb) || is_def(anb)) continue;  // sources never receive
+            // visited once: by its lowest-index violating neighbour
+            int first = 0x7fffffff;
+            for (int q = m.cptr[nb]; q < m.cptr[nb + 1]; ++q) {
+                int s = nbr_of(m, nb, q);
+                if (s < 0) continue;
+                double as = alpha[s];
+                if ((is_exc(as) || is_def(as)) && s < first) first = s;
+            }
+            if (first != c) continue;
+            double op, om;
+            offers(m, alpha, nb, op, om);
+            double rec = 0.0, out = 0.0;
+            for (int q = m.cptr[nb]; q < m.cptr[nb + 1]; ++q) {
+                int s = nbr_of(m, nb, q);
+                if (s < 0) continue;
+                double as = alpha[s];
+                if (is_exc(as) && gv[s] > 0.0) rec += gv[s] * (op / Cc[s]);
+                if (is_def(as) && gv[s] < 0.0) out += -gv[s] * (om / Cc[s]);
+            }
+            if (rec != 0.0 || out != 0.0) {
+                double Vn = m.vc[nb];
+                double na = (anb * Vn + rec - out) / Vn;
+                int pos = atomicAdd(npend, 1);
+                if (pos < cap) { pc[pos] = nb; pa[pos] = na; } else atomicOr(status, VOF_ST_CAPACITY);
+            }
+        }
+    }
+}
+
+__global__ void k_bound_apply(double *alpha, const int *src, const int *nsrc, double *gv, double *Cc,
+                              const int *pc, const double *pa, const int *npend)
+{
+    int n = *npend, ns = *nsrc;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        alpha[pc[i]] = pa[i];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
+        int c = src[i];
+        gv[c] = 0.0;
+        Cc[c] = 0.0;
+    }
+}
+
+__global__ void k_bound_collect(const double *alpha, const int *src, const int *nsrc, int *next,
+                                int *nnext, int cap, unsigned *status, int last)
+{
+    int n = *nsrc;
+    int lim = (n + 31) & ~31;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
+        bool keep = false;
+        int c = 0;
+        if (i < n) {
+            c = src[i];
+            double a = alpha[c];
+            keep = a > 1.0 + BOUND_TOL || a < -BOUND_TOL;
+            if (last && (a > 1.0 + BOUND_FLAG || a < -BOUND_FLAG)) atomicOr(status, VOF_ST_BOUND_RESIDUAL);
+        }
+        if (!last) warp_append(keep, c, next, nnext, cap, status);
+    }
+}
+
+__global__ void k_zero_int(int *p, int n)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0;
+}
+
+// ============================================== band classification (A2, R9)
+__global__ void k_point_state(DevMesh m, const double *__restrict__ alpha, uint8_t *state)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.np) return;
+    bool all_e = true, all_f = true;
+    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) {
+        double a = __ldg(alpha + m.pcell[j]);
+        all_e &= a <= m.eps;
+        all_f &= a >= 1.0 - m.eps;
+    }
+    state[p] = (all_e ? 1 : 0) | (all_f ? 2 : 0);
+}
+
+__global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const double *__restrict__ F,
+                           double dt, const uint8_t *__restrict__ state, double *Va, int *band, int *nband,
+                           int *icell, int *nicell, unsigned *status)
+{
+    const int lim = m.nf > m.nc ? m.nf : m.nc;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < lim; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        bool isband = false, isint = false;
+        if (i < m.nf) {
+            double Ff = F[i];
+            double v = 0.0;
+            if (Ff != 0.0 && !(i >= m.ni && Ff < 0.0)) {
+                unsigned st = 3u;
+                for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) st &= state[m.fpts[k]];
+                if (st & 1u) v = 0.0;
+                else if (st & 2u) v = Ff * dt;
+                else isband = true;
+            }
+            Va[i] = v;
+        }
+        if (i < m.nc) {
+            double a = alpha[i];
+            isint = a > m.eps && a < 1.0 - m.eps;
+        }
+        warp_append(isband, i, band, nband, m.nf, status);
+        warp_append(isint, i, icell, nicell, m.nc, status);
+    }
+}
+
+inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace
+
+// ================================================================ launchers
+#define LAUNCH_CHECK()                                            \
+    do {                                                          \
+        cudaError_t e_ = cudaGetLastError();                      \
+        if (e_ != cudaSuccess) return VOF_ERR_CUDA;               \
+    } while (0)
+
+static int g_sms = 0;
+static int num_sms(int dev)
+{
+    if (g_sms == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        g_sms = v > 0 ? v : 148;
+    }
+    return g_sms;
+}
+
+int launch_setup_geometry(vof_ctx *c, cudaStream_t s)
+{
+    DevMesh &m = c->m;
+    k_face_geom<<<cdiv(m.nf, 256), 256, 0, s>>>(m, (double *)m.cf, (double *)m.sf, (double *)m.nagc);
+    LAUNCH_CHECK();
+    unsigned *bad = c->status;
+    k_cell_geom<<<cdiv(m.nc, 256), 256, 0, s>>>(m, (double *)m.cc, (double *)m.vc, (double *)m.cbox, bad);
+    LAUNCH_CHECK();
+    k_point_weights<<<cdiv(m.np, 256), 256, 0, s>>>(m, (double *)m.pw);
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+int launch_wall_table(vof_ctx *c, const int *wptr, const int *wface, int nrows, cudaStream_t s)
+{
+    if (nrows == 0) return VOF_OK;
+    k_wall_table<<<cdiv(nrows, 256), 256, 0, s>>>(c->m, wptr, wface, nrows, (double *)c->m.wallt);
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t s)
+{
+    k_point_velocity<<<cdiv(c->np, 256), 256, 0, s>>>(c->m, Uc, Up);
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8_t *flags, int *iters,
+                       const int *list, const int *count, cudaStream_t s)
+{
+    int sms = num_sms(c->device);
+    if (list) {
+        k_reconstruct<true><<<sms * 8, 256, 0, s>>>(c->m, alpha, list, count, n, d, flags, iters,
+                                                    c->counters + CNT_MAXPOS, c->status);
+    } else {
+        k_reconstruct<false><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(c->m, alpha, nullptr, nullptr, n, d, flags,
+                                                                         iters, nullptr, c->status);
+    }
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+int launch_flux_polyhedra(vof_ctx *c, const double *Up, const double *F, const double *lambda, double dt,
+                          double *V, cudaStream_t s)
+{
+    k_flux_polyhedra<<<cdiv(c->nf, 128), 128, 0, s>>>(c->m, Up, F, lambda, dt, V);
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+int launch_correct_all(vof_ctx *c, const double *Up, const double *F, double dt, double *lambda, int *iters,
+                       cudaStream_t s)
+{
+    k_correct<false, false><<<cdiv(c->nf, 128), 128, 0, s>>>(c->m, Up, F, dt, nullptr, nullptr, lambda, iters,
+                                                             nullptr, nullptr, nullptr);
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, const double *d, const uint8_t *flags,
+                          const double *Up, const double *F, const double *lambda, double dt, double *Va,
+                          cudaStream_t s)
+{
+    PFArgs a{alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr, c->status, nullptr};
+    k_phase_flux<false><<<cdiv((long)c->nf * 32, PF_WARPS * 32), PF_WARPS * 32, 0, s>>>(c->m, a);
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
+static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches)
+{
+    int sms = num_sms(c->device);
+    int *cnt = c->counters;
+    for (int p = 0; p < BOUND_PASSES; ++p) {
+        int cur = p & 1;
+        int *src = c->viol[cur], *nsrc = cnt + CNT_VIOL0 + cur;
+        int *nxt = c->viol[cur ^ 1], *nnxt = cnt + CNT_VIOL0 + (cur ^ 1);
+        k_zero_int<<<1, 32, 0, s>>>(cnt + CNT_PEND, 1);
+        k_zero_int<<<1, 32, 0, s>>>(nnxt, 1);
+        k_bound_sources<<<sms * 2, 128, 0, s>>>(c->m, alpha, src, nsrc, c->gv, c->Cc);
+        k_bound_receivers<<<sms * 2, 128, 0, s>>>(c->m, alpha, src, nsrc, c->gv, c->Cc, c->pend_c, c->pend_a,
+                                                  cnt + CNT_PEND, 8 * c->nc, c->status);
+        k_bound_apply<<<sms * 2, 128, 0, s>>>(alpha, src, nsrc, c->gv, c->Cc, c->pend_c, c->pend_a,
+                                              cnt + CNT_PEND);
+        k_bound_collect<<<sms * 2, 128, 0, s>>>(alpha, src, nsrc, nxt, nnxt, c->nc, c->status,
+                                                p + 1 == BOUND_PASSES);
+        *launches += 6;
+        LAUNCH_CHECK();
+    }
+    return VOF_OK;
+}
+
+int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cudaStream_t s)
+{
+    int *cnt = c->counters;
+    int launches = 0;
+    k_zero_int<<<1, 32, 0, s>>>(cnt + CNT_VIOL0, 2);
+    k_update<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, Va, c->partial, c->bound ? c->viol[0] : nullptr,
+                                                cnt + CNT_VIOL0, c->nc, c->status);
+    LAUNCH_CHECK();
+    launches += 2;
+    if (c->bound) {
+        int r = run_bounding(c, alpha, s, &launches);
+        if (r) return r;
+        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, c->partial + 5 * UPD_BLOCKS);
+        ++launches;
+    }
+    k_stats<<<1, 32, 0, s>>>(c->partial, UPD_BLOCKS, nullptr, stats ? stats : c->stats_dev, c->bound,
+                             c->partial + 5 * UPD_BLOCKS);
+    ++launches;
+    LAUNCH_CHECK();
+    c->launches = launches;
+    return VOF_OK;
+}
+
+int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt, double *stats,
+                  cudaStream_t s)
+{
+    DevMesh &m = c->m;
+    int sms = num_sms(c->device);
+    int *cnt = c->counters;
+    int launches = 0;
+    cudaEvent_t *ev = nullptr;
+    if (c->prof_ev && c->prof_steps < c->prof_max) ev = c->prof_ev + (size_t)c->prof_steps++ * (VOF_PROF_GROUPS + 1);
+#define MARK(i) do { if (ev) cudaEventRecord(ev[i], s); } while (0)
+    MARK(0);
+    k_zero_int<<<1, 32, 0, s>>>(cnt, CNT_LEN);
+    k_point_state<<<cdiv(m.np, 256), 256, 0, s>>>(m, alpha, c->pstate);
+    k_classify<<<sms * 16, 256, 0, s>>>(m, alpha, F, dt, c->pstate, c->Va, c->band, cnt + CNT_BAND, c->icell,
+                                        cnt + CNT_ICELL, c->status);
+    launches += 3;
+    LAUNCH_CHECK();
+    MARK(1);
+    k_reconstruct<true><<<sms * 8, 256, 0, s>>>(m, alpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
+                                                cnt + CNT_MAXPOS, c->status);
+    MARK(2);
+    k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
+                                                  c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);
+    MARK(3);
+    PFArgs a{alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band, cnt + CNT_BAND, c->disp_b,
+             c->status, c->work};
+    k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
+    launches += 3;
+    LAUNCH_CHECK();
+    MARK(4);
+    // update + bounding + stats
+    k_zero_int<<<1, 32, 0, s>>>(cnt + CNT_VIOL0, 2);
+    k_update<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->Va, c->partial, c->bound ? c->viol[0] : nullptr,
+                                                cnt + CNT_VIOL0, c->nc, c->status);
+    launches += 2;
+    LAUNCH_CHECK();
+    if (c->bound) {
+        int r = run_bounding(c, alpha, s, &launches);
+        if (r) return r;
+        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->partial + 5 * UPD_BLOCKS);
+        ++launches;
+    }
+    k_stats<<<1, 32, 0, s>>>(c->partial, UPD_BLOCKS, cnt, stats ? stats : c->stats_dev, c->bound,
+                             c->partial + 5 * UPD_BLOCKS);
+    ++launches;
+    LAUNCH_CHECK();
+    MARK(5);
+#undef MARK
+    c->launches = launches;
+    return VOF_OK;
+}
+
+int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad)
+{
+    (void)c; (void)s; (void)bad;
+    return VOF_OK;
+}

@@ -1,0 +1,312 @@
+"""Thin ctypes binding of libvof (include/vof.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of libvof.so.  Per-step arrays are torch CUDA float64 tensors (flags uint8,
+counts int32) on the context's device; the stream defaults to torch's current
+stream.  There is no CPU fallback: if libvof.so is missing or cannot load,
+:func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvof.so")
+
+VOF_OK = 0
+FP64, MIXED = 0, 1
+INTERFACE, ORIENTED, FULL = 1, 2, 4
+STATUS_BITS = {1: "POS_NOT_CONVERGED", 2: "CORR_NOT_CONVERGED", 4: "CLIP_OVERFLOW",
+               8: "BOUND_RESIDUAL", 16: "INDEX", 32: "CAPACITY"}
+S = dict(mass_before=0, mass_after=1, min_pre=2, max_pre=3, min_post=4, max_post=5,
+         n_interface=6, n_band=7, max_pos_it=8, max_corr_it=9, boundary_out=10, n_fallback=11)
+S_LEN = 16
+
+
+class VofError(RuntimeError):
+    pass
+
+
+class _Mesh(ctypes.Structure):
+    _fields_ = [("n_points", ctypes.c_int32), ("n_faces", ctypes.c_int32),
+                ("n_internal", ctypes.c_int32), ("n_cells", ctypes.c_int32),
+                ("px", ctypes.c_void_p), ("py", ctypes.c_void_p), ("pz", ctypes.c_void_p),
+                ("face_ptr", ctypes.c_void_p), ("face_pts", ctypes.c_void_p),
+                ("owner", ctypes.c_void_p), ("neighbour", ctypes.c_void_p),
+                ("wall", ctypes.c_void_p)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("precision", ctypes.c_int),
+                ("bound", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "vof_reconstruct",
+           "vof_flux_polyhedra", "vof_correct_flux", "vof_phase_flux", "vof_update", "vof_advect",
+           "vof_advect_host", "vof_status", "vof_last_launch_count", "vof_error_string",
+           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma"]
+PROF_GROUPS = ["classify", "reconstruct", "correct", "phase_flux", "update"]
+
+_lib = None
+
+
+def lib():
+    """Loads libvof.so (built by paper_1305_3417_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise VofError(f"{LIB_PATH} is not built; run paper_1305_3417_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "vof_create": (I, [ctypes.POINTER(_Mesh), ctypes.POINTER(_Options), ctypes.POINTER(P)]),
+        "vof_destroy": (None, [P]),
+        "vof_geometry": (I, [P, P, P, P, P, P]),
+        "vof_point_velocity": (I, [P, P, P, P]),
+        "vof_reconstruct": (I, [P, P, P, P, P, P, P]),
+        "vof_flux_polyhedra": (I, [P, P, P, P, D, P, P]),
+        "vof_correct_flux": (I, [P, P, P, D, P, P, P]),
+        "vof_phase_flux": (I, [P, P, P, P, P, P, P, P, D, P, P]),
+        "vof_update": (I, [P, P, P, P, P]),
+        "vof_advect": (I, [P, P, P, P, D, P, P]),
+        "vof_advect_host": (I, [P, P, P, P, D, P, P]),
+        "vof_status": (I, [P, ctypes.POINTER(ctypes.c_uint32), P]),
+        "vof_last_launch_count": (I, [P]),
+        "vof_error_string": (ctypes.c_char_p, [I]),
+        "vof_profile_begin": (I, [P, I]),
+        "vof_profile_end": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
+        "vof_work_counts": (I, [P, P, I, P]),
+        "vof_probe_fma": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code: int, what: str):
+    if code != VOF_OK:
+        raise VofError(f"{what}: {lib().vof_error_string(code).decode()} ({code})")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, dtype, numel, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != dtype:
+        raise VofError(f"{name}: expected a CUDA {dtype} tensor")
+    if not t.is_contiguous() or t.numel() != numel:
+        raise VofError(f"{name}: expected {numel} contiguous elements, got {t.numel()}")
+    return t
+
+
+# ------------------------------------------------------------------ C names
+
+def vof_create(mesh, precision: int = FP64, eps: float = 1e-9, bound: bool = True, device: int = 0):
+    """mesh: paper_1305_3417_gb300.inputs.Mesh (host arrays).  Returns a handle."""
+    px, py, pz = (np.ascontiguousarray(v, np.float64) for v in mesh.soa_points())
+    fptr = np.ascontiguousarray(mesh.face_ptr, np.int32)
+    fpts = np.ascontiguousarray(mesh.face_pts, np.int32)
+    own = np.ascontiguousarray(mesh.owner, np.int32)
+    nei = np.ascontiguousarray(mesh.neighbour, np.int32)
+    wall = np.ascontiguousarray(mesh.wall_flags(), np.uint8)
+    m = _Mesh(mesh.n_points, mesh.n_faces, mesh.n_internal, mesh.n_cells,
+              px.ctypes.data, py.ctypes.data, pz.ctypes.data, fptr.ctypes.data, fpts.ctypes.data,
+              own.ctypes.data, nei.ctypes.data if nei.size else None, wall.ctypes.data if wall.size else None)
+    o = _Options(eps, int(precision), int(bool(bound)), int(device))
+    h = ctypes.c_void_p()
+    _check(lib().vof_create(ctypes.byref(m), ctypes.byref(o), ctypes.byref(h)), "vof_create")
+    return h
+
+
+def vof_destroy(h):
+    if h:
+        lib().vof_destroy(h)
+
+
+def vof_geometry(h, cc, vc, cf, sf, stream=None):
+    _check(lib().vof_geometry(h, _ptr(cc), _ptr(vc), _ptr(cf), _ptr(sf), _stream(stream)), "vof_geometry")
+
+
+def vof_point_velocity(h, Uc, Up, stream=None):
+    _check(lib().vof_point_velocity(h, _ptr(Uc), _ptr(Up), _stream(stream)), "vof_point_velocity")
+
+
+def vof_reconstruct(h, alpha, n, d, flags, iters=None, stream=None):
+    _check(lib().vof_reconstruct(h, _ptr(alpha), _ptr(n), _ptr(d), _ptr(flags), _ptr(iters), _stream(stream)),
+           "vof_reconstruct")
+
+
+def vof_flux_polyhedra(h, Up, F, lam, dt, V, stream=None):
+    _check(lib().vof_flux_polyhedra(h, _ptr(Up), _ptr(F), _ptr(lam), float(dt), _ptr(V), _stream(stream)),
+           "vof_flux_polyhedra")
+
+
+def vof_correct_flux(h, Up, F, dt, lam, iters=None, stream=None):
+    _check(lib().vof_correct_flux(h, _ptr(Up), _ptr(F), float(dt), _ptr(lam), _ptr(iters), _stream(stream)),
+           "vof_correct_flux")
+
+
+def vof_phase_flux(h, alpha, n, d, flags, Up, F, lam, dt, Va, stream=None):
+    _check(lib().vof_phase_flux(h, _ptr(alpha), _ptr(n), _ptr(d), _ptr(flags), _ptr(Up), _ptr(F), _ptr(lam),
+                                float(dt), _ptr(Va), _stream(stream)), "vof_phase_flux")
+
+
+def vof_update(h, alpha, Va, stats=None, stream=None):
+    _check(lib().vof_update(h, _ptr(alpha), _ptr(Va), _ptr(stats), _stream(stream)), "vof_update")
+
+
+def vof_advect(h, alpha, Uc, F, dt, stats=None, stream=None):
+    _check(lib().vof_advect(h, _ptr(alpha), _ptr(Uc), _ptr(F), float(dt), _ptr(stats), _stream(stream)),
+           "vof_advect")
+
+
+def vof_advect_host(h, alpha, Uc, F, dt, stats=None, stream=None):
+    """Host (preferably pinned) CPU tensors; copies happen inside the call."""
+    _check(lib().vof_advect_host(h, _ptr(alpha), _ptr(Uc), _ptr(F), float(dt), _ptr(stats), _stream(stream)),
+           "vof_advect_host")
+
+
+def vof_status(h, stream=None) -> int:
+    bits = ctypes.c_uint32(0)
+    _check(lib().vof_status(h, ctypes.byref(bits), _stream(stream)), "vof_status")
+    return int(bits.value)
+
+
+def vof_last_launch_count(h) -> int:
+    return int(lib().vof_last_launch_count(h))
+
+
+def vof_error_string(code: int) -> str:
+    return lib().vof_error_string(int(code)).decode()
+
+
+def vof_profile_begin(h, max_steps: int):
+    _check(lib().vof_profile_begin(h, int(max_steps)), "vof_profile_begin")
+
+
+def vof_profile_end(h):
+    """Returns ({group: summed ms}, steps)."""
+    ms = (ctypes.c_double * len(PROF_GROUPS))()
+    n = ctypes.c_int(0)
+    _check(lib().vof_profile_end(h, ms, ctypes.byref(n)), "vof_profile_end")
+    return dict(zip(PROF_GROUPS, list(ms))), int(n.value)
+
+
+def vof_work_counts(h, reset: bool = True, stream=None):
+    c = (ctypes.c_ulonglong * 3)()
+    _check(lib().vof_work_counts(h, c, int(bool(reset)), _stream(stream)), "vof_work_counts")
+    return dict(pairs=int(c[0]), cuts=int(c[1]), faces=int(c[2]))
+
+
+def vof_probe_fma(device: int = 0, precision: int = FP64, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    _check(lib().vof_probe_fma(int(device), int(precision), ctypes.byref(out), _stream(stream)),
+           "vof_probe_fma")
+    return float(out.value)
+
+
+# -------------------------------------------------------------- convenience
+
+class VofContext:
+    """Owns a libvof context and checks tensor shapes before each call."""
+
+    def __init__(self, mesh, precision: int = FP64, eps: float = 1e-9, bound: bool = True, device: int = 0):
+        import torch
+        self.nc, self.nf, self.np_, self.ni = mesh.n_cells, mesh.n_faces, mesh.n_points, mesh.n_internal
+        self.device = torch.device("cuda", device)
+        self.h = vof_create(mesh, precision, eps, bound, device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            vof_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _z(self, n, dtype=None):
+        import torch
+        return torch.zeros(n, dtype=dtype or torch.float64, device=self.device)
+
+    def geometry(self):
+        cc, vc, cf, sf = self._z(3 * self.nc), self._z(self.nc), self._z(3 * self.nf), self._z(3 * self.nf)
+        vof_geometry(self.h, cc, vc, cf, sf)
+        return cc.view(3, -1), vc, cf.view(3, -1), sf.view(3, -1)
+
+    def point_velocity(self, Uc):
+        import torch
+        _dev(Uc, torch.float64, 3 * self.nc, "Uc")
+        Up = self._z(3 * self.np_)
+        vof_point_velocity(self.h, Uc, Up)
+        return Up
+
+    def reconstruct(self, alpha):
+        import torch
+        _dev(alpha, torch.float64, self.nc, "alpha")
+        n, d = self._z(3 * self.nc), self._z(self.nc)
+        fl = self._z(self.nc, torch.uint8)
+        it = self._z(self.nc, torch.int32)
+        vof_reconstruct(self.h, alpha, n, d, fl, it)
+        return n, d, fl, it
+
+    def flux_polyhedra(self, Up, dt, lam=None, F=None):
+        import torch
+        _dev(Up, torch.float64, 3 * self.np_, "Up")
+        V = self._z(self.nf)
+        vof_flux_polyhedra(self.h, Up, F, lam, dt, V)
+        return V
+
+    def correct_flux(self, Up, F, dt):
+        import torch
+        _dev(Up, torch.float64, 3 * self.np_, "Up")
+        _dev(F, torch.float64, self.nf, "F")
+        lam = self._z(self.nf)
+        it = self._z(self.nf, torch.int32)
+        vof_correct_flux(self.h, Up, F, dt, lam, it)
+        return lam, it
+
+    def phase_flux(self, alpha, n, d, flags, Up, F, lam, dt):
+        Va = self._z(self.nf)
+        vof_phase_flux(self.h, alpha, n, d, flags, Up, F, lam, dt, Va)
+        return Va
+
+    def update(self, alpha, Va):
+        stats = self._z(S_LEN)
+        vof_update(self.h, alpha, Va, stats)
+        return stats
+
+    def advect(self, alpha, Uc, F, dt, stats=None):
+        import torch
+        _dev(alpha, torch.float64, self.nc, "alpha")
+        _dev(Uc, torch.float64, 3 * self.nc, "Uc")
+        _dev(F, torch.float64, self.nf, "F")
+        if stats is None:
+            stats = self._z(S_LEN)
+        vof_advect(self.h, alpha, Uc, F, dt, stats)
+        return stats
+
+    def status(self) -> int:
+        return vof_status(self.h)
