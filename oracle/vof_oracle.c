@@ -712,7 +712,8 @@ static double swept_abs(const vo_mesh *m, int f, const double *Up, double dt, do
 
 /* Reading R5: the swept end points move along their stream vectors by a common
  * factor lambda, and the secant method drives r(lambda) = V_f(lambda) - F_f dt
- * to zero (Eq. VF, Sec. 2.3).  The root taken is the one in the first of the
+ * to zero (Eq. VF, Sec. 2.3).  A flux below 1e-12 of |S_f| max_p |U_p| dt is
+ * rounding noise of the field (a wall face, for instance): lambda = 0, no sweep.  The root taken is the one in the first of the
  * intervals [k, k+1]*LMAX/NSAMP (k = 0..NSAMP-1) at whose ends r changes sign;
  * inside it the secant starts from the interval ends, and an iterate that
  * leaves the current bracket is replaced by bisection (the safeguard of
@@ -723,7 +724,14 @@ static int correct_face(const vo_mesh *m, int f, const double *Up, double F, dou
 {
     double tau = F * dt, lo = 0.0, hi = 0.0, rlo = -tau, rhi = 0.0, x0, r0, x1, r1, x, r, scale;
     int it = 0, k, bisect = 0, found = 0;
+    double umax = 0.0;
     if (tau == 0.0) { *lam = 0.0; return 0; }
+    for (k = m->fptr[f]; k < m->fptr[f + 1]; k++) {
+        int p = m->fpts[k];
+        double u = norm(mk(Up[p], Up[m->np + p], Up[2 * m->np + p]));
+        if (u > umax) umax = u;
+    }
+    if (fabs(tau) <= 1e-12 * norm(m->sf[f]) * umax * dt) { *lam = 0.0; return 0; }
     for (k = 1; k <= CORR_NSAMP; k++) {
         double lk = k * (CORR_LMAX / CORR_NSAMP);
         double rk = vo_swept_volume(m, f, Up, F, dt, lk) - tau;
@@ -896,7 +904,8 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 
 /* ---------------------------------------------------------- A7: update */
 #define BOUND_PASSES 8
-#define BOUND_TOL 1e-15   /* violations at round-off scale are left alone */
+#define BOUND_TOL 1e-13   /* excursions this small (round-off) are left alone and never
+                           * decide a redistribution; the target is 1e-12 */
 #define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
 
 /* Reading R10: a conservative bounding pass.  Excess above 1 (deficit below 0)
@@ -907,10 +916,11 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 static int bound_pass(const vo_mesh *m, double *alpha)
 {
     int nc = m->nc, c, any = 0;
-    double *e = (double *)calloc((size_t)nc, sizeof(double)), *u = (double *)calloc((size_t)nc, sizeof(double));
-    double *op = (double *)calloc((size_t)nc, sizeof(double)), *om = (double *)calloc((size_t)nc, sizeof(double));
-    double *Cp = (double *)calloc((size_t)nc, sizeof(double)), *Cm = (double *)calloc((size_t)nc, sizeof(double));
-    double *give = (double *)calloc((size_t)nc, sizeof(double)), *take = (double *)calloc((size_t)nc, sizeof(double));
+    size_t n1 = (size_t)(nc > 0 ? nc : 1);
+    double *e = (double *)calloc(n1, sizeof(double)), *u = (double *)calloc(n1, sizeof(double));
+    double *op = (double *)calloc(n1, sizeof(double)), *om = (double *)calloc(n1, sizeof(double));
+    double *Cp = (double *)calloc(n1, sizeof(double)), *Cm = (double *)calloc(n1, sizeof(double));
+    double *give = (double *)calloc(n1, sizeof(double)), *take = (double *)calloc(n1, sizeof(double));
     for (c = 0; c < nc; c++) {
         double a = alpha[c];
         if (a > 1.0 + BOUND_TOL) { e[c] = (a - 1.0) * m->vc[c]; any = 1; }

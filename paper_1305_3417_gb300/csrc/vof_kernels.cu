@@ -20,7 +20,7 @@ constexpr int CORR_MAXIT = 100;
 constexpr double CORR_TOL = 1e-14;
 constexpr double CORR_LMAX = 2.0;
 constexpr int CORR_NSAMP = 16;
-constexpr double BOUND_TOL = 1e-15;
+constexpr double BOUND_TOL = 1e-13;
 constexpr double BOUND_FLAG = 1e-12;
 constexpr int BOUND_PASSES = 8;
 constexpr int CLIP_STACK = 12;
@@ -452,10 +452,13 @@ __device__ __forceinline__ double cubic_at(const Cubic &q, double x) { return ((
 // k*LMAX/NSAMP (the bracket is the same one the secant oracle uses), refined by
 // Newton steps that fall back to bisection when they leave the bracket.
 // Returns lambda, or -1 (normal-sweep fallback) when no interval brackets a root.
-__device__ double solve_lambda(const Cubic &q, double tau, int &its)
+// A flux below 1e-12 of |S_f| max|w| (noise = the rounding of a zero flux, e.g.
+// on a wall) gives lambda = 0: no sweep.
+__device__ double solve_lambda(const Cubic &q, double tau, double noise, int &its)
 {
     its = 0;
     if (tau == 0.0) return 0.0;
+    if (fabs(tau) <= 1e-12 * noise) return 0.0;
     double lo = 0.0, rlo = -tau, hi = 0.0, rhi = 0.0;
     bool found = false;
     for (int k = 1; k <= CORR_NSAMP; ++k) {
@@ -516,8 +519,10 @@ __global__ void k_correct(DevMesh m, const double *__restrict__ U, const double 
         int n = face_points<IDW>(m, f, U, dt, A, W, id);
         double tau = F[f] * dt;
         Cubic q = face_cubic(m, f, n, A, W, id);
+        double wmax = 0.0;
+        for (int i = 0; i < n; ++i) wmax = fmax(wmax, norm3(W[i]));
         int its = 0;
-        double lam = solve_lambda(q, tau, its);
+        double lam = solve_lambda(q, tau, norm3(ld3(m.sf, m.nf, f)) * wmax, its);
         lam_out[item] = lam;
         if (it_out) it_out[item] = its;
         if (maxit && its > 0) atomicMax(maxit, its);
