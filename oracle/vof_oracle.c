@@ -903,16 +903,28 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 }
 
 /* ---------------------------------------------------------- A7: update */
-#define BOUND_PASSES 8
+#define BOUND_PASSES 16
 #define BOUND_TOL 1e-13   /* excursions this small (round-off) are left alone and never
                            * decide a redistribution; the target is 1e-12 */
 #define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
 
-/* Reading R10: a conservative bounding pass.  Excess above 1 (deficit below 0)
- * is handed to face neighbours in proportion to their free (filled) volume;
- * each receiver offers its capacity divided by its number of sources, so no
- * receiver can be pushed out of [0,1].  Written as gathers, repeated a fixed
- * number of passes at most. */
+/* Reading R10: a conservative bounding pass, repeated until no cell is out of
+ * [0,1] by more than BOUND_TOL (at most BOUND_PASSES times).  A source cell
+ * with excess e above 1 hands its face neighbours what they can take, in
+ * proportion to their free volume -- each receiver offers its free volume
+ * divided by the number of excess sources next to it -- and pushes the rest
+ * of e in equal parts to its face neighbours that are not excess sources, so
+ * that excess travels on until it meets free volume.  A deficit below 0 is
+ * treated the same way with the phase volume of the neighbours.  Every cell's
+ * new value is a gather over its face neighbours, so the result does not
+ * depend on the order in which cells are visited. */
+static int face_nbr(const vo_mesh *m, int c, int i)
+{
+    int f = m->cface[i];
+    if (f >= m->ni) return -1;
+    return m->own[f] == c ? m->nei[f] : m->own[f];
+}
+
 static int bound_pass(const vo_mesh *m, double *alpha)
 {
     int nc = m->nc, c, any = 0;
@@ -921,59 +933,109 @@ static int bound_pass(const vo_mesh *m, double *alpha)
     double *op = (double *)calloc(n1, sizeof(double)), *om = (double *)calloc(n1, sizeof(double));
     double *Cp = (double *)calloc(n1, sizeof(double)), *Cm = (double *)calloc(n1, sizeof(double));
     double *give = (double *)calloc(n1, sizeof(double)), *take = (double *)calloc(n1, sizeof(double));
+    double *rp = (double *)calloc(n1, sizeof(double)), *rm = (double *)calloc(n1, sizeof(double));
+    int *dp = (int *)calloc(n1, sizeof(int)), *dm = (int *)calloc(n1, sizeof(int));
+    double *na = (double *)malloc(n1 * sizeof(double));
     for (c = 0; c < nc; c++) {
         double a = alpha[c];
         if (a > 1.0 + BOUND_TOL) { e[c] = (a - 1.0) * m->vc[c]; any = 1; }
         if (a < -BOUND_TOL) { u[c] = -a * m->vc[c]; any = 1; }
     }
     if (any) {
+        /* offers of every cell */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i, sp = 0, sm = 0;
             double a = alpha[c];
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
-                int f = m->cface[i], nb;
-                if (f >= m->ni) continue;
-                nb = m->own[f] == c ? m->nei[f] : m->own[f];
+                int nb = face_nbr(m, c, i);
+                if (nb < 0) continue;
                 if (e[nb] > 0) sp++;
                 if (u[nb] > 0) sm++;
             }
             op[c] = (a >= 0.0 && a < 1.0) ? (1.0 - a) * m->vc[c] / (sp > 0 ? sp : 1) : 0.0;
             om[c] = (a > 0.0 && a <= 1.0) ? a * m->vc[c] / (sm > 0 ? sm : 1) : 0.0;
         }
+        /* what each source hands out by offer, and the rest it pushes on */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i;
             double sp = 0.0, sm = 0.0;
             if (e[c] == 0.0 && u[c] == 0.0) continue;
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
-                int f = m->cface[i], nb;
-                if (f >= m->ni) continue;
-                nb = m->own[f] == c ? m->nei[f] : m->own[f];
+                int nb = face_nbr(m, c, i);
+                if (nb < 0) continue;
                 sp += op[nb];
                 sm += om[nb];
+                if (e[nb] == 0.0) dp[c]++;
+                if (u[nb] == 0.0) dm[c]++;
             }
-            Cp[c] = sp; Cm[c] = sm;
-            give[c] = e[c] < sp ? e[c] : sp;
-            take[c] = u[c] < sm ? u[c] : sm;
+            if (e[c] > 0.0) {
+                Cp[c] = sp;
+                give[c] = e[c] < sp ? e[c] : sp;
+                rp[c] = dp[c] > 0 ? e[c] - give[c] : 0.0;
+            }
+            if (u[c] > 0.0) {
+                Cm[c] = sm;
+                take[c] = u[c] < sm ? u[c] : sm;
+                rm[c] = dm[c] > 0 ? u[c] - take[c] : 0.0;
+            }
         }
+        /* new value of every cell: its own hand-out, then its neighbours' */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i;
-            double rec = 0.0, out = 0.0;
+            double dV = 0.0;
+            if (e[c] > 0.0) dV -= give[c] + rp[c];
+            if (u[c] > 0.0) dV += take[c] + rm[c];
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
-                int f = m->cface[i], nb;
-                if (f >= m->ni) continue;
-                nb = m->own[f] == c ? m->nei[f] : m->own[f];
-                if (give[nb] > 0.0) rec += give[nb] * (op[c] / Cp[nb]);
-                if (take[nb] > 0.0) out += take[nb] * (om[c] / Cm[nb]);
+                int nb = face_nbr(m, c, i);
+                if (nb < 0) continue;
+                if (e[nb] > 0.0 && e[c] == 0.0) {
+                    if (Cp[nb] > 0.0) dV += give[nb] * (op[c] / Cp[nb]);
+                    if (dp[nb] > 0) dV += rp[nb] / dp[nb];
+                }
+                if (u[nb] > 0.0 && u[c] == 0.0) {
+                    if (Cm[nb] > 0.0) dV -= take[nb] * (om[c] / Cm[nb]);
+                    if (dm[nb] > 0) dV -= rm[nb] / dm[nb];
+                }
             }
-            if (give[c] != 0.0 || take[c] != 0.0 || rec != 0.0 || out != 0.0)
-                alpha[c] = (alpha[c] * m->vc[c] - give[c] + take[c] + rec - out) / m->vc[c];
+            na[c] = dV != 0.0 ? (alpha[c] * m->vc[c] + dV) / m->vc[c] : alpha[c];
         }
+        memcpy(alpha, na, sizeof(double) * (size_t)nc);
     }
     free(e); free(u); free(op); free(om); free(Cp); free(Cm); free(give); free(take);
+    free(rp); free(rm); free(dp); free(dm); free(na);
     return any;
+}
+
+/* What the local passes leave is moved in one global step: the total excess
+ * (deficit) goes to every cell strictly inside (BOUND_TOL, 1-BOUND_TOL) in
+ * proportion to its free (phase) volume, and the sources are set to 1 (0).
+ * Skipped when the receivers cannot hold it.  Returns 1 if applied. */
+static int bound_global(const vo_mesh *m, double *alpha)
+{
+    double Ep = 0.0, Em = 0.0, Sp = 0.0, Sm = 0.0;
+    int c;
+    for (c = 0; c < m->nc; c++) {
+        double a = alpha[c], V = m->vc[c];
+        if (a > 1.0 + BOUND_TOL) Ep += (a - 1.0) * V;
+        else if (a < -BOUND_TOL) Em += -a * V;
+        else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) { Sp += (1.0 - a) * V; Sm += a * V; }
+    }
+    if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return 0;
+    for (c = 0; c < m->nc; c++) {
+        double a = alpha[c], V = m->vc[c];
+        if (a > 1.0 + BOUND_TOL) alpha[c] = 1.0;
+        else if (a < -BOUND_TOL) alpha[c] = 0.0;
+        else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) {
+            double dV = 0.0;
+            if (Ep > 0.0) dV += Ep * ((1.0 - a) * V / Sp);
+            if (Em > 0.0) dV -= Em * (a * V / Sm);
+            alpha[c] = (a * V + dV) / V;
+        }
+    }
+    return 1;
 }
 
 int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, double *stats)
@@ -1000,6 +1062,7 @@ int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, doub
         int p;
         for (p = 0; p < BOUND_PASSES; p++)
             if (!bound_pass(m, alpha)) break;
+        if (p == BOUND_PASSES) bound_global(m, alpha);
         for (c = 0; c < m->nc; c++)
             if (alpha[c] < -BOUND_FLAG || alpha[c] > 1.0 + BOUND_FLAG) { st |= VO_ST_BOUND_RESIDUAL; break; }
     }

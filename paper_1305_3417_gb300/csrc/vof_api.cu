@@ -40,7 +40,7 @@ template <class T>
 T *dev_alloc(vof_ctx *c, size_t n, int *err)
 {
     if (*err) return nullptr;
-    if (c->nbufs >= 64) { *err = VOF_ERR_CUDA; return nullptr; }
+    if (c->nbufs >= (int)(sizeof(c->bufs) / sizeof(c->bufs[0]))) { *err = VOF_ERR_CUDA; return nullptr; }
     void *p = nullptr;
     if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) { *err = VOF_ERR_CUDA; return nullptr; }
     c->bufs[c->nbufs++] = p;
@@ -304,6 +304,9 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->Va = dev_alloc<double>(c, nf, &err);
     c->gv = dev_alloc<double>(c, nc, &err);
     c->Cc = dev_alloc<double>(c, nc, &err);
+    c->rmd = dev_alloc<double>(c, nc, &err);
+    c->dgi = dev_alloc<int>(c, nc, &err);
+    c->gpartial = dev_alloc<double>(c, 4 * 512, &err);
     c->partial = dev_alloc<double>(c, 10 * 1024, &err);
     c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
     c->status = dev_alloc<unsigned>(c, 1, &err);
@@ -315,6 +318,8 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
     cudaMemset(c->gv, 0, sizeof(double) * nc);
     cudaMemset(c->Cc, 0, sizeof(double) * nc);
+    cudaMemset(c->rmd, 0, sizeof(double) * nc);
+    cudaMemset(c->dgi, 0, sizeof(int) * nc);
     cudaMemset(c->counters, 0, sizeof(int) * 16);
     cudaMemset(c->status, 0, sizeof(unsigned));
     cudaMemset(c->n, 0, sizeof(double) * 3 * nc);

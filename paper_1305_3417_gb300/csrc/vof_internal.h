@@ -37,7 +37,7 @@ struct vof_ctx {
     int precision, bound;
     DevMesh m;
     // owned device buffers (freed in vof_destroy)
-    void *bufs[64];
+    void *bufs[128];
     int nbufs;
     // per-step scratch
     uint8_t *pstate;
@@ -50,7 +50,9 @@ struct vof_ctx {
     uint8_t *flags;
     int *pit;
     double *Va;
-    double *gv, *Cc;             // bounding scratch per cell
+    double *gv, *Cc, *rmd;       // bounding scratch per cell
+    int *dgi;
+    double *gpartial;            // global bounding partial sums
     double *partial;             // reduction partials
     double *stats_dev;           // internal stats buffer
     unsigned *status;

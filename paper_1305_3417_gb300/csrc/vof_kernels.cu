@@ -22,7 +22,7 @@ constexpr double CORR_LMAX = 2.0;
 constexpr int CORR_NSAMP = 16;
 constexpr double BOUND_TOL = 1e-13;
 constexpr double BOUND_FLAG = 1e-12;
-constexpr int BOUND_PASSES = 8;
+constexpr int BOUND_PASSES = 16;
 constexpr int CLIP_STACK = 12;
 constexpr int DISP_STRIDE = (VOF_MAXFP + 1) * 3;
 
@@ -917,25 +917,31 @@ __global__ void k_stats(const double *partial, int nblk, const int *counters, do
 }
 
 // post-bounding mass / extrema
-__global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *alpha, double *partial)
+__global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *alpha, double *partial,
+                                                      unsigned *status)
 {
     double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    bool bad = false;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
         double a = alpha[c];
         v[1] += m.vc[c] * a;
         v[2] = fmin(v[2], a);
         v[3] = fmax(v[3], a);
+        bad |= a > 1.0 + BOUND_FLAG || a < -BOUND_FLAG;
     }
+    if (bad) atomicOr(status, VOF_ST_BOUND_RESIDUAL);
     block_reduce5(v, partial + 5 * blockIdx.x);
 }
 
 // ------------------------------------------------- bounding pass (reading R10)
-// Excess above 1 (deficit below 0) of a source cell is handed to its face
-// neighbours in proportion to their free (filled) volume; a receiver offers its
-// capacity divided by its number of sources.  Three kernels per pass over the
-// list of violating cells: (1) per source the sum of its neighbours' offers and
-// the amount it gives or takes, (2) per receiver -- visited once, by its
-// lowest-index source -- the new value from all its sources, (3) apply.
+// Local passes: a source with excess above 1 hands its face neighbours what
+// they can take, in proportion to their free volume (each receiver offers its
+// free volume divided by its number of excess sources), and pushes the rest in
+// equal parts to its face neighbours that are not excess sources; deficits
+// below 0 mirror this with phase volume.  Every touched cell's new value is a
+// gather over its face neighbours in face order.  The sources are few, so one
+// block runs all passes with block barriers between the phases and stops as
+// soon as no cell is out of bounds.
 __device__ __forceinline__ int nbr_of(const DevMesh &m, int c, int k)
 {
     int code = m.cface[k], f = code >> 1;
@@ -945,7 +951,7 @@ __device__ __forceinline__ int nbr_of(const DevMesh &m, int c, int k)
 __device__ __forceinline__ bool is_exc(double a) { return a > 1.0 + BOUND_TOL; }
 __device__ __forceinline__ bool is_def(double a) { return a < -BOUND_TOL; }
 
-// offers of cell c: excess offer (free volume) and deficit offer (phase volume)
+// offers of cell c: free volume and phase volume, each split over its sources
 __device__ __forceinline__ void offers(const DevMesh &m, const double *alpha, int c, double &op, double &om)
 {
     int sp = 0, sm = 0;
@@ -961,103 +967,176 @@ __device__ __forceinline__ void offers(const DevMesh &m, const double *alpha, in
     om = (a > 0.0 && a <= 1.0) ? a * V / (sm > 0 ? sm : 1) : 0.0;
 }
 
-__global__ void k_bound_sources(DevMesh m, const double *alpha, const int *src, const int *nsrc,
-                                double *gv, double *Cc)
-{
-    int n = *nsrc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int c = src[i];
-        double a = alpha[c], V = m.vc[c], sp = 0.0, sm = 0.0;
-        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-            int nb = nbr_of(m, c, k);
-            if (nb < 0) continue;
-            double op, om;
-            offers(m, alpha, nb, op, om);
-            sp += op;
-            sm += om;
-        }
-        if (a > 1.0) { double e = (a - 1.0) * V; gv[c] = fmin(e, sp); Cc[c] = sp; }
-        else { double u = -a * V; gv[c] = -fmin(u, sm); Cc[c] = sm; }
-    }
-}
+struct BoundBufs {
+    int *la, *lb;        // source lists (ping-pong), capacity nc
+    const int *n0;       // initial count (from the update kernel)
+    int *pc;             // pending cells, capacity cap_pend
+    double *pa;          // pending values
+    double *gv, *rm, *Cc;  // per source: handed out by offer, pushed on, sum of offers
+    int *dg;             // per source: number of push receivers
+    int *left;           // out: sources left after the local passes
+    int cap, cap_pend;
+};
 
-__global__ void k_bound_receivers(DevMesh m, const double *alpha, const int *src, const int *nsrc,
-                                  const double *gv, const double *Cc, int *pc, double *pa, int *npend,
-                                  int cap, unsigned *status)
+constexpr int BOUND_THREADS = 1024;
+
+__global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double *alpha, BoundBufs b,
+                                                               unsigned *status)
 {
-    int n = *nsrc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int c = src[i];
-        double V = m.vc[c];
-        double g = gv[c];
-        // the source itself: gives its excess away or takes its deficit back
-        if (g != 0.0) {
-            double na = (alpha[c] * V - (g > 0.0 ? g : 0.0) + (g < 0.0 ? -g : 0.0)) / V;
-            int pos = atomicAdd(npend, 1);
-            if (pos < cap) { pc[pos] = c; pa[pos] = na; } else atomicOr(status, VOF_ST_CAPACITY);
-        }
-        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-            int nb = nbr_of(m, c, k);
-            if (nb < 0) continue;
-            double anb = alpha[nb];
-            if (is_exc(anb) || is_def(anb)) continue;  // sources never receive
-            // visited once: by its lowest-index violating neighbour
-            int first = 0x7fffffff;
-            for (int q = m.cptr[nb]; q < m.cptr[nb + 1]; ++q) {
-                int s = nbr_of(m, nb, q);
-                if (s < 0) continue;
-                double as = alpha[s];
-                if ((is_exc(as) || is_def(as)) && s < first) first = s;
+    __shared__ int s_n, s_next, s_pend;
+    if (threadIdx.x == 0) { s_n = min(*b.n0, b.cap); s_next = 0; s_pend = 0; }
+    __syncthreads();
+    int *src = b.la, *nxt = b.lb;
+    for (int pass = 0; pass < BOUND_PASSES; ++pass) {
+        const int n = s_n;
+        if (n == 0) break;
+        // (1) per source: sum of neighbour offers, hand-out and push-on amounts
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int c = src[i];
+            double a = alpha[c], V = m.vc[c], sp = 0.0, sm = 0.0;
+            int dp = 0, dm = 0;
+            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+                int nb = nbr_of(m, c, k);
+                if (nb < 0) continue;
+                double op, om;
+                offers(m, alpha, nb, op, om);
+                sp += op;
+                sm += om;
+                double an = alpha[nb];
+                dp += !is_exc(an);
+                dm += !is_def(an);
             }
-            if (first != c) continue;
-            double op, om;
-            offers(m, alpha, nb, op, om);
-            double rec = 0.0, out = 0.0;
-            for (int q = m.cptr[nb]; q < m.cptr[nb + 1]; ++q) {
-                int s = nbr_of(m, nb, q);
-                if (s < 0) continue;
-                double as = alpha[s];
-                if (is_exc(as) && gv[s] > 0.0) rec += gv[s] * (op / Cc[s]);
-                if (is_def(as) && gv[s] < 0.0) out += -gv[s] * (om / Cc[s]);
-            }
-            if (rec != 0.0 || out != 0.0) {
-                double Vn = m.vc[nb];
-                double na = (anb * Vn + rec - out) / Vn;
-                int pos = atomicAdd(npend, 1);
-                if (pos < cap) { pc[pos] = nb; pa[pos] = na; } else atomicOr(status, VOF_ST_CAPACITY);
+            if (is_exc(a)) {
+                double e = (a - 1.0) * V, g = fmin(e, sp);
+                b.gv[c] = g; b.Cc[c] = sp; b.dg[c] = dp; b.rm[c] = dp > 0 ? e - g : 0.0;
+            } else {
+                double u = -a * V, t = fmin(u, sm);
+                b.gv[c] = t; b.Cc[c] = sm; b.dg[c] = dm; b.rm[c] = dm > 0 ? u - t : 0.0;
             }
         }
-    }
-}
-
-__global__ void k_bound_apply(double *alpha, const int *src, const int *nsrc, double *gv, double *Cc,
-                              const int *pc, const double *pa, const int *npend)
-{
-    int n = *npend, ns = *nsrc;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        alpha[pc[i]] = pa[i];
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < ns; i += gridDim.x * blockDim.x) {
-        int c = src[i];
-        gv[c] = 0.0;
-        Cc[c] = 0.0;
-    }
-}
-
-__global__ void k_bound_collect(const double *alpha, const int *src, const int *nsrc, int *next,
-                                int *nnext, int cap, unsigned *status, int last)
-{
-    int n = *nsrc;
-    int lim = (n + 31) & ~31;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < lim; i += gridDim.x * blockDim.x) {
-        bool keep = false;
-        int c = 0;
-        if (i < n) {
-            c = src[i];
-            double a = alpha[c];
-            keep = a > 1.0 + BOUND_TOL || a < -BOUND_TOL;
-            if (last && (a > 1.0 + BOUND_FLAG || a < -BOUND_FLAG)) atomicOr(status, VOF_ST_BOUND_RESIDUAL);
+        __syncthreads();
+        // (2) new values of the sources and their neighbours, each cell once:
+        //     by the lowest-index source in its closed face neighbourhood
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int c = src[i];
+            for (int k = m.cptr[c] - 1; k < m.cptr[c + 1]; ++k) {
+                int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
+                if (x < 0) continue;
+                double ax = alpha[x];
+                bool xe = is_exc(ax), xd = is_def(ax);
+                int first = (xe || xd) ? x : 0x7fffffff;
+                for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
+                    int s = nbr_of(m, x, q);
+                    if (s < 0) continue;
+                    double as = alpha[s];
+                    if ((is_exc(as) || is_def(as)) && s < first) first = s;
+                }
+                if (first != c) continue;
+                double op, om;
+                offers(m, alpha, x, op, om);
+                double dV = 0.0;
+                if (xe) dV -= b.gv[x] + b.rm[x];
+                if (xd) dV += b.gv[x] + b.rm[x];
+                for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
+                    int s = nbr_of(m, x, q);
+                    if (s < 0) continue;
+                    double as = alpha[s];
+                    if (is_exc(as) && !xe) {
+                        if (b.Cc[s] > 0.0) dV += b.gv[s] * (op / b.Cc[s]);
+                        if (b.dg[s] > 0) dV += b.rm[s] / b.dg[s];
+                    }
+                    if (is_def(as) && !xd) {
+                        if (b.Cc[s] > 0.0) dV -= b.gv[s] * (om / b.Cc[s]);
+                        if (b.dg[s] > 0) dV -= b.rm[s] / b.dg[s];
+                    }
+                }
+                // sources always go to the pending list (a source that could not
+                // move keeps its value and stays a source next pass)
+                if (dV != 0.0 || xe || xd) {
+                    double V = m.vc[x];
+                    int pos = atomicAdd(&s_pend, 1);
+                    if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = dV != 0.0 ? (ax * V + dV) / V : ax; }
+                    else atomicOr(status, VOF_ST_CAPACITY);
+                }
+            }
         }
-        if (!last) warp_append(keep, c, next, nnext, cap, status);
+        __syncthreads();
+        // (3) apply, clear the per-source scratch
+        const int np = min(s_pend, b.cap_pend);
+        for (int i = threadIdx.x; i < np; i += blockDim.x) alpha[b.pc[i]] = b.pa[i];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int c = src[i];
+            b.gv[c] = 0.0; b.rm[c] = 0.0; b.Cc[c] = 0.0; b.dg[c] = 0;
+        }
+        __syncthreads();
+        // (4) the touched cells still out of bounds are the next sources
+        for (int i = threadIdx.x; i < np; i += blockDim.x) {
+            double a = alpha[b.pc[i]];
+            if (is_exc(a) || is_def(a)) {
+                int pos = atomicAdd(&s_next, 1);
+                if (pos < b.cap) nxt[pos] = b.pc[i];
+                else atomicOr(status, VOF_ST_CAPACITY);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) { s_n = min(s_next, b.cap); s_next = 0; s_pend = 0; }
+        int *t = src; src = nxt; nxt = t;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *b.left = s_n;
+}
+
+// Global step for what the local passes leave: the total excess (deficit) goes
+// to every cell strictly inside (tol, 1-tol) in proportion to its free (phase)
+// volume; sources are set to 1 (0).  Both kernels return at once when nothing
+// is left.  Partial sums per block, reduced in a fixed order.
+constexpr int GB_BLOCKS = 512, GB_THREADS = 256;
+
+__global__ void __launch_bounds__(GB_THREADS) k_bound_global_reduce(DevMesh m, const double *alpha,
+                                                                    const int *left, double *partial)
+{
+    if (*left == 0) return;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};  // Ep, Em, Sp, Sm
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
+        double a = alpha[c], V = m.vc[c];
+        if (a > 1.0 + BOUND_TOL) v[0] += (a - 1.0) * V;
+        else if (a < -BOUND_TOL) v[1] += -a * V;
+        else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) { v[2] += (1.0 - a) * V; v[3] += a * V; }
+    }
+    __shared__ double sh[4][GB_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int i = 0; i < 4; ++i) {
+        double x = warp_sum(v[i]);
+        if (lane == 0) sh[i][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) {
+            double r = 0.0;
+            for (int k = 0; k < GB_THREADS / 32; ++k) r += sh[i][k];
+            partial[4 * blockIdx.x + i] = r;
+        }
+}
+
+__global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, double *alpha, const int *left,
+                                                                   const double *partial, unsigned *status)
+{
+    if (*left == 0) return;
+    double Ep = 0.0, Em = 0.0, Sp = 0.0, Sm = 0.0;
+    for (int k = 0; k < GB_BLOCKS; ++k) {
+        Ep += partial[4 * k]; Em += partial[4 * k + 1]; Sp += partial[4 * k + 2]; Sm += partial[4 * k + 3];
+    }
+    if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
+        double a = alpha[c], V = m.vc[c];
+        if (a > 1.0 + BOUND_TOL) alpha[c] = 1.0;
+        else if (a < -BOUND_TOL) alpha[c] = 0.0;
+        else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) {
+            double dV = 0.0;
+            if (Ep > 0.0) dV += Ep * ((1.0 - a) * V / Sp);
+            if (Em > 0.0) dV -= Em * (a * V / Sm);
+            alpha[c] = (a * V + dV) / V;
+        }
     }
 }
 
@@ -1204,24 +1283,14 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
 
 static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches)
 {
-    int sms = num_sms(c->device);
-    int *cnt = c->counters;
-    for (int p = 0; p < BOUND_PASSES; ++p) {
-        int cur = p & 1;
-        int *src = c->viol[cur], *nsrc = cnt + CNT_VIOL0 + cur;
-        int *nxt = c->viol[cur ^ 1], *nnxt = cnt + CNT_VIOL0 + (cur ^ 1);
-        k_zero_int<<<1, 32, 0, s>>>(cnt + CNT_PEND, 1);
-        k_zero_int<<<1, 32, 0, s>>>(nnxt, 1);
-        k_bound_sources<<<sms * 2, 128, 0, s>>>(c->m, alpha, src, nsrc, c->gv, c->Cc);
-        k_bound_receivers<<<sms * 2, 128, 0, s>>>(c->m, alpha, src, nsrc, c->gv, c->Cc, c->pend_c, c->pend_a,
-                                                  cnt + CNT_PEND, 8 * c->nc, c->status);
-        k_bound_apply<<<sms * 2, 128, 0, s>>>(alpha, src, nsrc, c->gv, c->Cc, c->pend_c, c->pend_a,
-                                              cnt + CNT_PEND);
-        k_bound_collect<<<sms * 2, 128, 0, s>>>(alpha, src, nsrc, nxt, nnxt, c->nc, c->status,
-                                                p + 1 == BOUND_PASSES);
-        *launches += 6;
-        LAUNCH_CHECK();
-    }
+    BoundBufs b{c->viol[0], c->viol[1], c->counters + CNT_VIOL0, c->pend_c, c->pend_a, c->gv, c->rmd, c->Cc, c->dgi,
+                c->counters + CNT_VIOL1, c->nc, 8 * c->nc};
+    k_bound_local<<<1, BOUND_THREADS, 0, s>>>(c->m, alpha, b, c->status);
+    k_bound_global_reduce<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial);
+    k_bound_global_apply<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial,
+                                                          c->status);
+    *launches += 3;
+    LAUNCH_CHECK();
     return VOF_OK;
 }
 
@@ -1237,7 +1306,7 @@ int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cu
     if (c->bound) {
         int r = run_bounding(c, alpha, s, &launches);
         if (r) return r;
-        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, c->partial + 5 * UPD_BLOCKS);
+        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, c->partial + 5 * UPD_BLOCKS, c->status);
         ++launches;
     }
     k_stats<<<1, 32, 0, s>>>(c->partial, UPD_BLOCKS, nullptr, stats ? stats : c->stats_dev, c->bound,
@@ -1287,7 +1356,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     if (c->bound) {
         int r = run_bounding(c, alpha, s, &launches);
         if (r) return r;
-        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->partial + 5 * UPD_BLOCKS);
+        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->partial + 5 * UPD_BLOCKS, c->status);
         ++launches;
     }
     k_stats<<<1, 32, 0, s>>>(c->partial, UPD_BLOCKS, cnt, stats ? stats : c->stats_dev, c->bound,

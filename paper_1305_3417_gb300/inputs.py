@@ -540,7 +540,10 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
         raise ValueError(name)
     Us = cell_velocity(mesh, fld.u)
     umax = float(np.sqrt((Us ** 2).sum(0)).max())
-    dt = co * mesh.h / umax
+    # Courant number on the cell size h_c = V_c^(1/3) of the nominal lattice cell
+    # (2D: the in-plane spacing); a Kuhn tetrahedron has a sixth of the hexahedron
+    hc = mesh.h if (mesh.kind == "hex") else mesh.h / 6.0 ** (1.0 / 3.0)
+    dt = co * hc / umax
     Fs = face_flux_stokes(mesh, fld.A)
     t_end = {"disc2d": steps * dt if steps else None, "deform3d": 3.0, "vortex_tet": 8.0}[name]
     if steps is None:
