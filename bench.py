@@ -178,7 +178,8 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the plain FP64 form (comparison)")
     ap.add_argument("--workload", default="deform3d")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--skip", type=int, default=0, help="untimed steps advanced before warm-up")
@@ -243,6 +244,29 @@ def main():
     S = step_stats.cpu().numpy()
     drift = np.abs((S[:, 1] + S[:, 10] - S[:, 0]) / S[:, 0]).max()
 
+    # ---- the other form on the same steps, for comparison (plain FP64 vs mixed)
+    other = None
+    if args.fp64_steps > 0 and world == 1:
+        oprec = vof.FP64 if prec == vof.MIXED else vof.MIXED
+        octx = vof.VofContext(m, precision=oprec, device=local)
+        oa = torch.from_numpy(w.alpha0.copy()).to(dev)
+        ost = torch.zeros(vof.S_LEN, dtype=torch.float64, device=dev)
+        for k in range(args.skip + args.warmup):
+            octx.advect(oa, Uk[k], Fk[k], w.dt, ost)
+        torch.cuda.synchronize()
+        ns = min(args.fp64_steps, args.steps)
+        o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        o0.record(stream)
+        for j in range(ns):
+            octx.advect(oa, Uk[args.skip + args.warmup + j], Fk[args.skip + args.warmup + j], w.dt, ost)
+        o1.record(stream)
+        torch.cuda.synchronize()
+        oms = o0.elapsed_time(o1) / ns
+        other = {"precision": "fp64" if oprec == vof.FP64 else "mixed", "value": m.n_internal / (oms * 1e-3) / 1e6,
+                 "unit": UNIT, "ms_per_step": oms, "steps": ns}
+        octx.close()
+        del oa, ost
+
     # ---- end to end through the C ABI with host buffers (copies in the timed region)
     ha = torch.from_numpy(w.alpha0.copy()).pin_memory()
     hstat = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
@@ -294,7 +318,7 @@ def main():
                 "dtype": "f64" if prec == vof.FP64 else "f32+f64",
                 "data": "synthetic", "config": config(args, w),
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": base,
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "other_form": other,
                 "clocks": clk.summary(),
                 "quality": {"max_rel_volume_drift": float(drift), "alpha_min": float(S[:, 4].min()),
                             "alpha_max": float(S[:, 5].max()), "alpha_min_pre_bound": float(S[:, 2].min()),

@@ -244,6 +244,17 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         }
     }
     const int nwrows = (int)wptr.size() - 1;
+    // per cell: offset of its (face, point) entries in face order
+    std::vector<int> cfpptr(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) {
+        long v = cfpptr[c];
+        for (int i = cptr[c]; i < cptr[c + 1]; ++i) {
+            int f = cface[i] >> 1;
+            v += fptr[f + 1] - fptr[f];
+        }
+        if (v > 0x7fffffffL) return VOF_ERR_BAD_MESH;
+        cfpptr[c + 1] = (int)v;
+    }
 
     // ------------------------------------------------------------- device
     vof_ctx *c = new vof_ctx();
@@ -314,6 +325,11 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->h_Uc = dev_alloc<double>(c, 3 * (size_t)nc, &err);
     c->h_F = dev_alloc<double>(c, nf, &err);
     c->work = dev_alloc<unsigned long long>(c, 4, &err);
+    c->cfpptr = dev_copy(c, cfpptr.data(), cfpptr.size(), &err);
+    c->cfl = dev_alloc<float4>(c, cface.size(), &err);
+    c->cfpl = dev_alloc<float4>(c, cfpptr[nc], &err);
+    c->fpl = dev_alloc<float4>(c, nfp, &err);
+    c->cbl = dev_alloc<float4>(c, 2 * (size_t)nc, &err);
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
     cudaMemset(c->gv, 0, sizeof(double) * nc);
@@ -327,6 +343,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     cudaMemset(c->flags, 0, nc);
     int r = launch_setup_geometry(c, 0);
     if (!r) r = launch_wall_table(c, d_wptr, d_wface, nwrows, 0);
+    if (!r) r = launch_setup_mixed(c, 0);
     if (r) { vof_destroy(c); return r; }
     unsigned bad = 0;
     if (cudaMemcpy(&bad, c->status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||

@@ -59,6 +59,9 @@ struct vof_ctx {
     double *h_alpha, *h_Uc, *h_F;  // device staging for vof_advect_host
     int launches;
     unsigned long long *work;    // [3] phase-flux work counters
+    // FP32 geometry for the mixed kernels
+    float4 *cfl, *cfpl, *fpl, *cbl;
+    int *cfpptr;
     // kernel-group timing (vof_profile_begin / _end)
     cudaEvent_t *prof_ev;
     int prof_max, prof_steps;
@@ -80,3 +83,10 @@ int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cu
 int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt,
                   double *stats, cudaStream_t s);
 int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad);
+// ---- mixed precision (vof_mixed.cu) ----
+int launch_setup_mixed(vof_ctx *c, cudaStream_t s);
+int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
+                                const uint8_t *flags, const double *Up, const double *F, const double *lambda,
+                                double dt, double *Va, cudaStream_t s);
+int launch_phase_flux_mixed_list(vof_ctx *c, const double *alpha, const double *F, double dt, int sms,
+                                 cudaStream_t s);

@@ -8,133 +8,10 @@
 #include <stdint.h>
 
 #include "vof_internal.h"
+#include "vof_device.cuh"
 
 namespace {
-
-enum { CNT_BAND = 0, CNT_ICELL, CNT_VIOL0, CNT_VIOL1, CNT_PEND, CNT_MAXPOS, CNT_MAXCORR,
-       CNT_FALLBACK, CNT_LEN = 16 };
-
-constexpr int POS_MAXIT = 100;
-constexpr double POS_TOL = 1e-13;
-constexpr int CORR_MAXIT = 100;
-constexpr double CORR_TOL = 1e-14;
-constexpr double CORR_LMAX = 2.0;
-constexpr int CORR_NSAMP = 16;
-constexpr double BOUND_TOL = 1e-13;
-constexpr double BOUND_FLAG = 1e-12;
-constexpr int BOUND_PASSES = 16;
-constexpr int CLIP_STACK = 12;
-constexpr int DISP_STRIDE = (VOF_MAXFP + 1) * 3;
-
-// ------------------------------------------------------------------ vectors
-struct V3 { double x, y, z; };
-__device__ __forceinline__ V3 mk(double x, double y, double z) { return V3{x, y, z}; }
-__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ V3 operator-(V3 a, V3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ V3 operator*(V3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ V3 cross(V3 a, V3 b)
-{
-    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
-}
-__device__ __forceinline__ double det3(V3 a, V3 b, V3 c) { return dot(a, cross(b, c)); }
-__device__ __forceinline__ double norm3(V3 a) { return sqrt(dot(a, a)); }
-// signed volume of tetrahedron (a,b,c,d)
-__device__ __forceinline__ double tvol(V3 a, V3 b, V3 c, V3 d) { return det3(b - a, c - a, d - a) / 6.0; }
-
-__device__ __forceinline__ V3 ldP(const DevMesh &m, int p)
-{
-    return mk(__ldg(m.px + p), __ldg(m.py + p), __ldg(m.pz + p));
-}
-__device__ __forceinline__ V3 ld3(const double *a, int n, int i)
-{
-    return mk(__ldg(a + i), __ldg(a + n + i), __ldg(a + 2 * n + i));
-}
-__device__ __forceinline__ void st3(double *a, int n, int i, V3 v)
-{
-    a[i] = v.x; a[n + i] = v.y; a[2 * n + i] = v.z;
-}
-
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-__device__ __forceinline__ double warp_min(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ double warp_max(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// append with one atomic per warp
-__device__ __forceinline__ void warp_append(bool pred, int val, int *list, int *count, int cap,
-                                            unsigned *status)
-{
-    unsigned mask = __ballot_sync(0xffffffffu, pred);
-    if (!mask) return;
-    int lane = threadIdx.x & 31;
-    int leader = __ffs(mask) - 1;
-    int base = 0;
-    if (lane == leader) base = atomicAdd(count, __popc(mask));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    if (pred) {
-        int pos = base + __popc(mask & ((1u << lane) - 1u));
-        if (pos < cap) list[pos] = val;
-        else atomicOr(status, VOF_ST_CAPACITY);
-    }
-}
-
-// fraction of a tetrahedron below the level d of a linear function whose sorted
-// vertex values are h0 <= h1 <= h2 <= h3.  One/three vertices below: product of
-// edge fractions; two below: the wedge split into three tetrahedra, whose
-// barycentric volumes are ab, a(1-b)e and (1-a)ce -- all terms non-negative.
-__device__ __forceinline__ double frac_below(double h0, double h1, double h2, double h3, double d)
-{
-    if (d <= h0) return 0.0;
-    if (d >= h3) return 1.0;
-    if (d <= h1) {
-        double x = d - h0;
-        return (x / (h1 - h0)) * (x / (h2 - h0)) * (x / (h3 - h0));
-    }
-    if (d >= h2) {
-        double y = h3 - d;
-        return 1.0 - (y / (h3 - h0)) * (y / (h3 - h1)) * (y / (h3 - h2));
-    }
-    double a = (d - h0) / (h2 - h0), b = (d - h0) / (h3 - h0);
-    double c = (d - h1) / (h2 - h1), e = (d - h1) / (h3 - h1);
-    return a * b + a * (1.0 - b) * e + (1.0 - a) * c * e;
-}
-
-__device__ __forceinline__ void sort4(double &a, double &b, double &c, double &d)
-{
-    double t;
-#define CS(p, q) if (p > q) { t = p; p = q; q = t; }
-    CS(a, b) CS(c, d) CS(a, c) CS(b, d) CS(b, c)
-#undef CS
-}
-
-// i-th triangle of face f oriented along S_f (flip for the neighbour side)
-__device__ __forceinline__ void face_tri(const DevMesh &m, int f, int t, bool flip, V3 &t0, V3 &t1,
-                                         V3 &t2)
-{
-    int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
-    if (n == 3) {
-        t0 = ldP(m, __ldg(m.fpts + b)); t1 = ldP(m, __ldg(m.fpts + b + 1)); t2 = ldP(m, __ldg(m.fpts + b + 2));
-    } else {
-        t0 = ld3(m.cf, m.nf, f);
-        t1 = ldP(m, __ldg(m.fpts + b + t));
-        t2 = ldP(m, __ldg(m.fpts + b + (t + 1 == n ? 0 : t + 1)));
-    }
-    if (flip) { V3 s = t1; t1 = t2; t2 = s; }
-}
+using namespace vofd;
 
 // =========================================================== set-up kernels
 __global__ void k_face_geom(DevMesh m, double *cf, double *sf, double *nagc)
@@ -877,36 +754,46 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
     block_reduce5(v, partial + 5 * blockIdx.x);
 }
 
-// final fixed-order reduction of the per-block partials into stats
-__global__ void k_stats(const double *partial, int nblk, const int *counters, double *stats, int post,
-                        double *bound_partial)
+// final reduction of the per-block partials into stats: one block, each thread
+// folds a fixed strided subset, then a fixed tree (deterministic)
+constexpr int ST_THREADS = 256;
+
+__device__ __forceinline__ void fold5(double *r, const double *p)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double r[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
-    for (int k = 0; k < nblk; ++k) {
-        r[0] += partial[5 * k]; r[1] += partial[5 * k + 1];
-        r[2] = fmin(r[2], partial[5 * k + 2]); r[3] = fmax(r[3], partial[5 * k + 3]);
-        r[4] += partial[5 * k + 4];
+    r[0] += p[0]; r[1] += p[1]; r[2] = fmin(r[2], p[2]); r[3] = fmax(r[3], p[3]); r[4] += p[4];
+}
+
+__global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int nblk, const int *counters,
+                                                      double *stats, int post, const double *bound_partial)
+{
+    __shared__ double sh[2][5][ST_THREADS];
+    double r[5] = {0.0, 0.0, 1e300, -1e300, 0.0}, q[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    for (int k = threadIdx.x; k < nblk; k += ST_THREADS) {
+        fold5(r, partial + 5 * k);
+        if (post) fold5(q, bound_partial + 5 * k);
     }
-    stats[VOF_S_MASS_BEFORE] = r[0];
-    stats[VOF_S_MIN_PRE] = r[2];
-    stats[VOF_S_MAX_PRE] = r[3];
-    stats[VOF_S_BOUNDARY_OUT] = r[4];
-    if (!post) {
-        stats[VOF_S_MASS_AFTER] = r[1];
-        stats[VOF_S_MIN_POST] = r[2];
-        stats[VOF_S_MAX_POST] = r[3];
-    } else {
-        double q[3] = {0.0, 1e300, -1e300};
-        for (int k = 0; k < nblk; ++k) {
-            q[0] += bound_partial[5 * k + 1];
-            q[1] = fmin(q[1], bound_partial[5 * k + 2]);
-            q[2] = fmax(q[2], bound_partial[5 * k + 3]);
+    for (int i = 0; i < 5; ++i) { sh[0][i][threadIdx.x] = r[i]; sh[1][i][threadIdx.x] = q[i]; }
+    __syncthreads();
+    for (int w = ST_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            for (int t = 0; t < 2; ++t) {
+                double a[5], b2[5];
+                for (int i = 0; i < 5; ++i) { a[i] = sh[t][i][threadIdx.x]; b2[i] = sh[t][i][threadIdx.x + w]; }
+                fold5(a, b2);
+                for (int i = 0; i < 5; ++i) sh[t][i][threadIdx.x] = a[i];
+            }
         }
-        stats[VOF_S_MASS_AFTER] = q[0];
-        stats[VOF_S_MIN_POST] = q[1];
-        stats[VOF_S_MAX_POST] = q[2];
+        __syncthreads();
     }
+    if (threadIdx.x != 0) return;
+    stats[VOF_S_MASS_BEFORE] = sh[0][0][0];
+    stats[VOF_S_MIN_PRE] = sh[0][2][0];
+    stats[VOF_S_MAX_PRE] = sh[0][3][0];
+    stats[VOF_S_BOUNDARY_OUT] = sh[0][4][0];
+    const int t = post ? 1 : 0;
+    stats[VOF_S_MASS_AFTER] = sh[t][1][0];
+    stats[VOF_S_MIN_POST] = sh[t][2][0];
+    stats[VOF_S_MAX_POST] = sh[t][3][0];
     if (counters) {
         stats[VOF_S_N_INTERFACE] = counters[CNT_ICELL];
         stats[VOF_S_N_BAND] = counters[CNT_BAND];
@@ -1275,6 +1162,7 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
                           const double *Up, const double *F, const double *lambda, double dt, double *Va,
                           cudaStream_t s)
 {
+    if (c->precision == VOF_MIXED) return launch_phase_flux_mixed_all(c, alpha, n, d, flags, Up, F, lambda, dt, Va, s);
     PFArgs a{alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr, c->status, nullptr};
     k_phase_flux<false><<<cdiv((long)c->nf * 32, PF_WARPS * 32), PF_WARPS * 32, 0, s>>>(c->m, a);
     LAUNCH_CHECK();
@@ -1309,7 +1197,7 @@ int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cu
         k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, c->partial + 5 * UPD_BLOCKS, c->status);
         ++launches;
     }
-    k_stats<<<1, 32, 0, s>>>(c->partial, UPD_BLOCKS, nullptr, stats ? stats : c->stats_dev, c->bound,
+    k_stats<<<1, ST_THREADS, 0, s>>>(c->partial, UPD_BLOCKS, nullptr, stats ? stats : c->stats_dev, c->bound,
                              c->partial + 5 * UPD_BLOCKS);
     ++launches;
     LAUNCH_CHECK();
@@ -1341,9 +1229,14 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);
     MARK(3);
-    PFArgs a{alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band, cnt + CNT_BAND, c->disp_b,
-             c->status, c->work};
-    k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
+    if (c->precision == VOF_MIXED) {
+        int r = launch_phase_flux_mixed_list(c, alpha, F, dt, sms, s);
+        if (r) return r;
+    } else {
+        PFArgs a{alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band, cnt + CNT_BAND, c->disp_b,
+                 c->status, c->work};
+        k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
+    }
     launches += 3;
     LAUNCH_CHECK();
     MARK(4);
@@ -1359,7 +1252,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
         k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->partial + 5 * UPD_BLOCKS, c->status);
         ++launches;
     }
-    k_stats<<<1, 32, 0, s>>>(c->partial, UPD_BLOCKS, cnt, stats ? stats : c->stats_dev, c->bound,
+    k_stats<<<1, ST_THREADS, 0, s>>>(c->partial, UPD_BLOCKS, cnt, stats ? stats : c->stats_dev, c->bound,
                              c->partial + 5 * UPD_BLOCKS);
     ++launches;
     LAUNCH_CHECK();

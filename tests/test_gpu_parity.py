@@ -336,3 +336,49 @@ def test_full_size_sampled(torch, O, name):
     assert ctxb.status() == 0
     assert sb[4] >= -1e-12 and sb[5] <= 1 + 1e-12
     assert abs(sb[1] - sb[0]) / sb[0] < 1e-12
+
+
+# ------------------------------------------------------------ mixed precision
+# FP32 clipping in a face-centred frame: each piece carries a relative rounding
+# of a few 1e-7 of its own volume, so the phase volume of a face is within
+# ~1e-6 of the face's swept volume; tolerances are stated against the cell
+# volume.
+MIXED_VA_TOL = 2e-6     # |dVa| / max V_c
+MIXED_ALPHA_TOL = 2e-5  # |d alpha| after one full step
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_phase_flux_mixed_on_oracle_inputs(torch, O, name):
+    w, ctx, om = contexts(torch, O, name, precision=1)
+    F, U, dt = w.step_inputs(2)
+    a = w.alpha0
+    on, od, ofl, _, _ = om.reconstruct(a)
+    oUp = om.point_velocity(U)
+    olam, _, _ = om.correct_flux(oUp, F, dt)
+    oVa, ost = om.phase_flux(a, on, od, ofl, oUp, F, olam, dt)
+    Va = H(ctx.phase_flux(T(torch, a), T(torch, on), T(torch, od), T(torch, ofl, torch.uint8),
+                          T(torch, oUp), T(torch, F), T(torch, olam), dt))
+    _, vc, _, _ = om.geometry()
+    err = np.abs(Va - oVa).max() / vc.max()
+    print(f"mixed phase flux {name}: max |dVa|/V = {err:.3e}")
+    assert err < MIXED_VA_TOL
+    assert ctx.status() == 0
+
+
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_advect_mixed_replay(torch, O, name):
+    w, ctx, om = contexts(torch, O, name, precision=1)
+    ta = T(torch, w.alpha0)
+    worst = 0.0
+    for k in range(6):
+        F, U, dt = w.step_inputs(k)
+        a_in = H(ta).copy()
+        stats = H(ctx.advect(ta, T(torch, U), T(torch, F), dt))
+        oa, ost, st = om.advect(a_in, U, F, dt)
+        assert st == 0 and ctx.status() == 0
+        worst = max(worst, np.abs(H(ta) - oa).max())
+        drift = abs(stats[1] + stats[10] - stats[0]) / stats[0]
+        assert drift < 1e-12
+        assert stats[4] >= -1e-12 and stats[5] <= 1 + 1e-12
+    print(f"mixed advect {name}: max |d alpha| = {worst:.3e}")
+    assert worst < MIXED_ALPHA_TOL
