@@ -909,15 +909,15 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 #define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
 
 /* Reading R10: a conservative bounding pass, repeated until no cell is out of
- * [0,1] by more than BOUND_TOL (at most BOUND_PASSES times).  A source cell
- * with excess e above 1 hands its face neighbours what they can take, in
- * proportion to their free volume -- each receiver offers its free volume
- * divided by the number of excess sources next to it -- and pushes the rest
- * of e in equal parts to its face neighbours that are not excess sources, so
- * that excess travels on until it meets free volume.  A deficit below 0 is
- * treated the same way with the phase volume of the neighbours.  Every cell's
- * new value is a gather over its face neighbours, so the result does not
- * depend on the order in which cells are visited. */
+ * [0,1] by more than BOUND_TOL (at most BOUND_PASSES times).  Every cell has
+ * room for excess, (1-alpha)V, and for deficit, alpha V (zero outside [0,1]).
+ * A source with excess e above 1 requests from each face neighbour r the share
+ * e room_r / sum(room) of the room around it; a receiver whose requests exceed
+ * its room scales them all down to fit.  What a source could not place is
+ * pushed in equal parts to all its face neighbours (they pass it on in the next
+ * pass), so excess travels on until it meets room.  Deficits mirror this.  All
+ * amounts vary continuously with alpha, and every cell's new value is a gather
+ * over its face neighbours, so the result does not depend on visiting order. */
 static int face_nbr(const vo_mesh *m, int c, int i)
 {
     int f = m->cface[i];
@@ -925,16 +925,18 @@ static int face_nbr(const vo_mesh *m, int c, int i)
     return m->own[f] == c ? m->nei[f] : m->own[f];
 }
 
+static double room_exc(double a, double V) { return (a >= 0.0 && a < 1.0) ? (1.0 - a) * V : 0.0; }
+static double room_def(double a, double V) { return (a > 0.0 && a <= 1.0) ? a * V : 0.0; }
+
 static int bound_pass(const vo_mesh *m, double *alpha)
 {
     int nc = m->nc, c, any = 0;
     size_t n1 = (size_t)(nc > 0 ? nc : 1);
     double *e = (double *)calloc(n1, sizeof(double)), *u = (double *)calloc(n1, sizeof(double));
-    double *op = (double *)calloc(n1, sizeof(double)), *om = (double *)calloc(n1, sizeof(double));
     double *Cp = (double *)calloc(n1, sizeof(double)), *Cm = (double *)calloc(n1, sizeof(double));
-    double *give = (double *)calloc(n1, sizeof(double)), *take = (double *)calloc(n1, sizeof(double));
+    double *sp = (double *)malloc(n1 * sizeof(double)), *sm = (double *)malloc(n1 * sizeof(double));
     double *rp = (double *)calloc(n1, sizeof(double)), *rm = (double *)calloc(n1, sizeof(double));
-    int *dp = (int *)calloc(n1, sizeof(int)), *dm = (int *)calloc(n1, sizeof(int));
+    int *dg = (int *)calloc(n1, sizeof(int));
     double *na = (double *)malloc(n1 * sizeof(double));
     for (c = 0; c < nc; c++) {
         double a = alpha[c];
@@ -942,70 +944,74 @@ static int bound_pass(const vo_mesh *m, double *alpha)
         if (a < -BOUND_TOL) { u[c] = -a * m->vc[c]; any = 1; }
     }
     if (any) {
-        /* offers of every cell */
-#pragma omp parallel for schedule(static)
-        for (c = 0; c < nc; c++) {
-            int i, sp = 0, sm = 0;
-            double a = alpha[c];
-            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
-                int nb = face_nbr(m, c, i);
-                if (nb < 0) continue;
-                if (e[nb] > 0) sp++;
-                if (u[nb] > 0) sm++;
-            }
-            op[c] = (a >= 0.0 && a < 1.0) ? (1.0 - a) * m->vc[c] / (sp > 0 ? sp : 1) : 0.0;
-            om[c] = (a > 0.0 && a <= 1.0) ? a * m->vc[c] / (sm > 0 ? sm : 1) : 0.0;
-        }
-        /* what each source hands out by offer, and the rest it pushes on */
+        /* (1) room around each source */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i;
-            double sp = 0.0, sm = 0.0;
             if (e[c] == 0.0 && u[c] == 0.0) continue;
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
                 int nb = face_nbr(m, c, i);
                 if (nb < 0) continue;
-                sp += op[nb];
-                sm += om[nb];
-                if (e[nb] == 0.0) dp[c]++;
-                if (u[nb] == 0.0) dm[c]++;
-            }
-            if (e[c] > 0.0) {
-                Cp[c] = sp;
-                give[c] = e[c] < sp ? e[c] : sp;
-                rp[c] = dp[c] > 0 ? e[c] - give[c] : 0.0;
-            }
-            if (u[c] > 0.0) {
-                Cm[c] = sm;
-                take[c] = u[c] < sm ? u[c] : sm;
-                rm[c] = dm[c] > 0 ? u[c] - take[c] : 0.0;
+                Cp[c] += room_exc(alpha[nb], m->vc[nb]);
+                Cm[c] += room_def(alpha[nb], m->vc[nb]);
+                dg[c]++;
             }
         }
-        /* new value of every cell: its own hand-out, then its neighbours' */
+        /* (2) scale of each receiver: requests beyond its room are cut to fit */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i;
-            double dV = 0.0;
-            if (e[c] > 0.0) dV -= give[c] + rp[c];
-            if (u[c] > 0.0) dV += take[c] + rm[c];
+            double Qp = 0.0, Qm = 0.0, Rp = room_exc(alpha[c], m->vc[c]), Rm = room_def(alpha[c], m->vc[c]);
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
                 int nb = face_nbr(m, c, i);
                 if (nb < 0) continue;
-                if (e[nb] > 0.0 && e[c] == 0.0) {
-                    if (Cp[nb] > 0.0) dV += give[nb] * (op[c] / Cp[nb]);
-                    if (dp[nb] > 0) dV += rp[nb] / dp[nb];
+                if (e[nb] > 0.0 && Cp[nb] > 0.0) Qp += e[nb] * (Rp / Cp[nb]);
+                if (u[nb] > 0.0 && Cm[nb] > 0.0) Qm += u[nb] * (Rm / Cm[nb]);
+            }
+            sp[c] = Qp > Rp ? Rp / Qp : 1.0;
+            sm[c] = Qm > Rm ? Rm / Qm : 1.0;
+        }
+        /* (3) what each source placed, and the rest it pushes on */
+#pragma omp parallel for schedule(static)
+        for (c = 0; c < nc; c++) {
+            int i;
+            double gp = 0.0, gm = 0.0;
+            if (e[c] == 0.0 && u[c] == 0.0) continue;
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+                int nb = face_nbr(m, c, i);
+                if (nb < 0) continue;
+                if (e[c] > 0.0 && Cp[c] > 0.0) gp += e[c] * (room_exc(alpha[nb], m->vc[nb]) / Cp[c]) * sp[nb];
+                if (u[c] > 0.0 && Cm[c] > 0.0) gm += u[c] * (room_def(alpha[nb], m->vc[nb]) / Cm[c]) * sm[nb];
+            }
+            if (e[c] > 0.0) rp[c] = dg[c] > 0 ? e[c] - gp : 0.0;
+            if (u[c] > 0.0) rm[c] = dg[c] > 0 ? u[c] - gm : 0.0;
+            if (dg[c] == 0) { e[c] = gp; u[c] = gm; } /* nothing to push to: release only what was placed */
+        }
+        /* (4) new value of every cell: its own release, then what its neighbours send */
+#pragma omp parallel for schedule(static)
+        for (c = 0; c < nc; c++) {
+            int i;
+            double dV = 0.0, V = m->vc[c];
+            double Rp = room_exc(alpha[c], V), Rm = room_def(alpha[c], V);
+            if (e[c] > 0.0) dV -= e[c];
+            if (u[c] > 0.0) dV += u[c];
+            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+                int nb = face_nbr(m, c, i);
+                if (nb < 0) continue;
+                if (e[nb] > 0.0) {
+                    if (Cp[nb] > 0.0) dV += e[nb] * (Rp / Cp[nb]) * sp[c];
+                    if (dg[nb] > 0) dV += rp[nb] / dg[nb];
                 }
-                if (u[nb] > 0.0 && u[c] == 0.0) {
-                    if (Cm[nb] > 0.0) dV -= take[nb] * (om[c] / Cm[nb]);
-                    if (dm[nb] > 0) dV -= rm[nb] / dm[nb];
+                if (u[nb] > 0.0) {
+                    if (Cm[nb] > 0.0) dV -= u[nb] * (Rm / Cm[nb]) * sm[c];
+                    if (dg[nb] > 0) dV -= rm[nb] / dg[nb];
                 }
             }
-            na[c] = dV != 0.0 ? (alpha[c] * m->vc[c] + dV) / m->vc[c] : alpha[c];
+            na[c] = dV != 0.0 ? (alpha[c] * V + dV) / V : alpha[c];
         }
         memcpy(alpha, na, sizeof(double) * (size_t)nc);
     }
-    free(e); free(u); free(op); free(om); free(Cp); free(Cm); free(give); free(take);
-    free(rp); free(rm); free(dp); free(dm); free(na);
+    free(e); free(u); free(Cp); free(Cm); free(sp); free(sm); free(rp); free(rm); free(dg); free(na);
     return any;
 }
 

@@ -313,9 +313,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->flags = dev_alloc<uint8_t>(c, nc, &err);
     c->pit = dev_alloc<int>(c, nc, &err);
     c->Va = dev_alloc<double>(c, nf, &err);
-    c->gv = dev_alloc<double>(c, nc, &err);
-    c->Cc = dev_alloc<double>(c, nc, &err);
-    c->rmd = dev_alloc<double>(c, nc, &err);
+    c->bscr = dev_alloc<double>(c, 8 * (size_t)nc, &err);
     c->dgi = dev_alloc<int>(c, nc, &err);
     c->gpartial = dev_alloc<double>(c, 4 * 512, &err);
     c->partial = dev_alloc<double>(c, 10 * 1024, &err);
@@ -332,9 +330,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->cbl = dev_alloc<float4>(c, 2 * (size_t)nc, &err);
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
-    cudaMemset(c->gv, 0, sizeof(double) * nc);
-    cudaMemset(c->Cc, 0, sizeof(double) * nc);
-    cudaMemset(c->rmd, 0, sizeof(double) * nc);
+    cudaMemset(c->bscr, 0, sizeof(double) * 8 * nc);
     cudaMemset(c->dgi, 0, sizeof(int) * nc);
     cudaMemset(c->counters, 0, sizeof(int) * 16);
     cudaMemset(c->status, 0, sizeof(unsigned));

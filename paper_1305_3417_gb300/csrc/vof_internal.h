@@ -50,7 +50,7 @@ struct vof_ctx {
     uint8_t *flags;
     int *pit;
     double *Va;
-    double *gv, *Cc, *rmd;       // bounding scratch per cell
+    double *bscr;                // bounding scratch, 8 doubles per cell
     int *dgi;
     double *gpartial;            // global bounding partial sums
     double *partial;             // reduction partials

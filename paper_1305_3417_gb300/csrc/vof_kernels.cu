@@ -821,14 +821,14 @@ __global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *a
 }
 
 // ------------------------------------------------- bounding pass (reading R10)
-// Local passes: a source with excess above 1 hands its face neighbours what
-// they can take, in proportion to their free volume (each receiver offers its
-// free volume divided by its number of excess sources), and pushes the rest in
-// equal parts to its face neighbours that are not excess sources; deficits
-// below 0 mirror this with phase volume.  Every touched cell's new value is a
-// gather over its face neighbours in face order.  The sources are few, so one
-// block runs all passes with block barriers between the phases and stops as
-// soon as no cell is out of bounds.
+// Every cell has room for excess, (1-alpha)V, and for deficit, alpha V (zero
+// outside [0,1]).  A source with excess e requests from each face neighbour r
+// the share e room_r / sum(room) of the room around it; a receiver whose
+// requests exceed its room scales them down to fit; what a source could not
+// place is pushed in equal parts to all its face neighbours.  Deficits mirror
+// this.  Every touched cell's new value is a gather over its face neighbours in
+// face order.  The sources are few, so one block runs all passes with block
+// barriers between the phases and stops once no cell is out of bounds.
 __device__ __forceinline__ int nbr_of(const DevMesh &m, int c, int k)
 {
     int code = m.cface[k], f = code >> 1;
@@ -837,35 +837,41 @@ __device__ __forceinline__ int nbr_of(const DevMesh &m, int c, int k)
 }
 __device__ __forceinline__ bool is_exc(double a) { return a > 1.0 + BOUND_TOL; }
 __device__ __forceinline__ bool is_def(double a) { return a < -BOUND_TOL; }
+__device__ __forceinline__ double room_exc(double a, double V) { return (a >= 0.0 && a < 1.0) ? (1.0 - a) * V : 0.0; }
+__device__ __forceinline__ double room_def(double a, double V) { return (a > 0.0 && a <= 1.0) ? a * V : 0.0; }
 
-// offers of cell c: free volume and phase volume, each split over its sources
-__device__ __forceinline__ void offers(const DevMesh &m, const double *alpha, int c, double &op, double &om)
-{
-    int sp = 0, sm = 0;
-    for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-        int nb = nbr_of(m, c, k);
-        if (nb < 0) continue;
-        double a = alpha[nb];
-        sp += is_exc(a);
-        sm += is_def(a);
-    }
-    double a = alpha[c], V = m.vc[c];
-    op = (a >= 0.0 && a < 1.0) ? (1.0 - a) * V / (sp > 0 ? sp : 1) : 0.0;
-    om = (a > 0.0 && a <= 1.0) ? a * V / (sm > 0 ? sm : 1) : 0.0;
-}
+// scratch per cell: [Cp, Cm, rp, rm, release, sp, sm, -]
+enum { BS_CP = 0, BS_CM, BS_RP, BS_RM, BS_REL, BS_SP, BS_SM, BS_N = 8 };
 
 struct BoundBufs {
     int *la, *lb;        // source lists (ping-pong), capacity nc
     const int *n0;       // initial count (from the update kernel)
     int *pc;             // pending cells, capacity cap_pend
     double *pa;          // pending values
-    double *gv, *rm, *Cc;  // per source: handed out by offer, pushed on, sum of offers
-    int *dg;             // per source: number of push receivers
+    double *bs;          // BS_N doubles per cell
+    int *dg;             // per source: number of face neighbours
     int *left;           // out: sources left after the local passes
     int cap, cap_pend;
 };
 
 constexpr int BOUND_THREADS = 1024;
+
+// lowest-index source among x's face neighbours (and x itself if self)
+__device__ __forceinline__ int first_source(const DevMesh &m, const double *alpha, int x, bool self)
+{
+    int first = 0x7fffffff;
+    if (self) {
+        double ax = alpha[x];
+        if (is_exc(ax) || is_def(ax)) first = x;
+    }
+    for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
+        int s = nbr_of(m, x, q);
+        if (s < 0) continue;
+        double as = alpha[s];
+        if ((is_exc(as) || is_def(as)) && s < first) first = s;
+    }
+    return first;
+}
 
 __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double *alpha, BoundBufs b,
                                                                unsigned *status)
@@ -874,73 +880,99 @@ __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double
     if (threadIdx.x == 0) { s_n = min(*b.n0, b.cap); s_next = 0; s_pend = 0; }
     __syncthreads();
     int *src = b.la, *nxt = b.lb;
+    double *bs = b.bs;
     for (int pass = 0; pass < BOUND_PASSES; ++pass) {
         const int n = s_n;
         if (n == 0) break;
-        // (1) per source: sum of neighbour offers, hand-out and push-on amounts
+        // (1) room around each source
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             int c = src[i];
-            double a = alpha[c], V = m.vc[c], sp = 0.0, sm = 0.0;
-            int dp = 0, dm = 0;
+            double Cp = 0.0, Cm = 0.0;
+            int dg = 0;
             for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
                 int nb = nbr_of(m, c, k);
                 if (nb < 0) continue;
-                double op, om;
-                offers(m, alpha, nb, op, om);
-                sp += op;
-                sm += om;
-                double an = alpha[nb];
-                dp += !is_exc(an);
-                dm += !is_def(an);
+                double an = alpha[nb], Vn = m.vc[nb];
+                Cp += room_exc(an, Vn);
+                Cm += room_def(an, Vn);
+                ++dg;
             }
-            if (is_exc(a)) {
-                double e = (a - 1.0) * V, g = fmin(e, sp);
-                b.gv[c] = g; b.Cc[c] = sp; b.dg[c] = dp; b.rm[c] = dp > 0 ? e - g : 0.0;
-            } else {
-                double u = -a * V, t = fmin(u, sm);
-                b.gv[c] = t; b.Cc[c] = sm; b.dg[c] = dm; b.rm[c] = dm > 0 ? u - t : 0.0;
+            bs[BS_N * (size_t)c + BS_CP] = Cp;
+            bs[BS_N * (size_t)c + BS_CM] = Cm;
+            b.dg[c] = dg;
+        }
+        __syncthreads();
+        // (2) scale of each receiver (by its lowest-index neighbouring source)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int c = src[i];
+            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+                int r = nbr_of(m, c, k);
+                if (r < 0 || first_source(m, alpha, r, false) != c) continue;
+                double ar = alpha[r], Vr = m.vc[r], Rp = room_exc(ar, Vr), Rm = room_def(ar, Vr);
+                double Qp = 0.0, Qm = 0.0;
+                for (int q = m.cptr[r]; q < m.cptr[r + 1]; ++q) {
+                    int s = nbr_of(m, r, q);
+                    if (s < 0) continue;
+                    double as = alpha[s], Vs = m.vc[s];
+                    double Cps = bs[BS_N * (size_t)s + BS_CP], Cms = bs[BS_N * (size_t)s + BS_CM];
+                    if (is_exc(as) && Cps > 0.0) Qp += (as - 1.0) * Vs * (Rp / Cps);
+                    if (is_def(as) && Cms > 0.0) Qm += -as * Vs * (Rm / Cms);
+                }
+                bs[BS_N * (size_t)r + BS_SP] = Qp > Rp ? Rp / Qp : 1.0;
+                bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
             }
         }
         __syncthreads();
-        // (2) new values of the sources and their neighbours, each cell once:
+        // (3) what each source placed, the rest it pushes on, what it releases
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            int c = src[i];
+            double a = alpha[c], V = m.vc[c];
+            double *q = bs + BS_N * (size_t)c;
+            double gp = 0.0, gm = 0.0, e = is_exc(a) ? (a - 1.0) * V : 0.0, u = is_def(a) ? -a * V : 0.0;
+            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+                int nb = nbr_of(m, c, k);
+                if (nb < 0) continue;
+                double an = alpha[nb], Vn = m.vc[nb];
+                if (e > 0.0 && q[BS_CP] > 0.0) gp += e * (room_exc(an, Vn) / q[BS_CP]) * bs[BS_N * (size_t)nb + BS_SP];
+                if (u > 0.0 && q[BS_CM] > 0.0) gm += u * (room_def(an, Vn) / q[BS_CM]) * bs[BS_N * (size_t)nb + BS_SM];
+            }
+            int dg = b.dg[c];
+            q[BS_RP] = (e > 0.0 && dg > 0) ? e - gp : 0.0;
+            q[BS_RM] = (u > 0.0 && dg > 0) ? u - gm : 0.0;
+            q[BS_REL] = e > 0.0 ? (dg > 0 ? e : gp) : (dg > 0 ? u : gm);
+        }
+        __syncthreads();
+        // (4) new values of the sources and their neighbours, each cell once:
         //     by the lowest-index source in its closed face neighbourhood
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             int c = src[i];
             for (int k = m.cptr[c] - 1; k < m.cptr[c + 1]; ++k) {
                 int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
-                if (x < 0) continue;
-                double ax = alpha[x];
+                if (x < 0 || first_source(m, alpha, x, true) != c) continue;
+                double ax = alpha[x], V = m.vc[x];
                 bool xe = is_exc(ax), xd = is_def(ax);
-                int first = (xe || xd) ? x : 0x7fffffff;
-                for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
-                    int s = nbr_of(m, x, q);
-                    if (s < 0) continue;
-                    double as = alpha[s];
-                    if ((is_exc(as) || is_def(as)) && s < first) first = s;
-                }
-                if (first != c) continue;
-                double op, om;
-                offers(m, alpha, x, op, om);
+                double Rp = room_exc(ax, V), Rm = room_def(ax, V);
                 double dV = 0.0;
-                if (xe) dV -= b.gv[x] + b.rm[x];
-                if (xd) dV += b.gv[x] + b.rm[x];
+                if (xe) dV -= bs[BS_N * (size_t)x + BS_REL];
+                if (xd) dV += bs[BS_N * (size_t)x + BS_REL];
                 for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
                     int s = nbr_of(m, x, q);
                     if (s < 0) continue;
-                    double as = alpha[s];
-                    if (is_exc(as) && !xe) {
-                        if (b.Cc[s] > 0.0) dV += b.gv[s] * (op / b.Cc[s]);
-                        if (b.dg[s] > 0) dV += b.rm[s] / b.dg[s];
+                    double as = alpha[s], Vs = m.vc[s];
+                    const double *bq = bs + BS_N * (size_t)s;
+                    int dgs = b.dg[s];
+                    if (is_exc(as)) {
+                        if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp / bq[BS_CP]) * bs[BS_N * (size_t)x + BS_SP];
+                        if (dgs > 0) dV += bq[BS_RP] / dgs;
                     }
-                    if (is_def(as) && !xd) {
-                        if (b.Cc[s] > 0.0) dV -= b.gv[s] * (om / b.Cc[s]);
-                        if (b.dg[s] > 0) dV -= b.rm[s] / b.dg[s];
+                    if (is_def(as)) {
+                        if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm / bq[BS_CM]) * bs[BS_N * (size_t)x + BS_SM];
+                        if (dgs > 0) dV -= bq[BS_RM] / dgs;
                     }
                 }
                 // sources always go to the pending list (a source that could not
                 // move keeps its value and stays a source next pass)
                 if (dV != 0.0 || xe || xd) {
-                    double V = m.vc[x];
                     int pos = atomicAdd(&s_pend, 1);
                     if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = dV != 0.0 ? (ax * V + dV) / V : ax; }
                     else atomicOr(status, VOF_ST_CAPACITY);
@@ -948,15 +980,11 @@ __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double
             }
         }
         __syncthreads();
-        // (3) apply, clear the per-source scratch
+        // (5) apply
         const int np = min(s_pend, b.cap_pend);
         for (int i = threadIdx.x; i < np; i += blockDim.x) alpha[b.pc[i]] = b.pa[i];
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            int c = src[i];
-            b.gv[c] = 0.0; b.rm[c] = 0.0; b.Cc[c] = 0.0; b.dg[c] = 0;
-        }
         __syncthreads();
-        // (4) the touched cells still out of bounds are the next sources
+        // (6) the touched cells still out of bounds are the next sources
         for (int i = threadIdx.x; i < np; i += blockDim.x) {
             double a = alpha[b.pc[i]];
             if (is_exc(a) || is_def(a)) {
@@ -1171,7 +1199,7 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
 
 static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches)
 {
-    BoundBufs b{c->viol[0], c->viol[1], c->counters + CNT_VIOL0, c->pend_c, c->pend_a, c->gv, c->rmd, c->Cc, c->dgi,
+    BoundBufs b{c->viol[0], c->viol[1], c->counters + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, c->dgi,
                 c->counters + CNT_VIOL1, c->nc, 8 * c->nc};
     k_bound_local<<<1, BOUND_THREADS, 0, s>>>(c->m, alpha, b, c->status);
     k_bound_global_reduce<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial);

@@ -195,6 +195,14 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         }
         const V3 o = ld3(m.cf, m.nf, f);
         const int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
+        // Complement form: when the upwind cell is mostly phase, sum the void
+        // pieces and take V_alpha = F dt - void (equal in exact arithmetic since
+        // the corrected polyhedron holds F dt and the stencil covers it); a
+        // polyhedron inside full cells then carries exactly F dt, one inside
+        // empty cells exactly 0, and FP32 rounding stays with mixed cells.
+        const double Ff = a.F[f];
+        const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
+        const bool comp = a.alpha[up] >= 0.5;
         const int nt = n == 3 ? 3 : 3 * n;
         // ---- flux polyhedron tetrahedra in the face frame
         float bx[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
@@ -270,7 +278,8 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         for (int s = s0; s < s1; ++s) {
             const int c = __ldg(m.scell + s);
             const double al = a.alpha[c];
-            if (al <= eps) continue;  // empty cell carries no phase
+            if (!comp && al <= eps) continue;       // empty cell carries no phase
+            if (comp && al >= 1.0 - eps) continue;  // full cell carries no void
             const V3 cc = ld3(m.cc, m.nc, c);
             const F3 dc = f3((float)(cc.x - o.x), (float)(cc.y - o.y), (float)(cc.z - o.z));
             const float4 cb0 = __ldg(a.cbl + 2 * (size_t)c), cb1 = __ldg(a.cbl + 2 * (size_t)c + 1);
@@ -280,13 +289,15 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
             float wgt = 1.0f;
             bool useH = false;
             float4 H = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (al < 1.0 - eps) {
+            if (al > eps && al < 1.0 - eps) {
                 if (a.flags[c] & VOF_ORIENTED) {
                     V3 hn = ld3(a.n, m.nc, c);
                     double hd = a.d[c] - dot(hn, o);
-                    H = make_float4((float)hn.x, (float)hn.y, (float)hn.z, (float)hd);
+                    // phase side n.x <= d; the void side is -n.x <= -d
+                    float sg = comp ? -1.0f : 1.0f;
+                    H = make_float4(sg * (float)hn.x, sg * (float)hn.y, sg * (float)hn.z, sg * (float)hd);
                     useH = true;
-                } else wgt = (float)al;
+                } else wgt = comp ? (float)(1.0 - al) : (float)al;
             }
             // ---- this cell's tetrahedra, 32 at a time; lanes build, then pair
             const int f0 = __ldg(m.cptr + c), f1 = __ldg(m.cptr + c + 1);
@@ -381,6 +392,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         }
         // finish in FP64: lane sums and compensations, then the 1/6 of the volumes
         double acc = warp_sum((double)accs + (double)accc) / 6.0;
+        if (comp) acc = Ff * a.dt - acc;
         if (a.work) {
 #pragma unroll
             for (int o2 = 16; o2 > 0; o2 >>= 1) {
