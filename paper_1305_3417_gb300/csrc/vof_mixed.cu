@@ -150,7 +150,7 @@ struct MXArgs {
     double dt;
     double *Va;
     const int *list, *count;
-    const double *disp;
+    const double *disp, *lam_b;
     unsigned *status;
     unsigned long long *work;
     const float4 *cfl, *cfpl, *fpl, *cbl;  // FP32 local geometry
@@ -202,7 +202,9 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         // empty cells exactly 0, and FP32 rounding stays with mixed cells.
         const double Ff = a.F[f];
         const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
-        const bool comp = a.alpha[up] >= 0.5;
+        // (not for the normal-sweep fallback, which can leave the domain at walls)
+        const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
+        const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0;
         const int nt = n == 3 ? 3 : 3 * n;
         // ---- flux polyhedron tetrahedra in the face frame
         float bx[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
@@ -460,7 +462,7 @@ static MXArgs mx_args(vof_ctx *c, const double *alpha, const double *n, const do
                       const double *Up, const double *F, const double *lambda, double dt, double *Va,
                       const int *list, const int *count, const double *disp, unsigned long long *work)
 {
-    return MXArgs{alpha, n, d, flags, Up, F, lambda, dt, Va, list, count, disp, c->status, work,
+    return MXArgs{alpha, n, d, flags, Up, F, lambda, dt, Va, list, count, disp, c->lam_b, c->status, work,
                   c->cfl, c->cfpl, c->fpl, c->cbl, c->cfpptr};
 }
 
