@@ -903,7 +903,7 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 }
 
 /* ---------------------------------------------------------- A7: update */
-#define BOUND_PASSES 16
+#define BOUND_PASSES 4
 #define BOUND_TOL 1e-13   /* excursions this small (round-off) are left alone and never
                            * decide a redistribution; the target is 1e-12 */
 #define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
