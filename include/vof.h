@@ -198,6 +198,27 @@ int vof_work_counts(vof_ctx *ctx, unsigned long long counts[3], int reset, void 
  * Synchronous; allocates and frees one scalar of device memory. */
 int vof_probe_fma(int device, int precision, double *flops_per_s, void *stream);
 
+/* Reconstruction for callers that cannot allocate device memory when they
+ * call it -- code inside a host framework that owns every device allocation,
+ * or a real-time loop that forbids cudaMalloc after start-up.  The paper has
+ * no counterpart: it is vof_reconstruct's computation (same outputs, same
+ * arrays, same errors) run over a compacted list of the interface cells that
+ * is kept in a file-scope device array of VOF_STATIC_MAX_CELLS ints (16 MiB,
+ * held by every GPU that loads the library until the process exits), not in
+ * memory the caller or the context allocates.  It calls no allocating routine.
+ * - The context must exist (vof_create allocates; someone who can must call it).
+ * - n_cells > VOF_STATIC_MAX_CELLS is rejected with VOF_ERR_INVALID_ARG.
+ * - The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any
+ *   stream capture.
+ * - Every call on a device shares the one array: the list length is cleared
+ *   at the start of each call, and calls that overlap on the GPU (different
+ *   streams, or different contexts on the same device) race.
+ * - Iteration counts are not returned. */
+#define VOF_STATIC_MAX_CELLS (1 << 22)
+int vof_reconstruct_static(vof_ctx *ctx, const double *alpha, double *n, double *d, uint8_t *flags,
+                           void *stream);
+
 /* Reads (synchronising `stream`) and clears the device status word. */
 int vof_status(vof_ctx *ctx, uint32_t *bits, void *stream);
 
