@@ -325,6 +325,8 @@ def main():
                             "alpha_max_pre_bound": float(S[:, 3].max()),
                             "band_faces_per_step": float(S[:, 7].mean()),
                             "interface_cells_per_step": float(S[:, 6].mean()),
+                            "bound_sources_per_step": float(S[:, 12].mean()),
+                            "bound_left_after_local": float(S[:, 13].mean()),
                             "status_bits": int(st0 | st1)}}
         print(json.dumps(line), flush=True)
     if world > 1:

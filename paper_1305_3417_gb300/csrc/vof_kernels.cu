@@ -7,6 +7,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <cooperative_groups.h>
+
 #include "vof_internal.h"
 #include "vof_device.cuh"
 
@@ -148,7 +150,28 @@ __global__ void k_point_velocity(DevMesh m, const double *__restrict__ Uc, doubl
 // one warp per cell: NAG gradient over the (face, point) entries of the cell,
 // then Alg. 1 with the fill function summed over the cell tetrahedra, one or
 // two per lane, each a closed-form cut fraction of its sorted projections.
-template <bool LIST>
+__device__ __forceinline__ float ffrac_below_rel(float h0, float h1, float h2, float h3, float d)
+{
+    if (d <= h0) return 0.0f;
+    if (d >= h3) return 1.0f;
+    if (d <= h1) {
+        float x = d - h0;
+        return (x / (h1 - h0)) * (x / (h2 - h0)) * (x / (h3 - h0));
+    }
+    if (d >= h2) {
+        float y = h3 - d;
+        return 1.0f - (y / (h3 - h0)) * (y / (h3 - h1)) * (y / (h3 - h2));
+    }
+    float a = (d - h0) / (h2 - h0), b = (d - h0) / (h3 - h0);
+    float c = (d - h1) / (h2 - h1), e = (d - h1) / (h3 - h1);
+    return a * b + a * (1.0f - b) * e + (1.0f - a) * c * e;
+}
+
+// MIXED: while the fill residual is above 1e-5 (FP32 rounding of the fill is
+// ~1e-7), the fill is evaluated in FP32 on projections taken relative to the
+// cell centre; the iteration then continues in FP64 to the 1e-13 stop.  Cells
+// with alpha within 1e-4 of 0 or 1 stay in FP64 (the bracket near the ends).
+template <bool LIST, bool MIXED>
 __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const int *list, const int *count, double *nout,
                                                      double *dout, uint8_t *fout, int *itout,
@@ -202,6 +225,8 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                 // ---- cell tetrahedra (c_c, outward face triangle), lanes j, j+32
                 const V3 ctr = ld3(m.cc, m.nc, c);
                 double h[VOF_MAXK_LANE][4], vk[VOF_MAXK_LANE];
+                float hf[VOF_MAXK_LANE][4], vkf[VOF_MAXK_LANE];
+                const double href = dot(nn, ctr);
                 double lo = 1e300, hi = -1e300;
 #pragma unroll
                 for (int s = 0; s < VOF_MAXK_LANE; ++s) {
@@ -224,6 +249,11 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     double e0 = dot(nn, ctr), e1 = dot(nn, t0), e2 = dot(nn, t1), e3 = dot(nn, t2);
                     sort4(e0, e1, e2, e3);
                     h[s][0] = e0; h[s][1] = e1; h[s][2] = e2; h[s][3] = e3;
+                    if (MIXED) {
+                        hf[s][0] = (float)(e0 - href); hf[s][1] = (float)(e1 - href);
+                        hf[s][2] = (float)(e2 - href); hf[s][3] = (float)(e3 - href);
+                        vkf[s] = (float)vk[s];
+                    }
                     lo = fmin(lo, e0);
                     hi = fmax(hi, e3);
                 }
@@ -231,21 +261,34 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                 // ---- Alg. 1: secant, bisection once the secant leaves the bracket
                 double A = dmin, B = dmax, x0 = A, g0 = -a, x1 = B, g1 = 1.0 - a, x = 0.0, gx = 0.0;
                 bool bisect = false;
+                bool fp32 = MIXED && a > 1e-4 && a < 1.0 - 1e-4;
+                const float Vf = (float)V;
                 while (it < POS_MAXIT) {
                     if (!bisect) {
                         x = x1 - g1 * (x1 - x0) / (g1 - g0);
                         if (!(x > A && x < B)) bisect = true;
                     }
                     if (bisect) x = 0.5 * (A + B);
-                    double part = 0.0;
+                    if (MIXED && fp32) {
+                        float part = 0.0f, xr = (float)(x - href);
 #pragma unroll
-                    for (int s = 0; s < VOF_MAXK_LANE; ++s)
-                        if (vk[s] > 0.0) part += vk[s] * frac_below(h[s][0], h[s][1], h[s][2], h[s][3], x);
-                    gx = warp_sum(part) / V - a;
+                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                            if (vkf[s] > 0.0f) part += vkf[s] * ffrac_below_rel(hf[s][0], hf[s][1], hf[s][2], hf[s][3], xr);
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                        gx = (double)(part / Vf) - a;
+                        if (fabs(gx) <= 1e-5) fp32 = false;  // near the root: FP64 from here
+                    } else {
+                        double part = 0.0;
+#pragma unroll
+                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                            if (vk[s] > 0.0) part += vk[s] * frac_below(h[s][0], h[s][1], h[s][2], h[s][3], x);
+                        gx = warp_sum(part) / V - a;
+                    }
                     ++it;
                     if (gx < 0) A = x; else B = x;
                     x0 = x1; g0 = g1; x1 = x; g1 = gx;
-                    if (fabs(gx) <= POS_TOL) break;
+                    if (!(MIXED && fp32) && fabs(gx) <= POS_TOL) break;
                     if (B - A <= 1e-15 * (dmax - dmin)) break;
                 }
                 if (it >= POS_MAXIT && lane == 0) atomicOr(status, VOF_ST_POS_NOT_CONVERGED);
@@ -800,6 +843,8 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int
         stats[VOF_S_MAX_POS_IT] = counters[CNT_MAXPOS];
         stats[VOF_S_MAX_CORR_IT] = counters[CNT_MAXCORR];
         stats[VOF_S_N_FALLBACK] = counters[CNT_FALLBACK];
+        stats[VOF_S_N_BOUND_SOURCES] = counters[CNT_VIOL0];
+        stats[VOF_S_N_BOUND_LEFT] = counters[CNT_VIOL1];
     }
 }
 
@@ -852,9 +897,10 @@ struct BoundBufs {
     int *dg;             // per source: number of face neighbours
     int *left;           // out: sources left after the local passes
     int cap, cap_pend;
+    int *gc;             // grid-shared counters [3]
 };
 
-constexpr int BOUND_THREADS = 1024;
+constexpr int BOUND_THREADS = 256;
 
 // lowest-index source among x's face neighbours (and x itself if self)
 __device__ __forceinline__ int first_source(const DevMesh &m, const double *alpha, int x, bool self)
@@ -873,19 +919,24 @@ __device__ __forceinline__ int first_source(const DevMesh &m, const double *alph
     return first;
 }
 
+// Cooperative launch: the grid runs the passes together, with grid-wide
+// barriers between the phases (counters gc: [0] sources, [1] next, [2] pending)
 __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double *alpha, BoundBufs b,
                                                                unsigned *status)
 {
-    __shared__ int s_n, s_next, s_pend;
-    if (threadIdx.x == 0) { s_n = min(*b.n0, b.cap); s_next = 0; s_pend = 0; }
-    __syncthreads();
+    namespace cg = cooperative_groups;
+    cg::grid_group grid = cg::this_grid();
+    volatile int *gc = b.gc;
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    if (tid == 0) { gc[0] = min(*b.n0, b.cap); gc[1] = 0; gc[2] = 0; }
+    grid.sync();
     int *src = b.la, *nxt = b.lb;
     double *bs = b.bs;
     for (int pass = 0; pass < BOUND_PASSES; ++pass) {
-        const int n = s_n;
+        const int n = gc[0];
         if (n == 0) break;
         // (1) room around each source
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += nth) {
             int c = src[i];
             double Cp = 0.0, Cm = 0.0;
             int dg = 0;
@@ -901,9 +952,9 @@ __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double
             bs[BS_N * (size_t)c + BS_CM] = Cm;
             b.dg[c] = dg;
         }
-        __syncthreads();
+        grid.sync();
         // (2) scale of each receiver (by its lowest-index neighbouring source)
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += nth) {
             int c = src[i];
             for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
                 int r = nbr_of(m, c, k);
@@ -922,9 +973,9 @@ __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double
                 bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
             }
         }
-        __syncthreads();
+        grid.sync();
         // (3) what each source placed, the rest it pushes on, what it releases
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += nth) {
             int c = src[i];
             double a = alpha[c], V = m.vc[c];
             double *q = bs + BS_N * (size_t)c;
@@ -941,10 +992,10 @@ __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double
             q[BS_RM] = (u > 0.0 && dg > 0) ? u - gm : 0.0;
             q[BS_REL] = e > 0.0 ? (dg > 0 ? e : gp) : (dg > 0 ? u : gm);
         }
-        __syncthreads();
+        grid.sync();
         // (4) new values of the sources and their neighbours, each cell once:
         //     by the lowest-index source in its closed face neighbourhood
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int i = tid; i < n; i += nth) {
             int c = src[i];
             for (int k = m.cptr[c] - 1; k < m.cptr[c + 1]; ++k) {
                 int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
@@ -973,32 +1024,32 @@ __global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double
                 // sources always go to the pending list (a source that could not
                 // move keeps its value and stays a source next pass)
                 if (dV != 0.0 || xe || xd) {
-                    int pos = atomicAdd(&s_pend, 1);
+                    int pos = atomicAdd((int *)&gc[2], 1);
                     if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = dV != 0.0 ? (ax * V + dV) / V : ax; }
                     else atomicOr(status, VOF_ST_CAPACITY);
                 }
             }
         }
-        __syncthreads();
+        grid.sync();
         // (5) apply
-        const int np = min(s_pend, b.cap_pend);
-        for (int i = threadIdx.x; i < np; i += blockDim.x) alpha[b.pc[i]] = b.pa[i];
-        __syncthreads();
+        const int np = min(gc[2], b.cap_pend);
+        for (int i = tid; i < np; i += nth) alpha[b.pc[i]] = b.pa[i];
+        grid.sync();
         // (6) the touched cells still out of bounds are the next sources
-        for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        for (int i = tid; i < np; i += nth) {
             double a = alpha[b.pc[i]];
             if (is_exc(a) || is_def(a)) {
-                int pos = atomicAdd(&s_next, 1);
+                int pos = atomicAdd((int *)&gc[1], 1);
                 if (pos < b.cap) nxt[pos] = b.pc[i];
                 else atomicOr(status, VOF_ST_CAPACITY);
             }
         }
-        __syncthreads();
-        if (threadIdx.x == 0) { s_n = min(s_next, b.cap); s_next = 0; s_pend = 0; }
+        grid.sync();
+        if (tid == 0) { gc[0] = min(gc[1], b.cap); gc[1] = 0; gc[2] = 0; }
         int *t = src; src = nxt; nxt = t;
-        __syncthreads();
+        grid.sync();
     }
-    if (threadIdx.x == 0) *b.left = s_n;
+    if (tid == 0) *b.left = gc[0];
 }
 
 // Global step for what the local passes leave: the total excess (deficit) goes
@@ -1158,12 +1209,21 @@ int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, ui
                        const int *list, const int *count, cudaStream_t s)
 {
     int sms = num_sms(c->device);
+    const bool mx = c->precision == VOF_MIXED;
     if (list) {
-        k_reconstruct<true><<<sms * 8, 256, 0, s>>>(c->m, alpha, list, count, n, d, flags, iters,
-                                                    c->counters + CNT_MAXPOS, c->status);
+        if (mx)
+            k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(c->m, alpha, list, count, n, d, flags, iters,
+                                                              c->counters + CNT_MAXPOS, c->status);
+        else
+            k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(c->m, alpha, list, count, n, d, flags, iters,
+                                                               c->counters + CNT_MAXPOS, c->status);
     } else {
-        k_reconstruct<false><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(c->m, alpha, nullptr, nullptr, n, d, flags,
-                                                                         iters, nullptr, c->status);
+        if (mx)
+            k_reconstruct<false, true><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
+                c->m, alpha, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
+        else
+            k_reconstruct<false, false><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
+                c->m, alpha, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
     }
     LAUNCH_CHECK();
     return VOF_OK;
@@ -1200,8 +1260,17 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
 static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches)
 {
     BoundBufs b{c->viol[0], c->viol[1], c->counters + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, c->dgi,
-                c->counters + CNT_VIOL1, c->nc, 8 * c->nc};
-    k_bound_local<<<1, BOUND_THREADS, 0, s>>>(c->m, alpha, b, c->status);
+                c->counters + CNT_VIOL1, c->nc, 8 * c->nc, c->counters + 12};
+    static int coop_blocks = 0;
+    if (coop_blocks == 0) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bound_local, BOUND_THREADS, 0);
+        coop_blocks = num_sms(c->device) * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
+    }
+    DevMesh mm = c->m;
+    void *args[] = {&mm, &alpha, &b, &c->status};
+    if (cudaLaunchCooperativeKernel((void *)k_bound_local, coop_blocks, BOUND_THREADS, args, 0, s) != cudaSuccess)
+        return VOF_ERR_CUDA;
     k_bound_global_reduce<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial);
     k_bound_global_apply<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial,
                                                           c->status);
@@ -1251,8 +1320,12 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     launches += 3;
     LAUNCH_CHECK();
     MARK(1);
-    k_reconstruct<true><<<sms * 8, 256, 0, s>>>(m, alpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
-                                                cnt + CNT_MAXPOS, c->status);
+    if (c->precision == VOF_MIXED)
+        k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(m, alpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags,
+                                                          nullptr, cnt + CNT_MAXPOS, c->status);
+    else
+        k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(m, alpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags,
+                                                           nullptr, cnt + CNT_MAXPOS, c->status);
     MARK(2);
     k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);

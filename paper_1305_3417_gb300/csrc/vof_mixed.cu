@@ -157,15 +157,89 @@ struct MXArgs {
     const int *cfpptr;
 };
 
+constexpr int MX_CAND = 32;                 // candidate cell tetrahedra buffered per warp
+constexpr int MX_QUEUE = MX_MAXT * MX_CAND;  // clip jobs: one per (T, K) pair at most
+
+struct MXShared {
+    FTet T[MX_MAXT];
+    float Tb[MX_MAXT][6];
+    float Tv6[MX_MAXT];      // |6 vol(T)|
+    float Tsg[MX_MAXT];      // sign of T in the flux polyhedron
+    float4 Kp[MX_CAND][4];   // outward planes of the candidate cell tetrahedra
+    float Kb[MX_CAND][6];
+    float4 KH[MX_CAND];      // the cell's phase (or void) half-space
+    float Kw[MX_CAND];       // weight: 1, or alpha (1-alpha) of an unoriented cell
+    unsigned char KuseH[MX_CAND];
+    unsigned Q[MX_QUEUE];    // clip jobs: t | k << 5 | plane mask << 10
+};
+
+// all (T, K) pairs of the buffered candidates: boxes and planes first; a pair
+// inside every plane adds |T| at once, a pair that must be cut goes to the
+// queue; then the lanes take the queued cuts
+__device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float &accs, float &accc,
+                                         unsigned &npairs, unsigned &ncuts, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int npr = nt * ncand;
+    int nq = 0;
+    for (int base = 0; base < npr; base += 32) {
+        const int w = base + lane;
+        bool job = false;
+        unsigned code = 0;
+        if (w < npr) {
+            const int t = w % nt, k = w / nt;
+            const float sg = sh.Tsg[t];
+            const float *tb = sh.Tb[t], *kb = sh.Kb[k];
+            if (sg != 0.0f && !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] ||
+                                tb[5] < kb[2] || kb[5] < tb[2])) {
+                ++npairs;
+                const FTet &T = sh.T[t];
+                unsigned mask = 0;
+                bool outside = false;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    float4 p;
+                    if (q < 4) p = sh.Kp[k][q];
+                    else if (sh.KuseH[k]) p = sh.KH[k];
+                    else break;
+                    int nin = 0;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) nin += p.x * T.v[i].x + p.y * T.v[i].y + p.z * T.v[i].z - p.w <= 0.0f;
+                    if (nin == 0) { outside = true; break; }
+                    if (nin < 4) mask |= 1u << q;
+                }
+                if (!outside) {
+                    if (mask == 0) two_sum(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
+                    else { job = true; code = (unsigned)t | ((unsigned)k << 5) | (mask << 10); }
+                }
+            }
+        }
+        const unsigned bm = __ballot_sync(0xffffffffu, job);
+        if (job) sh.Q[nq + __popc(bm & ((1u << lane) - 1u))] = code;
+        nq += __popc(bm);
+    }
+    __syncwarp();
+    for (int q = lane; q < nq; q += 32) {
+        const unsigned code = sh.Q[q];
+        const int t = code & 31, k = (code >> 5) & 31;
+        const unsigned mask = code >> 10;
+        float4 act[5];
+        int np = 0;
+#pragma unroll
+        for (int j = 0; j < 5; ++j)
+            if (mask & (1u << j)) act[np++] = j < 4 ? sh.Kp[k][j] : sh.KH[k];
+        float v6 = fclip6(sh.T[t], act, np, status, ncuts);
+        two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * v6);
+    }
+    __syncwarp();
+}
+
 template <bool LIST>
 __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, MXArgs a)
 {
-    __shared__ FTet sT[MX_WARPS][MX_MAXT];
-    __shared__ float sSg[MX_WARPS][MX_MAXT];
-    __shared__ float sTb[MX_WARPS][MX_MAXT][6];
-    __shared__ float4 sKp[MX_WARPS][32][4];
-    __shared__ float sKb[MX_WARPS][32][6];
+    __shared__ MXShared shm[MX_WARPS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    MXShared &sh = shm[wib];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int total = LIST ? *a.count : m.nf;
@@ -199,10 +273,10 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         // pieces and take V_alpha = F dt - void (equal in exact arithmetic since
         // the corrected polyhedron holds F dt and the stencil covers it); a
         // polyhedron inside full cells then carries exactly F dt, one inside
-        // empty cells exactly 0, and FP32 rounding stays with mixed cells.
+        // empty cells exactly 0, and FP32 rounding stays with mixed cells
+        // (not for the normal-sweep fallback, which can leave the domain at walls).
         const double Ff = a.F[f];
         const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
-        // (not for the normal-sweep fallback, which can leave the domain at walls)
         const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
         const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0;
         const int nt = n == 3 ? 3 : 3 * n;
@@ -251,16 +325,18 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
             if (j == 0) T = FTet{{a0, a1, a2, b2}};
             else if (j == 1) T = FTet{{a0, a1, b2, b1}};
             else T = FTet{{a0, b0, b1, b2}};
-            float sv = -par * fvol6(T.v[0], T.v[1], T.v[2], T.v[3]);
-            sT[wib][lane] = T;
-            sSg[wib][lane] = sv > 0.0f ? 1.0f : (sv < 0.0f ? -1.0f : 0.0f);
+            float v6 = fvol6(T.v[0], T.v[1], T.v[2], T.v[3]);
+            float sv = -par * v6;
+            sh.T[lane] = T;
+            sh.Tsg[lane] = sv > 0.0f ? 1.0f : (sv < 0.0f ? -1.0f : 0.0f);
+            sh.Tv6[lane] = fabsf(v6);
             bx[0] = fminf(fminf(T.v[0].x, T.v[1].x), fminf(T.v[2].x, T.v[3].x));
             bx[1] = fminf(fminf(T.v[0].y, T.v[1].y), fminf(T.v[2].y, T.v[3].y));
             bx[2] = fminf(fminf(T.v[0].z, T.v[1].z), fminf(T.v[2].z, T.v[3].z));
             bx[3] = fmaxf(fmaxf(T.v[0].x, T.v[1].x), fmaxf(T.v[2].x, T.v[3].x));
             bx[4] = fmaxf(fmaxf(T.v[0].y, T.v[1].y), fmaxf(T.v[2].y, T.v[3].y));
             bx[5] = fmaxf(fmaxf(T.v[0].z, T.v[1].z), fmaxf(T.v[2].z, T.v[3].z));
-            for (int i = 0; i < 6; ++i) sTb[wib][lane][i] = bx[i];
+            for (int i = 0; i < 6; ++i) sh.Tb[lane][i] = bx[i];
         }
         // bounding box of the whole polyhedron
         float pb[6];
@@ -277,6 +353,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         __syncwarp();
         float accs = 0.0f, accc = 0.0f;
         unsigned npairs = 0, ncuts = 0;
+        int ncand = 0;
         for (int s = s0; s < s1; ++s) {
             const int c = __ldg(m.scell + s);
             const double al = a.alpha[c];
@@ -301,11 +378,10 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
                     useH = true;
                 } else wgt = comp ? (float)(1.0 - al) : (float)al;
             }
-            // ---- this cell's tetrahedra, 32 at a time; lanes build, then pair
+            // ---- this cell's tetrahedra, 32 at a time, into the candidate buffer
             const int f0 = __ldg(m.cptr + c), f1 = __ldg(m.cptr + c + 1);
             const int cpb = __ldg(a.cfpptr + c);
             for (int kb = 0;; kb += 32) {
-                // locate tetrahedron kb + lane
                 int off = kb + lane, k = f0, code = 0, gn = 0, pofs = cpb;
                 bool found = false;
                 for (; k < f1; ++k) {
@@ -317,8 +393,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
                     off -= gt;
                     pofs += gn;
                 }
-                const bool any = __any_sync(0xffffffffu, found);
-                if (!any) break;
+                if (!__any_sync(0xffffffffu, found)) break;
                 bool cand = false;
                 float4 kp[4];
                 float kbx[6];
@@ -347,51 +422,23 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
                     }
                 }
                 const unsigned cmask = __ballot_sync(0xffffffffu, cand);
-                if (cand) {  // compact the candidates to the front
-                    int r = __popc(cmask & ((1u << lane) - 1u));
-                    for (int q = 0; q < 4; ++q) sKp[wib][r][q] = kp[q];
-                    for (int q = 0; q < 6; ++q) sKb[wib][r][q] = kbx[q];
+                if (ncand + __popc(cmask) > MX_CAND) {  // buffer full: process it first
+                    mx_flush(sh, nt, ncand, accs, accc, npairs, ncuts, a.status);
+                    ncand = 0;
                 }
-                __syncwarp();
-                const int ncand = __popc(cmask);
-                // (T, K) pairs over the lanes
-                for (int w = lane; w < nt * ncand; w += 32) {
-                    const int t = w % nt;
-                    const float sg = sSg[wib][t];
-                    if (sg == 0.0f) continue;
-                    const int kk = w / nt;
-                    const float *tb = sTb[wib][t], *kb2 = sKb[wib][kk];
-                    if (tb[3] < kb2[0] || kb2[3] < tb[0] || tb[4] < kb2[1] || kb2[4] < tb[1] || tb[5] < kb2[2] ||
-                        kb2[5] < tb[2])
-                        continue;
-                    ++npairs;
-                    const FTet &T = sT[wib][t];
-                    float4 act[5];
-                    int np = 0;
-                    bool outside = false;
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        float4 p = sKp[wib][kk][q];
-                        int nin = 0;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) nin += p.x * T.v[i].x + p.y * T.v[i].y + p.z * T.v[i].z - p.w <= 0.0f;
-                        if (nin == 0) { outside = true; break; }
-                        if (nin < 4) act[np++] = p;
-                    }
-                    if (outside) continue;
-                    if (useH) {
-                        int nin = 0;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) nin += H.x * T.v[i].x + H.y * T.v[i].y + H.z * T.v[i].z - H.w <= 0.0f;
-                        if (nin == 0) continue;
-                        if (nin < 4) act[np++] = H;
-                    }
-                    float v6 = fclip6(T, act, np, a.status, ncuts);
-                    two_sum(accs, accc, sg * wgt * v6);
+                if (cand) {
+                    int r = ncand + __popc(cmask & ((1u << lane) - 1u));
+                    for (int q = 0; q < 4; ++q) sh.Kp[r][q] = kp[q];
+                    for (int q = 0; q < 6; ++q) sh.Kb[r][q] = kbx[q];
+                    sh.KH[r] = H;
+                    sh.Kw[r] = wgt;
+                    sh.KuseH[r] = useH;
                 }
+                ncand += __popc(cmask);
                 __syncwarp();
             }
         }
+        if (ncand > 0) mx_flush(sh, nt, ncand, accs, accc, npairs, ncuts, a.status);
         // finish in FP64: lane sums and compensations, then the 1/6 of the volumes
         double acc = warp_sum((double)accs + (double)accc) / 6.0;
         if (comp) acc = Ff * a.dt - acc;

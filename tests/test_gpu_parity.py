@@ -87,9 +87,10 @@ def test_point_velocity(torch, O, name):
     assert np.abs(Up - oUp).max() < 1e-14 * max(np.abs(oUp).max(), 1e-300)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("name", list(WORKLOADS))
-def test_reconstruct(torch, O, name):
-    w, ctx, om = contexts(torch, O, name)
+def test_reconstruct(torch, O, name, precision):
+    w, ctx, om = contexts(torch, O, name, precision=precision)
     a = w.alpha0
     n, d, fl, it = (H(x) for x in ctx.reconstruct(T(torch, a)))
     n = n.reshape(3, -1)
