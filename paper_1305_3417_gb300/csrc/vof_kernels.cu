@@ -277,8 +277,11 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
 #pragma unroll
                         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
                         gx = (double)(part / Vf) - a;
-                        if (fabs(gx) <= 1e-5) fp32 = false;  // near the root: FP64 from here
-                    } else {
+                        // near the root the FP32 sign is not reliable: this iterate
+                        // and all later ones are evaluated in FP64
+                        if (fabs(gx) <= 1e-5) fp32 = false;
+                    }
+                    if (!(MIXED && fp32)) {
                         double part = 0.0;
 #pragma unroll
                         for (int s = 0; s < VOF_MAXK_LANE; ++s)
