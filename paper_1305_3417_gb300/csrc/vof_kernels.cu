@@ -232,6 +232,8 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                 for (int s = 0; s < VOF_MAXK_LANE; ++s) {
                     vk[s] = 0.0;
                     h[s][0] = h[s][1] = h[s][2] = h[s][3] = 0.0;
+                    vkf[s] = 0.0f;
+                    hf[s][0] = hf[s][1] = hf[s][2] = hf[s][3] = 0.0f;
                     int off = lane + 32 * s, k = f0, code = 0, nt = 0;
                     bool found = false;
                     for (; k < f1; ++k) {
