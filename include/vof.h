@@ -90,7 +90,8 @@ typedef struct {
 enum {
     VOF_S_MASS_BEFORE = 0, VOF_S_MASS_AFTER, VOF_S_MIN_PRE, VOF_S_MAX_PRE, VOF_S_MIN_POST,
     VOF_S_MAX_POST, VOF_S_N_INTERFACE, VOF_S_N_BAND, VOF_S_MAX_POS_IT, VOF_S_MAX_CORR_IT,
-    VOF_S_BOUNDARY_OUT, VOF_S_N_FALLBACK, VOF_S_N_BOUND_SOURCES, VOF_S_N_BOUND_LEFT, VOF_S_LEN = 16
+    VOF_S_BOUNDARY_OUT, VOF_S_N_FALLBACK, VOF_S_N_BOUND_SOURCES, VOF_S_N_BOUND_LEFT /* after the local pass */,
+    VOF_S_LEN = 16
 };
 
 typedef struct vof_ctx vof_ctx;

@@ -903,13 +903,13 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 }
 
 /* ---------------------------------------------------------- A7: update */
-#define BOUND_PASSES 4
+#define BOUND_PASSES 1
 #define BOUND_TOL 1e-13   /* excursions this small (round-off) are left alone and never
                            * decide a redistribution; the target is 1e-12 */
 #define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
 
-/* Reading R10: a conservative bounding pass, repeated until no cell is out of
- * [0,1] by more than BOUND_TOL (at most BOUND_PASSES times).  Every cell has
+/* Reading R10: a conservative local bounding pass (BOUND_PASSES of them) for
+ * cells out of [0,1] by more than BOUND_TOL, then the global step below.  Every cell has
  * room for excess, (1-alpha)V, and for deficit, alpha V (zero outside [0,1]).
  * A source with excess e above 1 requests from each face neighbour r the share
  * e room_r / sum(room) of the room around it; a receiver whose requests exceed

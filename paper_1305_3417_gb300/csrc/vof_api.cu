@@ -315,7 +315,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->Va = dev_alloc<double>(c, nf, &err);
     c->bscr = dev_alloc<double>(c, 8 * (size_t)nc, &err);
     c->dgi = dev_alloc<int>(c, nc, &err);
-    c->gpartial = dev_alloc<double>(c, 4 * 512, &err);
+    c->gpartial = dev_alloc<double>(c, 4 * 512 + 8, &err);
     c->partial = dev_alloc<double>(c, 10 * 1024, &err);
     c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
     c->status = dev_alloc<unsigned>(c, 1, &err);

@@ -22,7 +22,7 @@ constexpr double CORR_LMAX = 2.0;
 constexpr int CORR_NSAMP = 16;
 constexpr double BOUND_TOL = 1e-13;
 constexpr double BOUND_FLAG = 1e-12;
-constexpr int BOUND_PASSES = 4;
+constexpr int BOUND_PASSES = 1;  // local passes before the global step
 constexpr int CLIP_STACK = 12;
 constexpr int DISP_STRIDE = (VOF_MAXFP + 1) * 3;
 

@@ -7,8 +7,6 @@
 #include <math.h>
 #include <stdint.h>
 
-#include <cooperative_groups.h>
-
 #include "vof_internal.h"
 #include "vof_device.cuh"
 
@@ -905,7 +903,6 @@ struct BoundBufs {
     int *gc;             // grid-shared counters [3]
 };
 
-constexpr int BOUND_THREADS = 256;
 
 // lowest-index source among x's face neighbours (and x itself if self)
 __device__ __forceinline__ int first_source(const DevMesh &m, const double *alpha, int x, bool self)
@@ -924,179 +921,174 @@ __device__ __forceinline__ int first_source(const DevMesh &m, const double *alph
     return first;
 }
 
-// Cooperative launch: the grid runs the passes together, with grid-wide
-// barriers between the phases (counters gc: [0] sources, [1] next, [2] pending)
-__global__ void __launch_bounds__(BOUND_THREADS) k_bound_local(DevMesh m, double *alpha, BoundBufs b,
-                                                               unsigned *status)
+// The local pass as five grid kernels over the source list (count on the
+// device): room, receiver scales, placement, new values, apply.
+__global__ void k_bp_room(DevMesh m, const double *alpha, BoundBufs b)
 {
-    namespace cg = cooperative_groups;
-    cg::grid_group grid = cg::this_grid();
-    volatile int *gc = b.gc;
-    const int tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
-    if (tid == 0) { gc[0] = min(*b.n0, b.cap); gc[1] = 0; gc[2] = 0; }
-    grid.sync();
-    int *src = b.la, *nxt = b.lb;
+    const int n = min(*b.n0, b.cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = b.la[i];
+        double Cp = 0.0, Cm = 0.0;
+        int dg = 0;
+        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+            int nb = nbr_of(m, c, k);
+            if (nb < 0) continue;
+            double an = alpha[nb], Vn = m.vc[nb];
+            Cp += room_exc(an, Vn);
+            Cm += room_def(an, Vn);
+            ++dg;
+        }
+        b.bs[BS_N * (size_t)c + BS_CP] = Cp;
+        b.bs[BS_N * (size_t)c + BS_CM] = Cm;
+        b.dg[c] = dg;
+    }
+}
+
+__global__ void k_bp_scale(DevMesh m, const double *alpha, BoundBufs b)
+{
+    const int n = min(*b.n0, b.cap);
     double *bs = b.bs;
-    for (int pass = 0; pass < BOUND_PASSES; ++pass) {
-        const int n = gc[0];
-        if (n == 0) break;
-        // (1) room around each source
-        for (int i = tid; i < n; i += nth) {
-            int c = src[i];
-            double Cp = 0.0, Cm = 0.0;
-            int dg = 0;
-            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-                int nb = nbr_of(m, c, k);
-                if (nb < 0) continue;
-                double an = alpha[nb], Vn = m.vc[nb];
-                Cp += room_exc(an, Vn);
-                Cm += room_def(an, Vn);
-                ++dg;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = b.la[i];
+        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+            int r = nbr_of(m, c, k);
+            if (r < 0 || first_source(m, alpha, r, false) != c) continue;
+            double ar = alpha[r], Vr = m.vc[r], Rp = room_exc(ar, Vr), Rm = room_def(ar, Vr);
+            double Qp = 0.0, Qm = 0.0;
+            for (int q = m.cptr[r]; q < m.cptr[r + 1]; ++q) {
+                int s = nbr_of(m, r, q);
+                if (s < 0) continue;
+                double as = alpha[s], Vs = m.vc[s];
+                double Cps = bs[BS_N * (size_t)s + BS_CP], Cms = bs[BS_N * (size_t)s + BS_CM];
+                if (is_exc(as) && Cps > 0.0) Qp += (as - 1.0) * Vs * (Rp / Cps);
+                if (is_def(as) && Cms > 0.0) Qm += -as * Vs * (Rm / Cms);
             }
-            bs[BS_N * (size_t)c + BS_CP] = Cp;
-            bs[BS_N * (size_t)c + BS_CM] = Cm;
-            b.dg[c] = dg;
+            bs[BS_N * (size_t)r + BS_SP] = Qp > Rp ? Rp / Qp : 1.0;
+            bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
         }
-        grid.sync();
-        // (2) scale of each receiver (by its lowest-index neighbouring source)
-        for (int i = tid; i < n; i += nth) {
-            int c = src[i];
-            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-                int r = nbr_of(m, c, k);
-                if (r < 0 || first_source(m, alpha, r, false) != c) continue;
-                double ar = alpha[r], Vr = m.vc[r], Rp = room_exc(ar, Vr), Rm = room_def(ar, Vr);
-                double Qp = 0.0, Qm = 0.0;
-                for (int q = m.cptr[r]; q < m.cptr[r + 1]; ++q) {
-                    int s = nbr_of(m, r, q);
-                    if (s < 0) continue;
-                    double as = alpha[s], Vs = m.vc[s];
-                    double Cps = bs[BS_N * (size_t)s + BS_CP], Cms = bs[BS_N * (size_t)s + BS_CM];
-                    if (is_exc(as) && Cps > 0.0) Qp += (as - 1.0) * Vs * (Rp / Cps);
-                    if (is_def(as) && Cms > 0.0) Qm += -as * Vs * (Rm / Cms);
+    }
+}
+
+__global__ void k_bp_place(DevMesh m, const double *alpha, BoundBufs b)
+{
+    const int n = min(*b.n0, b.cap);
+    double *bs = b.bs;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = b.la[i];
+        double a = alpha[c], V = m.vc[c];
+        double *q = bs + BS_N * (size_t)c;
+        double gp = 0.0, gm = 0.0, e = is_exc(a) ? (a - 1.0) * V : 0.0, u = is_def(a) ? -a * V : 0.0;
+        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+            int nb = nbr_of(m, c, k);
+            if (nb < 0) continue;
+            double an = alpha[nb], Vn = m.vc[nb];
+            if (e > 0.0 && q[BS_CP] > 0.0) gp += e * (room_exc(an, Vn) / q[BS_CP]) * bs[BS_N * (size_t)nb + BS_SP];
+            if (u > 0.0 && q[BS_CM] > 0.0) gm += u * (room_def(an, Vn) / q[BS_CM]) * bs[BS_N * (size_t)nb + BS_SM];
+        }
+        int dg = b.dg[c];
+        q[BS_RP] = (e > 0.0 && dg > 0) ? e - gp : 0.0;
+        q[BS_RM] = (u > 0.0 && dg > 0) ? u - gm : 0.0;
+        q[BS_REL] = e > 0.0 ? (dg > 0 ? e : gp) : (dg > 0 ? u : gm);
+    }
+}
+
+// new values of the sources and their neighbours, each cell once: by the
+// lowest-index source in its closed face neighbourhood
+__global__ void k_bp_new(DevMesh m, const double *alpha, BoundBufs b, int *npend, unsigned *status)
+{
+    const int n = min(*b.n0, b.cap);
+    const double *bs = b.bs;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        int c = b.la[i];
+        for (int k = m.cptr[c] - 1; k < m.cptr[c + 1]; ++k) {
+            int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
+            if (x < 0 || first_source(m, alpha, x, true) != c) continue;
+            double ax = alpha[x], V = m.vc[x];
+            bool xe = is_exc(ax), xd = is_def(ax);
+            double Rp = room_exc(ax, V), Rm = room_def(ax, V);
+            double dV = 0.0;
+            if (xe) dV -= bs[BS_N * (size_t)x + BS_REL];
+            if (xd) dV += bs[BS_N * (size_t)x + BS_REL];
+            for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
+                int s = nbr_of(m, x, q);
+                if (s < 0) continue;
+                double as = alpha[s], Vs = m.vc[s];
+                const double *bq = bs + BS_N * (size_t)s;
+                int dgs = b.dg[s];
+                if (is_exc(as)) {
+                    if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp / bq[BS_CP]) * bs[BS_N * (size_t)x + BS_SP];
+                    if (dgs > 0) dV += bq[BS_RP] / dgs;
                 }
-                bs[BS_N * (size_t)r + BS_SP] = Qp > Rp ? Rp / Qp : 1.0;
-                bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
-            }
-        }
-        grid.sync();
-        // (3) what each source placed, the rest it pushes on, what it releases
-        for (int i = tid; i < n; i += nth) {
-            int c = src[i];
-            double a = alpha[c], V = m.vc[c];
-            double *q = bs + BS_N * (size_t)c;
-            double gp = 0.0, gm = 0.0, e = is_exc(a) ? (a - 1.0) * V : 0.0, u = is_def(a) ? -a * V : 0.0;
-            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-                int nb = nbr_of(m, c, k);
-                if (nb < 0) continue;
-                double an = alpha[nb], Vn = m.vc[nb];
-                if (e > 0.0 && q[BS_CP] > 0.0) gp += e * (room_exc(an, Vn) / q[BS_CP]) * bs[BS_N * (size_t)nb + BS_SP];
-                if (u > 0.0 && q[BS_CM] > 0.0) gm += u * (room_def(an, Vn) / q[BS_CM]) * bs[BS_N * (size_t)nb + BS_SM];
-            }
-            int dg = b.dg[c];
-            q[BS_RP] = (e > 0.0 && dg > 0) ? e - gp : 0.0;
-            q[BS_RM] = (u > 0.0 && dg > 0) ? u - gm : 0.0;
-            q[BS_REL] = e > 0.0 ? (dg > 0 ? e : gp) : (dg > 0 ? u : gm);
-        }
-        grid.sync();
-        // (4) new values of the sources and their neighbours, each cell once:
-        //     by the lowest-index source in its closed face neighbourhood
-        for (int i = tid; i < n; i += nth) {
-            int c = src[i];
-            for (int k = m.cptr[c] - 1; k < m.cptr[c + 1]; ++k) {
-                int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
-                if (x < 0 || first_source(m, alpha, x, true) != c) continue;
-                double ax = alpha[x], V = m.vc[x];
-                bool xe = is_exc(ax), xd = is_def(ax);
-                double Rp = room_exc(ax, V), Rm = room_def(ax, V);
-                double dV = 0.0;
-                if (xe) dV -= bs[BS_N * (size_t)x + BS_REL];
-                if (xd) dV += bs[BS_N * (size_t)x + BS_REL];
-                for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
-                    int s = nbr_of(m, x, q);
-                    if (s < 0) continue;
-                    double as = alpha[s], Vs = m.vc[s];
-                    const double *bq = bs + BS_N * (size_t)s;
-                    int dgs = b.dg[s];
-                    if (is_exc(as)) {
-                        if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp / bq[BS_CP]) * bs[BS_N * (size_t)x + BS_SP];
-                        if (dgs > 0) dV += bq[BS_RP] / dgs;
-                    }
-                    if (is_def(as)) {
-                        if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm / bq[BS_CM]) * bs[BS_N * (size_t)x + BS_SM];
-                        if (dgs > 0) dV -= bq[BS_RM] / dgs;
-                    }
-                }
-                // sources always go to the pending list (a source that could not
-                // move keeps its value and stays a source next pass)
-                if (dV != 0.0 || xe || xd) {
-                    int pos = atomicAdd((int *)&gc[2], 1);
-                    if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = dV != 0.0 ? (ax * V + dV) / V : ax; }
-                    else atomicOr(status, VOF_ST_CAPACITY);
+                if (is_def(as)) {
+                    if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm / bq[BS_CM]) * bs[BS_N * (size_t)x + BS_SM];
+                    if (dgs > 0) dV -= bq[BS_RM] / dgs;
                 }
             }
-        }
-        grid.sync();
-        // (5) apply
-        const int np = min(gc[2], b.cap_pend);
-        for (int i = tid; i < np; i += nth) alpha[b.pc[i]] = b.pa[i];
-        grid.sync();
-        // (6) the touched cells still out of bounds are the next sources
-        for (int i = tid; i < np; i += nth) {
-            double a = alpha[b.pc[i]];
-            if (is_exc(a) || is_def(a)) {
-                int pos = atomicAdd((int *)&gc[1], 1);
-                if (pos < b.cap) nxt[pos] = b.pc[i];
+            if (dV != 0.0) {
+                int pos = atomicAdd(npend, 1);
+                if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = (ax * V + dV) / V; }
                 else atomicOr(status, VOF_ST_CAPACITY);
             }
         }
-        grid.sync();
-        if (tid == 0) { gc[0] = min(gc[1], b.cap); gc[1] = 0; gc[2] = 0; }
-        int *t = src; src = nxt; nxt = t;
-        grid.sync();
     }
-    if (tid == 0) *b.left = gc[0];
 }
 
-// Global step for what the local passes leave: the total excess (deficit) goes
+__global__ void k_bp_apply(double *alpha, const int *pc, const double *pa, const int *npend, int cap)
+{
+    const int n = min(*npend, cap);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alpha[pc[i]] = pa[i];
+}
+
+// Global step for what the local pass leaves: the total excess (deficit) goes
 // to every cell strictly inside (tol, 1-tol) in proportion to its free (phase)
-// volume; sources are set to 1 (0).  Both kernels return at once when nothing
-// is left.  Partial sums per block, reduced in a fixed order.
+// volume; sources are set to 1 (0).  Partial sums per block; the last block to
+// finish reduces them in block order (deterministic) into totals[4].
 constexpr int GB_BLOCKS = 512, GB_THREADS = 256;
 
 __global__ void __launch_bounds__(GB_THREADS) k_bound_global_reduce(DevMesh m, const double *alpha,
-                                                                    const int *left, double *partial)
+                                                                    double *partial, double *totals,
+                                                                    unsigned *done, int *nleft)
 {
-    if (*left == 0) return;
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // Ep, Em, Sp, Sm
+    int left = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
         double a = alpha[c], V = m.vc[c];
-        if (a > 1.0 + BOUND_TOL) v[0] += (a - 1.0) * V;
-        else if (a < -BOUND_TOL) v[1] += -a * V;
+        if (a > 1.0 + BOUND_TOL) { v[0] += (a - 1.0) * V; ++left; }
+        else if (a < -BOUND_TOL) { v[1] += -a * V; ++left; }
         else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) { v[2] += (1.0 - a) * V; v[3] += a * V; }
     }
+    if (left) atomicAdd(nleft, left);
     __shared__ double sh[4][GB_THREADS / 32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = 0; i < 4; ++i) {
         double x = warp_sum(v[i]);
         if (lane == 0) sh[i][w] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0)
+    if (threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i) {
             double r = 0.0;
             for (int k = 0; k < GB_THREADS / 32; ++k) r += sh[i][k];
             partial[4 * blockIdx.x + i] = r;
         }
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double t[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int k = 0; k < (int)gridDim.x; ++k)
+            for (int i = 0; i < 4; ++i) t[i] += ((volatile double *)partial)[4 * k + i];
+        for (int i = 0; i < 4; ++i) totals[i] = t[i];
+        *done = 0;
+    }
 }
 
-__global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, double *alpha, const int *left,
-                                                                   const double *partial, unsigned *status)
+__global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, double *alpha, const double *totals)
 {
-    if (*left == 0) return;
-    double Ep = 0.0, Em = 0.0, Sp = 0.0, Sm = 0.0;
-    for (int k = 0; k < GB_BLOCKS; ++k) {
-        Ep += partial[4 * k]; Em += partial[4 * k + 1]; Sp += partial[4 * k + 2]; Sm += partial[4 * k + 3];
-    }
+    const double Ep = totals[0], Em = totals[1], Sp = totals[2], Sm = totals[3];
     if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
         double a = alpha[c], V = m.vc[c];
@@ -1266,20 +1258,19 @@ static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches
 {
     BoundBufs b{c->viol[0], c->viol[1], c->counters + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, c->dgi,
                 c->counters + CNT_VIOL1, c->nc, 8 * c->nc, c->counters + 12};
-    static int coop_blocks = 0;
-    if (coop_blocks == 0) {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bound_local, BOUND_THREADS, 0);
-        coop_blocks = num_sms(c->device) * (per_sm < 2 ? (per_sm < 1 ? 1 : per_sm) : 2);
-    }
-    DevMesh mm = c->m;
-    void *args[] = {&mm, &alpha, &b, &c->status};
-    if (cudaLaunchCooperativeKernel((void *)k_bound_local, coop_blocks, BOUND_THREADS, args, 0, s) != cudaSuccess)
-        return VOF_ERR_CUDA;
-    k_bound_global_reduce<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial);
-    k_bound_global_apply<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->counters + CNT_VIOL1, c->gpartial,
-                                                          c->status);
-    *launches += 3;
+    const int g = num_sms(c->device) * 2;
+    int *npend = c->counters + CNT_PEND;
+    k_zero_int<<<1, 32, 0, s>>>(npend, 1);
+    k_bp_room<<<g, 128, 0, s>>>(c->m, alpha, b);
+    k_bp_scale<<<g, 128, 0, s>>>(c->m, alpha, b);
+    k_bp_place<<<g, 128, 0, s>>>(c->m, alpha, b);
+    k_bp_new<<<g, 128, 0, s>>>(c->m, alpha, b, npend, c->status);
+    k_bp_apply<<<g, 128, 0, s>>>(alpha, c->pend_c, c->pend_a, npend, b.cap_pend);
+    double *totals = c->gpartial + 4 * GB_BLOCKS;
+    k_bound_global_reduce<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->gpartial, totals,
+                                                           (unsigned *)(c->counters + 14), c->counters + CNT_VIOL1);
+    k_bound_global_apply<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, totals);
+    *launches += 8;
     LAUNCH_CHECK();
     return VOF_OK;
 }
