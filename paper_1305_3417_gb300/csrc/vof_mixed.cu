@@ -130,49 +130,6 @@ __device__ float fclip6(const FTet &T, const float4 *pl, int np, unsigned *statu
     return vol;
 }
 
-// Clipping by NP planes with the recursion unrolled at compile time: the
-// tetrahedra of each level stay in registers (no stack).  Plane j of the set is
-// P.p[K + j].
-struct Planes { float4 p[5]; };
-
-template <int NP, int K>
-__device__ __forceinline__ float fclipN(const FTet &t, const Planes &P, unsigned &cuts)
-{
-    const float4 p = P.p[K];
-    float s[4];
-    int nin = 0;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) { s[i] = p.x * t.v[i].x + p.y * t.v[i].y + p.z * t.v[i].z - p.w; nin += s[i] <= 0.0f; }
-    if (nin == 0) return 0.0f;
-    if (nin == 4) {
-        if constexpr (NP == 1) return fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
-        else return fclipN<NP - 1, K + 1>(t, P, cuts);
-    }
-    ++cuts;
-    if constexpr (NP == 1) {
-        float h0 = s[0], h1 = s[1], h2 = s[2], h3 = s[3];
-        fsort4(h0, h1, h2, h3);
-        return fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3])) * ffrac_below(h0, h1, h2, h3);
-    } else {
-        int ord[4], a = 0, b = 3;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { if (s[i] <= 0.0f) ord[a++] = i; else ord[b--] = i; }
-        F3 Q[4];
-        float S[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { Q[i] = t.v[ord[i]]; S[i] = s[ord[i]]; }
-        auto ep = [&](int i, int o) { return Q[i] + (Q[o] - Q[i]) * (S[i] / (S[i] - S[o])); };
-        if (nin == 1) return fclipN<NP - 1, K + 1>(FTet{{Q[0], ep(0, 1), ep(0, 2), ep(0, 3)}}, P, cuts);
-        F3 a0, a1, a2, b0, b1, b2;
-        if (nin == 2) { a0 = Q[0]; a1 = ep(0, 2); a2 = ep(0, 3); b0 = Q[1]; b1 = ep(1, 2); b2 = ep(1, 3); }
-        else { a0 = Q[0]; a1 = Q[1]; a2 = Q[2]; b0 = ep(0, 3); b1 = ep(1, 3); b2 = ep(2, 3); }
-        float v = fclipN<NP - 1, K + 1>(FTet{{a0, a1, a2, b2}}, P, cuts);
-        v += fclipN<NP - 1, K + 1>(FTet{{a0, a1, b2, b1}}, P, cuts);
-        v += fclipN<NP - 1, K + 1>(FTet{{a0, b0, b1, b2}}, P, cuts);
-        return v;
-    }
-}
-
 // TwoSum (Knuth): s + c carries the running sum exactly up to the last addend's
 // rounding; no multiplications, so no fused operation can change it
 __device__ __forceinline__ void two_sum(float &s, float &c, float x)
@@ -224,7 +181,7 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
 {
     const int lane = threadIdx.x & 31;
     const int npr = nt * ncand;
-    int n1 = 0, n2 = 0;
+    int nq = 0;
     for (int base = 0; base < npr; base += 32) {
         const int w = base + lane;
         bool job = false;
@@ -257,51 +214,28 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
                 }
             }
         }
-        // jobs grouped by their number of active planes: single-plane cuts
-        // (closed form) from the front, the rest from the back, so that a warp
-        // runs alike work; the two ends never meet (at most MX_QUEUE jobs)
-        const int pc = job ? __popc(code >> 10) : 0;
-        const unsigned b1 = __ballot_sync(0xffffffffu, pc == 1);
-        const unsigned b2 = __ballot_sync(0xffffffffu, pc >= 2);
-        const unsigned lt = (1u << lane) - 1u;
-        if (pc == 1) sh.Q[n1 + __popc(b1 & lt)] = code;
-        if (pc >= 2) sh.Q[MX_QUEUE - 1 - (n2 + __popc(b2 & lt))] = code;
-        n1 += __popc(b1);
-        n2 += __popc(b2);
+        const unsigned bm = __ballot_sync(0xffffffffu, job);
+        if (job) sh.Q[nq + __popc(bm & ((1u << lane) - 1u))] = code;
+        nq += __popc(bm);
     }
     __syncwarp();
-    auto planes_of = [&](unsigned code, Planes &P) {
-        const int k = (code >> 5) & 31;
+    for (int q = lane; q < nq; q += 32) {
+        const unsigned code = sh.Q[q];
+        const int t = code & 31, k = (code >> 5) & 31;
         const unsigned mask = code >> 10;
+        float4 act[5];
         int np = 0;
 #pragma unroll
         for (int j = 0; j < 5; ++j)
-            if (mask & (1u << j)) P.p[np++] = j < 4 ? sh.Kp[k][j] : sh.KH[k];
-        return np;
-    };
-    for (int q = lane; q < n1; q += 32) {
-        const unsigned code = sh.Q[q];
-        const int t = code & 31, k = (code >> 5) & 31;
-        Planes P;
-        planes_of(code, P);
-        two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * fclipN<1, 0>(sh.T[t], P, ncuts));
-    }
-    for (int q = lane; q < n2; q += 32) {
-        const unsigned code = sh.Q[MX_QUEUE - 1 - q];
-        const int t = code & 31, k = (code >> 5) & 31;
-        Planes P;
-        const int np = planes_of(code, P);
-        float v6;
-        if (np == 2) v6 = fclipN<2, 0>(sh.T[t], P, ncuts);
-        else if (np == 3) v6 = fclipN<3, 0>(sh.T[t], P, ncuts);
-        else v6 = fclip6(sh.T[t], P.p, np, status, ncuts);
+            if (mask & (1u << j)) act[np++] = j < 4 ? sh.Kp[k][j] : sh.KH[k];
+        float v6 = fclip6(sh.T[t], act, np, status, ncuts);
         two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * v6);
     }
     __syncwarp();
 }
 
 template <bool LIST>
-__global__ void __launch_bounds__(MX_WARPS * 32, 4) k_phase_flux_mixed(DevMesh m, MXArgs a)
+__global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, MXArgs a)
 {
     __shared__ MXShared shm[MX_WARPS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
