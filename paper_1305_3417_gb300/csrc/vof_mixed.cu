@@ -63,7 +63,7 @@ struct FTet { F3 v[4]; };
 
 // |T ^ {n_k.x <= d_k}| in FP32: depth-first split into the tetrahedra of the
 // inside parts, the last plane by the closed-form cut fraction (6x volume)
-__device__ float fclip6(const FTet &T, const float4 *pl, int np, unsigned *status, unsigned &cuts)
+__device__ float fclip6(const FTet &T, const float4 *pl, int np, float tol, unsigned *status, unsigned &cuts)
 {
     if (np == 0) return fabsf(fvol6(T.v[0], T.v[1], T.v[2], T.v[3]));
     FTet st[CLIP_STACK];
@@ -79,11 +79,16 @@ __device__ float fclip6(const FTet &T, const float4 *pl, int np, unsigned *statu
         float4 p = pl[k];
         F3 n = f3(p.x, p.y, p.z);
         float s[4];
-        int nin = 0;
+        int nin = 0, nup = 0;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { s[i] = fdot(n, t.v[i]) - p.w; nin += s[i] <= 0.0f; }
-        if (nin == 0) continue;
-        if (nin == 4) {
+        for (int i = 0; i < 4; ++i) {
+            s[i] = fdot(n, t.v[i]) - p.w;
+            if (fabsf(s[i]) <= tol) s[i] = 0.0f;  // on the plane (FP32 rounding of shared points)
+            nin += s[i] < 0.0f;
+            nup += s[i] > 0.0f;
+        }
+        if (nin == 0) continue;  // nothing strictly inside: no volume
+        if (nup == 0) {
             if (k + 1 == np) vol += fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
             else if (sp < CLIP_STACK) { st[sp] = t; lv[sp] = k + 1; ++sp; }
             else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
@@ -98,7 +103,7 @@ __device__ float fclip6(const FTet &T, const float4 *pl, int np, unsigned *statu
         }
         int ord[4], a = 0, b = 3;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) { if (s[i] <= 0.0f) ord[a++] = i; else ord[b--] = i; }
+        for (int i = 0; i < 4; ++i) { if (s[i] < 0.0f) ord[a++] = i; else ord[b--] = i; }
         F3 P[4];
         float S[4];
 #pragma unroll
@@ -176,7 +181,7 @@ struct MXShared {
 // all (T, K) pairs of the buffered candidates: boxes and planes first; a pair
 // inside every plane adds |T| at once, a pair that must be cut goes to the
 // queue; then the lanes take the queued cuts
-__device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float &accs, float &accc,
+__device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
                                          unsigned &npairs, unsigned &ncuts, unsigned *status)
 {
     const int lane = threadIdx.x & 31;
@@ -202,11 +207,18 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
                     if (q < 4) p = sh.Kp[k][q];
                     else if (sh.KuseH[k]) p = sh.KH[k];
                     else break;
-                    int nin = 0;
+                    // a vertex within tol of the plane is on it: the pair is outside
+                    // when no vertex is clearly inside, the plane cuts only when
+                    // vertices lie clearly on both sides
+                    int nneg = 0, npos = 0;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) nin += p.x * T.v[i].x + p.y * T.v[i].y + p.z * T.v[i].z - p.w <= 0.0f;
-                    if (nin == 0) { outside = true; break; }
-                    if (nin < 4) mask |= 1u << q;
+                    for (int i = 0; i < 4; ++i) {
+                        float sd = p.x * T.v[i].x + p.y * T.v[i].y + p.z * T.v[i].z - p.w;
+                        nneg += sd < -tol;
+                        npos += sd > tol;
+                    }
+                    if (nneg == 0) { outside = true; break; }
+                    if (npos > 0) mask |= 1u << q;
                 }
                 if (!outside) {
                     if (mask == 0) two_sum(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
@@ -228,7 +240,7 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
 #pragma unroll
         for (int j = 0; j < 5; ++j)
             if (mask & (1u << j)) act[np++] = j < 4 ? sh.Kp[k][j] : sh.KH[k];
-        float v6 = fclip6(sh.T[t], act, np, status, ncuts);
+        float v6 = fclip6(sh.T[t], act, np, tol, status, ncuts);
         two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * v6);
     }
     __syncwarp();
@@ -280,6 +292,10 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
         const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0;
         const int nt = n == 3 ? 3 : 3 * n;
+        // signed distances (to unit-normal planes) within 2e-6 of the face size are
+        // taken as zero: points shared by the polyhedron and the cell tetrahedra
+        // come out of different FP32 roundings and would otherwise look like cuts
+        const float tol = 2e-6f * (float)sqrt(sqrt(dot(ld3(m.sf, m.nf, f), ld3(m.sf, m.nf, f))));
         // ---- flux polyhedron tetrahedra in the face frame
         float bx[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
         if (lane < nt) {
@@ -415,6 +431,8 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
                     if (cand) {
                         F3 n0 = fcross(k2 - k0, k1 - k0), n1 = fcross(k1 - k0, k3 - k0);
                         F3 n2 = fcross(k3 - k0, k2 - k0), n3 = fcross(k2 - k1, k3 - k1);
+                        n0 = n0 * rsqrtf(fdot(n0, n0) + 1e-37f); n1 = n1 * rsqrtf(fdot(n1, n1) + 1e-37f);
+                        n2 = n2 * rsqrtf(fdot(n2, n2) + 1e-37f); n3 = n3 * rsqrtf(fdot(n3, n3) + 1e-37f);
                         kp[0] = make_float4(n0.x, n0.y, n0.z, fdot(n0, k0));
                         kp[1] = make_float4(n1.x, n1.y, n1.z, fdot(n1, k0));
                         kp[2] = make_float4(n2.x, n2.y, n2.z, fdot(n2, k0));
@@ -423,7 +441,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
                 }
                 const unsigned cmask = __ballot_sync(0xffffffffu, cand);
                 if (ncand + __popc(cmask) > MX_CAND) {  // buffer full: process it first
-                    mx_flush(sh, nt, ncand, accs, accc, npairs, ncuts, a.status);
+                    mx_flush(sh, nt, ncand, tol, accs, accc, npairs, ncuts, a.status);
                     ncand = 0;
                 }
                 if (cand) {
@@ -438,7 +456,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
                 __syncwarp();
             }
         }
-        if (ncand > 0) mx_flush(sh, nt, ncand, accs, accc, npairs, ncuts, a.status);
+        if (ncand > 0) mx_flush(sh, nt, ncand, tol, accs, accc, npairs, ncuts, a.status);
         // finish in FP64: lane sums and compensations, then the 1/6 of the volumes
         double acc = warp_sum((double)accs + (double)accc) / 6.0;
         if (comp) acc = Ff * a.dt - acc;
