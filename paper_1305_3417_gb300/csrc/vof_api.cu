@@ -255,6 +255,8 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         if (v > 0x7fffffffL) return VOF_ERR_BAD_MESH;
         cfpptr[c + 1] = (int)v;
     }
+    std::vector<int> ctptr(nc + 1, 0);
+    for (int c = 0; c < nc; ++c) ctptr[c + 1] = ctptr[c] + ktet[c];
 
     // ------------------------------------------------------------- device
     vof_ctx *c = new vof_ctx();
@@ -328,6 +330,10 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->cfpl = dev_alloc<float4>(c, cfpptr[nc], &err);
     c->fpl = dev_alloc<float4>(c, nfp, &err);
     c->cbl = dev_alloc<float4>(c, 2 * (size_t)nc, &err);
+    if (c->precision == VOF_MIXED) {
+        c->ctptr = dev_copy(c, ctptr.data(), ctptr.size(), &err);
+        c->ktl = dev_alloc<float4>(c, 6 * (size_t)ctptr[nc], &err);
+    }
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
     cudaMemset(c->bscr, 0, sizeof(double) * 8 * nc);

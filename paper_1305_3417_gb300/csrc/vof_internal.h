@@ -62,6 +62,10 @@ struct vof_ctx {
     // FP32 geometry for the mixed kernels
     float4 *cfl, *cfpl, *fpl, *cbl;
     int *cfpptr;
+    // per cell tetrahedron (mixed contexts): 4 outward unit-normal planes and the
+    // box, 6 float4, relative to the cell centre; ctptr: first of each cell
+    float4 *ktl;
+    int *ctptr;
     // kernel-group timing (vof_profile_begin / _end)
     cudaEvent_t *prof_ev;
     int prof_max, prof_steps;

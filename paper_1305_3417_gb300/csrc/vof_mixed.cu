@@ -61,80 +61,6 @@ __device__ __forceinline__ void fsort4(float &a, float &b, float &c, float &d)
 
 struct FTet { F3 v[4]; };
 
-// |T ^ {n_k.x <= d_k}| in FP32: depth-first split into the tetrahedra of the
-// inside parts, the last plane by the closed-form cut fraction (6x volume)
-__device__ float fclip6(const FTet &T, const float4 *pl, int np, float tol, unsigned *status, unsigned &cuts)
-{
-    if (np == 0) return fabsf(fvol6(T.v[0], T.v[1], T.v[2], T.v[3]));
-    FTet st[CLIP_STACK];
-    unsigned char lv[CLIP_STACK];
-    int sp = 1;
-    st[0] = T;
-    lv[0] = 0;
-    float vol = 0.0f;
-    while (sp > 0) {
-        --sp;
-        FTet t = st[sp];
-        int k = lv[sp];
-        float4 p = pl[k];
-        F3 n = f3(p.x, p.y, p.z);
-        float s[4];
-        int nin = 0, nup = 0;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            s[i] = fdot(n, t.v[i]) - p.w;
-            if (fabsf(s[i]) <= tol) s[i] = 0.0f;  // on the plane (FP32 rounding of shared points)
-            nin += s[i] < 0.0f;
-            nup += s[i] > 0.0f;
-        }
-        if (nin == 0) continue;  // nothing strictly inside: no volume
-        if (nup == 0) {
-            if (k + 1 == np) vol += fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
-            else if (sp < CLIP_STACK) { st[sp] = t; lv[sp] = k + 1; ++sp; }
-            else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
-            continue;
-        }
-        ++cuts;
-        if (k + 1 == np) {
-            float h0 = s[0], h1 = s[1], h2 = s[2], h3 = s[3];
-            fsort4(h0, h1, h2, h3);
-            vol += fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3])) * ffrac_below(h0, h1, h2, h3);
-            continue;
-        }
-        int ord[4], a = 0, b = 3;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { if (s[i] < 0.0f) ord[a++] = i; else ord[b--] = i; }
-        F3 P[4];
-        float S[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) { P[i] = t.v[ord[i]]; S[i] = s[ord[i]]; }
-        auto ep = [&](int i, int o) { return P[i] + (P[o] - P[i]) * (S[i] / (S[i] - S[o])); };
-        FTet out[3];
-        int nout;
-        if (nin == 1) {
-            out[0] = FTet{{P[0], ep(0, 1), ep(0, 2), ep(0, 3)}};
-            nout = 1;
-        } else if (nin == 2) {
-            F3 a0 = P[0], a1 = ep(0, 2), a2 = ep(0, 3), b0 = P[1], b1 = ep(1, 2), b2 = ep(1, 3);
-            out[0] = FTet{{a0, a1, a2, b2}};
-            out[1] = FTet{{a0, a1, b2, b1}};
-            out[2] = FTet{{a0, b0, b1, b2}};
-            nout = 3;
-        } else {
-            F3 a0 = P[0], a1 = P[1], a2 = P[2], b0 = ep(0, 3), b1 = ep(1, 3), b2 = ep(2, 3);
-            out[0] = FTet{{a0, a1, a2, b2}};
-            out[1] = FTet{{a0, a1, b2, b1}};
-            out[2] = FTet{{a0, b0, b1, b2}};
-            nout = 3;
-        }
-        for (int i = 0; i < nout; ++i) {
-            if (sp < CLIP_STACK) { st[sp] = out[i]; lv[sp] = k + 1; ++sp; }
-            else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
-        }
-    }
-    return vol;
-}
-
 // TwoSum (Knuth): s + c carries the running sum exactly up to the last addend's
 // rounding; no multiplications, so no fused operation can change it
 __device__ __forceinline__ void two_sum(float &s, float &c, float x)
@@ -145,8 +71,9 @@ __device__ __forceinline__ void two_sum(float &s, float &c, float x)
     s = t;
 }
 
-constexpr int MX_WARPS = 4;
+constexpr int MX_WARPS = 2;
 constexpr int MX_MAXT = 3 * VOF_MAXFP;
+static_assert(MX_MAXT <= 32, "one flux-polyhedron tetrahedron per lane");
 
 struct MXArgs {
     const double *alpha, *n, *d;
@@ -158,62 +85,238 @@ struct MXArgs {
     const double *disp, *lam_b;
     unsigned *status;
     unsigned long long *work;
-    const float4 *cfl, *cfpl, *fpl, *cbl;  // FP32 local geometry
-    const int *cfpptr;
+    const float4 *fpl, *cbl;  // FP32 face points (face frame), cell boxes (cell frame)
+    const float4 *ktl;        // cell tetrahedra: planes and box (cell frame)
+    const int *ctptr;
 };
 
-constexpr int MX_CAND = 32;                 // candidate cell tetrahedra buffered per warp
+constexpr int MX_CAND = 32;    // candidate cell tetrahedra buffered per warp: one per lane
 constexpr int MX_QUEUE = MX_MAXT * MX_CAND;  // clip jobs: one per (T, K) pair at most
+constexpr int MX_STACK = 96;                 // pieces of clip jobs waiting for their next plane
 
-struct MXShared {
-    FTet T[MX_MAXT];
+// per warp; the 48-byte tetrahedra are moved as three float4 (conflict-free
+// across a warp)
+struct __align__(16) MXShared {
+    FTet S[MX_STACK];        // pieces
+    FTet T[MX_MAXT];         // flux-polyhedron tetrahedra
+    float4 Kp[MX_CAND][4];   // outward unit-normal planes of the candidate cell tetrahedra
+    float4 KH[MX_CAND];      // the cell's phase (or void) half-space
     float Tb[MX_MAXT][6];
+    float Kb[MX_CAND][6];
     float Tv6[MX_MAXT];      // |6 vol(T)|
     float Tsg[MX_MAXT];      // sign of T in the flux polyhedron
-    float4 Kp[MX_CAND][4];   // outward planes of the candidate cell tetrahedra
-    float Kb[MX_CAND][6];
-    float4 KH[MX_CAND];      // the cell's phase (or void) half-space
     float Kw[MX_CAND];       // weight: 1, or alpha (1-alpha) of an unoriented cell
+    // stencil cells of the current chunk that reach the polyhedron's box
+    float4 CH[32];           // phase (or void) half-space
+    float Cdc[32][3];        // cell centre - face centre
+    float Cw[32];
+    int Ct0[32];             // first tetrahedron
+    int Cend[32];            // running count of tetrahedra, inclusive
+    unsigned short Sm[MX_STACK];  // piece: t | k << 5 | planes still to clip << 10
+    unsigned short Q[MX_QUEUE];   // clip job: t | k << 5 | plane mask << 10
     unsigned char KuseH[MX_CAND];
-    unsigned Q[MX_QUEUE];    // clip jobs: t | k << 5 | plane mask << 10
+    unsigned char CuseH[32];
 };
 
-// all (T, K) pairs of the buffered candidates: boxes and planes first; a pair
-// inside every plane adds |T| at once, a pair that must be cut goes to the
-// queue; then the lanes take the queued cuts
-__device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
-                                         unsigned &npairs, unsigned &ncuts, unsigned *status)
+__device__ __forceinline__ FTet ldT(const FTet &t)
+{
+    const float4 *p = reinterpret_cast<const float4 *>(&t);
+    const float4 a = p[0], b = p[1], c = p[2];
+    return FTet{{f3(a.x, a.y, a.z), f3(a.w, b.x, b.y), f3(b.z, b.w, c.x), f3(c.y, c.z, c.w)}};
+}
+
+__device__ __forceinline__ void stT(FTet &t, const FTet &v)
+{
+    float4 *p = reinterpret_cast<float4 *>(&t);
+    p[0] = make_float4(v.v[0].x, v.v[0].y, v.v[0].z, v.v[1].x);
+    p[1] = make_float4(v.v[1].y, v.v[1].z, v.v[2].x, v.v[2].y);
+    p[2] = make_float4(v.v[2].z, v.v[3].x, v.v[3].y, v.v[3].z);
+}
+
+// signed distances of the vertices to plane p, those within tol taken as 0;
+// nin / nup count the vertices strictly below / above
+__device__ __forceinline__ void fdist(const FTet &t, float4 p, float tol, float s[4], int &nin, int &nup)
+{
+    nin = 0;
+    nup = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float v = p.x * t.v[i].x + p.y * t.v[i].y + p.z * t.v[i].z - p.w;
+        if (fabsf(v) <= tol) v = 0.0f;
+        s[i] = v;
+        nin += v < 0.0f;
+        nup += v > 0.0f;
+    }
+}
+
+// the part of t below the plane (distances s, 1 <= nin <= 3 vertices strictly
+// below, at least one strictly above) as one tetrahedron (nin == 1) or three,
+// each handed to put(tet, i); vertices are ordered below-first by a
+// compare-exchange network so that every index stays static
+template <class Put>
+__device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin, Put put)
+{
+    F3 P0 = t.v[0], P1 = t.v[1], P2 = t.v[2], P3 = t.v[3];
+    float S0 = s[0], S1 = s[1], S2 = s[2], S3 = s[3];
+#define MX_CX(a, b)                                                   \
+    if (!(S##a < 0.0f) && S##b < 0.0f) {                              \
+        F3 tp = P##a; P##a = P##b; P##b = tp;                         \
+        float ts = S##a; S##a = S##b; S##b = ts;                      \
+    }
+    MX_CX(0, 1) MX_CX(2, 3) MX_CX(0, 2) MX_CX(1, 3) MX_CX(1, 2)
+#undef MX_CX
+    auto ep = [](F3 a, float sa, F3 b, float sb) { return a + (b - a) * (sa / (sa - sb)); };
+    if (nin == 1) {
+        put(FTet{{P0, ep(P0, S0, P1, S1), ep(P0, S0, P2, S2), ep(P0, S0, P3, S3)}}, 0);
+        return;
+    }
+    F3 a0, a1, a2, b0, b1, b2;
+    if (nin == 2) {
+        a0 = P0; a1 = ep(P0, S0, P2, S2); a2 = ep(P0, S0, P3, S3);
+        b0 = P1; b1 = ep(P1, S1, P2, S2); b2 = ep(P1, S1, P3, S3);
+    } else {
+        a0 = P0; a1 = P1; a2 = P2;
+        b0 = ep(P0, S0, P3, S3); b1 = ep(P1, S1, P3, S3); b2 = ep(P2, S2, P3, S3);
+    }
+    put(FTet{{a0, a1, a2, b2}}, 0);
+    put(FTet{{a0, a1, b2, b1}}, 1);
+    put(FTet{{a0, b0, b1, b2}}, 2);
+}
+
+// The queued clip jobs, worked through by the whole warp: each lane takes a
+// piece (from the top of the stack of pieces, else a new job), clips it by its
+// next plane and pushes the parts that still have planes to go; a piece at its
+// last plane adds its volume below that plane (closed-form cut fraction). All
+// lanes run the same step on different pieces, whatever the depth of a job.
+__device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &accs, float &accc, unsigned &ncuts)
 {
     const int lane = threadIdx.x & 31;
-    const int npr = nt * ncand;
+    __syncwarp();
+    int sp = 0, qn = 0;
+    for (;;) {
+        const int p = min(sp, 32), r = min(32 - p, nq - qn);
+        if (p + r == 0) break;
+        const bool act = lane < p + r;
+        FTet t;
+        unsigned meta = 0;
+        if (lane < p) {
+            t = ldT(sh.S[sp - 1 - lane]);
+            meta = sh.Sm[sp - 1 - lane];
+        } else if (act) {
+            meta = sh.Q[qn + lane - p];
+            t = ldT(sh.T[meta & 31]);
+        }
+        __syncwarp();  // every piece read before the pushes reuse the slots
+        int nch = 0, nin = 0, nup = 0, ti = 0, k = 0;
+        unsigned rem = 0;
+        float sd[4], v6 = 0.0f;
+        bool cut = false;
+        if (act) {
+            ti = meta & 31;
+            k = (meta >> 5) & 31;
+            rem = meta >> 10;
+            const int j = __ffs(rem) - 1;
+            rem &= rem - 1;
+            const float4 pl = j < 4 ? sh.Kp[k][j] : sh.KH[k];
+            fdist(t, pl, tol, sd, nin, nup);
+            if (nin > 0) {
+                if (nup == 0) {
+                    if (rem == 0) v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    else nch = 1;
+                } else {
+                    cut = true;
+                    if (rem == 0) {
+                        float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
+                        fsort4(h0, h1, h2, h3);
+                        v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3])) * ffrac_below(h0, h1, h2, h3);
+                    } else {
+                        nch = nin == 1 ? 1 : 3;
+                    }
+                }
+            }
+        }
+        int inc = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        // Commit the longest prefix of lanes whose parts leave the stack at most
+        // MX_STACK - 6 deep (the rest wait: stack pieces stay where they are,
+        // jobs stay queued); if none does, the top piece alone. Every part has at
+        // most 4 planes to go, so a piece at depth i with r planes to go always
+        // satisfies i + 1 + 2 (r - 1) <= MX_STACK, and the top piece alone always
+        // fits: the stack cannot overflow.
+        const bool fits = act && sp - min(lane + 1, p) + inc <= MX_STACK - 6;
+        const unsigned fm = __ballot_sync(0xffffffffu, fits);
+        const int L = fm ? 32 - __clz(fm) : 1;
+        const int base = sp - min(L, p);
+        if (lane < L) {
+            if (cut) ++ncuts;
+            if (v6 != 0.0f) two_sum(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
+            if (nch > 0) {
+                const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
+                const int at = base + inc - nch;
+                auto put = [&](const FTet &c, int i) {
+                    stT(sh.S[at + i], c);
+                    sh.Sm[at + i] = (unsigned short)cm;
+                };
+                if (nup == 0) put(t, 0);
+                else fsplit(t, sd, nin, put);
+            }
+        }
+        sp = base + __shfl_sync(0xffffffffu, inc, L - 1);
+        qn += max(0, L - p);
+        __syncwarp();
+    }
+}
+
+// all (T, K) pairs of the buffered candidates, lane k holding candidate k and
+// running over the polyhedron's tetrahedra (read by every lane at once): a
+// pair inside every plane adds |T| at once, a pair that must be cut becomes a
+// clip job
+__device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
+                                         unsigned &npairs, unsigned &ncuts)
+{
+    const int lane = threadIdx.x & 31;
+    const bool has = lane < ncand;
+    float4 pl[5];
+    float kb[6];
+    float kw = 0.0f;
+    bool uh = false;
+    if (has) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pl[q] = sh.Kp[lane][q];
+        pl[4] = sh.KH[lane];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) kb[q] = sh.Kb[lane][q];
+        kw = sh.Kw[lane];
+        uh = sh.KuseH[lane];
+    }
     int nq = 0;
-    for (int base = 0; base < npr; base += 32) {
-        const int w = base + lane;
+    for (int t = 0; t < nt; ++t) {
+        const float sg = sh.Tsg[t];
+        if (sg == 0.0f) continue;
         bool job = false;
         unsigned code = 0;
-        if (w < npr) {
-            const int t = w % nt, k = w / nt;
-            const float sg = sh.Tsg[t];
-            const float *tb = sh.Tb[t], *kb = sh.Kb[k];
-            if (sg != 0.0f && !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] ||
-                                tb[5] < kb[2] || kb[5] < tb[2])) {
+        if (has) {
+            const float *tb = sh.Tb[t];
+            if (!(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] || tb[5] < kb[2] ||
+                  kb[5] < tb[2])) {
                 ++npairs;
-                const FTet &T = sh.T[t];
+                const FTet T = ldT(sh.T[t]);
                 unsigned mask = 0;
                 bool outside = false;
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    float4 p;
-                    if (q < 4) p = sh.Kp[k][q];
-                    else if (sh.KuseH[k]) p = sh.KH[k];
-                    else break;
+                    if (q == 4 && !uh) break;
                     // a vertex within tol of the plane is on it: the pair is outside
                     // when no vertex is clearly inside, the plane cuts only when
                     // vertices lie clearly on both sides
                     int nneg = 0, npos = 0;
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        float sd = p.x * T.v[i].x + p.y * T.v[i].y + p.z * T.v[i].z - p.w;
+                        const float sd = pl[q].x * T.v[i].x + pl[q].y * T.v[i].y + pl[q].z * T.v[i].z - pl[q].w;
                         nneg += sd < -tol;
                         npos += sd > tol;
                     }
@@ -221,33 +324,21 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
                     if (npos > 0) mask |= 1u << q;
                 }
                 if (!outside) {
-                    if (mask == 0) two_sum(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
-                    else { job = true; code = (unsigned)t | ((unsigned)k << 5) | (mask << 10); }
+                    if (mask == 0) two_sum(accs, accc, sg * kw * sh.Tv6[t]);
+                    else { job = true; code = (unsigned)t | ((unsigned)lane << 5) | (mask << 10); }
                 }
             }
         }
         const unsigned bm = __ballot_sync(0xffffffffu, job);
-        if (job) sh.Q[nq + __popc(bm & ((1u << lane) - 1u))] = code;
+        if (job) sh.Q[nq + __popc(bm & ((1u << lane) - 1u))] = (unsigned short)code;
         nq += __popc(bm);
     }
-    __syncwarp();
-    for (int q = lane; q < nq; q += 32) {
-        const unsigned code = sh.Q[q];
-        const int t = code & 31, k = (code >> 5) & 31;
-        const unsigned mask = code >> 10;
-        float4 act[5];
-        int np = 0;
-#pragma unroll
-        for (int j = 0; j < 5; ++j)
-            if (mask & (1u << j)) act[np++] = j < 4 ? sh.Kp[k][j] : sh.KH[k];
-        float v6 = fclip6(sh.T[t], act, np, tol, status, ncuts);
-        two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * v6);
-    }
+    if (nq > 0) mx_clip(sh, nq, tol, accs, accc, ncuts);
     __syncwarp();
 }
 
 template <bool LIST>
-__global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, MXArgs a)
+__global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m, MXArgs a)
 {
     __shared__ MXShared shm[MX_WARPS];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -343,7 +434,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
             else T = FTet{{a0, b0, b1, b2}};
             float v6 = fvol6(T.v[0], T.v[1], T.v[2], T.v[3]);
             float sv = -par * v6;
-            sh.T[lane] = T;
+            stT(sh.T[lane], T);
             sh.Tsg[lane] = sv > 0.0f ? 1.0f : (sv < 0.0f ? -1.0f : 0.0f);
             sh.Tv6[lane] = fabsf(v6);
             bx[0] = fminf(fminf(T.v[0].x, T.v[1].x), fminf(T.v[2].x, T.v[3].x));
@@ -370,93 +461,127 @@ __global__ void __launch_bounds__(MX_WARPS * 32) k_phase_flux_mixed(DevMesh m, M
         float accs = 0.0f, accc = 0.0f;
         unsigned npairs = 0, ncuts = 0;
         int ncand = 0;
-        for (int s = s0; s < s1; ++s) {
-            const int c = __ldg(m.scell + s);
-            const double al = a.alpha[c];
-            if (!comp && al <= eps) continue;       // empty cell carries no phase
-            if (comp && al >= 1.0 - eps) continue;  // full cell carries no void
-            const V3 cc = ld3(m.cc, m.nc, c);
-            const F3 dc = f3((float)(cc.x - o.x), (float)(cc.y - o.y), (float)(cc.z - o.z));
-            const float4 cb0 = __ldg(a.cbl + 2 * (size_t)c), cb1 = __ldg(a.cbl + 2 * (size_t)c + 1);
-            if (cb1.x + dc.x < pb[0] || pb[3] < cb0.x + dc.x || cb1.y + dc.y < pb[1] || pb[4] < cb0.y + dc.y ||
-                cb1.z + dc.z < pb[2] || pb[5] < cb0.z + dc.z)
-                continue;
-            float wgt = 1.0f;
-            bool useH = false;
-            float4 H = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (al > eps && al < 1.0 - eps) {
-                if (a.flags[c] & VOF_ORIENTED) {
-                    V3 hn = ld3(a.n, m.nc, c);
-                    double hd = a.d[c] - dot(hn, o);
-                    // phase side n.x <= d; the void side is -n.x <= -d
-                    float sg = comp ? -1.0f : 1.0f;
-                    H = make_float4(sg * (float)hn.x, sg * (float)hn.y, sg * (float)hn.z, sg * (float)hd);
-                    useH = true;
-                } else wgt = comp ? (float)(1.0 - al) : (float)al;
+        // The stencil is taken 32 cells at a time, one per lane: the cells that
+        // reach the polyhedron's box are kept (with their half-space) in shared
+        // memory, then their tetrahedra come 32 at a time into the candidate
+        // buffer. A batch that does not fit is produced again after the buffer
+        // has been processed, so that the buffer is processed at one place and
+        // no candidate is held across it.
+        int sc = s0 - 32, tb = 0, ntot = 0, ncell = 0;
+        for (;;) {
+            if (tb >= ntot) {  // the chunk's tetrahedra are done: next chunk
+                sc += 32;
+                tb = 0;
+                ntot = 0;
+                if (sc < s1) {
+                    const int s = sc + lane;
+                    bool pass = false;
+                    int c = 0;
+                    double al = 0.0;
+                    F3 dc = f3(0.f, 0.f, 0.f);
+                    if (s < s1) {
+                        c = __ldg(m.scell + s);
+                        al = a.alpha[c];
+                        // an empty cell carries no phase, a full cell no void
+                        if (!((!comp && al <= eps) || (comp && al >= 1.0 - eps))) {
+                            const V3 cc = ld3(m.cc, m.nc, c);
+                            dc = f3((float)(cc.x - o.x), (float)(cc.y - o.y), (float)(cc.z - o.z));
+                            const float4 cb0 = __ldg(a.cbl + 2 * (size_t)c), cb1 = __ldg(a.cbl + 2 * (size_t)c + 1);
+                            pass = !(cb1.x + dc.x < pb[0] || pb[3] < cb0.x + dc.x || cb1.y + dc.y < pb[1] ||
+                                     pb[4] < cb0.y + dc.y || cb1.z + dc.z < pb[2] || pb[5] < cb0.z + dc.z);
+                        }
+                    }
+                    int nkt = 0, t0 = 0;
+                    float wgt = 1.0f;
+                    bool useH = false;
+                    float4 H = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (pass) {
+                        t0 = __ldg(a.ctptr + c);
+                        nkt = __ldg(a.ctptr + c + 1) - t0;
+                        if (al > eps && al < 1.0 - eps) {
+                            if (a.flags[c] & VOF_ORIENTED) {
+                                V3 hn = ld3(a.n, m.nc, c);
+                                double hd = a.d[c] - dot(hn, o);
+                                // phase side n.x <= d; the void side is -n.x <= -d
+                                float sg = comp ? -1.0f : 1.0f;
+                                H = make_float4(sg * (float)hn.x, sg * (float)hn.y, sg * (float)hn.z, sg * (float)hd);
+                                useH = true;
+                            } else wgt = comp ? (float)(1.0 - al) : (float)al;
+                        }
+                    }
+                    int inc = nkt;
+#pragma unroll
+                    for (int o2 = 1; o2 < 32; o2 <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, inc, o2);
+                        if (lane >= o2) inc += v;
+                    }
+                    const unsigned pm = __ballot_sync(0xffffffffu, pass);
+                    if (pass) {
+                        const int r = __popc(pm & ((1u << lane) - 1u));
+                        sh.CH[r] = H;
+                        sh.Cdc[r][0] = dc.x; sh.Cdc[r][1] = dc.y; sh.Cdc[r][2] = dc.z;
+                        sh.Cw[r] = wgt;
+                        sh.CuseH[r] = useH;
+                        sh.Ct0[r] = t0;
+                        sh.Cend[r] = inc;
+                    }
+                    ntot = __shfl_sync(0xffffffffu, inc, 31);
+                    ncell = __popc(pm);
+                    __syncwarp();
+                    continue;
+                }
             }
-            // ---- this cell's tetrahedra, 32 at a time, into the candidate buffer
-            const int f0 = __ldg(m.cptr + c), f1 = __ldg(m.cptr + c + 1);
-            const int cpb = __ldg(a.cfpptr + c);
-            for (int kb = 0;; kb += 32) {
-                int off = kb + lane, k = f0, code = 0, gn = 0, pofs = cpb;
-                bool found = false;
-                for (; k < f1; ++k) {
-                    code = __ldg(m.cface + k);
-                    int g = code >> 1;
-                    gn = __ldg(m.fptr + g + 1) - __ldg(m.fptr + g);
-                    int gt = gn == 3 ? 1 : gn;
-                    if (off < gt) { found = true; break; }
-                    off -= gt;
-                    pofs += gn;
+            const bool fin = sc >= s1;
+            bool cand = false;
+            int ci = 0;
+            float4 kp[4];
+            float kbx[6];
+            if (!fin && tb + lane < ntot) {
+                // this lane's tetrahedron: its cell by bisection on the running
+                // counts; planes and box move from the cell frame to the face
+                // frame by the shift dc
+                const int g = tb + lane;
+                int hi = ncell - 1;
+                while (ci < hi) {
+                    const int mid = (ci + hi) >> 1;
+                    if (sh.Cend[mid] > g) hi = mid;
+                    else ci = mid + 1;
                 }
-                if (!__any_sync(0xffffffffu, found)) break;
-                bool cand = false;
-                float4 kp[4];
-                float kbx[6];
-                if (found) {
-                    F3 k0 = dc, k1, k2, k3;
-                    if (gn == 3) {
-                        k1 = ld4(a.cfpl, pofs) + dc; k2 = ld4(a.cfpl, pofs + 1) + dc; k3 = ld4(a.cfpl, pofs + 2) + dc;
-                    } else {
-                        k1 = ld4(a.cfl, k) + dc;
-                        k2 = ld4(a.cfpl, pofs + off) + dc;
-                        k3 = ld4(a.cfpl, pofs + (off + 1 == gn ? 0 : off + 1)) + dc;
-                    }
-                    if (code & 1) { F3 t = k2; k2 = k3; k3 = t; }
-                    kbx[0] = fminf(fminf(k0.x, k1.x), fminf(k2.x, k3.x)); kbx[3] = fmaxf(fmaxf(k0.x, k1.x), fmaxf(k2.x, k3.x));
-                    kbx[1] = fminf(fminf(k0.y, k1.y), fminf(k2.y, k3.y)); kbx[4] = fmaxf(fmaxf(k0.y, k1.y), fmaxf(k2.y, k3.y));
-                    kbx[2] = fminf(fminf(k0.z, k1.z), fminf(k2.z, k3.z)); kbx[5] = fmaxf(fmaxf(k0.z, k1.z), fmaxf(k2.z, k3.z));
-                    cand = !(kbx[3] < pb[0] || pb[3] < kbx[0] || kbx[4] < pb[1] || pb[4] < kbx[1] ||
-                             kbx[5] < pb[2] || pb[5] < kbx[2]);
-                    if (cand) {
-                        F3 n0 = fcross(k2 - k0, k1 - k0), n1 = fcross(k1 - k0, k3 - k0);
-                        F3 n2 = fcross(k3 - k0, k2 - k0), n3 = fcross(k2 - k1, k3 - k1);
-                        n0 = n0 * rsqrtf(fdot(n0, n0) + 1e-37f); n1 = n1 * rsqrtf(fdot(n1, n1) + 1e-37f);
-                        n2 = n2 * rsqrtf(fdot(n2, n2) + 1e-37f); n3 = n3 * rsqrtf(fdot(n3, n3) + 1e-37f);
-                        kp[0] = make_float4(n0.x, n0.y, n0.z, fdot(n0, k0));
-                        kp[1] = make_float4(n1.x, n1.y, n1.z, fdot(n1, k0));
-                        kp[2] = make_float4(n2.x, n2.y, n2.z, fdot(n2, k0));
-                        kp[3] = make_float4(n3.x, n3.y, n3.z, fdot(n3, k1));
-                    }
-                }
-                const unsigned cmask = __ballot_sync(0xffffffffu, cand);
-                if (ncand + __popc(cmask) > MX_CAND) {  // buffer full: process it first
-                    mx_flush(sh, nt, ncand, tol, accs, accc, npairs, ncuts, a.status);
-                    ncand = 0;
-                }
+                const int j = sh.Ct0[ci] + g - (ci ? sh.Cend[ci - 1] : 0);
+                const F3 dc = f3(sh.Cdc[ci][0], sh.Cdc[ci][1], sh.Cdc[ci][2]);
+                const float4 *q = a.ktl + 6 * (size_t)j;
+                const float4 b0 = __ldg(q + 4), b1 = __ldg(q + 5);
+                kbx[0] = b0.x + dc.x; kbx[1] = b0.y + dc.y; kbx[2] = b0.z + dc.z;
+                kbx[3] = b1.x + dc.x; kbx[4] = b1.y + dc.y; kbx[5] = b1.z + dc.z;
+                cand = !(kbx[3] < pb[0] || pb[3] < kbx[0] || kbx[4] < pb[1] || pb[4] < kbx[1] ||
+                         kbx[5] < pb[2] || pb[5] < kbx[2]);
                 if (cand) {
-                    int r = ncand + __popc(cmask & ((1u << lane) - 1u));
-                    for (int q = 0; q < 4; ++q) sh.Kp[r][q] = kp[q];
-                    for (int q = 0; q < 6; ++q) sh.Kb[r][q] = kbx[q];
-                    sh.KH[r] = H;
-                    sh.Kw[r] = wgt;
-                    sh.KuseH[r] = useH;
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 pl = __ldg(q + i);
+                        kp[i] = make_float4(pl.x, pl.y, pl.z, pl.w + (pl.x * dc.x + pl.y * dc.y + pl.z * dc.z));
+                    }
                 }
-                ncand += __popc(cmask);
-                __syncwarp();
             }
+            const unsigned cmask = __ballot_sync(0xffffffffu, cand);
+            if (fin ? ncand > 0 : ncand + __popc(cmask) > MX_CAND) {
+                mx_flush(sh, nt, ncand, tol, accs, accc, npairs, ncuts);
+                ncand = 0;
+                continue;  // the batch again (or the end)
+            }
+            if (fin) break;
+            if (cand) {
+                int r = ncand + __popc(cmask & ((1u << lane) - 1u));
+                for (int q = 0; q < 4; ++q) sh.Kp[r][q] = kp[q];
+                for (int q = 0; q < 6; ++q) sh.Kb[r][q] = kbx[q];
+                sh.KH[r] = sh.CH[ci];
+                sh.Kw[r] = sh.Cw[ci];
+                sh.KuseH[r] = sh.CuseH[ci];
+            }
+            ncand += __popc(cmask);
+            tb += 32;
+            __syncwarp();
         }
-        if (ncand > 0) mx_flush(sh, nt, ncand, tol, accs, accc, npairs, ncuts, a.status);
         // finish in FP64: lane sums and compensations, then the 1/6 of the volumes
         double acc = warp_sum((double)accs + (double)accc) / 6.0;
         if (comp) acc = Ff * a.dt - acc;
@@ -501,6 +626,43 @@ __global__ void k_local_geom(DevMesh m, const int *cfpptr, float4 *cfl, float4 *
     cbl[2 * c + 1] = make_float4(hi(b[3] - cc.x), hi(b[4] - cc.y), hi(b[5] - cc.z), 0.f);
 }
 
+// the tetrahedra of every cell (cell centre + fan triangle of a face, in the
+// order of the cell's faces and of the face's points) as 4 outward unit-normal
+// planes and a box, in the cell frame (context creation)
+__global__ void k_cell_tets(DevMesh m, const int *cfpptr, const float4 *cfl, const float4 *cfpl, const int *ctptr,
+                            float4 *ktl)
+{
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    int o = cfpptr[c], j = ctptr[c];
+    for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+        const int code = m.cface[k], g = code >> 1, gn = m.fptr[g + 1] - m.fptr[g];
+        for (int i = 0; i < (gn == 3 ? 1 : gn); ++i, ++j) {
+            F3 k0 = f3(0.f, 0.f, 0.f), k1, k2, k3;
+            if (gn == 3) {
+                k1 = ld4(cfpl, o); k2 = ld4(cfpl, o + 1); k3 = ld4(cfpl, o + 2);
+            } else {
+                k1 = ld4(cfl, k); k2 = ld4(cfpl, o + i); k3 = ld4(cfpl, o + (i + 1 == gn ? 0 : i + 1));
+            }
+            if (code & 1) { F3 t = k2; k2 = k3; k3 = t; }
+            F3 n0 = fcross(k2 - k0, k1 - k0), n1 = fcross(k1 - k0, k3 - k0);
+            F3 n2 = fcross(k3 - k0, k2 - k0), n3 = fcross(k2 - k1, k3 - k1);
+            n0 = n0 * rsqrtf(fdot(n0, n0) + 1e-37f); n1 = n1 * rsqrtf(fdot(n1, n1) + 1e-37f);
+            n2 = n2 * rsqrtf(fdot(n2, n2) + 1e-37f); n3 = n3 * rsqrtf(fdot(n3, n3) + 1e-37f);
+            float4 *q = ktl + 6 * (size_t)j;
+            q[0] = make_float4(n0.x, n0.y, n0.z, 0.f);
+            q[1] = make_float4(n1.x, n1.y, n1.z, 0.f);
+            q[2] = make_float4(n2.x, n2.y, n2.z, 0.f);
+            q[3] = make_float4(n3.x, n3.y, n3.z, fdot(n3, k1));
+            q[4] = make_float4(fminf(fminf(k0.x, k1.x), fminf(k2.x, k3.x)), fminf(fminf(k0.y, k1.y), fminf(k2.y, k3.y)),
+                               fminf(fminf(k0.z, k1.z), fminf(k2.z, k3.z)), 0.f);
+            q[5] = make_float4(fmaxf(fmaxf(k0.x, k1.x), fmaxf(k2.x, k3.x)), fmaxf(fmaxf(k0.y, k1.y), fmaxf(k2.y, k3.y)),
+                               fmaxf(fmaxf(k0.z, k1.z), fmaxf(k2.z, k3.z)), 0.f);
+        }
+        o += gn;
+    }
+}
+
 __global__ void k_face_local(DevMesh m, float4 *fpl)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
@@ -520,6 +682,8 @@ int launch_setup_mixed(vof_ctx *c, cudaStream_t s)
 {
     k_local_geom<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->cbl);
     k_face_local<<<cdiv(c->nf, 256), 256, 0, s>>>(c->m, c->fpl);
+    if (c->ktl)
+        k_cell_tets<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->ctptr, c->ktl);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 
@@ -528,7 +692,7 @@ static MXArgs mx_args(vof_ctx *c, const double *alpha, const double *n, const do
                       const int *list, const int *count, const double *disp, unsigned long long *work)
 {
     return MXArgs{alpha, n, d, flags, Up, F, lambda, dt, Va, list, count, disp, c->lam_b, c->status, work,
-                  c->cfl, c->cfpl, c->fpl, c->cbl, c->cfpptr};
+                  c->fpl, c->cbl, c->ktl, c->ctptr};
 }
 
 int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
