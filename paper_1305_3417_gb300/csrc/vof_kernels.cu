@@ -148,27 +148,40 @@ __global__ void k_point_velocity(DevMesh m, const double *__restrict__ Uc, doubl
 // one warp per cell: NAG gradient over the (face, point) entries of the cell,
 // then Alg. 1 with the fill function summed over the cell tetrahedra, one or
 // two per lane, each a closed-form cut fraction of its sorted projections.
-__device__ __forceinline__ float ffrac_below_rel(float h0, float h1, float h2, float h3, float d)
+
+// Cut fraction of a tetrahedron with sorted projections h0..h3 below level d,
+// and its derivative in d (the cut area over the volume): the same closed form
+// as frac_below, differentiated piece by piece.
+template <class R>
+__device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 {
-    if (d <= h0) return 0.0f;
-    if (d >= h3) return 1.0f;
+    df = R(0);
+    if (d <= h0) return R(0);
+    if (d >= h3) return R(1);
     if (d <= h1) {
-        float x = d - h0;
-        return (x / (h1 - h0)) * (x / (h2 - h0)) * (x / (h3 - h0));
+        const R x = d - h0, p = R(1) / ((h1 - h0) * (h2 - h0) * (h3 - h0));
+        df = R(3) * x * x * p;
+        return x * x * x * p;
     }
     if (d >= h2) {
-        float y = h3 - d;
-        return 1.0f - (y / (h3 - h0)) * (y / (h3 - h1)) * (y / (h3 - h2));
+        const R y = h3 - d, q = R(1) / ((h3 - h0) * (h3 - h1) * (h3 - h2));
+        df = R(3) * y * y * q;
+        return R(1) - y * y * y * q;
     }
-    float a = (d - h0) / (h2 - h0), b = (d - h0) / (h3 - h0);
-    float c = (d - h1) / (h2 - h1), e = (d - h1) / (h3 - h1);
-    return a * b + a * (1.0f - b) * e + (1.0f - a) * c * e;
+    const R ra = R(1) / (h2 - h0), rb = R(1) / (h3 - h0), rc = R(1) / (h2 - h1), re = R(1) / (h3 - h1);
+    const R a = (d - h0) * ra, b = (d - h0) * rb, c = (d - h1) * rc, e = (d - h1) * re;
+    df = ra * b + a * rb + ra * (R(1) - b) * e - a * rb * e + a * (R(1) - b) * re - ra * c * e +
+         (R(1) - a) * rc * e + (R(1) - a) * c * re;
+    return a * b + a * (R(1) - b) * e + (R(1) - a) * c * e;
 }
 
-// MIXED: while the fill residual is above 1e-5 (FP32 rounding of the fill is
-// ~1e-7), the fill is evaluated in FP32 on projections taken relative to the
-// cell centre; the iteration then continues in FP64 to the 1e-13 stop.  Cells
-// with alpha within 1e-4 of 0 or 1 stay in FP64 (the bracket near the ends).
+// MIXED: cells with 1e-4 < alpha < 1 - 1e-4 are positioned by safeguarded
+// Newton steps on the fill, whose derivative is the cut area: first in FP32
+// on projections relative to the cell centre while the residual is above 1e-5
+// (FP32 rounding of the fill is ~1e-7), then in FP64 to the 1e-13 stop; a
+// step that leaves the bracket is replaced by bisection.  Other cells, and
+// the plain FP64 form, follow Alg. 1 (secant, bisection once the secant
+// leaves the bracket).
 template <bool LIST, bool MIXED>
 __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const int *list, const int *count, double *nout,
@@ -258,41 +271,80 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     hi = fmax(hi, e3);
                 }
                 const double dmin = warp_min(lo), dmax = warp_max(hi);
-                // ---- Alg. 1: secant, bisection once the secant leaves the bracket
-                double A = dmin, B = dmax, x0 = A, g0 = -a, x1 = B, g1 = 1.0 - a, x = 0.0, gx = 0.0;
-                bool bisect = false;
-                bool fp32 = MIXED && a > 1e-4 && a < 1.0 - 1e-4;
-                const float Vf = (float)V;
-                while (it < POS_MAXIT) {
-                    if (!bisect) {
-                        x = x1 - g1 * (x1 - x0) / (g1 - g0);
-                        if (!(x > A && x < B)) bisect = true;
-                    }
-                    if (bisect) x = 0.5 * (A + B);
-                    if (MIXED && fp32) {
-                        float part = 0.0f, xr = (float)(x - href);
+                double x = 0.0;
+                if (MIXED && a > 1e-4 && a < 1.0 - 1e-4) {
+                    // ---- FP32 Newton, relative to the cell centre's projection
+                    const float Vf = (float)V, af = (float)a;
+                    float Ar = (float)(dmin - href), Br = (float)(dmax - href);
+                    float xr = Ar + af * (Br - Ar);
+                    while (it < POS_MAXIT) {
+                        float part = 0.0f, dpart = 0.0f;
 #pragma unroll
                         for (int s = 0; s < VOF_MAXK_LANE; ++s)
-                            if (vkf[s] > 0.0f) part += vkf[s] * ffrac_below_rel(hf[s][0], hf[s][1], hf[s][2], hf[s][3], xr);
+                            if (vkf[s] > 0.0f) {
+                                float df;
+                                part += vkf[s] * frac_below_dd(hf[s][0], hf[s][1], hf[s][2], hf[s][3], xr, df);
+                                dpart += vkf[s] * df;
+                            }
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-                        gx = (double)(part / Vf) - a;
-                        // near the root the FP32 sign is not reliable: this iterate
-                        // and all later ones are evaluated in FP64
-                        if (fabs(gx) <= 1e-5) fp32 = false;
+                        for (int o = 16; o > 0; o >>= 1) {
+                            part += __shfl_xor_sync(0xffffffffu, part, o);
+                            dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
+                        }
+                        ++it;
+                        const float gf = part / Vf - af;
+                        // near the root the FP32 sign is not reliable: the bracket
+                        // takes no update from it and FP64 takes over here
+                        if (fabsf(gf) <= 1e-5f) break;
+                        if (gf < 0.0f) Ar = xr; else Br = xr;
+                        float xn = xr - gf * Vf / dpart;
+                        if (!(xn > Ar && xn < Br)) xn = 0.5f * (Ar + Br);
+                        if (!(xn > Ar && xn < Br)) break;  // bracket at FP32 resolution
+                        xr = xn;
                     }
-                    if (!(MIXED && fp32)) {
+                    // ---- FP64 Newton from there
+                    double A = href + (double)Ar, B = href + (double)Br;
+                    x = href + (double)xr;
+                    while (it < POS_MAXIT) {
+                        double part = 0.0, dpart = 0.0;
+#pragma unroll
+                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                            if (vk[s] > 0.0) {
+                                double df;
+                                part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
+                                dpart += vk[s] * df;
+                            }
+                        const double gx = warp_sum(part) / V - a;
+                        dpart = warp_sum(dpart);
+                        ++it;
+                        if (fabs(gx) <= POS_TOL) break;
+                        if (gx < 0) A = x; else B = x;
+                        if (B - A <= 1e-15 * (dmax - dmin)) break;
+                        double xn = x - gx * V / dpart;
+                        if (!(xn > A && xn < B)) xn = 0.5 * (A + B);
+                        x = xn;
+                    }
+                } else {
+                    // ---- Alg. 1: secant, bisection once the secant leaves the bracket
+                    double A = dmin, B = dmax, x0 = A, g0 = -a, x1 = B, g1 = 1.0 - a, gx = 0.0;
+                    bool bisect = false;
+                    while (it < POS_MAXIT) {
+                        if (!bisect) {
+                            x = x1 - g1 * (x1 - x0) / (g1 - g0);
+                            if (!(x > A && x < B)) bisect = true;
+                        }
+                        if (bisect) x = 0.5 * (A + B);
                         double part = 0.0;
 #pragma unroll
                         for (int s = 0; s < VOF_MAXK_LANE; ++s)
                             if (vk[s] > 0.0) part += vk[s] * frac_below(h[s][0], h[s][1], h[s][2], h[s][3], x);
                         gx = warp_sum(part) / V - a;
+                        ++it;
+                        if (gx < 0) A = x; else B = x;
+                        x0 = x1; g0 = g1; x1 = x; g1 = gx;
+                        if (fabs(gx) <= POS_TOL) break;
+                        if (B - A <= 1e-15 * (dmax - dmin)) break;
                     }
-                    ++it;
-                    if (gx < 0) A = x; else B = x;
-                    x0 = x1; g0 = g1; x1 = x; g1 = gx;
-                    if (!(MIXED && fp32) && fabs(gx) <= POS_TOL) break;
-                    if (B - A <= 1e-15 * (dmax - dmin)) break;
                 }
                 if (it >= POS_MAXIT && lane == 0) atomicOr(status, VOF_ST_POS_NOT_CONVERGED);
                 dd = x;

@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m
         // signed distances (to unit-normal planes) within 2e-6 of the face size are
         // taken as zero: points shared by the polyhedron and the cell tetrahedra
         // come out of different FP32 roundings and would otherwise look like cuts
-        const float tol = 2e-6f * (float)sqrt(sqrt(dot(ld3(m.sf, m.nf, f), ld3(m.sf, m.nf, f))));
+        const float tol = __ldg(a.fpl + b).w;
         // ---- flux polyhedron tetrahedra in the face frame
         float bx[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
         if (lane < nt) {
@@ -582,8 +582,16 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m
             tb += 32;
             __syncwarp();
         }
-        // finish in FP64: lane sums and compensations, then the 1/6 of the volumes
-        double acc = warp_sum((double)accs + (double)accc) / 6.0;
+        // lane sums and compensations merged across the warp by TwoSum, then the
+        // 1/6 of the volumes in FP64
+        float rs = accs, rc = accc;
+#pragma unroll
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            const float xs = __shfl_xor_sync(0xffffffffu, rs, o2), xc = __shfl_xor_sync(0xffffffffu, rc, o2);
+            two_sum(rs, rc, xs);
+            rc += xc;
+        }
+        double acc = ((double)rs + (double)rc) / 6.0;
         if (comp) acc = Ff * a.dt - acc;
         if (a.work) {
 #pragma unroll
@@ -667,10 +675,13 @@ __global__ void k_face_local(DevMesh m, float4 *fpl)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= m.nf) return;
-    V3 c = ld3(m.cf, m.nf, f);
+    V3 c = ld3(m.cf, m.nf, f), S = ld3(m.sf, m.nf, f);
+    // w of the face's first point: the on-plane band of the clipping, 2e-6 of
+    // the face size
+    const float tol = (float)(2e-6 * sqrt(sqrt(dot(S, S))));
     for (int j = m.fptr[f]; j < m.fptr[f + 1]; ++j) {
         V3 p = ldP(m, m.fpts[j]) - c;
-        fpl[j] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
+        fpl[j] = make_float4((float)p.x, (float)p.y, (float)p.z, j == m.fptr[f] ? tol : 0.f);
     }
 }
 
