@@ -55,6 +55,25 @@ __device__ __forceinline__ void st3(double *a, int n, int i, V3 v)
     a[i] = v.x; a[n + i] = v.y; a[2 * n + i] = v.z;
 }
 
+// Comparisons of a double with a threshold t > 0 through the order of the bit
+// patterns as signed 64-bit integers: monotone on the non-negative doubles, and
+// every negative double (-0 included) orders below t.  The same decision as the
+// FP64 compare for every value that is not NaN, taken on the integer pipe (the
+// FP64 pipe of this part runs 1/64 of the FP32 rate).
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool le_pos(double a, double t) { return dbits(a) <= dbits(t); }
+__device__ __forceinline__ bool lt_pos(double a, double t) { return dbits(a) < dbits(t); }
+__device__ __forceinline__ bool ge_pos(double a, double t) { return dbits(a) >= dbits(t); }
+__device__ __forceinline__ bool gt_pos(double a, double t) { return dbits(a) > dbits(t); }
+// a < -t (t > 0): negative, with a magnitude above t
+__device__ __forceinline__ bool lt_neg(double a, double t)
+{
+    const long long b = dbits(a);
+    return b < 0 && (b & 0x7fffffffffffffffLL) > dbits(t);
+}
+// a is +0 or -0
+__device__ __forceinline__ bool is_zero(double a) { return (dbits(a) << 1) == 0; }
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll

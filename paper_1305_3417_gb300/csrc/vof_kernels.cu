@@ -824,6 +824,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
                                                         unsigned *status)
 {
     double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    bool zero = false;
     const int nb = m.nf - m.ni;
     const int stride = gridDim.x * blockDim.x;
     const int lim = m.nc > nb ? m.nc : nb;
@@ -831,23 +832,33 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
         int c = i0 + threadIdx.x;
         bool bad = false;
         if (c < m.nc) {
+            // zero fluxes add nothing (s stays +0): skipped on the integer pipe
             double s = 0.0;
             for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
                 int code = m.cface[k];
                 double x = Va[code >> 1];
-                s += (code & 1) ? -x : x;
+                if (!is_zero(x)) s += (code & 1) ? -x : x;
             }
-            double a0 = alpha[c], V = m.vc[c];
-            double a1 = a0 - s / V;
-            alpha[c] = a1;
-            v[0] += V * a0;
-            v[1] += V * a1;
-            v[2] = fmin(v[2], a1);
-            v[3] = fmax(v[3], a1);
-            bad = a1 > 1.0 + BOUND_TOL || a1 < -BOUND_TOL;
+            double a0 = alpha[c];
+            if (is_zero(s) && dbits(a0) == 0) {
+                zero = true;  // an empty cell with no flux: alpha stays +0
+            } else {
+                double V = m.vc[c];
+                double a1 = a0 - s / V;
+                alpha[c] = a1;
+                v[0] += V * a0;
+                v[1] += V * a1;
+                v[2] = fmin(v[2], a1);
+                v[3] = fmax(v[3], a1);
+                bad = gt_pos(a1, 1.0 + BOUND_TOL) || lt_neg(a1, BOUND_TOL);
+            }
         }
         if (c < nb) v[4] += Va[m.ni + c];
         if (viol) warp_append(bad, c, viol, nviol, cap, status);
+    }
+    if (zero) {
+        v[2] = fmin(v[2], 0.0);
+        v[3] = fmax(v[3], 0.0);
     }
     block_reduce5(v, partial + 5 * blockIdx.x);
 }
@@ -908,13 +919,18 @@ __global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *a
                                                       unsigned *status)
 {
     double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
-    bool bad = false;
+    bool bad = false, zero = false;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
         double a = alpha[c];
+        if (dbits(a) == 0) { zero = true; continue; }  // +0 adds nothing to the mass
         v[1] += m.vc[c] * a;
         v[2] = fmin(v[2], a);
         v[3] = fmax(v[3], a);
-        bad |= a > 1.0 + BOUND_FLAG || a < -BOUND_FLAG;
+        bad |= gt_pos(a, 1.0 + BOUND_FLAG) || lt_neg(a, BOUND_FLAG);
+    }
+    if (zero) {
+        v[2] = fmin(v[2], 0.0);
+        v[3] = fmax(v[3], 0.0);
     }
     if (bad) atomicOr(status, VOF_ST_BOUND_RESIDUAL);
     block_reduce5(v, partial + 5 * blockIdx.x);
@@ -996,13 +1012,16 @@ __global__ void k_bp_room(DevMesh m, const double *alpha, BoundBufs b)
     }
 }
 
+// one thread per (source, face slot): slot j takes the faces j, j + BP_SLOTS, ...
+constexpr int BP_SLOTS = 8;
+
 __global__ void k_bp_scale(DevMesh m, const double *alpha, BoundBufs b)
 {
-    const int n = min(*b.n0, b.cap);
+    const long n = min(*b.n0, b.cap);
     double *bs = b.bs;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int c = b.la[i];
-        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n * BP_SLOTS; t += (long)gridDim.x * blockDim.x) {
+        int c = b.la[t / BP_SLOTS];
+        for (int k = m.cptr[c] + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
             int r = nbr_of(m, c, k);
             if (r < 0 || first_source(m, alpha, r, false) != c) continue;
             double ar = alpha[r], Vr = m.vc[r], Rp = room_exc(ar, Vr), Rm = room_def(ar, Vr);
@@ -1048,11 +1067,12 @@ __global__ void k_bp_place(DevMesh m, const double *alpha, BoundBufs b)
 // lowest-index source in its closed face neighbourhood
 __global__ void k_bp_new(DevMesh m, const double *alpha, BoundBufs b, int *npend, unsigned *status)
 {
-    const int n = min(*b.n0, b.cap);
+    const long n = min(*b.n0, b.cap);
     const double *bs = b.bs;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        int c = b.la[i];
-        for (int k = m.cptr[c] - 1; k < m.cptr[c + 1]; ++k) {
+    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n * BP_SLOTS; t += (long)gridDim.x * blockDim.x) {
+        int c = b.la[t / BP_SLOTS];
+        // slot 0 takes the source itself (k = cptr[c] - 1)
+        for (int k = m.cptr[c] - 1 + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
             int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
             if (x < 0 || first_source(m, alpha, x, true) != c) continue;
             double ax = alpha[x], V = m.vc[x];
@@ -1104,10 +1124,14 @@ __global__ void __launch_bounds__(GB_THREADS) k_bound_global_reduce(DevMesh m, c
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // Ep, Em, Sp, Sm
     int left = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
-        double a = alpha[c], V = m.vc[c];
-        if (a > 1.0 + BOUND_TOL) { v[0] += (a - 1.0) * V; ++left; }
-        else if (a < -BOUND_TOL) { v[1] += -a * V; ++left; }
-        else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) { v[2] += (1.0 - a) * V; v[3] += a * V; }
+        double a = alpha[c];
+        if (gt_pos(a, 1.0 + BOUND_TOL)) { v[0] += (a - 1.0) * m.vc[c]; ++left; }
+        else if (lt_neg(a, BOUND_TOL)) { v[1] += -a * m.vc[c]; ++left; }
+        else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) {
+            double V = m.vc[c];
+            v[2] += (1.0 - a) * V;
+            v[3] += a * V;
+        }
     }
     if (left) atomicAdd(nleft, left);
     __shared__ double sh[4][GB_THREADS / 32];
@@ -1128,12 +1152,25 @@ __global__ void __launch_bounds__(GB_THREADS) k_bound_global_reduce(DevMesh m, c
         last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        double t[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int k = 0; k < (int)gridDim.x; ++k)
-            for (int i = 0; i < 4; ++i) t[i] += ((volatile double *)partial)[4 * k + i];
-        for (int i = 0; i < 4; ++i) totals[i] = t[i];
+    if (!last) return;
+    // the last block: each thread sums a fixed strided set of block partials,
+    // then the block tree (fixed order: deterministic)
+    __threadfence();
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += GB_THREADS)
+        for (int i = 0; i < 4; ++i) t[i] += ((volatile double *)partial)[4 * k + i];
+    __syncthreads();
+    for (int i = 0; i < 4; ++i) {
+        double x = warp_sum(t[i]);
+        if (lane == 0) sh[i][w] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) {
+            double r = 0.0;
+            for (int k = 0; k < GB_THREADS / 32; ++k) r += sh[i][k];
+            totals[i] = r;
+        }
         *done = 0;
     }
 }
@@ -1143,11 +1180,11 @@ __global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, do
     const double Ep = totals[0], Em = totals[1], Sp = totals[2], Sm = totals[3];
     if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
-        double a = alpha[c], V = m.vc[c];
-        if (a > 1.0 + BOUND_TOL) alpha[c] = 1.0;
-        else if (a < -BOUND_TOL) alpha[c] = 0.0;
-        else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) {
-            double dV = 0.0;
+        double a = alpha[c];
+        if (gt_pos(a, 1.0 + BOUND_TOL)) alpha[c] = 1.0;
+        else if (lt_neg(a, BOUND_TOL)) alpha[c] = 0.0;
+        else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) {
+            double V = m.vc[c], dV = 0.0;
             if (Ep > 0.0) dV += Ep * ((1.0 - a) * V / Sp);
             if (Em > 0.0) dV -= Em * (a * V / Sm);
             alpha[c] = (a * V + dV) / V;
@@ -1167,10 +1204,11 @@ __global__ void k_point_state(DevMesh m, const double *__restrict__ alpha, uint8
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m.np) return;
     bool all_e = true, all_f = true;
+    const double full = 1.0 - m.eps;
     for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) {
         double a = __ldg(alpha + m.pcell[j]);
-        all_e &= a <= m.eps;
-        all_f &= a >= 1.0 - m.eps;
+        all_e &= le_pos(a, m.eps);
+        all_f &= ge_pos(a, full);
     }
     state[p] = (all_e ? 1 : 0) | (all_f ? 2 : 0);
 }
@@ -1186,7 +1224,7 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
         if (i < m.nf) {
             double Ff = F[i];
             double v = 0.0;
-            if (Ff != 0.0 && !(i >= m.ni && Ff < 0.0)) {
+            if (!is_zero(Ff) && !(i >= m.ni && dbits(Ff) < 0)) {
                 unsigned st = 3u;
                 for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) st &= state[m.fpts[k]];
                 if (st & 1u) v = 0.0;
@@ -1197,7 +1235,7 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
         }
         if (i < m.nc) {
             double a = alpha[i];
-            isint = a > m.eps && a < 1.0 - m.eps;
+            isint = gt_pos(a, m.eps) && lt_pos(a, 1.0 - m.eps);
         }
         warp_append(isband, i, band, nband, m.nf, status);
         warp_append(isint, i, icell, nicell, m.nc, status);
