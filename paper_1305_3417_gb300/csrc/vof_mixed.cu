@@ -235,12 +235,9 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
                 }
             }
         }
-        int inc = nch;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += v;
-        }
+        // running count of parts over the lanes (nch is 0, 1 or 3): two ballots
+        const unsigned b0 = __ballot_sync(0xffffffffu, nch & 1), b1 = __ballot_sync(0xffffffffu, nch & 2);
+        const int inc = __popc(b0 & (((1u << lane) << 1) - 1u)) + 2 * __popc(b1 & (((1u << lane) << 1) - 1u));
         // Commit the longest prefix of lanes whose parts leave the stack at most
         // MX_STACK - 6 deep (the rest wait: stack pieces stay where they are,
         // jobs stay queued); if none does, the top piece alone. Every part has at
@@ -265,7 +262,8 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
                 else fsplit(t, sd, nin, put);
             }
         }
-        sp = base + __shfl_sync(0xffffffffu, inc, L - 1);
+        const unsigned lm = L >= 32 ? 0xffffffffu : (1u << L) - 1u;
+        sp = base + __popc(b0 & lm) + 2 * __popc(b1 & lm);
         qn += max(0, L - p);
         __syncwarp();
     }
@@ -536,17 +534,18 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m
             int ci = 0;
             float4 kp[4];
             float kbx[6];
+            if (!fin) {
+                // the cell of tetrahedron tb + lane: the cells that end at or
+                // before tb, plus one for each cell that ends inside the batch at
+                // or before this lane (cell 'lane' ends rel tetrahedra after tb)
+                const int rel = lane < ncell ? sh.Cend[lane] - tb : 0x7fffffff;
+                const unsigned ends = __reduce_or_sync(0xffffffffu, rel > 0 && rel < 32 ? 1u << rel : 0u);
+                ci = __popc(__ballot_sync(0xffffffffu, rel <= 0)) + __popc(ends & (((1u << lane) << 1) - 1u));
+            }
             if (!fin && tb + lane < ntot) {
-                // this lane's tetrahedron: its cell by bisection on the running
-                // counts; planes and box move from the cell frame to the face
-                // frame by the shift dc
+                // this lane's tetrahedron: planes and box move from the cell frame
+                // to the face frame by the shift dc
                 const int g = tb + lane;
-                int hi = ncell - 1;
-                while (ci < hi) {
-                    const int mid = (ci + hi) >> 1;
-                    if (sh.Cend[mid] > g) hi = mid;
-                    else ci = mid + 1;
-                }
                 const int j = sh.Ct0[ci] + g - (ci ? sh.Cend[ci - 1] : 0);
                 const F3 dc = f3(sh.Cdc[ci][0], sh.Cdc[ci][1], sh.Cdc[ci][2]);
                 const float4 *q = a.ktl + 6 * (size_t)j;
