@@ -35,19 +35,21 @@ __device__ __forceinline__ F3 ld4(const float4 *p, long i)
 }
 
 // fraction of a tetrahedron below level 0 for sorted vertex values h0..h3
+// (fast reciprocal divisions: 2 ulp, far inside the form's FP32 rounding)
 __device__ __forceinline__ float ffrac_below(float h0, float h1, float h2, float h3)
 {
     if (0.0f <= h0) return 0.0f;
     if (0.0f >= h3) return 1.0f;
     if (0.0f <= h1) {
         float x = -h0;
-        return (x / (h1 - h0)) * (x / (h2 - h0)) * (x / (h3 - h0));
+        return __fdividef(x, h1 - h0) * __fdividef(x, h2 - h0) * __fdividef(x, h3 - h0);
     }
     if (0.0f >= h2) {
         float y = h3;
-        return 1.0f - (y / (h3 - h0)) * (y / (h3 - h1)) * (y / (h3 - h2));
+        return 1.0f - __fdividef(y, h3 - h0) * __fdividef(y, h3 - h1) * __fdividef(y, h3 - h2);
     }
-    float a = -h0 / (h2 - h0), b = -h0 / (h3 - h0), c = -h1 / (h2 - h1), e = -h1 / (h3 - h1);
+    float a = __fdividef(-h0, h2 - h0), b = __fdividef(-h0, h3 - h0);
+    float c = __fdividef(-h1, h2 - h1), e = __fdividef(-h1, h3 - h1);
     return a * b + a * (1.0f - b) * e + (1.0f - a) * c * e;
 }
 
@@ -99,8 +101,9 @@ constexpr int MX_STACK = 96;                 // pieces of clip jobs waiting for 
 struct __align__(16) MXShared {
     FTet S[MX_STACK];        // pieces
     FTet T[MX_MAXT];         // flux-polyhedron tetrahedra
-    float4 Kp[MX_CAND][4];   // outward unit-normal planes of the candidate cell tetrahedra
-    float4 KH[MX_CAND];      // the cell's phase (or void) half-space
+    float4 Kp[MX_CAND][5];   // outward unit-normal planes of the candidate cell tetrahedra, then
+                             // the cell's phase (or void) half-space; 80-byte rows: a warp's
+                             // float4 reads of different rows are conflict-free
     float Tb[MX_MAXT][6];
     float Kb[MX_CAND][6];
     float Tv6[MX_MAXT];      // |6 vol(T)|
@@ -165,7 +168,7 @@ __device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin,
     }
     MX_CX(0, 1) MX_CX(2, 3) MX_CX(0, 2) MX_CX(1, 3) MX_CX(1, 2)
 #undef MX_CX
-    auto ep = [](F3 a, float sa, F3 b, float sb) { return a + (b - a) * (sa / (sa - sb)); };
+    auto ep = [](F3 a, float sa, F3 b, float sb) { return a + (b - a) * __fdividef(sa, sa - sb); };
     if (nin == 1) {
         put(FTet{{P0, ep(P0, S0, P1, S1), ep(P0, S0, P2, S2), ep(P0, S0, P3, S3)}}, 0);
         return;
@@ -217,7 +220,7 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
             rem = meta >> 10;
             const int j = __ffs(rem) - 1;
             rem &= rem - 1;
-            const float4 pl = j < 4 ? sh.Kp[k][j] : sh.KH[k];
+            const float4 pl = sh.Kp[k][j];
             fdist(t, pl, tol, sd, nin, nup);
             if (nin > 0) {
                 if (nup == 0) {
@@ -269,62 +272,84 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
     }
 }
 
-// all (T, K) pairs of the buffered candidates, lane k holding candidate k and
-// running over the polyhedron's tetrahedra (read by every lane at once): a
-// pair inside every plane adds |T| at once, a pair that must be cut becomes a
-// clip job
+// All (T, K) pairs of the buffered candidates.  First lane k marks the
+// polyhedron tetrahedra whose box meets candidate k's box (a bit mask); then
+// the marked pairs are classified 32 at a time, one per lane: a pair inside
+// every plane adds |T| at once, a pair that must be cut becomes a clip job.
 __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
                                          unsigned &npairs, unsigned &ncuts)
 {
     const int lane = threadIdx.x & 31;
-    const bool has = lane < ncand;
-    float4 pl[5];
-    float kb[6];
-    float kw = 0.0f;
-    bool uh = false;
-    if (has) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) pl[q] = sh.Kp[lane][q];
-        pl[4] = sh.KH[lane];
+    unsigned tm = 0;
+    if (lane < ncand) {
+        float kb[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) kb[q] = sh.Kb[lane][q];
-        kw = sh.Kw[lane];
-        uh = sh.KuseH[lane];
+        for (int t = 0; t < nt; ++t) {
+            const float *tb = sh.Tb[t];
+            if (sh.Tsg[t] != 0.0f && !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] ||
+                                       tb[5] < kb[2] || kb[5] < tb[2]))
+                tm |= 1u << t;
+        }
     }
+    // running pair counts over the candidates (non-decreasing in the lane)
+    const int cnt = __popc(tm);
+    int end = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, end, o);
+        if (lane >= o) end += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, end, 31);
     int nq = 0;
-    for (int t = 0; t < nt; ++t) {
-        const float sg = sh.Tsg[t];
-        if (sg == 0.0f) continue;
+    for (int pb = 0; pb < total; pb += 32) {
+        const int pi = pb + lane;
         bool job = false;
         unsigned code = 0;
-        if (has) {
-            const float *tb = sh.Tb[t];
-            if (!(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] || tb[5] < kb[2] ||
-                  kb[5] < tb[2])) {
-                ++npairs;
-                const FTet T = ldT(sh.T[t]);
-                unsigned mask = 0;
-                bool outside = false;
+        // candidate of pair pi: the first lane whose end exceeds pi (bisection
+        // over the lanes by shuffles; every lane takes part)
+        int lo = 0, hi = 31;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    if (q == 4 && !uh) break;
-                    // a vertex within tol of the plane is on it: the pair is outside
-                    // when no vertex is clearly inside, the plane cuts only when
-                    // vertices lie clearly on both sides
-                    int nneg = 0, npos = 0;
+        for (int step = 0; step < 5; ++step) {
+            const int mid = (lo + hi) >> 1;
+            const int em = __shfl_sync(0xffffffffu, end, mid);
+            if (em > pi) hi = mid; else lo = mid + 1;
+        }
+        const int k = lo;
+        const unsigned tmk = __shfl_sync(0xffffffffu, tm, k);
+        const int startk = __shfl_sync(0xffffffffu, end - cnt, k);
+        if (pi < total) {
+            ++npairs;
+            // t: the (pi - startk + 1)-th set bit of tmk (bisection on bit counts)
+            const int j = pi - startk;
+            int t = 0;
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        const float sd = pl[q].x * T.v[i].x + pl[q].y * T.v[i].y + pl[q].z * T.v[i].z - pl[q].w;
-                        nneg += sd < -tol;
-                        npos += sd > tol;
-                    }
-                    if (nneg == 0) { outside = true; break; }
-                    if (npos > 0) mask |= 1u << q;
+            for (int w = 16; w >= 1; w >>= 1)
+                if (__popc(tmk & ((1u << (t + w)) - 1u)) <= j) t += w;
+            const FTet T = ldT(sh.T[t]);
+            const bool uh = sh.KuseH[k];
+            unsigned mask = 0;
+            bool outside = false;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (q == 4 && !uh) break;
+                const float4 pl = sh.Kp[k][q];
+                // a vertex within tol of the plane is on it: the pair is outside
+                // when no vertex is clearly inside, the plane cuts only when
+                // vertices lie clearly on both sides
+                int nneg = 0, npos = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float sd = pl.x * T.v[i].x + pl.y * T.v[i].y + pl.z * T.v[i].z - pl.w;
+                    nneg += sd < -tol;
+                    npos += sd > tol;
                 }
-                if (!outside) {
-                    if (mask == 0) two_sum(accs, accc, sg * kw * sh.Tv6[t]);
-                    else { job = true; code = (unsigned)t | ((unsigned)lane << 5) | (mask << 10); }
-                }
+                if (nneg == 0) { outside = true; break; }
+                if (npos > 0) mask |= 1u << q;
+            }
+            if (!outside) {
+                if (mask == 0) two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * sh.Tv6[t]);
+                else { job = true; code = (unsigned)t | ((unsigned)k << 5) | (mask << 10); }
             }
         }
         const unsigned bm = __ballot_sync(0xffffffffu, job);
@@ -573,7 +598,7 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m
                 int r = ncand + __popc(cmask & ((1u << lane) - 1u));
                 for (int q = 0; q < 4; ++q) sh.Kp[r][q] = kp[q];
                 for (int q = 0; q < 6; ++q) sh.Kb[r][q] = kbx[q];
-                sh.KH[r] = sh.CH[ci];
+                sh.Kp[r][4] = sh.CH[ci];
                 sh.Kw[r] = sh.Cw[ci];
                 sh.KuseH[r] = sh.CuseH[ci];
             }
