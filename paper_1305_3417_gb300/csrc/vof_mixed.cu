@@ -327,25 +327,26 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
             for (int w = 16; w >= 1; w >>= 1)
                 if (__popc(tmk & ((1u << (t + w)) - 1u)) <= j) t += w;
             const FTet T = ldT(sh.T[t]);
-            const bool uh = sh.KuseH[k];
+            const int npl = sh.KuseH[k] ? 5 : 4;
             unsigned mask = 0;
             bool outside = false;
+            // a vertex within tol of the plane is on it: the pair is outside when
+            // no vertex is clearly inside a plane, a plane cuts only when vertices
+            // lie clearly on both sides (all planes evaluated: straight-line code)
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                if (q == 4 && !uh) break;
                 const float4 pl = sh.Kp[k][q];
-                // a vertex within tol of the plane is on it: the pair is outside
-                // when no vertex is clearly inside, the plane cuts only when
-                // vertices lie clearly on both sides
-                int nneg = 0, npos = 0;
+                float lo = 3e38f, hi = -3e38f;
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float sd = pl.x * T.v[i].x + pl.y * T.v[i].y + pl.z * T.v[i].z - pl.w;
-                    nneg += sd < -tol;
-                    npos += sd > tol;
+                    const float sd = fmaf(pl.x, T.v[i].x, fmaf(pl.y, T.v[i].y, fmaf(pl.z, T.v[i].z, -pl.w)));
+                    lo = fminf(lo, sd);
+                    hi = fmaxf(hi, sd);
                 }
-                if (nneg == 0) { outside = true; break; }
-                if (npos > 0) mask |= 1u << q;
+                if (q < npl) {
+                    outside |= lo >= -tol;
+                    if (hi > tol) mask |= 1u << q;
+                }
             }
             if (!outside) {
                 if (mask == 0) two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * sh.Tv6[t]);
