@@ -257,6 +257,19 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     }
     std::vector<int> ctptr(nc + 1, 0);
     for (int c = 0; c < nc; ++c) ctptr[c + 1] = ctptr[c] + ktet[c];
+    // (face, point) entries and tetrahedra of every cell, in face order
+    std::vector<int2> cent(cfpptr[nc]);
+    std::vector<int4> ctet(ctptr[nc]);
+    parallel_for(nc, [&](long c) {
+        int e = cfpptr[c], t = ctptr[c];
+        for (int i = cptr[c]; i < cptr[c + 1]; ++i) {
+            const int code = cface[i], f = code >> 1, b = fptr[f], n = fptr[f + 1] - b;
+            for (int j = 0; j < n; ++j) cent[e++] = make_int2(b + j, code);
+            if (n == 3) ctet[t++] = make_int4(code, b, b + 1, b + 2);
+            else
+                for (int j = 0; j < n; ++j) ctet[t++] = make_int4(code, b + j, b + (j + 1 == n ? 0 : j + 1), -1);
+        }
+    });
 
     // ------------------------------------------------------------- device
     vof_ctx *c = new vof_ctx();
@@ -296,8 +309,10 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     m.vc = dev_alloc<double>(c, nc, &err);
     m.cbox = dev_alloc<double>(c, 6 * (size_t)nc, &err);
     m.nagc = dev_alloc<double>(c, nfp, &err);
-    m.cf32 = nullptr;
-    m.cc32 = nullptr;
+    m.ceptr = dev_copy(c, cfpptr.data(), cfpptr.size(), &err);
+    m.cent = dev_copy(c, cent.data(), cent.size(), &err);
+    m.ctptr = dev_copy(c, ctptr.data(), ctptr.size(), &err);
+    m.ctet = dev_copy(c, ctet.data(), ctet.size(), &err);
     // per-step scratch
     c->pstate = dev_alloc<uint8_t>(c, np, &err);
     c->band = dev_alloc<int>(c, nf, &err);
@@ -330,10 +345,8 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->cfpl = dev_alloc<float4>(c, cfpptr[nc], &err);
     c->fpl = dev_alloc<float4>(c, nfp, &err);
     c->cbl = dev_alloc<float4>(c, 2 * (size_t)nc, &err);
-    if (c->precision == VOF_MIXED) {
-        c->ctptr = dev_copy(c, ctptr.data(), ctptr.size(), &err);
-        c->ktl = dev_alloc<float4>(c, 6 * (size_t)ctptr[nc], &err);
-    }
+    c->palpha = dev_alloc<double>(c, np, &err);
+    if (c->precision == VOF_MIXED) c->ktl = dev_alloc<float4>(c, 6 * (size_t)ctptr[nc], &err);
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
     cudaMemset(c->bscr, 0, sizeof(double) * 8 * nc);

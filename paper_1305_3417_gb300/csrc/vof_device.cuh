@@ -58,21 +58,42 @@ __device__ __forceinline__ void st3(double *a, int n, int i, V3 v)
 // Comparisons of a double with a threshold t > 0 through the order of the bit
 // patterns as signed 64-bit integers: monotone on the non-negative doubles, and
 // every negative double (-0 included) orders below t.  The same decision as the
-// FP64 compare for every value that is not NaN, taken on the integer pipe (the
-// FP64 pipe of this part runs 1/64 of the FP32 rate).
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
-__device__ __forceinline__ bool le_pos(double a, double t) { return dbits(a) <= dbits(t); }
-__device__ __forceinline__ bool lt_pos(double a, double t) { return dbits(a) < dbits(t); }
-__device__ __forceinline__ bool ge_pos(double a, double t) { return dbits(a) >= dbits(t); }
-__device__ __forceinline__ bool gt_pos(double a, double t) { return dbits(a) > dbits(t); }
+// FP64 compare for every value that is not NaN, taken in 32-bit integer
+// instructions on the two halves (the FP64 pipe of this part runs at 1/64 of
+// the FP32 rate).  The halves come out of an opaque register move, so that the
+// compiler cannot fold the tests back into FP64 compares.
+struct DBits { int hi; unsigned lo; };
+__device__ __forceinline__ DBits dbits(double x)
+{
+    DBits r;
+    asm("mov.b64 {%0, %1}, %2;" : "=r"(r.lo), "=r"(r.hi) : "d"(x));
+    return r;
+}
+__device__ __forceinline__ bool bits_le(DBits a, DBits b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+__device__ __forceinline__ bool le_pos(double a, double t) { return bits_le(dbits(a), dbits(t)); }
+__device__ __forceinline__ bool lt_pos(double a, double t) { return !bits_le(dbits(t), dbits(a)); }
+__device__ __forceinline__ bool ge_pos(double a, double t) { return bits_le(dbits(t), dbits(a)); }
+__device__ __forceinline__ bool gt_pos(double a, double t) { return !bits_le(dbits(a), dbits(t)); }
 // a < -t (t > 0): negative, with a magnitude above t
 __device__ __forceinline__ bool lt_neg(double a, double t)
 {
-    const long long b = dbits(a);
-    return b < 0 && (b & 0x7fffffffffffffffLL) > dbits(t);
+    DBits x = dbits(a);
+    const bool neg = x.hi < 0;
+    x.hi &= 0x7fffffff;
+    return neg && !bits_le(x, dbits(t));
 }
 // a is +0 or -0
-__device__ __forceinline__ bool is_zero(double a) { return (dbits(a) << 1) == 0; }
+__device__ __forceinline__ bool is_zero(double a)
+{
+    const DBits x = dbits(a);
+    return ((x.hi & 0x7fffffff) | x.lo) == 0;
+}
+// a is +0
+__device__ __forceinline__ bool is_pzero(double a)
+{
+    const DBits x = dbits(a);
+    return (x.hi | x.lo) == 0;
+}
 
 __device__ __forceinline__ double warp_sum(double v)
 {

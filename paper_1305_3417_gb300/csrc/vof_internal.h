@@ -27,7 +27,13 @@ struct DevMesh {
     const double *cf, *sf;       // face centre, area vector [3*nf]
     const double *cc, *vc, *cbox;  // cell centre [3*nc], volume [nc], box [6*nc]
     const double *nagc;          // NAG face-value weight per face-point entry
-    const float *cf32, *cc32;    // single-precision copies for the mixed kernels
+    // per cell, in face order then point order: the (face, point) entries
+    // {fpts slot, face code} and the tetrahedra (c_c, outward face triangle)
+    // {face code, slot a, slot b, slot c or -1 for the face centre}
+    const int *ceptr;
+    const int2 *cent;
+    const int *ctptr;
+    const int4 *ctet;
 };
 
 struct vof_ctx {
@@ -63,9 +69,9 @@ struct vof_ctx {
     float4 *cfl, *cfpl, *fpl, *cbl;
     int *cfpptr;
     // per cell tetrahedron (mixed contexts): 4 outward unit-normal planes and the
-    // box, 6 float4, relative to the cell centre; ctptr: first of each cell
+    // box, 6 float4, relative to the cell centre (first of each cell: m.ctptr)
     float4 *ktl;
-    int *ctptr;
+    double *palpha;              // IDW point values of the points that are not all-empty / all-full
     // kernel-group timing (vof_profile_begin / _end)
     cudaEvent_t *prof_ev;
     int prof_max, prof_steps;

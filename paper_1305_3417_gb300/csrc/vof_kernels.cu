@@ -184,9 +184,9 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // leaves the bracket).
 template <bool LIST, bool MIXED>
 __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
-                                                     const int *list, const int *count, double *nout,
-                                                     double *dout, uint8_t *fout, int *itout,
-                                                     int *maxit, unsigned *status)
+                                                     const double *__restrict__ palpha, const int *list,
+                                                     const int *count, double *nout, double *dout,
+                                                     uint8_t *fout, int *itout, int *maxit, unsigned *status)
 {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -203,29 +203,19 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
         if (a >= 1.0 - eps) fl = VOF_FULL;
         else if (a > eps) {
             fl = VOF_INTERFACE;
-            const int f0 = m.cptr[c], f1 = m.cptr[c + 1];
             const double V = m.vc[c];
             // ---- NAG gradient: lane j handles the j-th (face, point) entry
             V3 g = mk(0, 0, 0);
-            for (int j = lane;; j += 32) {
-                int off = j, k = f0, code = 0, base = 0;
-                bool found = false;
-                for (; k < f1; ++k) {
-                    code = __ldg(m.cface + k);
-                    int f = code >> 1;
-                    base = __ldg(m.fptr + f);
-                    int n = __ldg(m.fptr + f + 1) - base;
-                    if (off < n) { found = true; break; }
-                    off -= n;
-                }
-                if (!found) break;
-                int f = code >> 1;
-                int p = __ldg(m.fpts + base + off);
-                double ap = 0.0;  // Eq. idwpointphi
-                for (int q = __ldg(m.pptr + p); q < __ldg(m.pptr + p + 1); ++q)
-                    ap += __ldg(m.pw + q) * __ldg(alpha + __ldg(m.pcell + q));
-                double w = __ldg(m.nagc + base + off) * ap;
-                if (code & 1) w = -w;  // Eq. own-nei: the neighbour sees -S_f
+            for (int j = __ldg(m.ceptr + c) + lane, e1 = __ldg(m.ceptr + c + 1); j < e1; j += 32) {
+                const int2 en = __ldg(m.cent + j);  // {fpts slot, face code}
+                const int f = en.y >> 1, p = __ldg(m.fpts + en.x);
+                double ap = 0.0;  // Eq. idwpointphi (precomputed per point when palpha is given)
+                if (palpha) ap = __ldg(palpha + p);
+                else
+                    for (int q = __ldg(m.pptr + p); q < __ldg(m.pptr + p + 1); ++q)
+                        ap += __ldg(m.pw + q) * __ldg(alpha + __ldg(m.pcell + q));
+                double w = __ldg(m.nagc + en.x) * ap;
+                if (en.y & 1) w = -w;  // Eq. own-nei: the neighbour sees -S_f
                 g = g + ld3(m.sf, m.nf, f) * w;
             }
             g = mk(warp_sum(g.x), warp_sum(g.y), warp_sum(g.z)) * (1.0 / V);
@@ -245,19 +235,16 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     h[s][0] = h[s][1] = h[s][2] = h[s][3] = 0.0;
                     vkf[s] = 0.0f;
                     hf[s][0] = hf[s][1] = hf[s][2] = hf[s][3] = 0.0f;
-                    int off = lane + 32 * s, k = f0, code = 0, nt = 0;
-                    bool found = false;
-                    for (; k < f1; ++k) {
-                        code = __ldg(m.cface + k);
-                        int f = code >> 1;
-                        int n = __ldg(m.fptr + f + 1) - __ldg(m.fptr + f);
-                        nt = n == 3 ? 1 : n;
-                        if (off < nt) { found = true; break; }
-                        off -= nt;
-                    }
-                    if (!found) continue;
+                    const int tj = __ldg(m.ctptr + c) + lane + 32 * s;
+                    if (tj >= __ldg(m.ctptr + c + 1)) continue;
+                    const int4 te = __ldg(m.ctet + tj);  // {face code, slot a, slot b, slot c or -1}
                     V3 t0, t1, t2;
-                    face_tri(m, code >> 1, off, code & 1, t0, t1, t2);
+                    if (te.w >= 0) {
+                        t0 = ldP(m, __ldg(m.fpts + te.y)); t1 = ldP(m, __ldg(m.fpts + te.z)); t2 = ldP(m, __ldg(m.fpts + te.w));
+                    } else {
+                        t0 = ld3(m.cf, m.nf, te.x >> 1); t1 = ldP(m, __ldg(m.fpts + te.y)); t2 = ldP(m, __ldg(m.fpts + te.z));
+                    }
+                    if (te.x & 1) { V3 q = t1; t1 = t2; t2 = q; }
                     vk[s] = fabs(tvol(ctr, t0, t1, t2));
                     double e0 = dot(nn, ctr), e1 = dot(nn, t0), e2 = dot(nn, t1), e3 = dot(nn, t2);
                     sort4(e0, e1, e2, e3);
@@ -277,6 +264,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     const float Vf = (float)V, af = (float)a;
                     float Ar = (float)(dmin - href), Br = (float)(dmax - href);
                     float xr = Ar + af * (Br - Ar);
+                    int near = 0;
                     while (it < POS_MAXIT) {
                         float part = 0.0f, dpart = 0.0f;
 #pragma unroll
@@ -293,18 +281,47 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                         }
                         ++it;
                         const float gf = part / Vf - af;
-                        // near the root the FP32 sign is not reliable: the bracket
-                        // takes no update from it and FP64 takes over here
-                        if (fabsf(gf) <= 1e-5f) break;
-                        if (gf < 0.0f) Ar = xr; else Br = xr;
+                        // below 1e-5 the FP32 sign is not reliable: the bracket takes
+                        // no update from it, and after two more Newton steps (down to
+                        // the FP32 rounding of the fill) FP64 takes over
+                        const bool sure = fabsf(gf) > 1e-5f;
+                        if (sure) {
+                            if (gf < 0.0f) Ar = xr; else Br = xr;
+                        }
                         float xn = xr - gf * Vf / dpart;
                         if (!(xn > Ar && xn < Br)) xn = 0.5f * (Ar + Br);
                         if (!(xn > Ar && xn < Br)) break;  // bracket at FP32 resolution
                         xr = xn;
+                        if (!sure && ++near >= 2) break;
                     }
                     // ---- FP64 Newton from there
                     double A = href + (double)Ar, B = href + (double)Br;
                     x = href + (double)xr;
+                    while (it < POS_MAXIT) {
+                        double part = 0.0, dpart = 0.0;
+#pragma unroll
+                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                            if (vk[s] > 0.0) {
+                                double df;
+                                part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
+                                dpart += vk[s] * df;
+                            }
+                        const double gx = warp_sum(part) / V - a;
+                        dpart = warp_sum(dpart);
+                        ++it;
+                        if (fabs(gx) <= POS_TOL) break;
+                        if (gx < 0) A = x; else B = x;
+                        if (B - A <= 1e-15 * (dmax - dmin)) break;
+                        double xn = x - gx * V / dpart;
+                        if (!(xn > A && xn < B)) xn = 0.5 * (A + B);
+                        x = xn;
+                    }
+                } else if (MIXED) {
+                    // ---- alpha within 1e-4 of 0 or 1: FP64 Newton from the corner
+                    // estimate (near an end the fill grows like the cube of the
+                    // distance from the extreme vertex)
+                    double A = dmin, B = dmax;
+                    x = a < 0.5 ? dmin + (dmax - dmin) * cbrt(a) : dmax - (dmax - dmin) * cbrt(1.0 - a);
                     while (it < POS_MAXIT) {
                         double part = 0.0, dpart = 0.0;
 #pragma unroll
@@ -832,15 +849,14 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
         int c = i0 + threadIdx.x;
         bool bad = false;
         if (c < m.nc) {
-            // zero fluxes add nothing (s stays +0): skipped on the integer pipe
             double s = 0.0;
             for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
                 int code = m.cface[k];
                 double x = Va[code >> 1];
-                if (!is_zero(x)) s += (code & 1) ? -x : x;
+                s += (code & 1) ? -x : x;
             }
             double a0 = alpha[c];
-            if (is_zero(s) && dbits(a0) == 0) {
+            if (is_zero(s) && is_pzero(a0)) {
                 zero = true;  // an empty cell with no flux: alpha stays +0
             } else {
                 double V = m.vc[c];
@@ -922,7 +938,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *a
     bool bad = false, zero = false;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
         double a = alpha[c];
-        if (dbits(a) == 0) { zero = true; continue; }  // +0 adds nothing to the mass
+        if (is_pzero(a)) { zero = true; continue; }  // +0 adds nothing to the mass
         v[1] += m.vc[c] * a;
         v[2] = fmin(v[2], a);
         v[3] = fmax(v[3], a);
@@ -1199,18 +1215,27 @@ __global__ void k_zero_int(int *p, int n)
 }
 
 // ============================================== band classification (A2, R9)
-__global__ void k_point_state(DevMesh m, const double *__restrict__ alpha, uint8_t *state)
+// per point: all cells empty (bit 0) / all full (bit 1); for the other points
+// (every point of an interface cell is one) the IDW point value of Eq.
+// idwpointphi, in the order the reconstruction would sum it
+__global__ void k_point_state(DevMesh m, const double *__restrict__ alpha, uint8_t *state, double *palpha)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m.np) return;
     bool all_e = true, all_f = true;
     const double full = 1.0 - m.eps;
-    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) {
+    const int j0 = m.pptr[p], j1 = m.pptr[p + 1];
+    for (int j = j0; j < j1; ++j) {
         double a = __ldg(alpha + m.pcell[j]);
         all_e &= le_pos(a, m.eps);
         all_f &= ge_pos(a, full);
     }
     state[p] = (all_e ? 1 : 0) | (all_f ? 2 : 0);
+    if (!all_e && !all_f) {
+        double ap = 0.0;
+        for (int j = j0; j < j1; ++j) ap += __ldg(m.pw + j) * __ldg(alpha + m.pcell[j]);
+        palpha[p] = ap;
+    }
 }
 
 __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const double *__restrict__ F,
@@ -1224,7 +1249,7 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
         if (i < m.nf) {
             double Ff = F[i];
             double v = 0.0;
-            if (!is_zero(Ff) && !(i >= m.ni && dbits(Ff) < 0)) {
+            if (!is_zero(Ff) && !(i >= m.ni && dbits(Ff).hi < 0)) {
                 unsigned st = 3u;
                 for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) st &= state[m.fpts[k]];
                 if (st & 1u) v = 0.0;
@@ -1299,18 +1324,18 @@ int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, ui
     const bool mx = c->precision == VOF_MIXED;
     if (list) {
         if (mx)
-            k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(c->m, alpha, list, count, n, d, flags, iters,
-                                                              c->counters + CNT_MAXPOS, c->status);
+            k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(c->m, alpha, nullptr, list, count, n, d, flags,
+                                                              iters, c->counters + CNT_MAXPOS, c->status);
         else
-            k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(c->m, alpha, list, count, n, d, flags, iters,
-                                                               c->counters + CNT_MAXPOS, c->status);
+            k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(c->m, alpha, nullptr, list, count, n, d, flags,
+                                                               iters, c->counters + CNT_MAXPOS, c->status);
     } else {
         if (mx)
             k_reconstruct<false, true><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
-                c->m, alpha, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
+                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
         else
             k_reconstruct<false, false><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
-                c->m, alpha, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
+                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
     }
     LAUNCH_CHECK();
     return VOF_OK;
@@ -1400,18 +1425,18 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
 #define MARK(i) do { if (ev) cudaEventRecord(ev[i], s); } while (0)
     MARK(0);
     k_zero_int<<<1, 32, 0, s>>>(cnt, CNT_LEN);
-    k_point_state<<<cdiv(m.np, 256), 256, 0, s>>>(m, alpha, c->pstate);
+    k_point_state<<<cdiv(m.np, 256), 256, 0, s>>>(m, alpha, c->pstate, c->palpha);
     k_classify<<<sms * 16, 256, 0, s>>>(m, alpha, F, dt, c->pstate, c->Va, c->band, cnt + CNT_BAND, c->icell,
                                         cnt + CNT_ICELL, c->status);
     launches += 3;
     LAUNCH_CHECK();
     MARK(1);
     if (c->precision == VOF_MIXED)
-        k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(m, alpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags,
-                                                          nullptr, cnt + CNT_MAXPOS, c->status);
+        k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d,
+                                                          c->flags, nullptr, cnt + CNT_MAXPOS, c->status);
     else
-        k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(m, alpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags,
-                                                           nullptr, cnt + CNT_MAXPOS, c->status);
+        k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n,
+                                                           c->d, c->flags, nullptr, cnt + CNT_MAXPOS, c->status);
     MARK(2);
     k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);

@@ -719,7 +719,7 @@ int launch_setup_mixed(vof_ctx *c, cudaStream_t s)
     k_local_geom<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->cbl);
     k_face_local<<<cdiv(c->nf, 256), 256, 0, s>>>(c->m, c->fpl);
     if (c->ktl)
-        k_cell_tets<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->ctptr, c->ktl);
+        k_cell_tets<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->m.ctptr, c->ktl);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 
@@ -728,7 +728,7 @@ static MXArgs mx_args(vof_ctx *c, const double *alpha, const double *n, const do
                       const int *list, const int *count, const double *disp, unsigned long long *work)
 {
     return MXArgs{alpha, n, d, flags, Up, F, lambda, dt, Va, list, count, disp, c->lam_b, c->status, work,
-                  c->fpl, c->cbl, c->ktl, c->ctptr};
+                  c->fpl, c->cbl, c->ktl, c->m.ctptr};
 }
 
 int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
