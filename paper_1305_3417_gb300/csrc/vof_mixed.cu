@@ -272,60 +272,42 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
     }
 }
 
-// All (T, K) pairs of the buffered candidates.  First lane k marks the
-// polyhedron tetrahedra whose box meets candidate k's box (a bit mask); then
-// the marked pairs are classified 32 at a time, one per lane: a pair inside
-// every plane adds |T| at once, a pair that must be cut becomes a clip job.
+// All (T, K) pairs of the buffered candidates.  First lane k tests candidate
+// k's box against each polyhedron tetrahedron's box, and the overlapping pairs
+// are listed (in the job queue's storage); then they are classified 32 at a
+// time, one per lane: a pair inside every plane adds |T| at once, a pair that
+// must be cut becomes a clip job (written over pairs already read).
 __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
                                          unsigned &npairs, unsigned &ncuts)
 {
     const int lane = threadIdx.x & 31;
-    unsigned tm = 0;
-    if (lane < ncand) {
+    const unsigned lt = (1u << lane) - 1u;
+    int total = 0;
+    {
         float kb[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) kb[q] = sh.Kb[lane][q];
+        for (int q = 0; q < 6; ++q) kb[q] = lane < ncand ? sh.Kb[lane][q] : 0.0f;
         for (int t = 0; t < nt; ++t) {
             const float *tb = sh.Tb[t];
-            if (sh.Tsg[t] != 0.0f && !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] ||
-                                       tb[5] < kb[2] || kb[5] < tb[2]))
-                tm |= 1u << t;
+            const bool ov = lane < ncand && sh.Tsg[t] != 0.0f &&
+                            !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] || tb[5] < kb[2] ||
+                              kb[5] < tb[2]);
+            const unsigned bm = __ballot_sync(0xffffffffu, ov);
+            if (ov) sh.Q[total + __popc(bm & lt)] = (unsigned short)(t | lane << 5);
+            total += __popc(bm);
         }
     }
-    // running pair counts over the candidates (non-decreasing in the lane)
-    const int cnt = __popc(tm);
-    int end = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, end, o);
-        if (lane >= o) end += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, end, 31);
+    __syncwarp();
     int nq = 0;
     for (int pb = 0; pb < total; pb += 32) {
         const int pi = pb + lane;
         bool job = false;
         unsigned code = 0;
-        // candidate of pair pi: the first lane whose end exceeds pi (bisection
-        // over the lanes by shuffles; every lane takes part)
-        int lo = 0, hi = 31;
-#pragma unroll
-        for (int step = 0; step < 5; ++step) {
-            const int mid = (lo + hi) >> 1;
-            const int em = __shfl_sync(0xffffffffu, end, mid);
-            if (em > pi) hi = mid; else lo = mid + 1;
-        }
-        const int k = lo;
-        const unsigned tmk = __shfl_sync(0xffffffffu, tm, k);
-        const int startk = __shfl_sync(0xffffffffu, end - cnt, k);
+        const unsigned pc = pi < total ? sh.Q[pi] : 0u;
+        __syncwarp();  // the batch is read before jobs are written over it
         if (pi < total) {
             ++npairs;
-            // t: the (pi - startk + 1)-th set bit of tmk (bisection on bit counts)
-            const int j = pi - startk;
-            int t = 0;
-#pragma unroll
-            for (int w = 16; w >= 1; w >>= 1)
-                if (__popc(tmk & ((1u << (t + w)) - 1u)) <= j) t += w;
+            const int t = pc & 31, k = pc >> 5;
             const FTet T = ldT(sh.T[t]);
             const int npl = sh.KuseH[k] ? 5 : 4;
             unsigned mask = 0;
@@ -354,7 +336,7 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
             }
         }
         const unsigned bm = __ballot_sync(0xffffffffu, job);
-        if (job) sh.Q[nq + __popc(bm & ((1u << lane) - 1u))] = (unsigned short)code;
+        if (job) sh.Q[nq + __popc(bm & lt)] = (unsigned short)code;
         nq += __popc(bm);
     }
     if (nq > 0) mx_clip(sh, nq, tol, accs, accc, ncuts);
