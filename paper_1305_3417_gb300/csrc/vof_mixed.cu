@@ -186,25 +186,66 @@ __device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin,
     put(FTet{{a0, b0, b1, b2}}, 2);
 }
 
-// The queued clip jobs, worked through by the whole warp: each lane takes a
-// piece (from the top of the stack of pieces, else a new job), clips it by its
-// next plane and pushes the parts that still have planes to go; a piece at its
-// last plane adds its volume below that plane (closed-form cut fraction). All
-// lanes run the same step on different pieces, whatever the depth of a job.
+// The queued clip jobs, worked through by the whole warp, one piece per lane
+// and step.  Pieces with one plane left (leaves) stack up from the bottom of S,
+// the others down from its top, and a step works on one kind only, so that the
+// lanes run the same code:
+//  - leaf step: a piece adds its volume below its last plane (closed-form cut
+//    fraction);
+//  - split step: a piece from the other stack (else a new job) is cut by its
+//    next plane and the parts below are pushed, to the leaves if one plane is
+//    left.
+// A split step commits the longest prefix of lanes that leaves the two stacks
+// at most MX_STACK - 6 full; if none does, the top piece alone when it fits,
+// else a leaf step runs first (leaves need no room).  Every part of a split
+// piece has at most 4 planes to go, so the split pieces keep i + 1 + 2 (r - 1)
+// <= MX_STACK for depth i and r planes to go: the top one alone always fits
+// once the leaves are gone, and the stacks cannot overflow.
 __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &accs, float &accc, unsigned &ncuts)
 {
     const int lane = threadIdx.x & 31;
+    const unsigned le = ((1u << lane) << 1) - 1u;
     __syncwarp();
-    int sp = 0, qn = 0;
+    int nl = 0, nn = 0, qn = 0;
+    bool force_leaf = false;
     for (;;) {
-        const int p = min(sp, 32), r = min(32 - p, nq - qn);
-        if (p + r == 0) break;
+        const bool more = nn > 0 || qn < nq;
+        if (!more && nl == 0) break;
+        if (force_leaf || nl >= 32 || !more) {
+            // ---- leaf step
+            force_leaf = false;
+            const int p = min(nl, 32);
+            if (lane < p) {
+                const FTet t = ldT(sh.S[nl - 1 - lane]);
+                const unsigned meta = sh.Sm[nl - 1 - lane];
+                const int ti = meta & 31, k = (meta >> 5) & 31, j = __ffs(meta >> 10) - 1;
+                float sd[4];
+                int nin, nup;
+                fdist(t, sh.Kp[k][j], tol, sd, nin, nup);
+                float v6 = 0.0f;
+                if (nin > 0) {
+                    v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    if (nup > 0) {
+                        ++ncuts;
+                        float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
+                        fsort4(h0, h1, h2, h3);
+                        v6 *= ffrac_below(h0, h1, h2, h3);
+                    }
+                }
+                if (v6 != 0.0f) two_sum(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
+            }
+            nl -= p;
+            __syncwarp();
+            continue;
+        }
+        // ---- split step
+        const int p = min(nn, 32), r = min(32 - p, nq - qn);
         const bool act = lane < p + r;
         FTet t;
         unsigned meta = 0;
         if (lane < p) {
-            t = ldT(sh.S[sp - 1 - lane]);
-            meta = sh.Sm[sp - 1 - lane];
+            t = ldT(sh.S[MX_STACK - nn + lane]);
+            meta = sh.Sm[MX_STACK - nn + lane];
         } else if (act) {
             meta = sh.Q[qn + lane - p];
             t = ldT(sh.T[meta & 31]);
@@ -220,53 +261,53 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
             rem = meta >> 10;
             const int j = __ffs(rem) - 1;
             rem &= rem - 1;
-            const float4 pl = sh.Kp[k][j];
-            fdist(t, pl, tol, sd, nin, nup);
+            fdist(t, sh.Kp[k][j], tol, sd, nin, nup);
             if (nin > 0) {
-                if (nup == 0) {
-                    if (rem == 0) v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
-                    else nch = 1;
-                } else {
-                    cut = true;
-                    if (rem == 0) {
+                if (nup > 0) cut = true;
+                if (rem != 0) nch = nup == 0 || nin == 1 ? 1 : 3;
+                else {  // a job with one plane: its leaf here
+                    v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    if (nup > 0) {
                         float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
                         fsort4(h0, h1, h2, h3);
-                        v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3])) * ffrac_below(h0, h1, h2, h3);
-                    } else {
-                        nch = nin == 1 ? 1 : 3;
+                        v6 *= ffrac_below(h0, h1, h2, h3);
                     }
                 }
             }
         }
-        // running count of parts over the lanes (nch is 0, 1 or 3): two ballots
+        const bool toleaf = (rem & (rem - 1)) == 0;  // one plane left after this one
         const unsigned b0 = __ballot_sync(0xffffffffu, nch & 1), b1 = __ballot_sync(0xffffffffu, nch & 2);
-        const int inc = __popc(b0 & (((1u << lane) << 1) - 1u)) + 2 * __popc(b1 & (((1u << lane) << 1) - 1u));
-        // Commit the longest prefix of lanes whose parts leave the stack at most
-        // MX_STACK - 6 deep (the rest wait: stack pieces stay where they are,
-        // jobs stay queued); if none does, the top piece alone. Every part has at
-        // most 4 planes to go, so a piece at depth i with r planes to go always
-        // satisfies i + 1 + 2 (r - 1) <= MX_STACK, and the top piece alone always
-        // fits: the stack cannot overflow.
-        const bool fits = act && sp - min(lane + 1, p) + inc <= MX_STACK - 6;
+        const unsigned bl = __ballot_sync(0xffffffffu, toleaf);
+        const int inc = __popc(b0 & le) + 2 * __popc(b1 & le);
+        const bool fits = act && nl + nn - min(lane + 1, p) + inc <= MX_STACK - 6;
         const unsigned fm = __ballot_sync(0xffffffffu, fits);
-        const int L = fm ? 32 - __clz(fm) : 1;
-        const int base = sp - min(L, p);
+        int L = fm ? 32 - __clz(fm) : 0;
+        if (L == 0) {
+            const int nch0 = __shfl_sync(0xffffffffu, nch, 0);
+            if (nl + nn - (p > 0 ? 1 : 0) + nch0 <= MX_STACK) L = 1;
+            else { force_leaf = true; continue; }  // nothing written: the leaves first
+        }
+        const unsigned lm = L >= 32 ? 0xffffffffu : (1u << L) - 1u;
+        const int top = MX_STACK - nn + min(L, p);  // the split stack's top after the pops
         if (lane < L) {
             if (cut) ++ncuts;
             if (v6 != 0.0f) two_sum(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
             if (nch > 0) {
                 const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
-                const int at = base + inc - nch;
+                // parts of the lanes before this one that go the same way
+                const unsigned same = (toleaf ? bl : ~bl) & ((1u << lane) - 1u);
+                const int before = __popc(b0 & same) + 2 * __popc(b1 & same);
                 auto put = [&](const FTet &c, int i) {
-                    stT(sh.S[at + i], c);
-                    sh.Sm[at + i] = (unsigned short)cm;
+                    const int at = toleaf ? nl + before + i : top - 1 - before - i;
+                    stT(sh.S[at], c);
+                    sh.Sm[at] = (unsigned short)cm;
                 };
                 if (nup == 0) put(t, 0);
                 else fsplit(t, sd, nin, put);
             }
         }
-        const unsigned lm = L >= 32 ? 0xffffffffu : (1u << L) - 1u;
-        sp = base + __popc(b0 & lm) + 2 * __popc(b1 & lm);
+        nl += __popc(b0 & bl & lm) + 2 * __popc(b1 & bl & lm);
+        nn = MX_STACK - top + __popc(b0 & ~bl & lm) + 2 * __popc(b1 & ~bl & lm);
         qn += max(0, L - p);
         __syncwarp();
     }
