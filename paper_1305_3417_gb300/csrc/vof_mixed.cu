@@ -94,7 +94,7 @@ struct MXArgs {
 
 constexpr int MX_CAND = 32;    // candidate cell tetrahedra buffered per warp: one per lane
 constexpr int MX_QUEUE = MX_MAXT * MX_CAND;  // clip jobs: one per (T, K) pair at most
-constexpr int MX_STACK = 96;                 // pieces of clip jobs waiting for their next plane
+constexpr int MX_STACK = 92;                 // pieces of clip jobs waiting for their next plane
 
 // per warp; the 48-byte tetrahedra are moved as three float4 (conflict-free
 // across a warp)
@@ -104,7 +104,8 @@ struct __align__(16) MXShared {
     float4 Kp[MX_CAND][5];   // outward unit-normal planes of the candidate cell tetrahedra, then
                              // the cell's phase (or void) half-space; 80-byte rows: a warp's
                              // float4 reads of different rows are conflict-free
-    float Tb[MX_MAXT][6];
+    float4 P6[VOF_MAXFP][5]; // per prism (face triangle swept): a0 a1 a2 b0 b1 b2, 18 floats in 80 bytes
+    float Pb[VOF_MAXFP][6];  // prism box
     float Kb[MX_CAND][6];
     float Tv6[MX_MAXT];      // |6 vol(T)|
     float Tsg[MX_MAXT];      // sign of T in the flux polyhedron
@@ -117,6 +118,7 @@ struct __align__(16) MXShared {
     int Cend[32];            // running count of tetrahedra, inclusive
     unsigned short Sm[MX_STACK];  // piece: t | k << 5 | planes still to clip << 10
     unsigned short Q[MX_QUEUE];   // clip job: t | k << 5 | plane mask << 10
+    unsigned short PQ[VOF_MAXFP * MX_CAND];  // (prism, candidate) pairs with overlapping boxes
     unsigned char KuseH[MX_CAND];
     unsigned char CuseH[32];
 };
@@ -313,28 +315,32 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
     }
 }
 
-// All (T, K) pairs of the buffered candidates.  First lane k tests candidate
-// k's box against each polyhedron tetrahedron's box, and the overlapping pairs
-// are listed (in the job queue's storage); then they are classified 32 at a
-// time, one per lane: a pair inside every plane adds |T| at once, a pair that
-// must be cut becomes a clip job (written over pairs already read).
+// All (T, K) pairs of the buffered candidates, taken a prism (the three
+// tetrahedra of one swept face triangle) at a time.  First lane k tests
+// candidate k's box against each prism's box and the overlapping (prism, K)
+// pairs are listed; then each listed pair, one per lane, gets the signed
+// distances of the prism's six points to K's planes, from which each of its
+// three tetrahedra is classified: outside a plane, inside every plane (adds
+// |T| at once), or a clip job.
 __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
                                          unsigned &npairs, unsigned &ncuts)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
+    const int nprism = nt / 3;
     int total = 0;
     {
         float kb[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) kb[q] = lane < ncand ? sh.Kb[lane][q] : 0.0f;
-        for (int t = 0; t < nt; ++t) {
-            const float *tb = sh.Tb[t];
-            const bool ov = lane < ncand && sh.Tsg[t] != 0.0f &&
+        for (int pr = 0; pr < nprism; ++pr) {
+            const float *tb = sh.Pb[pr];
+            const bool live = sh.Tsg[3 * pr] != 0.0f || sh.Tsg[3 * pr + 1] != 0.0f || sh.Tsg[3 * pr + 2] != 0.0f;
+            const bool ov = lane < ncand && live &&
                             !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] || tb[5] < kb[2] ||
                               kb[5] < tb[2]);
             const unsigned bm = __ballot_sync(0xffffffffu, ov);
-            if (ov) sh.Q[total + __popc(bm & lt)] = (unsigned short)(t | lane << 5);
+            if (ov) sh.PQ[total + __popc(bm & lt)] = (unsigned short)(pr | lane << 3);
             total += __popc(bm);
         }
     }
@@ -342,43 +348,59 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
     int nq = 0;
     for (int pb = 0; pb < total; pb += 32) {
         const int pi = pb + lane;
-        bool job = false;
-        unsigned code = 0;
-        const unsigned pc = pi < total ? sh.Q[pi] : 0u;
-        __syncwarp();  // the batch is read before jobs are written over it
+        unsigned code[3] = {0u, 0u, 0u};
+        bool job[3] = {false, false, false};
         if (pi < total) {
-            ++npairs;
-            const int t = pc & 31, k = pc >> 5;
-            const FTet T = ldT(sh.T[t]);
+            const unsigned pc = sh.PQ[pi];
+            const int pr = pc & 7, k = pc >> 3;
+            npairs += 3;
+            float v[20];
+#pragma unroll
+            for (int i = 0; i < 5; ++i) {
+                const float4 q = sh.P6[pr][i];
+                v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+            }
             const int npl = sh.KuseH[k] ? 5 : 4;
-            unsigned mask = 0;
-            bool outside = false;
-            // a vertex within tol of the plane is on it: the pair is outside when
-            // no vertex is clearly inside a plane, a plane cuts only when vertices
-            // lie clearly on both sides (all planes evaluated: straight-line code)
+            unsigned mask[3] = {0u, 0u, 0u};
+            bool outside[3] = {false, false, false};
+            // a point within tol of a plane is on it: a tetrahedron is outside
+            // when none of its points is clearly inside a plane, and a plane cuts
+            // it only when its points lie clearly on both sides
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
                 const float4 pl = sh.Kp[k][q];
-                float lo = 3e38f, hi = -3e38f;
+                float d[6];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float sd = fmaf(pl.x, T.v[i].x, fmaf(pl.y, T.v[i].y, fmaf(pl.z, T.v[i].z, -pl.w)));
-                    lo = fminf(lo, sd);
-                    hi = fmaxf(hi, sd);
-                }
+                for (int i = 0; i < 6; ++i)
+                    d[i] = fmaf(pl.x, v[3 * i], fmaf(pl.y, v[3 * i + 1], fmaf(pl.z, v[3 * i + 2], -pl.w)));
+                // T0 = a0 a1 a2 b2, T1 = a0 a1 b2 b1, T2 = a0 b0 b1 b2
+                const float l01 = fminf(d[0], d[1]), h01 = fmaxf(d[0], d[1]);
+                const float lo0 = fminf(l01, fminf(d[2], d[5])), hi0 = fmaxf(h01, fmaxf(d[2], d[5]));
+                const float lo1 = fminf(l01, fminf(d[5], d[4])), hi1 = fmaxf(h01, fmaxf(d[5], d[4]));
+                const float lo2 = fminf(fminf(d[0], d[3]), fminf(d[4], d[5])), hi2 = fmaxf(fmaxf(d[0], d[3]), fmaxf(d[4], d[5]));
                 if (q < npl) {
-                    outside |= lo >= -tol;
-                    if (hi > tol) mask |= 1u << q;
+                    outside[0] |= lo0 >= -tol; outside[1] |= lo1 >= -tol; outside[2] |= lo2 >= -tol;
+                    if (hi0 > tol) mask[0] |= 1u << q;
+                    if (hi1 > tol) mask[1] |= 1u << q;
+                    if (hi2 > tol) mask[2] |= 1u << q;
                 }
             }
-            if (!outside) {
-                if (mask == 0) two_sum(accs, accc, sh.Tsg[t] * sh.Kw[k] * sh.Tv6[t]);
-                else { job = true; code = (unsigned)t | ((unsigned)k << 5) | (mask << 10); }
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const int t = 3 * pr + j;
+                const float sg = sh.Tsg[t];
+                if (sg != 0.0f && !outside[j]) {
+                    if (mask[j] == 0) two_sum(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
+                    else { job[j] = true; code[j] = (unsigned)t | ((unsigned)k << 5) | (mask[j] << 10); }
+                }
             }
         }
-        const unsigned bm = __ballot_sync(0xffffffffu, job);
-        if (job) sh.Q[nq + __popc(bm & lt)] = (unsigned short)code;
-        nq += __popc(bm);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const unsigned bm = __ballot_sync(0xffffffffu, job[j]);
+            if (job[j]) sh.Q[nq + __popc(bm & lt)] = (unsigned short)code[j];
+            nq += __popc(bm);
+        }
     }
     if (nq > 0) mx_clip(sh, nq, tol, accs, accc, ncuts);
     __syncwarp();
@@ -490,7 +512,19 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m
             bx[3] = fmaxf(fmaxf(T.v[0].x, T.v[1].x), fmaxf(T.v[2].x, T.v[3].x));
             bx[4] = fmaxf(fmaxf(T.v[0].y, T.v[1].y), fmaxf(T.v[2].y, T.v[3].y));
             bx[5] = fmaxf(fmaxf(T.v[0].z, T.v[1].z), fmaxf(T.v[2].z, T.v[3].z));
-            for (int i = 0; i < 6; ++i) sh.Tb[lane][i] = bx[i];
+            if (j == 0) {
+                float *q = reinterpret_cast<float *>(sh.P6[pr]);
+                const F3 pv[6] = {a0, a1, a2, b0, b1, b2};
+#pragma unroll
+                for (int i = 0; i < 6; ++i) { q[3 * i] = pv[i].x; q[3 * i + 1] = pv[i].y; q[3 * i + 2] = pv[i].z; }
+                float lo3[3] = {3e38f, 3e38f, 3e38f}, hi3[3] = {-3e38f, -3e38f, -3e38f};
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    lo3[0] = fminf(lo3[0], pv[i].x); lo3[1] = fminf(lo3[1], pv[i].y); lo3[2] = fminf(lo3[2], pv[i].z);
+                    hi3[0] = fmaxf(hi3[0], pv[i].x); hi3[1] = fmaxf(hi3[1], pv[i].y); hi3[2] = fmaxf(hi3[2], pv[i].z);
+                }
+                for (int i = 0; i < 3; ++i) { sh.Pb[pr][i] = lo3[i]; sh.Pb[pr][3 + i] = hi3[i]; }
+            }
         }
         // bounding box of the whole polyhedron
         float pb[6];
