@@ -9,6 +9,12 @@ fluxes, update and bounding) with the step's flux F and cell velocity U_c
 already resident in HBM.  Metric: internal face fluxes with final phase volume
 per second (millions), whole job.
 
+--workload batch: the batched form -- independent cases of uneven size (half
+hexahedral boxes n^3, n in [16, 64], half Kuhn-split lattices n in [16, 48],
+each with a random sphere or plane under a solid-body rotation at Courant
+0.3-0.8; --cases, --batch-scale shrinks the size ranges) advanced as one mesh,
+one CUDA-graph launch per step, phase-flux launch shape from the autotuner.
+
 --impl reference times the CPU oracle (test infrastructure) on the host cores
 on the same workload and metric.
 """
@@ -172,6 +178,137 @@ def config(args, w):
             "l2": "inputs larger than L2 (mesh, fluxes and per-step arrays > 129 MB)"}
 
 
+def make_batch(args):
+    from paper_1305_3417_gb300 import inputs as I
+    s = args.batch_scale
+    hr = (max(4, round(16 * s)), max(4, round(64 * s)))
+    tr = (max(3, round(16 * s)), max(3, round(48 * s)))
+    return I.make_batch(args.cases, seed=1304, hex_range=hr, tet_range=tr, steps=50), hr, tr
+
+
+def batch_config(args, b, hr, tr, tune):
+    m = b.mesh
+    nh = sum(c.kind == "hex" for c in b.cases)
+    return {"workload": f"batch: {len(b.cases)} cases ({nh} hex n in {list(hr)}, {len(b.cases) - nh} Kuhn tet n in "
+                        f"{list(tr)}), sphere or plane, solid-body rotation, Co 0.3-0.8, seed 1304 "
+                        f"({m.n_cells} cells, {m.n_internal} internal faces)",
+            "n_cells": m.n_cells, "n_internal_faces": m.n_internal, "precision": "mixed", "cases": len(b.cases),
+            "batch_scale": args.batch_scale, "graph": True, "tuned_config": tune,
+            "l2": "inputs larger than L2" if m.n_cells * 48 > 129e6 else "inputs smaller than L2 (batch scale)"}
+
+
+def batch_cpu_baseline(b, ncase=4):
+    """The oracle on a bounded sample: one step of each of the first ncase cases."""
+    from oracle import oracle as O
+    threads = O.set_threads(os.cpu_count() or 1)
+    faces, t = 0, 0.0
+    for i in range(min(ncase, len(b.cases))):
+        om = O.OracleMesh(b.meshes[i])
+        t0 = time.perf_counter()
+        om.advect(b.alpha_case[i].copy(), b.U_case[i], b.F_case[i], b.cases[i].dt)
+        t += time.perf_counter() - t0
+        faces += b.meshes[i].n_internal
+    return {"value": faces / t / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one oracle step of each of the first {min(ncase, len(b.cases))} cases "
+                      f"({faces} internal faces), {t:.1f} s"}
+
+
+def run_batch(args, world, rank, local):
+    b, hr, tr = make_batch(args)
+    m = b.mesh
+    if args.impl == "reference":
+        if rank == 0:
+            base = batch_cpu_baseline(b, ncase=max(1, args.steps))
+            line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": 1,
+                    "steps": max(1, args.steps), "warmup": 0, "ms_per_step": m.n_internal / base["value"] / 1e3,
+                    "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                    "data": "synthetic", "config": batch_config(args, b, hr, tr, None), "cpu_baseline": base,
+                    "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            print(json.dumps(line), flush=True)
+        return
+    import torch
+    from paper_1305_3417_gb300 import build, vof
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    bt = vof.VofBatch(b, precision=vof.MIXED, device=local)
+    ctx = bt.context()
+    U = torch.from_numpy(b.U_dt.reshape(-1).copy()).to(dev)
+    F = torch.from_numpy(b.F_dt.copy()).to(dev)
+    alpha = torch.from_numpy(b.alpha0.copy()).to(dev)
+    tune, tune_ms = bt.tune(alpha, U, F)
+    mass0 = torch.zeros(len(b.cases), dtype=torch.float64, device=dev)
+    mass = torch.zeros_like(mass0)
+    stats = torch.zeros(vof.S_LEN, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        bt.advect(alpha, U, F, stats, mass0)
+    torch.cuda.synchronize()
+    st0 = vof.vof_status(ctx)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            bt.advect(alpha, U, F, stats, mass)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms_max = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    faces = world * args.steps * m.n_internal
+    value = faces / (ms_max * 1e-3) / 1e6
+    # per-case mass change over the timed steps, against the boundary flux it allows
+    m0, m1 = mass0.cpu().numpy(), mass.cpu().numpy()
+    S = stats.cpu().numpy()
+    st1 = vof.vof_status(ctx)
+    # kernel groups and work (direct launches, profiled; the graph holds the same kernels)
+    pa = alpha.clone()
+    vof.vof_work_counts(ctx, reset=True)
+    vof.vof_profile_begin(ctx, 3)
+    for _ in range(3):
+        vof.vof_advect(ctx, pa, U, F, 1.0, stats)
+    group_ms, nprof = vof.vof_profile_end(ctx)
+    work = vof.vof_work_counts(ctx, reset=True)
+    launches = vof.vof_last_launch_count(ctx) * args.steps
+    per_launch = {g: v / max(nprof, 1) for g, v in group_ms.items()}
+    fl = (work["pairs"] * FLOPS_PER_PAIR + work["cuts"] * FLOPS_PER_CUT) / max(nprof, 1)
+    alu = vof.vof_probe_fma(local, vof.MIXED)
+    achieved = fl / (per_launch["phase_flux"] * 1e-3) / 1e12
+    roof = {"kernel": "k_phase_flux", "bound": "alu", "achieved": achieved, "peak": alu / 1e12, "unit": "TFLOP/s",
+            "frac": achieved * 1e12 / alu, "traffic": None, "peak_source": "measured FP32 FMA probe (vof_probe_fma)",
+            "group_ms_per_step": per_launch}
+    # end to end with host buffers (context's host-buffer step, dt = 1)
+    ha = torch.from_numpy(b.alpha0.copy()).pin_memory()
+    hU, hF = U.cpu().pin_memory(), F.cpu().pin_memory()
+    hstat = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
+    vof.vof_advect_host(ctx, ha, hU, hF, 1.0, hstat)
+    torch.cuda.synchronize()
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        vof.vof_advect_host(ctx, ha, hU, hF, 1.0, hstat)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    e2e = faces / (max_over_ranks(e2.elapsed_time(e3), world, dev) * 1e-3) / 1e6
+    base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        base = batch_cpu_baseline(b, ncase=args.cpu_steps * 4)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": batch_config(args, b, hr, tr, {"config": tune, "ms": tune_ms}),
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * m.n_cells + 24 * m.n_cells + 8 * m.n_faces,
+                        "d2h_bytes_per_step": 8 * m.n_cells + 8 * vof.S_LEN},
+                "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
+                "quality": {"rel_volume_drift_last_step": float(abs(S[1] + S[10] - S[0]) / S[0]),
+                            "case_mass_min": float(m1.min()),
+                            "alpha_min": float(S[4]), "alpha_max": float(S[5]),
+                            "band_faces_last_step": float(S[7]), "status_bits": int(st0 | st1)}}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -185,9 +322,14 @@ def main():
     ap.add_argument("--skip", type=int, default=0, help="untimed steps advanced before warm-up")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cases", type=int, default=256, help="batch workload: number of cases")
+    ap.add_argument("--batch-scale", type=float, default=1.0, help="batch workload: scale of the n ranges")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init(args)
+    if args.workload == "batch":
+        run_batch(args, world, rank, local)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
         return

@@ -123,7 +123,9 @@ int vof_point_velocity(vof_ctx *ctx, const double *Uc, double *Up, void *stream)
  * phase), and the plane offset d with |C ^ {x : n.x <= d}| = alpha |C| found by
  * the secant iteration with bisection fallback (Sec. 2.2.2; stops at a fill
  * residual of 1e-13 or a bracket of 1e-15 of the cell's extent, at most 100
- * iterations).  Outputs (device): n [3*n_cells], d [n_cells], flags [n_cells]
+ * iterations).  A VOF_MIXED context finds the same plane by safeguarded Newton
+ * steps on the fill (the cut area is its derivative), FP32 then FP64, with the
+ * same stop.  Outputs (device): n [3*n_cells], d [n_cells], flags [n_cells]
  * (VOF_INTERFACE / VOF_ORIENTED / VOF_FULL), iters [n_cells] or NULL.  Cells
  * that are not oriented interface cells get n = 0, d = 0. */
 int vof_reconstruct(vof_ctx *ctx, const double *alpha, double *n, double *d, uint8_t *flags,
@@ -175,6 +177,45 @@ int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, d
  * the host arrays must stay valid until the stream reaches the end of it. */
 int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                     double *stats, void *stream);
+
+/* ---- Batched form --------------------------------------------------------
+ * Many independent cases of uneven size advanced together; the paper advances
+ * one case and has no counterpart.  The cases' meshes are joined into one mesh
+ * (disjoint union: concatenated points, cells and faces, the internal faces of
+ * every case first), described by `mesh` as for vof_create, with
+ * case_cell_ptr[ncases + 1] (host) the first cell of each case (0 first,
+ * n_cells last, strictly increasing).  Synchronous; *out receives a batch the
+ * caller releases with vof_batch_destroy.  Errors as vof_create, and
+ * VOF_ERR_INVALID_ARG for bad case offsets. */
+typedef struct vof_batch vof_batch;
+int vof_batch_create(const vof_mesh *mesh, const int32_t *case_cell_ptr, int ncases, const vof_options *opt,
+                     vof_batch **out);
+void vof_batch_destroy(vof_batch *batch);
+
+/* The batch's context (owned by the batch), for the other entry points. */
+vof_ctx *vof_batch_context(vof_batch *batch);
+
+/* One step of every case (A1-A7, as vof_advect) with each case's own time step
+ * folded into its inputs: U_dt [3*n_cells] = U_c dt_case and F_dt [n_faces] =
+ * F_f dt_case (the method uses the field only through these products), so the
+ * step runs with dt = 1.  The step's kernels are captured into a CUDA graph at
+ * the first call (again when an array pointer or the launch configuration
+ * changes) and replayed as one graph launch on an internal stream that is
+ * ordered after, and before, `stream` by events.  stats (device, VOF_S_LEN)
+ * and case_mass (device [ncases]: sum of V alpha per case after the step, in a
+ * fixed order) may be NULL.  Errors: VOF_ERR_INVALID_ARG, VOF_ERR_CUDA. */
+int vof_batch_advect(vof_batch *batch, double *alpha, const double *U_dt, const double *F_dt, double *stats,
+                     double *case_mass, void *stream);
+
+/* Autotuner for the phase-flux launch of a mixed batch: times one step from
+ * the state alpha (left unchanged: the steps run on a copy in the context's
+ * staging buffer) for 1, 2 and 3 warps (faces) per block and grid multipliers
+ * 1, 2 and 4 over the resident blocks, keeps the fastest for later steps, and
+ * returns it as config = 16 * warps + multiplier with its step time in ms
+ * (either pointer may be NULL).  An FP64 batch keeps its launch (config 0).
+ * Synchronous on `stream`. */
+int vof_batch_tune(vof_batch *batch, const double *alpha, const double *U_dt, const double *F_dt, int *config,
+                   float *best_ms, void *stream);
 
 /* Kernel-group timing with CUDA events recorded on the launching stream.
  * vof_profile_begin arms recording for up to max_steps subsequent vof_advect

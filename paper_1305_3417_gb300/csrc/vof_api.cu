@@ -60,6 +60,31 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 
 }  // namespace
 
+// regions of the global bounding step, cut into segments of at most 4096
+// cells; replaces any earlier regions (buffers of earlier calls stay owned by
+// the context until vof_destroy)
+int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg)
+{
+    constexpr int SEG = 4096;
+    std::vector<int4> seg;
+    std::vector<int> rs(1, 0);
+    for (int r = 0; r < nreg; ++r) {
+        for (int a = reg_cell[r]; a < reg_cell[r + 1]; a += SEG)
+            seg.push_back(make_int4(r, a, std::min(a + SEG, reg_cell[r + 1]), 0));
+        rs.push_back((int)seg.size());
+    }
+    if (seg.empty()) seg.push_back(make_int4(0, 0, 0, 0));
+    int err = 0;
+    c->seg = dev_copy(c, seg.data(), seg.size(), &err);
+    c->reg_seg = dev_copy(c, rs.data(), rs.size(), &err);
+    c->gpartial = dev_alloc<double>(c, 4 * seg.size(), &err);
+    c->reg_tot = dev_alloc<double>(c, 4 * (size_t)nreg, &err);
+    if (err) return err;
+    c->nseg = (int)seg.size();
+    c->nreg = nreg;
+    return VOF_OK;
+}
+
 extern "C" {
 
 const char *vof_error_string(int code)
@@ -244,6 +269,16 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         }
     }
     const int nwrows = (int)wptr.size() - 1;
+    // faces with a point on an open boundary face: their flux polyhedra can
+    // reach outside the domain, where the stencil does not cover them
+    std::vector<uint8_t> popen(np, 0), fopen(nf, 0);
+    for (int f = ni; f < nf; ++f)
+        if (mesh->wall && mesh->wall[f - ni] == 0)
+            for (int j = fptr[f]; j < fptr[f + 1]; ++j) popen[fpts[j]] = 1;
+    parallel_for(nf, [&](long f) {
+        for (int j = fptr[f]; j < fptr[f + 1]; ++j)
+            if (popen[fpts[j]]) { fopen[f] = 1; break; }
+    });
     // per cell: offset of its (face, point) entries in face order
     std::vector<int> cfpptr(nc + 1, 0);
     for (int c = 0; c < nc; ++c) {
@@ -300,6 +335,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     m.sptr = dev_copy(c, sptr.data(), sptr.size(), &err);
     m.scell = dev_copy(c, scell.data(), scell.size(), &err);
     m.pwall = dev_copy(c, pwall.data(), pwall.size(), &err);
+    m.fopen = dev_copy(c, fopen.data(), fopen.size(), &err);
     m.wallt = dev_alloc<double>(c, 7 * (size_t)std::max(nwrows, 1), &err);
     int *d_wptr = dev_copy(c, wptr.data(), wptr.size(), &err);
     int *d_wface = dev_copy(c, wface.empty() ? wptr.data() : wface.data(), std::max<size_t>(wface.size(), 1), &err);
@@ -332,7 +368,6 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->Va = dev_alloc<double>(c, nf, &err);
     c->bscr = dev_alloc<double>(c, 8 * (size_t)nc, &err);
     c->dgi = dev_alloc<int>(c, nc, &err);
-    c->gpartial = dev_alloc<double>(c, 4 * 512 + 8, &err);
     c->partial = dev_alloc<double>(c, 10 * 1024, &err);
     c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
     c->status = dev_alloc<unsigned>(c, 1, &err);
@@ -356,6 +391,11 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     cudaMemset(c->n, 0, sizeof(double) * 3 * nc);
     cudaMemset(c->d, 0, sizeof(double) * nc);
     cudaMemset(c->flags, 0, nc);
+    {
+        const int whole[2] = {0, nc};
+        if (!err) err = set_bound_regions(c, whole, 1);
+        if (err) { vof_destroy(c); return err; }
+    }
     int r = launch_setup_geometry(c, 0);
     if (!r) r = launch_wall_table(c, d_wptr, d_wface, nwrows, 0);
     if (!r) r = launch_setup_mixed(c, 0);

@@ -23,6 +23,7 @@ struct DevMesh {
     const double *pw;            // inverse-distance weight per (point, cell) entry
     const int *sptr, *scell;     // face stencil: cells sharing a point with the face
     const int *pwall;            // per point: wall-table row or -1
+    const uint8_t *fopen;        // per face: 1 if a point lies on an open boundary face
     const double *wallt;         // wall table rows: count, n1 (3), n2 (3)
     const double *cf, *sf;       // face centre, area vector [3*nf]
     const double *cc, *vc, *cbox;  // cell centre [3*nc], volume [nc], box [6*nc]
@@ -58,7 +59,14 @@ struct vof_ctx {
     double *Va;
     double *bscr;                // bounding scratch, 8 doubles per cell
     int *dgi;
-    double *gpartial;            // global bounding partial sums
+    double *gpartial;            // global bounding partial sums, 4 per segment
+    // regions of the global bounding step (whole mesh, or the cases of a
+    // batch): segments {region, first cell, end cell, -} and, per region, its
+    // segment range and totals
+    int nseg, nreg;
+    int4 *seg;
+    int *reg_seg;
+    double *reg_tot;
     double *partial;             // reduction partials
     double *stats_dev;           // internal stats buffer
     unsigned *status;
@@ -72,6 +80,9 @@ struct vof_ctx {
     // box, 6 float4, relative to the cell centre (first of each cell: m.ctptr)
     float4 *ktl;
     double *palpha;              // IDW point values of the points that are not all-empty / all-full
+    // mixed phase-flux launch configuration (0: defaults): warps per block 1-3,
+    // grid multiplier over the resident blocks
+    int pf_warps, pf_mult;
     // kernel-group timing (vof_profile_begin / _end)
     cudaEvent_t *prof_ev;
     int prof_max, prof_steps;
@@ -95,6 +106,8 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
 int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad);
 // ---- mixed precision (vof_mixed.cu) ----
 int launch_setup_mixed(vof_ctx *c, cudaStream_t s);
+// regions of the global bounding step: region r = cells [reg_cell[r], reg_cell[r+1]) (host array)
+int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg);
 int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
                                 const uint8_t *flags, const double *Up, const double *F, const double *lambda,
                                 double dt, double *Va, cudaStream_t s);

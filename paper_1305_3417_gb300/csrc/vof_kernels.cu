@@ -1127,19 +1127,21 @@ __global__ void k_bp_apply(double *alpha, const int *pc, const double *pa, const
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alpha[pc[i]] = pa[i];
 }
 
-// Global step for what the local pass leaves: the total excess (deficit) goes
-// to every cell strictly inside (tol, 1-tol) in proportion to its free (phase)
-// volume; sources are set to 1 (0).  Partial sums per block; the last block to
-// finish reduces them in block order (deterministic) into totals[4].
-constexpr int GB_BLOCKS = 512, GB_THREADS = 256;
+// Global step for what the local pass leaves: the total excess (deficit) of a
+// region (the whole mesh, or one case of a batch) goes to every cell of that
+// region strictly inside (tol, 1-tol) in proportion to its free (phase)
+// volume; sources are set to 1 (0).  A region's cells are contiguous and cut
+// into segments; one block sums a segment, then one warp per region sums its
+// segments in order (deterministic).
+constexpr int GB_THREADS = 256;
 
-__global__ void __launch_bounds__(GB_THREADS) k_bound_global_reduce(DevMesh m, const double *alpha,
-                                                                    double *partial, double *totals,
-                                                                    unsigned *done, int *nleft)
+__global__ void __launch_bounds__(GB_THREADS) k_bound_seg_reduce(DevMesh m, const double *alpha, const int4 *seg,
+                                                                 double *spartial, int *nleft)
 {
+    const int4 sg = seg[blockIdx.x];
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // Ep, Em, Sp, Sm
     int left = 0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
+    for (int c = sg.y + threadIdx.x; c < sg.z; c += blockDim.x) {
         double a = alpha[c];
         if (gt_pos(a, 1.0 + BOUND_TOL)) { v[0] += (a - 1.0) * m.vc[c]; ++left; }
         else if (lt_neg(a, BOUND_TOL)) { v[1] += -a * m.vc[c]; ++left; }
@@ -1149,53 +1151,44 @@ __global__ void __launch_bounds__(GB_THREADS) k_bound_global_reduce(DevMesh m, c
             v[3] += a * V;
         }
     }
-    if (left) atomicAdd(nleft, left);
+    left = __reduce_add_sync(0xffffffffu, left);
+    if ((threadIdx.x & 31) == 0 && left) atomicAdd(nleft, left);
     __shared__ double sh[4][GB_THREADS / 32];
-    __shared__ bool last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int i = 0; i < 4; ++i) {
         double x = warp_sum(v[i]);
         if (lane == 0) sh[i][w] = x;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0)
         for (int i = 0; i < 4; ++i) {
             double r = 0.0;
             for (int k = 0; k < GB_THREADS / 32; ++k) r += sh[i][k];
-            partial[4 * blockIdx.x + i] = r;
+            spartial[4 * blockIdx.x + i] = r;
         }
-        __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    // the last block: each thread sums a fixed strided set of block partials,
-    // then the block tree (fixed order: deterministic)
-    __threadfence();
+}
+
+__global__ void k_bound_region_totals(const int *reg_seg, int nreg, const double *spartial, double *totals)
+{
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (r >= nreg) return;
     double t[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += GB_THREADS)
-        for (int i = 0; i < 4; ++i) t[i] += ((volatile double *)partial)[4 * k + i];
-    __syncthreads();
+    for (int k = reg_seg[r] + lane; k < reg_seg[r + 1]; k += 32)
+        for (int i = 0; i < 4; ++i) t[i] += spartial[4 * k + i];
     for (int i = 0; i < 4; ++i) {
         double x = warp_sum(t[i]);
-        if (lane == 0) sh[i][w] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) {
-            double r = 0.0;
-            for (int k = 0; k < GB_THREADS / 32; ++k) r += sh[i][k];
-            totals[i] = r;
-        }
-        *done = 0;
+        if (lane == 0) totals[4 * r + i] = x;
     }
 }
 
-__global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, double *alpha, const double *totals)
+__global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, double *alpha, const int4 *seg,
+                                                                   const double *totals)
 {
-    const double Ep = totals[0], Em = totals[1], Sp = totals[2], Sm = totals[3];
+    const int4 sg = seg[blockIdx.x];
+    const double *tt = totals + 4 * sg.x;
+    const double Ep = tt[0], Em = tt[1], Sp = tt[2], Sm = tt[3];
     if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
+    for (int c = sg.y + threadIdx.x; c < sg.z; c += blockDim.x) {
         double a = alpha[c];
         if (gt_pos(a, 1.0 + BOUND_TOL)) alpha[c] = 1.0;
         else if (lt_neg(a, BOUND_TOL)) alpha[c] = 0.0;
@@ -1381,11 +1374,10 @@ static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches
     k_bp_place<<<g, 128, 0, s>>>(c->m, alpha, b);
     k_bp_new<<<g, 128, 0, s>>>(c->m, alpha, b, npend, c->status);
     k_bp_apply<<<g, 128, 0, s>>>(alpha, c->pend_c, c->pend_a, npend, b.cap_pend);
-    double *totals = c->gpartial + 4 * GB_BLOCKS;
-    k_bound_global_reduce<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, c->gpartial, totals,
-                                                           (unsigned *)(c->counters + 14), c->counters + CNT_VIOL1);
-    k_bound_global_apply<<<GB_BLOCKS, GB_THREADS, 0, s>>>(c->m, alpha, totals);
-    *launches += 8;
+    k_bound_seg_reduce<<<c->nseg, GB_THREADS, 0, s>>>(c->m, alpha, c->seg, c->gpartial, c->counters + CNT_VIOL1);
+    k_bound_region_totals<<<(c->nreg + 3) / 4, 128, 0, s>>>(c->reg_seg, c->nreg, c->gpartial, c->reg_tot);
+    k_bound_global_apply<<<c->nseg, GB_THREADS, 0, s>>>(c->m, alpha, c->seg, c->reg_tot);
+    *launches += 9;
     LAUNCH_CHECK();
     return VOF_OK;
 }

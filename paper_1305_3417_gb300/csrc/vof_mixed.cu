@@ -73,7 +73,6 @@ __device__ __forceinline__ void two_sum(float &s, float &c, float x)
     s = t;
 }
 
-constexpr int MX_WARPS = 2;
 constexpr int MX_MAXT = 3 * VOF_MAXFP;
 static_assert(MX_MAXT <= 32, "one flux-polyhedron tetrahedron per lane");
 
@@ -406,10 +405,13 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
     __syncwarp();
 }
 
-template <bool LIST>
-__global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m, MXArgs a)
+// W warps (faces) per block; blocks per SM as shared memory allows
+constexpr int mx_resident(int w) { return w == 1 ? 15 : w == 2 ? 8 : 5; }
+
+template <bool LIST, int W>
+__global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(DevMesh m, MXArgs a)
 {
-    __shared__ MXShared shm[MX_WARPS];
+    __shared__ MXShared shm[W];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     MXShared &sh = shm[wib];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -445,12 +447,14 @@ __global__ void __launch_bounds__(MX_WARPS * 32, 8) k_phase_flux_mixed(DevMesh m
         // pieces and take V_alpha = F dt - void (equal in exact arithmetic since
         // the corrected polyhedron holds F dt and the stencil covers it); a
         // polyhedron inside full cells then carries exactly F dt, one inside
-        // empty cells exactly 0, and FP32 rounding stays with mixed cells
-        // (not for the normal-sweep fallback, which can leave the domain at walls).
+        // empty cells exactly 0, and FP32 rounding stays with mixed cells.  Not
+        // where the polyhedron can leave the domain (the normal-sweep fallback at
+        // walls; a face touching an open boundary), since the part outside is
+        // empty and the stencil does not cover it.
         const double Ff = a.F[f];
         const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
         const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
-        const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0;
+        const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0 && !__ldg(m.fopen + f);
         const int nt = n == 3 ? 3 : 3 * n;
         // signed distances (to unit-normal planes) within 2e-6 of the face size are
         // taken as zero: points shared by the polyhedron and the cell tetrahedra
@@ -793,7 +797,7 @@ int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n
                                 double dt, double *Va, cudaStream_t s)
 {
     MXArgs a = mx_args(c, alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr, nullptr);
-    k_phase_flux_mixed<false><<<cdiv((long)c->nf * 32, MX_WARPS * 32), MX_WARPS * 32, 0, s>>>(c->m, a);
+    k_phase_flux_mixed<false, 2><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 
@@ -802,6 +806,15 @@ int launch_phase_flux_mixed_list(vof_ctx *c, const double *alpha, const double *
 {
     MXArgs a = mx_args(c, alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band,
                        c->counters + CNT_BAND, c->disp_b, c->work);
-    k_phase_flux_mixed<true><<<sms * 16, MX_WARPS * 32, 0, s>>>(c->m, a);
+    // launch configuration (vof_batch_tune): warps per block, and grid = SMs x
+    // resident blocks x multiplier
+    const int w = c->pf_warps >= 1 && c->pf_warps <= 3 ? c->pf_warps : 2;
+    const int mult = c->pf_mult >= 1 ? c->pf_mult : 2;
+    if (w == 1)
+        k_phase_flux_mixed<true, 1><<<sms * mx_resident(1) * mult, 32, 0, s>>>(c->m, a);
+    else if (w == 2)
+        k_phase_flux_mixed<true, 2><<<sms * mx_resident(2) * mult, 64, 0, s>>>(c->m, a);
+    else
+        k_phase_flux_mixed<true, 3><<<sms * mx_resident(3) * mult, 96, 0, s>>>(c->m, a);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }

@@ -37,6 +37,7 @@ __all__ = [
     "sampled_fraction", "sphere_sdf", "cylinder_sdf", "Field", "translation_field",
     "deformation_field", "single_vortex_field", "rotation_field",
     "face_flux_stokes", "cell_velocity", "Workload", "make_workload",
+    "concat_meshes", "BatchCase", "Batch", "make_batch",
 ]
 
 
@@ -553,3 +554,145 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
         def exact(t, _m=mesh):
             return disc_fraction_2d(_m, 0.5 + t, 0.75 + t, 0.15)
     return Workload(name, mesh, a0, fld, Fs, Us, dt, steps, t_end, exact)
+
+
+# --------------------------------------------------------------------------
+# Batches of independent cases
+# --------------------------------------------------------------------------
+
+def concat_meshes(meshes) -> tuple[Mesh, np.ndarray, np.ndarray]:
+    """Disjoint union of meshes as one mesh in the same form: points and cells
+    of case i follow those of case i-1, the internal faces of every case come
+    first (case order), then the boundary faces.  Returns (mesh, cell offsets
+    (n+1,), point offsets (n+1,))."""
+    cpo = np.zeros(len(meshes) + 1, np.int64)
+    ppo = np.zeros(len(meshes) + 1, np.int64)
+    for i, m in enumerate(meshes):
+        cpo[i + 1] = cpo[i] + m.n_cells
+        ppo[i + 1] = ppo[i] + m.n_points
+    pts = np.concatenate([m.points for m in meshes])
+
+    def faces(sel):
+        ptrs, fps, owns = [], [], []
+        for i, m in enumerate(meshes):
+            f0, f1 = sel(m)
+            a, b = int(m.face_ptr[f0]), int(m.face_ptr[f1])
+            ptrs.append(np.diff(m.face_ptr[f0:f1 + 1]).astype(np.int64))
+            fps.append(m.face_pts[a:b].astype(np.int64) + ppo[i])
+            owns.append(m.owner[f0:f1].astype(np.int64) + cpo[i])
+        return np.concatenate(ptrs), np.concatenate(fps), np.concatenate(owns)
+
+    ci, pi_, oi = faces(lambda m: (0, m.n_internal))
+    cb, pb, ob = faces(lambda m: (m.n_internal, m.n_faces))
+    nei = np.concatenate([m.neighbour.astype(np.int64) + cpo[i] for i, m in enumerate(meshes)])
+    counts = np.concatenate([ci, cb])
+    face_ptr = np.zeros(counts.size + 1, np.int64)
+    np.cumsum(counts, out=face_ptr[1:])
+    wall = np.concatenate([m.wall_flags() for m in meshes]).astype(np.uint8)
+    kinds = {m.kind for m in meshes}
+    cv = None
+    if len({m.cell_verts.shape[1] for m in meshes}) == 1:
+        cv = np.concatenate([m.cell_verts.astype(np.int64) + ppo[i] for i, m in enumerate(meshes)]).astype(np.int32)
+    mesh = Mesh(pts, face_ptr.astype(np.int32), np.concatenate([pi_, pb]).astype(np.int32),
+                np.concatenate([oi, ob]).astype(np.int32), nei.astype(np.int32), int(cpo[-1]),
+                cv, min(m.h for m in meshes), 3, kinds.pop() if len(kinds) == 1 else "mixed", (), wall)
+    return mesh, cpo, ppo
+
+
+@dataclasses.dataclass
+class BatchCase:
+    kind: str            # "hex" or "tet"
+    n: int               # lattice cells per side
+    interface: str       # "sphere" or "plane"
+    centre: np.ndarray
+    radius: float        # sphere radius (plane: 0)
+    normal: np.ndarray   # plane normal (sphere: 0)
+    axis: np.ndarray     # rotation axis (unit)
+    omega: float         # rotation rate (max |U| over the box = 1)
+    co: float
+    dt: float
+
+
+@dataclasses.dataclass
+class Batch:
+    cases: list
+    mesh: Mesh                 # disjoint union of the cases' meshes
+    cell_off: np.ndarray       # (n_cases+1,)
+    alpha0: np.ndarray
+    F_dt: np.ndarray           # F_f dt_case per face (steady fields: every step)
+    U_dt: np.ndarray           # (3, n_cells) U_c dt_case
+    meshes: list               # the cases' own meshes (for per-case checks)
+    F_case: list               # per case: F_f (spatial, unscaled)
+    U_case: list               # per case: (3, n_cells_case)
+    alpha_case: list
+    n_steps: int
+
+
+def make_batch(n_cases: int = 256, seed: int = 1304, hex_range=(16, 64), tet_range=(16, 48),
+               steps: int = 50) -> Batch:
+    """Independent cases of uneven size: half uniform hexahedral boxes with
+    n^3 cells (n uniform on hex_range), half Kuhn-split n^3 lattices (n on
+    tet_range), on [0,1]^3 with open boundaries; each with a sphere (R uniform
+    in [0.1, 0.25], centre within 0.5 - R - 2h of the box centre) or a plane
+    through the box centre, under a solid-body rotation about an axis through
+    the centre (random for a sphere, the plane normal for a plane) scaled so
+    that max |U| over the box is 1, at a Courant number uniform in [0.3, 0.8].
+
+    The step uses a field only through F dt and U dt, so F_dt and U_dt carry
+    each case's own time step and the batch advances with dt = 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cases, meshes, alphas, Fc, Uc = [], [], [], [], []
+    corners = np.array([[i, j, k] for i in (0, 1) for j in (0, 1) for k in (0, 1)], float)
+    for ci in range(n_cases):
+        kind = "hex" if ci % 2 == 0 else "tet"
+        lo, hi = hex_range if kind == "hex" else tet_range
+        n = int(rng.integers(lo, hi + 1))
+        h = 1.0 / n
+        iface = "sphere" if rng.random() < 0.5 else "plane"
+        v = rng.normal(size=3)
+        v /= np.linalg.norm(v)
+        if iface == "sphere":
+            R = float(rng.uniform(0.1, 0.25))
+            reach = max(0.5 - R - 2.0 * h, 0.0)
+            off = rng.uniform(-1.0, 1.0, 3) * reach
+            centre = 0.5 + off
+            axis = rng.normal(size=3)
+            axis /= np.linalg.norm(axis)
+            sdf = sphere_sdf(tuple(centre), R)
+            normal = np.zeros(3)
+        else:
+            R = 0.0
+            centre = np.full(3, 0.5)
+            normal = v
+            axis = v
+
+            def sdf(x, _n=normal):
+                return (x - 0.5) @ _n
+        # max |omega x (x - c)| over the box is at a corner
+        r = corners - 0.5
+        dist = np.sqrt(np.maximum((r * r).sum(1) - (r @ axis) ** 2, 0.0)).max()
+        omega = 1.0 / dist
+        fld = rotation_field(omega * axis)
+        co = float(rng.uniform(0.3, 0.8))
+        hc = h if kind == "hex" else h / 6.0 ** (1.0 / 3.0)
+        dt = co * hc / 1.0
+        if kind == "hex":
+            m = hex_mesh((n, n, n), open_sides=("x-", "x+", "y-", "y+", "z-", "z+"))
+        else:
+            m = kuhn_tet_mesh((n, n, n))
+            m.wall = np.zeros(m.n_faces - m.n_internal, np.uint8)
+        a0 = sampled_fraction(m, sdf)
+        F = face_flux_stokes(m, fld.A)
+        U = cell_velocity(m, fld.u)
+        cases.append(BatchCase(kind, n, iface, centre, R, normal, axis, omega, co, dt))
+        meshes.append(m)
+        alphas.append(a0)
+        Fc.append(F)
+        Uc.append(U)
+    mesh, cpo, _ = concat_meshes(meshes)
+    nif = [m.n_internal for m in meshes]
+    F_int = np.concatenate([Fc[i][:nif[i]] * cases[i].dt for i in range(n_cases)])
+    F_bnd = np.concatenate([Fc[i][nif[i]:] * cases[i].dt for i in range(n_cases)])
+    U_dt = np.concatenate([Uc[i] * cases[i].dt for i in range(n_cases)], axis=1)
+    return Batch(cases, mesh, cpo, np.concatenate(alphas), np.concatenate([F_int, F_bnd]),
+                 np.ascontiguousarray(U_dt), meshes, Fc, Uc, alphas, steps)

@@ -48,7 +48,8 @@ class _Options(ctypes.Structure):
 EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "vof_reconstruct",
            "vof_flux_polyhedra", "vof_correct_flux", "vof_phase_flux", "vof_update", "vof_advect",
            "vof_advect_host", "vof_status", "vof_last_launch_count", "vof_error_string",
-           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma"]
+           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma",
+           "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune"]
 PROF_GROUPS = ["classify", "reconstruct", "correct", "phase_flux", "update"]
 
 _lib = None
@@ -82,6 +83,11 @@ def lib():
         "vof_profile_end": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "vof_work_counts": (I, [P, P, I, P]),
         "vof_probe_fma": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
+        "vof_batch_create": (I, [ctypes.POINTER(_Mesh), P, I, ctypes.POINTER(_Options), ctypes.POINTER(P)]),
+        "vof_batch_destroy": (None, [P]),
+        "vof_batch_context": (P, [P]),
+        "vof_batch_advect": (I, [P, P, P, P, P, P, P]),
+        "vof_batch_tune": (I, [P, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -121,6 +127,54 @@ def _dev(t, dtype, numel, name):
 
 
 # ------------------------------------------------------------------ C names
+
+def _mesh_struct(mesh):
+    """(_Mesh, arrays kept alive) for a paper_1305_3417_gb300.inputs.Mesh."""
+    px, py, pz = (np.ascontiguousarray(v, np.float64) for v in mesh.soa_points())
+    fptr = np.ascontiguousarray(mesh.face_ptr, np.int32)
+    fpts = np.ascontiguousarray(mesh.face_pts, np.int32)
+    own = np.ascontiguousarray(mesh.owner, np.int32)
+    nei = np.ascontiguousarray(mesh.neighbour, np.int32)
+    wall = np.ascontiguousarray(mesh.wall_flags(), np.uint8)
+    m = _Mesh(mesh.n_points, mesh.n_faces, mesh.n_internal, mesh.n_cells,
+              px.ctypes.data, py.ctypes.data, pz.ctypes.data, fptr.ctypes.data, fpts.ctypes.data,
+              own.ctypes.data, nei.ctypes.data if nei.size else None, wall.ctypes.data if wall.size else None)
+    return m, (px, py, pz, fptr, fpts, own, nei, wall)
+
+
+def vof_batch_create(mesh, case_cell_ptr, precision: int = MIXED, eps: float = 1e-9, bound: bool = True,
+                     device: int = 0):
+    """mesh: the joined mesh (inputs.concat_meshes); case_cell_ptr: (ncases+1,) cell offsets."""
+    m, keep = _mesh_struct(mesh)
+    cp = np.ascontiguousarray(case_cell_ptr, np.int32)
+    o = _Options(eps, int(precision), int(bool(bound)), int(device))
+    h = ctypes.c_void_p()
+    _check(lib().vof_batch_create(ctypes.byref(m), cp.ctypes.data, int(cp.size - 1), ctypes.byref(o),
+                                  ctypes.byref(h)), "vof_batch_create")
+    return h
+
+
+def vof_batch_destroy(h):
+    if h:
+        lib().vof_batch_destroy(h)
+
+
+def vof_batch_context(h):
+    return ctypes.c_void_p(lib().vof_batch_context(h))
+
+
+def vof_batch_advect(h, alpha, U_dt, F_dt, stats=None, case_mass=None, stream=None):
+    _check(lib().vof_batch_advect(h, _ptr(alpha), _ptr(U_dt), _ptr(F_dt), _ptr(stats), _ptr(case_mass),
+                                  _stream(stream)), "vof_batch_advect")
+
+
+def vof_batch_tune(h, alpha, U_dt, F_dt, stream=None):
+    """Returns (config = 16*warps + multiplier, step ms)."""
+    cfg, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    _check(lib().vof_batch_tune(h, _ptr(alpha), _ptr(U_dt), _ptr(F_dt), ctypes.byref(cfg), ctypes.byref(ms),
+                                _stream(stream)), "vof_batch_tune")
+    return int(cfg.value), float(ms.value)
+
 
 def vof_create(mesh, precision: int = FP64, eps: float = 1e-9, bound: bool = True, device: int = 0):
     """mesh: paper_1305_3417_gb300.inputs.Mesh (host arrays).  Returns a handle."""
@@ -311,3 +365,40 @@ class VofContext:
 
     def status(self) -> int:
         return vof_status(self.h)
+
+
+class VofBatch:
+    """A batch of cases (inputs.Batch) advanced as one mesh, one graph launch per step."""
+
+    def __init__(self, batch, precision: int = MIXED, eps: float = 1e-9, bound: bool = True, device: int = 0):
+        import torch
+        m = batch.mesh
+        self.nc, self.nf, self.ncases = m.n_cells, m.n_faces, len(batch.cases)
+        self.device = torch.device("cuda", device)
+        self.h = vof_batch_create(m, batch.cell_off, precision, eps, bound, device)
+
+    def close(self):
+        if getattr(self, "h", None):
+            vof_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def context(self):
+        return vof_batch_context(self.h)
+
+    def advect(self, alpha, U_dt, F_dt, stats=None, case_mass=None):
+        import torch
+        _dev(alpha, torch.float64, self.nc, "alpha")
+        _dev(U_dt, torch.float64, 3 * self.nc, "U_dt")
+        _dev(F_dt, torch.float64, self.nf, "F_dt")
+        if case_mass is not None:
+            _dev(case_mass, torch.float64, self.ncases, "case_mass")
+        vof_batch_advect(self.h, alpha, U_dt, F_dt, stats, case_mass)
+
+    def tune(self, alpha, U_dt, F_dt):
+        return vof_batch_tune(self.h, alpha, U_dt, F_dt)
