@@ -217,6 +217,58 @@ int vof_batch_advect(vof_batch *batch, double *alpha, const double *U_dt, const 
 int vof_batch_tune(vof_batch *batch, const double *alpha, const double *U_dt, const double *F_dt, int *config,
                    float *best_ms, void *stream);
 
+/* ---- Learned initial guess of the plane positioning ----------------------
+ * The paper has no learned part.  A small network (VOF_MLP_IN features of an
+ * interface cell -> two ReLU layers of VOF_MLP_HID -> VOF_MLP_OUT outputs: a
+ * unit normal and the offset s = (d - d_min)/(d_max - d_min) of the plane in
+ * the cell's projection range) with BF16 weights and activations and FP32
+ * accumulation on the tensor cores, trained by Adam on the mean squared
+ * error.  In a VOF_MIXED context with a network attached (vof_set_guess) the
+ * Newton positioning of a cell starts from the network's offset (clamped to
+ * [0.02, 0.98]) instead of the linear guess alpha; the root, the stop and the
+ * normal (NAG's) are unchanged, so the plane is the same to the 1e-13 stop.
+ * Parameters: one float array of VOF_MLP_NPARAM values, W1 [IN x HID]
+ * (input-major), b1 [HID], W2 [HID x HID], b2 [HID], W3 [HID x OUT], b3 [OUT].
+ * Features (vof_mlp_features): the volume fractions of the cell's 3x3x3
+ * lattice neighbourhood (cells sharing a point with it, placed by the sign of
+ * their centre offset beyond half the cell size; missing slots take the
+ * cell's own value), then box extents / V^(1/3) (3), V / box volume,
+ * faces / 24, points / 8. */
+#define VOF_MLP_IN 33
+#define VOF_MLP_HID 64
+#define VOF_MLP_OUT 4
+#define VOF_MLP_NPARAM (VOF_MLP_IN * VOF_MLP_HID + VOF_MLP_HID + VOF_MLP_HID * VOF_MLP_HID + VOF_MLP_HID + \
+                        VOF_MLP_HID * VOF_MLP_OUT + VOF_MLP_OUT)
+typedef struct vof_mlp vof_mlp;
+/* A network on `device` with room for batches of up to max_batch (>= 16)
+ * samples, initialised from params (host, VOF_MLP_NPARAM floats).
+ * Synchronous; release with vof_mlp_destroy. */
+int vof_mlp_create(int max_batch, const float *params, int device, vof_mlp **out);
+void vof_mlp_destroy(vof_mlp *mlp);
+/* Copies the current FP32 parameters to params (host).  Synchronous. */
+int vof_mlp_params(vof_mlp *mlp, float *params);
+/* Features of ncells cells (device list `cells`, or cells 0..ncells-1 when
+ * NULL) from alpha (device) into feat (device, [ncells x VOF_MLP_IN]). */
+int vof_mlp_features(vof_ctx *ctx, const double *alpha, const int32_t *cells, int ncells, float *feat,
+                     void *stream);
+/* Forward pass of n (<= max_batch) samples: feat (device [n x IN]) -> out
+ * (device [n x OUT]). */
+int vof_mlp_forward(vof_mlp *mlp, const float *feat, int n, float *out, void *stream);
+/* Forward and backward pass of the mean squared error against target (device
+ * [n x OUT]): gradient (device [VOF_MLP_NPARAM], or NULL) and the loss (host,
+ * or NULL; reading it synchronises `stream`). */
+int vof_mlp_gradient(vof_mlp *mlp, const float *feat, const float *target, int n, float *grad, float *loss,
+                     void *stream);
+/* One Adam step (beta 0.9, 0.999) with learning rate lr on a batch; loss as
+ * vof_mlp_gradient. */
+int vof_mlp_train_step(vof_mlp *mlp, const float *feat, const float *target, int n, float lr, float *loss,
+                       void *stream);
+/* Attaches (mlp) or detaches (NULL) the network whose offsets start the
+ * positioning of vof_advect and vof_reconstruct in a VOF_MIXED context; the
+ * network must live on the context's device and outlive its use.  Allocates
+ * the context's guess buffers the first time (outside any capture). */
+int vof_set_guess(vof_ctx *ctx, vof_mlp *mlp);
+
 /* Kernel-group timing with CUDA events recorded on the launching stream.
  * vof_profile_begin arms recording for up to max_steps subsequent vof_advect
  * calls (creating events, no device memory); vof_profile_end synchronises on

@@ -117,6 +117,8 @@ void vof_destroy(vof_ctx *c)
     cudaSetDevice(c->device);
     free_profile(c);
     for (int i = 0; i < c->nbufs; ++i) cudaFree(c->bufs[i]);
+    cudaFree(c->mlp_s0);
+    cudaFree(c->mlp_feat);
     delete c;
 }
 

@@ -83,6 +83,11 @@ struct vof_ctx {
     // mixed phase-flux launch configuration (0: defaults): warps per block 1-3,
     // grid multiplier over the resident blocks
     int pf_warps, pf_mult;
+    // learned guess of the positioning (vof_set_guess): the network, offsets by
+    // interface-list position, features
+    struct vof_mlp *mlp;
+    float *mlp_s0, *mlp_feat;
+    int mlp_feat_cap;
     // kernel-group timing (vof_profile_begin / _end)
     cudaEvent_t *prof_ev;
     int prof_max, prof_steps;
@@ -108,6 +113,11 @@ int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad);
 int launch_setup_mixed(vof_ctx *c, cudaStream_t s);
 // regions of the global bounding step: region r = cells [reg_cell[r], reg_cell[r+1]) (host array)
 int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg);
+// learned guess (vof_mlp.cu): offsets of the first min(nmax, batch) listed cells
+// (count on the device, or all nmax when count is NULL) into c->mlp_s0
+int launch_mlp_guess(vof_ctx *c, const double *alpha, const int *cells, const int *count, int nmax,
+                     cudaStream_t s);
+int mlp_cap(const vof_ctx *c);
 int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
                                 const uint8_t *flags, const double *Up, const double *F, const double *lambda,
                                 double dt, double *Va, cudaStream_t s);

@@ -186,7 +186,8 @@ template <bool LIST, bool MIXED>
 __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
-                                                     uint8_t *fout, int *itout, int *maxit, unsigned *status)
+                                                     uint8_t *fout, int *itout, int *maxit, unsigned *status,
+                                                     const float *__restrict__ s0, int s0cap)
 {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -263,7 +264,9 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     // ---- FP32 Newton, relative to the cell centre's projection
                     const float Vf = (float)V, af = (float)a;
                     float Ar = (float)(dmin - href), Br = (float)(dmax - href);
-                    float xr = Ar + af * (Br - Ar);
+                    // start: the learned offset where one is given, else alpha
+                    const float sg = (s0 && item < s0cap) ? s0[item] : af;
+                    float xr = Ar + sg * (Br - Ar);
                     int near = 0;
                     while (it < POS_MAXIT) {
                         float part = 0.0f, dpart = 0.0f;
@@ -1315,20 +1318,24 @@ int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, ui
 {
     int sms = num_sms(c->device);
     const bool mx = c->precision == VOF_MIXED;
+    if (mx && c->mlp) {
+        int r = launch_mlp_guess(c, alpha, list, count, c->nc, s);
+        if (r) return r;
+    }
     if (list) {
         if (mx)
             k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(c->m, alpha, nullptr, list, count, n, d, flags,
-                                                              iters, c->counters + CNT_MAXPOS, c->status);
+                                                              iters, c->counters + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
         else
             k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(c->m, alpha, nullptr, list, count, n, d, flags,
-                                                               iters, c->counters + CNT_MAXPOS, c->status);
+                                                               iters, c->counters + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
     } else {
         if (mx)
             k_reconstruct<false, true><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
-                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
+                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status, c->mlp_s0, mlp_cap(c));
         else
             k_reconstruct<false, false><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
-                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status);
+                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status, c->mlp_s0, mlp_cap(c));
     }
     LAUNCH_CHECK();
     return VOF_OK;
@@ -1423,12 +1430,16 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     launches += 3;
     LAUNCH_CHECK();
     MARK(1);
+    if (c->precision == VOF_MIXED && c->mlp) {
+        int r = launch_mlp_guess(c, alpha, c->icell, cnt + CNT_ICELL, c->nc, s);
+        if (r) return r;
+    }
     if (c->precision == VOF_MIXED)
         k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d,
-                                                          c->flags, nullptr, cnt + CNT_MAXPOS, c->status);
+                                                          c->flags, nullptr, cnt + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
     else
         k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n,
-                                                           c->d, c->flags, nullptr, cnt + CNT_MAXPOS, c->status);
+                                                           c->d, c->flags, nullptr, cnt + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
     MARK(2);
     k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);

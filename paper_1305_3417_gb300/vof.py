@@ -49,7 +49,11 @@ EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "v
            "vof_flux_polyhedra", "vof_correct_flux", "vof_phase_flux", "vof_update", "vof_advect",
            "vof_advect_host", "vof_status", "vof_last_launch_count", "vof_error_string",
            "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma",
-           "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune"]
+           "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
+           "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
+           "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess"]
+MLP_IN, MLP_HID, MLP_OUT = 33, 64, 4
+MLP_NPARAM = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
 PROF_GROUPS = ["classify", "reconstruct", "correct", "phase_flux", "update"]
 
 _lib = None
@@ -88,6 +92,14 @@ def lib():
         "vof_batch_context": (P, [P]),
         "vof_batch_advect": (I, [P, P, P, P, P, P, P]),
         "vof_batch_tune": (I, [P, P, P, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), P]),
+        "vof_mlp_create": (I, [I, P, I, ctypes.POINTER(P)]),
+        "vof_mlp_destroy": (None, [P]),
+        "vof_mlp_params": (I, [P, P]),
+        "vof_mlp_features": (I, [P, P, P, I, P, P]),
+        "vof_mlp_forward": (I, [P, P, I, P, P]),
+        "vof_mlp_gradient": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_float), P]),
+        "vof_mlp_train_step": (I, [P, P, P, I, ctypes.c_float, ctypes.POINTER(ctypes.c_float), P]),
+        "vof_set_guess": (I, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -402,3 +414,62 @@ class VofBatch:
 
     def tune(self, alpha, U_dt, F_dt):
         return vof_batch_tune(self.h, alpha, U_dt, F_dt)
+
+
+class Mlp:
+    """The initial-guess network (BF16 tensor-core forward/backward, Adam)."""
+
+    def __init__(self, params, max_batch: int = 1 << 16, device: int = 0):
+        p = np.ascontiguousarray(params, np.float32)
+        if p.size != MLP_NPARAM:
+            raise VofError(f"expected {MLP_NPARAM} parameters, got {p.size}")
+        self.max_batch, self.device = int(max_batch), device
+        self.h = ctypes.c_void_p()
+        _check(lib().vof_mlp_create(self.max_batch, p.ctypes.data, int(device), ctypes.byref(self.h)),
+               "vof_mlp_create")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vof_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_NPARAM, np.float32)
+        _check(lib().vof_mlp_params(self.h, out.ctypes.data), "vof_mlp_params")
+        return out
+
+    def forward(self, feat):
+        import torch
+        n = feat.shape[0]
+        out = torch.empty((n, MLP_OUT), dtype=torch.float32, device=feat.device)
+        _check(lib().vof_mlp_forward(self.h, _ptr(feat), int(n), _ptr(out), _stream(None)), "vof_mlp_forward")
+        return out
+
+    def gradient(self, feat, target):
+        import torch
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device=feat.device)
+        loss = ctypes.c_float(0.0)
+        _check(lib().vof_mlp_gradient(self.h, _ptr(feat), _ptr(target), int(feat.shape[0]), _ptr(g),
+                                      ctypes.byref(loss), _stream(None)), "vof_mlp_gradient")
+        return float(loss.value), g
+
+    def train_step(self, feat, target, lr: float) -> float:
+        loss = ctypes.c_float(0.0)
+        _check(lib().vof_mlp_train_step(self.h, _ptr(feat), _ptr(target), int(feat.shape[0]), float(lr),
+                                        ctypes.byref(loss), _stream(None)), "vof_mlp_train_step")
+        return float(loss.value)
+
+
+def vof_mlp_features(h, alpha, cells, n, feat, stream=None):
+    _check(lib().vof_mlp_features(h, _ptr(alpha), _ptr(cells), int(n), _ptr(feat), _stream(stream)),
+           "vof_mlp_features")
+
+
+def vof_set_guess(h, mlp):
+    _check(lib().vof_set_guess(h, mlp.h if mlp is not None else None), "vof_set_guess")

@@ -1,0 +1,139 @@
+"""Learned initial guess of the plane positioning.
+
+The tensor-core forward and backward passes are checked against the plain
+FP64 reference network in oracle/mlp_ref.py run on the same BF16-rounded
+operands; the features against a host computation; the training targets
+(from the FP64 GPU reconstruction) against the oracle's own reconstruction;
+and the trained network against the method without it: fewer positioning
+iterations, the same planes (fill residual within the 1e-13 stop, checked by
+the oracle's clipper) and the same step.
+"""
+import numpy as np
+import pytest
+
+from paper_1305_3417_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1305_3417_gb300 import build
+    build.build()
+    return torch
+
+
+def _params(seed):
+    from oracle import mlp_ref as M
+    rng = np.random.default_rng(seed)
+    p = np.zeros(M.N_PARAM)
+    o = 0
+    for s in M.SHAPES:
+        n = int(np.prod(s))
+        p[o:o + n] = rng.normal(0.0, (2.0 / s[0]) ** 0.5 if len(s) == 2 else 0.1, n)
+        o += n
+    return p.astype(np.float32).astype(np.float64)
+
+
+def test_mlp_forward_matches_reference(torch):
+    from oracle import mlp_ref as M
+    from paper_1305_3417_gb300 import vof
+    p = _params(3)
+    rng = np.random.default_rng(4)
+    X = rng.uniform(0.0, 1.2, (203, M.N_IN)).astype(np.float32)
+    net = vof.Mlp(p, max_batch=256)
+    Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    Yr, _ = M.forward(p, X.astype(np.float64))
+    err = np.abs(Y - Yr).max() / np.abs(Yr).max()
+    print(f"forward: max |dY| / max |Y| = {err:.2e}")
+    assert err < 1e-2
+
+
+def test_mlp_gradient_matches_reference(torch):
+    from oracle import mlp_ref as M
+    from paper_1305_3417_gb300 import vof
+    p = _params(5)
+    rng = np.random.default_rng(6)
+    X = rng.uniform(0.0, 1.2, (700, M.N_IN)).astype(np.float32)
+    T = rng.normal(0.0, 1.0, (700, M.N_OUT)).astype(np.float32)
+    net = vof.Mlp(p, max_batch=1024)
+    loss, g = net.gradient(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    lr, gr = M.backward(p, X.astype(np.float64), T.astype(np.float64))
+    g = g.cpu().numpy()
+    rel = np.linalg.norm(g - gr) / np.linalg.norm(gr)
+    print(f"gradient: |dg| / |g| = {rel:.2e}, loss {loss:.6f} vs {lr:.6f}")
+    assert abs(loss - lr) <= 1e-4 * abs(lr)
+    assert rel < 1e-2
+    big = np.abs(gr) > 0.1 * np.abs(gr).max()
+    assert np.all(np.abs(g[big] - gr[big]) <= 2e-2 * np.abs(gr[big]))
+
+
+def test_mlp_features(torch):
+    from paper_1305_3417_gb300 import vof
+    m = I.hex_mesh((6, 5, 4), jitter=0.15, seed=8)
+    a = np.random.default_rng(9).uniform(0, 1, m.n_cells)
+    ctx = vof.VofContext(m, precision=1)
+    f = torch.empty((m.n_cells, vof.MLP_IN), dtype=torch.float32, device="cuda")
+    vof.vof_mlp_features(ctx.h, torch.from_numpy(a).cuda(), None, m.n_cells, f)
+    f = f.cpu().numpy()
+    nx, ny, nz = m.shape
+    for c in [0, 7, 33, m.n_cells - 1, 61]:
+        i, j, k = c % nx, (c // nx) % ny, c // (nx * ny)
+        want = np.full(27, a[c])
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    ii, jj, kk = i + dx, j + dy, k + dz
+                    if 0 <= ii < nx and 0 <= jj < ny and 0 <= kk < nz:
+                        want[(dx + 1) + 3 * (dy + 1) + 9 * (dz + 1)] = a[ii + nx * (jj + ny * kk)]
+        np.testing.assert_allclose(f[c, :27], want.astype(np.float32), rtol=0, atol=0)
+        assert f[c, 31] == pytest.approx(6 / 24) and f[c, 32] == pytest.approx(1.0)
+
+
+def test_mlp_training_gain(torch, oracle_lib):
+    from paper_1305_3417_gb300 import mlp, vof
+    m = I.hex_mesh((24, 24, 24), jitter=0.2, seed=11)
+    c64 = vof.VofContext(m, precision=0)
+    train_f = mlp.random_fields(m, 24, seed=12)
+    test_f = mlp.random_fields(m, 4, seed=13)
+    X, Y = mlp.samples(c64, m, train_f)
+    # targets: the FP64 GPU reconstruction is the oracle's
+    om = oracle_lib.OracleMesh(m)
+    on, od, ofl, _, _ = om.reconstruct(train_f[0])
+    cells = np.flatnonzero(ofl & oracle_lib.ORIENTED)[:200]
+    Xc, Yc = mlp.samples(c64, m, train_f[:1])
+    pts = m.points[m.cell_verts[cells]]
+    proj = np.einsum("ckd,dc->ck", pts, on[:, cells])
+    s = (od[cells] - proj.min(1)) / (proj.max(1) - proj.min(1))
+    allc = np.flatnonzero(ofl & oracle_lib.ORIENTED)
+    pos = np.searchsorted(allc, cells)
+    Yc = Yc.cpu().numpy()
+    assert np.abs(Yc[pos, :3] - on[:, cells].T).max() < 1e-6      # FP32 targets
+    assert np.abs(Yc[pos, 3] - s).max() < 1e-6
+    # training lowers the loss
+    net = vof.Mlp(mlp.init_params(1306), max_batch=1 << 15)
+    hist = mlp.train(net, X, Y, epochs=25, batch=2048, lr=3e-3)
+    print("training loss", hist[0], "->", hist[-1])
+    assert hist[-1] < 0.2 * hist[0]
+    # the guess saves iterations; the planes and the step are the method's
+    c32 = vof.VofContext(m, precision=1)
+    tot0 = tot1 = 0
+    for a in test_f:
+        ta = torch.from_numpy(a).cuda()
+        n0_, d0, fl0, it0 = (t.cpu().numpy() for t in c32.reconstruct(ta))
+        vof.vof_set_guess(c32.h, net)
+        n1, d1, fl1, it1 = (t.cpu().numpy() for t in c32.reconstruct(ta))
+        vof.vof_set_guess(c32.h, None)
+        assert np.array_equal(fl0, fl1) and np.array_equal(n0_, n1)
+        ori = np.flatnonzero(fl1 & 2)
+        tot0 += int(it0[ori].sum())
+        tot1 += int(it1[ori].sum())
+        nn = n1.reshape(3, -1)
+        _, vc, _, _ = om.geometry()
+        for c in ori[:: max(1, ori.size // 60)]:
+            g = om.cut_volume(c, nn[:, c], d1[c]) / vc[c] - a[c]
+            assert abs(g) <= 3e-13, (c, g)
+    print(f"positioning iterations without / with the network: {tot0} / {tot1}")
+    assert tot1 < tot0

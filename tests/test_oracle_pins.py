@@ -513,3 +513,33 @@ def test_conservation_and_boundedness_tet_vortex(oracle_lib):
         assert stats[S["min_post"]] >= -1e-12 and stats[S["max_post"]] <= 1 + 1e-12
         assert a.min() >= -1e-12 and a.max() <= 1 + 1e-12
     assert worst_pre > 1e-3  # the pass had real work to do
+
+
+# ---------------------------------------------------------------- MLP reference
+def test_mlp_reference_gradient_by_central_differences():
+    """The reference backward pass (real-valued network, no BF16 rounding)
+    equals central differences of its loss."""
+    from oracle import mlp_ref as M
+    rng = np.random.default_rng(31)
+    p = rng.normal(0.0, 0.3, M.N_PARAM)
+    X = rng.uniform(0.0, 1.0, (7, M.N_IN))
+    T = rng.normal(0.0, 1.0, (7, M.N_OUT))
+    _, g = M.backward(p, X, T, quant=False)
+    idx = rng.choice(M.N_PARAM, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(M.N_PARAM)
+        e[i] = h
+        fd = (M.loss(p + e, X, T, quant=False) - M.loss(p - e, X, T, quant=False)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_mlp_reference_bf16_rounding():
+    """BF16 rounding: exact for values with 8 significant bits, ties to even."""
+    from oracle import mlp_ref as M
+    x = np.array([1.0, 1.0 + 2 ** -7, 1.0 + 2 ** -8, 1.0 + 3 * 2 ** -8, -2.5, 0.0])
+    r = M.bf16(x)
+    assert r[0] == 1.0 and r[1] == 1.0 + 2 ** -7     # representable
+    assert r[2] == 1.0                                  # tie -> even (down)
+    assert r[3] == 1.0 + 2 ** -6                        # tie -> even (up)
+    assert r[4] == -2.5 and r[5] == 0.0
