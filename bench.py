@@ -174,8 +174,38 @@ def config(args, w):
     return {"workload": f"{w.name}: {m.shape[0]}x{m.shape[1]}x{m.shape[2]} {m.kind} mesh "
                         f"({m.n_cells} cells, {m.n_internal} internal faces), jitter, {w.field.name} field, Co 0.5",
             "n_cells": m.n_cells, "n_internal_faces": m.n_internal, "precision": args.precision,
-            "skip_steps": args.skip, "dt": w.dt,
+            "learned_guess": bool(args.mlp), "skip_steps": args.skip, "dt": w.dt,
             "l2": "inputs larger than L2 (mesh, fluxes and per-step arrays > 129 MB)"}
+
+
+def train_guess(device):
+    """The initial-guess network trained on seeded sphere/plane fields of a
+    48^3 jittered hexahedral mesh (targets from the FP64 reconstruction)."""
+    import torch
+    from paper_1305_3417_gb300 import inputs as I, mlp, vof
+    t0 = time.perf_counter()
+    m = I.hex_mesh((48, 48, 48), jitter=0.2, seed=21)
+    c64 = vof.VofContext(m, precision=vof.FP64, device=device)
+    X, Y = mlp.samples(c64, m, mlp.random_fields(m, 40, seed=22))
+    net = vof.Mlp(mlp.init_params(1306), max_batch=1 << 17, device=device)
+    hist = mlp.train(net, X, Y, epochs=30, batch=4096, lr=3e-3)
+    torch.cuda.synchronize()
+    return {"net": net, "samples": int(X.shape[0]), "loss_first": hist[0], "loss_last": hist[-1],
+            "train_s": time.perf_counter() - t0}
+
+
+def positioning_iterations(ctx, alpha, net):
+    """Mean positioning iterations per oriented interface cell, without and
+    with the network, on the state alpha (vof_reconstruct)."""
+    from paper_1305_3417_gb300 import vof
+    out = []
+    for q in (None, net):
+        vof.vof_set_guess(ctx.h, q)
+        _, _, fl, it = ctx.reconstruct(alpha)
+        sel = (fl & 2) != 0
+        out.append(float(it[sel].double().mean()))
+    vof.vof_set_guess(ctx.h, net)
+    return out
 
 
 def make_batch(args):
@@ -323,6 +353,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--cases", type=int, default=256, help="batch workload: number of cases")
+    ap.add_argument("--mlp", action="store_true", help="learned initial guess of the positioning (trained first)")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="batch workload: scale of the n ranges")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -343,6 +374,10 @@ def main():
     m = w.mesh
     prec = vof.MIXED if args.precision == "mixed" else vof.FP64
     ctx = vof.VofContext(m, precision=prec, device=local)
+    learned = None
+    if args.mlp and prec == vof.MIXED:
+        learned = train_guess(local)
+        vof.vof_set_guess(ctx.h, learned["net"])
     total = args.skip + args.warmup + args.steps
     # per-step inputs resident in HBM before the timed region
     Fs = torch.from_numpy(w.F_spatial).to(dev)
@@ -453,6 +488,12 @@ def main():
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base, _ = cpu_baseline(w, steps=args.cpu_steps)
+    guess = None
+    if learned is not None:
+        it0, it1 = positioning_iterations(ctx, alpha, learned["net"])
+        guess = {"iterations_per_cell_plain": it0, "iterations_per_cell_learned": it1,
+                 "train_samples": learned["samples"], "train_loss": [learned["loss_first"], learned["loss_last"]],
+                 "train_s": learned["train_s"]}
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -461,6 +502,7 @@ def main():
                 "data": "synthetic", "config": config(args, w),
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "other_form": other,
+                "learned_guess": guess,
                 "clocks": clk.summary(),
                 "quality": {"max_rel_volume_drift": float(drift), "alpha_min": float(S[:, 4].min()),
                             "alpha_max": float(S[:, 5].max()), "alpha_min_pre_bound": float(S[:, 2].min()),

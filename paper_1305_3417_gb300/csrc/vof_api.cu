@@ -119,6 +119,8 @@ void vof_destroy(vof_ctx *c)
     for (int i = 0; i < c->nbufs; ++i) cudaFree(c->bufs[i]);
     cudaFree(c->mlp_s0);
     cudaFree(c->mlp_feat);
+    cudaFree(c->mlp_nbr);
+    cudaFree(c->mlp_geo);
     delete c;
 }
 
@@ -240,12 +242,9 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         std::sort(stmp.begin() + o, stmp.begin() + o + k);
         scount[f] = (int)(std::unique(stmp.begin() + o, stmp.begin() + o + k) - (stmp.begin() + o));
     });
-    std::vector<int> sptr(nf + 1, 0);
-    for (int f = 0; f < nf; ++f) {
-        long v = (long)sptr[f] + scount[f];
-        if (v > 0x7fffffffL) return VOF_ERR_BAD_MESH;
-        sptr[f + 1] = (int)v;
-    }
+    // 64-bit offsets: a large batch of tetrahedral cases holds billions of entries
+    std::vector<long long> sptr(nf + 1, 0);
+    for (int f = 0; f < nf; ++f) sptr[f + 1] = sptr[f] + scount[f];
     std::vector<int> scell(sptr[nf]);
     parallel_for(nf, [&](long f) {
         std::copy(stmp.begin() + soff[f], stmp.begin() + soff[f] + scount[f], scell.begin() + sptr[f]);

@@ -21,7 +21,8 @@ struct DevMesh {
     const int *cpptr, *cpts;     // cell -> distinct points (ascending)
     const int *pptr, *pcell;     // point -> cells (ascending)
     const double *pw;            // inverse-distance weight per (point, cell) entry
-    const int *sptr, *scell;     // face stencil: cells sharing a point with the face
+    const long long *sptr;       // face stencil: cells sharing a point with the face
+    const int *scell;
     const int *pwall;            // per point: wall-table row or -1
     const uint8_t *fopen;        // per face: 1 if a point lies on an open boundary face
     const double *wallt;         // wall table rows: count, n1 (3), n2 (3)
@@ -88,6 +89,8 @@ struct vof_ctx {
     struct vof_mlp *mlp;
     float *mlp_s0, *mlp_feat;
     int mlp_feat_cap;
+    int *mlp_nbr;                // per cell: 27 lattice-slot cell indices (-1: itself)
+    float *mlp_geo;              // per cell: 6 shape numbers
     // kernel-group timing (vof_profile_begin / _end)
     cudaEvent_t *prof_ev;
     int prof_max, prof_steps;

@@ -643,12 +643,12 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
     const double eps = m.eps;
     for (int item = warp; item < total; item += nwarps) {
         const int f = LIST ? a.list[item] : item;
-        const int s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
+        const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
         if (!LIST) {
             // trivial faces (reading R9) and boundary inflow
             double Ff = a.F[f];
             bool all_e = true, all_f = true;
-            for (int s = s0 + lane; s < s1; s += 32) {
+            for (long long s = s0 + lane; s < s1; s += 32) {
                 double al = a.alpha[__ldg(m.scell + s)];
                 all_e &= al <= eps;
                 all_f &= al >= 1.0 - eps;
@@ -721,7 +721,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
         // ---- (tetrahedron, stencil cell) pairs over the lanes
         double acc = 0.0;
         unsigned npairs = 0, ncuts = 0;
-        const int ns = s1 - s0, nitems = nt * ns;
+        const int ns = (int)(s1 - s0), nitems = nt * ns;
         for (int w = lane; w < nitems; w += 32) {
             const int t = w % nt, c = __ldg(m.scell + s0 + w / nt);
             const double sg = sSg[wib][t];
@@ -1313,11 +1313,37 @@ int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t
     return VOF_OK;
 }
 
+// defaults of every cell (n = 0, d = 0, flags FULL or 0, iterations 0), and
+// the interface cells appended to a list
+__global__ void k_fill_list(int nc, double eps, const double *__restrict__ alpha, double *n, double *d,
+                            uint8_t *flags, int *iters, int *list, int *count, unsigned *status)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    bool isint = false;
+    if (c < nc) {
+        const double a = alpha[c];
+        flags[c] = a >= 1.0 - eps ? VOF_FULL : 0;
+        n[c] = 0.0; n[nc + c] = 0.0; n[2 * nc + c] = 0.0;
+        d[c] = 0.0;
+        if (iters) iters[c] = 0;
+        isint = a > eps && a < 1.0 - eps;
+    }
+    warp_append(isint, c, list, count, nc, status);
+}
+
 int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8_t *flags, int *iters,
                        const int *list, const int *count, cudaStream_t s)
 {
     int sms = num_sms(c->device);
     const bool mx = c->precision == VOF_MIXED;
+    if (mx && c->mlp && !list) {
+        // the guess is indexed by list position: list the interface cells first
+        k_zero_int<<<1, 32, 0, s>>>(c->counters + CNT_ICELL, 1);
+        k_fill_list<<<cdiv(c->nc, 256), 256, 0, s>>>(c->nc, c->eps, alpha, n, d, flags, iters, c->icell,
+                                                     c->counters + CNT_ICELL, c->status);
+        list = c->icell;
+        count = c->counters + CNT_ICELL;
+    }
     if (mx && c->mlp) {
         int r = launch_mlp_guess(c, alpha, list, count, c->nc, s);
         if (r) return r;
@@ -1433,6 +1459,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     if (c->precision == VOF_MIXED && c->mlp) {
         int r = launch_mlp_guess(c, alpha, c->icell, cnt + CNT_ICELL, c->nc, s);
         if (r) return r;
+        ++launches;
     }
     if (c->precision == VOF_MIXED)
         k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d,

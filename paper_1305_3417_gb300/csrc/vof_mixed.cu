@@ -420,11 +420,11 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
     const double eps = m.eps;
     for (int item = warp; item < total; item += nwarps) {
         const int f = LIST ? a.list[item] : item;
-        const int s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
+        const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
         if (!LIST) {
             double Ff = a.F[f];
             bool all_e = true, all_f = true;
-            for (int s = s0 + lane; s < s1; s += 32) {
+            for (long long s = s0 + lane; s < s1; s += 32) {
                 double al = a.alpha[__ldg(m.scell + s)];
                 all_e &= al <= eps;
                 all_f &= al >= 1.0 - eps;
@@ -552,14 +552,15 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
         // buffer. A batch that does not fit is produced again after the buffer
         // has been processed, so that the buffer is processed at one place and
         // no candidate is held across it.
-        int sc = s0 - 32, tb = 0, ntot = 0, ncell = 0;
+        long long sc = s0 - 32;
+        int tb = 0, ntot = 0, ncell = 0;
         for (;;) {
             if (tb >= ntot) {  // the chunk's tetrahedra are done: next chunk
                 sc += 32;
                 tb = 0;
                 ntot = 0;
                 if (sc < s1) {
-                    const int s = sc + lane;
+                    const long long s = sc + lane;
                     bool pass = false;
                     int c = 0;
                     double al = 0.0;

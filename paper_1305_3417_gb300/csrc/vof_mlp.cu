@@ -290,12 +290,118 @@ __global__ void k_mlp_adam(float *p, const float *g, float *m1, float *m2, float
     p[i] -= lr * (m / c1) / (sqrtf(v / c2) + 1e-8f);
 }
 
-// offsets from the network's last output, clamped inside the bracket
-__global__ void k_mlp_guess(const float *Y, int ncap, const int *ndev, float *s0)
+
+
+// Per cell, once (vof_set_guess): the 27 lattice slots as cell indices (-1:
+// the cell itself) and the 6 shape numbers, as vof_mlp_features places them
+__global__ void k_mlp_tables(DevMesh m, int *nbr, float *geo)
 {
-    const int n = ndev ? min(*ndev, ncap) : ncap;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        s0[i] = fminf(fmaxf(Y[(size_t)i * OUTP + 3], 0.02f), 0.98f);
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= m.nc) return;
+    int *t = nbr + 27 * (size_t)c;
+    for (int k = 0; k < 27; ++k) t[k] = -1;
+    const double V = m.vc[c], h = cbrt(V);
+    const vofd::V3 cc = vofd::ld3(m.cc, m.nc, c);
+    for (int j = m.cpptr[c]; j < m.cpptr[c + 1]; ++j) {
+        const int p = m.cpts[j];
+        for (int q = m.pptr[p]; q < m.pptr[p + 1]; ++q) {
+            const int nb = m.pcell[q];
+            const vofd::V3 d = vofd::ld3(m.cc, m.nc, nb) - cc;
+            const int sx = (d.x > 0.5 * h) - (d.x < -0.5 * h), sy = (d.y > 0.5 * h) - (d.y < -0.5 * h),
+                      sz = (d.z > 0.5 * h) - (d.z < -0.5 * h);
+            t[(sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)] = nb;
+        }
+    }
+    const double *bx = m.cbox + 6 * (size_t)c;
+    const double ex = bx[3] - bx[0], ey = bx[4] - bx[1], ez = bx[5] - bx[2];
+    float *g = geo + 6 * (size_t)c;
+    g[0] = (float)(ex / h);
+    g[1] = (float)(ey / h);
+    g[2] = (float)(ez / h);
+    g[3] = (float)(V / (ex * ey * ez));
+    g[4] = (float)((m.cptr[c + 1] - m.cptr[c]) / 24.0);
+    g[5] = (float)((m.cpptr[c + 1] - m.cpptr[c]) / 8.0);
+}
+
+// The guess of a step in one kernel: one warp per 16 listed cells gathers
+// their features straight into the tensor-core operand layout (from the
+// tables), runs the three layers chaining each layer's accumulators into the
+// next layer's operands in registers, and writes the clamped offsets.
+__global__ void __launch_bounds__(128) k_mlp_guess_fused(const int *nbr, const float *geo,
+                                                          const double *__restrict__ alpha, const int *list,
+                                                          const int *count, int cap, const bf *W1t, const bf *W2t,
+                                                          const bf *W3t, const float *p, float *s0)
+{
+    const int n = min(*count, cap);
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int wstride = (gridDim.x * blockDim.x) >> 5;
+    for (int r0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 16; r0 < n; r0 += wstride * 16) {
+        // feature (row r, column k) of the tile
+        const int ra = r0 + g, rb = r0 + g + 8;
+        const int ca = ra < n ? list[ra] : -1, cb = rb < n ? list[rb] : -1;
+        auto feat = [&](int c, int k) -> bf {
+            if (c < 0 || k >= IN) return (bf)0;
+            if (k < 27) {
+                const int q = nbr[27 * (size_t)c + k];
+                return to_bf((float)alpha[q < 0 ? c : q]);
+            }
+            return to_bf(geo[6 * (size_t)c + (k - 27)]);
+        };
+        // layer 1: [16 x 48] . [48 x 64]
+        float h1[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h1[j][0] = h1[j][1] = h1[j][2] = h1[j][3] = 0.0f;
+#pragma unroll
+        for (int k0 = 0; k0 < K0; k0 += 16) {
+            const uint32_t a0 = pk(feat(ca, k0 + 2 * t), feat(ca, k0 + 2 * t + 1));
+            const uint32_t a1 = pk(feat(cb, k0 + 2 * t), feat(cb, k0 + 2 * t + 1));
+            const uint32_t a2 = pk(feat(ca, k0 + 2 * t + 8), feat(ca, k0 + 2 * t + 9));
+            const uint32_t a3 = pk(feat(cb, k0 + 2 * t + 8), feat(cb, k0 + 2 * t + 9));
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bf *bt = W1t + (size_t)(8 * j + g) * K0 + k0 + 2 * t;
+                mma16816(h1[j], a0, a1, a2, a3, pk(bt[0], bt[1]), pk(bt[8], bt[9]));
+            }
+        }
+        // bias, ReLU, BF16: the accumulators of two n-tiles form one k-step of
+        // the next layer's operand
+        auto act = [&](float (*h)[4], const float *bias, int kk, uint32_t &a0, uint32_t &a1, uint32_t &a2,
+                       uint32_t &a3) {
+            const int c0 = 16 * kk + 2 * t, c1 = c0 + 8;
+            a0 = pk(to_bf(fmaxf(h[2 * kk][0] + bias[c0], 0.f)), to_bf(fmaxf(h[2 * kk][1] + bias[c0 + 1], 0.f)));
+            a1 = pk(to_bf(fmaxf(h[2 * kk][2] + bias[c0], 0.f)), to_bf(fmaxf(h[2 * kk][3] + bias[c0 + 1], 0.f)));
+            a2 = pk(to_bf(fmaxf(h[2 * kk + 1][0] + bias[c1], 0.f)),
+                    to_bf(fmaxf(h[2 * kk + 1][1] + bias[c1 + 1], 0.f)));
+            a3 = pk(to_bf(fmaxf(h[2 * kk + 1][2] + bias[c1], 0.f)),
+                    to_bf(fmaxf(h[2 * kk + 1][3] + bias[c1 + 1], 0.f)));
+        };
+        float h2[8][4];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) h2[j][0] = h2[j][1] = h2[j][2] = h2[j][3] = 0.0f;
+#pragma unroll
+        for (int kk = 0; kk < HID / 16; ++kk) {
+            uint32_t a0, a1, a2, a3;
+            act(h1, p + OB1, kk, a0, a1, a2, a3);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const bf *bt = W2t + (size_t)(8 * j + g) * HID + 16 * kk + 2 * t;
+                mma16816(h2[j], a0, a1, a2, a3, pk(bt[0], bt[1]), pk(bt[8], bt[9]));
+            }
+        }
+        float y[4] = {0.f, 0.f, 0.f, 0.f};  // output columns 0..7 (the offset is column 3)
+#pragma unroll
+        for (int kk = 0; kk < HID / 16; ++kk) {
+            uint32_t a0, a1, a2, a3;
+            act(h2, p + OB2, kk, a0, a1, a2, a3);
+            const bf *bt = W3t + (size_t)g * HID + 16 * kk + 2 * t;
+            mma16816(y, a0, a1, a2, a3, pk(bt[0], bt[1]), pk(bt[8], bt[9]));
+        }
+        if (t == 1) {  // column 2t + 1 = 3
+            const float b3 = p[OB3 + 3];
+            if (ra < n) s0[ra] = fminf(fmaxf(y[1] + b3, 0.02f), 0.98f);
+            if (rb < n) s0[rb] = fminf(fmaxf(y[3] + b3, 0.02f), 0.98f);
+        }
+    }
 }
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
@@ -364,18 +470,17 @@ int mlp_pack(vof_mlp *q, cudaStream_t s)
 
 }  // namespace
 
-// the reconstruction guess of a step: features of the first max_batch listed
-// interface cells (device count), the forward pass, and their clamped offsets
-// by list position in c->mlp_s0
+// the reconstruction guess of a step: for the first max_batch listed
+// interface cells (device count), the clamped offsets by list position in
+// c->mlp_s0 (one fused kernel)
 int launch_mlp_guess(vof_ctx *c, const double *alpha, const int *cells, const int *count, int nmax, cudaStream_t s)
 {
     vof_mlp *q = c->mlp;
     if (!q) return VOF_OK;
     const int cap = std::min(q->max_batch, nmax);
-    k_mlp_features<<<std::min(cdiv(cap, 128), 1024), 128, 0, s>>>(c->m, alpha, cells, cap, count, c->mlp_feat);
-    int r = mlp_forward(q, c->mlp_feat, cap, count, s);
-    if (r) return r;
-    k_mlp_guess<<<std::min(cdiv(cap, 256), 1024), 256, 0, s>>>(q->Y, cap, count, c->mlp_s0);
+    if (!cells || !count) return VOF_ERR_INVALID_ARG;
+    k_mlp_guess_fused<<<std::min(cdiv(cap, 64), 1024), 128, 0, s>>>(c->mlp_nbr, c->mlp_geo, alpha, cells, count,
+                                                                     cap, q->W1t, q->W2t, q->W3t, q->p, c->mlp_s0);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 
@@ -509,6 +614,13 @@ int vof_set_guess(vof_ctx *c, vof_mlp *q)
     if (!c) return VOF_ERR_INVALID_ARG;
     if (cudaSetDevice(c->device) != cudaSuccess) return VOF_ERR_CUDA;
     if (q && q->device != c->device) return VOF_ERR_INVALID_ARG;
+    if (q && !c->mlp_nbr) {
+        if (cudaMalloc(&c->mlp_nbr, sizeof(int) * 27 * (size_t)c->nc) != cudaSuccess ||
+            cudaMalloc(&c->mlp_geo, sizeof(float) * 6 * (size_t)c->nc) != cudaSuccess)
+            return VOF_ERR_CUDA;
+        k_mlp_tables<<<cdiv(c->nc, 128), 128>>>(c->m, c->mlp_nbr, c->mlp_geo);
+        if (cudaDeviceSynchronize() != cudaSuccess) return VOF_ERR_CUDA;
+    }
     if (q && c->mlp_feat_cap < q->max_batch) {
         // guess and feature buffers for the network's batch (kept until vof_destroy)
         cudaFree(c->mlp_s0);
