@@ -174,7 +174,10 @@ int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, d
 /* vof_advect with HOST arrays (pinned memory gives full copy speed): copies
  * alpha, Uc, F to the context's device buffers, runs the step, copies alpha
  * (and stats, VOF_S_LEN doubles, if not NULL) back.  Asynchronous on `stream`;
- * the host arrays must stay valid until the stream reaches the end of it. */
+ * the host arrays must stay valid until the stream reaches the end of it.  The
+ * Uc copy runs on an internal stream (created with two events at the first
+ * call), after all earlier work on `stream` and before the flux correction,
+ * so that it overlaps the classification and the reconstruction. */
 int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                     double *stats, void *stream);
 

@@ -121,6 +121,9 @@ void vof_destroy(vof_ctx *c)
     cudaFree(c->mlp_feat);
     cudaFree(c->mlp_nbr);
     cudaFree(c->mlp_geo);
+    if (c->s_copy) cudaStreamDestroy(c->s_copy);
+    if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+    if (c->ev_u) cudaEventDestroy(c->ev_u);
     delete c;
 }
 
@@ -485,11 +488,20 @@ int vof_advect_host(vof_ctx *c, double *alpha, const double *Uc, const double *F
     if (!c || !alpha || !Uc || !F || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(c->h_Uc, Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
+    // alpha and F first (classification and reconstruction need them); the
+    // cell velocities on a second stream, overlapping those kernels, after
+    // everything earlier on `stream` (the previous step still reads them)
+    if (!c->s_copy && (cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking) ||
+                       cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) ||
+                       cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming)))
+        return VOF_ERR_CUDA;
+    if (cudaEventRecord(c->ev_ready, s) || cudaStreamWaitEvent(c->s_copy, c->ev_ready, 0) ||
+        cudaMemcpyAsync(c->h_Uc, Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->s_copy) ||
+        cudaEventRecord(c->ev_u, c->s_copy) ||
+        cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
         cudaMemcpyAsync(c->h_F, F, sizeof(double) * c->nf, cudaMemcpyHostToDevice, s))
         return VOF_ERR_CUDA;
-    int r = launch_advect(c, c->h_alpha, c->h_Uc, c->h_F, dt, c->stats_dev, s);
+    int r = launch_advect(c, c->h_alpha, c->h_Uc, c->h_F, dt, c->stats_dev, s, c->ev_u);
     if (r) return r;
     if (cudaMemcpyAsync(alpha, c->h_alpha, sizeof(double) * c->nc, cudaMemcpyDeviceToHost, s)) return VOF_ERR_CUDA;
     if (stats && cudaMemcpyAsync(stats, c->stats_dev, sizeof(double) * VOF_S_LEN, cudaMemcpyDeviceToHost, s))

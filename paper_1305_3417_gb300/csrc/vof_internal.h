@@ -72,6 +72,8 @@ struct vof_ctx {
     double *stats_dev;           // internal stats buffer
     unsigned *status;
     double *h_alpha, *h_Uc, *h_F;  // device staging for vof_advect_host
+    cudaStream_t s_copy;           // vof_advect_host: the velocity copy overlaps the first kernels
+    cudaEvent_t ev_ready, ev_u;
     int launches;
     unsigned long long *work;    // [3] phase-flux work counters
     // FP32 geometry for the mixed kernels
@@ -110,7 +112,8 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
                           const double *lambda, double dt, double *Va, cudaStream_t s);
 int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cudaStream_t s);
 int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt,
-                  double *stats, cudaStream_t s);
+                  double *stats, cudaStream_t s,
+                  cudaEvent_t wait_before_correct = nullptr);
 int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad);
 // ---- mixed precision (vof_mixed.cu) ----
 int launch_setup_mixed(vof_ctx *c, cudaStream_t s);

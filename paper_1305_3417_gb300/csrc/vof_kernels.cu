@@ -1439,7 +1439,7 @@ int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cu
 }
 
 int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt, double *stats,
-                  cudaStream_t s)
+                  cudaStream_t s, cudaEvent_t wait_before_correct)
 {
     DevMesh &m = c->m;
     int sms = num_sms(c->device);
@@ -1468,6 +1468,8 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
         k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n,
                                                            c->d, c->flags, nullptr, cnt + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
     MARK(2);
+    // the first use of Uc: a velocity copy in flight on another stream ends here
+    if (wait_before_correct && cudaStreamWaitEvent(s, wait_before_correct, 0) != cudaSuccess) return VOF_ERR_CUDA;
     k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);
     MARK(3);
