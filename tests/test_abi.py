@@ -57,3 +57,25 @@ def test_binding_fails_loudly_when_library_missing(monkeypatch):
     monkeypatch.setattr(vof, "LIB_PATH", "/nonexistent/libvof.so")
     with pytest.raises(vof.VofError):
         vof.lib()
+
+
+def test_batch_and_network_reject_bad_arguments_without_gpu():
+    """The batch and network entry points check their arguments on the host
+    before any device work: bad case offsets, a batch size below one tile."""
+    import numpy as np
+    from paper_1305_3417_gb300 import build, vof
+    build.build()
+    L = vof.lib()
+    h = ctypes.c_void_p()
+    m = vof._Mesh(0, 0, 0, 8, None, None, None, None, None, None, None, None)
+    o = vof._Options(1e-9, 1, 1, 0)
+    for off in ([0, 4, 4, 8], [1, 8], [0, 7], [0, 9, 8]):   # empty case, bad first/last, decreasing
+        cp = np.asarray(off, np.int32)
+        assert L.vof_batch_create(ctypes.byref(m), cp.ctypes.data, cp.size - 1, ctypes.byref(o),
+                                  ctypes.byref(h)) == -1, off
+    assert L.vof_batch_create(ctypes.byref(m), None, 1, ctypes.byref(o), ctypes.byref(h)) == -1
+    p = np.zeros(vof.MLP_NPARAM, np.float32)
+    assert L.vof_mlp_create(8, p.ctypes.data, 0, ctypes.byref(h)) == -1          # below 16 samples
+    assert L.vof_mlp_create(64, None, 0, ctypes.byref(h)) == -1
+    assert L.vof_batch_advect(None, None, None, None, None, None, None) == -1
+    assert L.vof_set_guess(None, None) == -1

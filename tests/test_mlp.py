@@ -137,3 +137,25 @@ def test_mlp_training_gain(torch, oracle_lib):
             assert abs(g) <= 3e-13, (c, g)
     print(f"positioning iterations without / with the network: {tot0} / {tot1}")
     assert tot1 < tot0
+
+
+def test_guess_batch_smaller_than_interface(torch):
+    """A network whose batch is smaller than the interface list guesses the
+    first cells only; every plane is still the method's (same flags and
+    normals, offsets within the positioning stop), and detaching restores the
+    plain start exactly."""
+    from paper_1305_3417_gb300 import mlp, vof
+    m = I.hex_mesh((20, 20, 20), jitter=0.2, seed=31)
+    a = mlp.random_fields(m, 1, seed=32)[0]
+    ctx = vof.VofContext(m, precision=1)
+    ta = torch.from_numpy(a).cuda()
+    n0, d0, f0, i0 = (t.cpu().numpy() for t in ctx.reconstruct(ta))
+    assert int((f0 & 2).sum()) > 64
+    net = vof.Mlp(mlp.init_params(7), max_batch=64)
+    vof.vof_set_guess(ctx.h, net)
+    n1, d1, f1, i1 = (t.cpu().numpy() for t in ctx.reconstruct(ta))
+    vof.vof_set_guess(ctx.h, None)
+    n2, d2, f2, i2 = (t.cpu().numpy() for t in ctx.reconstruct(ta))
+    assert np.array_equal(f0, f1) and np.array_equal(n0, n1)
+    assert np.abs(d1 - d0).max() < 1e-11 * m.h
+    assert np.array_equal(d2, d0) and np.array_equal(i2, i0)
