@@ -86,6 +86,7 @@ struct vof_ctx {
     // mixed phase-flux launch configuration (0: defaults): warps per block 1-3,
     // grid multiplier over the resident blocks
     int pf_warps, pf_mult;
+    int rc_g;                    // reconstruction lanes per cell: 8 if every cell has <= 16 tetrahedra, else 32
     // learned guess of the positioning (vof_set_guess): the network, offsets by
     // interface-list position, features
     struct vof_mlp *mlp;

@@ -182,16 +182,34 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // step that leaves the bracket is replaced by bisection.  Other cells, and
 // the plain FP64 form, follow Alg. 1 (secant, bisection once the secant
 // leaves the bracket).
-template <bool LIST, bool MIXED>
+// G lanes per cell: 32, or 8 where every cell has at most 16 tetrahedra (a
+// tetrahedral mesh: four cells per warp); reductions over the cell's lanes
+template <bool LIST, bool MIXED, int G>
 __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
                                                      uint8_t *fout, int *itout, int *maxit, unsigned *status,
                                                      const float *__restrict__ s0, int s0cap)
 {
-    const int lane = threadIdx.x & 31;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const int lane = threadIdx.x & (G - 1);
+    const unsigned tm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1));
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+    const int nwarps = (gridDim.x * blockDim.x) / G;
+    auto tsum = [&](double v) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(tm, v, o);
+        return v;
+    };
+    auto tmin = [&](double v) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(tm, v, o));
+        return v;
+    };
+    auto tmax = [&](double v) {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(tm, v, o));
+        return v;
+    };
     const int total = LIST ? *count : m.nc;
     const double eps = m.eps;
     for (int item = warp; item < total; item += nwarps) {
@@ -207,7 +225,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
             const double V = m.vc[c];
             // ---- NAG gradient: lane j handles the j-th (face, point) entry
             V3 g = mk(0, 0, 0);
-            for (int j = __ldg(m.ceptr + c) + lane, e1 = __ldg(m.ceptr + c + 1); j < e1; j += 32) {
+            for (int j = __ldg(m.ceptr + c) + lane, e1 = __ldg(m.ceptr + c + 1); j < e1; j += G) {
                 const int2 en = __ldg(m.cent + j);  // {fpts slot, face code}
                 const int f = en.y >> 1, p = __ldg(m.fpts + en.x);
                 double ap = 0.0;  // Eq. idwpointphi (precomputed per point when palpha is given)
@@ -219,7 +237,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                 if (en.y & 1) w = -w;  // Eq. own-nei: the neighbour sees -S_f
                 g = g + ld3(m.sf, m.nf, f) * w;
             }
-            g = mk(warp_sum(g.x), warp_sum(g.y), warp_sum(g.z)) * (1.0 / V);
+            g = mk(tsum(g.x), tsum(g.y), tsum(g.z)) * (1.0 / V);
             double gm = norm3(g);
             if (gm * cbrt(V) > 1e-12) {
                 nn = g * (-1.0 / gm);  // points out of the phase
@@ -236,7 +254,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     h[s][0] = h[s][1] = h[s][2] = h[s][3] = 0.0;
                     vkf[s] = 0.0f;
                     hf[s][0] = hf[s][1] = hf[s][2] = hf[s][3] = 0.0f;
-                    const int tj = __ldg(m.ctptr + c) + lane + 32 * s;
+                    const int tj = __ldg(m.ctptr + c) + lane + G * s;
                     if (tj >= __ldg(m.ctptr + c + 1)) continue;
                     const int4 te = __ldg(m.ctet + tj);  // {face code, slot a, slot b, slot c or -1}
                     V3 t0, t1, t2;
@@ -258,7 +276,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                     lo = fmin(lo, e0);
                     hi = fmax(hi, e3);
                 }
-                const double dmin = warp_min(lo), dmax = warp_max(hi);
+                const double dmin = tmin(lo), dmax = tmax(hi);
                 double x = 0.0;
                 if (MIXED && a > 1e-4 && a < 1.0 - 1e-4) {
                     // ---- FP32 Newton, relative to the cell centre's projection
@@ -278,9 +296,9 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                                 dpart += vkf[s] * df;
                             }
 #pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            part += __shfl_xor_sync(0xffffffffu, part, o);
-                            dpart += __shfl_xor_sync(0xffffffffu, dpart, o);
+                        for (int o = G / 2; o > 0; o >>= 1) {
+                            part += __shfl_xor_sync(tm, part, o);
+                            dpart += __shfl_xor_sync(tm, dpart, o);
                         }
                         ++it;
                         const float gf = part / Vf - af;
@@ -309,8 +327,8 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                                 part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
                                 dpart += vk[s] * df;
                             }
-                        const double gx = warp_sum(part) / V - a;
-                        dpart = warp_sum(dpart);
+                        const double gx = tsum(part) / V - a;
+                        dpart = tsum(dpart);
                         ++it;
                         if (fabs(gx) <= POS_TOL) break;
                         if (gx < 0) A = x; else B = x;
@@ -334,8 +352,8 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                                 part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
                                 dpart += vk[s] * df;
                             }
-                        const double gx = warp_sum(part) / V - a;
-                        dpart = warp_sum(dpart);
+                        const double gx = tsum(part) / V - a;
+                        dpart = tsum(dpart);
                         ++it;
                         if (fabs(gx) <= POS_TOL) break;
                         if (gx < 0) A = x; else B = x;
@@ -358,7 +376,7 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
 #pragma unroll
                         for (int s = 0; s < VOF_MAXK_LANE; ++s)
                             if (vk[s] > 0.0) part += vk[s] * frac_below(h[s][0], h[s][1], h[s][2], h[s][3], x);
-                        gx = warp_sum(part) / V - a;
+                        gx = tsum(part) / V - a;
                         ++it;
                         if (gx < 0) A = x; else B = x;
                         x0 = x1; g0 = g1; x1 = x; g1 = gx;
@@ -1313,6 +1331,23 @@ int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t
     return VOF_OK;
 }
 
+// reconstruction launch with the context's lanes per cell (8 or 32)
+template <bool LIST, bool MIXED>
+static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const double *palpha, const int *list,
+                      const int *count, double *n, double *d, uint8_t *flags, int *iters, int *maxit,
+                      cudaStream_t s)
+{
+    if (c->rc_g == 8) {
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 256);
+        k_reconstruct<LIST, MIXED, 8><<<blocks, 256, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+                                                             maxit, c->status, c->mlp_s0, mlp_cap(c));
+    } else {
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 256);
+        k_reconstruct<LIST, MIXED, 32><<<blocks, 256, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+                                                              maxit, c->status, c->mlp_s0, mlp_cap(c));
+    }
+}
+
 // defaults of every cell (n = 0, d = 0, flags FULL or 0, iterations 0), and
 // the interface cells appended to a list
 __global__ void k_fill_list(int nc, double eps, const double *__restrict__ alpha, double *n, double *d,
@@ -1350,18 +1385,16 @@ int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, ui
     }
     if (list) {
         if (mx)
-            k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(c->m, alpha, nullptr, list, count, n, d, flags,
-                                                              iters, c->counters + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
+            rc_launch<true, true>(c, sms * 8, alpha, nullptr, list, count, n, d, flags, iters,
+                                  c->counters + CNT_MAXPOS, s);
         else
-            k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(c->m, alpha, nullptr, list, count, n, d, flags,
-                                                               iters, c->counters + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
+            rc_launch<true, false>(c, sms * 8, alpha, nullptr, list, count, n, d, flags, iters,
+                                   c->counters + CNT_MAXPOS, s);
     } else {
         if (mx)
-            k_reconstruct<false, true><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
-                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status, c->mlp_s0, mlp_cap(c));
+            rc_launch<false, true>(c, 0, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, s);
         else
-            k_reconstruct<false, false><<<cdiv((long)c->nc * 32, 256), 256, 0, s>>>(
-                c->m, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, c->status, c->mlp_s0, mlp_cap(c));
+            rc_launch<false, false>(c, 0, alpha, nullptr, nullptr, nullptr, n, d, flags, iters, nullptr, s);
     }
     LAUNCH_CHECK();
     return VOF_OK;
@@ -1462,11 +1495,11 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
         ++launches;
     }
     if (c->precision == VOF_MIXED)
-        k_reconstruct<true, true><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d,
-                                                          c->flags, nullptr, cnt + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
+        rc_launch<true, true>(c, sms * 8, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
+                              cnt + CNT_MAXPOS, s);
     else
-        k_reconstruct<true, false><<<sms * 8, 256, 0, s>>>(m, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n,
-                                                           c->d, c->flags, nullptr, cnt + CNT_MAXPOS, c->status, c->mlp_s0, mlp_cap(c));
+        rc_launch<true, false>(c, sms * 8, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
+                               cnt + CNT_MAXPOS, s);
     MARK(2);
     // the first use of Uc: a velocity copy in flight on another stream ends here
     if (wait_before_correct && cudaStreamWaitEvent(s, wait_before_correct, 0) != cudaSuccess) return VOF_ERR_CUDA;
