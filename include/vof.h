@@ -167,17 +167,23 @@ int vof_update(vof_ctx *ctx, double *alpha, const double *Valpha, double *stats,
  * reconstruction of interface cells, point velocities and flux correction of
  * band faces, phase fluxes, update.  alpha [n_cells] in/out, Uc [3*n_cells]
  * cell velocity at the step midpoint, F [n_faces] volumetric flux averaged over
- * the step (discretely divergence-free, Eq. discretedivergence), dt > 0. */
+ * the step (discretely divergence-free, Eq. discretedivergence), dt > 0.
+ * The flux correction runs on a second stream of the context, beside the
+ * reconstruction, forked from and joined back into `stream` (also under CUDA
+ * graph capture); `stream` orders the whole step as one unit. */
 int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                double *stats, void *stream);
 
 /* vof_advect with HOST arrays (pinned memory gives full copy speed): copies
  * alpha, Uc, F to the context's device buffers, runs the step, copies alpha
  * (and stats, VOF_S_LEN doubles, if not NULL) back.  Asynchronous on `stream`;
- * the host arrays must stay valid until the stream reaches the end of it.  The
- * Uc copy runs on an internal stream (created with two events at the first
- * call), after all earlier work on `stream` and before the flux correction,
- * so that it overlaps the classification and the reconstruction. */
+ * the host arrays must stay valid until the stream reaches the end of it.
+ * alpha is copied in order on `stream`.  Uc and F are copied on an internal
+ * stream (created with four events at the first call) into one of two device
+ * buffer pairs, alternating by call, as soon as the step two calls back is
+ * done: the copies of consecutive calls overlap the previous step's kernels,
+ * so Uc and F must hold this step's values when the call is made (they are not
+ * ordered after earlier work on `stream`). */
 int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                     double *stats, void *stream);
 
@@ -277,7 +283,8 @@ int vof_set_guess(vof_ctx *ctx, vof_mlp *mlp);
  * calls (creating events, no device memory); vof_profile_end synchronises on
  * the last event and returns, per group, the summed milliseconds over the
  * recorded steps: [0] band classification, [1] reconstruction, [2] flux
- * correction, [3] phase flux, [4] update, bounding and statistics; *steps
+ * correction (the time it adds after the reconstruction, beside which it
+ * runs), [3] phase flux, [4] update, bounding and statistics; *steps
  * receives the number of steps recorded.  Recording stops at max_steps. */
 enum { VOF_PROF_GROUPS = 5 };
 int vof_profile_begin(vof_ctx *ctx, int max_steps);

@@ -122,8 +122,13 @@ void vof_destroy(vof_ctx *c)
     cudaFree(c->mlp_nbr);
     cudaFree(c->mlp_geo);
     if (c->s_copy) cudaStreamDestroy(c->s_copy);
-    if (c->ev_ready) cudaEventDestroy(c->ev_ready);
+    if (c->ev_f) cudaEventDestroy(c->ev_f);
     if (c->ev_u) cudaEventDestroy(c->ev_u);
+    for (int i = 0; i < 2; ++i)
+        if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+    if (c->s_aux) cudaStreamDestroy(c->s_aux);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
@@ -171,6 +176,11 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
             cface[cptr[own[f]] + fill[own[f]]++] = 2 * f;
             if (f < ni) cface[cptr[nei[f]] + fill[nei[f]]++] = 2 * f + 1;
         }
+    }
+    std::vector<int> cnb(cface.size());
+    for (size_t k = 0; k < cface.size(); ++k) {
+        const int f = cface[k] >> 1;
+        cnb[k] = f >= ni ? -1 : (cface[k] & 1) ? own[f] : nei[f];
     }
     // cell -> distinct points, and the tetrahedron count per cell
     std::vector<int> cpcount(nc);
@@ -332,6 +342,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     m.nei = dev_copy(c, ni > 0 ? nei : own, std::max(ni, 1), &err);
     m.cptr = dev_copy(c, cptr.data(), cptr.size(), &err);
     m.cface = dev_copy(c, cface.data(), cface.size(), &err);
+    m.cnb = dev_copy(c, cnb.data(), cnb.size(), &err);
     m.cpptr = dev_copy(c, cpptr.data(), cpptr.size(), &err);
     m.cpts = dev_copy(c, cpts.data(), cpts.size(), &err);
     m.pptr = dev_copy(c, pptr.data(), pptr.size(), &err);
@@ -377,8 +388,10 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
     c->status = dev_alloc<unsigned>(c, 1, &err);
     c->h_alpha = dev_alloc<double>(c, nc, &err);
-    c->h_Uc = dev_alloc<double>(c, 3 * (size_t)nc, &err);
-    c->h_F = dev_alloc<double>(c, nf, &err);
+    for (int i = 0; i < 2; ++i) {
+        c->h_Uc[i] = dev_alloc<double>(c, 3 * (size_t)nc, &err);
+        c->h_F[i] = dev_alloc<double>(c, nf, &err);
+    }
     c->work = dev_alloc<unsigned long long>(c, 4, &err);
     c->cfpptr = dev_copy(c, cfpptr.data(), cfpptr.size(), &err);
     c->cfl = dev_alloc<float4>(c, cface.size(), &err);
@@ -386,6 +399,8 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->fpl = dev_alloc<float4>(c, nfp, &err);
     c->cbl = dev_alloc<float4>(c, 2 * (size_t)nc, &err);
     c->palpha = dev_alloc<double>(c, np, &err);
+    c->bpflag = dev_alloc<uint8_t>(c, np, &err);
+    c->upb = dev_alloc<double>(c, 3 * (size_t)np, &err);
     if (c->precision == VOF_MIXED) c->ktl = dev_alloc<float4>(c, 6 * (size_t)ctptr[nc], &err);
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
@@ -396,6 +411,11 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     cudaMemset(c->n, 0, sizeof(double) * 3 * nc);
     cudaMemset(c->d, 0, sizeof(double) * nc);
     cudaMemset(c->flags, 0, nc);
+    cudaMemset(c->bpflag, 0, np);
+    if (!err && (cudaStreamCreateWithFlags(&c->s_aux, cudaStreamNonBlocking) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                 cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess))
+        err = VOF_ERR_CUDA;
     {
         const int whole[2] = {0, nc};
         if (!err) err = set_bound_regions(c, whole, 1);
@@ -489,21 +509,30 @@ int vof_advect_host(vof_ctx *c, double *alpha, const double *Uc, const double *F
     if (!c || !alpha || !Uc || !F || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    // alpha and F first (classification and reconstruction need them); the
-    // cell velocities on a second stream, overlapping those kernels, after
-    // everything earlier on `stream` (the previous step still reads them)
+    // F and U go to the staging pair of this call's parity on the copy stream,
+    // once the step that last read that pair (two calls back) is done: they
+    // overlap the previous step's kernels.  alpha (in place, so ordered after
+    // the previous step's read-back) goes on `stream`; the classification
+    // waits for F, the flux correction (inside the step) for U.
     if (!c->s_copy && (cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking) ||
-                       cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) ||
-                       cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming)))
+                       cudaEventCreateWithFlags(&c->ev_f, cudaEventDisableTiming) ||
+                       cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming) ||
+                       cudaEventCreateWithFlags(&c->ev_free[0], cudaEventDisableTiming) ||
+                       cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming)))
         return VOF_ERR_CUDA;
-    if (cudaEventRecord(c->ev_ready, s) || cudaStreamWaitEvent(c->s_copy, c->ev_ready, 0) ||
-        cudaMemcpyAsync(c->h_Uc, Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->s_copy) ||
+    const int p = c->h_par;
+    if (cudaStreamWaitEvent(c->s_copy, c->ev_free[p], 0) ||
+        cudaMemcpyAsync(c->h_F[p], F, sizeof(double) * c->nf, cudaMemcpyHostToDevice, c->s_copy) ||
+        cudaEventRecord(c->ev_f, c->s_copy) ||
+        cudaMemcpyAsync(c->h_Uc[p], Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->s_copy) ||
         cudaEventRecord(c->ev_u, c->s_copy) ||
         cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
-        cudaMemcpyAsync(c->h_F, F, sizeof(double) * c->nf, cudaMemcpyHostToDevice, s))
+        cudaStreamWaitEvent(s, c->ev_f, 0))
         return VOF_ERR_CUDA;
-    int r = launch_advect(c, c->h_alpha, c->h_Uc, c->h_F, dt, c->stats_dev, s, c->ev_u);
+    c->h_par ^= 1;
+    int r = launch_advect(c, c->h_alpha, c->h_Uc[p], c->h_F[p], dt, c->stats_dev, s, c->ev_u);
     if (r) return r;
+    if (cudaEventRecord(c->ev_free[p], s)) return VOF_ERR_CUDA;
     if (cudaMemcpyAsync(alpha, c->h_alpha, sizeof(double) * c->nc, cudaMemcpyDeviceToHost, s)) return VOF_ERR_CUDA;
     if (stats && cudaMemcpyAsync(stats, c->stats_dev, sizeof(double) * VOF_S_LEN, cudaMemcpyDeviceToHost, s))
         return VOF_ERR_CUDA;

@@ -18,6 +18,7 @@ struct DevMesh {
     const double *px, *py, *pz;
     const int *fptr, *fpts, *own, *nei;
     const int *cptr, *cface;     // cell -> face codes, code = 2*f + (cell is neighbour)
+    const int *cnb;              // per cface entry: the cell across that face, -1 on a boundary face
     const int *cpptr, *cpts;     // cell -> distinct points (ascending)
     const int *pptr, *pcell;     // point -> cells (ascending)
     const double *pw;            // inverse-distance weight per (point, cell) entry
@@ -71,9 +72,13 @@ struct vof_ctx {
     double *partial;             // reduction partials
     double *stats_dev;           // internal stats buffer
     unsigned *status;
-    double *h_alpha, *h_Uc, *h_F;  // device staging for vof_advect_host
+    double *h_alpha;               // device staging for vof_advect_host; U and F double-buffered
+    double *h_Uc[2], *h_F[2];      // by call parity, so that a call's copies overlap the previous step
+    int h_par;
     cudaStream_t s_copy;           // vof_advect_host: the velocity copy overlaps the first kernels
-    cudaEvent_t ev_ready, ev_u;
+    cudaEvent_t ev_f, ev_u, ev_free[2];
+    cudaStream_t s_aux;            // the correction runs here, beside the reconstruction
+    cudaEvent_t ev_fork, ev_join;
     int launches;
     unsigned long long *work;    // [3] phase-flux work counters
     // FP32 geometry for the mixed kernels
@@ -83,6 +88,8 @@ struct vof_ctx {
     // box, 6 float4, relative to the cell centre (first of each cell: m.ctptr)
     float4 *ktl;
     double *palpha;              // IDW point values of the points that are not all-empty / all-full
+    uint8_t *bpflag;             // per point: a point of a band face this step (cleared by its reader)
+    double *upb;                 // point velocities of the flagged points
     // mixed phase-flux launch configuration (0: defaults): warps per block 1-3,
     // grid multiplier over the resident blocks
     int pf_warps, pf_mult;

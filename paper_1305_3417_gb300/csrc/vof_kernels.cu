@@ -185,7 +185,7 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // G lanes per cell: 32, or 8 where every cell has at most 16 tetrahedra (a
 // tetrahedral mesh: four cells per warp); reductions over the cell's lanes
 template <bool LIST, bool MIXED, int G>
-__global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
+__global__ void __launch_bounds__(128) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
                                                      uint8_t *fout, int *itout, int *maxit, unsigned *status,
@@ -237,10 +237,12 @@ __global__ void __launch_bounds__(256) k_reconstruct(DevMesh m, const double *__
                 if (en.y & 1) w = -w;  // Eq. own-nei: the neighbour sees -S_f
                 g = g + ld3(m.sf, m.nf, f) * w;
             }
-            g = mk(tsum(g.x), tsum(g.y), tsum(g.z)) * (1.0 / V);
-            double gm = norm3(g);
-            if (gm * cbrt(V) > 1e-12) {
-                nn = g * (-1.0 / gm);  // points out of the phase
+            // g = G / V; the cell is oriented where |g| V^(1/3) > 1e-12, taken
+            // as |G|^6 > 1e-72 V^4 (no cube root, square root or division)
+            g = mk(tsum(g.x), tsum(g.y), tsum(g.z));
+            const double g2 = dot(g, g);
+            if (g2 * g2 * g2 > 1e-72 * (V * V) * (V * V)) {
+                nn = g * -rsqrt(g2);  // points out of the phase
                 fl |= VOF_ORIENTED;
                 // ---- cell tetrahedra (c_c, outward face triangle), lanes j, j+32
                 const V3 ctr = ld3(m.cc, m.nc, c);
@@ -417,7 +419,7 @@ __device__ __forceinline__ void prism_cubic(V3 a0, V3 a1, V3 a2, V3 w0, V3 w1, V
     if (k2 < k1) { V3 t = a1; a1 = a2; a2 = t; t = w1; w1 = w2; w2 = t; long u = k1; k1 = k2; k2 = u; par = -par; }
     if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long u = k0; k0 = k1; k1 = u; par = -par; }
     V3 E1 = a1 - a0, E2 = a2 - a0;
-    double f = -par / 6.0;
+    const double f = par > 0 ? -1.0 / 6.0 : 1.0 / 6.0;
     double t1 = -det3(E1, E2, w0 + w1 + w2) * f;
     double t2 = (det3(E1, w2, w1) + det3(w0, w1, E2) + det3(w0, E1, w2)) * f;
     double t3 = -det3(w0, w1, w2) * f;
@@ -441,6 +443,20 @@ __device__ __forceinline__ int face_points(const DevMesh &m, int f, const double
     return n;
 }
 
+// 1/n for the face-centre average (a table: no FP64 division)
+__device__ __forceinline__ double inv_n(int n)
+{
+    return n == 4 ? 0.25 : n == 3 ? 1.0 / 3.0 : n == 5 ? 0.2 : n == 6 ? 1.0 / 6.0 : n == 7 ? 1.0 / 7.0 : 0.125;
+}
+
+// face-centre displacement: the mean of the point displacements
+__device__ __forceinline__ V3 centre_disp(int n, const V3 *W)
+{
+    V3 wc = mk(0, 0, 0);
+    for (int i = 0; i < n; ++i) wc = wc + W[i];
+    return wc * inv_n(n);
+}
+
 __device__ __forceinline__ Cubic face_cubic(const DevMesh &m, int f, int n, const V3 *A, const V3 *W,
                                             const int *id)
 {
@@ -448,9 +464,7 @@ __device__ __forceinline__ Cubic face_cubic(const DevMesh &m, int f, int n, cons
     if (n == 3) {
         prism_cubic(A[0], A[1], A[2], W[0], W[1], W[2], id[0], id[1], id[2], q);
     } else {
-        V3 c = ld3(m.cf, m.nf, f), wc = mk(0, 0, 0);
-        for (int i = 0; i < n; ++i) wc = wc + W[i];
-        wc = wc * (1.0 / n);
+        V3 c = ld3(m.cf, m.nf, f), wc = centre_disp(n, W);
         for (int t = 0; t < n; ++t) {
             int u = t + 1 == n ? 0 : t + 1;
             prism_cubic(c, A[t], A[u], wc, W[t], W[u], -1, id[t], id[u], q);
@@ -466,12 +480,13 @@ __device__ __forceinline__ double cubic_at(const Cubic &q, double x) { return ((
 // Newton steps that fall back to bisection when they leave the bracket.
 // Returns lambda, or -1 (normal-sweep fallback) when no interval brackets a root.
 // A flux below 1e-12 of |S_f| max|w| (noise = the rounding of a zero flux, e.g.
-// on a wall) gives lambda = 0: no sweep.
-__device__ double solve_lambda(const Cubic &q, double tau, double noise, int &its)
+// on a wall) gives lambda = 0: no sweep.  The test is taken on squares,
+// tau^2 <= 1e-24 |S_f|^2 max|w|^2 (noise2), which needs no square root.
+__device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &its)
 {
     its = 0;
     if (tau == 0.0) return 0.0;
-    if (fabs(tau) <= 1e-12 * noise) return 0.0;
+    if (tau * tau <= 1e-24 * noise2) return 0.0;
     double lo = 0.0, rlo = -tau, hi = 0.0, rhi = 0.0;
     bool found = false;
     for (int k = 1; k <= CORR_NSAMP; ++k) {
@@ -519,7 +534,78 @@ __global__ void k_flux_polyhedra(DevMesh m, const double *__restrict__ Up, const
     V[f] = cubic_at(q, lam);
 }
 
-template <bool IDW, bool LIST>
+// The correction of one face with points b .. b+n-1 of m.fpts.  N = 3 or 4:
+// the face has exactly N points and every array index is static after
+// unrolling (registers); N = VOF_MAXFP: any n (local arrays).
+template <int N>
+__device__ __forceinline__ void correct_face(const DevMesh &m, int f, int b, int n, const double *__restrict__ U,
+                                             const double *__restrict__ F, double dt, int item, double *lam_out,
+                                             int *it_out, double *disp_out, int *maxit, int *nfallback)
+{
+    constexpr bool FIXED = N <= 4;
+    const int nn = FIXED ? N : n;
+    V3 A[N], W[N];
+    int id[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        if (i < nn) {
+            int p = __ldg(m.fpts + b + i);
+            id[i] = p;
+            A[i] = ldP(m, p);
+            W[i] = ld3(U, m.np, p) * dt;
+        }
+    }
+    const double tau = F[f] * dt;
+    Cubic q = {0, 0, 0, 0, 0, 0};
+    if (nn == 3) {
+        prism_cubic(A[0], A[1], A[2], W[0], W[1], W[2], id[0], id[1], id[2], q);
+    } else {
+        V3 c = ld3(m.cf, m.nf, f), wc = mk(0, 0, 0);
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < nn) wc = wc + W[i];
+        wc = wc * inv_n(nn);
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            if (t < nn) {
+                int u = t + 1 == nn ? 0 : t + 1;
+                prism_cubic(c, A[t], A[u], wc, W[t], W[u], -1, id[t], id[u], q);
+            }
+        }
+    }
+    double w2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+        if (i < nn) w2 = fmax(w2, dot(W[i], W[i]));
+    const V3 S = ld3(m.sf, m.nf, f);
+    int its = 0;
+    const double lam = solve_lambda(q, tau, dot(S, S) * w2, its);
+    lam_out[item] = lam;
+    if (it_out) it_out[item] = its;
+    if (maxit && its > 0) atomicMax(maxit, its);
+    if (lam < 0.0 && nfallback) atomicAdd(nfallback, 1);
+    if (disp_out) {
+        double *o = disp_out + (size_t)item * DISP_STRIDE;
+        V3 wc = mk(0, 0, 0);
+        if (lam < 0.0) {
+            wc = S * (-lam * F[f] * dt / dot(S, S));
+#pragma unroll
+            for (int i = 0; i < N; ++i) W[i] = wc;
+        } else {
+#pragma unroll
+            for (int i = 0; i < N; ++i)
+                if (i < nn) { W[i] = W[i] * lam; wc = wc + W[i]; }
+            wc = wc * inv_n(nn);
+        }
+        o[0] = wc.x; o[1] = wc.y; o[2] = wc.z;
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            if (i < nn) { o[3 + 3 * i] = W[i].x; o[4 + 3 * i] = W[i].y; o[5 + 3 * i] = W[i].z; }
+    }
+}
+
+// One thread per face (LIST: per band slot).  U holds the point velocities.
+template <bool LIST>
 __global__ void k_correct(DevMesh m, const double *__restrict__ U, const double *__restrict__ F,
                           double dt, const int *list, const int *count, double *lam_out,
                           int *it_out, double *disp_out, int *maxit, int *nfallback)
@@ -527,33 +613,25 @@ __global__ void k_correct(DevMesh m, const double *__restrict__ U, const double 
     const int total = LIST ? *count : m.nf;
     for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
         const int f = LIST ? list[item] : item;
-        V3 A[VOF_MAXFP], W[VOF_MAXFP];
-        int id[VOF_MAXFP];
-        int n = face_points<IDW>(m, f, U, dt, A, W, id);
-        double tau = F[f] * dt;
-        Cubic q = face_cubic(m, f, n, A, W, id);
-        double wmax = 0.0;
-        for (int i = 0; i < n; ++i) wmax = fmax(wmax, norm3(W[i]));
-        int its = 0;
-        double lam = solve_lambda(q, tau, norm3(ld3(m.sf, m.nf, f)) * wmax, its);
-        lam_out[item] = lam;
-        if (it_out) it_out[item] = its;
-        if (maxit && its > 0) atomicMax(maxit, its);
-        if (lam < 0.0 && nfallback) atomicAdd(nfallback, 1);
-        if (disp_out) {
-            double *o = disp_out + (size_t)item * DISP_STRIDE;
-            V3 wc = mk(0, 0, 0);
-            if (lam < 0.0) {
-                V3 S = ld3(m.sf, m.nf, f);
-                wc = S * (-lam * F[f] * dt / dot(S, S));
-                for (int i = 0; i < n; ++i) W[i] = wc;
-            } else {
-                for (int i = 0; i < n; ++i) { W[i] = W[i] * lam; wc = wc + W[i]; }
-                wc = wc * (1.0 / n);
-            }
-            o[0] = wc.x; o[1] = wc.y; o[2] = wc.z;
-            for (int i = 0; i < n; ++i) { o[3 + 3 * i] = W[i].x; o[4 + 3 * i] = W[i].y; o[5 + 3 * i] = W[i].z; }
-        }
+        const int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
+        if (n == 4)
+            correct_face<4>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback);
+        else if (n == 3)
+            correct_face<3>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback);
+        else
+            correct_face<VOF_MAXFP>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback);
+    }
+}
+
+// Point velocities (Eq. 4 weights, wall projection) of the points of this
+// step's band faces, flagged by the classification; each point once, and the
+// flag cleared for the next step.
+__global__ void k_band_point_velocity(DevMesh m, const double *__restrict__ Uc, uint8_t *flag, double *Up)
+{
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < m.np; p += gridDim.x * blockDim.x) {
+        if (!flag[p]) continue;
+        flag[p] = 0;
+        st3(Up, m.np, p, point_velocity(m, p, Uc));
     }
 }
 
@@ -870,12 +948,22 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
         int c = i0 + threadIdx.x;
         bool bad = false;
         if (c < m.nc) {
-            double s = 0.0;
-            for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-                int code = m.cface[k];
-                double x = Va[code >> 1];
-                s += (code & 1) ? -x : x;
+            // A cell whose face fluxes are all zero (the bulk of either phase
+            // away from the band) has s = +0; the FP64 sum runs only where some
+            // flux is not zero, so warps of such cells issue no FP64 adds.
+            const int k0 = m.cptr[c], k1 = m.cptr[c + 1];
+            unsigned nz = 0;
+            for (int k = k0; k < k1; ++k) {
+                DBits b = dbits(Va[m.cface[k] >> 1]);
+                nz |= (unsigned)(b.hi & 0x7fffffff) | b.lo;
             }
+            double s = 0.0;
+            if (nz)
+                for (int k = k0; k < k1; ++k) {
+                    int code = m.cface[k];
+                    double x = Va[code >> 1];
+                    s += (code & 1) ? -x : x;
+                }
             double a0 = alpha[c];
             if (is_zero(s) && is_pzero(a0)) {
                 zero = true;  // an empty cell with no flux: alpha stays +0
@@ -982,11 +1070,24 @@ __global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *a
 // this.  Every touched cell's new value is a gather over its face neighbours in
 // face order.  The sources are few, so one block runs all passes with block
 // barriers between the phases and stops once no cell is out of bounds.
-__device__ __forceinline__ int nbr_of(const DevMesh &m, int c, int k)
+// Face neighbours of x in face order, handed to fn(s, k) (s the neighbour, k
+// its cface slot).  The indices of a chunk of up to BP_CHUNK neighbours are
+// loaded together, and fn's own loads across the unrolled chunk can issue
+// together too: a few dependent load rounds per chunk instead of a chain per
+// neighbour.
+constexpr int BP_CHUNK = 8;
+template <class Fn>
+__device__ __forceinline__ void for_nbrs(const DevMesh &m, int x, Fn fn)
 {
-    int code = m.cface[k], f = code >> 1;
-    if (f >= m.ni) return -1;
-    return (code & 1) ? m.own[f] : m.nei[f];
+    const int k0 = m.cptr[x], k1 = m.cptr[x + 1];
+    for (int kb = k0; kb < k1; kb += BP_CHUNK) {
+        int nb[BP_CHUNK];
+#pragma unroll
+        for (int j = 0; j < BP_CHUNK; ++j) nb[j] = kb + j < k1 ? m.cnb[kb + j] : -1;
+#pragma unroll
+        for (int j = 0; j < BP_CHUNK; ++j)
+            if (nb[j] >= 0) fn(nb[j], kb + j);
+    }
 }
 __device__ __forceinline__ bool is_exc(double a) { return a > 1.0 + BOUND_TOL; }
 __device__ __forceinline__ bool is_def(double a) { return a < -BOUND_TOL; }
@@ -1017,12 +1118,10 @@ __device__ __forceinline__ int first_source(const DevMesh &m, const double *alph
         double ax = alpha[x];
         if (is_exc(ax) || is_def(ax)) first = x;
     }
-    for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
-        int s = nbr_of(m, x, q);
-        if (s < 0) continue;
+    for_nbrs(m, x, [&](int s, int) {
         double as = alpha[s];
         if ((is_exc(as) || is_def(as)) && s < first) first = s;
-    }
+    });
     return first;
 }
 
@@ -1035,14 +1134,12 @@ __global__ void k_bp_room(DevMesh m, const double *alpha, BoundBufs b)
         int c = b.la[i];
         double Cp = 0.0, Cm = 0.0;
         int dg = 0;
-        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-            int nb = nbr_of(m, c, k);
-            if (nb < 0) continue;
+        for_nbrs(m, c, [&](int nb, int) {
             double an = alpha[nb], Vn = m.vc[nb];
             Cp += room_exc(an, Vn);
             Cm += room_def(an, Vn);
             ++dg;
-        }
+        });
         b.bs[BS_N * (size_t)c + BS_CP] = Cp;
         b.bs[BS_N * (size_t)c + BS_CM] = Cm;
         b.dg[c] = dg;
@@ -1059,18 +1156,16 @@ __global__ void k_bp_scale(DevMesh m, const double *alpha, BoundBufs b)
     for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n * BP_SLOTS; t += (long)gridDim.x * blockDim.x) {
         int c = b.la[t / BP_SLOTS];
         for (int k = m.cptr[c] + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
-            int r = nbr_of(m, c, k);
+            int r = m.cnb[k];
             if (r < 0 || first_source(m, alpha, r, false) != c) continue;
             double ar = alpha[r], Vr = m.vc[r], Rp = room_exc(ar, Vr), Rm = room_def(ar, Vr);
             double Qp = 0.0, Qm = 0.0;
-            for (int q = m.cptr[r]; q < m.cptr[r + 1]; ++q) {
-                int s = nbr_of(m, r, q);
-                if (s < 0) continue;
+            for_nbrs(m, r, [&](int s, int) {
                 double as = alpha[s], Vs = m.vc[s];
                 double Cps = bs[BS_N * (size_t)s + BS_CP], Cms = bs[BS_N * (size_t)s + BS_CM];
                 if (is_exc(as) && Cps > 0.0) Qp += (as - 1.0) * Vs * (Rp / Cps);
                 if (is_def(as) && Cms > 0.0) Qm += -as * Vs * (Rm / Cms);
-            }
+            });
             bs[BS_N * (size_t)r + BS_SP] = Qp > Rp ? Rp / Qp : 1.0;
             bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
         }
@@ -1085,14 +1180,13 @@ __global__ void k_bp_place(DevMesh m, const double *alpha, BoundBufs b)
         int c = b.la[i];
         double a = alpha[c], V = m.vc[c];
         double *q = bs + BS_N * (size_t)c;
+        const double Cp = q[BS_CP], Cm = q[BS_CM];
         double gp = 0.0, gm = 0.0, e = is_exc(a) ? (a - 1.0) * V : 0.0, u = is_def(a) ? -a * V : 0.0;
-        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
-            int nb = nbr_of(m, c, k);
-            if (nb < 0) continue;
+        for_nbrs(m, c, [&](int nb, int) {
             double an = alpha[nb], Vn = m.vc[nb];
-            if (e > 0.0 && q[BS_CP] > 0.0) gp += e * (room_exc(an, Vn) / q[BS_CP]) * bs[BS_N * (size_t)nb + BS_SP];
-            if (u > 0.0 && q[BS_CM] > 0.0) gm += u * (room_def(an, Vn) / q[BS_CM]) * bs[BS_N * (size_t)nb + BS_SM];
-        }
+            if (e > 0.0 && Cp > 0.0) gp += e * (room_exc(an, Vn) / Cp) * bs[BS_N * (size_t)nb + BS_SP];
+            if (u > 0.0 && Cm > 0.0) gm += u * (room_def(an, Vn) / Cm) * bs[BS_N * (size_t)nb + BS_SM];
+        });
         int dg = b.dg[c];
         q[BS_RP] = (e > 0.0 && dg > 0) ? e - gp : 0.0;
         q[BS_RM] = (u > 0.0 && dg > 0) ? u - gm : 0.0;
@@ -1110,29 +1204,28 @@ __global__ void k_bp_new(DevMesh m, const double *alpha, BoundBufs b, int *npend
         int c = b.la[t / BP_SLOTS];
         // slot 0 takes the source itself (k = cptr[c] - 1)
         for (int k = m.cptr[c] - 1 + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
-            int x = k < m.cptr[c] ? c : nbr_of(m, c, k);
+            int x = k < m.cptr[c] ? c : m.cnb[k];
             if (x < 0 || first_source(m, alpha, x, true) != c) continue;
             double ax = alpha[x], V = m.vc[x];
             bool xe = is_exc(ax), xd = is_def(ax);
             double Rp = room_exc(ax, V), Rm = room_def(ax, V);
+            const double SPx = bs[BS_N * (size_t)x + BS_SP], SMx = bs[BS_N * (size_t)x + BS_SM];
             double dV = 0.0;
             if (xe) dV -= bs[BS_N * (size_t)x + BS_REL];
             if (xd) dV += bs[BS_N * (size_t)x + BS_REL];
-            for (int q = m.cptr[x]; q < m.cptr[x + 1]; ++q) {
-                int s = nbr_of(m, x, q);
-                if (s < 0) continue;
+            for_nbrs(m, x, [&](int s, int) {
                 double as = alpha[s], Vs = m.vc[s];
                 const double *bq = bs + BS_N * (size_t)s;
                 int dgs = b.dg[s];
                 if (is_exc(as)) {
-                    if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp / bq[BS_CP]) * bs[BS_N * (size_t)x + BS_SP];
+                    if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp / bq[BS_CP]) * SPx;
                     if (dgs > 0) dV += bq[BS_RP] / dgs;
                 }
                 if (is_def(as)) {
-                    if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm / bq[BS_CM]) * bs[BS_N * (size_t)x + BS_SM];
+                    if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm / bq[BS_CM]) * SMx;
                     if (dgs > 0) dV -= bq[BS_RM] / dgs;
                 }
-            }
+            });
             if (dV != 0.0) {
                 int pos = atomicAdd(npend, 1);
                 if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = (ax * V + dV) / V; }
@@ -1254,7 +1347,7 @@ __global__ void k_point_state(DevMesh m, const double *__restrict__ alpha, uint8
 
 __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const double *__restrict__ F,
                            double dt, const uint8_t *__restrict__ state, double *Va, int *band, int *nband,
-                           int *icell, int *nicell, unsigned *status)
+                           int *icell, int *nicell, uint8_t *bpflag, unsigned *status)
 {
     const int lim = m.nf > m.nc ? m.nf : m.nc;
     for (int i0 = blockIdx.x * blockDim.x; i0 < lim; i0 += gridDim.x * blockDim.x) {
@@ -1268,7 +1361,10 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
                 for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) st &= state[m.fpts[k]];
                 if (st & 1u) v = 0.0;
                 else if (st & 2u) v = Ff * dt;
-                else isband = true;
+                else {
+                    isband = true;
+                    for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) bpflag[m.fpts[k]] = 1;
+                }
             }
             Va[i] = v;
         }
@@ -1338,12 +1434,12 @@ static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const do
                       cudaStream_t s)
 {
     if (c->rc_g == 8) {
-        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 256);
-        k_reconstruct<LIST, MIXED, 8><<<blocks, 256, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
+        k_reconstruct<LIST, MIXED, 8><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
                                                              maxit, c->status, c->mlp_s0, mlp_cap(c));
     } else {
-        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 256);
-        k_reconstruct<LIST, MIXED, 32><<<blocks, 256, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
+        k_reconstruct<LIST, MIXED, 32><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
                                                               maxit, c->status, c->mlp_s0, mlp_cap(c));
     }
 }
@@ -1385,10 +1481,10 @@ int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, ui
     }
     if (list) {
         if (mx)
-            rc_launch<true, true>(c, sms * 8, alpha, nullptr, list, count, n, d, flags, iters,
+            rc_launch<true, true>(c, sms * 16, alpha, nullptr, list, count, n, d, flags, iters,
                                   c->counters + CNT_MAXPOS, s);
         else
-            rc_launch<true, false>(c, sms * 8, alpha, nullptr, list, count, n, d, flags, iters,
+            rc_launch<true, false>(c, sms * 16, alpha, nullptr, list, count, n, d, flags, iters,
                                    c->counters + CNT_MAXPOS, s);
     } else {
         if (mx)
@@ -1411,7 +1507,7 @@ int launch_flux_polyhedra(vof_ctx *c, const double *Up, const double *F, const d
 int launch_correct_all(vof_ctx *c, const double *Up, const double *F, double dt, double *lambda, int *iters,
                        cudaStream_t s)
 {
-    k_correct<false, false><<<cdiv(c->nf, 128), 128, 0, s>>>(c->m, Up, F, dt, nullptr, nullptr, lambda, iters,
+    k_correct<false><<<cdiv(c->nf, 128), 128, 0, s>>>(c->m, Up, F, dt, nullptr, nullptr, lambda, iters,
                                                              nullptr, nullptr, nullptr);
     LAUNCH_CHECK();
     return VOF_OK;
@@ -1485,26 +1581,37 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     k_zero_int<<<1, 32, 0, s>>>(cnt, CNT_LEN);
     k_point_state<<<cdiv(m.np, 256), 256, 0, s>>>(m, alpha, c->pstate, c->palpha);
     k_classify<<<sms * 16, 256, 0, s>>>(m, alpha, F, dt, c->pstate, c->Va, c->band, cnt + CNT_BAND, c->icell,
-                                        cnt + CNT_ICELL, c->status);
+                                        cnt + CNT_ICELL, c->bpflag, c->status);
     launches += 3;
     LAUNCH_CHECK();
     MARK(1);
+    // The correction (band point velocities, then lambda per band face) needs
+    // the band list and the velocities, the reconstruction the interface list:
+    // the two run side by side, the correction on the context's second stream,
+    // joined before the phase flux.  The first use of Uc is there, so a
+    // velocity copy still in flight on another stream is waited for there.
+    if (cudaEventRecord(c->ev_fork, s) != cudaSuccess || cudaStreamWaitEvent(c->s_aux, c->ev_fork, 0) != cudaSuccess)
+        return VOF_ERR_CUDA;
+    if (wait_before_correct && cudaStreamWaitEvent(c->s_aux, wait_before_correct, 0) != cudaSuccess)
+        return VOF_ERR_CUDA;
+    k_band_point_velocity<<<cdiv(m.np, 256), 256, 0, c->s_aux>>>(m, Uc, c->bpflag, c->upb);
+    k_correct<true><<<sms * 8, 128, 0, c->s_aux>>>(m, c->upb, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
+                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);
+    LAUNCH_CHECK();
+    if (cudaEventRecord(c->ev_join, c->s_aux) != cudaSuccess) return VOF_ERR_CUDA;
     if (c->precision == VOF_MIXED && c->mlp) {
         int r = launch_mlp_guess(c, alpha, c->icell, cnt + CNT_ICELL, c->nc, s);
         if (r) return r;
         ++launches;
     }
     if (c->precision == VOF_MIXED)
-        rc_launch<true, true>(c, sms * 8, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
+        rc_launch<true, true>(c, sms * 16, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
                               cnt + CNT_MAXPOS, s);
     else
-        rc_launch<true, false>(c, sms * 8, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
+        rc_launch<true, false>(c, sms * 16, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
                                cnt + CNT_MAXPOS, s);
     MARK(2);
-    // the first use of Uc: a velocity copy in flight on another stream ends here
-    if (wait_before_correct && cudaStreamWaitEvent(s, wait_before_correct, 0) != cudaSuccess) return VOF_ERR_CUDA;
-    k_correct<true, true><<<sms * 8, 128, 0, s>>>(m, Uc, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
-                                                  c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);
+    if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return VOF_ERR_CUDA;
     MARK(3);
     if (c->precision == VOF_MIXED) {
         int r = launch_phase_flux_mixed_list(c, alpha, F, dt, sms, s);
@@ -1514,7 +1621,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
                  c->status, c->work};
         k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
     }
-    launches += 3;
+    launches += 4;  // reconstruct, band point velocities, correct, phase flux
     LAUNCH_CHECK();
     MARK(4);
     // update + bounding + stats

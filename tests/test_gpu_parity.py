@@ -290,6 +290,28 @@ def test_advect_host_matches_device(torch, O):
     assert np.array_equal(ha.numpy(), H(ta))
 
 
+def test_advect_host_steps_queued(torch, O):
+    """Five host-buffer steps queued back to back (the velocity and flux copies
+    of a call overlap the previous step, alternating between two device
+    buffer pairs) give the same fields and statistics, bit for bit, as the
+    device-buffer steps one by one."""
+    from paper_1305_3417_gb300 import vof
+    w, ctx, om = contexts(torch, O, "deform20")
+    steps = [w.step_inputs(k) for k in range(5)]
+    ta = T(torch, w.alpha0)
+    for F, U, dt in steps:
+        st = ctx.advect(ta, T(torch, U), T(torch, F), dt)
+    ha = torch.from_numpy(w.alpha0.copy()).pin_memory()
+    hU = [torch.from_numpy(np.ascontiguousarray(U).reshape(-1).copy()).pin_memory() for _, U, _ in steps]
+    hF = [torch.from_numpy(F.copy()).pin_memory() for F, _, _ in steps]
+    hs = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
+    for k, (_, _, dt) in enumerate(steps):
+        vof.vof_advect_host(ctx.h, ha, hU[k], hF[k], dt, hs)
+    torch.cuda.synchronize()
+    assert np.array_equal(ha.numpy(), H(ta))
+    assert np.array_equal(hs.numpy(), H(st))
+
+
 _FULL = {}
 
 
