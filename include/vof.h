@@ -56,6 +56,7 @@ enum {
     VOF_ST_BOUND_RESIDUAL = 1u << 3,     /* |alpha - clamp(alpha)| > 1e-12 after bounding */
     VOF_ST_INDEX = 1u << 4,              /* an index check failed inside a kernel */
     VOF_ST_CAPACITY = 1u << 5,           /* a per-step list exceeded its capacity */
+    VOF_ST_TIMEOUT = 1u << 6,            /* a grid barrier inside a kernel gave up waiting */
 };
 
 /* precision of the geometric kernels */

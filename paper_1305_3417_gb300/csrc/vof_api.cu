@@ -373,7 +373,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->viol[1] = dev_alloc<int>(c, nc, &err);
     c->pend_c = dev_alloc<int>(c, 8 * (size_t)nc, &err);
     c->pend_a = dev_alloc<double>(c, 8 * (size_t)nc, &err);
-    c->counters = dev_alloc<int>(c, 16, &err);
+    c->counters = dev_alloc<int>(c, CNT_ALLOC, &err);
     c->lam_b = dev_alloc<double>(c, nf, &err);
     c->disp_b = dev_alloc<double>(c, (size_t)nf * (VOF_MAXFP + 1) * 3, &err);
     c->it_b = dev_alloc<int>(c, nf, &err);
@@ -406,7 +406,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
     cudaMemset(c->bscr, 0, sizeof(double) * 8 * nc);
     cudaMemset(c->dgi, 0, sizeof(int) * nc);
-    cudaMemset(c->counters, 0, sizeof(int) * 16);
+    cudaMemset(c->counters, 0, sizeof(int) * CNT_ALLOC);
     cudaMemset(c->status, 0, sizeof(unsigned));
     cudaMemset(c->n, 0, sizeof(double) * 3 * nc);
     cudaMemset(c->d, 0, sizeof(double) * nc);

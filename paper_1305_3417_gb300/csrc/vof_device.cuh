@@ -11,8 +11,6 @@
 
 namespace vofd {
 
-enum { CNT_BAND = 0, CNT_ICELL, CNT_VIOL0, CNT_VIOL1, CNT_PEND, CNT_MAXPOS, CNT_MAXCORR,
-       CNT_FALLBACK, CNT_LEN = 16 };
 
 constexpr int POS_MAXIT = 100;
 constexpr double POS_TOL = 1e-13;

@@ -39,6 +39,11 @@ struct DevMesh {
     const int4 *ctet;
 };
 
+// the context's counter buffer: per-step counters (the first CNT_LEN ints),
+// then the two words of the grid barrier, each on its own 128-byte line
+enum { CNT_BAND = 0, CNT_ICELL, CNT_MAXPOS, CNT_MAXCORR, CNT_FALLBACK, CNT_VIOL0, CNT_VIOL1, CNT_PEND, CNT_LEN = 16 };
+enum { CNT_BAR = 32, CNT_BARGEN = 64, CNT_ALLOC = 96 };
+
 struct vof_ctx {
     int device;
     int np, nf, ni, nc;
@@ -52,7 +57,7 @@ struct vof_ctx {
     uint8_t *pstate;
     int *band, *icell, *viol[2], *pend_c;
     double *pend_a;
-    int *counters;               // see CNT_* in vof_kernels.cu
+    int *counters;               // CNT_ALLOC ints, laid out as CNT_* above
     double *lam_b, *disp_b;      // per band slot
     int *it_b;
     double *n, *d;

@@ -997,15 +997,15 @@ __device__ __forceinline__ void fold5(double *r, const double *p)
     r[0] += p[0]; r[1] += p[1]; r[2] = fmin(r[2], p[2]); r[3] = fmax(r[3], p[3]); r[4] += p[4];
 }
 
-__global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int nblk, const int *counters,
-                                                      double *stats, int post, const double *bound_partial)
+// called by every thread of a block of ST_THREADS threads
+__device__ void stats_block(const double *partial, int nblk, const int *counters, double *stats, int post,
+                            const double *bound_partial, int nblk_post)
 {
     __shared__ double sh[2][5][ST_THREADS];
     double r[5] = {0.0, 0.0, 1e300, -1e300, 0.0}, q[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
-    for (int k = threadIdx.x; k < nblk; k += ST_THREADS) {
-        fold5(r, partial + 5 * k);
-        if (post) fold5(q, bound_partial + 5 * k);
-    }
+    for (int k = threadIdx.x; k < nblk; k += ST_THREADS) fold5(r, partial + 5 * k);
+    if (post)
+        for (int k = threadIdx.x; k < nblk_post; k += ST_THREADS) fold5(q, bound_partial + 5 * k);
     for (int i = 0; i < 5; ++i) { sh[0][i][threadIdx.x] = r[i]; sh[1][i][threadIdx.x] = q[i]; }
     __syncthreads();
     for (int w = ST_THREADS / 2; w > 0; w >>= 1) {
@@ -1039,26 +1039,11 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int
     }
 }
 
-// post-bounding mass / extrema
-__global__ void __launch_bounds__(UPD_THREADS) k_mass(DevMesh m, const double *alpha, double *partial,
-                                                      unsigned *status)
+__global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int nblk, const int *counters,
+                                                      double *stats, int post, const double *bound_partial,
+                                                      int nblk_post)
 {
-    double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
-    bool bad = false, zero = false;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
-        double a = alpha[c];
-        if (is_pzero(a)) { zero = true; continue; }  // +0 adds nothing to the mass
-        v[1] += m.vc[c] * a;
-        v[2] = fmin(v[2], a);
-        v[3] = fmax(v[3], a);
-        bad |= gt_pos(a, 1.0 + BOUND_FLAG) || lt_neg(a, BOUND_FLAG);
-    }
-    if (zero) {
-        v[2] = fmin(v[2], 0.0);
-        v[3] = fmax(v[3], 0.0);
-    }
-    if (bad) atomicOr(status, VOF_ST_BOUND_RESIDUAL);
-    block_reduce5(v, partial + 5 * blockIdx.x);
+    stats_block(partial, nblk, counters, stats, post, bound_partial, nblk_post);
 }
 
 // ------------------------------------------------- bounding pass (reading R10)
@@ -1106,7 +1091,6 @@ struct BoundBufs {
     int *dg;             // per source: number of face neighbours
     int *left;           // out: sources left after the local passes
     int cap, cap_pend;
-    int *gc;             // grid-shared counters [3]
 };
 
 
@@ -1125,12 +1109,13 @@ __device__ __forceinline__ int first_source(const DevMesh &m, const double *alph
     return first;
 }
 
-// The local pass as five grid kernels over the source list (count on the
-// device): room, receiver scales, placement, new values, apply.
-__global__ void k_bp_room(DevMesh m, const double *alpha, BoundBufs b)
+// The local pass as five phases over the source list (count on the device):
+// room, receiver scales, placement, new values, apply; t0 / nt: this thread's
+// index and the thread count of the grid.
+__device__ void bp_room(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
 {
     const int n = min(*b.n0, b.cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (long i = t0; i < n; i += nt) {
         int c = b.la[i];
         double Cp = 0.0, Cm = 0.0;
         int dg = 0;
@@ -1149,11 +1134,11 @@ __global__ void k_bp_room(DevMesh m, const double *alpha, BoundBufs b)
 // one thread per (source, face slot): slot j takes the faces j, j + BP_SLOTS, ...
 constexpr int BP_SLOTS = 8;
 
-__global__ void k_bp_scale(DevMesh m, const double *alpha, BoundBufs b)
+__device__ void bp_scale(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
 {
     const long n = min(*b.n0, b.cap);
     double *bs = b.bs;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n * BP_SLOTS; t += (long)gridDim.x * blockDim.x) {
+    for (long t = t0; t < n * BP_SLOTS; t += nt) {
         int c = b.la[t / BP_SLOTS];
         for (int k = m.cptr[c] + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
             int r = m.cnb[k];
@@ -1172,11 +1157,11 @@ __global__ void k_bp_scale(DevMesh m, const double *alpha, BoundBufs b)
     }
 }
 
-__global__ void k_bp_place(DevMesh m, const double *alpha, BoundBufs b)
+__device__ void bp_place(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
 {
     const int n = min(*b.n0, b.cap);
     double *bs = b.bs;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (long i = t0; i < n; i += nt) {
         int c = b.la[i];
         double a = alpha[c], V = m.vc[c];
         double *q = bs + BS_N * (size_t)c;
@@ -1196,11 +1181,12 @@ __global__ void k_bp_place(DevMesh m, const double *alpha, BoundBufs b)
 
 // new values of the sources and their neighbours, each cell once: by the
 // lowest-index source in its closed face neighbourhood
-__global__ void k_bp_new(DevMesh m, const double *alpha, BoundBufs b, int *npend, unsigned *status)
+__device__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b, int *npend, unsigned *status,
+                       long t0, long nt)
 {
     const long n = min(*b.n0, b.cap);
     const double *bs = b.bs;
-    for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < n * BP_SLOTS; t += (long)gridDim.x * blockDim.x) {
+    for (long t = t0; t < n * BP_SLOTS; t += nt) {
         int c = b.la[t / BP_SLOTS];
         // slot 0 takes the source itself (k = cptr[c] - 1)
         for (int k = m.cptr[c] - 1 + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
@@ -1235,10 +1221,10 @@ __global__ void k_bp_new(DevMesh m, const double *alpha, BoundBufs b, int *npend
     }
 }
 
-__global__ void k_bp_apply(double *alpha, const int *pc, const double *pa, const int *npend, int cap)
+__device__ void bp_apply(double *alpha, const int *pc, const double *pa, const int *npend, int cap, long t0, long nt)
 {
     const int n = min(*npend, cap);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) alpha[pc[i]] = pa[i];
+    for (long i = t0; i < n; i += nt) alpha[pc[i]] = pa[i];
 }
 
 // Global step for what the local pass leaves: the total excess (deficit) of a
@@ -1249,14 +1235,15 @@ __global__ void k_bp_apply(double *alpha, const int *pc, const double *pa, const
 // segments in order (deterministic).
 constexpr int GB_THREADS = 256;
 
-__global__ void __launch_bounds__(GB_THREADS) k_bound_seg_reduce(DevMesh m, const double *alpha, const int4 *seg,
-                                                                 double *spartial, int *nleft)
+// one segment, by a whole block of GB_THREADS threads
+// A thread takes the cells c, c + blockDim.x, ... of the segment in order; the
+// loads of SEG_UNROLL consecutive ones of its cells are issued together.
+constexpr int SEG_UNROLL = 4;
+__device__ void seg_reduce(const DevMesh &m, const double *alpha, int4 sg, double *spartial, int *nleft)
 {
-    const int4 sg = seg[blockIdx.x];
     double v[4] = {0.0, 0.0, 0.0, 0.0};  // Ep, Em, Sp, Sm
     int left = 0;
-    for (int c = sg.y + threadIdx.x; c < sg.z; c += blockDim.x) {
-        double a = alpha[c];
+    auto cell = [&](int c, double a) {
         if (gt_pos(a, 1.0 + BOUND_TOL)) { v[0] += (a - 1.0) * m.vc[c]; ++left; }
         else if (lt_neg(a, BOUND_TOL)) { v[1] += -a * m.vc[c]; ++left; }
         else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) {
@@ -1264,7 +1251,17 @@ __global__ void __launch_bounds__(GB_THREADS) k_bound_seg_reduce(DevMesh m, cons
             v[2] += (1.0 - a) * V;
             v[3] += a * V;
         }
+    };
+    const int step = blockDim.x;
+    int c = sg.y + threadIdx.x;
+    for (; c + (SEG_UNROLL - 1) * step < sg.z; c += SEG_UNROLL * step) {
+        double a[SEG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < SEG_UNROLL; ++u) a[u] = alpha[c + u * step];
+#pragma unroll
+        for (int u = 0; u < SEG_UNROLL; ++u) cell(c + u * step, a[u]);
     }
+    for (; c < sg.z; c += step) cell(c, alpha[c]);
     left = __reduce_add_sync(0xffffffffu, left);
     if ((threadIdx.x & 31) == 0 && left) atomicAdd(nleft, left);
     __shared__ double sh[4][GB_THREADS / 32];
@@ -1278,14 +1275,15 @@ __global__ void __launch_bounds__(GB_THREADS) k_bound_seg_reduce(DevMesh m, cons
         for (int i = 0; i < 4; ++i) {
             double r = 0.0;
             for (int k = 0; k < GB_THREADS / 32; ++k) r += sh[i][k];
-            spartial[4 * blockIdx.x + i] = r;
+            spartial[i] = r;
         }
+    __syncthreads();
 }
 
-__global__ void k_bound_region_totals(const int *reg_seg, int nreg, const double *spartial, double *totals)
+// region r, by a whole warp
+__device__ void region_totals(const int *reg_seg, int r, const double *spartial, double *totals)
 {
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (r >= nreg) return;
+    const int lane = threadIdx.x & 31;
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = reg_seg[r] + lane; k < reg_seg[r + 1]; k += 32)
         for (int i = 0; i < 4; ++i) t[i] += spartial[4 * k + i];
@@ -1295,30 +1293,155 @@ __global__ void k_bound_region_totals(const int *reg_seg, int nreg, const double
     }
 }
 
-__global__ void __launch_bounds__(GB_THREADS) k_bound_global_apply(DevMesh m, double *alpha, const int4 *seg,
-                                                                   const double *totals)
+// one segment, by a whole block: the global step where its region needs one,
+// then the segment's share of the post-bounding mass and extrema (v as in the
+// update partials; +0 cells add nothing to the mass and set 'zero')
+__device__ void seg_apply(const DevMesh &m, double *alpha, int4 sg, const double *totals, double v[5], bool &zero,
+                          bool &bad)
 {
-    const int4 sg = seg[blockIdx.x];
     const double *tt = totals + 4 * sg.x;
     const double Ep = tt[0], Em = tt[1], Sp = tt[2], Sm = tt[3];
-    if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return;
-    for (int c = sg.y + threadIdx.x; c < sg.z; c += blockDim.x) {
-        double a = alpha[c];
-        if (gt_pos(a, 1.0 + BOUND_TOL)) alpha[c] = 1.0;
-        else if (lt_neg(a, BOUND_TOL)) alpha[c] = 0.0;
-        else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) {
-            double V = m.vc[c], dV = 0.0;
-            if (Ep > 0.0) dV += Ep * ((1.0 - a) * V / Sp);
-            if (Em > 0.0) dV -= Em * (a * V / Sm);
-            alpha[c] = (a * V + dV) / V;
+    const bool apply = !((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm);
+    auto cell = [&](int c, double a) {
+        if (apply) {
+            if (gt_pos(a, 1.0 + BOUND_TOL)) alpha[c] = a = 1.0;
+            else if (lt_neg(a, BOUND_TOL)) alpha[c] = a = 0.0;
+            else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) {
+                double V = m.vc[c], dV = 0.0;
+                if (Ep > 0.0) dV += Ep * ((1.0 - a) * V / Sp);
+                if (Em > 0.0) dV -= Em * (a * V / Sm);
+                alpha[c] = a = (a * V + dV) / V;
+            }
         }
+        if (is_pzero(a)) { zero = true; return; }
+        v[1] += m.vc[c] * a;
+        v[2] = fmin(v[2], a);
+        v[3] = fmax(v[3], a);
+        bad |= gt_pos(a, 1.0 + BOUND_FLAG) || lt_neg(a, BOUND_FLAG);
+    };
+    const int step = blockDim.x;
+    int c = sg.y + threadIdx.x;
+    for (; c + (SEG_UNROLL - 1) * step < sg.z; c += SEG_UNROLL * step) {
+        double a[SEG_UNROLL];
+#pragma unroll
+        for (int u = 0; u < SEG_UNROLL; ++u) a[u] = alpha[c + u * step];
+#pragma unroll
+        for (int u = 0; u < SEG_UNROLL; ++u) cell(c + u * step, a[u]);
     }
+    for (; c < sg.z; c += step) cell(c, alpha[c]);
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident): a block
+// arrives on the count; the last to arrive resets it and advances the generation
+// gen, which the others poll with a growing pause (count and generation sit
+// on separate cache lines, so the polls do not hold up the arrivals).  A wait
+// gives up after BAR_SPIN_LIMIT polls (seconds), flags VOF_ST_TIMEOUT and
+// returns: the launch's results are then not to be trusted, and the flag says
+// so.
+constexpr long BAR_SPIN_LIMIT = 4000000;
+__device__ void grid_sync(unsigned *count, unsigned *generation, unsigned *status)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = generation;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            atomicExch(count, 0u);
+            __threadfence();
+            atomicAdd(generation, 1u);
+        } else {
+            long it = 0;
+            unsigned pause = 32;
+            while (*gen == g) {
+                if (++it > BAR_SPIN_LIMIT) { atomicOr(status, VOF_ST_TIMEOUT); break; }
+                __nanosleep(pause);
+                if (pause < 1024) pause <<= 1;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// The whole bounding pass, the post-bounding mass and the step statistics in
+// one cooperative launch, a grid barrier between the phases: local pass
+// (room, scales, placement, new values, apply), segment sums, region totals,
+// global step with the mass partials, statistics (block 0).  Each phase does
+// the arithmetic, in the order, of the pass as separate kernels.
+struct BoundStep {
+    double *alpha;
+    BoundBufs b;
+    int *npend;
+    const int4 *seg;
+    int nseg;
+    double *gpartial;            // 4 per segment
+    int *nleft;
+    const int *reg_seg;
+    int nreg;
+    double *reg_tot;
+    double *mpartial;            // 5 per block: post-bounding mass, extrema
+    const double *upartial;      // the update kernel's partials
+    int nupd;
+    const int *counters;         // or null: no counter statistics
+    double *stats;
+    unsigned *bar_count;         // grid barrier: arrivals (zero before the launch)
+    unsigned *bar_gen;           // and generation (any value)
+    unsigned *status;
+};
+
+constexpr int BA_THREADS = 256;
+static_assert(BA_THREADS == GB_THREADS && BA_THREADS == UPD_THREADS && BA_THREADS == ST_THREADS,
+              "the phases share one block shape");
+
+__global__ void __launch_bounds__(BA_THREADS) k_bound_step(DevMesh m, BoundStep a)
+{
+    const long t0 = blockIdx.x * (long)blockDim.x + threadIdx.x, nt = (long)gridDim.x * blockDim.x;
+    // the local pass has few items (sources x slots): item i goes to block
+    // i mod gridDim.x, so that they spread over every SM rather than fill the
+    // first few blocks (the FP64 divisions of a phase run on all SMs' units)
+    const long tl = threadIdx.x * (long)gridDim.x + blockIdx.x;
+    bp_room(m, a.alpha, a.b, tl, nt);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    bp_scale(m, a.alpha, a.b, tl, nt);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    bp_place(m, a.alpha, a.b, tl, nt);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    bp_new(m, a.alpha, a.b, a.npend, a.status, tl, nt);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    bp_apply(a.alpha, a.b.pc, a.b.pa, a.npend, a.b.cap_pend, tl, nt);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    for (int sgi = blockIdx.x; sgi < a.nseg; sgi += gridDim.x)
+        seg_reduce(m, a.alpha, a.seg[sgi], a.gpartial + 4 * (size_t)sgi, a.nleft);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    for (int r = (int)(t0 >> 5); r < a.nreg; r += (int)(nt >> 5)) region_totals(a.reg_seg, r, a.gpartial, a.reg_tot);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
+    bool zero = false, bad = false;
+    for (int sgi = blockIdx.x; sgi < a.nseg; sgi += gridDim.x) seg_apply(m, a.alpha, a.seg[sgi], a.reg_tot, v, zero, bad);
+    if (zero) {
+        v[2] = fmin(v[2], 0.0);
+        v[3] = fmax(v[3], 0.0);
+    }
+    if (bad) atomicOr(a.status, VOF_ST_BOUND_RESIDUAL);
+    block_reduce5(v, a.mpartial + 5 * blockIdx.x);
+    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (blockIdx.x == 0) stats_block(a.upartial, a.nupd, a.counters, a.stats, 1, a.mpartial, gridDim.x);
 }
 
 __global__ void k_zero_int(int *p, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = 0;
+}
+
+// the update group's counters: violations before / after the local pass,
+// pending cells, and the grid barrier's arrival count
+__global__ void k_zero_update(int *cnt)
+{
+    const int i = threadIdx.x;
+    if (i < 3) cnt[CNT_VIOL0 + i] = 0;
+    if (i == 3) cnt[CNT_BAR] = 0;
 }
 
 // ============================================== band classification (A2, R9)
@@ -1379,6 +1502,16 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Grid of the update kernel: the blocks resident at once (at most
+// UPD_BLOCKS), so that no block of the grid-stride loop waits for a second wave.
+template <class K>
+int resident_blocks(K kernel, int sms)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, UPD_THREADS, 0) != cudaSuccess || occ < 1) occ = 1;
+    return sms * occ < UPD_BLOCKS ? sms * occ : UPD_BLOCKS;
+}
+
 }  // namespace
 
 // ================================================================ launchers
@@ -1397,6 +1530,12 @@ static int num_sms(int dev)
         g_sms = v > 0 ? v : 148;
     }
     return g_sms;
+}
+static int g_upd_blocks = 0;
+static int upd_blocks(int dev)
+{
+    if (g_upd_blocks == 0) g_upd_blocks = resident_blocks(k_update, num_sms(dev));
+    return g_upd_blocks;
 }
 
 int launch_setup_geometry(vof_ctx *c, cudaStream_t s)
@@ -1524,23 +1663,37 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
     return VOF_OK;
 }
 
-static int run_bounding(vof_ctx *c, double *alpha, cudaStream_t s, int *launches)
+// The bounding pass, post-bounding mass and statistics: one cooperative
+// launch of k_bound_step, as many blocks as are resident at once (at most
+// UPD_BLOCKS: the mass partials' room).
+static int g_bound_blocks = 0;
+static int launch_bound_step(vof_ctx *c, double *alpha, int nupd, const int *counters, double *stats,
+                             cudaStream_t s)
 {
-    BoundBufs b{c->viol[0], c->viol[1], c->counters + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, c->dgi,
-                c->counters + CNT_VIOL1, c->nc, 8 * c->nc, c->counters + 12};
-    const int g = num_sms(c->device) * 2;
-    int *npend = c->counters + CNT_PEND;
-    k_zero_int<<<1, 32, 0, s>>>(npend, 1);
-    k_bp_room<<<g, 128, 0, s>>>(c->m, alpha, b);
-    k_bp_scale<<<g, 128, 0, s>>>(c->m, alpha, b);
-    k_bp_place<<<g, 128, 0, s>>>(c->m, alpha, b);
-    k_bp_new<<<g, 128, 0, s>>>(c->m, alpha, b, npend, c->status);
-    k_bp_apply<<<g, 128, 0, s>>>(alpha, c->pend_c, c->pend_a, npend, b.cap_pend);
-    k_bound_seg_reduce<<<c->nseg, GB_THREADS, 0, s>>>(c->m, alpha, c->seg, c->gpartial, c->counters + CNT_VIOL1);
-    k_bound_region_totals<<<(c->nreg + 3) / 4, 128, 0, s>>>(c->reg_seg, c->nreg, c->gpartial, c->reg_tot);
-    k_bound_global_apply<<<c->nseg, GB_THREADS, 0, s>>>(c->m, alpha, c->seg, c->reg_tot);
-    *launches += 9;
-    LAUNCH_CHECK();
+    if (g_bound_blocks == 0) {
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bound_step, BA_THREADS, 0) != cudaSuccess || occ < 1)
+            return VOF_ERR_CUDA;
+        g_bound_blocks = std::min(num_sms(c->device) * occ, UPD_BLOCKS);
+    }
+    int *cnt = c->counters;
+    BoundStep a{alpha,
+                BoundBufs{c->viol[0], c->viol[1], cnt + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, c->dgi,
+                          cnt + CNT_VIOL1, c->nc, 8 * c->nc},
+                cnt + CNT_PEND, c->seg, c->nseg, c->gpartial, cnt + CNT_VIOL1, c->reg_seg, c->nreg, c->reg_tot,
+                c->partial + 5 * UPD_BLOCKS, c->partial, nupd, counters, stats,
+                reinterpret_cast<unsigned *>(cnt + CNT_BAR), reinterpret_cast<unsigned *>(cnt + CNT_BARGEN), c->status};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(g_bound_blocks);
+    cfg.blockDim = dim3(BA_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_bound_step, c->m, a) != cudaSuccess) return VOF_ERR_CUDA;
     return VOF_OK;
 }
 
@@ -1548,21 +1701,19 @@ int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cu
 {
     int *cnt = c->counters;
     int launches = 0;
-    k_zero_int<<<1, 32, 0, s>>>(cnt + CNT_VIOL0, 2);
-    k_update<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, Va, c->partial, c->bound ? c->viol[0] : nullptr,
-                                                cnt + CNT_VIOL0, c->nc, c->status);
+    k_zero_update<<<1, 32, 0, s>>>(cnt);
+    const int nu = upd_blocks(c->device);
+    k_update<<<nu, UPD_THREADS, 0, s>>>(c->m, alpha, Va, c->partial, c->bound ? c->viol[0] : nullptr,
+                                        cnt + CNT_VIOL0, c->nc, c->status);
     LAUNCH_CHECK();
-    launches += 2;
+    launches += 3;
     if (c->bound) {
-        int r = run_bounding(c, alpha, s, &launches);
+        int r = launch_bound_step(c, alpha, nu, nullptr, stats ? stats : c->stats_dev, s);
         if (r) return r;
-        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(c->m, alpha, c->partial + 5 * UPD_BLOCKS, c->status);
-        ++launches;
+    } else {
+        k_stats<<<1, ST_THREADS, 0, s>>>(c->partial, nu, nullptr, stats ? stats : c->stats_dev, 0, nullptr, 0);
+        LAUNCH_CHECK();
     }
-    k_stats<<<1, ST_THREADS, 0, s>>>(c->partial, UPD_BLOCKS, nullptr, stats ? stats : c->stats_dev, c->bound,
-                             c->partial + 5 * UPD_BLOCKS);
-    ++launches;
-    LAUNCH_CHECK();
     c->launches = launches;
     return VOF_OK;
 }
@@ -1625,21 +1776,19 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     LAUNCH_CHECK();
     MARK(4);
     // update + bounding + stats
-    k_zero_int<<<1, 32, 0, s>>>(cnt + CNT_VIOL0, 2);
-    k_update<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->Va, c->partial, c->bound ? c->viol[0] : nullptr,
-                                                cnt + CNT_VIOL0, c->nc, c->status);
-    launches += 2;
+    k_zero_update<<<1, 32, 0, s>>>(cnt);
+    const int nu = upd_blocks(c->device);
+    k_update<<<nu, UPD_THREADS, 0, s>>>(m, alpha, c->Va, c->partial, c->bound ? c->viol[0] : nullptr,
+                                        cnt + CNT_VIOL0, c->nc, c->status);
+    launches += 3;
     LAUNCH_CHECK();
     if (c->bound) {
-        int r = run_bounding(c, alpha, s, &launches);
+        int r = launch_bound_step(c, alpha, nu, cnt, stats ? stats : c->stats_dev, s);
         if (r) return r;
-        k_mass<<<UPD_BLOCKS, UPD_THREADS, 0, s>>>(m, alpha, c->partial + 5 * UPD_BLOCKS, c->status);
-        ++launches;
+    } else {
+        k_stats<<<1, ST_THREADS, 0, s>>>(c->partial, nu, cnt, stats ? stats : c->stats_dev, 0, nullptr, 0);
+        LAUNCH_CHECK();
     }
-    k_stats<<<1, ST_THREADS, 0, s>>>(c->partial, UPD_BLOCKS, cnt, stats ? stats : c->stats_dev, c->bound,
-                             c->partial + 5 * UPD_BLOCKS);
-    ++launches;
-    LAUNCH_CHECK();
     MARK(5);
 #undef MARK
     c->launches = launches;

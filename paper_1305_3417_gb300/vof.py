@@ -20,7 +20,7 @@ VOF_OK = 0
 FP64, MIXED = 0, 1
 INTERFACE, ORIENTED, FULL = 1, 2, 4
 STATUS_BITS = {1: "POS_NOT_CONVERGED", 2: "CORR_NOT_CONVERGED", 4: "CLIP_OVERFLOW",
-               8: "BOUND_RESIDUAL", 16: "INDEX", 32: "CAPACITY"}
+               8: "BOUND_RESIDUAL", 16: "INDEX", 32: "CAPACITY", 64: "TIMEOUT"}
 S = dict(mass_before=0, mass_after=1, min_pre=2, max_pre=3, min_post=4, max_post=5,
          n_interface=6, n_band=7, max_pos_it=8, max_corr_it=9, boundary_out=10, n_fallback=11,
          n_bound_sources=12, n_bound_left=13)
