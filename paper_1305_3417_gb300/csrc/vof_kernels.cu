@@ -149,6 +149,23 @@ __global__ void k_point_velocity(DevMesh m, const double *__restrict__ Uc, doubl
 // then Alg. 1 with the fill function summed over the cell tetrahedra, one or
 // two per lane, each a closed-form cut fraction of its sorted projections.
 
+// Reciprocal for the fill of the mixed positioning: FP32 division for R =
+// float; for R = double the FP32 reciprocal refined by one Newton-Raphson step
+// r <- r + r (1 - x r) in FP64, whose relative error is about the square of
+// the FP32 one (~4e-15), with exact division where x is outside the FP32
+// range.  The FP64 pipe of this part runs at 1/64 of the FP32 rate: this is a
+// conversion pair and two FMAs in place of a full FP64 division.
+__device__ __noinline__ double exact_rcp(double x) { return 1.0 / x; }
+template <class R> __device__ __forceinline__ R mx_rcp(R x);
+template <> __device__ __forceinline__ float mx_rcp<float>(float x) { return 1.0f / x; }
+template <> __device__ __forceinline__ double mx_rcp<double>(double x)
+{
+    const float r0 = __frcp_rn((float)x);
+    if (!isfinite(r0) || r0 == 0.0f) return exact_rcp(x);
+    const double r = (double)r0;
+    return fma(r, fma(-x, r, 1.0), r);
+}
+
 // Cut fraction of a tetrahedron with sorted projections h0..h3 below level d,
 // and its derivative in d (the cut area over the volume): the same closed form
 // as frac_below, differentiated piece by piece.
@@ -159,16 +176,16 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
     if (d <= h0) return R(0);
     if (d >= h3) return R(1);
     if (d <= h1) {
-        const R x = d - h0, p = R(1) / ((h1 - h0) * (h2 - h0) * (h3 - h0));
+        const R x = d - h0, p = mx_rcp<R>((h1 - h0) * (h2 - h0) * (h3 - h0));
         df = R(3) * x * x * p;
         return x * x * x * p;
     }
     if (d >= h2) {
-        const R y = h3 - d, q = R(1) / ((h3 - h0) * (h3 - h1) * (h3 - h2));
+        const R y = h3 - d, q = mx_rcp<R>((h3 - h0) * (h3 - h1) * (h3 - h2));
         df = R(3) * y * y * q;
         return R(1) - y * y * y * q;
     }
-    const R ra = R(1) / (h2 - h0), rb = R(1) / (h3 - h0), rc = R(1) / (h2 - h1), re = R(1) / (h3 - h1);
+    const R ra = mx_rcp<R>(h2 - h0), rb = mx_rcp<R>(h3 - h0), rc = mx_rcp<R>(h2 - h1), re = mx_rcp<R>(h3 - h1);
     const R a = (d - h0) * ra, b = (d - h0) * rb, c = (d - h1) * rc, e = (d - h1) * re;
     df = ra * b + a * rb + ra * (R(1) - b) * e - a * rb * e + a * (R(1) - b) * re - ra * c * e +
          (R(1) - a) * rc * e + (R(1) - a) * c * re;
@@ -185,7 +202,7 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // G lanes per cell: 32, or 8 where every cell has at most 16 tetrahedra (a
 // tetrahedral mesh: four cells per warp); reductions over the cell's lanes
 template <bool LIST, bool MIXED, int G>
-__global__ void __launch_bounds__(128) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
+__global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
                                                      uint8_t *fout, int *itout, int *maxit, unsigned *status,
@@ -318,6 +335,7 @@ __global__ void __launch_bounds__(128) k_reconstruct(DevMesh m, const double *__
                         if (!sure && ++near >= 2) break;
                     }
                     // ---- FP64 Newton from there
+                    const double rV = 1.0 / V;
                     double A = href + (double)Ar, B = href + (double)Br;
                     x = href + (double)xr;
                     while (it < POS_MAXIT) {
@@ -329,13 +347,16 @@ __global__ void __launch_bounds__(128) k_reconstruct(DevMesh m, const double *__
                                 part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
                                 dpart += vk[s] * df;
                             }
-                        const double gx = tsum(part) / V - a;
+                        const double gx = tsum(part) * rV - a;
                         dpart = tsum(dpart);
                         ++it;
                         if (fabs(gx) <= POS_TOL) break;
                         if (gx < 0) A = x; else B = x;
                         if (B - A <= 1e-15 * (dmax - dmin)) break;
-                        double xn = x - gx * V / dpart;
+                        // the slope only sets the rate, not the root: an FP32
+                        // reciprocal of it (a step that leaves the bracket, or is
+                        // NaN, is replaced by bisection)
+                        double xn = x - gx * V * (double)__frcp_rn((float)dpart);
                         if (!(xn > A && xn < B)) xn = 0.5 * (A + B);
                         x = xn;
                     }
@@ -344,6 +365,7 @@ __global__ void __launch_bounds__(128) k_reconstruct(DevMesh m, const double *__
                     // estimate (near an end the fill grows like the cube of the
                     // distance from the extreme vertex)
                     double A = dmin, B = dmax;
+                    const double rV = 1.0 / V;
                     x = a < 0.5 ? dmin + (dmax - dmin) * cbrt(a) : dmax - (dmax - dmin) * cbrt(1.0 - a);
                     while (it < POS_MAXIT) {
                         double part = 0.0, dpart = 0.0;
@@ -354,13 +376,16 @@ __global__ void __launch_bounds__(128) k_reconstruct(DevMesh m, const double *__
                                 part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
                                 dpart += vk[s] * df;
                             }
-                        const double gx = tsum(part) / V - a;
+                        const double gx = tsum(part) * rV - a;
                         dpart = tsum(dpart);
                         ++it;
                         if (fabs(gx) <= POS_TOL) break;
                         if (gx < 0) A = x; else B = x;
                         if (B - A <= 1e-15 * (dmax - dmin)) break;
-                        double xn = x - gx * V / dpart;
+                        // the slope only sets the rate, not the root: an FP32
+                        // reciprocal of it (a step that leaves the bracket, or is
+                        // NaN, is replaced by bisection)
+                        double xn = x - gx * V * (double)__frcp_rn((float)dpart);
                         if (!(xn > A && xn < B)) xn = 0.5 * (A + B);
                         x = xn;
                     }
