@@ -38,6 +38,28 @@ UNIT = "M face fluxes/s"
 # algorithmic flop cost model of the phase-flux kernel (primitive costs: signed
 # distance 6, edge intersection 10, tetrahedron volume 17, plane from 3 points 20)
 FLOPS_PER_PAIR = 16 * 6 + 4 * 20     # 4 planes of the cell tetrahedron, 4x4 distances
+
+# DRAM bytes per launch of the mixed phase-flux kernel: dram__bytes_read.sum +
+# dram__bytes_write.sum, mean of three launches (the 4th to 6th) of one ncu
+# capture of the default command (ncu --metrics dram__bytes_read.sum,
+# dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_phase_flux_mixed -s 3
+# -c 3 python bench.py --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0);
+# valid while the kernel's sources hash to the captured digest, else null.
+TRAFFIC = {("deform3d", 128, "mixed"): {"bytes": 67.99e6,
+           "sources_sha256": "6b0d06b17013e5365a8d5f0d0de8610afb484975cc90b056c79af87e3a9d17bd"}}
+TRAFFIC_SOURCES = ["paper_1305_3417_gb300/csrc/vof_mixed.cu", "paper_1305_3417_gb300/csrc/vof_device.cuh"]
+
+
+def captured_traffic(workload, n, precision):
+    t = TRAFFIC.get((workload, n, precision))
+    if t is None:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return t["bytes"] if h.hexdigest() == t["sources_sha256"] else None
 FLOPS_PER_CUT = 4 * 10 + 3 * 17      # edge intersections + resulting tetrahedra volumes
 
 
@@ -113,6 +135,26 @@ def barrier(world):
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
+
+
+def host_link_gbps(stream, host):
+    """Copy bandwidth between pinned host memory and the device on this machine
+    (GB/s, three timed copies each way of the given pinned tensor): the host
+    link bounds the end-to-end number, whose copies are in its timed region."""
+    import torch
+    dev = torch.empty_like(host, device="cuda")
+    out = {}
+    for name, dst, src in (("h2d", dev, host), ("d2h", host, dev)):
+        dst.copy_(src, non_blocking=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = 3 * host.numel() * host.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del dev
+    return out
 
 
 def max_over_ranks(x, world, device=None):
@@ -463,6 +505,7 @@ def main():
     e2e = faces / (ms_e2e * 1e-3) / 1e6
     h2d = 8 * m.n_cells + 24 * m.n_cells + 8 * m.n_faces
     d2h = 8 * m.n_cells + 8 * vof.S_LEN
+    link = host_link_gbps(stream, hU[0])
 
     # ---- roofline of the dominant kernel group
     pk, pk_src = peaks()
@@ -472,13 +515,17 @@ def main():
         fl = (work["pairs"] * FLOPS_PER_PAIR + work["cuts"] * FLOPS_PER_CUT) / max(nprof, 1)
         alu = vof.vof_probe_fma(local, prec)
         achieved = fl / (per_launch[dom] * 1e-3) / 1e12
+        traffic = captured_traffic(args.workload, m.shape[0], "fp64" if prec == vof.FP64 else "mixed") \
+            if args.skip == 0 else None
         roof = {"kernel": "k_phase_flux", "bound": "alu", "achieved": achieved, "peak": alu / 1e12,
-                "unit": "TFLOP/s", "frac": achieved * 1e12 / alu, "traffic": None,
+                "unit": "TFLOP/s", "frac": achieved * 1e12 / alu, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu capture)",
                 "peak_source": f"measured {'FP64' if prec == vof.FP64 else 'FP32'} FMA probe (vof_probe_fma)",
                 "work_per_launch": {"pairs": work["pairs"] / max(nprof, 1), "cuts": work["cuts"] / max(nprof, 1),
                                     "band_faces": work["faces"] / max(nprof, 1)}}
     else:
-        # HBM-bound groups: algorithmic bytes per internal face
+        # HBM-bound groups: algorithmic bytes per internal face (72 B: flux, owner and
+        # neighbour, face points, alpha and volume, point data, per face of a hex mesh)
         byts = 72.0 * m.n_internal
         achieved = byts / (per_launch[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -500,7 +547,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == vof.FP64 else "f32+f64",
                 "data": "synthetic", "config": config(args, w),
-                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": ms_e2e / args.steps, "host_link_GBps": link},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "other_form": other,
                 "learned_guess": guess,
                 "clocks": clk.summary(),

@@ -182,7 +182,9 @@ int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, d
  * alpha is copied in order on `stream`.  Uc and F are copied on an internal
  * stream (created with four events at the first call) into one of two device
  * buffer pairs, alternating by call, as soon as the step two calls back is
- * done: the copies of consecutive calls overlap the previous step's kernels,
+ * done and the previous call's alpha copy is in (so that this, on the step's
+ * critical path, never waits in the copy engine behind them): the copies of
+ * consecutive calls overlap the previous step's kernels,
  * so Uc and F must hold this step's values when the call is made (they are not
  * ordered after earlier work on `stream`). */
 int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,

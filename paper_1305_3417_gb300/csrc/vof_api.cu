@@ -124,6 +124,7 @@ void vof_destroy(vof_ctx *c)
     if (c->s_copy) cudaStreamDestroy(c->s_copy);
     if (c->ev_f) cudaEventDestroy(c->ev_f);
     if (c->ev_u) cudaEventDestroy(c->ev_u);
+    if (c->ev_ain) cudaEventDestroy(c->ev_ain);
     for (int i = 0; i < 2; ++i)
         if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
     if (c->s_aux) cudaStreamDestroy(c->s_aux);
@@ -510,24 +511,27 @@ int vof_advect_host(vof_ctx *c, double *alpha, const double *Uc, const double *F
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
     // F and U go to the staging pair of this call's parity on the copy stream,
-    // once the step that last read that pair (two calls back) is done: they
-    // overlap the previous step's kernels.  alpha (in place, so ordered after
+    // once the step that last read that pair (two calls back) is done and the
+    // previous call's alpha is in: they overlap the previous step's kernels.  alpha (in place, so ordered after
     // the previous step's read-back) goes on `stream`; the classification
     // waits for F, the flux correction (inside the step) for U.
     if (!c->s_copy && (cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking) ||
                        cudaEventCreateWithFlags(&c->ev_f, cudaEventDisableTiming) ||
                        cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming) ||
                        cudaEventCreateWithFlags(&c->ev_free[0], cudaEventDisableTiming) ||
-                       cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming)))
+                       cudaEventCreateWithFlags(&c->ev_free[1], cudaEventDisableTiming) ||
+                       cudaEventCreateWithFlags(&c->ev_ain, cudaEventDisableTiming)))
         return VOF_ERR_CUDA;
     const int p = c->h_par;
-    if (cudaStreamWaitEvent(c->s_copy, c->ev_free[p], 0) ||
+    // ev_ain: the previous call's alpha copy, which must not queue in the copy
+    // engine behind this call's larger copies (it is on the step's critical path)
+    if (cudaStreamWaitEvent(c->s_copy, c->ev_free[p], 0) || cudaStreamWaitEvent(c->s_copy, c->ev_ain, 0) ||
         cudaMemcpyAsync(c->h_F[p], F, sizeof(double) * c->nf, cudaMemcpyHostToDevice, c->s_copy) ||
         cudaEventRecord(c->ev_f, c->s_copy) ||
         cudaMemcpyAsync(c->h_Uc[p], Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->s_copy) ||
         cudaEventRecord(c->ev_u, c->s_copy) ||
         cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
-        cudaStreamWaitEvent(s, c->ev_f, 0))
+        cudaEventRecord(c->ev_ain, s) || cudaStreamWaitEvent(s, c->ev_f, 0))
         return VOF_ERR_CUDA;
     c->h_par ^= 1;
     int r = launch_advect(c, c->h_alpha, c->h_Uc[p], c->h_F[p], dt, c->stats_dev, s, c->ev_u);

@@ -81,7 +81,7 @@ struct vof_ctx {
     double *h_Uc[2], *h_F[2];      // by call parity, so that a call's copies overlap the previous step
     int h_par;
     cudaStream_t s_copy;           // vof_advect_host: the velocity copy overlaps the first kernels
-    cudaEvent_t ev_f, ev_u, ev_free[2];
+    cudaEvent_t ev_f, ev_u, ev_free[2], ev_ain;
     cudaStream_t s_aux;            // the correction runs here, beside the reconstruction
     cudaEvent_t ev_fork, ev_join;
     int launches;

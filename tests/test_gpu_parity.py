@@ -290,6 +290,24 @@ def test_advect_host_matches_device(torch, O):
     assert np.array_equal(ha.numpy(), H(ta))
 
 
+def test_advect_host_pageable_buffers(torch, O):
+    """Host arrays that are not pinned (staged copies, synchronous with respect
+    to the host): the same step bit for bit."""
+    from paper_1305_3417_gb300 import vof
+    w, ctx, om = contexts(torch, O, "deform20")
+    F, U, dt = w.step_inputs(2)
+    ta = T(torch, w.alpha0)
+    st = ctx.advect(ta, T(torch, U), T(torch, F), dt)
+    ha = torch.from_numpy(w.alpha0.copy())
+    assert not ha.is_pinned()
+    hs = torch.zeros(vof.S_LEN, dtype=torch.float64)
+    vof.vof_advect_host(ctx.h, ha, torch.from_numpy(np.ascontiguousarray(U).reshape(-1).copy()),
+                        torch.from_numpy(F.copy()), dt, hs)
+    torch.cuda.synchronize()
+    assert np.array_equal(ha.numpy(), H(ta))
+    assert np.array_equal(hs.numpy(), H(st))
+
+
 def test_advect_host_steps_queued(torch, O):
     """Five host-buffer steps queued back to back (the velocity and flux copies
     of a call overlap the previous step, alternating between two device
