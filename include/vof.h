@@ -305,6 +305,16 @@ int vof_work_counts(vof_ctx *ctx, unsigned long long counts[3], int reset, void 
  * Synchronous; allocates and frees one scalar of device memory. */
 int vof_probe_fma(int device, int precision, double *flops_per_s, void *stream);
 
+/* Check of the grid barrier inside the cooperative bounding kernel (no paper
+ * counterpart): a cooperative launch of two blocks per SM that pass four
+ * barriers, with a wait limit of 2000 polls (milliseconds).  skip_block >= 0
+ * makes that block leave at once, so that the others' waits run out: they set
+ * VOF_ST_TIMEOUT in the status word (vof_status) and leave; no wait is
+ * unbounded and the context stays usable.  skip_block = -1: every block
+ * arrives and nothing is flagged.  Asynchronous on `stream`; skip_block beyond
+ * the launch's blocks, or below -1: VOF_ERR_INVALID_ARG. */
+int vof_probe_barrier(vof_ctx *ctx, int skip_block, void *stream);
+
 /* Reconstruction for callers that cannot allocate device memory when they
  * call it -- code inside a host framework that owns every device allocation,
  * or a real-time loop that forbids cudaMalloc after start-up.  The paper has

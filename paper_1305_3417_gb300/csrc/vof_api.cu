@@ -597,6 +597,13 @@ int vof_profile_end(vof_ctx *c, double *group_ms, int *steps)
     return VOF_OK;
 }
 
+int vof_probe_barrier(vof_ctx *c, int skip_block, void *stream)
+{
+    if (!c || skip_block < -1) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_barrier_probe(c, skip_block, (cudaStream_t)stream);
+}
+
 int vof_work_counts(vof_ctx *c, unsigned long long counts[3], int reset, void *stream)
 {
     if (!c || !counts) return VOF_ERR_INVALID_ARG;

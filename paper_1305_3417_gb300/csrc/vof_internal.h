@@ -134,6 +134,9 @@ int launch_setup_mixed(vof_ctx *c, cudaStream_t s);
 int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg);
 // learned guess (vof_mlp.cu): offsets of the first min(nmax, batch) listed cells
 // (count on the device, or all nmax when count is NULL) into c->mlp_s0
+// the grid barrier's check: a cooperative launch in which block `skip` (if >= 0)
+// leaves at once, so that the other blocks' waits run out (VOF_ST_TIMEOUT)
+int launch_barrier_probe(vof_ctx *c, int skip, cudaStream_t s);
 int launch_mlp_guess(vof_ctx *c, const double *alpha, const int *cells, const int *count, int nmax,
                      cudaStream_t s);
 int mlp_cap(const vof_ctx *c);

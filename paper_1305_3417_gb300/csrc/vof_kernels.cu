@@ -1360,14 +1360,16 @@ __device__ void seg_apply(const DevMesh &m, double *alpha, int4 sg, const double
 // arrives on the count; the last to arrive resets it and advances the generation
 // gen, which the others poll with a growing pause (count and generation sit
 // on separate cache lines, so the polls do not hold up the arrivals).  A wait
-// gives up after BAR_SPIN_LIMIT polls (seconds), flags VOF_ST_TIMEOUT and
-// returns: the launch's results are then not to be trusted, and the flag says
-// so.
+// gives up after `limit` polls (BAR_SPIN_LIMIT: seconds) and flags VOF_ST_TIMEOUT;
+// grid_sync then returns false in every thread of the block, which leaves the
+// kernel (the blocks still waiting give up the same way: every wait ends).
 constexpr long BAR_SPIN_LIMIT = 4000000;
-__device__ void grid_sync(unsigned *count, unsigned *generation, unsigned *status)
+__device__ bool grid_sync(unsigned *count, unsigned *generation, unsigned *status, long limit = BAR_SPIN_LIMIT)
 {
+    __shared__ int gave_up;
     __syncthreads();
     if (threadIdx.x == 0) {
+        gave_up = 0;
         volatile unsigned *gen = generation;
         const unsigned g = *gen;
         __threadfence();
@@ -1379,7 +1381,11 @@ __device__ void grid_sync(unsigned *count, unsigned *generation, unsigned *statu
             long it = 0;
             unsigned pause = 32;
             while (*gen == g) {
-                if (++it > BAR_SPIN_LIMIT) { atomicOr(status, VOF_ST_TIMEOUT); break; }
+                if (++it > limit) {
+                    atomicOr(status, VOF_ST_TIMEOUT);
+                    gave_up = 1;
+                    break;
+                }
                 __nanosleep(pause);
                 if (pause < 1024) pause <<= 1;
             }
@@ -1387,6 +1393,7 @@ __device__ void grid_sync(unsigned *count, unsigned *generation, unsigned *statu
         __threadfence();
     }
     __syncthreads();
+    return !gave_up;
 }
 
 // The whole bounding pass, the post-bounding mass and the step statistics in
@@ -1427,20 +1434,20 @@ __global__ void __launch_bounds__(BA_THREADS) k_bound_step(DevMesh m, BoundStep 
     // first few blocks (the FP64 divisions of a phase run on all SMs' units)
     const long tl = threadIdx.x * (long)gridDim.x + blockIdx.x;
     bp_room(m, a.alpha, a.b, tl, nt);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     bp_scale(m, a.alpha, a.b, tl, nt);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     bp_place(m, a.alpha, a.b, tl, nt);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     bp_new(m, a.alpha, a.b, a.npend, a.status, tl, nt);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     bp_apply(a.alpha, a.b.pc, a.b.pa, a.npend, a.b.cap_pend, tl, nt);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     for (int sgi = blockIdx.x; sgi < a.nseg; sgi += gridDim.x)
         seg_reduce(m, a.alpha, a.seg[sgi], a.gpartial + 4 * (size_t)sgi, a.nleft);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     for (int r = (int)(t0 >> 5); r < a.nreg; r += (int)(nt >> 5)) region_totals(a.reg_seg, r, a.gpartial, a.reg_tot);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     double v[5] = {0.0, 0.0, 1e300, -1e300, 0.0};
     bool zero = false, bad = false;
     for (int sgi = blockIdx.x; sgi < a.nseg; sgi += gridDim.x) seg_apply(m, a.alpha, a.seg[sgi], a.reg_tot, v, zero, bad);
@@ -1450,8 +1457,20 @@ __global__ void __launch_bounds__(BA_THREADS) k_bound_step(DevMesh m, BoundStep 
     }
     if (bad) atomicOr(a.status, VOF_ST_BOUND_RESIDUAL);
     block_reduce5(v, a.mpartial + 5 * blockIdx.x);
-    grid_sync(a.bar_count, a.bar_gen, a.status);
+    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
     if (blockIdx.x == 0) stats_block(a.upartial, a.nupd, a.counters, a.stats, 1, a.mpartial, gridDim.x);
+}
+
+// The barrier's own check (a cooperative launch): every block passes `rounds`
+// barriers, except block `skip`, which leaves at once, so that the others'
+// waits run out after `limit` polls and flag VOF_ST_TIMEOUT (skip < 0: none
+// leaves and nothing is flagged).
+__global__ void k_barrier_probe(unsigned *count, unsigned *generation, unsigned *status, int skip, int rounds,
+                                long limit)
+{
+    if ((int)blockIdx.x == skip) return;
+    for (int r = 0; r < rounds; ++r)
+        if (!grid_sync(count, generation, status, limit)) return;
 }
 
 __global__ void k_zero_int(int *p, int n)
@@ -1719,6 +1738,24 @@ static int launch_bound_step(vof_ctx *c, double *alpha, int nupd, const int *cou
     cfg.attrs = at;
     cfg.numAttrs = 1;
     if (cudaLaunchKernelEx(&cfg, k_bound_step, c->m, a) != cudaSuccess) return VOF_ERR_CUDA;
+    return VOF_OK;
+}
+
+int launch_barrier_probe(vof_ctx *c, int skip, cudaStream_t s)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_barrier_probe, 128, 0) != cudaSuccess || occ < 1)
+        return VOF_ERR_CUDA;
+    const int blocks = num_sms(c->device) * std::min(occ, 2);
+    if (skip >= blocks) return VOF_ERR_INVALID_ARG;
+    unsigned *cnt = reinterpret_cast<unsigned *>(c->counters + CNT_BAR);
+    unsigned *gen = reinterpret_cast<unsigned *>(c->counters + CNT_BARGEN);
+    if (cudaMemsetAsync(cnt, 0, sizeof(unsigned), s) != cudaSuccess) return VOF_ERR_CUDA;
+    int rounds = 4;
+    long limit = 2000;  // with the pauses (up to ~1 us) a few milliseconds
+    void *args[] = {&cnt, &gen, &c->status, &skip, &rounds, &limit};
+    if (cudaLaunchCooperativeKernel((const void *)k_barrier_probe, dim3(blocks), dim3(128), args, 0, s) != cudaSuccess)
+        return VOF_ERR_CUDA;
     return VOF_OK;
 }
 

@@ -48,7 +48,7 @@ class _Options(ctypes.Structure):
 EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "vof_reconstruct",
            "vof_flux_polyhedra", "vof_correct_flux", "vof_phase_flux", "vof_update", "vof_advect",
            "vof_advect_host", "vof_status", "vof_last_launch_count", "vof_error_string",
-           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma",
+           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma", "vof_probe_barrier",
            "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
            "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
            "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess"]
@@ -87,6 +87,7 @@ def lib():
         "vof_profile_end": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "vof_work_counts": (I, [P, P, I, P]),
         "vof_probe_fma": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
+        "vof_probe_barrier": (I, [P, I, P]),
         "vof_batch_create": (I, [ctypes.POINTER(_Mesh), P, I, ctypes.POINTER(_Options), ctypes.POINTER(P)]),
         "vof_batch_destroy": (None, [P]),
         "vof_batch_context": (P, [P]),
@@ -283,6 +284,12 @@ def vof_work_counts(h, reset: bool = True, stream=None):
     c = (ctypes.c_ulonglong * 3)()
     _check(lib().vof_work_counts(h, c, int(bool(reset)), _stream(stream)), "vof_work_counts")
     return dict(pairs=int(c[0]), cuts=int(c[1]), faces=int(c[2]))
+
+
+def vof_probe_barrier(h, skip_block: int = -1, stream=None):
+    """Check of the cooperative kernels' grid barrier: block skip_block leaves at
+    once and the others' bounded waits run out (VOF_ST_TIMEOUT)."""
+    _check(lib().vof_probe_barrier(h, int(skip_block), _stream(stream)), "vof_probe_barrier")
 
 
 def vof_probe_fma(device: int = 0, precision: int = FP64, stream=None) -> float:

@@ -290,6 +290,28 @@ def test_advect_host_matches_device(torch, O):
     assert np.array_equal(ha.numpy(), H(ta))
 
 
+def test_grid_barrier_wait_runs_out(torch, O):
+    """The cooperative bounding kernel's grid barrier: with every block arriving
+    nothing is flagged; with one block leaving at once the others' bounded
+    waits run out, set VOF_ST_TIMEOUT and leave (no hang), and the context
+    still steps correctly afterwards."""
+    from paper_1305_3417_gb300 import vof
+    w, ctx, om = contexts(torch, O, "deform20")
+    vof.vof_probe_barrier(ctx.h, -1)
+    torch.cuda.synchronize()
+    assert ctx.status() == 0
+    vof.vof_probe_barrier(ctx.h, 0)
+    torch.cuda.synchronize()
+    assert ctx.status() & 64
+    assert ctx.status() == 0           # reading clears the word
+    F, U, dt = w.step_inputs(0)
+    ta = T(torch, w.alpha0)
+    ctx.advect(ta, T(torch, U), T(torch, F), dt)
+    oa, _, st = om.advect(w.alpha0.copy(), U, F, dt)
+    assert st == 0 and ctx.status() == 0
+    assert np.abs(H(ta) - oa).max() < 1e-11
+
+
 def test_advect_host_pageable_buffers(torch, O):
     """Host arrays that are not pinned (staged copies, synchronous with respect
     to the host): the same step bit for bit."""
