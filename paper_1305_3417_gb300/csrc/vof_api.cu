@@ -78,7 +78,7 @@ int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg)
     c->seg = dev_copy(c, seg.data(), seg.size(), &err);
     c->reg_seg = dev_copy(c, rs.data(), rs.size(), &err);
     c->gpartial = dev_alloc<double>(c, 4 * seg.size(), &err);
-    c->reg_tot = dev_alloc<double>(c, 4 * (size_t)nreg, &err);
+    c->reg_tot = dev_alloc<double>(c, 6 * (size_t)nreg, &err);  // per region: Ep, Em, Sp, Sm, Ep/Sp, Em/Sm
     if (err) return err;
     c->nseg = (int)seg.size();
     c->nreg = nreg;

@@ -1104,8 +1104,11 @@ __device__ __forceinline__ bool is_def(double a) { return a < -BOUND_TOL; }
 __device__ __forceinline__ double room_exc(double a, double V) { return (a >= 0.0 && a < 1.0) ? (1.0 - a) * V : 0.0; }
 __device__ __forceinline__ double room_def(double a, double V) { return (a > 0.0 && a <= 1.0) ? a * V : 0.0; }
 
-// scratch per cell: [Cp, Cm, rp, rm, release, sp, sm, -]
-enum { BS_CP = 0, BS_CM, BS_RP, BS_RM, BS_REL, BS_SP, BS_SM, BS_N = 8 };
+// scratch per cell: [1/Cp, 1/Cm (0 where the room is 0), rp, rm, release, sp,
+// sm, 1/dg]: the phases multiply by the reciprocals (each source's room sums
+// and neighbour count divide many terms; the FP64 pipe of this part runs at
+// 1/62 of the FP32 rate)
+enum { BS_CP = 0, BS_CM, BS_RP, BS_RM, BS_REL, BS_SP, BS_SM, BS_RDG, BS_N = 8 };
 
 struct BoundBufs {
     int *la, *lb;        // source lists (ping-pong), capacity nc
@@ -1150,8 +1153,9 @@ __device__ void bp_room(const DevMesh &m, const double *alpha, const BoundBufs &
             Cm += room_def(an, Vn);
             ++dg;
         });
-        b.bs[BS_N * (size_t)c + BS_CP] = Cp;
-        b.bs[BS_N * (size_t)c + BS_CM] = Cm;
+        b.bs[BS_N * (size_t)c + BS_CP] = Cp > 0.0 ? 1.0 / Cp : 0.0;
+        b.bs[BS_N * (size_t)c + BS_CM] = Cm > 0.0 ? 1.0 / Cm : 0.0;
+        b.bs[BS_N * (size_t)c + BS_RDG] = dg > 0 ? 1.0 / dg : 0.0;
         b.dg[c] = dg;
     }
 }
@@ -1172,9 +1176,9 @@ __device__ void bp_scale(const DevMesh &m, const double *alpha, const BoundBufs 
             double Qp = 0.0, Qm = 0.0;
             for_nbrs(m, r, [&](int s, int) {
                 double as = alpha[s], Vs = m.vc[s];
-                double Cps = bs[BS_N * (size_t)s + BS_CP], Cms = bs[BS_N * (size_t)s + BS_CM];
-                if (is_exc(as) && Cps > 0.0) Qp += (as - 1.0) * Vs * (Rp / Cps);
-                if (is_def(as) && Cms > 0.0) Qm += -as * Vs * (Rm / Cms);
+                double rCps = bs[BS_N * (size_t)s + BS_CP], rCms = bs[BS_N * (size_t)s + BS_CM];
+                if (is_exc(as) && rCps > 0.0) Qp += (as - 1.0) * Vs * (Rp * rCps);
+                if (is_def(as) && rCms > 0.0) Qm += -as * Vs * (Rm * rCms);
             });
             bs[BS_N * (size_t)r + BS_SP] = Qp > Rp ? Rp / Qp : 1.0;
             bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
@@ -1190,12 +1194,12 @@ __device__ void bp_place(const DevMesh &m, const double *alpha, const BoundBufs 
         int c = b.la[i];
         double a = alpha[c], V = m.vc[c];
         double *q = bs + BS_N * (size_t)c;
-        const double Cp = q[BS_CP], Cm = q[BS_CM];
+        const double rCp = q[BS_CP], rCm = q[BS_CM];
         double gp = 0.0, gm = 0.0, e = is_exc(a) ? (a - 1.0) * V : 0.0, u = is_def(a) ? -a * V : 0.0;
         for_nbrs(m, c, [&](int nb, int) {
             double an = alpha[nb], Vn = m.vc[nb];
-            if (e > 0.0 && Cp > 0.0) gp += e * (room_exc(an, Vn) / Cp) * bs[BS_N * (size_t)nb + BS_SP];
-            if (u > 0.0 && Cm > 0.0) gm += u * (room_def(an, Vn) / Cm) * bs[BS_N * (size_t)nb + BS_SM];
+            if (e > 0.0 && rCp > 0.0) gp += e * (room_exc(an, Vn) * rCp) * bs[BS_N * (size_t)nb + BS_SP];
+            if (u > 0.0 && rCm > 0.0) gm += u * (room_def(an, Vn) * rCm) * bs[BS_N * (size_t)nb + BS_SM];
         });
         int dg = b.dg[c];
         q[BS_RP] = (e > 0.0 && dg > 0) ? e - gp : 0.0;
@@ -1227,14 +1231,13 @@ __device__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b
             for_nbrs(m, x, [&](int s, int) {
                 double as = alpha[s], Vs = m.vc[s];
                 const double *bq = bs + BS_N * (size_t)s;
-                int dgs = b.dg[s];
                 if (is_exc(as)) {
-                    if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp / bq[BS_CP]) * SPx;
-                    if (dgs > 0) dV += bq[BS_RP] / dgs;
+                    if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp * bq[BS_CP]) * SPx;
+                    dV += bq[BS_RP] * bq[BS_RDG];
                 }
                 if (is_def(as)) {
-                    if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm / bq[BS_CM]) * SMx;
-                    if (dgs > 0) dV -= bq[BS_RM] / dgs;
+                    if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm * bq[BS_CM]) * SMx;
+                    dV -= bq[BS_RM] * bq[BS_RDG];
                 }
             });
             if (dV != 0.0) {
@@ -1305,16 +1308,21 @@ __device__ void seg_reduce(const DevMesh &m, const double *alpha, int4 sg, doubl
     __syncthreads();
 }
 
-// region r, by a whole warp
+// region r, by a whole warp: totals[REG_TOT * r + 0..3] = Ep, Em, Sp, Sm and
+// [4], [5] the shares Ep / Sp, Em / Sm of the global step (0 where none)
+constexpr int REG_TOT = 6;
 __device__ void region_totals(const int *reg_seg, int r, const double *spartial, double *totals)
 {
     const int lane = threadIdx.x & 31;
     double t[4] = {0.0, 0.0, 0.0, 0.0};
     for (int k = reg_seg[r] + lane; k < reg_seg[r + 1]; k += 32)
         for (int i = 0; i < 4; ++i) t[i] += spartial[4 * k + i];
-    for (int i = 0; i < 4; ++i) {
-        double x = warp_sum(t[i]);
-        if (lane == 0) totals[4 * r + i] = x;
+    for (int i = 0; i < 4; ++i) t[i] = warp_sum(t[i]);
+    if (lane == 0) {
+        double *o = totals + REG_TOT * (size_t)r;
+        for (int i = 0; i < 4; ++i) o[i] = t[i];
+        o[4] = t[0] > 0.0 && t[2] > 0.0 ? t[0] / t[2] : 0.0;
+        o[5] = t[1] > 0.0 && t[3] > 0.0 ? t[1] / t[3] : 0.0;
     }
 }
 
@@ -1324,19 +1332,16 @@ __device__ void region_totals(const int *reg_seg, int r, const double *spartial,
 __device__ void seg_apply(const DevMesh &m, double *alpha, int4 sg, const double *totals, double v[5], bool &zero,
                           bool &bad)
 {
-    const double *tt = totals + 4 * sg.x;
-    const double Ep = tt[0], Em = tt[1], Sp = tt[2], Sm = tt[3];
+    const double *tt = totals + REG_TOT * (size_t)sg.x;
+    const double Ep = tt[0], Em = tt[1], Sp = tt[2], Sm = tt[3], sp = tt[4], sm = tt[5];
     const bool apply = !((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm);
     auto cell = [&](int c, double a) {
         if (apply) {
+            // a cell strictly inside takes Ep (1 - a) V / Sp and gives Em a V / Sm:
+            // a + (Ep / Sp)(1 - a) - (Em / Sm) a, no division per cell
             if (gt_pos(a, 1.0 + BOUND_TOL)) alpha[c] = a = 1.0;
             else if (lt_neg(a, BOUND_TOL)) alpha[c] = a = 0.0;
-            else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) {
-                double V = m.vc[c], dV = 0.0;
-                if (Ep > 0.0) dV += Ep * ((1.0 - a) * V / Sp);
-                if (Em > 0.0) dV -= Em * (a * V / Sm);
-                alpha[c] = a = (a * V + dV) / V;
-            }
+            else if (gt_pos(a, BOUND_TOL) && lt_pos(a, 1.0 - BOUND_TOL)) alpha[c] = a = a + sp * (1.0 - a) - sm * a;
         }
         if (is_pzero(a)) { zero = true; return; }
         v[1] += m.vc[c] * a;
