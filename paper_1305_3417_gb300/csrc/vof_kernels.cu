@@ -149,15 +149,16 @@ __global__ void k_point_velocity(DevMesh m, const double *__restrict__ Uc, doubl
 // then Alg. 1 with the fill function summed over the cell tetrahedra, one or
 // two per lane, each a closed-form cut fraction of its sorted projections.
 
-// Reciprocal for the fill of the mixed positioning: FP32 division for R =
-// float; for R = double the FP32 reciprocal refined by one Newton-Raphson step
+// Reciprocal for the fill of the mixed positioning: the correctly rounded FP32
+// reciprocal for R = float (the FP32 stage only brings the residual to 1e-5);
+// for R = double the FP32 reciprocal refined by one Newton-Raphson step
 // r <- r + r (1 - x r) in FP64, whose relative error is about the square of
 // the FP32 one (~4e-15), with exact division where x is outside the FP32
 // range.  The FP64 pipe of this part runs at 1/64 of the FP32 rate: this is a
 // conversion pair and two FMAs in place of a full FP64 division.
 __device__ __noinline__ double exact_rcp(double x) { return 1.0 / x; }
 template <class R> __device__ __forceinline__ R mx_rcp(R x);
-template <> __device__ __forceinline__ float mx_rcp<float>(float x) { return 1.0f / x; }
+template <> __device__ __forceinline__ float mx_rcp<float>(float x) { return __frcp_rn(x); }
 template <> __device__ __forceinline__ double mx_rcp<double>(double x)
 {
     const float r0 = __frcp_rn((float)x);
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                 double x = 0.0;
                 if (MIXED && a > 1e-4 && a < 1.0 - 1e-4) {
                     // ---- FP32 Newton, relative to the cell centre's projection
-                    const float Vf = (float)V, af = (float)a;
+                    const float Vf = (float)V, af = (float)a, rVf = __frcp_rn(Vf);
                     float Ar = (float)(dmin - href), Br = (float)(dmax - href);
                     // start: the learned offset where one is given, else alpha
                     const float sg = (s0 && item < s0cap) ? s0[item] : af;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                             dpart += __shfl_xor_sync(tm, dpart, o);
                         }
                         ++it;
-                        const float gf = part / Vf - af;
+                        const float gf = part * rVf - af;
                         // below 1e-5 the FP32 sign is not reliable: the bracket takes
                         // no update from it, and after two more Newton steps (down to
                         // the FP32 rounding of the fill) FP64 takes over
@@ -328,7 +329,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                         if (sure) {
                             if (gf < 0.0f) Ar = xr; else Br = xr;
                         }
-                        float xn = xr - gf * Vf / dpart;
+                        float xn = xr - gf * Vf * __frcp_rn(dpart);
                         if (!(xn > Ar && xn < Br)) xn = 0.5f * (Ar + Br);
                         if (!(xn > Ar && xn < Br)) break;  // bracket at FP32 resolution
                         xr = xn;
