@@ -89,6 +89,7 @@ struct MXArgs {
     const float4 *fpl, *cbl;  // FP32 face points (face frame), cell boxes (cell frame)
     const float4 *ktl;        // cell tetrahedra: planes and box (cell frame)
     const int *ctptr;
+    int *next;                // list form: next band slot to take (zero before the launch), or null
 };
 
 constexpr int MX_CAND = 32;    // candidate cell tetrahedra buffered per warp: one per lane
@@ -418,7 +419,18 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int total = LIST ? *a.count : m.nf;
     const double eps = m.eps;
-    for (int item = warp; item < total; item += nwarps) {
+    // Band faces differ in cost by an order of magnitude (a face whose
+    // polyhedron cuts interface cells clips, one among uniform cells hardly
+    // does): in the list form a warp takes its next face from a counter as it
+    // finishes one, so that no warp ends long after the others; a face's flux
+    // is one warp's work either way.
+    const bool dyn = LIST && a.next != nullptr;
+    auto take = [&]() {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(a.next, 1);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    for (int item = dyn ? take() : warp; item < total; item = dyn ? take() : item + nwarps) {
         const int f = LIST ? a.list[item] : item;
         const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
         if (!LIST) {
@@ -790,7 +802,7 @@ static MXArgs mx_args(vof_ctx *c, const double *alpha, const double *n, const do
                       const int *list, const int *count, const double *disp, unsigned long long *work)
 {
     return MXArgs{alpha, n, d, flags, Up, F, lambda, dt, Va, list, count, disp, c->lam_b, c->status, work,
-                  c->fpl, c->cbl, c->ktl, c->m.ctptr};
+                  c->fpl, c->cbl, c->ktl, c->m.ctptr, nullptr};
 }
 
 int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
@@ -807,10 +819,11 @@ int launch_phase_flux_mixed_list(vof_ctx *c, const double *alpha, const double *
 {
     MXArgs a = mx_args(c, alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band,
                        c->counters + CNT_BAND, c->disp_b, c->work);
+    a.next = c->counters + CNT_PFNEXT;  // zeroed with the step's counters
     // launch configuration (vof_batch_tune): warps per block, and grid = SMs x
     // resident blocks x multiplier
     const int w = c->pf_warps >= 1 && c->pf_warps <= 3 ? c->pf_warps : 2;
-    const int mult = c->pf_mult >= 1 ? c->pf_mult : 2;
+    const int mult = c->pf_mult >= 1 ? c->pf_mult : 1;
     if (w == 1)
         k_phase_flux_mixed<true, 1><<<sms * mx_resident(1) * mult, 32, 0, s>>>(c->m, a);
     else if (w == 2)
