@@ -42,7 +42,7 @@ struct DevMesh {
 // the context's counter buffer: per-step counters (the first CNT_LEN ints),
 // then the two words of the grid barrier, each on its own 128-byte line
 enum { CNT_BAND = 0, CNT_ICELL, CNT_MAXPOS, CNT_MAXCORR, CNT_FALLBACK, CNT_VIOL0, CNT_VIOL1, CNT_PEND, CNT_PFNEXT,
-       CNT_LEN = 16 };
+       CNT_RCNEXT, CNT_LEN = 16 };
 enum { CNT_BAR = 32, CNT_BARGEN = 64, CNT_ALLOC = 96 };
 
 struct vof_ctx {

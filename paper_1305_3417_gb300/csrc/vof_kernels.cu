@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
                                                      uint8_t *fout, int *itout, int *maxit, unsigned *status,
-                                                     const float *__restrict__ s0, int s0cap)
+                                                     const float *__restrict__ s0, int s0cap, int *next)
 {
     const int lane = threadIdx.x & (G - 1);
     const unsigned tm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1));
@@ -230,7 +230,15 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
     };
     const int total = LIST ? *count : m.nc;
     const double eps = m.eps;
-    for (int item = warp; item < total; item += nwarps) {
+    // LIST with a counter: a lane group takes its next cell as it finishes one
+    // (cells differ in positioning iterations); else static striding
+    const bool dyn = LIST && next != nullptr;
+    auto take = [&]() {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(next, 1);
+        return __shfl_sync(tm, v, 0, G);
+    };
+    for (int item = dyn ? take() : warp; item < total; item = dyn ? take() : item + nwarps) {
         const int c = LIST ? list[item] : item;
         const double a = alpha[c];
         uint8_t fl = 0;
@@ -508,21 +516,54 @@ __device__ __forceinline__ double cubic_at(const Cubic &q, double x) { return ((
 // A flux below 1e-12 of |S_f| max|w| (noise = the rounding of a zero flux, e.g.
 // on a wall) gives lambda = 0: no sweep.  The test is taken on squares,
 // tau^2 <= 1e-24 |S_f|^2 max|w|^2 (noise2), which needs no square root.
+// The sign of V(lambda_k) - tau at a grid point is read from an FP32
+// evaluation where that is clearly away from zero (the FP32 conversion of the
+// four coefficients and Horner's rounding stay below about 7 units of 2^-24,
+// 4.2e-7, of the terms' magnitude B; the test asks for 1e-6 B),
+// else from the FP64 one: the same signs, so the same bracket, as FP64
+// throughout.  The bracket's end values are FP64.  The Newton step divides by
+// the slope through an FP32 reciprocal (the slope sets the rate, not the root).
 __device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &its)
 {
     its = 0;
     if (tau == 0.0) return 0.0;
     if (tau * tau <= 1e-24 * noise2) return 0.0;
-    double lo = 0.0, rlo = -tau, hi = 0.0, rhi = 0.0;
-    bool found = false;
+    const float c1 = (float)q.c1, c2 = (float)q.c2, c3 = (float)q.c3, tf = (float)tau;
+    const float a1 = fabsf(c1), a2 = fabsf(c2), a3 = fabsf(c3), at = fabsf(tf);
+    constexpr double STEP = CORR_LMAX / CORR_NSAMP;
+    const bool pos0 = -tau > 0.0;
+    int klo = 0, khi = 0;
+    double rhi = 0.0;
+    bool have_rhi = false;
     for (int k = 1; k <= CORR_NSAMP; ++k) {
-        double lk = k * (CORR_LMAX / CORR_NSAMP);
-        double rk = cubic_at(q, lk) - tau;
-        if (rk == 0.0) return lk;
-        if ((rk > 0) != (rlo > 0)) { hi = lk; rhi = rk; found = true; break; }
-        lo = lk; rlo = rk;
+        const float L = (float)(k * STEP);
+        const float r32 = ((c3 * L + c2) * L + c1) * L - tf;
+        const float B = ((a3 * L + a2) * L + a1) * L + at;
+        bool pos;
+        double rk = 0.0;
+        const bool sure = fabsf(r32) > 1e-6f * B;
+        if (sure) {
+            pos = r32 > 0.0f;
+        } else {
+            rk = cubic_at(q, k * STEP) - tau;
+            if (rk == 0.0) return k * STEP;
+            pos = rk > 0.0;
+        }
+        if (pos != pos0) {
+            khi = k;
+            rhi = rk;
+            have_rhi = !sure;
+            break;
+        }
+        klo = k;
     }
-    if (!found) return -1.0;
+    if (khi == 0) return -1.0;
+    double lo = klo * STEP, hi = khi * STEP;
+    double rlo = klo == 0 ? -tau : cubic_at(q, lo) - tau;
+    if (!have_rhi) {
+        rhi = cubic_at(q, hi) - tau;
+        if (rhi == 0.0) return hi;
+    }
     double x = lo - rlo * (hi - lo) / (rhi - rlo);
     if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
     while (its < CORR_MAXIT) {
@@ -534,7 +575,7 @@ __device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &i
         if (fabs(r) <= CORR_TOL * scale) break;
         if (hi - lo <= 1e-15 * hi) break;
         double dr = (3.0 * q.c3 * x + 2.0 * q.c2) * x + q.c1;
-        double xn = x - r / dr;
+        double xn = x - r * (double)__frcp_rn((float)dr);
         if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
         x = xn;
     }
@@ -747,6 +788,7 @@ struct PFArgs {
     const double *disp;   // per list slot displacements (LIST mode)
     unsigned *status;
     unsigned long long *work;  // [pairs, cuts, faces]
+    int *next;                 // LIST: next band slot to take (zero before the launch), or null
 };
 
 constexpr int PF_WARPS = 4;
@@ -763,7 +805,15 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int total = LIST ? *a.count : m.nf;
     const double eps = m.eps;
-    for (int item = warp; item < total; item += nwarps) {
+    // LIST: a warp takes its next band face from a counter as it finishes one
+    // (face costs differ widely; a face's flux is one warp's work either way)
+    const bool dyn = LIST && a.next != nullptr;
+    auto take = [&]() {
+        int v = 0;
+        if (lane == 0) v = atomicAdd(a.next, 1);
+        return __shfl_sync(0xffffffffu, v, 0);
+    };
+    for (int item = dyn ? take() : warp; item < total; item = dyn ? take() : item + nwarps) {
         const int f = LIST ? a.list[item] : item;
         const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
         if (!LIST) {
@@ -1620,16 +1670,16 @@ int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t
 template <bool LIST, bool MIXED>
 static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const double *palpha, const int *list,
                       const int *count, double *n, double *d, uint8_t *flags, int *iters, int *maxit,
-                      cudaStream_t s)
+                      cudaStream_t s, int *next = nullptr)
 {
     if (c->rc_g == 8) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
         k_reconstruct<LIST, MIXED, 8><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                             maxit, c->status, c->mlp_s0, mlp_cap(c));
+                                                             maxit, c->status, c->mlp_s0, mlp_cap(c), next);
     } else {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
         k_reconstruct<LIST, MIXED, 32><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                              maxit, c->status, c->mlp_s0, mlp_cap(c));
+                                                              maxit, c->status, c->mlp_s0, mlp_cap(c), next);
     }
 }
 
@@ -1825,10 +1875,10 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     }
     if (c->precision == VOF_MIXED)
         rc_launch<true, true>(c, sms * 16, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
-                              cnt + CNT_MAXPOS, s);
+                              cnt + CNT_MAXPOS, s, cnt + CNT_RCNEXT);
     else
         rc_launch<true, false>(c, sms * 16, alpha, c->palpha, c->icell, cnt + CNT_ICELL, c->n, c->d, c->flags, nullptr,
-                               cnt + CNT_MAXPOS, s);
+                               cnt + CNT_MAXPOS, s, cnt + CNT_RCNEXT);
     MARK(2);
     if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return VOF_ERR_CUDA;
     MARK(3);
@@ -1837,7 +1887,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
         if (r) return r;
     } else {
         PFArgs a{alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band, cnt + CNT_BAND, c->disp_b,
-                 c->status, c->work};
+                 c->status, c->work, cnt + CNT_PFNEXT};
         k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
     }
     launches += 4;  // reconstruct, band point velocities, correct, phase flux
