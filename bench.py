@@ -213,20 +213,31 @@ def run_reference(args, world, rank):
 
 def config(args, w):
     m = w.mesh
-    return {"workload": f"{w.name}: {m.shape[0]}x{m.shape[1]}x{m.shape[2]} {m.kind} mesh "
-                        f"({m.n_cells} cells, {m.n_internal} internal faces), jitter, {w.field.name} field, Co 0.5",
+    if m.kind == "octree":
+        desc = (f"{w.name}: octree on a {m.shape[0]}^3 base lattice split twice near the sphere (finest h = "
+                f"1/{round(1 / m.h)}), 2:1 balanced ({m.n_cells} cells, {m.n_internal} internal faces), "
+                f"{w.field.name} field, Co 0.5 on the finest cells")
+    else:
+        desc = (f"{w.name}: {m.shape[0]}x{m.shape[1]}x{m.shape[2]} {m.kind} mesh "
+                f"({m.n_cells} cells, {m.n_internal} internal faces), jitter, {w.field.name} field, Co 0.5")
+    return {"workload": desc,
             "n_cells": m.n_cells, "n_internal_faces": m.n_internal, "precision": args.precision,
             "learned_guess": bool(args.mlp), "skip_steps": args.skip, "dt": w.dt,
             "l2": "inputs larger than L2 (mesh, fluxes and per-step arrays > 129 MB)"}
 
 
-def train_guess(device):
+def train_guess(device, workload="deform3d"):
     """The initial-guess network trained on seeded sphere/plane fields of a
-    48^3 jittered hexahedral mesh (targets from the FP64 reconstruction)."""
+    48^3 jittered hexahedral mesh, or for the octree workload of a 24^3-based
+    two-level octree (cells like the workload's: boxes of three sizes with
+    hanging points); targets from the FP64 reconstruction."""
     import torch
     from paper_1305_3417_gb300 import inputs as I, mlp, vof
     t0 = time.perf_counter()
-    m = I.hex_mesh((48, 48, 48), jitter=0.2, seed=21)
+    if workload == "octree":
+        m = I.octree_mesh(24, 2)
+    else:
+        m = I.hex_mesh((48, 48, 48), jitter=0.2, seed=21)
     c64 = vof.VofContext(m, precision=vof.FP64, device=device)
     X, Y = mlp.samples(c64, m, mlp.random_fields(m, 40, seed=22))
     net = vof.Mlp(mlp.init_params(1306), max_batch=1 << 17, device=device)
@@ -418,7 +429,7 @@ def main():
     ctx = vof.VofContext(m, precision=prec, device=local)
     learned = None
     if args.mlp and prec == vof.MIXED:
-        learned = train_guess(local)
+        learned = train_guess(local, args.workload)
         vof.vof_set_guess(ctx.h, learned["net"])
     total = args.skip + args.warmup + args.steps
     # per-step inputs resident in HBM before the timed region

@@ -103,8 +103,10 @@ typedef struct vof_ctx vof_ctx;
  * vectors, cell centres, volumes and bounding boxes, inverse-distance weights
  * of Eq. w_pc, NAG face weights of Sec. 2.2.1) in kernels, and allocates all
  * per-step scratch.  Synchronous.  Fails with VOF_ERR_BAD_MESH on an index out
- * of range or a cell tetrahedron of non-positive volume.  *out receives a
- * context the caller releases with vof_destroy. */
+ * of range, a cell tetrahedron of non-positive volume, a face of fewer than 3
+ * or more than 8 points, or a cell of more than 96 tetrahedra (a face of n > 3
+ * points gives n; 2:1 octree cells have up to 78).  *out receives a context the
+ * caller releases with vof_destroy. */
 int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out);
 void vof_destroy(vof_ctx *ctx);
 

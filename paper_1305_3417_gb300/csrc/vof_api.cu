@@ -329,7 +329,11 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->np = np; c->nf = nf; c->ni = ni; c->nc = nc;
     c->eps = (opt && opt->eps > 0.0) ? opt->eps : 1e-9;
     c->precision = opt ? opt->precision : VOF_FP64;
-    c->rc_g = *std::max_element(ktet.begin(), ktet.end()) <= 16 ? 8 : 32;
+    {
+        const int kmax = *std::max_element(ktet.begin(), ktet.end());
+        c->rc_g = kmax <= 16 ? 8 : 32;
+        c->rc_k = kmax <= 64 ? 2 : 3;
+    }
     c->bound = opt ? (opt->bound != 0) : 1;
     int err = 0;
     DevMesh &m = c->m;

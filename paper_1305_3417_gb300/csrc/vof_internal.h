@@ -8,7 +8,7 @@
 #include "../../include/vof.h"
 
 #define VOF_MAXFP 8       // points per face handled by the per-face kernels
-#define VOF_MAXK_LANE 2   // cell tetrahedra per lane in the reconstruction warp (64 per cell)
+#define VOF_MAXK_LANE 3   // cell tetrahedra per lane in the reconstruction warp at most (96 per cell)
 
 // Device view of the mesh, its derived topology and its geometry.  All
 // pointers are device pointers owned by the context.
@@ -100,6 +100,7 @@ struct vof_ctx {
     // grid multiplier over the resident blocks
     int pf_warps, pf_mult;
     int rc_g;                    // reconstruction lanes per cell: 8 if every cell has <= 16 tetrahedra, else 32
+    int rc_k;                    // tetrahedra per lane: 3 where some cell has more than 64, else 2
     // learned guess of the positioning (vof_set_guess): the network, offsets by
     // interface-list position, features
     struct vof_mlp *mlp;

@@ -202,7 +202,7 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // leaves the bracket).
 // G lanes per cell: 32, or 8 where every cell has at most 16 tetrahedra (a
 // tetrahedral mesh: four cells per warp); reductions over the cell's lanes
-template <bool LIST, bool MIXED, int G>
+template <bool LIST, bool MIXED, int G, int KL>
 __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
@@ -272,12 +272,12 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                 fl |= VOF_ORIENTED;
                 // ---- cell tetrahedra (c_c, outward face triangle), lanes j, j+32
                 const V3 ctr = ld3(m.cc, m.nc, c);
-                double h[VOF_MAXK_LANE][4], vk[VOF_MAXK_LANE];
-                float hf[VOF_MAXK_LANE][4], vkf[VOF_MAXK_LANE];
+                double h[KL][4], vk[KL];
+                float hf[KL][4], vkf[KL];
                 const double href = dot(nn, ctr);
                 double lo = 1e300, hi = -1e300;
 #pragma unroll
-                for (int s = 0; s < VOF_MAXK_LANE; ++s) {
+                for (int s = 0; s < KL; ++s) {
                     vk[s] = 0.0;
                     h[s][0] = h[s][1] = h[s][2] = h[s][3] = 0.0;
                     vkf[s] = 0.0f;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                     while (it < POS_MAXIT) {
                         float part = 0.0f, dpart = 0.0f;
 #pragma unroll
-                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                        for (int s = 0; s < KL; ++s)
                             if (vkf[s] > 0.0f) {
                                 float df;
                                 part += vkf[s] * frac_below_dd(hf[s][0], hf[s][1], hf[s][2], hf[s][3], xr, df);
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                     while (it < POS_MAXIT) {
                         double part = 0.0, dpart = 0.0;
 #pragma unroll
-                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                        for (int s = 0; s < KL; ++s)
                             if (vk[s] > 0.0) {
                                 double df;
                                 part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                     while (it < POS_MAXIT) {
                         double part = 0.0, dpart = 0.0;
 #pragma unroll
-                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                        for (int s = 0; s < KL; ++s)
                             if (vk[s] > 0.0) {
                                 double df;
                                 part += vk[s] * frac_below_dd(h[s][0], h[s][1], h[s][2], h[s][3], x, df);
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                         if (bisect) x = 0.5 * (A + B);
                         double part = 0.0;
 #pragma unroll
-                        for (int s = 0; s < VOF_MAXK_LANE; ++s)
+                        for (int s = 0; s < KL; ++s)
                             if (vk[s] > 0.0) part += vk[s] * frac_below(h[s][0], h[s][1], h[s][2], h[s][3], x);
                         gx = tsum(part) / V - a;
                         ++it;
@@ -1672,14 +1672,20 @@ static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const do
                       const int *count, double *n, double *d, uint8_t *flags, int *iters, int *maxit,
                       cudaStream_t s, int *next = nullptr)
 {
+    // lanes per cell and tetrahedra per lane: 8 x 2 (cells of <= 16 tetrahedra),
+    // 32 x 2 (<= 64), 32 x 3 (<= 96: octree cells next to finer ones)
     if (c->rc_g == 8) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
-        k_reconstruct<LIST, MIXED, 8><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                             maxit, c->status, c->mlp_s0, mlp_cap(c), next);
+        k_reconstruct<LIST, MIXED, 8, 2><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+                                                                maxit, c->status, c->mlp_s0, mlp_cap(c), next);
+    } else if (c->rc_k <= 2) {
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
+        k_reconstruct<LIST, MIXED, 32, 2><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+                                                                 maxit, c->status, c->mlp_s0, mlp_cap(c), next);
     } else {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
-        k_reconstruct<LIST, MIXED, 32><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                              maxit, c->status, c->mlp_s0, mlp_cap(c), next);
+        k_reconstruct<LIST, MIXED, 32, 3><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
+                                                                 maxit, c->status, c->mlp_s0, mlp_cap(c), next);
     }
 }
 

@@ -187,6 +187,194 @@ def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = 
 
 
 # --------------------------------------------------------------------------
+# Static octree: a cubic base lattice refined near a sphere, 2:1 face-balanced
+# --------------------------------------------------------------------------
+
+def octree_mesh(n0: int = 64, levels: int = 2, center=(0.35, 0.35, 0.35), R: float = 0.15,
+                band: float = 3.0) -> Mesh:
+    """Unit cube: an n0^3 lattice whose cells are split into 8 wherever the cell
+    centre lies within band * (the cell's size) of the sphere |x - center| = R,
+    level by level down to `levels` splits, then split further until every
+    two face neighbours differ by at most one level (2:1 face balance).
+
+    The result is a conforming polyhedral mesh: every cell is an axis-aligned
+    box; a side facing four finer cells is four faces (one per finer cell); a
+    face gets the midpoints of its edges that are corners of smaller cells
+    (hanging points) as extra polygon points, so faces have 4 to 8 points.  A
+    face is listed once, owned by the cell whose side it is (the finer of the
+    two, or the lower one across +x/+y/+z between equal cells), with its points
+    counter-clockwise about the owner's outward normal.  Boundary faces are
+    walls.  cell_verts holds each box's 8 corners in the hex corner order.
+    Integer lattice coordinates are in units of the finest size 1/(n0 2^levels).
+    """
+    N = n0 << levels
+    cen = np.asarray(center, float)
+
+    def near(L, i, j, k):
+        s = 1 << (levels - L)
+        c = (np.stack([i, j, k], 1) * s + 0.5 * s) / N
+        d = np.abs(np.sqrt(((c - cen) ** 2).sum(1)) - R)
+        return d <= band * s / N
+
+    g = np.arange(n0)
+    I, J, K = (a.ravel() for a in np.meshgrid(g, g, g, indexing="ij"))
+    leaves = {0: (I, J, K)}
+    for L in range(levels):
+        leaves.setdefault(L + 1, (np.zeros(0, np.int64),) * 3)
+    kids = np.array([(a, b, c) for c in (0, 1) for b in (0, 1) for a in (0, 1)])
+
+    def split(L, m):
+        i, j, k = leaves[L]
+        ci, cj, ck = i[m], j[m], k[m]
+        leaves[L] = (i[~m], j[~m], k[~m])
+        ni = (2 * ci[:, None] + kids[None, :, 0]).ravel()
+        nj = (2 * cj[:, None] + kids[None, :, 1]).ravel()
+        nk = (2 * ck[:, None] + kids[None, :, 2]).ravel()
+        pi, pj, pk = leaves[L + 1]
+        leaves[L + 1] = (np.concatenate([pi, ni]), np.concatenate([pj, nj]), np.concatenate([pk, nk]))
+
+    for L in range(levels):
+        i, j, k = leaves[L]
+        split(L, near(L, i, j, k))
+
+    def level_map():
+        lm = np.zeros((N, N, N), np.int8)
+        for L in range(levels + 1):
+            i, j, k = leaves[L]
+            if i.size == 0:
+                continue
+            s = 1 << (levels - L)
+            nL = N // s
+            v = lm.reshape(nL, s, nL, s, nL, s).transpose(0, 2, 4, 1, 3, 5)
+            v[i, j, k] = L
+        return lm
+
+    while True:                                   # 2:1 face balance
+        lm = level_map()
+        nb = np.zeros_like(lm)
+        nb[1:] = np.maximum(nb[1:], lm[:-1]); nb[:-1] = np.maximum(nb[:-1], lm[1:])
+        nb[:, 1:] = np.maximum(nb[:, 1:], lm[:, :-1]); nb[:, :-1] = np.maximum(nb[:, :-1], lm[:, 1:])
+        nb[:, :, 1:] = np.maximum(nb[:, :, 1:], lm[:, :, :-1]); nb[:, :, :-1] = np.maximum(nb[:, :, :-1], lm[:, :, 1:])
+        changed = False
+        for L in range(levels - 1):
+            i, j, k = leaves[L]
+            if i.size == 0:
+                continue
+            s = 1 << (levels - L)
+            nL = N // s
+            bm = nb.reshape(nL, s, nL, s, nL, s).max(axis=(1, 3, 5))
+            m = bm[i, j, k] >= L + 2
+            if m.any():
+                split(L, m)
+                changed = True
+        if not changed:
+            break
+    lm = level_map()
+
+    # cells: every leaf, ordered by its origin (z, y, x)
+    lv, ox, oy, oz, sz = [], [], [], [], []
+    for L in range(levels + 1):
+        i, j, k = leaves[L]
+        s = 1 << (levels - L)
+        lv.append(np.full(i.size, L)); ox.append(i * s); oy.append(j * s); oz.append(k * s)
+        sz.append(np.full(i.size, s))
+    lv, ox, oy, oz, sz = (np.concatenate(a).astype(np.int64) for a in (lv, ox, oy, oz, sz))
+    order = np.lexsort((ox, oy, oz))
+    lv, ox, oy, oz, sz = lv[order], ox[order], oy[order], oz[order], sz[order]
+    nc = lv.size
+    cmap = np.empty((N, N, N), np.int32)
+    for L in range(levels + 1):
+        sel = np.flatnonzero(lv == L)
+        if sel.size == 0:
+            continue
+        s = 1 << (levels - L)
+        nL = N // s
+        v = cmap.reshape(nL, s, nL, s, nL, s).transpose(0, 2, 4, 1, 3, 5)
+        v[ox[sel] // s, oy[sel] // s, oz[sel] // s] = sel[:, None, None, None]
+
+    # points: the corners of the cells
+    M = N + 1
+    corner = np.array([(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0), (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)])
+    cx = ox[:, None] + corner[None, :, 0] * sz[:, None]
+    cy = oy[:, None] + corner[None, :, 1] * sz[:, None]
+    cz = oz[:, None] + corner[None, :, 2] * sz[:, None]
+    key = (cx + M * (cy + M * cz)).ravel()
+    uk, inv = np.unique(key, return_inverse=True)
+    pmap = np.full(M * M * M, -1, np.int64)
+    pmap[uk] = np.arange(uk.size)
+    pts = np.stack([uk % M, (uk // M) % M, uk // (M * M)], 1).astype(float) / N
+    cell_verts = inv.reshape(nc, 8).astype(np.int32)
+
+    def pid(x, y, z):
+        return pmap[x + M * (y + M * z)]
+
+    # the six sides: (axis, +1/-1); the 4 corners of a side counter-clockwise
+    # about the outward normal, as in hex_mesh's x/y/z faces
+    def side_corners(ax, sgn, x0, y0, z0, s):
+        if ax == 0:
+            x = x0 + (s if sgn > 0 else 0)
+            c = [(x, y0, z0), (x, y0 + s, z0), (x, y0 + s, z0 + s), (x, y0, z0 + s)]
+        elif ax == 1:
+            y = y0 + (s if sgn > 0 else 0)
+            c = [(x0, y, z0), (x0, y, z0 + s), (x0 + s, y, z0 + s), (x0 + s, y, z0)]
+        else:
+            z = z0 + (s if sgn > 0 else 0)
+            c = [(x0, y0, z), (x0 + s, y0, z), (x0 + s, y0 + s, z), (x0, y0 + s, z)]
+        if sgn < 0:
+            c = c[::-1]
+        return [tuple(np.asarray(v) for v in p) for p in c]
+
+    int_own, int_nei, int_pts, bnd_own, bnd_pts = [], [], [], [], []
+    cells = np.arange(nc)
+    for ax in range(3):
+        for sgn in (1, -1):
+            lo = (ox, oy, oz)[ax]
+            if sgn > 0:
+                edge = lo + sz >= N
+                adj = lo + sz                     # first finest index beyond the side
+            else:
+                edge = lo == 0
+                adj = lo - 1
+            # the finest cell just outside the side, at the side's low corner
+            ax_ = [ox, oy, oz]
+            q = [a.copy() for a in ax_]
+            q[ax] = np.where(edge, 0, adj)
+            nlev = lm[q[0], q[1], q[2]].astype(np.int64)
+            nidx = cmap[q[0], q[1], q[2]].astype(np.int64)
+            emit_int = ~edge & ((nlev < lv) | ((nlev == lv) & (sgn > 0)))
+            for sel, is_b in ((np.flatnonzero(edge), True), (np.flatnonzero(emit_int), False)):
+                if sel.size == 0:
+                    continue
+                c4 = side_corners(ax, sgn, ox[sel], oy[sel], oz[sel], sz[sel])
+                ids = []
+                for t in range(4):
+                    a, b = c4[t], c4[(t + 1) % 4]
+                    ids.append(pid(*a))
+                    half = (sz[sel] % 2 == 0)
+                    mx, my, mz = ((a[0] + b[0]) // 2, (a[1] + b[1]) // 2, (a[2] + b[2]) // 2)
+                    mid = np.where(half, pid(mx, my, mz), -1)
+                    ids.append(mid)
+                F = np.stack(ids, 1)              # (f, 8): corner, midpoint or -1, ...
+                if is_b:
+                    bnd_own.append(cells[sel]); bnd_pts.append(F)
+                else:
+                    int_own.append(cells[sel]); int_nei.append(nidx[sel]); int_pts.append(F)
+    own_i = np.concatenate(int_own); nei_i = np.concatenate(int_nei); F_i = np.concatenate(int_pts)
+    o = np.lexsort((nei_i, own_i))
+    own_i, nei_i, F_i = own_i[o], nei_i[o], F_i[o]
+    own_b = np.concatenate(bnd_own); F_b = np.concatenate(bnd_pts)
+    o = np.argsort(own_b, kind="stable")
+    own_b, F_b = own_b[o], F_b[o]
+    Fall = np.concatenate([F_i, F_b])
+    cnt = (Fall >= 0).sum(1)
+    face_ptr = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
+    face_pts = Fall[Fall >= 0].astype(np.int32)          # row-major: each face's points in order
+    owner = np.concatenate([own_i, own_b]).astype(np.int32)
+    return Mesh(pts, face_ptr, face_pts, owner, nei_i.astype(np.int32), nc, cell_verts, 1.0 / N, 3, "octree",
+                (n0, n0, n0), np.ones(own_b.size, np.uint8))
+
+
+# --------------------------------------------------------------------------
 # Kuhn split of a hexahedral lattice into tetrahedra
 # --------------------------------------------------------------------------
 
@@ -354,7 +542,7 @@ def sampled_fraction(mesh: Mesh, sdf: Callable, m: int = 8, chunk: int = 4096) -
     near = np.flatnonzero(np.abs(dc) <= rad * 1.0001)
     g = (np.arange(m) + 0.5) / m
     xi = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
-    if mesh.kind == "hex":
+    if cv.shape[1] == 8:                          # hexahedra and octree boxes
         N, dN = _hex_shape(xi)
         for s in range(0, near.size, chunk):
             ids = near[s:s + chunk]
@@ -518,6 +706,10 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
                   (0.35,0.35,0.35), deformation field T=3, Co 0.5 to t=3.
     vortex_tet:   jittered (+-0.15h, seed 1303) Kuhn split of n^3 (n=96), cylinder
                   R=0.15 at (0.5,0.75), single vortex T=8, Co 0.5 to t=8.
+    octree:       static octree, base n^3 (n=64) split twice (finest h = 1/(4n))
+                  within 3 cell sizes of the sphere R=0.15 at (0.35,0.35,0.35),
+                  2:1 face-balanced; deformation field T=3, Co 0.5 on the finest
+                  cells, to t=0.5 (the interface leaves the refined band later).
     """
     if name == "disc2d":
         n = 32 if n is None else n
@@ -537,16 +729,23 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
         a0 = sampled_fraction(mesh, cylinder_sdf(0.5, 0.75, 0.15))
         fld = single_vortex_field(8.0)
         steps = None
+    elif name == "octree":
+        n = 64 if n is None else n
+        mesh = octree_mesh(n, 2, (0.35, 0.35, 0.35), 0.15)
+        a0 = sampled_fraction(mesh, sphere_sdf((0.35, 0.35, 0.35), 0.15))
+        fld = deformation_field(3.0)
+        steps = None
     else:
         raise ValueError(name)
     Us = cell_velocity(mesh, fld.u)
     umax = float(np.sqrt((Us ** 2).sum(0)).max())
     # Courant number on the cell size h_c = V_c^(1/3) of the nominal lattice cell
     # (2D: the in-plane spacing); a Kuhn tetrahedron has a sixth of the hexahedron
-    hc = mesh.h if (mesh.kind == "hex") else mesh.h / 6.0 ** (1.0 / 3.0)
+    # (octree: the finest cells)
+    hc = mesh.h if mesh.kind in ("hex", "octree") else mesh.h / 6.0 ** (1.0 / 3.0)
     dt = co * hc / umax
     Fs = face_flux_stokes(mesh, fld.A)
-    t_end = {"disc2d": steps * dt if steps else None, "deform3d": 3.0, "vortex_tet": 8.0}[name]
+    t_end = {"disc2d": steps * dt if steps else None, "deform3d": 3.0, "vortex_tet": 8.0, "octree": 0.5}[name]
     if steps is None:
         steps = int(math.ceil(t_end / dt - 1e-12))
     exact = None

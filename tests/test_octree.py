@@ -1,0 +1,118 @@
+"""Config 5's mesh: a static octree (base lattice split twice near a sphere,
+2:1 face-balanced, hanging points on face edges).
+
+CPU: the generator's mesh is a closed, balanced partition of the unit cube,
+and the oracle's step on it conserves volume and stays bounded.  GPU: the
+CUDA path against the oracle on the same octree -- reconstruction (cells of
+up to 96 tetrahedra: three per lane) and full steps by replay, FP64 and mixed.
+"""
+import numpy as np
+import pytest
+
+from paper_1305_3417_gb300 import inputs as I
+
+N0 = 12   # 13.4k cells; some cells have 96 tetrahedra, some faces 6 points
+
+
+@pytest.fixture(scope="module")
+def wl():
+    return I.make_workload("octree", n=N0)
+
+
+def test_octree_mesh_is_a_balanced_closed_partition(oracle_lib, wl):
+    m = wl.mesh
+    om = oracle_lib.OracleMesh(m)
+    cc, vc, cf, sf = om.geometry()
+    sf = sf.reshape(3, -1) if sf.ndim == 1 else sf
+    sf = sf if sf.shape[0] == 3 else sf.T
+    # volumes: the boxes', summing to the cube
+    box = m.points[m.cell_verts]
+    ext = box.max(1) - box.min(1)
+    np.testing.assert_allclose(vc, ext.prod(1), rtol=1e-12, atol=0)
+    assert abs(vc.sum() - 1.0) < 1e-13
+    # every cell's surface is closed
+    net = np.zeros((3, m.n_cells))
+    ni = m.n_internal
+    for d in range(3):
+        np.add.at(net[d], m.owner, sf[d])
+        np.add.at(net[d], m.neighbour, -sf[d][:ni])
+    assert np.abs(net).max() < 1e-15
+    # 2:1 balance across faces, faces of 4..8 points, every point used
+    h = ext[:, 0]
+    r = h[m.owner[:ni]] / h[m.neighbour]
+    assert set(np.unique(np.round(r, 12))) <= {0.5, 1.0, 2.0}
+    npf = np.diff(m.face_ptr)
+    assert npf.min() >= 4 and npf.max() <= 8 and (npf > 4).any()
+    assert np.unique(m.face_pts).size == m.n_points
+    # three cell sizes, the finest near the sphere
+    assert np.unique(np.round(1.0 / h).astype(int)).tolist() == [N0, 2 * N0, 4 * N0]
+
+
+def test_octree_oracle_steps_conserve_and_stay_bounded(oracle_lib, wl):
+    om = oracle_lib.OracleMesh(wl.mesh)
+    S = oracle_lib.S
+    a = wl.alpha0.copy()
+    assert ((a > 1e-9) & (a < 1 - 1e-9)).sum() > 100
+    for k in range(3):
+        F, U, dt = wl.step_inputs(k)
+        a, st, status = om.advect(a, U, F, dt)
+        assert status == 0
+        drift = abs(st[S["mass_after"]] - st[S["mass_before"]]) / st[S["mass_before"]]
+        assert drift <= 1e-12
+        assert st[S["min_post"]] >= -1e-12 and st[S["max_post"]] <= 1 + 1e-12
+
+
+# ------------------------------------------------------------------ GPU parity
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1305_3417_gb300 import build
+    build.build()
+    return torch
+
+
+def _T(torch, x):
+    return torch.from_numpy(np.ascontiguousarray(x).reshape(-1).copy()).cuda()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 1])
+def test_octree_reconstruct_parity(torch, oracle_lib, wl, precision):
+    from paper_1305_3417_gb300 import vof
+    m = wl.mesh
+    ctx = vof.VofContext(m, precision=precision)
+    om = oracle_lib.OracleMesh(m)
+    a = wl.alpha0
+    n, d, fl, it = (t.cpu().numpy() for t in ctx.reconstruct(_T(torch, a)))
+    on, od, ofl, _, _ = om.reconstruct(a)
+    assert np.array_equal(fl, ofl)
+    cells = np.flatnonzero(fl & oracle_lib.ORIENTED)
+    assert cells.size > 100
+    n = n.reshape(3, -1)
+    assert np.abs(n[:, cells] - on[:, cells]).max() < 1e-11
+    _, vc, _, _ = om.geometry()
+    for c in cells[:: max(1, cells.size // 300)]:
+        g = om.cut_volume(c, n[:, c], d[c]) / vc[c] - a[c]
+        assert abs(g) <= 3e-13, (c, g)
+    assert ctx.status() == 0
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [(0, 1e-11), (1, 2e-5)])
+def test_octree_step_replay_parity(torch, oracle_lib, wl, precision, tol):
+    from paper_1305_3417_gb300 import vof
+    m = wl.mesh
+    ctx = vof.VofContext(m, precision=precision)
+    om = oracle_lib.OracleMesh(m)
+    ta = _T(torch, wl.alpha0)
+    for k in range(4):
+        F, U, dt = wl.step_inputs(k)
+        a_in = ta.cpu().numpy().copy()
+        st = ctx.advect(ta, _T(torch, U), _T(torch, F), dt).cpu().numpy()
+        oa, ost, status = om.advect(a_in, U, F, dt)
+        assert status == 0 and ctx.status() == 0
+        assert np.abs(ta.cpu().numpy() - oa).max() < tol, k
+        assert st[6] == ost[6] and st[7] == ost[7]      # interface cells, band faces
+        assert abs(st[1] + st[10] - st[0]) <= 1e-12 * st[0]
