@@ -116,3 +116,36 @@ def test_octree_step_replay_parity(torch, oracle_lib, wl, precision, tol):
         assert np.abs(ta.cpu().numpy() - oa).max() < tol, k
         assert st[6] == ost[6] and st[7] == ost[7]      # interface cells, band faces
         assert abs(st[1] + st[10] - st[0]) <= 1e-12 * st[0]
+
+
+def test_octree_nag_exact_on_uniform_neighbourhoods(oracle_lib, wl):
+    """NAG reproduces a linear field's gradient where every cell around every
+    point of the cell is a box of the same size with no hanging points and no
+    point is on the boundary (as on a uniform lattice's interior): checks the
+    octree's topology and face orientation through the oracle's gradient."""
+    m = wl.mesh
+    om = oracle_lib.OracleMesh(m)
+    cc, _, _, _ = om.geometry()
+    cc = cc.reshape(3, -1) if cc.ndim == 1 else (cc if cc.shape[0] == 3 else cc.T)
+    gr = np.array([0.7, -1.1, 0.4])
+    alpha = 0.3 + gr @ cc
+    g = om.nag_gradient(alpha)
+    # point -> cells through the faces (hanging points included)
+    npf = np.diff(m.face_ptr)
+    fid = np.repeat(np.arange(m.n_faces), npf)
+    P = np.concatenate([m.face_pts, m.face_pts[fid < m.n_internal]])
+    C = np.concatenate([m.owner[fid], m.neighbour[fid[fid < m.n_internal]]])
+    pc = np.unique(np.stack([P, C], 1), axis=0)
+    npts = np.bincount(pc[:, 1], minlength=m.n_cells)                # distinct points per cell
+    box = m.points[m.cell_verts]
+    h = (box.max(1) - box.min(1))[:, 0]
+    plain = (npts == 8) & np.isclose(h, h.max())                    # coarsest boxes, no hanging points
+    # a point on the boundary has a one-sided neighbourhood (as the hex pin's
+    # boundary layer): its cells are left out
+    bad_at_point = np.any(np.isclose(m.points, 0.0) | np.isclose(m.points, 1.0), axis=1)
+    np.logical_or.at(bad_at_point, pc[:, 0], ~plain[pc[:, 1]])
+    cell_bad = np.zeros(m.n_cells, bool)
+    np.logical_or.at(cell_bad, pc[:, 1], bad_at_point[pc[:, 0]])
+    sel = np.flatnonzero(plain & ~cell_bad)
+    assert sel.size > 100
+    assert np.abs(g[:, sel] - gr[:, None]).max() < 1e-11
