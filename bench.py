@@ -250,6 +250,40 @@ def train_guess(device, workload="deform3d"):
             "train_s": time.perf_counter() - t0}
 
 
+def full_run_l1(ctx, w, dev):
+    """The whole case, t = 0 to the workload's end time, on the device (inputs
+    formed on the device from the spatial fields with the same time factors as
+    the timed steps, the last step trimmed to land on the end time), then the L1
+    shape error sum_c V_c |alpha_c(t_end) - alpha_c(0)|: the deformation and
+    vortex fields reverse (cos(pi t / T)), so the exact state at t_end = T is
+    the initial one.  Also the relative volume change over the run."""
+    import torch
+    from paper_1305_3417_gb300 import vof
+    Fs = torch.from_numpy(w.F_spatial).to(dev)
+    Us = torch.from_numpy(np.ascontiguousarray(w.U_spatial).reshape(-1)).to(dev)
+    a0 = torch.from_numpy(w.alpha0.copy()).to(dev)
+    a = a0.clone()
+    st = torch.zeros(vof.S_LEN, dtype=torch.float64, device=dev)
+    f = w.field
+    ctx.status()
+    t, n = 0.0, 0
+    t0 = time.perf_counter()
+    while t < w.t_end - 1e-12 * w.t_end:
+        dt = min(w.dt, w.t_end - t)
+        tf = (f.tau_int(t + dt) - f.tau_int(t)) / dt
+        ctx.advect(a, Us * f.tau(t + 0.5 * dt), Fs * tf, dt, st)
+        t += dt
+        n += 1
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    vc = ctx.geometry()[1]
+    m0 = float((vc * a0).sum())
+    l1 = float((vc * (a - a0).abs()).sum())
+    return {"t_end": w.t_end, "steps": n, "l1": l1, "l1_rel_to_initial_volume": l1 / m0,
+            "rel_volume_change": float((vc * a).sum()) / m0 - 1.0, "alpha_min": float(a.min()),
+            "alpha_max": float(a.max()), "status_bits": int(ctx.status()), "wall_s": secs}
+
+
 def positioning_iterations(ctx, alpha, net):
     """Mean positioning iterations per oriented interface cell, without and
     with the network, on the state alpha (vof_reconstruct)."""
@@ -411,6 +445,10 @@ def main():
     ap.add_argument("--cases", type=int, default=256, help="batch workload: number of cases")
     ap.add_argument("--mlp", action="store_true", help="learned initial guess of the positioning (trained first)")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="batch workload: scale of the n ranges")
+    ap.add_argument("--full-run", type=int, default=-1,
+                    help="after the timed steps, run the whole case (t = 0 to its end) on the device and report the "
+                         "L1 shape error against the initial field (1 on, 0 off; default: on for the periodic "
+                         "deform3d and vortex_tet fields in the mixed form)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init(args)
@@ -521,6 +559,12 @@ def main():
     d2h = 8 * m.n_cells + 8 * vof.S_LEN
     link = host_link_gbps(stream, hU[0])
 
+    full = None
+    do_full = args.full_run if args.full_run >= 0 else int(args.workload in ("deform3d", "vortex_tet")
+                                                          and prec == vof.MIXED)
+    if do_full and rank == 0:
+        full = full_run_l1(ctx, w, dev)
+
     # ---- roofline of the dominant kernel group
     pk, pk_src = peaks()
     per_launch = {g: v / max(nprof, 1) for g, v in group_ms.items()}
@@ -573,7 +617,7 @@ def main():
                             "interface_cells_per_step": float(S[:, 6].mean()),
                             "bound_sources_per_step": float(S[:, 12].mean()),
                             "bound_left_after_local": float(S[:, 13].mean()),
-                            "status_bits": int(st0 | st1)}}
+                            "status_bits": int(st0 | st1), "full_run": full}}
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
