@@ -19,8 +19,12 @@ def wl():
     return I.make_workload("octree", n=N0)
 
 
-def test_octree_mesh_is_a_balanced_closed_partition(oracle_lib, wl):
-    m = wl.mesh
+@pytest.mark.parametrize("levels", [2, 3])
+def test_octree_mesh_is_a_balanced_closed_partition(oracle_lib, wl, levels):
+    """Two levels: the workload's octree; three: a 5^3 base split three times,
+    where the 2:1 balance has to cascade over several levels."""
+    m = wl.mesh if levels == 2 else I.octree_mesh(5, 3, (0.3, 0.6, 0.5), 0.25, band=2.0)
+    n0 = N0 if levels == 2 else 5
     om = oracle_lib.OracleMesh(m)
     cc, vc, cf, sf = om.geometry()
     sf = sf.reshape(3, -1) if sf.ndim == 1 else sf
@@ -44,8 +48,8 @@ def test_octree_mesh_is_a_balanced_closed_partition(oracle_lib, wl):
     npf = np.diff(m.face_ptr)
     assert npf.min() >= 4 and npf.max() <= 8 and (npf > 4).any()
     assert np.unique(m.face_pts).size == m.n_points
-    # three cell sizes, the finest near the sphere
-    assert np.unique(np.round(1.0 / h).astype(int)).tolist() == [N0, 2 * N0, 4 * N0]
+    # levels + 1 cell sizes
+    assert np.unique(np.round(1.0 / h).astype(int)).tolist() == [n0 << L for L in range(levels + 1)]
 
 
 def test_octree_oracle_steps_conserve_and_stay_bounded(oracle_lib, wl):
