@@ -543,3 +543,44 @@ def test_mlp_reference_bf16_rounding():
     assert r[2] == 1.0                                  # tie -> even (down)
     assert r[3] == 1.0 + 2 ** -6                        # tie -> even (up)
     assert r[4] == -2.5 and r[5] == 0.0
+
+
+def _deformation_l1(oracle_lib, n, co):
+    """The oracle through the paper's deformation case on a uniform n^3 hex mesh
+    (sphere R = 0.15 at (0.35, 0.35, 0.35), T = 3, Courant number co on the
+    peak cell-centre speed, last step trimmed to t = T): L1 error against the
+    initial field, and the number of steps with a status bit."""
+    import math
+    mesh = I.hex_mesh((n, n, n))
+    a0 = I.sampled_fraction(mesh, I.sphere_sdf((0.35, 0.35, 0.35), 0.15))
+    fld = I.deformation_field(3.0)
+    Us = I.cell_velocity(mesh, fld.u)
+    dt = co * mesh.h / float(np.sqrt((Us ** 2).sum(0)).max())
+    Fs = I.face_flux_stokes(mesh, fld.A)
+    om = oracle_lib.OracleMesh(mesh)
+    _, vc, _, _ = om.geometry()
+    a, t, flagged = a0.copy(), 0.0, 0
+    while t < 3.0 - 1e-12:
+        d = min(dt, 3.0 - t)
+        tf = (fld.tau_int(t + d) - fld.tau_int(t)) / d
+        a, _, st = om.advect(a, Us * fld.tau(t + 0.5 * d), Fs * tf, d)
+        flagged += st != 0
+        t += d
+    assert math.isclose(t, 3.0)
+    return float((vc * np.abs(a - a0)).sum()), float((vc * (a - a0)).sum()), flagged
+
+
+def test_deformation_error_near_paper_table(oracle_lib):
+    """The whole deformation case (Sec. 5) at 16^3, Co 0.5: the oracle's L1
+    error within [0.75, 1.1] of the paper's printed E_g (table
+    tab:errors:deformation; tests/golden/paper_deformation_eg.txt), the signed
+    sum zero (conservation).  A wrong sign, sweep direction or plane side
+    anywhere in the step moves this error by far more."""
+    import os
+    rows = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "paper_deformation_eg.txt"))
+    paper = rows[rows[:, 0] == 0.5][0, 1]
+    l1, signed, flagged = _deformation_l1(oracle_lib, 16, 0.5)
+    print(f"oracle L1 {l1:.5e}, paper E_g {paper:.5e}")
+    assert abs(signed) < 1e-15
+    assert flagged == 0
+    assert 0.75 * paper <= l1 <= 1.1 * paper
