@@ -182,13 +182,13 @@ int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, d
  * (and stats, VOF_S_LEN doubles, if not NULL) back.  Asynchronous on `stream`;
  * the host arrays must stay valid until the stream reaches the end of it.
  * alpha is copied in order on `stream`.  Uc and F are copied on an internal
- * stream (created with four events at the first call) into one of two device
+ * stream (created, with its events, at the first call) into one of two device
  * buffer pairs, alternating by call, as soon as the step two calls back is
- * done and the previous call's alpha copy is in (so that this, on the step's
- * critical path, never waits in the copy engine behind them): the copies of
- * consecutive calls overlap the previous step's kernels,
- * so Uc and F must hold this step's values when the call is made (they are not
- * ordered after earlier work on `stream`). */
+ * done and the previous call's alpha copy is in (so that the alpha copy, on
+ * the step's critical path, never waits in the copy engine behind them).  The
+ * copies of consecutive calls thus overlap the previous step's kernels, and Uc
+ * and F must hold this step's values when the call is made: they are not
+ * ordered after earlier work on `stream`. */
 int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                     double *stats, void *stream);
 
