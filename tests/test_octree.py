@@ -153,3 +153,19 @@ def test_octree_nag_exact_on_uniform_neighbourhoods(oracle_lib, wl):
     sel = np.flatnonzero(plain & ~cell_bad)
     assert sel.size > 100
     assert np.abs(g[:, sel] - gr[:, None]).max() < 1e-11
+
+
+def test_octree_stokes_fluxes_divergence_free(wl):
+    """Face fluxes from the vector potential (Stokes, edge by edge) sum to zero
+    over every cell's faces to round-off: every face that shares an edge with a
+    hanging point splits it the same way, so the edge integrals cancel."""
+    m = wl.mesh
+    F = wl.F_spatial
+    ni = m.n_internal
+    div = np.zeros(m.n_cells)
+    np.add.at(div, m.owner, F)
+    np.add.at(div, m.neighbour, -F[:ni])
+    scale = np.zeros(m.n_cells)
+    np.add.at(scale, m.owner, np.abs(F))
+    np.add.at(scale, m.neighbour, np.abs(F[:ni]))
+    assert np.abs(div).max() <= 1e-14 * scale.max()
