@@ -169,3 +169,14 @@ def test_octree_stokes_fluxes_divergence_free(wl):
     np.add.at(scale, m.owner, np.abs(F))
     np.add.at(scale, m.neighbour, np.abs(F[:ni]))
     assert np.abs(div).max() <= 1e-14 * scale.max()
+
+
+def test_octree_initial_fractions_hold_the_sphere(wl):
+    """The initial fractions (8^3-point rule per box near the surface) hold the
+    sphere's volume 4/3 pi R^3 to the rule's accuracy, and lie in [0, 1]."""
+    m = wl.mesh
+    box = m.points[m.cell_verts]
+    V = np.prod(box.max(1) - box.min(1), axis=1)
+    a = wl.alpha0
+    assert a.min() >= 0.0 and a.max() <= 1.0
+    assert abs((V * a).sum() / (4.0 / 3.0 * np.pi * 0.15 ** 3) - 1.0) < 1e-3
