@@ -172,9 +172,24 @@ def workload(args):
     return I.make_workload(args.workload, n=args.n)
 
 
-def cpu_baseline(w, steps=1, warmup=0):
+def cpu_model():
+    """The host CPU's model name (lscpu), or the platform's processor string."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(w, steps=1, warmup=0, one_thread=False):
     """The oracle as it stands, timed on the host cores on full steps of the
-    same workload (after `warmup` untimed ones)."""
+    same workload (after `warmup` untimed ones); with one_thread, one more step
+    timed on a single thread beside it."""
     from oracle import oracle as O
     threads = O.set_threads(os.cpu_count() or 1)
     om = O.OracleMesh(w.mesh)
@@ -189,7 +204,17 @@ def cpu_baseline(w, steps=1, warmup=0):
         a, st, s = om.advect(a, U, F, dt)
         t_total += time.perf_counter() - t0
     v = steps * w.mesh.n_internal / t_total / 1e6
-    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+    one = None
+    if one_thread:
+        O.set_threads(1)
+        F, U, dt = w.step_inputs(warmup + steps)
+        t1 = time.perf_counter()
+        om.advect(a, U, F, dt)
+        t1 = time.perf_counter() - t1
+        O.set_threads(threads)
+        one = {"value": w.mesh.n_internal / t1 / 1e6, "cores": 1, "sample": f"1 full oracle step, {t1:.1f} s"}
+    return {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "cpu_model": cpu_model(),
+            "one_thread": one,
             "sample": f"{steps} full oracle step(s) of the {args_workload_name(w)} workload after {warmup} "
                       f"untimed one(s) from t=0 "
                       f"({w.mesh.n_internal} internal faces each), {t_total:.1f} s"}, st
@@ -592,7 +617,7 @@ def main():
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        base, _ = cpu_baseline(w, steps=args.cpu_steps)
+        base, _ = cpu_baseline(w, steps=args.cpu_steps, one_thread=True)
     guess = None
     if learned is not None:
         it0, it1 = positioning_iterations(ctx, alpha, learned["net"])

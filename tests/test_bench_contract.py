@@ -25,3 +25,17 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and "sample" in cb
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("deform3d")
+
+
+def test_cpu_baseline_leg_with_one_thread():
+    """The benchmark's cpu_baseline leg: the oracle on all host cores, the CPU
+    model, and one step on a single thread beside it."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1305_3417_gb300 import inputs as I
+    w = I.make_workload("deform3d", n=8)
+    base, _ = bench.cpu_baseline(w, steps=1, one_thread=True)
+    assert base["kind"] == "oracle" and base["value"] > 0 and base["cores"] >= 1
+    assert isinstance(base["cpu_model"], str) and base["cpu_model"]
+    one = base["one_thread"]
+    assert one["cores"] == 1 and one["value"] > 0
