@@ -17,8 +17,9 @@ LIB = os.path.join(HERE, "liboracle.so")
 
 INTERFACE, ORIENTED, FULL = 1, 2, 4
 S = dict(mass_before=0, mass_after=1, min_pre=2, max_pre=3, min_post=4, max_post=5,
-         n_interface=6, n_band=7, max_pos_it=8, max_corr_it=9, boundary_out=10, status=11)
-S_LEN = 12
+         n_interface=6, n_band=7, max_pos_it=8, max_corr_it=9, boundary_out=10, status=11,
+         bound_passes=12, bound_global=13)
+S_LEN = 14
 EPS = 1e-9
 
 
@@ -52,6 +53,7 @@ def lib():
             "vo_nag_gradient": (V, [P, P, I, P, P]),
             "vo_cut_volume": (D, [P, I, P, D]),
             "vo_reconstruct": (I, [P, P, D, I, P, P, P, P, P]),
+            "vo_position": (I, [P, I, D, P, P]),
             "vo_point_velocity": (V, [P, P, P]),
             "vo_swept_volume": (D, [P, I, P, D, D, D]),
             "vo_correct_flux": (I, [P, P, P, D, I, P, P, P]),
@@ -151,6 +153,12 @@ class OracleMesh:
     def cut_volume(self, cell, n, d):
         n = _f64(n)
         return lib().vo_cut_volume(self.h, int(cell), _p(n), float(d))
+
+    def position(self, cell, alpha, n):
+        """Alg. 1 for one cell and a given unit normal: (d, iterations)."""
+        n = _f64(n); d = np.zeros(1)
+        it = lib().vo_position(self.h, int(cell), float(alpha), _p(n), _p(d))
+        return float(d[0]), int(it)
 
     def reconstruct(self, alpha, eps=EPS, sel=None):
         alpha = _f64(alpha)

@@ -537,10 +537,18 @@ double vo_cut_volume(const vo_mesh *m, int c, const double nn[3], double d)
 #define POS_TOL 1e-13
 #define POS_MAXIT 100
 
+#define POS_SECANT_MAX 20
+
 static int position_cell(const vo_mesh *m, int c, double alpha, v3 n, double *dout)
 {
     /* fill level g(d) = |C ^ {n.x <= d}|/V - alpha rises monotonically from -alpha
-     * at d_min to 1-alpha at d_max (Sec. 2.2.2) */
+     * at d_min to 1-alpha at d_max (Sec. 2.2.2).  Alg. 1: secant steps through the
+     * last two arguments until the secant diverges, then bisection.  Reading R3 of
+     * "diverges": the new argument leaves the current bracket [a, b], or the
+     * secant has taken POS_SECANT_MAX steps without meeting the tolerance (a
+     * stall: deep in the cubic corner of the fill, near alpha = 0 or 1, each
+     * secant step advances by about alpha times the cell extent, while a secant
+     * that converges does so within a dozen steps). */
     double dmin = 1e300, dmax = -1e300, a, b, x0, g0, x1, g1, x = 0.0, gx = 0.0;
     double nn[3] = {n.x, n.y, n.z};
     int i, it = 0, bisect = 0;
@@ -552,9 +560,9 @@ static int position_cell(const vo_mesh *m, int c, double alpha, v3 n, double *do
     a = dmin; b = dmax;
     x0 = a; g0 = -alpha; x1 = b; g1 = 1.0 - alpha;
     while (it < POS_MAXIT) {
+        if (!bisect && it >= POS_SECANT_MAX) bisect = 1;
         if (!bisect) {
-            /* secant through the last two arguments; it has diverged when the new
-             * argument leaves the search interval -> bisection from then on */
+            /* secant through the last two arguments */
             x = x1 - g1 * (x1 - x0) / (g1 - g0);
             if (!(x > a && x < b)) bisect = 1;
         }
@@ -568,6 +576,11 @@ static int position_cell(const vo_mesh *m, int c, double alpha, v3 n, double *do
     }
     *dout = x;
     return it;
+}
+
+int vo_position(const vo_mesh *m, int c, double alpha, const double nn[3], double *d)
+{
+    return position_cell(m, c, alpha, mk(nn[0], nn[1], nn[2]), d);
 }
 
 int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel, const int *sel,
@@ -903,21 +916,30 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 }
 
 /* ---------------------------------------------------------- A7: update */
-#define BOUND_PASSES 1
+#define BOUND_PASSES_MAX 32
 #define BOUND_TOL 1e-13   /* excursions this small (round-off) are left alone and never
                            * decide a redistribution; the target is 1e-12 */
 #define BOUND_FLAG 1e-12  /* a violation above this after the passes is flagged */
 
-/* Reading R10: a conservative local bounding pass (BOUND_PASSES of them) for
- * cells out of [0,1] by more than BOUND_TOL, then the global step below.  Every cell has
- * room for excess, (1-alpha)V, and for deficit, alpha V (zero outside [0,1]).
- * A source with excess e above 1 requests from each face neighbour r the share
- * e room_r / sum(room) of the room around it; a receiver whose requests exceed
- * its room scales them all down to fit.  What a source could not place is
- * pushed in equal parts to all its face neighbours (they pass it on in the next
- * pass), so excess travels on until it meets room.  Deficits mirror this.  All
- * amounts vary continuously with alpha, and every cell's new value is a gather
- * over its face neighbours, so the result does not depend on visiting order. */
+/* Reading R10 of the wisp redistribution of Sec. 2.3: over- and undershoots
+ * are redistributed conservatively to the surrounding interface cells, and
+ * neither the removal nor the addition may create new over/undershoots or
+ * wisps.  Read as passes of a local redistribution among face neighbours:
+ *  - a source is a cell with alpha > 1 + BOUND_TOL (excess e = (alpha-1) V) or
+ *    alpha < -BOUND_TOL (deficit u = -alpha V);
+ *  - a receiver is an interface cell, BOUND_TOL < alpha < 1 - BOUND_TOL; its
+ *    weight w = alpha (1 - alpha) V vanishes at both ends, so that no bulk cell
+ *    receives (no wisp is made) and the amounts vary continuously with alpha;
+ *  - a source asks each face neighbour r for e w_r / W, W the sum of its
+ *    neighbours' weights; a receiver takes at most its room, (1 - alpha) V for
+ *    excess and alpha V for deficit, and scales all requests down to fit, so
+ *    it never leaves [0, 1] (no new over/undershoot);
+ *  - what a source could not place stays with it for the next pass.
+ * Each pass either finishes a source or fills (empties) at least one of its
+ * receivers, whose weight is then zero; passes run until no source has both
+ * something left and a receiver with room (BOUND_PASSES_MAX is a safety cap).
+ * Every cell's new value is a gather over its face neighbours, so the result
+ * does not depend on visiting order. */
 static int face_nbr(const vo_mesh *m, int c, int i)
 {
     int f = m->cface[i];
@@ -925,101 +947,83 @@ static int face_nbr(const vo_mesh *m, int c, int i)
     return m->own[f] == c ? m->nei[f] : m->own[f];
 }
 
-static double room_exc(double a, double V) { return (a >= 0.0 && a < 1.0) ? (1.0 - a) * V : 0.0; }
-static double room_def(double a, double V) { return (a > 0.0 && a <= 1.0) ? a * V : 0.0; }
+static double recv_w(double a, double V) { return (a > BOUND_TOL && a < 1.0 - BOUND_TOL) ? a * (1.0 - a) * V : 0.0; }
+static double room_exc(double a, double V) { return recv_w(a, V) > 0.0 ? (1.0 - a) * V : 0.0; }
+static double room_def(double a, double V) { return recv_w(a, V) > 0.0 ? a * V : 0.0; }
 
+/* one pass; returns the number of sources that had a receiver */
 static int bound_pass(const vo_mesh *m, double *alpha)
 {
-    int nc = m->nc, c, any = 0;
+    int nc = m->nc, c, active = 0;
     size_t n1 = (size_t)(nc > 0 ? nc : 1);
     double *e = (double *)calloc(n1, sizeof(double)), *u = (double *)calloc(n1, sizeof(double));
-    double *Cp = (double *)calloc(n1, sizeof(double)), *Cm = (double *)calloc(n1, sizeof(double));
+    double *W = (double *)calloc(n1, sizeof(double));
     double *sp = (double *)malloc(n1 * sizeof(double)), *sm = (double *)malloc(n1 * sizeof(double));
-    double *rp = (double *)calloc(n1, sizeof(double)), *rm = (double *)calloc(n1, sizeof(double));
-    int *dg = (int *)calloc(n1, sizeof(int));
     double *na = (double *)malloc(n1 * sizeof(double));
     for (c = 0; c < nc; c++) {
         double a = alpha[c];
-        if (a > 1.0 + BOUND_TOL) { e[c] = (a - 1.0) * m->vc[c]; any = 1; }
-        if (a < -BOUND_TOL) { u[c] = -a * m->vc[c]; any = 1; }
+        if (a > 1.0 + BOUND_TOL) e[c] = (a - 1.0) * m->vc[c];
+        if (a < -BOUND_TOL) u[c] = -a * m->vc[c];
     }
-    if (any) {
-        /* (1) room around each source */
-#pragma omp parallel for schedule(static)
-        for (c = 0; c < nc; c++) {
-            int i;
-            if (e[c] == 0.0 && u[c] == 0.0) continue;
-            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
-                int nb = face_nbr(m, c, i);
-                if (nb < 0) continue;
-                Cp[c] += room_exc(alpha[nb], m->vc[nb]);
-                Cm[c] += room_def(alpha[nb], m->vc[nb]);
-                dg[c]++;
-            }
+    /* (1) total receiver weight around each source */
+    for (c = 0; c < nc; c++) {
+        int i;
+        if (e[c] == 0.0 && u[c] == 0.0) continue;
+        for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+            int nb = face_nbr(m, c, i);
+            if (nb >= 0) W[c] += recv_w(alpha[nb], m->vc[nb]);
         }
+        if (W[c] > 0.0) active++;
+    }
+    if (active) {
         /* (2) scale of each receiver: requests beyond its room are cut to fit */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i;
-            double Qp = 0.0, Qm = 0.0, Rp = room_exc(alpha[c], m->vc[c]), Rm = room_def(alpha[c], m->vc[c]);
+            double Qp = 0.0, Qm = 0.0, wc = recv_w(alpha[c], m->vc[c]);
+            double Rp = room_exc(alpha[c], m->vc[c]), Rm = room_def(alpha[c], m->vc[c]);
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
                 int nb = face_nbr(m, c, i);
-                if (nb < 0) continue;
-                if (e[nb] > 0.0 && Cp[nb] > 0.0) Qp += e[nb] * (Rp / Cp[nb]);
-                if (u[nb] > 0.0 && Cm[nb] > 0.0) Qm += u[nb] * (Rm / Cm[nb]);
+                if (nb < 0 || W[nb] == 0.0) continue;
+                if (e[nb] > 0.0) Qp += e[nb] * (wc / W[nb]);
+                if (u[nb] > 0.0) Qm += u[nb] * (wc / W[nb]);
             }
             sp[c] = Qp > Rp ? Rp / Qp : 1.0;
             sm[c] = Qm > Rm ? Rm / Qm : 1.0;
         }
-        /* (3) what each source placed, and the rest it pushes on */
+        /* (3) new value of every cell: what it placed (a source), what its
+         * source neighbours placed in it (a receiver) */
 #pragma omp parallel for schedule(static)
         for (c = 0; c < nc; c++) {
             int i;
-            double gp = 0.0, gm = 0.0;
-            if (e[c] == 0.0 && u[c] == 0.0) continue;
+            double dV = 0.0, V = m->vc[c], wc = recv_w(alpha[c], V);
             for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
                 int nb = face_nbr(m, c, i);
                 if (nb < 0) continue;
-                if (e[c] > 0.0 && Cp[c] > 0.0) gp += e[c] * (room_exc(alpha[nb], m->vc[nb]) / Cp[c]) * sp[nb];
-                if (u[c] > 0.0 && Cm[c] > 0.0) gm += u[c] * (room_def(alpha[nb], m->vc[nb]) / Cm[c]) * sm[nb];
-            }
-            if (e[c] > 0.0) rp[c] = dg[c] > 0 ? e[c] - gp : 0.0;
-            if (u[c] > 0.0) rm[c] = dg[c] > 0 ? u[c] - gm : 0.0;
-            if (dg[c] == 0) { e[c] = gp; u[c] = gm; } /* nothing to push to: release only what was placed */
-        }
-        /* (4) new value of every cell: its own release, then what its neighbours send */
-#pragma omp parallel for schedule(static)
-        for (c = 0; c < nc; c++) {
-            int i;
-            double dV = 0.0, V = m->vc[c];
-            double Rp = room_exc(alpha[c], V), Rm = room_def(alpha[c], V);
-            if (e[c] > 0.0) dV -= e[c];
-            if (u[c] > 0.0) dV += u[c];
-            for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
-                int nb = face_nbr(m, c, i);
-                if (nb < 0) continue;
-                if (e[nb] > 0.0) {
-                    if (Cp[nb] > 0.0) dV += e[nb] * (Rp / Cp[nb]) * sp[c];
-                    if (dg[nb] > 0) dV += rp[nb] / dg[nb];
+                if (W[c] > 0.0) { /* c is a source: what it placed in nb */
+                    double wn = recv_w(alpha[nb], m->vc[nb]);
+                    if (e[c] > 0.0) dV -= e[c] * (wn / W[c]) * sp[nb];
+                    if (u[c] > 0.0) dV += u[c] * (wn / W[c]) * sm[nb];
                 }
-                if (u[nb] > 0.0) {
-                    if (Cm[nb] > 0.0) dV -= u[nb] * (Rm / Cm[nb]) * sm[c];
-                    if (dg[nb] > 0) dV -= rm[nb] / dg[nb];
+                if (W[nb] > 0.0) { /* nb is a source: what it placed in c */
+                    if (e[nb] > 0.0) dV += e[nb] * (wc / W[nb]) * sp[c];
+                    if (u[nb] > 0.0) dV -= u[nb] * (wc / W[nb]) * sm[c];
                 }
             }
             na[c] = dV != 0.0 ? (alpha[c] * V + dV) / V : alpha[c];
         }
         memcpy(alpha, na, sizeof(double) * (size_t)nc);
     }
-    free(e); free(u); free(Cp); free(Cm); free(sp); free(sm); free(rp); free(rm); free(dg); free(na);
-    return any;
+    free(e); free(u); free(W); free(sp); free(sm); free(na);
+    return active;
 }
 
-/* What the local passes leave is moved in one global step: the total excess
- * (deficit) goes to every cell strictly inside (BOUND_TOL, 1-BOUND_TOL) in
- * proportion to its free (phase) volume, and the sources are set to 1 (0).
- * Skipped when the receivers cannot hold it.  Returns 1 if applied. */
-static int bound_global(const vo_mesh *m, double *alpha)
+/* Fallback for what the local passes leave (a source none of whose face
+ * neighbours is an interface cell with room): the total excess (deficit) goes
+ * to every cell strictly inside (BOUND_TOL, 1-BOUND_TOL) in proportion to its
+ * free (phase) volume, and the sources are set to 1 (0).  Skipped when the
+ * receivers cannot hold it.  Returns the volume moved (0 if none). */
+static double bound_global(const vo_mesh *m, double *alpha)
 {
     double Ep = 0.0, Em = 0.0, Sp = 0.0, Sm = 0.0;
     int c;
@@ -1029,7 +1033,7 @@ static int bound_global(const vo_mesh *m, double *alpha)
         else if (a < -BOUND_TOL) Em += -a * V;
         else if (a > BOUND_TOL && a < 1.0 - BOUND_TOL) { Sp += (1.0 - a) * V; Sm += a * V; }
     }
-    if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return 0;
+    if ((Ep == 0.0 && Em == 0.0) || Ep > Sp || Em > Sm) return 0.0;
     for (c = 0; c < m->nc; c++) {
         double a = alpha[c], V = m->vc[c];
         if (a > 1.0 + BOUND_TOL) alpha[c] = 1.0;
@@ -1041,7 +1045,7 @@ static int bound_global(const vo_mesh *m, double *alpha)
             alpha[c] = (a * V + dV) / V;
         }
     }
-    return 1;
+    return Ep + Em;
 }
 
 int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, double *stats)
@@ -1066,9 +1070,12 @@ int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, doub
     if (stats) { stats[VO_S_MIN_PRE] = mn; stats[VO_S_MAX_PRE] = mx; }
     if (bound) {
         int p;
-        for (p = 0; p < BOUND_PASSES; p++)
+        double gv;
+        for (p = 0; p < BOUND_PASSES_MAX; p++)
             if (!bound_pass(m, alpha)) break;
-        if (p == BOUND_PASSES) bound_global(m, alpha);
+        gv = bound_global(m, alpha);
+        if (stats) { stats[VO_S_BOUND_PASSES] = p; stats[VO_S_BOUND_GLOBAL] = gv; }
+        if (p == BOUND_PASSES_MAX) st |= VO_ST_BOUND_RESIDUAL;
         for (c = 0; c < m->nc; c++)
             if (alpha[c] < -BOUND_FLAG || alpha[c] > 1.0 + BOUND_FLAG) { st |= VO_ST_BOUND_RESIDUAL; break; }
     }

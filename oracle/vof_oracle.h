@@ -33,7 +33,10 @@ enum { VO_ST_POS_NOT_CONVERGED = 1, VO_ST_CORR_NOT_CONVERGED = 2, VO_ST_BAD_VOLU
 /* stats[] layout written by vo_update / vo_advect */
 enum { VO_S_MASS_BEFORE = 0, VO_S_MASS_AFTER, VO_S_MIN_PRE, VO_S_MAX_PRE, VO_S_MIN_POST,
        VO_S_MAX_POST, VO_S_N_INTERFACE, VO_S_N_BAND, VO_S_MAX_POS_IT, VO_S_MAX_CORR_IT,
-       VO_S_BOUNDARY_OUT, VO_S_STATUS, VO_S_LEN };
+       VO_S_BOUNDARY_OUT, VO_S_STATUS,
+       VO_S_BOUND_PASSES,   /* local redistribution passes that moved something */
+       VO_S_BOUND_GLOBAL,   /* volume left to the global fallback after them */
+       VO_S_LEN };
 
 typedef struct vo_mesh vo_mesh;
 
@@ -61,6 +64,9 @@ void vo_nag_gradient(const vo_mesh *m, const double *alpha, int n_sel, const int
 
 /* |C_c ^ {x : n.x <= d}| by clipping and capping every centre-apex tetrahedron */
 double vo_cut_volume(const vo_mesh *m, int cell, const double n[3], double d);
+/* Alg. 1 for one cell with a given unit normal: d with |C ^ {n.x <= d}| = alpha V;
+ * returns the iterations taken (POS_MAXIT = 100 means not converged) */
+int vo_position(const vo_mesh *m, int cell, double alpha, const double n[3], double *d);
 /* Alg. 1 for the selected cells (all when sel == NULL); n (3*nc SoA), d, flags,
  * iters are indexed by cell.  Returns status bits. */
 int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel,
@@ -85,7 +91,8 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 /* sum over stencil cells of |S_f ^ C_s| with the polyhedron's signs (coverage) */
 double vo_stencil_coverage(const vo_mesh *m, int face, const double *Up, double F, double dt,
                            double lambda);
-/* Eq. alpha-discrete with Eq. own-nei; optional conservative bounding pass */
+/* Eq. alpha-discrete with Eq. own-nei; optional conservative redistribution of
+ * over/undershoots (reading R10 of Sec. 2.3's wisp redistribution) */
 int vo_update(const vo_mesh *m, double *alpha, const double *Valpha, int bound, double *stats);
 /* full step: classify, reconstruct, point velocity, correct, phase flux, update */
 int vo_advect(const vo_mesh *m, double *alpha, const double *Uc, const double *F, double dt,

@@ -241,6 +241,36 @@ def test_reconstruct_flags(oracle_lib):
     assert fl[2] & oracle_lib.INTERFACE and fl[3] == 0
 
 
+@pytest.mark.parametrize("a", [1e-7, 1e-6, 1 - 1e-7])
+def test_positioning_converges_near_the_cube_corner(oracle_lib, a):
+    """Alg. 1 (Sec. 2.2.2) for alpha near 0 or 1 and a nearly axis-aligned
+    normal: the root lies deep in the cubic corner region of the fill, where
+    a secant step advances by about alpha times the cell extent.  The plane
+    must still meet |g| <= 1e-13 well under the 100-iteration limit (reading
+    R3: a secant that has not converged in 20 steps is taken as divergent).
+    Checked against the Scardovelli & Zaleski closed form, which near the
+    corner is the single well-conditioned term d^3 / (6 n1 n2 n3)."""
+    m = I.hex_mesh((1, 1, 1))
+    om = oracle_lib.OracleMesh(m)
+    rng = np.random.default_rng(31)
+    worst_it = 0
+    for k in range(60):
+        n = np.array([1.0, *(rng.uniform(0.2, 1.0, 2) * 10.0 ** rng.uniform(-4, -2, 2))])
+        n = n[rng.permutation(3)] * rng.choice([-1.0, 1.0], 3)
+        n /= np.linalg.norm(n)
+        d, it = om.position(0, a, n)
+        assert it < 60, (k, it)
+        worst_it = max(worst_it, it)
+        if a < 0.5:
+            # plane n.x <= d within the unit cube: shift to the corner of min n.x
+            v = sz_cube_volume(n, d)
+            assert v == pytest.approx(a, abs=1e-13)
+        else:
+            v = sz_cube_volume(-n, -d)  # the void side, near its own corner
+            assert v == pytest.approx(1 - a, abs=1e-13)
+    assert worst_it > 20  # the stall branch was exercised
+
+
 # ------------------------------------------------------------- A4/A5: sweep
 
 def test_uniform_sweep_volume_is_flux(oracle_lib):
@@ -462,7 +492,94 @@ def test_unoriented_constant_field_carries_alpha(oracle_lib):
     assert np.abs(Va[fb] - 0.6 * F[fb] * dt).max(initial=0) < 1e-2 * np.abs(F * dt).max()
 
 
+# --------------------------------------------------------------- A4: walls
+
+@pytest.mark.parametrize("open_sides", [(), ("x+", "z-")])
+def test_wall_points_keep_the_tangential_velocity(oracle_lib, open_sides):
+    """Reading R2: at a point on wall faces only the component of the IDW
+    velocity tangent to every wall through it is kept.  On a box with an
+    oblique uniform field (IDW reproduces it) that is U with the components
+    along the normals of the point's wall planes removed: U minus its normal
+    component on a wall face, the edge-direction component on a wall edge,
+    zero at a wall corner; a point on an open side keeps that component."""
+    m = I.hex_mesh((3, 4, 3), jitter=0.2, seed=41, open_sides=open_sides)
+    om = oracle_lib.OracleMesh(m)
+    U = np.array([0.3, -0.5, 0.8])
+    Uc = np.repeat(U[:, None], m.n_cells, 1)
+    Up = om.point_velocity(Uc)
+    x = m.points
+    expect = np.repeat(U[None, :], m.n_points, 0)
+    for ax, nm in enumerate("xyz"):
+        for side, val in (("-", 0.0), ("+", 1.0)):
+            if nm + side in open_sides:
+                continue
+            on = np.abs(x[:, ax] - val) < 1e-14
+            expect[on, ax] = 0.0
+    n_walls = np.zeros(m.n_points, int)
+    for ax, nm in enumerate("xyz"):
+        for side, val in (("-", 0.0), ("+", 1.0)):
+            if nm + side not in open_sides:
+                n_walls += np.abs(x[:, ax] - val) < 1e-14
+    assert (n_walls == 1).any() and (n_walls == 2).any() and (n_walls == 3).any()
+    assert np.abs(Up.T - expect).max() < 1e-14
+
+
 # --------------------------------------------------------------- A7: update
+
+def _row_update(oracle_lib, alpha):
+    """vo_update with zero fluxes on a row of unit-volume-fraction cells
+    (a 1 x 1 x n hexahedral row: face neighbours i-1 and i+1, equal volumes):
+    only the redistribution of reading R10 changes alpha."""
+    n = len(alpha)
+    m = I.hex_mesh((n, 1, 1), length=(1.0, 1.0 / n, 1.0 / n))
+    om = oracle_lib.OracleMesh(m)
+    _, vc, _, _ = om.geometry()
+    a, st, status = om.update(np.array(alpha, float), np.zeros(m.n_faces))
+    return a, st, status, vc[0]
+
+
+def test_redistribution_amounts_proportional_to_weights(oracle_lib):
+    """Reading R10 (Sec. 2.3 wisp redistribution), amounts by hand.  Source 1
+    (excess 0.2) asks its neighbours in proportion to w = alpha (1 - alpha):
+    0.21 and 0.09 of 0.30, so cell 0 gets 0.14 and cell 2 gets 0.06.
+    Source 4 (deficit 0.05) has one receiver with weight (cell 5 is empty:
+    weight 0, no wisp is made): cell 3 gives 0.05."""
+    a, st, status, V = _row_update(oracle_lib, [0.3, 1.2, 0.9, 0.5, -0.05, 0.0, 0.0])
+    S = oracle_lib.S
+    assert status == 0
+    np.testing.assert_allclose(a, [0.44, 1.0, 0.96, 0.45, 0.0, 0.0, 0.0], rtol=0, atol=1e-14)
+    assert st[S["bound_passes"]] == 1 and st[S["bound_global"]] == 0.0
+    assert st[S["max_pre"]] == 1.2 and st[S["min_pre"]] == -0.05
+
+
+def test_redistribution_shared_receiver_scales_then_global(oracle_lib):
+    """Two sources share receiver 1 (room 0.4): requests 0.2 and 0.3 are
+    scaled by 0.8 to 0.16 and 0.24, filling it.  Neither source has another
+    receiver (cell 3 is empty), so the rest, 0.04 + 0.06 = 0.10, goes to the
+    global fallback: each strictly mixed cell takes 0.10 (1 - alpha) / 2.0,
+    here 0.025, and the sources are set to 1."""
+    a, st, status, V = _row_update(oracle_lib, [1.2, 0.6, 1.3, 0.0, 0.5, 0.5, 0.5, 0.5])
+    S = oracle_lib.S
+    assert status == 0
+    np.testing.assert_allclose(a, [1.0, 1.0, 1.0, 0.0, 0.525, 0.525, 0.525, 0.525], rtol=0, atol=1e-14)
+    assert st[S["bound_passes"]] == 1
+    assert st[S["bound_global"]] == pytest.approx(0.10 * V, rel=1e-12)
+
+
+def test_redistribution_second_pass_after_a_receiver_fills(oracle_lib):
+    """Source 1 (excess 0.5): receiver 0 (alpha 0.95, weight 0.0475, room
+    0.05) is asked for 0.5 * 0.0475 / 0.2075 > 0.05 and fills; receiver 2
+    (weight 0.16, room 0.8) takes its request 0.5 * 0.16 / 0.2075.  The rest
+    stays with the source and goes to cell 2 in a second pass: cell 2 ends at
+    0.2 + 0.5 - 0.05 = 0.65."""
+    a, st, status, V = _row_update(oracle_lib, [0.95, 1.5, 0.2, 0.0, 0.0])
+    S = oracle_lib.S
+    assert status == 0
+    np.testing.assert_allclose(a, [1.0, 1.0, 0.65, 0.0, 0.0], rtol=0, atol=1e-14)
+    assert st[S["bound_passes"]] == 2 and st[S["bound_global"]] == 0.0
+
+
+
 
 def test_conservation_and_boundedness_deformation(oracle_lib):
     w = I.make_workload("deform3d", n=16)
