@@ -35,18 +35,32 @@ sys.path.insert(0, ROOT)
 
 METRIC = "geometric VoF face fluxes/s (M/s), mixed vs plain FP64 GPU, at stated L1 error"
 UNIT = "M face fluxes/s"
-# algorithmic flop cost model of the phase-flux kernel (primitive costs: signed
-# distance 6, edge intersection 10, tetrahedron volume 17, plane from 3 points 20)
-FLOPS_PER_PAIR = 16 * 6 + 4 * 20     # 4 planes of the cell tetrahedron, 4x4 distances
+# Algorithmic flop cost of each primitive the step kernels count (vof_work_counts;
+# signed point-plane distance 6 = 3 FMA, edge intersection 10 including its
+# division, tetrahedron volume 17, closed-form cut fraction 30 = three
+# division-bearing edge parameters and their product):
+#  - phase flux, FP32 in the mixed form and FP64 in the plain one: six
+#    distances per prism-plane set, four per piece-plane test, the rest as named
+PF_FLOPS = {"prism_planes": 6 * 6, "piece_tests": 4 * 6, "edges": 10, "tet_volumes": 17, "cut_fractions": 30,
+            "plane_shifts": 6}
+#  - positioning: one fill evaluation of a cell tetrahedron (sorted projections,
+#    closed-form cut fraction and its derivative) 30, FP64 or FP32 as counted
+FILL_FLOPS = 30
+#  - correction (FP64): the cubic's coefficients from one swept face triangle
+#    (E1, E2, the summed stream vector and four 3x3 determinants) 110, one cubic
+#    evaluation with its scale and Newton step 20
+CTRI_FLOPS, CEVAL_FLOPS = 110, 20
+# algorithmic HBM bytes per internal face and step (flux 8, owner/neighbour 8,
+# face point indices 20, alpha r/w and volume 8, point data 28)
+BYTES_PER_FACE = 72.0
 
 # DRAM bytes per launch of the mixed phase-flux kernel: dram__bytes_read.sum +
-# dram__bytes_write.sum, mean of three launches (the 4th to 6th) of one ncu
-# capture of the default command (ncu --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum,gpu__time_duration.sum -k regex:k_phase_flux_mixed -s 3
-# -c 3 python bench.py --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0);
+# dram__bytes_write.sum, mean of three launches of one ncu capture of the
+# default command (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
+# gpu__time_duration.sum -k regex:k_phase_flux_mixed -s 3 -c 3 python bench.py
+# --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 --full-run 0);
 # valid while the kernel's sources hash to the captured digest, else null.
-TRAFFIC = {("deform3d", 128, "mixed"): {"bytes": 67.99e6,
-           "sources_sha256": "6b0d06b17013e5365a8d5f0d0de8610afb484975cc90b056c79af87e3a9d17bd"}}
+TRAFFIC = {}
 TRAFFIC_SOURCES = ["paper_1305_3417_gb300/csrc/vof_mixed.cu", "paper_1305_3417_gb300/csrc/vof_device.cuh"]
 
 
@@ -60,7 +74,36 @@ def captured_traffic(workload, n, precision):
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return t["bytes"] if h.hexdigest() == t["sources_sha256"] else None
-FLOPS_PER_CUT = 4 * 10 + 3 * 17      # edge intersections + resulting tetrahedra volumes
+
+
+def work_flops(work, fp64_phase_flux):
+    """(FP32 flops, FP64 flops, phase-flux flops) of counted work."""
+    pf = sum(work[k] * v for k, v in PF_FLOPS.items())
+    f32 = work["fill32"] * FILL_FLOPS
+    f64 = work["fill64"] * FILL_FLOPS + work["cubic_triangles"] * CTRI_FLOPS + work["cubic_evals"] * CEVAL_FLOPS
+    if fp64_phase_flux:
+        f64 += pf
+    else:
+        f32 += pf
+    return f32, f64, pf
+
+
+def counted_work(ctx, alpha, steps):
+    """The algorithmic work of the given steps (list of (U, F, dt)), counted by
+    the instrumented kernels from the state alpha (a copy is advanced; the
+    timed steps ran the uninstrumented kernels from the same state).  Per step."""
+    import torch
+    from paper_1305_3417_gb300 import vof
+    a = alpha.clone()
+    st = torch.zeros(vof.S_LEN, dtype=torch.float64, device=alpha.device)
+    vof.vof_work_counts(ctx.h, reset=True)
+    vof.vof_count_work(ctx.h, True)
+    for U, F, dt in steps:
+        ctx.advect(a, U, F, dt, st)
+    torch.cuda.synchronize()
+    vof.vof_count_work(ctx.h, False)
+    w = vof.vof_work_counts(ctx.h, reset=True)
+    return {k: v / max(len(steps), 1) for k, v in w.items()}
 
 
 def peaks():
@@ -291,22 +334,34 @@ def full_run_l1(ctx, w, dev):
     st = torch.zeros(vof.S_LEN, dtype=torch.float64, device=dev)
     f = w.field
     ctx.status()
-    t, n = 0.0, 0
-    t0 = time.perf_counter()
+    # the step inputs of the whole case formed first (device), so that the
+    # events below time the steps alone
+    sched, t = [], 0.0
     while t < w.t_end - 1e-12 * w.t_end:
         dt = min(w.dt, w.t_end - t)
-        tf = (f.tau_int(t + dt) - f.tau_int(t)) / dt
-        ctx.advect(a, Us * f.tau(t + 0.5 * dt), Fs * tf, dt, st)
+        sched.append((t, dt))
         t += dt
-        n += 1
-    torch.cuda.synchronize()
+    n = len(sched)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gpu_ms = 0.0
+    t0 = time.perf_counter()
+    for i0 in range(0, n, 64):
+        chunk = [(Us * f.tau(t + 0.5 * dt), Fs * ((f.tau_int(t + dt) - f.tau_int(t)) / dt), dt)
+                 for t, dt in sched[i0:i0 + 64]]
+        e0.record(stream)
+        for U, F, dt in chunk:
+            ctx.advect(a, U, F, dt, st)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        gpu_ms += e0.elapsed_time(e1)
     secs = time.perf_counter() - t0
     vc = ctx.geometry()[1]
     m0 = float((vc * a0).sum())
     l1 = float((vc * (a - a0).abs()).sum())
     return {"t_end": w.t_end, "steps": n, "l1": l1, "l1_rel_to_initial_volume": l1 / m0,
             "rel_volume_change": float((vc * a).sum()) / m0 - 1.0, "alpha_min": float(a.min()),
-            "alpha_max": float(a.max()), "status_bits": int(ctx.status()), "wall_s": secs}
+            "alpha_max": float(a.max()), "status_bits": int(ctx.status()), "wall_s": secs, "gpu_ms": gpu_ms}
 
 
 def positioning_iterations(ctx, alpha, net):
@@ -407,22 +462,30 @@ def run_batch(args, world, rank, local):
     m0, m1 = mass0.cpu().numpy(), mass.cpu().numpy()
     S = stats.cpu().numpy()
     st1 = vof.vof_status(ctx)
-    # kernel groups and work (direct launches, profiled; the graph holds the same kernels)
+    # kernel groups (direct launches, profiled; the graph holds the same
+    # kernels), then the same steps' work from the instrumented kernels
     pa = alpha.clone()
-    vof.vof_work_counts(ctx, reset=True)
     vof.vof_profile_begin(ctx, 3)
     for _ in range(3):
         vof.vof_advect(ctx, pa, U, F, 1.0, stats)
     group_ms, nprof = vof.vof_profile_end(ctx)
-    work = vof.vof_work_counts(ctx, reset=True)
     launches = vof.vof_last_launch_count(ctx) * args.steps
     per_launch = {g: v / max(nprof, 1) for g, v in group_ms.items()}
-    fl = (work["pairs"] * FLOPS_PER_PAIR + work["cuts"] * FLOPS_PER_CUT) / max(nprof, 1)
+    pa = alpha.clone()
+    vof.vof_work_counts(ctx, reset=True)
+    vof.vof_count_work(ctx, True)
+    for _ in range(3):
+        vof.vof_advect(ctx, pa, U, F, 1.0, stats)
+    torch.cuda.synchronize()
+    vof.vof_count_work(ctx, False)
+    work = {k: v / 3 for k, v in vof.vof_work_counts(ctx, reset=True).items()}
+    f32, f64, pf = work_flops(work, False)
     alu = vof.vof_probe_fma(local, vof.MIXED)
-    achieved = fl / (per_launch["phase_flux"] * 1e-3) / 1e12
-    roof = {"kernel": "k_phase_flux", "bound": "alu", "achieved": achieved, "peak": alu / 1e12, "unit": "TFLOP/s",
-            "frac": achieved * 1e12 / alu, "traffic": None, "peak_source": "measured FP32 FMA probe (vof_probe_fma)",
-            "group_ms_per_step": per_launch}
+    achieved = pf / (per_launch["phase_flux"] * 1e-3) / 1e12
+    roof = {"kernel": "k_phase_flux_mixed", "bound": "alu", "achieved": achieved, "peak": alu / 1e12,
+            "unit": "TFLOP/s", "frac": achieved * 1e12 / alu, "traffic": None,
+            "peak_source": "measured FP32 FMA probe (vof_probe_fma)", "group_ms_per_step": per_launch,
+            "work_per_launch": work, "flops_per_launch": pf}
     # end to end with host buffers (context's host-buffer step, dt = 1)
     ha = torch.from_numpy(b.alpha0.copy()).pin_memory()
     hU, hF = U.cpu().pin_memory(), F.cpu().pin_memory()
@@ -472,8 +535,8 @@ def main():
     ap.add_argument("--batch-scale", type=float, default=1.0, help="batch workload: scale of the n ranges")
     ap.add_argument("--full-run", type=int, default=-1,
                     help="after the timed steps, run the whole case (t = 0 to its end) on the device and report the "
-                         "L1 shape error against the initial field (1 on, 0 off; default: on for the periodic "
-                         "deform3d and vortex_tet fields in the mixed form)")
+                         "L1 shape error against the initial field and the whole-case rate (1 on, 0 off; default: "
+                         "on for the periodic deform3d and vortex_tet fields in the mixed form)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_init(args)
@@ -514,8 +577,9 @@ def main():
     for k in range(args.skip + args.warmup):
         ctx.advect(alpha, Uk[k], Fk[k], w.dt, stats)
     torch.cuda.synchronize()
+    a_start = alpha.clone()
+    timed = [(Uk[args.skip + args.warmup + j], Fk[args.skip + args.warmup + j], w.dt) for j in range(args.steps)]
     st0 = ctx.status()
-    vof.vof_work_counts(ctx.h, reset=True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     step_stats = torch.zeros((args.steps, vof.S_LEN), dtype=torch.float64, device=dev)
     vof.vof_profile_begin(ctx.h, args.steps)
@@ -523,15 +587,13 @@ def main():
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         e0.record(stream)
-        for j in range(args.steps):
-            k = args.skip + args.warmup + j
-            ctx.advect(alpha, Uk[k], Fk[k], w.dt, step_stats[j])
+        for j, (U, F, dt) in enumerate(timed):
+            ctx.advect(alpha, U, F, dt, step_stats[j])
         e1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
     ms = e0.elapsed_time(e1)
     group_ms, nprof = vof.vof_profile_end(ctx.h)
-    work = vof.vof_work_counts(ctx.h, reset=True)
     launches = vof.vof_last_launch_count(ctx.h) * args.steps
     st1 = ctx.status()
     ms_max = max_over_ranks(ms, world, dev)
@@ -539,6 +601,10 @@ def main():
     value = faces / (ms_max * 1e-3) / 1e6
     S = step_stats.cpu().numpy()
     drift = np.abs((S[:, 1] + S[:, 10] - S[:, 0]) / S[:, 0]).max()
+    # the timed steps' algorithmic work, from the instrumented kernels on the same states
+    work = counted_work(ctx, a_start, timed)
+    peak32 = vof.vof_probe_fma(local, vof.MIXED)
+    peak64 = vof.vof_probe_fma(local, vof.FP64)
 
     # ---- the other form on the same steps, for comparison (plain FP64 vs mixed)
     other = None
@@ -551,23 +617,36 @@ def main():
             octx.advect(oa, Uk[k], Fk[k], w.dt, ost)
         torch.cuda.synchronize()
         ns = min(args.fp64_steps, args.steps)
+        oa_start = oa.clone()
         o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vof.vof_profile_begin(octx.h, ns)
         o0.record(stream)
         for j in range(ns):
-            octx.advect(oa, Uk[args.skip + args.warmup + j], Fk[args.skip + args.warmup + j], w.dt, ost)
+            octx.advect(oa, *timed[j][:2], w.dt, ost)
         o1.record(stream)
         torch.cuda.synchronize()
+        ogroup, onprof = vof.vof_profile_end(octx.h)
         oms = o0.elapsed_time(o1) / ns
+        owork = counted_work(octx, oa_start, timed[:1])
+        of32, of64, opf = work_flops(owork, oprec == vof.FP64)
+        opk = peak64 if oprec == vof.FP64 else peak32
+        ot_pf = ogroup["phase_flux"] / max(onprof, 1)
         other = {"precision": "fp64" if oprec == vof.FP64 else "mixed", "value": m.n_internal / (oms * 1e-3) / 1e6,
-                 "unit": UNIT, "ms_per_step": oms, "steps": ns}
+                 "unit": UNIT, "ms_per_step": oms, "steps": ns,
+                 "group_ms_per_step": {g: v / max(onprof, 1) for g, v in ogroup.items()},
+                 "roofline": {"kernel": "k_phase_flux" if oprec == vof.FP64 else "k_phase_flux_mixed", "bound": "alu",
+                              "achieved": opf / (ot_pf * 1e-3) / 1e12, "peak": opk / 1e12, "unit": "TFLOP/s",
+                              "frac": opf / (ot_pf * 1e-3) / opk,
+                              "peak_source": f"measured {'FP64' if oprec == vof.FP64 else 'FP32'} FMA probe",
+                              "work_per_launch": owork, "flops_per_launch": opf}}
         octx.close()
-        del oa, ost
+        del oa, ost, oa_start
 
     # ---- end to end through the C ABI with host buffers (copies in the timed region)
     ha = torch.from_numpy(w.alpha0.copy()).pin_memory()
     hstat = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
-    hF = [Fk[args.skip + args.warmup + j].cpu().pin_memory() for j in range(args.steps)]
-    hU = [Uk[args.skip + args.warmup + j].cpu().pin_memory() for j in range(args.steps)]
+    hF = [F.cpu().pin_memory() for _, F, _ in timed]
+    hU = [U.cpu().pin_memory() for U, _, _ in timed]
     for k in range(args.skip + args.warmup):
         vof.vof_advect_host(ctx.h, ha, Uk[k].cpu(), Fk[k].cpu(), w.dt, hstat)
     torch.cuda.synchronize()
@@ -590,30 +669,38 @@ def main():
     if do_full and rank == 0:
         full = full_run_l1(ctx, w, dev)
 
-    # ---- roofline of the dominant kernel group
+    # ---- roofline of the dominant kernel group, and of the whole step
     pk, pk_src = peaks()
     per_launch = {g: v / max(nprof, 1) for g, v in group_ms.items()}
     dom = max(per_launch, key=per_launch.get)
+    f32, f64, pf = work_flops(work, prec == vof.FP64)
     if dom == "phase_flux":
-        fl = (work["pairs"] * FLOPS_PER_PAIR + work["cuts"] * FLOPS_PER_CUT) / max(nprof, 1)
-        alu = vof.vof_probe_fma(local, prec)
-        achieved = fl / (per_launch[dom] * 1e-3) / 1e12
+        alu = peak64 if prec == vof.FP64 else peak32
+        achieved = pf / (per_launch[dom] * 1e-3) / 1e12
         traffic = captured_traffic(args.workload, m.shape[0], "fp64" if prec == vof.FP64 else "mixed") \
             if args.skip == 0 else None
-        roof = {"kernel": "k_phase_flux", "bound": "alu", "achieved": achieved, "peak": alu / 1e12,
-                "unit": "TFLOP/s", "frac": achieved * 1e12 / alu, "traffic": traffic,
-                "traffic_unit": "bytes per launch (ncu capture)",
+        roof = {"kernel": "k_phase_flux" if prec == vof.FP64 else "k_phase_flux_mixed", "bound": "alu",
+                "achieved": achieved, "peak": alu / 1e12, "unit": "TFLOP/s", "frac": achieved * 1e12 / alu,
+                "traffic": traffic, "traffic_unit": "bytes per launch (ncu capture)",
                 "peak_source": f"measured {'FP64' if prec == vof.FP64 else 'FP32'} FMA probe (vof_probe_fma)",
-                "work_per_launch": {"pairs": work["pairs"] / max(nprof, 1), "cuts": work["cuts"] / max(nprof, 1),
-                                    "band_faces": work["faces"] / max(nprof, 1)}}
+                "work_per_launch": work, "flops_per_launch": pf}
     else:
-        # HBM-bound groups: algorithmic bytes per internal face (72 B: flux, owner and
-        # neighbour, face points, alpha and volume, point data, per face of a hex mesh)
-        byts = 72.0 * m.n_internal
+        # HBM-bound groups: algorithmic bytes per internal face
+        byts = BYTES_PER_FACE * m.n_internal
         achieved = byts / (per_launch[dom] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": None, "peak_source": pk_src}
     roof["group_ms_per_step"] = per_launch
+    # step: T_min = max(bytes / HBM, flops32 / peak32 + flops64 / peak64)
+    byts = BYTES_PER_FACE * m.n_internal
+    t_hbm = byts / (pk["hbm_gbs"] * 1e9) * 1e3
+    t_alu = (f32 / peak32 + f64 / peak64) * 1e3
+    t_min = max(t_hbm, t_alu)
+    step_roof = {"bytes": byts, "flops32": f32, "flops64": f64, "t_hbm_ms": t_hbm, "t_alu_ms": t_alu,
+                 "t_min_ms": t_min, "ms_per_step": ms_max / args.steps, "frac": t_min / (ms_max / args.steps),
+                 "peak32_tflops": peak32 / 1e12, "peak64_tflops": peak64 / 1e12, "hbm_gbs": pk["hbm_gbs"],
+                 "peak_source": f"FP32/FP64: measured FMA probe; HBM: {pk_src}"}
+    band = float(S[:, 7].mean())
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -632,16 +719,24 @@ def main():
                 "data": "synthetic", "config": config(args, w),
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": ms_e2e / args.steps, "host_link_GBps": link},
-                "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "other_form": other,
+                "gpu_launches": launches, "roofline": roof, "step_roofline": step_roof,
+                "band_face_fluxes": {"value": world * band * args.steps / (ms_max * 1e-3) / 1e6, "unit": UNIT,
+                                     "band_faces_per_step": band},
+                "whole_case": None if full is None else {
+                    "value": full["steps"] * m.n_internal / (full["gpu_ms"] * 1e-3) / 1e6, "unit": UNIT,
+                    "ms_per_step": full["gpu_ms"] / full["steps"], "steps": full["steps"]},
+                "cpu_baseline": base, "other_form": other,
                 "learned_guess": guess,
                 "clocks": clk.summary(),
                 "quality": {"max_rel_volume_drift": float(drift), "alpha_min": float(S[:, 4].min()),
                             "alpha_max": float(S[:, 5].max()), "alpha_min_pre_bound": float(S[:, 2].min()),
                             "alpha_max_pre_bound": float(S[:, 3].max()),
-                            "band_faces_per_step": float(S[:, 7].mean()),
+                            "band_faces_per_step": band,
                             "interface_cells_per_step": float(S[:, 6].mean()),
                             "bound_sources_per_step": float(S[:, 12].mean()),
                             "bound_left_after_local": float(S[:, 13].mean()),
+                            "bound_passes_max": float(S[:, 14].max()),
+                            "bound_global_volume": float(S[:, 15].sum()),
                             "status_bits": int(st0 | st1), "full_run": full}}
         print(json.dumps(line), flush=True)
     if world > 1:

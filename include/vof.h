@@ -91,7 +91,10 @@ typedef struct {
 enum {
     VOF_S_MASS_BEFORE = 0, VOF_S_MASS_AFTER, VOF_S_MIN_PRE, VOF_S_MAX_PRE, VOF_S_MIN_POST,
     VOF_S_MAX_POST, VOF_S_N_INTERFACE, VOF_S_N_BAND, VOF_S_MAX_POS_IT, VOF_S_MAX_CORR_IT,
-    VOF_S_BOUNDARY_OUT, VOF_S_N_FALLBACK, VOF_S_N_BOUND_SOURCES, VOF_S_N_BOUND_LEFT /* after the local pass */,
+    VOF_S_BOUNDARY_OUT, VOF_S_N_FALLBACK, VOF_S_N_BOUND_SOURCES,
+    VOF_S_N_BOUND_LEFT,   /* sources left after the local redistribution passes */
+    VOF_S_BOUND_PASSES,   /* local redistribution passes that moved something */
+    VOF_S_BOUND_GLOBAL,   /* volume the global fallback moved after them */
     VOF_S_LEN = 16
 };
 
@@ -115,6 +118,37 @@ void vof_destroy(vof_ctx *ctx);
  * vectors [3*n_faces]. */
 int vof_geometry(vof_ctx *ctx, double *cell_centre, double *cell_vol, double *face_centre,
                  double *face_area, void *stream);
+
+/* Gradient of the reconstruction (Sec. 2.2.1): VOF_GRAD_NAG (the default, the
+ * node-averaged gradient) or VOF_GRAD_LSQ (the generalised least-squares
+ * gradient over the cells sharing a point with each cell, Eq.
+ * generalizedLSQminimize with inverse-distance weights).  Selecting LSQ the
+ * first time builds its stencil (host, then device) and a gradient buffer:
+ * synchronous, allocates.  Later reconstructions (vof_reconstruct,
+ * vof_advect, ...) take the normal -grad/|grad| of the selected gradient.
+ * VOF_ERR_INVALID_ARG for another kind. */
+enum { VOF_GRAD_NAG = 0, VOF_GRAD_LSQ = 1 };
+int vof_set_gradient(vof_ctx *ctx, int kind);
+
+/* The generalised LSQ gradient (Sec. 2.2.1) of alpha for every cell, grad
+ * [3*n_cells] SoA (device).  Builds the LSQ stencil first if no earlier call
+ * did (synchronous then, and allocating). */
+int vof_lsq_gradient(vof_ctx *ctx, const double *alpha, double *grad, void *stream);
+
+/* Reconstruction error of Sec. 4.1 against a ball (ball[0..2] its centre,
+ * ball[3] its radius; host array): per cell the volume of the symmetric
+ * difference between the reconstructed phase (the PLIC polyhedron of an
+ * oriented interface cell, the whole cell for a full one, nothing for any
+ * other; flags, n [3*n_cells], d [n_cells] as vof_reconstruct writes them) and
+ * the ball, E_vsd = E_vsd^- + E_vsd^+, into evsd [n_cells] (device).  The ball
+ * is resolved like the paper's tool mesh: each cell tetrahedron split into
+ * eight, `levels` times (0..6), pieces wholly in or out of the ball kept
+ * whole, the undecided ones of the last level cut by the sphere's tangent
+ * plane at the point nearest their centroid.  With flags NULL it gives the
+ * ball's volume in each cell (exact volume fractions of that description).
+ * VOF_ERR_INVALID_ARG for levels outside 0..6 or R <= 0. */
+int vof_evsd(vof_ctx *ctx, const uint8_t *flags, const double *n, const double *d, const double ball[4],
+             int levels, double *evsd, void *stream);
 
 /* A4, Eq. idwpointphi: point velocity Up [3*n_points] from the cell velocity
  * Uc [3*n_cells] by inverse-distance weighting over the point's cells; at a
@@ -295,11 +329,33 @@ enum { VOF_PROF_GROUPS = 5 };
 int vof_profile_begin(vof_ctx *ctx, int max_steps);
 int vof_profile_end(vof_ctx *ctx, double *group_ms, int *steps);
 
-/* Algorithmic work counted by the phase-flux kernel since the last reset:
- * counts[0] (tetrahedron, cell-tetrahedron) pairs whose bounding boxes overlap,
- * counts[1] plane cuts that split a tetrahedron, counts[2] band faces.  Reading
- * synchronises `stream`; reset zeroes the counters. */
-int vof_work_counts(vof_ctx *ctx, unsigned long long counts[3], int reset, void *stream);
+/* Algorithmic work counted by the step kernels since the last reset, as
+ * counts of primitives (a measurement helper; the paper gives no costs):
+ *  [0] prism-plane distance sets (six signed point-plane distances: the flux
+ *      polyhedron prism of one face triangle against one plane of a cell
+ *      tetrahedron or a PLIC plane),
+ *  [1] piece-plane tests (four signed distances),
+ *  [2] edge intersections,
+ *  [3] tetrahedron volumes,
+ *  [4] closed-form cut fractions of a tetrahedron below a plane,
+ *  [5] plane shifts into a face's frame (one dot product each),
+ *  [6] band faces fluxed geometrically,
+ *  [7] FP64 fill evaluations of the positioning, per cell tetrahedron,
+ *  [8] FP32 fill evaluations of the positioning, per cell tetrahedron,
+ *  [9] face triangles whose swept prism enters the correction's cubic,
+ *  [10] cubic evaluations of the correction,
+ *  [11] reserved (0).
+ * [0]-[5] are FP32 work in a VOF_MIXED context and FP64 in a VOF_FP64 one;
+ * [7], [9], [10] are FP64.  Reading synchronises `stream`; reset zeroes the
+ * counters. */
+enum { VOF_WORK_LEN = 12 };
+/* Work counting on (1) or off (0, the default): while on, later steps run
+ * instrumented variants of the reconstruction, correction and phase-flux
+ * kernels that add to the counters read by vof_work_counts; while off, the
+ * uninstrumented ones run and the counters stay as they are.  A host-side
+ * setting, effective for calls made after it. */
+int vof_count_work(vof_ctx *ctx, int on);
+int vof_work_counts(vof_ctx *ctx, unsigned long long counts[VOF_WORK_LEN], int reset, void *stream);
 
 /* Measurement helper with no counterpart in the paper: sustained fused
  * multiply-add rate (FLOP/s, 2 per FMA) of the plain FP64 (VOF_FP64) or FP32

@@ -54,6 +54,9 @@ def lib():
             "vo_cut_volume": (D, [P, I, P, D]),
             "vo_reconstruct": (I, [P, P, D, I, P, P, P, P, P]),
             "vo_position": (I, [P, I, D, P, P]),
+            "vo_reconstruct_grad": (I, [P, P, P, D, I, P, P, P, P, P]),
+            "vo_lsq_gradient": (V, [P, P, I, P, P]),
+            "vo_evsd": (V, [P, P, P, P, P, I, I, P, P]),
             "vo_point_velocity": (V, [P, P, P]),
             "vo_swept_volume": (D, [P, I, P, D, D, D]),
             "vo_correct_flux": (I, [P, P, P, D, I, P, P, P]),
@@ -168,6 +171,34 @@ class OracleMesh:
         st = lib().vo_reconstruct(self.h, _p(alpha), eps, 0 if s is None else s.size, _p(s),
                                   _p(n), _p(d), _p(fl), _p(it))
         return n.reshape(3, -1), d, fl, it, st
+
+    def lsq_gradient(self, phi, sel=None):
+        """Generalised least-squares gradient (Sec. 2.2.1), (3, nc)."""
+        phi = _f64(phi); g = np.zeros(3 * self.nc)
+        s = None if sel is None else _i32(sel)
+        lib().vo_lsq_gradient(self.h, _p(phi), 0 if s is None else s.size, _p(s), _p(g))
+        return g.reshape(3, -1)
+
+    def reconstruct_grad(self, alpha, grad, eps=EPS, sel=None):
+        """Reconstruction with the normal of a given gradient (3, nc)."""
+        alpha = _f64(alpha); grad = _f64(grad).reshape(-1)
+        n = np.zeros(3 * self.nc); d = np.zeros(self.nc)
+        fl = np.zeros(self.nc, np.uint8); it = np.zeros(self.nc, np.int32)
+        s = None if sel is None else _i32(sel)
+        st = lib().vo_reconstruct_grad(self.h, _p(alpha), _p(grad), eps, 0 if s is None else s.size, _p(s),
+                                       _p(n), _p(d), _p(fl), _p(it))
+        return n.reshape(3, -1), d, fl, it, st
+
+    def evsd(self, flags, n, d, ball, levels, sel=None):
+        """E_vsd (Sec. 4.1) per cell against a ball (cx, cy, cz, R); flags None:
+        the ball's volume in each cell."""
+        fl = None if flags is None else np.ascontiguousarray(flags, np.uint8)
+        n = None if n is None else _f64(n).reshape(-1)
+        d = None if d is None else _f64(d)
+        b = _f64(ball); out = np.zeros(self.nc)
+        s = None if sel is None else _i32(sel)
+        lib().vo_evsd(self.h, _p(fl), _p(n), _p(d), _p(b), int(levels), 0 if s is None else s.size, _p(s), _p(out))
+        return out
 
     # A4/A5 -----------------------------------------------------------------
     def point_velocity(self, Uc):

@@ -586,6 +586,13 @@ int vo_position(const vo_mesh *m, int c, double alpha, const double nn[3], doubl
 int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel, const int *sel,
                    double *nout, double *dout, unsigned char *flags, int *iters)
 {
+    return vo_reconstruct_grad(m, alpha, NULL, eps, n_sel, sel, nout, dout, flags, iters);
+}
+
+/* as vo_reconstruct, the normal from a given gradient (3*nc SoA; NULL: NAG) */
+int vo_reconstruct_grad(const vo_mesh *m, const double *alpha, const double *grad, double eps, int n_sel,
+                        const int *sel, double *nout, double *dout, unsigned char *flags, int *iters)
+{
     int k, nn = sel ? n_sel : m->nc, st = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(| : st)
     for (k = 0; k < nn; k++) {
@@ -595,7 +602,7 @@ int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel,
         v3 n = mk(0, 0, 0);
         if (a >= 1.0 - eps) fl = VO_FULL;
         else if (a > eps) {
-            v3 g = nag_gradient_cell(m, c, alpha);
+            v3 g = grad ? mk(grad[c], grad[m->nc + c], grad[2 * m->nc + c]) : nag_gradient_cell(m, c, alpha);
             double gm = norm(g), hc = cbrt(m->vc[c]);
             fl = VO_INTERFACE;
             /* R4: a vanishing gradient leaves the cell unoriented */
@@ -612,6 +619,149 @@ int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel,
         if (iters) iters[c] = it;
     }
     return st;
+}
+
+/* ------------------------------ generalised LSQ gradient (Sec. 2.2.1) */
+/* The cell's stencil: every other cell that shares a point with it. */
+static int point_nbrs(const vo_mesh *m, int c, int *out, int cap)
+{
+    int k = 0, i, j, u = 0;
+    int buf[4096];
+    for (i = m->cpptr[c]; i < m->cpptr[c + 1]; i++) {
+        int p = m->cpt[i];
+        for (j = m->pptr[p]; j < m->pptr[p + 1]; j++)
+            if (m->pcell[j] != c && k < 4096) buf[k++] = m->pcell[j];
+    }
+    qsort(buf, (size_t)k, sizeof(int), cmp_int);
+    for (i = 0; i < k; i++)
+        if (i == 0 || buf[i] != buf[i - 1]) {
+            if (u < cap) out[u] = buf[i];
+            u++;
+        }
+    return u;
+}
+
+/* The gradient minimising E_c = sum_k w_ck^2 E_ck^2 (Eq. generalizedLSQminimize),
+ * E_ck = -(phi_c - phi_k) + grad.(x_c - x_k), w_ck the inverse distance of the
+ * two cell centres: the normal equations (sum w^2 d d^T) g = sum w^2 d (phi_k -
+ * phi_c), d = x_k - x_c, solved by Cramer's rule (g = 0 for a singular system). */
+static v3 lsq_gradient_cell(const vo_mesh *m, int c, const double *phi)
+{
+    int nb[1024], k, nk = point_nbrs(m, c, nb, 1024);
+    double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0}, det, x[3];
+    int i, j, col;
+    for (k = 0; k < nk && k < 1024; k++) {
+        v3 d = sub(m->cc[nb[k]], m->cc[c]);
+        double dv[3] = {d.x, d.y, d.z}, w2 = 1.0 / dot(d, d), dphi = phi[nb[k]] - phi[c];
+        for (i = 0; i < 3; i++) {
+            b[i] += w2 * dv[i] * dphi;
+            for (j = 0; j < 3; j++) A[i][j] += w2 * dv[i] * dv[j];
+        }
+    }
+    det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+          A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (det == 0.0) return mk(0, 0, 0);
+    for (col = 0; col < 3; col++) { /* replace column col by b */
+        double M[3][3];
+        for (i = 0; i < 3; i++)
+            for (j = 0; j < 3; j++) M[i][j] = j == col ? b[i] : A[i][j];
+        x[col] = (M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+                  M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0])) / det;
+    }
+    return mk(x[0], x[1], x[2]);
+}
+
+void vo_lsq_gradient(const vo_mesh *m, const double *phi, int n_sel, const int *sel, double *grad)
+{
+    int k, nn = sel ? n_sel : m->nc;
+#pragma omp parallel for schedule(dynamic, 256)
+    for (k = 0; k < nn; k++) {
+        int c = sel ? sel[k] : k;
+        v3 g = lsq_gradient_cell(m, c, phi);
+        grad[c] = g.x; grad[m->nc + c] = g.y; grad[2 * m->nc + c] = g.z;
+    }
+}
+
+/* ---------------------- reconstruction error E_vsd (Sec. 4.1, Eqs. E_vsd) */
+/* The true phase is a ball B (centre bc, radius R), described the way the
+ * paper's tool mesh describes a geometry: every cell tetrahedron is split
+ * into eight (edge midpoints; the inner octahedron about the diagonal joining
+ * the midpoints of edges ab and cd) down to `levels`, where a piece is taken
+ * as wholly in B (all four vertices in the closed ball), wholly outside (its
+ * centroid's distance to bc less its largest vertex distance to the centroid
+ * is at least R), or, still undecided at the last level, cut by the plane
+ * tangent to the sphere at the point nearest its centroid.  With P the true
+ * phase in a piece S and H the cell's reconstructed phase (PLIC half-space of
+ * an oriented interface cell, all of S for a full cell, none for any other),
+ * the piece contributes |P \ H| + |(S ^ H) \ P| = |P| + |S ^ H| - 2 |P ^ H|:
+ * E_vsd^- and E_vsd^+ of the paper summed.  With no H this is |P|, so the
+ * same routine gives the ball's volume in the cell. */
+static double d2(v3 a, v3 b) { v3 t = sub(a, b); return dot(t, t); }
+
+static double tet_abs(v3 a, v3 b, v3 c, v3 d) { return fabs(tetvol(a, b, c, d)); }
+
+static double evsd_piece(v3 a, v3 b, v3 c, v3 d, int level, int levels, v3 bc, double R, int hmode, v3 hn,
+                         double hd)
+{
+    double R2 = R * R, S, SH, P, PH;
+    v3 g = scl(add(add(a, b), add(c, d)), 0.25);
+    double rt = sqrt(d2(a, g)), dist;
+    int inside = d2(a, bc) <= R2 && d2(b, bc) <= R2 && d2(c, bc) <= R2 && d2(d, bc) <= R2;
+    if (sqrt(d2(b, g)) > rt) rt = sqrt(d2(b, g));
+    if (sqrt(d2(c, g)) > rt) rt = sqrt(d2(c, g));
+    if (sqrt(d2(d, g)) > rt) rt = sqrt(d2(d, g));
+    dist = sqrt(d2(g, bc));
+    S = tet_abs(a, b, c, d);
+    SH = hmode == 0 ? 0.0 : hmode == 1 ? S : tet_clip(a, b, c, d, 1, &hn, &hd, NULL);
+    if (inside) return S + SH - 2.0 * SH;
+    if (dist - rt >= R) return SH;
+    if (level < levels) {
+        v3 ab = scl(add(a, b), 0.5), ac = scl(add(a, c), 0.5), ad = scl(add(a, d), 0.5);
+        v3 bcm = scl(add(b, c), 0.5), bd = scl(add(b, d), 0.5), cd = scl(add(c, d), 0.5);
+        int l = level + 1;
+        return evsd_piece(a, ab, ac, ad, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(b, ab, bcm, bd, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(c, ac, bcm, cd, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(d, ad, bd, cd, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(ab, cd, ac, ad, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(ab, cd, ad, bd, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(ab, cd, bd, bcm, l, levels, bc, R, hmode, hn, hd) +
+               evsd_piece(ab, cd, bcm, ac, l, levels, bc, R, hmode, hn, hd);
+    }
+    {
+        v3 pn[2], u = dist > 0.0 ? scl(sub(g, bc), 1.0 / dist) : mk(1, 0, 0);
+        double pd[2];
+        pn[0] = u; pd[0] = dot(u, bc) + R;
+        P = tet_clip(a, b, c, d, 1, pn, pd, NULL);
+        if (hmode == 0) PH = 0.0;
+        else if (hmode == 1) PH = P;
+        else { pn[1] = hn; pd[1] = hd; PH = tet_clip(a, b, c, d, 2, pn, pd, NULL); }
+        return P + SH - 2.0 * PH;
+    }
+}
+
+void vo_evsd(const vo_mesh *m, const unsigned char *flags, const double *n, const double *d,
+             const double ball[4], int levels, int n_sel, const int *sel, double *out)
+{
+    int k, nn = sel ? n_sel : m->nc;
+    v3 bc = mk(ball[0], ball[1], ball[2]);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (k = 0; k < nn; k++) {
+        int c = sel ? sel[k] : k, nk, t, hmode = 0;
+        v3 K[MAXK][4], hn = mk(0, 0, 0);
+        double hd = 0.0, e = 0.0;
+        if (flags) {
+            if (flags[c] & VO_FULL) hmode = 1;
+            else if ((flags[c] & VO_INTERFACE) && (flags[c] & VO_ORIENTED)) {
+                hmode = 2;
+                hn = mk(n[c], n[m->nc + c], n[2 * m->nc + c]);
+                hd = d[c];
+            }
+        }
+        nk = cell_tets(m, c, K, MAXK);
+        for (t = 0; t < nk; t++) e += evsd_piece(K[t][0], K[t][1], K[t][2], K[t][3], 0, levels, bc, ball[3], hmode, hn, hd);
+        out[c] = e;
+    }
 }
 
 /* ------------------------------------------- A4: point velocity + sweep */

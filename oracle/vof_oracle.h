@@ -72,6 +72,18 @@ int vo_position(const vo_mesh *m, int cell, double alpha, const double n[3], dou
 int vo_reconstruct(const vo_mesh *m, const double *alpha, double eps, int n_sel,
                    const int *sel, double *n, double *d, unsigned char *flags, int *iters);
 
+/* Alg. 1 with the normal -grad/|grad| of a given gradient (3*nc SoA; NULL: NAG) */
+int vo_reconstruct_grad(const vo_mesh *m, const double *alpha, const double *grad, double eps, int n_sel,
+                        const int *sel, double *n, double *d, unsigned char *flags, int *iters);
+/* generalised least-squares gradient (Sec. 2.2.1, Eq. generalizedLSQminimize)
+ * over the cells sharing a point with each selected cell */
+void vo_lsq_gradient(const vo_mesh *m, const double *phi, int n_sel, const int *sel, double *grad);
+/* reconstruction error E_vsd (Sec. 4.1) per selected cell against the ball
+ * ball[0..2] centre, ball[3] radius, resolved to `levels` splits of the cell
+ * tetrahedra; flags NULL: no reconstruction (gives |C ^ ball|) */
+void vo_evsd(const vo_mesh *m, const unsigned char *flags, const double *n, const double *d,
+             const double ball[4], int levels, int n_sel, const int *sel, double *out);
+
 /* Eq. idwpointphi applied to the cell velocity (3*nc SoA) -> point velocity; at
  * wall points only the component tangent to the walls is kept */
 void vo_point_velocity(const vo_mesh *m, const double *Uc, double *Up);

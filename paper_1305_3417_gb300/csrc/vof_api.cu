@@ -375,7 +375,6 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->band = dev_alloc<int>(c, nf, &err);
     c->icell = dev_alloc<int>(c, nc, &err);
     c->viol[0] = dev_alloc<int>(c, nc, &err);
-    c->viol[1] = dev_alloc<int>(c, nc, &err);
     c->pend_c = dev_alloc<int>(c, 8 * (size_t)nc, &err);
     c->pend_a = dev_alloc<double>(c, 8 * (size_t)nc, &err);
     c->counters = dev_alloc<int>(c, CNT_ALLOC, &err);
@@ -387,8 +386,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->flags = dev_alloc<uint8_t>(c, nc, &err);
     c->pit = dev_alloc<int>(c, nc, &err);
     c->Va = dev_alloc<double>(c, nf, &err);
-    c->bscr = dev_alloc<double>(c, 8 * (size_t)nc, &err);
-    c->dgi = dev_alloc<int>(c, nc, &err);
+    c->bscr = dev_alloc<double>(c, 4 * (size_t)nc, &err);
     c->partial = dev_alloc<double>(c, 10 * 1024, &err);
     c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
     c->status = dev_alloc<unsigned>(c, 1, &err);
@@ -397,7 +395,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         c->h_Uc[i] = dev_alloc<double>(c, 3 * (size_t)nc, &err);
         c->h_F[i] = dev_alloc<double>(c, nf, &err);
     }
-    c->work = dev_alloc<unsigned long long>(c, 4, &err);
+    c->work = dev_alloc<unsigned long long>(c, WK_LEN, &err);
     c->cfpptr = dev_copy(c, cfpptr.data(), cfpptr.size(), &err);
     c->cfl = dev_alloc<float4>(c, cface.size(), &err);
     c->cfpl = dev_alloc<float4>(c, cfpptr[nc], &err);
@@ -408,9 +406,8 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->upb = dev_alloc<double>(c, 3 * (size_t)np, &err);
     if (c->precision == VOF_MIXED) c->ktl = dev_alloc<float4>(c, 6 * (size_t)ctptr[nc], &err);
     if (err) { vof_destroy(c); return err; }
-    cudaMemset(c->work, 0, 4 * sizeof(unsigned long long));
-    cudaMemset(c->bscr, 0, sizeof(double) * 8 * nc);
-    cudaMemset(c->dgi, 0, sizeof(int) * nc);
+    cudaMemset(c->work, 0, WK_LEN * sizeof(unsigned long long));
+    cudaMemset(c->bscr, 0, sizeof(double) * 4 * nc);
     cudaMemset(c->counters, 0, sizeof(int) * CNT_ALLOC);
     cudaMemset(c->status, 0, sizeof(unsigned));
     cudaMemset(c->n, 0, sizeof(double) * 3 * nc);
@@ -466,6 +463,85 @@ int vof_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8
     if (!c || !alpha || !n || !d || !flags) return VOF_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     return launch_reconstruct(c, alpha, n, d, flags, iters, nullptr, nullptr, (cudaStream_t)stream);
+}
+
+// the LSQ stencil: every other cell sharing a point with each cell (host, from
+// the device copies of cell->point and point->cell), and the gradient buffer
+static int build_lsq(vof_ctx *c)
+{
+    if (c->lptr) return VOF_OK;
+    const int nc = c->nc, np = c->np;
+    std::vector<int> cpptr(nc + 1), pptr(np + 1);
+    if (cudaMemcpy(cpptr.data(), c->m.cpptr, sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pptr.data(), c->m.pptr, sizeof(int) * (np + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return VOF_ERR_CUDA;
+    std::vector<int> cpts(cpptr[nc]), pcell(pptr[np]);
+    if (cudaMemcpy(cpts.data(), c->m.cpts, sizeof(int) * cpts.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pcell.data(), c->m.pcell, sizeof(int) * pcell.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return VOF_ERR_CUDA;
+    std::vector<long> off(nc + 1, 0);
+    for (int x = 0; x < nc; ++x) {
+        long k = 0;
+        for (int i = cpptr[x]; i < cpptr[x + 1]; ++i) k += pptr[cpts[i] + 1] - pptr[cpts[i]];
+        off[x + 1] = off[x] + k;
+    }
+    std::vector<int> tmp(off[nc]), cnt(nc);
+    parallel_for(nc, [&](long x) {
+        long o = off[x];
+        int k = 0;
+        for (int i = cpptr[x]; i < cpptr[x + 1]; ++i)
+            for (int q = pptr[cpts[i]]; q < pptr[cpts[i] + 1]; ++q)
+                if (pcell[q] != x) tmp[o + k++] = pcell[q];
+        std::sort(tmp.begin() + o, tmp.begin() + o + k);
+        cnt[x] = (int)(std::unique(tmp.begin() + o, tmp.begin() + o + k) - (tmp.begin() + o));
+    });
+    std::vector<int> lptr(nc + 1, 0);
+    for (int x = 0; x < nc; ++x) {
+        if ((long)lptr[x] + cnt[x] > 0x7fffffffL) return VOF_ERR_INVALID_ARG;
+        lptr[x + 1] = lptr[x] + cnt[x];
+    }
+    std::vector<int> lcell(lptr[nc]);
+    parallel_for(nc, [&](long x) { std::copy(tmp.begin() + off[x], tmp.begin() + off[x] + cnt[x], lcell.begin() + lptr[x]); });
+    int err = 0;
+    int *dp = dev_copy(c, lptr.data(), lptr.size(), &err);
+    int *dc = dev_copy(c, lcell.data(), lcell.size(), &err);
+    double *g = dev_alloc<double>(c, 3 * (size_t)nc, &err);
+    if (err) return err;
+    c->lptr = dp;
+    c->lcell = dc;
+    c->grad = g;
+    return VOF_OK;
+}
+
+int vof_set_gradient(vof_ctx *c, int kind)
+{
+    if (!c || (kind != VOF_GRAD_NAG && kind != VOF_GRAD_LSQ)) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    if (kind == VOF_GRAD_LSQ) {
+        int r = build_lsq(c);
+        if (r) return r;
+    }
+    c->grad_kind = kind;
+    return VOF_OK;
+}
+
+int vof_lsq_gradient(vof_ctx *c, const double *alpha, double *grad, void *stream)
+{
+    if (!c || !alpha || !grad) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    int r = build_lsq(c);
+    if (r) return r;
+    return launch_lsq_gradient(c, alpha, nullptr, nullptr, grad, (cudaStream_t)stream);
+}
+
+int vof_evsd(vof_ctx *c, const uint8_t *flags, const double *n, const double *d, const double ball[4], int levels,
+             double *evsd, void *stream)
+{
+    if (!c || !ball || !evsd || (flags && (!n || !d))) return VOF_ERR_INVALID_ARG;
+    if (!(ball[3] > 0.0) || !std::isfinite(ball[0]) || !std::isfinite(ball[1]) || !std::isfinite(ball[2]))
+        return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_evsd(c, flags, n, d, ball, levels, evsd, (cudaStream_t)stream);
 }
 
 int vof_flux_polyhedra(vof_ctx *c, const double *Up, const double *F, const double *lambda, double dt,
@@ -608,16 +684,24 @@ int vof_probe_barrier(vof_ctx *c, int skip_block, void *stream)
     return launch_barrier_probe(c, skip_block, (cudaStream_t)stream);
 }
 
-int vof_work_counts(vof_ctx *c, unsigned long long counts[3], int reset, void *stream)
+int vof_count_work(vof_ctx *c, int on)
 {
+    if (!c) return VOF_ERR_INVALID_ARG;
+    c->work_on = on ? 1 : 0;
+    return VOF_OK;
+}
+
+int vof_work_counts(vof_ctx *c, unsigned long long counts[VOF_WORK_LEN], int reset, void *stream)
+{
+    static_assert(VOF_WORK_LEN == WK_LEN, "work counter layout");
     if (!c || !counts) return VOF_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    unsigned long long v[4] = {0, 0, 0, 0};
+    unsigned long long v[WK_LEN] = {};
     if (cudaMemcpyAsync(v, c->work, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess) return VOF_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return VOF_ERR_CUDA;
     if (reset && cudaMemsetAsync(c->work, 0, sizeof(v), s) != cudaSuccess) return VOF_ERR_CUDA;
-    counts[0] = v[0]; counts[1] = v[1]; counts[2] = v[2];
+    for (int i = 0; i < WK_LEN; ++i) counts[i] = v[i];
     return VOF_OK;
 }
 

@@ -14,15 +14,52 @@ namespace vofd {
 
 constexpr int POS_MAXIT = 100;
 constexpr double POS_TOL = 1e-13;
+// Alg. 1's secant is taken as divergent after this many steps without meeting
+// POS_TOL (a stall deep in the cubic corner of the fill near alpha = 0 or 1;
+// a converging secant needs about a dozen): bisection from then on
+constexpr int POS_SECANT_MAX = 20;
 constexpr int CORR_MAXIT = 100;
 constexpr double CORR_TOL = 1e-14;
 constexpr double CORR_LMAX = 2.0;
 constexpr int CORR_NSAMP = 16;
 constexpr double BOUND_TOL = 1e-13;
 constexpr double BOUND_FLAG = 1e-12;
-constexpr int BOUND_PASSES = 1;  // local passes before the global step
+// local redistribution passes run until no source has both something left
+// and a receiver with room; this caps them (each pass finishes a source or
+// fills at least one of its receivers)
+constexpr int BOUND_PASSES_MAX = 32;
 constexpr int CLIP_STACK = 12;
 constexpr int DISP_STRIDE = (VOF_MAXFP + 1) * 3;
+
+// Per-lane phase-flux work counters of the instrumented kernel variants
+// (WkOn; WkOff compiles to nothing), added to the context's counters at a
+// warp's end: one atomic per counter and warp
+struct WkOn {
+    unsigned v[WK_N] = {};
+    unsigned faces = 0;
+    __device__ __forceinline__ void add(int i, unsigned x) { v[i] += x; }
+    __device__ __forceinline__ void face() { ++faces; }
+    __device__ __forceinline__ void flush(unsigned long long *work, int lane)
+    {
+        if (!work) return;
+#pragma unroll
+        for (int i = 0; i < WK_N; ++i) {
+            const unsigned r = __reduce_add_sync(0xffffffffu, v[i]);
+            if (lane == 0 && r) atomicAdd(work + i, (unsigned long long)r);
+        }
+        if (lane == 0 && faces) atomicAdd(work + WK_FACES, (unsigned long long)faces);
+    }
+};
+struct WkOff {
+    __device__ __forceinline__ void add(int, unsigned) {}
+    __device__ __forceinline__ void face() {}
+    __device__ __forceinline__ void flush(unsigned long long *, int) {}
+};
+// one lane's count added to counter i (a few per thread)
+__device__ __forceinline__ void work_add1(unsigned long long *work, int i, unsigned long long v)
+{
+    if (work && v) atomicAdd(work + i, v);
+}
 
 // ------------------------------------------------------------------ vectors
 struct V3 { double x, y, z; };

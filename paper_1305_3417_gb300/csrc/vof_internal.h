@@ -42,8 +42,17 @@ struct DevMesh {
 // the context's counter buffer: per-step counters (the first CNT_LEN ints),
 // then the two words of the grid barrier, each on its own 128-byte line
 enum { CNT_BAND = 0, CNT_ICELL, CNT_MAXPOS, CNT_MAXCORR, CNT_FALLBACK, CNT_VIOL0, CNT_VIOL1, CNT_PEND, CNT_PFNEXT,
-       CNT_RCNEXT, CNT_LEN = 16 };
+       CNT_RCNEXT, CNT_BPASS, CNT_BACT0, CNT_BACT1, CNT_LEN = 16 };
 enum { CNT_BAR = 32, CNT_BARGEN = 64, CNT_ALLOC = 96 };
+// algorithmic work counted by the step kernels (vof_work_counts): the phase
+// flux's primitives (FP32 in the mixed form, FP64 in the plain one) -- signed
+// distances of a prism's six points to a plane, of a piece's four points to a
+// plane, edge intersections, tetrahedron volumes, closed-form cut fractions,
+// plane shifts to the face frame -- and band faces; the reconstruction's fill
+// evaluations per cell tetrahedron (FP64, FP32); the correction's cubic
+// coefficient triangles and cubic evaluations (FP64)
+enum { WK_PRISM = 0, WK_TEST, WK_EDGE, WK_VOL, WK_FRAC, WK_SHIFT, WK_N, WK_FACES = WK_N, WK_FILL64, WK_FILL32,
+       WK_CTRI, WK_CEVAL, WK_LEN = 12 };
 
 struct vof_ctx {
     int device;
@@ -65,8 +74,7 @@ struct vof_ctx {
     uint8_t *flags;
     int *pit;
     double *Va;
-    double *bscr;                // bounding scratch, 8 doubles per cell
-    int *dgi;
+    double *bscr;                // redistribution scratch, 4 doubles per cell
     double *gpartial;            // global bounding partial sums, 4 per segment
     // regions of the global bounding step (whole mesh, or the cases of a
     // batch): segments {region, first cell, end cell, -} and, per region, its
@@ -86,7 +94,8 @@ struct vof_ctx {
     cudaStream_t s_aux;            // the correction runs here, beside the reconstruction
     cudaEvent_t ev_fork, ev_join;
     int launches;
-    unsigned long long *work;    // [3] phase-flux work counters
+    unsigned long long *work;    // WK_LEN work counters
+    int work_on;                 // 1: the step kernels count their work (instrumented variants)
     // FP32 geometry for the mixed kernels
     float4 *cfl, *cfpl, *fpl, *cbl;
     int *cfpptr;
@@ -101,6 +110,12 @@ struct vof_ctx {
     int pf_warps, pf_mult;
     int rc_g;                    // reconstruction lanes per cell: 8 if every cell has <= 16 tetrahedra, else 32
     int rc_k;                    // tetrahedra per lane: 3 where some cell has more than 64, else 2
+    // gradient of the reconstruction (vof_set_gradient): VOF_GRAD_NAG or
+    // VOF_GRAD_LSQ; the LSQ stencil (cells sharing a point with each cell, CSR)
+    // and the gradient buffer are made at the first selection of LSQ
+    int grad_kind;
+    int *lptr, *lcell;
+    double *grad;
     // learned guess of the positioning (vof_set_guess): the network, offsets by
     // interface-list position, features
     struct vof_mlp *mlp;
@@ -114,6 +129,10 @@ struct vof_ctx {
 };
 
 // ---- launchers (vof_kernels.cu) ----
+int launch_lsq_gradient(vof_ctx *c, const double *alpha, const int *list, const int *count, double *grad,
+                        cudaStream_t s);
+int launch_evsd(vof_ctx *c, const uint8_t *flags, const double *n, const double *d, const double ball[4],
+                int levels, double *out, cudaStream_t s);
 int launch_setup_geometry(vof_ctx *c, cudaStream_t s);
 int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t s);
 int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8_t *flags,

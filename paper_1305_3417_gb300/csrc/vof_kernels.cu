@@ -197,18 +197,23 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // Newton steps on the fill, whose derivative is the cut area: first in FP32
 // on projections relative to the cell centre while the residual is above 1e-5
 // (FP32 rounding of the fill is ~1e-7), then in FP64 to the 1e-13 stop; a
-// step that leaves the bracket is replaced by bisection.  Other cells, and
-// the plain FP64 form, follow Alg. 1 (secant, bisection once the secant
-// leaves the bracket).
+// step that leaves the bracket is replaced by bisection.  Cells within 1e-4
+// of 0 or 1 take FP64 Newton from the corner estimate.  The plain FP64 form
+// follows Alg. 1 (secant; bisection once the secant leaves the bracket or
+// has not converged in POS_SECANT_MAX steps).
 // G lanes per cell: 32, or 8 where every cell has at most 16 tetrahedra (a
 // tetrahedral mesh: four cells per warp); reductions over the cell's lanes
-template <bool LIST, bool MIXED, int G, int KL>
+template <bool LIST, bool MIXED, int G, int KL, bool COUNT>
 __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
                                                      uint8_t *fout, int *itout, int *maxit, unsigned *status,
-                                                     const float *__restrict__ s0, int s0cap, int *next)
+                                                     const float *__restrict__ s0, int s0cap, int *next,
+                                                     unsigned long long *work, const double *__restrict__ gin)
 {
+    // fill evaluations per cell tetrahedron (FP64, FP32), counted by the
+    // cell's first lane and added once per thread at the end
+    unsigned long long nf64 = 0, nf32 = 0;
     const int lane = threadIdx.x & (G - 1);
     const unsigned tm = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << (threadIdx.x & 31 & ~(G - 1));
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
@@ -250,7 +255,11 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
             fl = VOF_INTERFACE;
             const double V = m.vc[c];
             // ---- NAG gradient: lane j handles the j-th (face, point) entry
+            // (a given gradient instead, times V: the generalised LSQ one)
             V3 g = mk(0, 0, 0);
+            if (gin) {
+                if (lane == 0) g = ld3(gin, m.nc, c) * V;
+            } else
             for (int j = __ldg(m.ceptr + c) + lane, e1 = __ldg(m.ceptr + c + 1); j < e1; j += G) {
                 const int2 en = __ldg(m.cent + j);  // {fpts slot, face code}
                 const int f = en.y >> 1, p = __ldg(m.fpts + en.x);
@@ -306,6 +315,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                 }
                 const double dmin = tmin(lo), dmax = tmax(hi);
                 double x = 0.0;
+                int it32 = 0;
                 if (MIXED && a > 1e-4 && a < 1.0 - 1e-4) {
                     // ---- FP32 Newton, relative to the cell centre's projection
                     const float Vf = (float)V, af = (float)a, rVf = __frcp_rn(Vf);
@@ -344,6 +354,7 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                         if (!sure && ++near >= 2) break;
                     }
                     // ---- FP64 Newton from there
+                    it32 = it;
                     const double rV = 1.0 / V;
                     double A = href + (double)Ar, B = href + (double)Br;
                     x = href + (double)xr;
@@ -399,10 +410,12 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                         x = xn;
                     }
                 } else {
-                    // ---- Alg. 1: secant, bisection once the secant leaves the bracket
+                    // ---- Alg. 1: secant, bisection once the secant leaves the
+                    // bracket or has stalled for POS_SECANT_MAX steps
                     double A = dmin, B = dmax, x0 = A, g0 = -a, x1 = B, g1 = 1.0 - a, gx = 0.0;
                     bool bisect = false;
                     while (it < POS_MAXIT) {
+                        if (it >= POS_SECANT_MAX) bisect = true;
                         if (!bisect) {
                             x = x1 - g1 * (x1 - x0) / (g1 - g0);
                             if (!(x > A && x < B)) bisect = true;
@@ -421,6 +434,11 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
                     }
                 }
                 if (it >= POS_MAXIT && lane == 0) atomicOr(status, VOF_ST_POS_NOT_CONVERGED);
+                if (COUNT && lane == 0) {
+                    const unsigned nte = __ldg(m.ctptr + c + 1) - __ldg(m.ctptr + c);
+                    nf32 += (unsigned long long)it32 * nte;
+                    nf64 += (unsigned long long)(it - it32) * nte;
+                }
                 dd = x;
             }
         }
@@ -431,6 +449,13 @@ __global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double 
             if (itout) itout[c] = it;
             if (maxit && it > 0) atomicMax(maxit, it);
         }
+    }
+    if (!COUNT) return;
+    const unsigned r64 = __reduce_add_sync(0xffffffffu, (unsigned)nf64);
+    const unsigned r32 = __reduce_add_sync(0xffffffffu, (unsigned)nf32);
+    if ((threadIdx.x & 31) == 0) {
+        work_add1(work, WK_FILL64, r64);
+        work_add1(work, WK_FILL32, r32);
     }
 }
 
@@ -523,7 +548,7 @@ __device__ __forceinline__ double cubic_at(const Cubic &q, double x) { return ((
 // else from the FP64 one: the same signs, so the same bracket, as FP64
 // throughout.  The bracket's end values are FP64.  The Newton step divides by
 // the slope through an FP32 reciprocal (the slope sets the rate, not the root).
-__device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &its)
+__device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &its, unsigned &nev)
 {
     its = 0;
     if (tau == 0.0) return 0.0;
@@ -546,6 +571,7 @@ __device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &i
             pos = r32 > 0.0f;
         } else {
             rk = cubic_at(q, k * STEP) - tau;
+            ++nev;
             if (rk == 0.0) return k * STEP;
             pos = rk > 0.0;
         }
@@ -560,14 +586,17 @@ __device__ double solve_lambda(const Cubic &q, double tau, double noise2, int &i
     if (khi == 0) return -1.0;
     double lo = klo * STEP, hi = khi * STEP;
     double rlo = klo == 0 ? -tau : cubic_at(q, lo) - tau;
+    nev += klo != 0;
     if (!have_rhi) {
         rhi = cubic_at(q, hi) - tau;
+        ++nev;
         if (rhi == 0.0) return hi;
     }
     double x = lo - rlo * (hi - lo) / (rhi - rlo);
     if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
     while (its < CORR_MAXIT) {
         double r = cubic_at(q, x) - tau;
+        ++nev;
         double ax = fabs(x);
         double scale = fmax(fabs(tau), ((q.s3 * ax + q.s2) * ax + q.s1) * ax);
         ++its;
@@ -607,7 +636,8 @@ __global__ void k_flux_polyhedra(DevMesh m, const double *__restrict__ Up, const
 template <int N>
 __device__ __forceinline__ void correct_face(const DevMesh &m, int f, int b, int n, const double *__restrict__ U,
                                              const double *__restrict__ F, double dt, int item, double *lam_out,
-                                             int *it_out, double *disp_out, int *maxit, int *nfallback)
+                                             int *it_out, double *disp_out, int *maxit, int *nfallback,
+                                             unsigned &ntri, unsigned &nev)
 {
     constexpr bool FIXED = N <= 4;
     const int nn = FIXED ? N : n;
@@ -646,7 +676,8 @@ __device__ __forceinline__ void correct_face(const DevMesh &m, int f, int b, int
         if (i < nn) w2 = fmax(w2, dot(W[i], W[i]));
     const V3 S = ld3(m.sf, m.nf, f);
     int its = 0;
-    const double lam = solve_lambda(q, tau, dot(S, S) * w2, its);
+    ntri += nn == 3 ? 1 : nn;
+    const double lam = solve_lambda(q, tau, dot(S, S) * w2, its, nev);
     lam_out[item] = lam;
     if (it_out) it_out[item] = its;
     if (maxit && its > 0) atomicMax(maxit, its);
@@ -675,18 +706,26 @@ __device__ __forceinline__ void correct_face(const DevMesh &m, int f, int b, int
 template <bool LIST>
 __global__ void k_correct(DevMesh m, const double *__restrict__ U, const double *__restrict__ F,
                           double dt, const int *list, const int *count, double *lam_out,
-                          int *it_out, double *disp_out, int *maxit, int *nfallback)
+                          int *it_out, double *disp_out, int *maxit, int *nfallback, unsigned long long *work)
 {
     const int total = LIST ? *count : m.nf;
+    unsigned ntri = 0, nev = 0;  // FP64 work: cubic coefficient triangles, cubic evaluations
     for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
         const int f = LIST ? list[item] : item;
         const int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
         if (n == 4)
-            correct_face<4>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback);
+            correct_face<4>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback, ntri, nev);
         else if (n == 3)
-            correct_face<3>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback);
+            correct_face<3>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback, ntri, nev);
         else
-            correct_face<VOF_MAXFP>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback);
+            correct_face<VOF_MAXFP>(m, f, b, n, U, F, dt, item, lam_out, it_out, disp_out, maxit, nfallback, ntri,
+                                    nev);
+    }
+    ntri = __reduce_add_sync(0xffffffffu, ntri);
+    nev = __reduce_add_sync(0xffffffffu, nev);
+    if ((threadIdx.x & 31) == 0) {
+        work_add1(work, WK_CTRI, ntri);
+        work_add1(work, WK_CEVAL, nev);
     }
 }
 
@@ -708,9 +747,9 @@ struct Tet { V3 v[4]; };
 // |T ^ {n_k.x <= d_k, k < np}| by depth-first splitting of T into the
 // tetrahedra of its inside parts (1 or 3 per plane); the last plane is applied
 // with the closed-form cut fraction.  Bounded stack: 1 + 2(np-1) entries.
-__device__ double clip_tet(const Tet &T, const V3 *pn, const double *pd, int np, unsigned *status,
-                          unsigned &cuts)
+__device__ double clip_tet(const Tet &T, const V3 *pn, const double *pd, int np, unsigned *status, WkOn &wk)
 {
+    wk.add(WK_VOL, 1);
     if (np == 0) return fabs(tvol(T.v[0], T.v[1], T.v[2], T.v[3]));
     Tet st[CLIP_STACK];
     unsigned char lv[CLIP_STACK];
@@ -726,15 +765,17 @@ __device__ double clip_tet(const Tet &T, const V3 *pn, const double *pd, int np,
         int nin = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) { s[i] = dot(pn[k], t.v[i]) - pd[k]; nin += s[i] <= 0.0; }
+        wk.add(WK_TEST, 1);
         if (nin == 0) continue;
         if (nin == 4) {
-            if (k + 1 == np) vol += fabs(tvol(t.v[0], t.v[1], t.v[2], t.v[3]));
+            if (k + 1 == np) { vol += fabs(tvol(t.v[0], t.v[1], t.v[2], t.v[3])); wk.add(WK_VOL, 1); }
             else if (sp < CLIP_STACK) { st[sp] = t; lv[sp] = k + 1; ++sp; }
             else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
             continue;
         }
-        ++cuts;
         if (k + 1 == np) {
+            wk.add(WK_VOL, 1);
+            wk.add(WK_FRAC, 1);
             double h0 = s[0], h1 = s[1], h2 = s[2], h3 = s[3];
             sort4(h0, h1, h2, h3);
             vol += fabs(tvol(t.v[0], t.v[1], t.v[2], t.v[3])) * frac_below(h0, h1, h2, h3, 0.0);
@@ -770,6 +811,7 @@ __device__ double clip_tet(const Tet &T, const V3 *pn, const double *pd, int np,
             out[2] = Tet{{a0, b0, b1, b2}};
             nout = 3;
         }
+        wk.add(WK_EDGE, nin == 2 ? 4 : 3);
         for (int i = 0; i < nout; ++i) {
             if (sp < CLIP_STACK) { st[sp] = out[i]; lv[sp] = k + 1; ++sp; }
             else atomicOr(status, VOF_ST_CLIP_OVERFLOW);
@@ -787,7 +829,7 @@ struct PFArgs {
     const int *list, *count;
     const double *disp;   // per list slot displacements (LIST mode)
     unsigned *status;
-    unsigned long long *work;  // [pairs, cuts, faces]
+    unsigned long long *work;  // WK_LEN counters (vof_internal.h)
     int *next;                 // LIST: next band slot to take (zero before the launch), or null
 };
 
@@ -813,6 +855,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
         if (lane == 0) v = atomicAdd(a.next, 1);
         return __shfl_sync(0xffffffffu, v, 0);
     };
+    WkOn wk;
     for (int item = dyn ? take() : warp; item < total; item = dyn ? take() : item + nwarps) {
         const int f = LIST ? a.list[item] : item;
         const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
@@ -892,7 +935,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
         __syncwarp();
         // ---- (tetrahedron, stencil cell) pairs over the lanes
         double acc = 0.0;
-        unsigned npairs = 0, ncuts = 0;
+        wk.face();
         const int ns = (int)(s1 - s0), nitems = nt * ns;
         for (int w = lane; w < nitems; w += 32) {
             const int t = w % nt, c = __ldg(m.scell + s0 + w / nt);
@@ -936,7 +979,7 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
                     if (hy < bx[1] || bx[4] < ly) continue;
                     double lz = fmin(fmin(ctr.z, k1.z), fmin(k2.z, k3.z)), hz = fmax(fmax(ctr.z, k1.z), fmax(k2.z, k3.z));
                     if (hz < bx[2] || bx[5] < lz) continue;
-                    ++npairs;
+                    wk.add(WK_TEST, 4);  // T's points against K's four planes
                     V3 pn[5];
                     double pd[5];
                     // outward planes of (ctr,k1,k2,k3): faces (ctr,k2,k1),(ctr,k1,k3),(ctr,k3,k2),(k1,k2,k3)
@@ -957,27 +1000,16 @@ __global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs 
                     }
                     if (outside) continue;
                     if (useH) { an[np] = hn; ad[np] = hd; ++np; }
-                    vsum += clip_tet(T, an, ad, np, a.status, ncuts);
+                    vsum += clip_tet(T, an, ad, np, a.status, wk);
                 }
             }
             acc += sg * wgt * vsum;
         }
         acc = warp_sum(acc);
-        if (a.work) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                npairs += __shfl_xor_sync(0xffffffffu, npairs, o);
-                ncuts += __shfl_xor_sync(0xffffffffu, ncuts, o);
-            }
-            if (lane == 0) {
-                atomicAdd(a.work, (unsigned long long)npairs);
-                atomicAdd(a.work + 1, (unsigned long long)ncuts);
-                atomicAdd(a.work + 2, 1ull);
-            }
-        }
         if (lane == 0) a.Va[f] = acc;
         __syncwarp();
     }
+    if (a.work) wk.flush(a.work, lane);
 }
 
 // ============================================================ update (A7)
@@ -1113,6 +1145,7 @@ __device__ void stats_block(const double *partial, int nblk, const int *counters
         stats[VOF_S_N_BOUND_SOURCES] = counters[CNT_VIOL0];
         stats[VOF_S_N_BOUND_LEFT] = counters[CNT_VIOL1];
     }
+    if (!post) stats[VOF_S_BOUND_PASSES] = stats[VOF_S_BOUND_GLOBAL] = 0.0;
 }
 
 __global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int nblk, const int *counters,
@@ -1122,15 +1155,18 @@ __global__ void __launch_bounds__(ST_THREADS) k_stats(const double *partial, int
     stats_block(partial, nblk, counters, stats, post, bound_partial, nblk_post);
 }
 
-// ------------------------------------------------- bounding pass (reading R10)
-// Every cell has room for excess, (1-alpha)V, and for deficit, alpha V (zero
-// outside [0,1]).  A source with excess e requests from each face neighbour r
-// the share e room_r / sum(room) of the room around it; a receiver whose
-// requests exceed its room scales them down to fit; what a source could not
-// place is pushed in equal parts to all its face neighbours.  Deficits mirror
-// this.  Every touched cell's new value is a gather over its face neighbours in
-// face order.  The sources are few, so one block runs all passes with block
-// barriers between the phases and stops once no cell is out of bounds.
+// ------------------------------------------ redistribution passes (reading R10)
+// Sec. 2.3's wisp redistribution, read as passes of a local redistribution:
+// a source (alpha > 1 + tol: excess e = (alpha - 1) V; alpha < -tol: deficit
+// u = -alpha V) asks each face neighbour r for e w_r / W, where the receiver
+// weight w = alpha (1 - alpha) V of an interface cell (tol < alpha < 1 - tol;
+// 0 elsewhere, so no bulk cell receives and no wisp is made) and W the sum
+// over the source's neighbours; a receiver takes at most its room, (1 - alpha)
+// V for excess and alpha V for deficit, and scales all requests to fit, so it
+// never leaves [0, 1]; what a source could not place stays with it for the
+// next pass.  Passes run while some source has both something left and a
+// receiver with room.  Every touched cell's new value is a gather over its
+// face neighbours in face order.
 // Face neighbours of x in face order, handed to fn(s, k) (s the neighbour, k
 // its cface slot).  The indices of a chunk of up to BP_CHUNK neighbours are
 // loaded together, and fn's own loads across the unrolled chunk can issue
@@ -1152,23 +1188,23 @@ __device__ __forceinline__ void for_nbrs(const DevMesh &m, int x, Fn fn)
 }
 __device__ __forceinline__ bool is_exc(double a) { return a > 1.0 + BOUND_TOL; }
 __device__ __forceinline__ bool is_def(double a) { return a < -BOUND_TOL; }
-__device__ __forceinline__ double room_exc(double a, double V) { return (a >= 0.0 && a < 1.0) ? (1.0 - a) * V : 0.0; }
-__device__ __forceinline__ double room_def(double a, double V) { return (a > 0.0 && a <= 1.0) ? a * V : 0.0; }
+__device__ __forceinline__ double recv_w(double a, double V)
+{
+    return (a > BOUND_TOL && a < 1.0 - BOUND_TOL) ? a * (1.0 - a) * V : 0.0;
+}
 
-// scratch per cell: [1/Cp, 1/Cm (0 where the room is 0), rp, rm, release, sp,
-// sm, 1/dg]: the phases multiply by the reciprocals (each source's room sums
-// and neighbour count divide many terms; the FP64 pipe of this part runs at
-// 1/62 of the FP32 rate)
-enum { BS_CP = 0, BS_CM, BS_RP, BS_RM, BS_REL, BS_SP, BS_SM, BS_RDG, BS_N = 8 };
+// scratch per cell: [1/W (0 where the source has no receiver), receiver
+// scales sp, sm, amount the source placed]
+enum { BS_RW = 0, BS_SP, BS_SM, BS_REL, BS_N = 4 };
 
 struct BoundBufs {
-    int *la, *lb;        // source lists (ping-pong), capacity nc
-    const int *n0;       // initial count (from the update kernel)
+    int *la;             // source list (from the update kernel), capacity nc
+    const int *n0;       // its count
     int *pc;             // pending cells, capacity cap_pend
     double *pa;          // pending values
     double *bs;          // BS_N doubles per cell
-    int *dg;             // per source: number of face neighbours
-    int *left;           // out: sources left after the local passes
+    int *npass;          // out: passes that moved something
+    int *act;            // two counters of active sources (pass parity)
     int cap, cap_pend;
 };
 
@@ -1188,33 +1224,30 @@ __device__ __forceinline__ int first_source(const DevMesh &m, const double *alph
     return first;
 }
 
-// The local pass as five phases over the source list (count on the device):
-// room, receiver scales, placement, new values, apply; t0 / nt: this thread's
-// index and the thread count of the grid.
-__device__ void bp_room(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
+// One pass as four phases over the source list (count on the device): the
+// receiver weight around each source, receiver scales, placement, new values
+// (then apply); t0 / nt: this thread's index and the thread count of the grid.
+// A source with something left and a receiver is counted in *act.
+__device__ __forceinline__ void bp_room(const DevMesh &m, const double *alpha, const BoundBufs &b, int *act, long t0, long nt)
 {
     const int n = min(*b.n0, b.cap);
+    int active = 0;
     for (long i = t0; i < n; i += nt) {
         int c = b.la[i];
-        double Cp = 0.0, Cm = 0.0;
-        int dg = 0;
-        for_nbrs(m, c, [&](int nb, int) {
-            double an = alpha[nb], Vn = m.vc[nb];
-            Cp += room_exc(an, Vn);
-            Cm += room_def(an, Vn);
-            ++dg;
-        });
-        b.bs[BS_N * (size_t)c + BS_CP] = Cp > 0.0 ? 1.0 / Cp : 0.0;
-        b.bs[BS_N * (size_t)c + BS_CM] = Cm > 0.0 ? 1.0 / Cm : 0.0;
-        b.bs[BS_N * (size_t)c + BS_RDG] = dg > 0 ? 1.0 / dg : 0.0;
-        b.dg[c] = dg;
+        const double a = alpha[c];
+        double W = 0.0;
+        if (is_exc(a) || is_def(a))
+            for_nbrs(m, c, [&](int nb, int) { W += recv_w(alpha[nb], m.vc[nb]); });
+        b.bs[BS_N * (size_t)c + BS_RW] = W > 0.0 ? 1.0 / W : 0.0;
+        active += W > 0.0;
     }
+    if (active) atomicAdd(act, active);
 }
 
 // one thread per (source, face slot): slot j takes the faces j, j + BP_SLOTS, ...
 constexpr int BP_SLOTS = 8;
 
-__device__ void bp_scale(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
+__device__ __forceinline__ void bp_scale(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
 {
     const long n = min(*b.n0, b.cap);
     double *bs = b.bs;
@@ -1223,45 +1256,47 @@ __device__ void bp_scale(const DevMesh &m, const double *alpha, const BoundBufs 
         for (int k = m.cptr[c] + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
             int r = m.cnb[k];
             if (r < 0 || first_source(m, alpha, r, false) != c) continue;
-            double ar = alpha[r], Vr = m.vc[r], Rp = room_exc(ar, Vr), Rm = room_def(ar, Vr);
+            const double ar = alpha[r], Vr = m.vc[r], wr = recv_w(ar, Vr);
+            const double Rp = wr > 0.0 ? (1.0 - ar) * Vr : 0.0, Rm = wr > 0.0 ? ar * Vr : 0.0;
             double Qp = 0.0, Qm = 0.0;
-            for_nbrs(m, r, [&](int s, int) {
-                double as = alpha[s], Vs = m.vc[s];
-                double rCps = bs[BS_N * (size_t)s + BS_CP], rCms = bs[BS_N * (size_t)s + BS_CM];
-                if (is_exc(as) && rCps > 0.0) Qp += (as - 1.0) * Vs * (Rp * rCps);
-                if (is_def(as) && rCms > 0.0) Qm += -as * Vs * (Rm * rCms);
-            });
+            if (wr > 0.0)
+                for_nbrs(m, r, [&](int s, int) {
+                    const double as = alpha[s], rW = bs[BS_N * (size_t)s + BS_RW];
+                    if (rW > 0.0) {
+                        if (is_exc(as)) Qp += (as - 1.0) * m.vc[s] * (wr * rW);
+                        else if (is_def(as)) Qm += -as * m.vc[s] * (wr * rW);
+                    }
+                });
             bs[BS_N * (size_t)r + BS_SP] = Qp > Rp ? Rp / Qp : 1.0;
             bs[BS_N * (size_t)r + BS_SM] = Qm > Rm ? Rm / Qm : 1.0;
         }
     }
 }
 
-__device__ void bp_place(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
+__device__ __forceinline__ void bp_place(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
 {
     const int n = min(*b.n0, b.cap);
     double *bs = b.bs;
     for (long i = t0; i < n; i += nt) {
         int c = b.la[i];
-        double a = alpha[c], V = m.vc[c];
         double *q = bs + BS_N * (size_t)c;
-        const double rCp = q[BS_CP], rCm = q[BS_CM];
-        double gp = 0.0, gm = 0.0, e = is_exc(a) ? (a - 1.0) * V : 0.0, u = is_def(a) ? -a * V : 0.0;
-        for_nbrs(m, c, [&](int nb, int) {
-            double an = alpha[nb], Vn = m.vc[nb];
-            if (e > 0.0 && rCp > 0.0) gp += e * (room_exc(an, Vn) * rCp) * bs[BS_N * (size_t)nb + BS_SP];
-            if (u > 0.0 && rCm > 0.0) gm += u * (room_def(an, Vn) * rCm) * bs[BS_N * (size_t)nb + BS_SM];
-        });
-        int dg = b.dg[c];
-        q[BS_RP] = (e > 0.0 && dg > 0) ? e - gp : 0.0;
-        q[BS_RM] = (u > 0.0 && dg > 0) ? u - gm : 0.0;
-        q[BS_REL] = e > 0.0 ? (dg > 0 ? e : gp) : (dg > 0 ? u : gm);
+        const double a = alpha[c], V = m.vc[c], rW = q[BS_RW];
+        double g = 0.0;
+        if (rW > 0.0) {
+            const bool xe = is_exc(a);
+            const double e = xe ? (a - 1.0) * V : -a * V;
+            for_nbrs(m, c, [&](int nb, int) {
+                const double w = recv_w(alpha[nb], m.vc[nb]);
+                if (w > 0.0) g += e * (w * rW) * bs[BS_N * (size_t)nb + (xe ? BS_SP : BS_SM)];
+            });
+        }
+        q[BS_REL] = g;
     }
 }
 
 // new values of the sources and their neighbours, each cell once: by the
 // lowest-index source in its closed face neighbourhood
-__device__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b, int *npend, unsigned *status,
+__device__ __forceinline__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b, int *npend, unsigned *status,
                        long t0, long nt)
 {
     const long n = min(*b.n0, b.cap);
@@ -1272,25 +1307,20 @@ __device__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b
         for (int k = m.cptr[c] - 1 + (int)(t % BP_SLOTS); k < m.cptr[c + 1]; k += BP_SLOTS) {
             int x = k < m.cptr[c] ? c : m.cnb[k];
             if (x < 0 || first_source(m, alpha, x, true) != c) continue;
-            double ax = alpha[x], V = m.vc[x];
-            bool xe = is_exc(ax), xd = is_def(ax);
-            double Rp = room_exc(ax, V), Rm = room_def(ax, V);
-            const double SPx = bs[BS_N * (size_t)x + BS_SP], SMx = bs[BS_N * (size_t)x + BS_SM];
+            const double ax = alpha[x], V = m.vc[x], wx = recv_w(ax, V);
             double dV = 0.0;
-            if (xe) dV -= bs[BS_N * (size_t)x + BS_REL];
-            if (xd) dV += bs[BS_N * (size_t)x + BS_REL];
-            for_nbrs(m, x, [&](int s, int) {
-                double as = alpha[s], Vs = m.vc[s];
-                const double *bq = bs + BS_N * (size_t)s;
-                if (is_exc(as)) {
-                    if (bq[BS_CP] > 0.0) dV += (as - 1.0) * Vs * (Rp * bq[BS_CP]) * SPx;
-                    dV += bq[BS_RP] * bq[BS_RDG];
-                }
-                if (is_def(as)) {
-                    if (bq[BS_CM] > 0.0) dV -= -as * Vs * (Rm * bq[BS_CM]) * SMx;
-                    dV -= bq[BS_RM] * bq[BS_RDG];
-                }
-            });
+            if (is_exc(ax)) dV -= bs[BS_N * (size_t)x + BS_REL];
+            else if (is_def(ax)) dV += bs[BS_N * (size_t)x + BS_REL];
+            if (wx > 0.0) {
+                const double SPx = bs[BS_N * (size_t)x + BS_SP], SMx = bs[BS_N * (size_t)x + BS_SM];
+                for_nbrs(m, x, [&](int s, int) {
+                    const double as = alpha[s], rW = bs[BS_N * (size_t)s + BS_RW];
+                    if (rW > 0.0) {
+                        if (is_exc(as)) dV += (as - 1.0) * m.vc[s] * (wx * rW) * SPx;
+                        else if (is_def(as)) dV -= -as * m.vc[s] * (wx * rW) * SMx;
+                    }
+                });
+            }
             if (dV != 0.0) {
                 int pos = atomicAdd(npend, 1);
                 if (pos < b.cap_pend) { b.pc[pos] = x; b.pa[pos] = (ax * V + dV) / V; }
@@ -1300,13 +1330,14 @@ __device__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b
     }
 }
 
-__device__ void bp_apply(double *alpha, const int *pc, const double *pa, const int *npend, int cap, long t0, long nt)
+__device__ __forceinline__ void bp_apply(double *alpha, const int *pc, const double *pa, const int *npend, int cap, long t0, long nt)
 {
     const int n = min(*npend, cap);
     for (long i = t0; i < n; i += nt) alpha[pc[i]] = pa[i];
 }
 
-// Global step for what the local pass leaves: the total excess (deficit) of a
+// Global fallback for what the local passes leave (a source none of whose face
+// neighbours is an interface cell with room): the total excess (deficit) of a
 // region (the whole mesh, or one case of a batch) goes to every cell of that
 // region strictly inside (tol, 1-tol) in proportion to its free (phase)
 // volume; sources are set to 1 (0).  A region's cells are contiguous and cut
@@ -1452,11 +1483,11 @@ __device__ bool grid_sync(unsigned *count, unsigned *generation, unsigned *statu
     return !gave_up;
 }
 
-// The whole bounding pass, the post-bounding mass and the step statistics in
-// one cooperative launch, a grid barrier between the phases: local pass
-// (room, scales, placement, new values, apply), segment sums, region totals,
-// global step with the mass partials, statistics (block 0).  Each phase does
-// the arithmetic, in the order, of the pass as separate kernels.
+// The whole redistribution, the post-bounding mass and the step statistics in
+// one cooperative launch, a grid barrier between the phases: passes of the
+// local redistribution (weights, scales, placement, new values, apply) while
+// some source has something left and a receiver, segment sums, region totals,
+// global fallback with the mass partials, statistics (block 0).
 struct BoundStep {
     double *alpha;
     BoundBufs b;
@@ -1482,23 +1513,36 @@ constexpr int BA_THREADS = 256;
 static_assert(BA_THREADS == GB_THREADS && BA_THREADS == UPD_THREADS && BA_THREADS == ST_THREADS,
               "the phases share one block shape");
 
-__global__ void __launch_bounds__(BA_THREADS) k_bound_step(DevMesh m, BoundStep a)
+__global__ void __launch_bounds__(BA_THREADS, 4) k_bound_step(DevMesh m, BoundStep a)
 {
     const long t0 = blockIdx.x * (long)blockDim.x + threadIdx.x, nt = (long)gridDim.x * blockDim.x;
-    // the local pass has few items (sources x slots): item i goes to block
+    // the passes have few items (sources x slots): item i goes to block
     // i mod gridDim.x, so that they spread over every SM rather than fill the
     // first few blocks (the FP64 divisions of a phase run on all SMs' units)
     const long tl = threadIdx.x * (long)gridDim.x + blockIdx.x;
-    bp_room(m, a.alpha, a.b, tl, nt);
-    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
-    bp_scale(m, a.alpha, a.b, tl, nt);
-    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
-    bp_place(m, a.alpha, a.b, tl, nt);
-    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
-    bp_new(m, a.alpha, a.b, a.npend, a.status, tl, nt);
-    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
-    bp_apply(a.alpha, a.b.pc, a.b.pa, a.npend, a.b.cap_pend, tl, nt);
-    if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    // act[p & 1] counts pass p's active sources; it was zeroed by the pass
+    // before (act[0] before the launch), after every block had read it
+#pragma unroll 1
+    for (int p = 0; p < BOUND_PASSES_MAX; ++p) {
+        int *act = a.b.act + (p & 1);
+        if (lead) {
+            a.b.act[(p + 1) & 1] = 0;
+            *a.npend = 0;  // the previous pass's apply phase is behind a barrier
+        }
+        bp_room(m, a.alpha, a.b, act, tl, nt);
+        if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
+        if (*(volatile int *)act == 0) break;
+        if (lead) *a.b.npass = p + 1;
+        bp_scale(m, a.alpha, a.b, tl, nt);
+        if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
+        bp_place(m, a.alpha, a.b, tl, nt);
+        if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
+        bp_new(m, a.alpha, a.b, a.npend, a.status, tl, nt);
+        if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
+        bp_apply(a.alpha, a.b.pc, a.b.pa, a.npend, a.b.cap_pend, tl, nt);
+        if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
+    }
     for (int sgi = blockIdx.x; sgi < a.nseg; sgi += gridDim.x)
         seg_reduce(m, a.alpha, a.seg[sgi], a.gpartial + 4 * (size_t)sgi, a.nleft);
     if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
@@ -1514,7 +1558,19 @@ __global__ void __launch_bounds__(BA_THREADS) k_bound_step(DevMesh m, BoundStep 
     if (bad) atomicOr(a.status, VOF_ST_BOUND_RESIDUAL);
     block_reduce5(v, a.mpartial + 5 * blockIdx.x);
     if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
-    if (blockIdx.x == 0) stats_block(a.upartial, a.nupd, a.counters, a.stats, 1, a.mpartial, gridDim.x);
+    if (blockIdx.x == 0) {
+        stats_block(a.upartial, a.nupd, a.counters, a.stats, 1, a.mpartial, gridDim.x);
+        if (threadIdx.x == 0) {
+            // volume the global fallback moved (regions where it applied)
+            double gv = 0.0;
+            for (int r = 0; r < a.nreg; ++r) {
+                const double *tt = a.reg_tot + REG_TOT * (size_t)r;
+                if (!((tt[0] == 0.0 && tt[1] == 0.0) || tt[0] > tt[2] || tt[1] > tt[3])) gv += tt[0] + tt[1];
+            }
+            a.stats[VOF_S_BOUND_PASSES] = *(volatile int *)a.b.npass;
+            a.stats[VOF_S_BOUND_GLOBAL] = gv;
+        }
+    }
 }
 
 // The barrier's own check (a cooperative launch): every block passes `rounds`
@@ -1535,13 +1591,16 @@ __global__ void k_zero_int(int *p, int n)
     if (i < n) p[i] = 0;
 }
 
-// the update group's counters: violations before / after the local pass,
-// pending cells, and the grid barrier's arrival count
+// the update group's counters: violations before / after the local passes,
+// pending cells, passes, the first pass's active sources, and the grid
+// barrier's arrival count
 __global__ void k_zero_update(int *cnt)
 {
     const int i = threadIdx.x;
     if (i < 3) cnt[CNT_VIOL0 + i] = 0;
     if (i == 3) cnt[CNT_BAR] = 0;
+    if (i == 4) cnt[CNT_BPASS] = 0;
+    if (i == 5) cnt[CNT_BACT0] = 0;
 }
 
 // ============================================== band classification (A2, R9)
@@ -1667,26 +1726,211 @@ int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t
 }
 
 // reconstruction launch with the context's lanes per cell (8 or 32)
+// ===================================== generalised LSQ gradient (Sec. 2.2.1)
+// Per cell the gradient minimising sum_k w^2 (phi_k - phi_c - g.d)^2 over the
+// cells k sharing a point with c (d = x_k - x_c, w = 1/|d|, the inverse
+// distance of Eq. generalizedLSQminimize): the 3x3 normal equations solved by
+// the adjugate of their symmetric matrix (g = 0 where it is singular).
+template <bool LIST>
+__global__ void k_lsq_gradient(DevMesh m, const double *__restrict__ alpha, const int *list, const int *count,
+                               const int *__restrict__ lptr, const int *__restrict__ lcell, double *grad)
+{
+    const int total = LIST ? *count : m.nc;
+    for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
+        const int c = LIST ? list[item] : item;
+        const V3 xc = ld3(m.cc, m.nc, c);
+        const double pc = alpha[c];
+        double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0, b0 = 0, b1 = 0, b2 = 0;
+        for (int k = __ldg(lptr + c), k1 = __ldg(lptr + c + 1); k < k1; ++k) {
+            const int q = __ldg(lcell + k);
+            const V3 dd = ld3(m.cc, m.nc, q) - xc;
+            const double w2 = 1.0 / dot(dd, dd), dp = (alpha[q] - pc) * w2;
+            const V3 wd = dd * w2;
+            a00 += wd.x * dd.x; a01 += wd.x * dd.y; a02 += wd.x * dd.z;
+            a11 += wd.y * dd.y; a12 += wd.y * dd.z; a22 += wd.z * dd.z;
+            b0 += dp * dd.x; b1 += dp * dd.y; b2 += dp * dd.z;
+        }
+        const double c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+        const double c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+        const double det = a00 * c00 + a01 * c01 + a02 * c02;
+        V3 g = mk(0, 0, 0);
+        if (det != 0.0) {
+            const double r = 1.0 / det;
+            g = mk((c00 * b0 + c01 * b1 + c02 * b2) * r, (c01 * b0 + c11 * b1 + c12 * b2) * r,
+                   (c02 * b0 + c12 * b1 + c22 * b2) * r);
+        }
+        st3(grad, m.nc, c, g);
+    }
+}
+
+int launch_lsq_gradient(vof_ctx *c, const double *alpha, const int *list, const int *count, double *grad,
+                        cudaStream_t s)
+{
+    if (list)
+        k_lsq_gradient<true><<<num_sms(c->device) * 8, 128, 0, s>>>(c->m, alpha, list, count, c->lptr, c->lcell, grad);
+    else
+        k_lsq_gradient<false><<<cdiv(c->nc, 128), 128, 0, s>>>(c->m, alpha, nullptr, nullptr, c->lptr, c->lcell, grad);
+    return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
+}
+
+// ======================================= reconstruction error E_vsd (Sec. 4.1)
+// The true phase is a ball (centre bc, radius R), resolved as the paper's tool
+// mesh resolves a geometry: each cell tetrahedron is split into eight (edge
+// midpoints; the inner octahedron about the diagonal joining the midpoints of
+// edges ab and cd) down to `levels`; a piece is wholly in the ball (its four
+// vertices in the closed ball), wholly outside (centroid distance less the
+// largest vertex distance to the centroid at least R), or, undecided at the
+// last level, cut by the plane tangent to the sphere at the point nearest its
+// centroid.  A piece S with true phase P and reconstructed phase H adds
+// |P| + |S ^ H| - 2 |P ^ H| (E_vsd^- + E_vsd^+).  The decisions use
+// round-to-nearest operations without contraction, so that every piece is
+// decided as the plain definition decides it.
+constexpr int EVSD_MAX_LEVELS = 6;
+constexpr int EVSD_STACK = 7 * EVSD_MAX_LEVELS + 1;
+
+__device__ __forceinline__ V3 ev_sub(V3 a, V3 b) { return mk(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y), __dsub_rn(a.z, b.z)); }
+__device__ __forceinline__ double ev_d2(V3 a, V3 b)
+{
+    const V3 t = ev_sub(a, b);
+    return __dadd_rn(__dadd_rn(__dmul_rn(t.x, t.x), __dmul_rn(t.y, t.y)), __dmul_rn(t.z, t.z));
+}
+__device__ __forceinline__ V3 ev_mid(V3 a, V3 b)
+{
+    return mk(__dmul_rn(__dadd_rn(a.x, b.x), 0.5), __dmul_rn(__dadd_rn(a.y, b.y), 0.5), __dmul_rn(__dadd_rn(a.z, b.z), 0.5));
+}
+
+struct EvPiece { V3 v[4]; int lev; };
+
+__device__ double evsd_tet(const Tet &T0, int levels, V3 bc, double R, int hmode, V3 hn, double hd, unsigned *status)
+{
+    WkOn wk;  // counts nothing here; clip_tet's bookkeeping
+    EvPiece st[EVSD_STACK];
+    int sp = 0;
+    st[sp++] = EvPiece{{T0.v[0], T0.v[1], T0.v[2], T0.v[3]}, 0};
+    const double R2 = __dmul_rn(R, R);
+    double e = 0.0;
+    while (sp > 0) {
+        const EvPiece q = st[--sp];
+        const V3 a = q.v[0], b = q.v[1], c = q.v[2], d = q.v[3];
+        const V3 g = mk(__dmul_rn(__dadd_rn(__dadd_rn(a.x, b.x), __dadd_rn(c.x, d.x)), 0.25),
+                        __dmul_rn(__dadd_rn(__dadd_rn(a.y, b.y), __dadd_rn(c.y, d.y)), 0.25),
+                        __dmul_rn(__dadd_rn(__dadd_rn(a.z, b.z), __dadd_rn(c.z, d.z)), 0.25));
+        const bool inside = ev_d2(a, bc) <= R2 && ev_d2(b, bc) <= R2 && ev_d2(c, bc) <= R2 && ev_d2(d, bc) <= R2;
+        double rt = sqrt(ev_d2(a, g));
+        rt = fmax(rt, sqrt(ev_d2(b, g)));
+        rt = fmax(rt, sqrt(ev_d2(c, g)));
+        rt = fmax(rt, sqrt(ev_d2(d, g)));
+        const double dist = sqrt(ev_d2(g, bc));
+        const Tet S{{a, b, c, d}};
+        const bool outside = !inside && __dsub_rn(dist, rt) >= R;
+        if (inside || outside || q.lev >= levels) {
+            const double vS = fabs(tvol(a, b, c, d));
+            const double SH = hmode == 0 ? 0.0 : hmode == 1 ? vS : clip_tet(S, &hn, &hd, 1, status, wk);
+            if (inside) { e += vS - SH; continue; }
+            if (outside) { e += SH; continue; }
+            V3 pn[2];
+            double pd[2];
+            const V3 u = dist > 0.0 ? (g - bc) * (1.0 / dist) : mk(1, 0, 0);
+            pn[0] = u; pd[0] = dot(u, bc) + R;
+            const double P = clip_tet(S, pn, pd, 1, status, wk);
+            double PH = 0.0;
+            if (hmode == 1) PH = P;
+            else if (hmode == 2) { pn[1] = hn; pd[1] = hd; PH = clip_tet(S, pn, pd, 2, status, wk); }
+            e += P + SH - 2.0 * PH;
+            continue;
+        }
+        if (sp + 8 > EVSD_STACK) { atomicOr(status, VOF_ST_CAPACITY); continue; }
+        const V3 ab = ev_mid(a, b), ac = ev_mid(a, c), ad = ev_mid(a, d), bm = ev_mid(b, c), bd = ev_mid(b, d),
+                 cd = ev_mid(c, d);
+        const int l = q.lev + 1;
+        st[sp++] = EvPiece{{a, ab, ac, ad}, l};
+        st[sp++] = EvPiece{{b, ab, bm, bd}, l};
+        st[sp++] = EvPiece{{c, ac, bm, cd}, l};
+        st[sp++] = EvPiece{{d, ad, bd, cd}, l};
+        st[sp++] = EvPiece{{ab, cd, ac, ad}, l};
+        st[sp++] = EvPiece{{ab, cd, ad, bd}, l};
+        st[sp++] = EvPiece{{ab, cd, bd, bm}, l};
+        st[sp++] = EvPiece{{ab, cd, bm, ac}, l};
+    }
+    return e;
+}
+
+// one warp per cell, a lane per cell tetrahedron; the lanes' sums in a fixed order
+__global__ void k_evsd(DevMesh m, const uint8_t *flags, const double *n, const double *d, double bx, double by,
+                       double bz, double R, int levels, double *out, unsigned *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const V3 bc = mk(bx, by, bz);
+    for (int c = warp; c < m.nc; c += nw) {
+        int hmode = 0;
+        V3 hn = mk(0, 0, 0);
+        double hd = 0.0;
+        if (flags) {
+            const uint8_t f = flags[c];
+            if (f & VOF_FULL) hmode = 1;
+            else if ((f & VOF_INTERFACE) && (f & VOF_ORIENTED)) { hmode = 2; hn = ld3(n, m.nc, c); hd = d[c]; }
+        }
+        const V3 ctr = ld3(m.cc, m.nc, c);
+        double e = 0.0;
+        for (int tj = __ldg(m.ctptr + c) + lane; tj < __ldg(m.ctptr + c + 1); tj += 32) {
+            const int4 te = __ldg(m.ctet + tj);
+            V3 t0, t1, t2;
+            if (te.w >= 0) {
+                t0 = ldP(m, __ldg(m.fpts + te.y)); t1 = ldP(m, __ldg(m.fpts + te.z)); t2 = ldP(m, __ldg(m.fpts + te.w));
+            } else {
+                t0 = ld3(m.cf, m.nf, te.x >> 1); t1 = ldP(m, __ldg(m.fpts + te.y)); t2 = ldP(m, __ldg(m.fpts + te.z));
+            }
+            e += evsd_tet(Tet{{ctr, t0, t1, t2}}, levels, bc, R, hmode, hn, hd, status);
+        }
+        e = warp_sum(e);
+        if (lane == 0) out[c] = e;
+    }
+}
+
+int launch_evsd(vof_ctx *c, const uint8_t *flags, const double *n, const double *d, const double ball[4],
+                int levels, double *out, cudaStream_t s)
+{
+    if (levels < 0 || levels > EVSD_MAX_LEVELS) return VOF_ERR_INVALID_ARG;
+    k_evsd<<<num_sms(c->device) * 16, 128, 0, s>>>(c->m, flags, n, d, ball[0], ball[1], ball[2], ball[3], levels,
+                                                   out, c->status);
+    return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
+}
+
 template <bool LIST, bool MIXED>
 static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const double *palpha, const int *list,
                       const int *count, double *n, double *d, uint8_t *flags, int *iters, int *maxit,
                       cudaStream_t s, int *next = nullptr)
 {
+    // the generalised LSQ gradient of the cells first, where selected
+    const double *gin = nullptr;
+    if (c->grad_kind == VOF_GRAD_LSQ) {
+        launch_lsq_gradient(c, alpha, list, count, c->grad, s);
+        gin = c->grad;
+    }
     // lanes per cell and tetrahedra per lane: 8 x 2 (cells of <= 16 tetrahedra),
-    // 32 x 2 (<= 64), 32 x 3 (<= 96: octree cells next to finer ones)
+    // 32 x 2 (<= 64), 32 x 3 (<= 96: octree cells next to finer ones); the
+    // instrumented variant while work counting is on (vof_count_work)
+#define RC_GO(G_, K_, BL)                                                                                    \
+    do {                                                                                                     \
+        if (c->work_on)                                                                                      \
+            k_reconstruct<LIST, MIXED, G_, K_, true><<<BL, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, \
+                flags, iters, maxit, c->status, c->mlp_s0, mlp_cap(c), next, c->work, gin);                  \
+        else                                                                                                 \
+            k_reconstruct<LIST, MIXED, G_, K_, false><<<BL, 128, 0, s>>>(c->m, alpha, palpha, list, count, n,   \
+                d, flags, iters, maxit, c->status, c->mlp_s0, mlp_cap(c), next, nullptr, gin);                \
+    } while (0)
     if (c->rc_g == 8) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
-        k_reconstruct<LIST, MIXED, 8, 2><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                                maxit, c->status, c->mlp_s0, mlp_cap(c), next);
+        RC_GO(8, 2, blocks);
     } else if (c->rc_k <= 2) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
-        k_reconstruct<LIST, MIXED, 32, 2><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                                 maxit, c->status, c->mlp_s0, mlp_cap(c), next);
+        RC_GO(32, 2, blocks);
     } else {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
-        k_reconstruct<LIST, MIXED, 32, 3><<<blocks, 128, 0, s>>>(c->m, alpha, palpha, list, count, n, d, flags, iters,
-                                                                 maxit, c->status, c->mlp_s0, mlp_cap(c), next);
+        RC_GO(32, 3, blocks);
     }
+#undef RC_GO
 }
 
 // defaults of every cell (n = 0, d = 0, flags FULL or 0, iterations 0), and
@@ -1753,7 +1997,7 @@ int launch_correct_all(vof_ctx *c, const double *Up, const double *F, double dt,
                        cudaStream_t s)
 {
     k_correct<false><<<cdiv(c->nf, 128), 128, 0, s>>>(c->m, Up, F, dt, nullptr, nullptr, lambda, iters,
-                                                             nullptr, nullptr, nullptr);
+                                                             nullptr, nullptr, nullptr, c->work_on ? c->work : nullptr);
     LAUNCH_CHECK();
     return VOF_OK;
 }
@@ -1784,8 +2028,8 @@ static int launch_bound_step(vof_ctx *c, double *alpha, int nupd, const int *cou
     }
     int *cnt = c->counters;
     BoundStep a{alpha,
-                BoundBufs{c->viol[0], c->viol[1], cnt + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, c->dgi,
-                          cnt + CNT_VIOL1, c->nc, 8 * c->nc},
+                BoundBufs{c->viol[0], cnt + CNT_VIOL0, c->pend_c, c->pend_a, c->bscr, cnt + CNT_BPASS,
+                          cnt + CNT_BACT0, c->nc, 8 * c->nc},
                 cnt + CNT_PEND, c->seg, c->nseg, c->gpartial, cnt + CNT_VIOL1, c->reg_seg, c->nreg, c->reg_tot,
                 c->partial + 5 * UPD_BLOCKS, c->partial, nupd, counters, stats,
                 reinterpret_cast<unsigned *>(cnt + CNT_BAR), reinterpret_cast<unsigned *>(cnt + CNT_BARGEN), c->status};
@@ -1871,7 +2115,8 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
         return VOF_ERR_CUDA;
     k_band_point_velocity<<<cdiv(m.np, 256), 256, 0, c->s_aux>>>(m, Uc, c->bpflag, c->upb);
     k_correct<true><<<sms * 8, 128, 0, c->s_aux>>>(m, c->upb, F, dt, c->band, cnt + CNT_BAND, c->lam_b, c->it_b,
-                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK);
+                                                   c->disp_b, cnt + CNT_MAXCORR, cnt + CNT_FALLBACK,
+                                                   c->work_on ? c->work : nullptr);
     LAUNCH_CHECK();
     if (cudaEventRecord(c->ev_join, c->s_aux) != cudaSuccess) return VOF_ERR_CUDA;
     if (c->precision == VOF_MIXED && c->mlp) {
@@ -1893,7 +2138,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
         if (r) return r;
     } else {
         PFArgs a{alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band, cnt + CNT_BAND, c->disp_b,
-                 c->status, c->work, cnt + CNT_PFNEXT};
+                 c->status, c->work_on ? c->work : nullptr, cnt + CNT_PFNEXT};
         k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
     }
     launches += 4;  // reconstruct, band point velocities, correct, phase flux

@@ -203,7 +203,8 @@ __device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin,
 // piece has at most 4 planes to go, so the split pieces keep i + 1 + 2 (r - 1)
 // <= MX_STACK for depth i and r planes to go: the top one alone always fits
 // once the leaves are gone, and the stacks cannot overflow.
-__device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &accs, float &accc, unsigned &ncuts)
+template <class Wk>
+__device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &accs, float &accc, Wk &wk)
 {
     const int lane = threadIdx.x & 31;
     const unsigned le = ((1u << lane) << 1) - 1u;
@@ -224,11 +225,13 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
                 float sd[4];
                 int nin, nup;
                 fdist(t, sh.Kp[k][j], tol, sd, nin, nup);
+                wk.add(WK_TEST, 1);
                 float v6 = 0.0f;
                 if (nin > 0) {
                     v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    wk.add(WK_VOL, 1);
                     if (nup > 0) {
-                        ++ncuts;
+                        wk.add(WK_FRAC, 1);
                         float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
                         fsort4(h0, h1, h2, h3);
                         v6 *= ffrac_below(h0, h1, h2, h3);
@@ -257,6 +260,7 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
         unsigned rem = 0;
         float sd[4], v6 = 0.0f;
         bool cut = false;
+        unsigned lw = 0;  // this lane's leaf work: 1 volume, 2 cut fraction
         if (act) {
             ti = meta & 31;
             k = (meta >> 5) & 31;
@@ -269,7 +273,9 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
                 if (rem != 0) nch = nup == 0 || nin == 1 ? 1 : 3;
                 else {  // a job with one plane: its leaf here
                     v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    lw = 1;
                     if (nup > 0) {
+                        lw = 3;
                         float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
                         fsort4(h0, h1, h2, h3);
                         v6 *= ffrac_below(h0, h1, h2, h3);
@@ -292,7 +298,11 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
         const unsigned lm = L >= 32 ? 0xffffffffu : (1u << L) - 1u;
         const int top = MX_STACK - nn + min(L, p);  // the split stack's top after the pops
         if (lane < L) {
-            if (cut) ++ncuts;
+            // work of the committed lanes (the others redo theirs later)
+            wk.add(WK_TEST, 1);
+            wk.add(WK_VOL, lw & 1);
+            wk.add(WK_FRAC, lw >> 1);
+            if (cut && nch > 0) wk.add(WK_EDGE, nin == 2 ? 4 : 3);
             if (v6 != 0.0f) two_sum(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
             if (nch > 0) {
                 const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
@@ -322,8 +332,9 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
 // distances of the prism's six points to K's planes, from which each of its
 // three tetrahedra is classified: outside a plane, inside every plane (adds
 // |T| at once), or a clip job.
+template <class Wk>
 __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
-                                         unsigned &npairs, unsigned &ncuts)
+                                         Wk &wk)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -353,7 +364,6 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
         if (pi < total) {
             const unsigned pc = sh.PQ[pi];
             const int pr = pc & 7, k = pc >> 3;
-            npairs += 3;
             float v[20];
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
@@ -361,6 +371,7 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
                 v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
             }
             const int npl = sh.KuseH[k] ? 5 : 4;
+            wk.add(WK_PRISM, npl);
             unsigned mask[3] = {0u, 0u, 0u};
             bool outside[3] = {false, false, false};
             // a point within tol of a plane is on it: a tetrahedron is outside
@@ -402,14 +413,14 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
             nq += __popc(bm);
         }
     }
-    if (nq > 0) mx_clip(sh, nq, tol, accs, accc, ncuts);
+    if (nq > 0) mx_clip(sh, nq, tol, accs, accc, wk);
     __syncwarp();
 }
 
 // W warps (faces) per block; blocks per SM as shared memory allows
 constexpr int mx_resident(int w) { return w == 1 ? 15 : w == 2 ? 8 : 5; }
 
-template <bool LIST, int W>
+template <bool LIST, int W, class Wk>
 __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(DevMesh m, MXArgs a)
 {
     __shared__ MXShared shm[W];
@@ -430,6 +441,7 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
         if (lane == 0) v = atomicAdd(a.next, 1);
         return __shfl_sync(0xffffffffu, v, 0);
     };
+    Wk wk;
     for (int item = dyn ? take() : warp; item < total; item = dyn ? take() : item + nwarps) {
         const int f = LIST ? a.list[item] : item;
         const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
@@ -556,7 +568,8 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
         }
         __syncwarp();
         float accs = 0.0f, accc = 0.0f;
-        unsigned npairs = 0, ncuts = 0;
+        wk.add(WK_VOL, lane < nt);  // the flux polyhedron's tetrahedra
+        wk.face();
         int ncand = 0;
         // The stencil is taken 32 cells at a time, one per lane: the cells that
         // reach the polyhedron's box are kept (with their half-space) in shared
@@ -655,6 +668,7 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
                 cand = !(kbx[3] < pb[0] || pb[3] < kbx[0] || kbx[4] < pb[1] || pb[4] < kbx[1] ||
                          kbx[5] < pb[2] || pb[5] < kbx[2]);
                 if (cand) {
+                    wk.add(WK_SHIFT, 4);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
                         const float4 pl = __ldg(q + i);
@@ -664,7 +678,7 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
             }
             const unsigned cmask = __ballot_sync(0xffffffffu, cand);
             if (fin ? ncand > 0 : ncand + __popc(cmask) > MX_CAND) {
-                mx_flush(sh, nt, ncand, tol, accs, accc, npairs, ncuts);
+                mx_flush(sh, nt, ncand, tol, accs, accc, wk);
                 ncand = 0;
                 continue;  // the batch again (or the end)
             }
@@ -692,21 +706,10 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
         }
         double acc = ((double)rs + (double)rc) / 6.0;
         if (comp) acc = Ff * a.dt - acc;
-        if (a.work) {
-#pragma unroll
-            for (int o2 = 16; o2 > 0; o2 >>= 1) {
-                npairs += __shfl_xor_sync(0xffffffffu, npairs, o2);
-                ncuts += __shfl_xor_sync(0xffffffffu, ncuts, o2);
-            }
-            if (lane == 0) {
-                atomicAdd(a.work, (unsigned long long)npairs);
-                atomicAdd(a.work + 1, (unsigned long long)ncuts);
-                atomicAdd(a.work + 2, 1ull);
-            }
-        }
         if (lane == 0) a.Va[f] = acc;
         __syncwarp();
     }
+    wk.flush(a.work, lane);
 }
 
 // FP32 geometry of every cell relative to its centre (context creation)
@@ -810,7 +813,8 @@ int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n
                                 double dt, double *Va, cudaStream_t s)
 {
     MXArgs a = mx_args(c, alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr, nullptr);
-    k_phase_flux_mixed<false, 2><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+    if (c->work_on) k_phase_flux_mixed<false, 2, WkOn><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+    else k_phase_flux_mixed<false, 2, WkOff><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 
@@ -824,11 +828,13 @@ int launch_phase_flux_mixed_list(vof_ctx *c, const double *alpha, const double *
     // resident blocks x multiplier
     const int w = c->pf_warps >= 1 && c->pf_warps <= 3 ? c->pf_warps : 2;
     const int mult = c->pf_mult >= 1 ? c->pf_mult : 1;
-    if (w == 1)
-        k_phase_flux_mixed<true, 1><<<sms * mx_resident(1) * mult, 32, 0, s>>>(c->m, a);
+    if (c->work_on)  // instrumented variant (vof_count_work), the 2-warp shape
+        k_phase_flux_mixed<true, 2, WkOn><<<sms * mx_resident(2) * mult, 64, 0, s>>>(c->m, a);
+    else if (w == 1)
+        k_phase_flux_mixed<true, 1, WkOff><<<sms * mx_resident(1) * mult, 32, 0, s>>>(c->m, a);
     else if (w == 2)
-        k_phase_flux_mixed<true, 2><<<sms * mx_resident(2) * mult, 64, 0, s>>>(c->m, a);
+        k_phase_flux_mixed<true, 2, WkOff><<<sms * mx_resident(2) * mult, 64, 0, s>>>(c->m, a);
     else
-        k_phase_flux_mixed<true, 3><<<sms * mx_resident(3) * mult, 96, 0, s>>>(c->m, a);
+        k_phase_flux_mixed<true, 3, WkOff><<<sms * mx_resident(3) * mult, 96, 0, s>>>(c->m, a);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }

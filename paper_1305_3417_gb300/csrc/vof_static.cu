@@ -70,6 +70,7 @@ extern "C" int vof_reconstruct_static(vof_ctx *c, const double *alpha, double *n
 {
     if (!c || !alpha || !n || !d || !flags) return VOF_ERR_INVALID_ARG;
     if (c->nc > STATIC_MAX_CELLS) return VOF_ERR_INVALID_ARG;  // beyond the static list
+    if (c->nc == 0) return VOF_OK;                               // nothing to reconstruct
     if (cudaSetDevice(c->device) != cudaSuccess) return VOF_ERR_CUDA;
     int *scratch = nullptr;
     int r = static_scratch(c->device, &scratch);
@@ -78,7 +79,13 @@ extern "C" int vof_reconstruct_static(vof_ctx *c, const double *alpha, double *n
     // the list length starts at zero on every call (the array keeps the last
     // call's contents otherwise)
     if (cudaMemsetAsync(scratch, 0, sizeof(int), s) != cudaSuccess) return VOF_ERR_CUDA;
-    k_static_fill<<<(c->nc + 255) / 256, 256, 0, s>>>(c->nc, c->eps, alpha, n, d, flags, scratch);
-    if (cudaGetLastError() != cudaSuccess) return VOF_ERR_CUDA;
+    // launched through cudaLaunchKernelEx, whose return code is this launch's
+    // own (an error left by earlier, unrelated work is not blamed on it)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((c->nc + 255) / 256);
+    cfg.blockDim = dim3(256);
+    cfg.stream = s;
+    if (cudaLaunchKernelEx(&cfg, k_static_fill, c->nc, c->eps, alpha, n, d, flags, scratch) != cudaSuccess)
+        return VOF_ERR_CUDA;
     return launch_reconstruct(c, alpha, n, d, flags, nullptr, scratch + STATIC_HEAD, scratch, s);
 }

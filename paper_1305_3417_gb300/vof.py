@@ -23,7 +23,7 @@ STATUS_BITS = {1: "POS_NOT_CONVERGED", 2: "CORR_NOT_CONVERGED", 4: "CLIP_OVERFLO
                8: "BOUND_RESIDUAL", 16: "INDEX", 32: "CAPACITY", 64: "TIMEOUT"}
 S = dict(mass_before=0, mass_after=1, min_pre=2, max_pre=3, min_post=4, max_post=5,
          n_interface=6, n_band=7, max_pos_it=8, max_corr_it=9, boundary_out=10, n_fallback=11,
-         n_bound_sources=12, n_bound_left=13)
+         n_bound_sources=12, n_bound_left=13, bound_passes=14, bound_global=15)
 S_LEN = 16
 
 
@@ -48,10 +48,12 @@ class _Options(ctypes.Structure):
 EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "vof_reconstruct",
            "vof_flux_polyhedra", "vof_correct_flux", "vof_phase_flux", "vof_update", "vof_advect",
            "vof_advect_host", "vof_status", "vof_last_launch_count", "vof_error_string",
-           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_probe_fma", "vof_probe_barrier",
+           "vof_profile_begin", "vof_profile_end", "vof_work_counts", "vof_count_work", "vof_probe_fma", "vof_probe_barrier",
            "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
            "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
-           "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess"]
+           "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess", "vof_set_gradient", "vof_lsq_gradient",
+           "vof_evsd"]
+GRAD_NAG, GRAD_LSQ = 0, 1
 MLP_IN, MLP_HID, MLP_OUT = 33, 64, 4
 MLP_NPARAM = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
 PROF_GROUPS = ["classify", "reconstruct", "correct", "phase_flux", "update"]
@@ -86,6 +88,7 @@ def lib():
         "vof_profile_begin": (I, [P, I]),
         "vof_profile_end": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "vof_work_counts": (I, [P, P, I, P]),
+        "vof_count_work": (I, [P, I]),
         "vof_probe_fma": (I, [I, I, ctypes.POINTER(ctypes.c_double), P]),
         "vof_probe_barrier": (I, [P, I, P]),
         "vof_batch_create": (I, [ctypes.POINTER(_Mesh), P, I, ctypes.POINTER(_Options), ctypes.POINTER(P)]),
@@ -101,6 +104,9 @@ def lib():
         "vof_mlp_gradient": (I, [P, P, P, I, P, ctypes.POINTER(ctypes.c_float), P]),
         "vof_mlp_train_step": (I, [P, P, P, I, ctypes.c_float, ctypes.POINTER(ctypes.c_float), P]),
         "vof_set_guess": (I, [P, P]),
+        "vof_set_gradient": (I, [P, I]),
+        "vof_lsq_gradient": (I, [P, P, P, P]),
+        "vof_evsd": (I, [P, P, P, P, ctypes.POINTER(ctypes.c_double), I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -280,10 +286,38 @@ def vof_profile_end(h):
     return dict(zip(PROF_GROUPS, list(ms))), int(n.value)
 
 
+WORK = ["prism_planes", "piece_tests", "edges", "tet_volumes", "cut_fractions", "plane_shifts", "faces",
+        "fill64", "fill32", "cubic_triangles", "cubic_evals", "reserved"]
+
+
+def vof_set_gradient(h, kind: int):
+    """Gradient of the reconstruction: GRAD_NAG (default) or GRAD_LSQ."""
+    _check(lib().vof_set_gradient(h, int(kind)), "vof_set_gradient")
+
+
+def vof_lsq_gradient(h, alpha, grad, stream=None):
+    _check(lib().vof_lsq_gradient(h, _ptr(alpha), _ptr(grad), _stream(stream)), "vof_lsq_gradient")
+
+
+def vof_evsd(h, flags, n, d, ball, levels, out, stream=None):
+    """E_vsd per cell against the ball (cx, cy, cz, R); flags None: the ball's
+    volume in each cell."""
+    b = (ctypes.c_double * 4)(*[float(x) for x in ball])
+    _check(lib().vof_evsd(h, _ptr(flags) if flags is not None else None, _ptr(n) if n is not None else None,
+                          _ptr(d) if d is not None else None, b, int(levels), _ptr(out), _stream(stream)),
+           "vof_evsd")
+
+
+def vof_count_work(h, on: bool = True):
+    """Instrumented step kernels (work counting) on or off."""
+    _check(lib().vof_count_work(h, int(bool(on))), "vof_count_work")
+
+
 def vof_work_counts(h, reset: bool = True, stream=None):
-    c = (ctypes.c_ulonglong * 3)()
+    """Counted primitives since the last reset (include/vof.h), by name."""
+    c = (ctypes.c_ulonglong * len(WORK))()
     _check(lib().vof_work_counts(h, c, int(bool(reset)), _stream(stream)), "vof_work_counts")
-    return dict(pairs=int(c[0]), cuts=int(c[1]), faces=int(c[2]))
+    return {k: int(c[i]) for i, k in enumerate(WORK)}
 
 
 def vof_probe_barrier(h, skip_block: int = -1, stream=None):

@@ -271,6 +271,125 @@ def test_positioning_converges_near_the_cube_corner(oracle_lib, a):
     assert worst_it > 20  # the stall branch was exercised
 
 
+# ------------------------------ generalised LSQ gradient (Sec. 2.2.1)
+
+@pytest.mark.parametrize("kind", ["hex", "tet"])
+def test_lsq_gradient_exact_for_linear_fields(oracle_lib, kind):
+    """The least-squares gradient reproduces the gradient of a linear field
+    exactly (every residual E_ck vanishes at it) on any cell whose stencil
+    spans three dimensions: boundary cells of jittered meshes included."""
+    m = I.hex_mesh((5, 4, 4), jitter=0.2, seed=71) if kind == "hex" else \
+        I.kuhn_tet_mesh((3, 3, 3), jitter=0.15, seed=72)
+    om = oracle_lib.OracleMesh(m)
+    cc, _, _, _ = om.geometry()
+    g0 = np.array([0.7, -1.3, 2.1])
+    phi = g0 @ cc + 0.4
+    g = om.lsq_gradient(phi)
+    assert np.abs(g - g0[:, None]).max() < 1e-11
+    assert np.abs(om.lsq_gradient(np.full(m.n_cells, 0.3))).max() < 1e-12
+
+
+def test_lsq_gradient_matches_weighted_least_squares(oracle_lib):
+    """Against numpy's weighted least squares (QR, not the normal equations)
+    on a random field, for cells of a jittered mesh: rows w_ck (x_k - x_c),
+    right-hand side w_ck (phi_k - phi_c), over the cells sharing a point."""
+    m = I.hex_mesh((4, 4, 3), jitter=0.2, seed=73)
+    om = oracle_lib.OracleMesh(m)
+    cc, _, _, _ = om.geometry()
+    phi = np.random.default_rng(74).uniform(0, 1, m.n_cells)
+    g = om.lsq_gradient(phi)
+    pts_of = [set(m.cell_verts[c]) for c in range(m.n_cells)]
+    for c in range(0, m.n_cells, 5):
+        nb = [k for k in range(m.n_cells) if k != c and pts_of[c] & pts_of[k]]
+        D = cc[:, nb].T - cc[:, c]
+        w = 1.0 / np.linalg.norm(D, axis=1)
+        ref = np.linalg.lstsq(D * w[:, None], (phi[nb] - phi[c]) * w, rcond=None)[0]
+        assert np.abs(g[:, c] - ref).max() < 1e-10 * max(1.0, np.abs(ref).max())
+
+
+def test_reconstruct_with_given_gradient(oracle_lib):
+    """Alg. 1 from a supplied gradient: the NAG gradient gives vo_reconstruct's
+    planes exactly; the LSQ gradient's planes still hold alpha V."""
+    w = I.make_workload("deform3d", n=10)
+    om = oracle_lib.OracleMesh(w.mesh)
+    a = w.alpha0
+    n0, d0, f0, _, _ = om.reconstruct(a)
+    n1, d1, f1, _, _ = om.reconstruct_grad(a, om.nag_gradient(a))
+    assert np.array_equal(f0, f1) and np.array_equal(n0, n1) and np.array_equal(d0, d1)
+    n2, d2, f2, _, st = om.reconstruct_grad(a, om.lsq_gradient(a))
+    assert st == 0 and np.array_equal(f0 & 5, f2 & 5)
+    _, vc, _, _ = om.geometry()
+    for c in np.flatnonzero(f2 & oracle_lib.ORIENTED)[:40]:
+        assert om.cut_volume(c, n2[:, c], d2[c]) / vc[c] == pytest.approx(a[c], abs=2e-13)
+
+
+# ------------------------------------ reconstruction error E_vsd (Sec. 4.1)
+
+def test_evsd_ball_volume_converges(oracle_lib):
+    """With no reconstruction E_vsd is the ball's volume in the cell; a ball
+    inside the unit cube gives 4/3 pi R^3 in the limit, the tangent-plane
+    pieces at the last level converging at second order (error / 4 a level)."""
+    m = I.hex_mesh((1, 1, 1))
+    om = oracle_lib.OracleMesh(m)
+    ex = 4.0 / 3.0 * math.pi * 0.3 ** 3
+    err = [om.evsd(None, None, None, [0.5, 0.5, 0.5, 0.3], L)[0] / ex - 1.0 for L in (4, 5, 6)]
+    assert 0 < err[2] < 2e-4
+    assert 3.0 < err[0] / err[1] < 5.0 and 3.0 < err[1] / err[2] < 5.0
+
+
+def test_evsd_half_space_identities(oracle_lib):
+    """A full cell's error is |C| - |C ^ B|; a plane through the centre of a
+    ball inside the unit cube leaves |B| + 1/2 - 2 |B|/2 = 1/2."""
+    m = I.hex_mesh((1, 1, 1))
+    om = oracle_lib.OracleMesh(m)
+    ball = [0.5, 0.5, 0.5, 0.3]
+    vb = om.evsd(None, None, None, ball, 5)[0]
+    full = om.evsd(np.array([oracle_lib.FULL], np.uint8), np.zeros(3), np.zeros(1), ball, 5)[0]
+    assert full == pytest.approx(1.0 - vb, abs=1e-14)
+    fl = np.array([oracle_lib.INTERFACE | oracle_lib.ORIENTED], np.uint8)
+    for nv in ([1.0, 0.0, 0.0], [0.0, 0.0, -1.0]):
+        n = np.array(nv)
+        e = om.evsd(fl, n, np.array([n @ np.array(ball[:3])]), ball, 5)[0]
+        assert e == pytest.approx(0.5, abs=1e-12)
+
+
+def test_evsd_monte_carlo(oracle_lib):
+    """E_vsd of oblique PLIC planes in jittered hexahedra against a
+    Monte-Carlo estimate of |(C ^ B) xor (C ^ H)| (points uniform in each
+    cell tetrahedron, by volume), within 5 sigma plus the resolution error."""
+    m = I.hex_mesh((2, 2, 2), jitter=0.2, seed=75)
+    om = oracle_lib.OracleMesh(m)
+    cc, vc, cf, _ = om.geometry()
+    rng = np.random.default_rng(76)
+    ball = np.array([0.45, 0.55, 0.5, 0.4])
+    n = rng.normal(size=(3, m.n_cells))
+    n /= np.linalg.norm(n, axis=0)
+    d = np.einsum("ic,ic->c", n, cc) + rng.uniform(-0.1, 0.1, m.n_cells)
+    fl = np.full(m.n_cells, oracle_lib.INTERFACE | oracle_lib.ORIENTED, np.uint8)
+    e = om.evsd(fl, n, d, ball, 6)
+    for c in range(m.n_cells):
+        # the cell's tetrahedra (cell centre, face centre, consecutive face points)
+        tets = []
+        for f in np.flatnonzero((m.owner == c) | (np.r_[m.neighbour, -np.ones(m.n_faces - m.n_internal, int)] == c)):
+            p = m.points[m.face_pts[m.face_ptr[f]:m.face_ptr[f + 1]]]
+            for i in range(len(p)):
+                tets.append(np.array([cc[:, c], cf[:, f], p[i], p[(i + 1) % len(p)]]))
+        tets = np.array(tets)
+        vols = np.abs(np.einsum("ti,ti->t", tets[:, 1] - tets[:, 0],
+                                np.cross(tets[:, 2] - tets[:, 0], tets[:, 3] - tets[:, 0]))) / 6
+        N = 20000
+        est, var = 0.0, 0.0
+        for T, V in zip(tets, vols):
+            b = rng.dirichlet(np.ones(4), N)
+            x = b @ T
+            inB = np.linalg.norm(x - ball[:3], axis=1) <= ball[3]
+            inH = x @ n[:, c] <= d[c]
+            p = np.mean(inB != inH)
+            est += V * p
+            var += V * V * p * (1 - p) / N
+        assert abs(e[c] - est) <= 5 * math.sqrt(var) + 2e-4 * vc[c], (c, e[c], est, math.sqrt(var))
+
+
 # ------------------------------------------------------------- A4/A5: sweep
 
 def test_uniform_sweep_volume_is_flux(oracle_lib):
