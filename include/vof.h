@@ -150,6 +150,25 @@ int vof_lsq_gradient(vof_ctx *ctx, const double *alpha, double *grad, void *stre
 int vof_evsd(vof_ctx *ctx, const uint8_t *flags, const double *n, const double *d, const double ball[4],
              int levels, double *evsd, void *stream);
 
+/* Geometric mapping of the volume fraction for adaptive refinement (Sec. 3,
+ * Alg. 2): the volume fractions alpha_dst [dst n_cells] of a new mesh (dst)
+ * from an old mesh of the same domain (src: alpha_src and its reconstruction
+ * n_src [3*src n_cells], d_src, flags_src as vof_reconstruct on src writes
+ * them).  pair_ptr [dst n_cells + 1] and pair_src (device, int32, caller-owned)
+ * are Alg. 2's cell map: per destination cell the source cells sharing volume
+ * with it, which must be nested with it -- the same cell, a cell containing it
+ * (refinement) or cells inside it (un-refinement), as one octree lattice
+ * gives.  A destination cell inside an oriented interface source takes the
+ * part of the source's PLIC polyhedron it holds (its cell tetrahedra clipped
+ * by the source plane); inside any other source it takes the source's
+ * fraction; a source inside it adds its whole phase volume; cells count as
+ * the same where their volumes agree to 1e-9.  The phase volume is conserved
+ * to the positioning tolerance.  Both contexts on one device (else
+ * VOF_ERR_INVALID_ARG); asynchronous on `stream`. */
+int vof_remap(vof_ctx *dst, const vof_ctx *src, const double *alpha_src, const double *n_src, const double *d_src,
+              const uint8_t *flags_src, const int32_t *pair_ptr, const int32_t *pair_src, double *alpha_dst,
+              void *stream);
+
 /* A4, Eq. idwpointphi: point velocity Up [3*n_points] from the cell velocity
  * Uc [3*n_cells] by inverse-distance weighting over the point's cells; at a
  * point on wall faces only the component tangent to the walls is kept. */

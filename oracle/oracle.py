@@ -57,6 +57,7 @@ def lib():
             "vo_reconstruct_grad": (I, [P, P, P, D, I, P, P, P, P, P]),
             "vo_lsq_gradient": (V, [P, P, I, P, P]),
             "vo_evsd": (V, [P, P, P, P, P, I, I, P, P]),
+            "vo_remap": (I, [P, P, P, P, P, P, P, P, P]),
             "vo_point_velocity": (V, [P, P, P]),
             "vo_swept_volume": (D, [P, I, P, D, D, D]),
             "vo_correct_flux": (I, [P, P, P, D, I, P, P, P]),
@@ -198,6 +199,16 @@ class OracleMesh:
         b = _f64(ball); out = np.zeros(self.nc)
         s = None if sel is None else _i32(sel)
         lib().vo_evsd(self.h, _p(fl), _p(n), _p(d), _p(b), int(levels), 0 if s is None else s.size, _p(s), _p(out))
+        return out
+
+    def remap_from(self, src, alpha_src, n_src, d_src, flags_src, pair_ptr, pair_src):
+        """Alg. 2: this mesh's volume fractions from the planes of `src` (an
+        OracleMesh of the same domain) over the cell pairs (CSR)."""
+        a = _f64(alpha_src); n = _f64(n_src).reshape(-1); d = _f64(d_src)
+        fl = np.ascontiguousarray(flags_src, np.uint8)
+        pp, ps = _i32(pair_ptr), _i32(pair_src)
+        out = np.zeros(self.nc)
+        lib().vo_remap(self.h, src.h, _p(a), _p(n), _p(d), _p(fl), _p(pp), _p(ps), _p(out))
         return out
 
     # A4/A5 -----------------------------------------------------------------

@@ -764,6 +764,47 @@ void vo_evsd(const vo_mesh *m, const unsigned char *flags, const double *n, cons
     }
 }
 
+/* ------------------------- geometric mapping for AMR (Sec. 3, Alg. 2) */
+/* The volume fraction of each destination cell from the interface planes of
+ * the source cells its cell map lists (pairs, CSR over destination cells).
+ * The cells of a pair are nested: the destination cell is the source cell,
+ * lies inside it (refined), or contains it (un-refined).  Its phase volume is
+ * the sum over its pairs of |PLIC polyhedron of the source ^ destination|:
+ *  - same cell: alpha_s V;
+ *  - destination inside an oriented interface source: the destination
+ *    cell's tetrahedra clipped by the source's plane n_s.x <= d_s;
+ *  - destination inside any other source (empty, full, unoriented): the
+ *    source's phase spread evenly, alpha_s V_dst (so no volume is lost to the
+ *    eps thresholds);
+ *  - source inside the destination: the source's whole phase, alpha_s V_s.
+ * Cells count as the same where their volumes agree to 1e-9. */
+int vo_remap(const vo_mesh *dst, const vo_mesh *src, const double *alpha_src, const double *n_src,
+             const double *d_src, const unsigned char *flags_src, const int *pair_ptr, const int *pair_src,
+             double *alpha_dst)
+{
+    int c;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (c = 0; c < dst->nc; c++) {
+        double Vc = dst->vc[c], acc = 0.0;
+        int q;
+        for (q = pair_ptr[c]; q < pair_ptr[c + 1]; q++) {
+            int s = pair_src[q];
+            double Vs = src->vc[s], as = alpha_src[s];
+            if (fabs(Vc - Vs) <= 1e-9 * Vs) acc += as * Vc;
+            else if (Vc < Vs) {
+                if ((flags_src[s] & VO_INTERFACE) && (flags_src[s] & VO_ORIENTED)) {
+                    v3 K[MAXK][4], n = mk(n_src[s], n_src[src->nc + s], n_src[2 * src->nc + s]);
+                    double dd = d_src[s];
+                    int nk = cell_tets(dst, c, K, MAXK), k;
+                    for (k = 0; k < nk; k++) acc += tet_clip(K[k][0], K[k][1], K[k][2], K[k][3], 1, &n, &dd, NULL);
+                } else acc += as * Vc;
+            } else acc += as * Vs;
+        }
+        alpha_dst[c] = acc / Vc;
+    }
+    return 0;
+}
+
 /* ------------------------------------------- A4: point velocity + sweep */
 void vo_point_velocity(const vo_mesh *m, const double *Uc, double *Up)
 {

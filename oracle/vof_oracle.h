@@ -84,6 +84,14 @@ void vo_lsq_gradient(const vo_mesh *m, const double *phi, int n_sel, const int *
 void vo_evsd(const vo_mesh *m, const unsigned char *flags, const double *n, const double *d,
              const double ball[4], int levels, int n_sel, const int *sel, double *out);
 
+/* geometric mapping of the volume fraction (Sec. 3, Alg. 2) from a source
+ * mesh (alpha, its reconstruction n, d, flags) onto a destination mesh of the
+ * same domain; pair_ptr [dst n_cells + 1] / pair_src list, per destination
+ * cell, the source cells sharing volume with it (nested cells) */
+int vo_remap(const vo_mesh *dst, const vo_mesh *src, const double *alpha_src, const double *n_src,
+             const double *d_src, const unsigned char *flags_src, const int *pair_ptr, const int *pair_src,
+             double *alpha_dst);
+
 /* Eq. idwpointphi applied to the cell velocity (3*nc SoA) -> point velocity; at
  * wall points only the component tangent to the walls is kept */
 void vo_point_velocity(const vo_mesh *m, const double *Uc, double *Up);

@@ -544,6 +544,18 @@ int vof_evsd(vof_ctx *c, const uint8_t *flags, const double *n, const double *d,
     return launch_evsd(c, flags, n, d, ball, levels, evsd, (cudaStream_t)stream);
 }
 
+int vof_remap(vof_ctx *dst, const vof_ctx *src, const double *alpha_src, const double *n_src, const double *d_src,
+              const uint8_t *flags_src, const int32_t *pair_ptr, const int32_t *pair_src, double *alpha_dst,
+              void *stream)
+{
+    if (!dst || !src || !alpha_src || !n_src || !d_src || !flags_src || !pair_ptr || !pair_src || !alpha_dst)
+        return VOF_ERR_INVALID_ARG;
+    if (dst->device != src->device) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(dst->device);
+    return launch_remap(dst, src, alpha_src, n_src, d_src, flags_src, pair_ptr, pair_src, alpha_dst,
+                        (cudaStream_t)stream);
+}
+
 int vof_flux_polyhedra(vof_ctx *c, const double *Up, const double *F, const double *lambda, double dt,
                        double *V, void *stream)
 {

@@ -133,6 +133,9 @@ int launch_lsq_gradient(vof_ctx *c, const double *alpha, const int *list, const 
                         cudaStream_t s);
 int launch_evsd(vof_ctx *c, const uint8_t *flags, const double *n, const double *d, const double ball[4],
                 int levels, double *out, cudaStream_t s);
+int launch_remap(vof_ctx *dst, const vof_ctx *src, const double *alpha_src, const double *n_src,
+                 const double *d_src, const uint8_t *flags_src, const int *pair_ptr, const int *pair_src,
+                 double *alpha_dst, cudaStream_t s);
 int launch_setup_geometry(vof_ctx *c, cudaStream_t s);
 int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t s);
 int launch_reconstruct(vof_ctx *c, const double *alpha, double *n, double *d, uint8_t *flags,

@@ -55,6 +55,8 @@ class Mesh:
     kind: str
     shape: tuple = ()
     wall: np.ndarray | None = None   # (n_faces - n_internal,) uint8: 1 = wall (no normal flow)
+    octree: dict | None = None       # octree meshes: lattice size N, levels, per cell level / origin /
+                                     # size in finest units, and the finest-lattice cell map
 
     @property
     def n_points(self) -> int:
@@ -191,7 +193,7 @@ def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = 
 # --------------------------------------------------------------------------
 
 def octree_mesh(n0: int = 64, levels: int = 2, center=(0.35, 0.35, 0.35), R: float = 0.15,
-                band: float = 3.0) -> Mesh:
+                band: float = 3.0, refine=None) -> Mesh:
     """Unit cube: an n0^3 lattice whose cells are split into 8 wherever the cell
     centre lies within band * (the cell's size) of the sphere |x - center| = R,
     level by level down to `levels` splits, then split further until every
@@ -206,12 +208,20 @@ def octree_mesh(n0: int = 64, levels: int = 2, center=(0.35, 0.35, 0.35), R: flo
     counter-clockwise about the owner's outward normal.  Boundary faces are
     walls.  cell_verts holds each box's 8 corners in the hex corner order.
     Integer lattice coordinates are in units of the finest size 1/(n0 2^levels).
+
+    ``refine(L, i, j, k, s)``, if given, replaces the sphere criterion: a mask
+    of the level-L cells (integer coordinates i, j, k at that level, size s in
+    finest units) to split.  The returned mesh carries ``octree``: the lattice
+    size N, the levels, per cell its level and origin and size (finest units),
+    and the (N, N, N) map from finest-lattice voxels to cells.
     """
     N = n0 << levels
     cen = np.asarray(center, float)
 
     def near(L, i, j, k):
         s = 1 << (levels - L)
+        if refine is not None:
+            return np.asarray(refine(L, i, j, k, s), bool)
         c = (np.stack([i, j, k], 1) * s + 0.5 * s) / N
         d = np.abs(np.sqrt(((c - cen) ** 2).sum(1)) - R)
         return d <= band * s / N
@@ -370,8 +380,10 @@ def octree_mesh(n0: int = 64, levels: int = 2, center=(0.35, 0.35, 0.35), R: flo
     face_ptr = np.concatenate([[0], np.cumsum(cnt)]).astype(np.int32)
     face_pts = Fall[Fall >= 0].astype(np.int32)          # row-major: each face's points in order
     owner = np.concatenate([own_i, own_b]).astype(np.int32)
+    octree = {"N": N, "levels": levels, "n0": n0, "level": lv, "origin": np.stack([ox, oy, oz], 1),
+              "size": sz, "cmap": cmap}
     return Mesh(pts, face_ptr, face_pts, owner, nei_i.astype(np.int32), nc, cell_verts, 1.0 / N, 3, "octree",
-                (n0, n0, n0), np.ones(own_b.size, np.uint8))
+                (n0, n0, n0), np.ones(own_b.size, np.uint8), octree)
 
 
 # --------------------------------------------------------------------------

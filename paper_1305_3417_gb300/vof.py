@@ -52,7 +52,7 @@ EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "v
            "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
            "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
            "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess", "vof_set_gradient", "vof_lsq_gradient",
-           "vof_evsd"]
+           "vof_evsd", "vof_remap"]
 GRAD_NAG, GRAD_LSQ = 0, 1
 MLP_IN, MLP_HID, MLP_OUT = 33, 64, 4
 MLP_NPARAM = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
@@ -107,6 +107,7 @@ def lib():
         "vof_set_gradient": (I, [P, I]),
         "vof_lsq_gradient": (I, [P, P, P, P]),
         "vof_evsd": (I, [P, P, P, P, ctypes.POINTER(ctypes.c_double), I, P, P]),
+        "vof_remap": (I, [P, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -306,6 +307,12 @@ def vof_evsd(h, flags, n, d, ball, levels, out, stream=None):
     _check(lib().vof_evsd(h, _ptr(flags) if flags is not None else None, _ptr(n) if n is not None else None,
                           _ptr(d) if d is not None else None, b, int(levels), _ptr(out), _stream(stream)),
            "vof_evsd")
+
+
+def vof_remap(dst, src, alpha_src, n_src, d_src, flags_src, pair_ptr, pair_src, alpha_dst, stream=None):
+    """Alg. 2: alpha_dst of context dst from src's planes over the cell pairs."""
+    _check(lib().vof_remap(dst, src, _ptr(alpha_src), _ptr(n_src), _ptr(d_src), _ptr(flags_src), _ptr(pair_ptr),
+                           _ptr(pair_src), _ptr(alpha_dst), _stream(stream)), "vof_remap")
 
 
 def vof_count_work(h, on: bool = True):

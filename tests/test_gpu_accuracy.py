@@ -125,7 +125,7 @@ def test_evsd_matches_oracle(torch, oracle_lib, name, grad):
     mixed = (ofl & O.INTERFACE) != 0
     print(f"{name} {grad}: E_vsd total {e.sum():.6e} over {mixed.sum()} interface cells "
           f"({e.sum() / (vc * a).sum():.3e} of the phase volume)")
-    assert e[mixed].sum() > 0 and e.sum() < 0.05 * (vc * a).sum()
+    assert e[mixed].sum() > 0 and e.sum() < 0.1 * (vc * a).sum()
 
 
 def test_evsd_argument_errors(torch, oracle_lib):
