@@ -61,7 +61,7 @@ BYTES_PER_FACE = 72.0
 # --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 --full-run 0);
 # valid while the kernel's sources hash to the captured digest, else null.
 TRAFFIC = {}
-TRAFFIC_SOURCES = ["paper_1305_3417_gb300/csrc/vof_mixed.cu", "paper_1305_3417_gb300/csrc/vof_device.cuh"]
+TRAFFIC_SOURCES = ["paper_1305_3417_gb300/csrc/vof_phase_flux.cu", "paper_1305_3417_gb300/csrc/vof_device.cuh"]
 
 
 def captured_traffic(workload, n, precision):

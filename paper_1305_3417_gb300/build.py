@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libvof.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["vof_kernels.cu", "vof_mixed.cu", "vof_api.cu", "vof_probe.cu", "vof_static.cu", "vof_batch.cu", "vof_mlp.cu"]
+SOURCES = ["vof_kernels.cu", "vof_phase_flux.cu", "vof_api.cu", "vof_probe.cu", "vof_static.cu", "vof_batch.cu",
+           "vof_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(os.path.dirname(HERE), "include")]

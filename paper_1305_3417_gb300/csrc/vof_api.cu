@@ -397,14 +397,16 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     }
     c->work = dev_alloc<unsigned long long>(c, WK_LEN, &err);
     c->cfpptr = dev_copy(c, cfpptr.data(), cfpptr.size(), &err);
-    c->cfl = dev_alloc<float4>(c, cface.size(), &err);
-    c->cfpl = dev_alloc<float4>(c, cfpptr[nc], &err);
-    c->fpl = dev_alloc<float4>(c, nfp, &err);
-    c->cbl = dev_alloc<float4>(c, 2 * (size_t)nc, &err);
+    // the phase-flux kernels' tables, 4-vectors of the context's form
+    const size_t e4 = phase_flux_table_entry_bytes(c->precision);
+    c->cfl = dev_alloc<unsigned char>(c, e4 * cface.size(), &err);
+    c->cfpl = dev_alloc<unsigned char>(c, e4 * cfpptr[nc], &err);
+    c->fpl = dev_alloc<unsigned char>(c, e4 * nfp, &err);
+    c->cbl = dev_alloc<unsigned char>(c, e4 * 2 * (size_t)nc, &err);
     c->palpha = dev_alloc<double>(c, np, &err);
     c->bpflag = dev_alloc<uint8_t>(c, np, &err);
     c->upb = dev_alloc<double>(c, 3 * (size_t)np, &err);
-    if (c->precision == VOF_MIXED) c->ktl = dev_alloc<float4>(c, 6 * (size_t)ctptr[nc], &err);
+    c->ktl = dev_alloc<unsigned char>(c, e4 * 6 * (size_t)ctptr[nc], &err);
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, WK_LEN * sizeof(unsigned long long));
     cudaMemset(c->bscr, 0, sizeof(double) * 4 * nc);

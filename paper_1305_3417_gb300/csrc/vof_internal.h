@@ -96,12 +96,15 @@ struct vof_ctx {
     int launches;
     unsigned long long *work;    // WK_LEN work counters
     int work_on;                 // 1: the step kernels count their work (instrumented variants)
-    // FP32 geometry for the mixed kernels
-    float4 *cfl, *cfpl, *fpl, *cbl;
+    // geometry of the phase-flux kernels, 4-vectors of the context's form (float4
+    // in a mixed context, four doubles in an FP64 one): face centres and face
+    // points relative to each cell centre (cfl, cfpl), face points relative to
+    // the face centre (fpl), cell boxes relative to the cell centre (cbl)
+    void *cfl, *cfpl, *fpl, *cbl;
     int *cfpptr;
-    // per cell tetrahedron (mixed contexts): 4 outward unit-normal planes and the
-    // box, 6 float4, relative to the cell centre (first of each cell: m.ctptr)
-    float4 *ktl;
+    // per cell tetrahedron: 4 outward unit-normal planes and the box, 6
+    // 4-vectors, relative to the cell centre (first of each cell: m.ctptr)
+    void *ktl;
     double *palpha;              // IDW point values of the points that are not all-empty / all-full
     uint8_t *bpflag;             // per point: a point of a band face this step (cleared by its reader)
     double *upb;                 // point velocities of the flagged points
@@ -152,7 +155,7 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
                   double *stats, cudaStream_t s,
                   cudaEvent_t wait_before_correct = nullptr);
 int launch_validate(vof_ctx *c, cudaStream_t s, unsigned *bad);
-// ---- mixed precision (vof_mixed.cu) ----
+// ---- phase-flux tables (vof_phase_flux.cu) ----
 int launch_setup_mixed(vof_ctx *c, cudaStream_t s);
 // regions of the global bounding step: region r = cells [reg_cell[r], reg_cell[r+1]) (host array)
 int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg);
@@ -164,8 +167,9 @@ int launch_barrier_probe(vof_ctx *c, int skip, cudaStream_t s);
 int launch_mlp_guess(vof_ctx *c, const double *alpha, const int *cells, const int *count, int nmax,
                      cudaStream_t s);
 int mlp_cap(const vof_ctx *c);
-int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
-                                const uint8_t *flags, const double *Up, const double *F, const double *lambda,
-                                double dt, double *Va, cudaStream_t s);
-int launch_phase_flux_mixed_list(vof_ctx *c, const double *alpha, const double *F, double dt, int sms,
-                                 cudaStream_t s);
+// phase flux (vof_phase_flux.cu): every face (the standalone call) or the band
+// list of a step, in the context's form (mixed FP32 or plain FP64)
+int launch_pf_all(vof_ctx *c, const double *alpha, const double *n, const double *d, const uint8_t *flags,
+                  const double *Up, const double *F, const double *lambda, double dt, double *Va, cudaStream_t s);
+int launch_pf_list(vof_ctx *c, const double *alpha, const double *F, double dt, int sms, cudaStream_t s);
+size_t phase_flux_table_entry_bytes(int precision);

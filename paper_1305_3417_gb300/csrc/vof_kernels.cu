@@ -820,198 +820,6 @@ __device__ double clip_tet(const Tet &T, const V3 *pn, const double *pd, int np,
     return vol;
 }
 
-struct PFArgs {
-    const double *alpha, *n, *d;
-    const uint8_t *flags;
-    const double *Up, *F, *lambda;
-    double dt;
-    double *Va;
-    const int *list, *count;
-    const double *disp;   // per list slot displacements (LIST mode)
-    unsigned *status;
-    unsigned long long *work;  // WK_LEN counters (vof_internal.h)
-    int *next;                 // LIST: next band slot to take (zero before the launch), or null
-};
-
-constexpr int PF_WARPS = 4;
-constexpr int PF_MAXT = 3 * VOF_MAXFP;
-
-template <bool LIST>
-__global__ void __launch_bounds__(PF_WARPS * 32) k_phase_flux(DevMesh m, PFArgs a)
-{
-    __shared__ Tet sT[PF_WARPS][PF_MAXT];
-    __shared__ double sSg[PF_WARPS][PF_MAXT];
-    __shared__ double sBox[PF_WARPS][PF_MAXT][6];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    const int total = LIST ? *a.count : m.nf;
-    const double eps = m.eps;
-    // LIST: a warp takes its next band face from a counter as it finishes one
-    // (face costs differ widely; a face's flux is one warp's work either way)
-    const bool dyn = LIST && a.next != nullptr;
-    auto take = [&]() {
-        int v = 0;
-        if (lane == 0) v = atomicAdd(a.next, 1);
-        return __shfl_sync(0xffffffffu, v, 0);
-    };
-    WkOn wk;
-    for (int item = dyn ? take() : warp; item < total; item = dyn ? take() : item + nwarps) {
-        const int f = LIST ? a.list[item] : item;
-        const long long s0 = __ldg(m.sptr + f), s1 = __ldg(m.sptr + f + 1);
-        if (!LIST) {
-            // trivial faces (reading R9) and boundary inflow
-            double Ff = a.F[f];
-            bool all_e = true, all_f = true;
-            for (long long s = s0 + lane; s < s1; s += 32) {
-                double al = a.alpha[__ldg(m.scell + s)];
-                all_e &= al <= eps;
-                all_f &= al >= 1.0 - eps;
-            }
-            all_e = __all_sync(0xffffffffu, all_e);
-            all_f = __all_sync(0xffffffffu, all_f);
-            double triv = 0.0;
-            bool done = true;
-            if (Ff == 0.0 || (f >= m.ni && Ff < 0.0) || all_e) triv = 0.0;
-            else if (all_f) triv = Ff * a.dt;
-            else done = false;
-            if (done) {
-                if (lane == 0) a.Va[f] = triv;
-                continue;
-            }
-        }
-        // ---- flux polyhedron tetrahedra, one per lane
-        const int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
-        const int nt = n == 3 ? 3 : 3 * n;
-        if (lane < nt) {
-            int pr = lane / 3, j = lane % 3;
-            V3 a0, a1, a2, w0, w1, w2;
-            long k0, k1, k2;
-            auto disp = [&](int i) -> V3 {  // i < 0: face centre
-                if (LIST) {
-                    const double *o = a.disp + (size_t)item * DISP_STRIDE + (i < 0 ? 0 : 3 + 3 * i);
-                    return mk(o[0], o[1], o[2]);
-                }
-                double lam = a.lambda[f];
-                if (lam < 0.0) {
-                    V3 S = ld3(m.sf, m.nf, f);
-                    return S * (-lam * a.F[f] * a.dt / dot(S, S));
-                }
-                if (i >= 0) return ld3(a.Up, m.np, __ldg(m.fpts + b + i)) * (a.dt * lam);
-                V3 wc = mk(0, 0, 0);
-                for (int q = 0; q < n; ++q) wc = wc + ld3(a.Up, m.np, __ldg(m.fpts + b + q)) * (a.dt * lam);
-                return wc * (1.0 / n);
-            };
-            if (n == 3) {
-                k0 = __ldg(m.fpts + b); k1 = __ldg(m.fpts + b + 1); k2 = __ldg(m.fpts + b + 2);
-                a0 = ldP(m, (int)k0); a1 = ldP(m, (int)k1); a2 = ldP(m, (int)k2);
-                w0 = disp(0); w1 = disp(1); w2 = disp(2);
-            } else {
-                int u = pr + 1 == n ? 0 : pr + 1;
-                k0 = -1; k1 = __ldg(m.fpts + b + pr); k2 = __ldg(m.fpts + b + u);
-                a0 = ld3(m.cf, m.nf, f); a1 = ldP(m, (int)k1); a2 = ldP(m, (int)k2);
-                w0 = disp(-1); w1 = disp(pr); w2 = disp(u);
-            }
-            int par = 1;
-            if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
-            if (k2 < k1) { V3 t = a1; a1 = a2; a2 = t; t = w1; w1 = w2; w2 = t; long q = k1; k1 = k2; k2 = q; par = -par; }
-            if (k1 < k0) { V3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
-            V3 b0 = a0 - w0, b1 = a1 - w1, b2 = a2 - w2;
-            Tet T;
-            if (j == 0) T = Tet{{a0, a1, a2, b2}};
-            else if (j == 1) T = Tet{{a0, a1, b2, b1}};
-            else T = Tet{{a0, b0, b1, b2}};
-            double sv = -par * tvol(T.v[0], T.v[1], T.v[2], T.v[3]);
-            sT[wib][lane] = T;
-            sSg[wib][lane] = sv > 0.0 ? 1.0 : (sv < 0.0 ? -1.0 : 0.0);
-            double *bx = sBox[wib][lane];
-            bx[0] = fmin(fmin(T.v[0].x, T.v[1].x), fmin(T.v[2].x, T.v[3].x));
-            bx[1] = fmin(fmin(T.v[0].y, T.v[1].y), fmin(T.v[2].y, T.v[3].y));
-            bx[2] = fmin(fmin(T.v[0].z, T.v[1].z), fmin(T.v[2].z, T.v[3].z));
-            bx[3] = fmax(fmax(T.v[0].x, T.v[1].x), fmax(T.v[2].x, T.v[3].x));
-            bx[4] = fmax(fmax(T.v[0].y, T.v[1].y), fmax(T.v[2].y, T.v[3].y));
-            bx[5] = fmax(fmax(T.v[0].z, T.v[1].z), fmax(T.v[2].z, T.v[3].z));
-        }
-        __syncwarp();
-        // ---- (tetrahedron, stencil cell) pairs over the lanes
-        double acc = 0.0;
-        wk.face();
-        const int ns = (int)(s1 - s0), nitems = nt * ns;
-        for (int w = lane; w < nitems; w += 32) {
-            const int t = w % nt, c = __ldg(m.scell + s0 + w / nt);
-            const double sg = sSg[wib][t];
-            if (sg == 0.0) continue;
-            const double al = a.alpha[c];
-            if (al <= eps) continue;  // empty cell carries no phase
-            const double *bx = sBox[wib][t];
-            const double *cb = m.cbox + 6 * (size_t)c;
-            if (bx[3] < cb[0] || cb[3] < bx[0] || bx[4] < cb[1] || cb[4] < bx[1] || bx[5] < cb[2] || cb[5] < bx[2])
-                continue;
-            const Tet &T = sT[wib][t];
-            double wgt = 1.0;
-            bool useH = false;
-            V3 hn = mk(0, 0, 0);
-            double hd = 0.0;
-            if (al < 1.0 - eps) {
-                if (a.flags[c] & VOF_ORIENTED) {
-                    hn = ld3(a.n, m.nc, c);
-                    hd = a.d[c];
-                    int nin = 0;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) nin += dot(hn, T.v[i]) - hd <= 0.0;
-                    if (nin == 0) continue;
-                    useH = nin < 4;
-                } else wgt = al;  // unoriented mixed cell: homogeneous
-            }
-            const V3 ctr = ld3(m.cc, m.nc, c);
-            double vsum = 0.0;
-            for (int k = __ldg(m.cptr + c); k < __ldg(m.cptr + c + 1); ++k) {
-                const int code = __ldg(m.cface + k), g = code >> 1;
-                const int gn = __ldg(m.fptr + g + 1) - __ldg(m.fptr + g);
-                const int gt = gn == 3 ? 1 : gn;
-                for (int tt = 0; tt < gt; ++tt) {
-                    V3 k1, k2, k3;
-                    face_tri(m, g, tt, code & 1, k1, k2, k3);
-                    // K = (ctr, k1, k2, k3), positively oriented
-                    double lx = fmin(fmin(ctr.x, k1.x), fmin(k2.x, k3.x)), hx = fmax(fmax(ctr.x, k1.x), fmax(k2.x, k3.x));
-                    if (hx < bx[0] || bx[3] < lx) continue;
-                    double ly = fmin(fmin(ctr.y, k1.y), fmin(k2.y, k3.y)), hy = fmax(fmax(ctr.y, k1.y), fmax(k2.y, k3.y));
-                    if (hy < bx[1] || bx[4] < ly) continue;
-                    double lz = fmin(fmin(ctr.z, k1.z), fmin(k2.z, k3.z)), hz = fmax(fmax(ctr.z, k1.z), fmax(k2.z, k3.z));
-                    if (hz < bx[2] || bx[5] < lz) continue;
-                    wk.add(WK_TEST, 4);  // T's points against K's four planes
-                    V3 pn[5];
-                    double pd[5];
-                    // outward planes of (ctr,k1,k2,k3): faces (ctr,k2,k1),(ctr,k1,k3),(ctr,k3,k2),(k1,k2,k3)
-                    pn[0] = cross(k2 - ctr, k1 - ctr); pd[0] = dot(pn[0], ctr);
-                    pn[1] = cross(k1 - ctr, k3 - ctr); pd[1] = dot(pn[1], ctr);
-                    pn[2] = cross(k3 - ctr, k2 - ctr); pd[2] = dot(pn[2], ctr);
-                    pn[3] = cross(k2 - k1, k3 - k1);   pd[3] = dot(pn[3], k1);
-                    int np = 0;
-                    V3 an[5];
-                    double ad[5];
-                    bool outside = false;
-                    for (int q = 0; q < 4; ++q) {
-                        int nin = 0;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) nin += dot(pn[q], T.v[i]) - pd[q] <= 0.0;
-                        if (nin == 0) { outside = true; break; }
-                        if (nin < 4) { an[np] = pn[q]; ad[np] = pd[q]; ++np; }
-                    }
-                    if (outside) continue;
-                    if (useH) { an[np] = hn; ad[np] = hd; ++np; }
-                    vsum += clip_tet(T, an, ad, np, a.status, wk);
-                }
-            }
-            acc += sg * wgt * vsum;
-        }
-        acc = warp_sum(acc);
-        if (lane == 0) a.Va[f] = acc;
-        __syncwarp();
-    }
-    if (a.work) wk.flush(a.work, lane);
-}
-
 // ============================================================ update (A7)
 constexpr int UPD_THREADS = 256;
 constexpr int UPD_BLOCKS = 1024;
@@ -2067,14 +1875,9 @@ int launch_correct_all(vof_ctx *c, const double *Up, const double *F, double dt,
 }
 
 int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, const double *d, const uint8_t *flags,
-                          const double *Up, const double *F, const double *lambda, double dt, double *Va,
-                          cudaStream_t s)
+                          const double *Up, const double *F, const double *lambda, double dt, double *Va, cudaStream_t s)
 {
-    if (c->precision == VOF_MIXED) return launch_phase_flux_mixed_all(c, alpha, n, d, flags, Up, F, lambda, dt, Va, s);
-    PFArgs a{alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr, c->status, nullptr};
-    k_phase_flux<false><<<cdiv((long)c->nf * 32, PF_WARPS * 32), PF_WARPS * 32, 0, s>>>(c->m, a);
-    LAUNCH_CHECK();
-    return VOF_OK;
+    return launch_pf_all(c, alpha, n, d, flags, Up, F, lambda, dt, Va, s);
 }
 
 // The bounding pass, post-bounding mass and statistics: one cooperative
@@ -2197,13 +2000,9 @@ int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, 
     MARK(2);
     if (cudaStreamWaitEvent(s, c->ev_join, 0) != cudaSuccess) return VOF_ERR_CUDA;
     MARK(3);
-    if (c->precision == VOF_MIXED) {
-        int r = launch_phase_flux_mixed_list(c, alpha, F, dt, sms, s);
+    {
+        int r = launch_pf_list(c, alpha, F, dt, sms, s);
         if (r) return r;
-    } else {
-        PFArgs a{alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band, cnt + CNT_BAND, c->disp_b,
-                 c->status, c->work_on ? c->work : nullptr, cnt + CNT_PFNEXT};
-        k_phase_flux<true><<<sms * 16, PF_WARPS * 32, 0, s>>>(m, a);
     }
     launches += 4;  // reconstruct, band point velocities, correct, phase flux
     LAUNCH_CHECK();

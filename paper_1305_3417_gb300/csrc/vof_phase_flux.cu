@@ -1,11 +1,14 @@
-// Mixed-precision phase flux (A6): the flux-polyhedron tetrahedra T, the cell
-// tetrahedra K and the PLIC planes are taken to a frame centred on the face
-// centre and clipped in FP32; the pieces are summed per lane with TwoSum
-// compensation and finished in FP64.
+// Phase flux (A6, Eqs. S'_f, S''_f): the flux-polyhedron tetrahedra T of a
+// band face, the cell tetrahedra K of its stencil cells and their PLIC planes
+// are taken to a frame centred on the face centre and intersected there, one
+// warp per face.  One source for both forms:
+//  - mixed (R = float): FP32 clipping, pieces summed per lane with TwoSum
+//    compensation and finished in FP64 (reading R13 on the on-plane band);
+//  - plain (R = double): the same structure in FP64 throughout.
 //
 // Only the frame shift of a stencil cell (its centre minus the face centre) and
 // of its plane offset are formed in FP64; the cell's own geometry comes from
-// FP32 offsets to the cell centre computed once at context creation, so the
+// offsets to the cell centre computed once at context creation, so the
 // rounding of a coordinate is relative to the cell size, not to its position.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -17,61 +20,100 @@
 namespace {
 using namespace vofd;
 
-struct F3 { float x, y, z; };
-__device__ __forceinline__ F3 f3(float x, float y, float z) { return F3{x, y, z}; }
-__device__ __forceinline__ F3 operator+(F3 a, F3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ F3 operator-(F3 a, F3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ F3 operator*(F3 a, float s) { return f3(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ float fdot(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ F3 fcross(F3 a, F3 b)
+// ------------------------------------------------------------ real types
+template <class R>
+struct R3 { R x, y, z; };
+struct __align__(16) D4 { double x, y, z, w; };
+template <class R> struct Q4;
+template <> struct Q4<float> { using T = float4; };
+template <> struct Q4<double> { using T = D4; };
+template <class R> using R4 = typename Q4<R>::T;
+
+template <class R> __device__ __forceinline__ R3<R> r3(R x, R y, R z) { return R3<R>{x, y, z}; }
+template <class R> __device__ __forceinline__ R3<R> operator+(R3<R> a, R3<R> b) { return r3(a.x + b.x, a.y + b.y, a.z + b.z); }
+template <class R> __device__ __forceinline__ R3<R> operator-(R3<R> a, R3<R> b) { return r3(a.x - b.x, a.y - b.y, a.z - b.z); }
+template <class R> __device__ __forceinline__ R3<R> operator*(R3<R> a, R s) { return r3(a.x * s, a.y * s, a.z * s); }
+template <class R> __device__ __forceinline__ R rdot(R3<R> a, R3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class R> __device__ __forceinline__ R3<R> rcross(R3<R> a, R3<R> b)
 {
-    return f3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+    return r3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
 }
-__device__ __forceinline__ float fvol6(F3 a, F3 b, F3 c, F3 d) { return fdot(b - a, fcross(c - a, d - a)); }
-__device__ __forceinline__ F3 ld4(const float4 *p, long i)
+template <class R> __device__ __forceinline__ R rvol6(R3<R> a, R3<R> b, R3<R> c, R3<R> d)
 {
-    float4 v = __ldg(p + i);
-    return f3(v.x, v.y, v.z);
+    return rdot(b - a, rcross(c - a, d - a));
+}
+__device__ __forceinline__ float rmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double rmin(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float rmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double rmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float rabs(float a) { return fabsf(a); }
+__device__ __forceinline__ float rfma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rfma(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float rnext(float a, float b) { return nextafterf(a, b); }
+__device__ __forceinline__ double rnext(double a, double b) { return nextafter(a, b); }
+__device__ __forceinline__ double rabs(double a) { return fabs(a); }
+// divisions of the clip: the fast FP32 reciprocal-multiply (2 ulp, far inside
+// the mixed form's rounding) or a correctly rounded FP64 division
+__device__ __forceinline__ float rdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double rdiv(double a, double b) { return a / b; }
+
+template <class R> __device__ __forceinline__ R4<R> mk4(R x, R y, R z, R w);
+template <> __device__ __forceinline__ float4 mk4<float>(float x, float y, float z, float w) { return make_float4(x, y, z, w); }
+template <> __device__ __forceinline__ D4 mk4<double>(double x, double y, double z, double w) { return D4{x, y, z, w}; }
+__device__ __forceinline__ float4 ldg4(const float4 *p, long i) { return __ldg(p + i); }
+__device__ __forceinline__ D4 ldg4(const D4 *p, long i)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p + i);
+    const double2 a = __ldg(q), b = __ldg(q + 1);
+    return D4{a.x, a.y, b.x, b.y};
+}
+template <class R> __device__ __forceinline__ R3<R> ld43(const R4<R> *p, long i)
+{
+    const R4<R> v = ldg4(p, i);
+    return r3<R>(v.x, v.y, v.z);
 }
 
 // fraction of a tetrahedron below level 0 for sorted vertex values h0..h3
-// (fast reciprocal divisions: 2 ulp, far inside the form's FP32 rounding)
-__device__ __forceinline__ float ffrac_below(float h0, float h1, float h2, float h3)
+template <class R>
+__device__ __forceinline__ R rfrac_below(R h0, R h1, R h2, R h3)
 {
-    if (0.0f <= h0) return 0.0f;
-    if (0.0f >= h3) return 1.0f;
-    if (0.0f <= h1) {
-        float x = -h0;
-        return __fdividef(x, h1 - h0) * __fdividef(x, h2 - h0) * __fdividef(x, h3 - h0);
+    if (R(0) <= h0) return R(0);
+    if (R(0) >= h3) return R(1);
+    if (R(0) <= h1) {
+        const R x = -h0;
+        return rdiv(x, h1 - h0) * rdiv(x, h2 - h0) * rdiv(x, h3 - h0);
     }
-    if (0.0f >= h2) {
-        float y = h3;
-        return 1.0f - __fdividef(y, h3 - h0) * __fdividef(y, h3 - h1) * __fdividef(y, h3 - h2);
+    if (R(0) >= h2) {
+        const R y = h3;
+        return R(1) - rdiv(y, h3 - h0) * rdiv(y, h3 - h1) * rdiv(y, h3 - h2);
     }
-    float a = __fdividef(-h0, h2 - h0), b = __fdividef(-h0, h3 - h0);
-    float c = __fdividef(-h1, h2 - h1), e = __fdividef(-h1, h3 - h1);
-    return a * b + a * (1.0f - b) * e + (1.0f - a) * c * e;
+    const R a = rdiv(-h0, h2 - h0), b = rdiv(-h0, h3 - h0);
+    const R c = rdiv(-h1, h2 - h1), e = rdiv(-h1, h3 - h1);
+    return a * b + a * (R(1) - b) * e + (R(1) - a) * c * e;
 }
 
-__device__ __forceinline__ void fsort4(float &a, float &b, float &c, float &d)
+template <class R>
+__device__ __forceinline__ void rsort4(R &a, R &b, R &c, R &d)
 {
-    float t;
+    R t;
 #define CS(p, q) if (p > q) { t = p; p = q; q = t; }
     CS(a, b) CS(c, d) CS(a, c) CS(b, d) CS(b, c)
 #undef CS
 }
 
-struct FTet { F3 v[4]; };
+template <class R> struct RTet { R3<R> v[4]; };
 
-// TwoSum (Knuth): s + c carries the running sum exactly up to the last addend's
-// rounding; no multiplications, so no fused operation can change it
-__device__ __forceinline__ void two_sum(float &s, float &c, float x)
+// Running sum of the pieces: FP32 with TwoSum (Knuth) compensation, s + c
+// carrying the sum exactly up to the last addend's rounding (no
+// multiplications, so no fused operation can change it); FP64 plainly.
+__device__ __forceinline__ void acc_add(float &s, float &c, float x)
 {
     float t = s + x;
     float bp = t - s;
     c += (s - (t - bp)) + (x - bp);
     s = t;
 }
+__device__ __forceinline__ void acc_add(double &s, double &, double x) { s += x; }
 
 constexpr int MX_MAXT = 3 * VOF_MAXFP;
 static_assert(MX_MAXT <= 32, "one flux-polyhedron tetrahedron per lane");
@@ -86,8 +128,7 @@ struct MXArgs {
     const double *disp, *lam_b;
     unsigned *status;
     unsigned long long *work;
-    const float4 *fpl, *cbl;  // FP32 face points (face frame), cell boxes (cell frame)
-    const float4 *ktl;        // cell tetrahedra: planes and box (cell frame)
+    const void *fpl, *cbl, *ktl;  // the context's tables (R4 of the form's type)
     const int *ctptr;
     int *next;                // list form: next band slot to take (zero before the launch), or null
 };
@@ -96,24 +137,25 @@ constexpr int MX_CAND = 32;    // candidate cell tetrahedra buffered per warp: o
 constexpr int MX_QUEUE = MX_MAXT * MX_CAND;  // clip jobs: one per (T, K) pair at most
 constexpr int MX_STACK = 92;                 // pieces of clip jobs waiting for their next plane
 
-// per warp; the 48-byte tetrahedra are moved as three float4 (conflict-free
-// across a warp)
+// per warp; in FP32 the 48-byte tetrahedra are moved as three float4
+// (conflict-free across a warp)
+template <class R>
 struct __align__(16) MXShared {
-    FTet S[MX_STACK];        // pieces
-    FTet T[MX_MAXT];         // flux-polyhedron tetrahedra
-    float4 Kp[MX_CAND][5];   // outward unit-normal planes of the candidate cell tetrahedra, then
-                             // the cell's phase (or void) half-space; 80-byte rows: a warp's
+    RTet<R> S[MX_STACK];     // pieces
+    RTet<R> T[MX_MAXT];      // flux-polyhedron tetrahedra
+    R4<R> Kp[MX_CAND][5];    // outward unit-normal planes of the candidate cell tetrahedra, then
+                             // the cell's phase (or void) half-space; 80-byte rows (FP32): a warp's
                              // float4 reads of different rows are conflict-free
-    float4 P6[VOF_MAXFP][5]; // per prism (face triangle swept): a0 a1 a2 b0 b1 b2, 18 floats in 80 bytes
-    float Pb[VOF_MAXFP][6];  // prism box
-    float Kb[MX_CAND][6];
-    float Tv6[MX_MAXT];      // |6 vol(T)|
-    float Tsg[MX_MAXT];      // sign of T in the flux polyhedron
-    float Kw[MX_CAND];       // weight: 1, or alpha (1-alpha) of an unoriented cell
+    R4<R> P6[VOF_MAXFP][5];  // per prism (face triangle swept): a0 a1 a2 b0 b1 b2, 18 values in 20
+    R Pb[VOF_MAXFP][6];      // prism box
+    R Kb[MX_CAND][6];
+    R Tv6[MX_MAXT];          // |6 vol(T)|
+    R Tsg[MX_MAXT];          // sign of T in the flux polyhedron
+    R Kw[MX_CAND];           // weight: 1, or alpha (1-alpha) of an unoriented cell
     // stencil cells of the current chunk that reach the polyhedron's box
-    float4 CH[32];           // phase (or void) half-space
-    float Cdc[32][3];        // cell centre - face centre
-    float Cw[32];
+    R4<R> CH[32];            // phase (or void) half-space
+    R Cdc[32][3];            // cell centre - face centre
+    R Cw[32];
     int Ct0[32];             // first tetrahedron
     int Cend[32];            // running count of tetrahedra, inclusive
     unsigned short Sm[MX_STACK];  // piece: t | k << 5 | planes still to clip << 10
@@ -123,34 +165,37 @@ struct __align__(16) MXShared {
     unsigned char CuseH[32];
 };
 
-__device__ __forceinline__ FTet ldT(const FTet &t)
+__device__ __forceinline__ RTet<float> ldT(const RTet<float> &t)
 {
     const float4 *p = reinterpret_cast<const float4 *>(&t);
     const float4 a = p[0], b = p[1], c = p[2];
-    return FTet{{f3(a.x, a.y, a.z), f3(a.w, b.x, b.y), f3(b.z, b.w, c.x), f3(c.y, c.z, c.w)}};
+    return RTet<float>{{r3(a.x, a.y, a.z), r3(a.w, b.x, b.y), r3(b.z, b.w, c.x), r3(c.y, c.z, c.w)}};
 }
+__device__ __forceinline__ RTet<double> ldT(const RTet<double> &t) { return t; }
 
-__device__ __forceinline__ void stT(FTet &t, const FTet &v)
+__device__ __forceinline__ void stT(RTet<float> &t, const RTet<float> &v)
 {
     float4 *p = reinterpret_cast<float4 *>(&t);
     p[0] = make_float4(v.v[0].x, v.v[0].y, v.v[0].z, v.v[1].x);
     p[1] = make_float4(v.v[1].y, v.v[1].z, v.v[2].x, v.v[2].y);
     p[2] = make_float4(v.v[2].z, v.v[3].x, v.v[3].y, v.v[3].z);
 }
+__device__ __forceinline__ void stT(RTet<double> &t, const RTet<double> &v) { t = v; }
 
 // signed distances of the vertices to plane p, those within tol taken as 0;
 // nin / nup count the vertices strictly below / above
-__device__ __forceinline__ void fdist(const FTet &t, float4 p, float tol, float s[4], int &nin, int &nup)
+template <class R>
+__device__ __forceinline__ void fdist(const RTet<R> &t, R4<R> p, R tol, R s[4], int &nin, int &nup)
 {
     nin = 0;
     nup = 0;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        float v = p.x * t.v[i].x + p.y * t.v[i].y + p.z * t.v[i].z - p.w;
-        if (fabsf(v) <= tol) v = 0.0f;
+        R v = p.x * t.v[i].x + p.y * t.v[i].y + p.z * t.v[i].z - p.w;
+        if (rabs(v) <= tol) v = R(0);
         s[i] = v;
-        nin += v < 0.0f;
-        nup += v > 0.0f;
+        nin += v < R(0);
+        nup += v > R(0);
     }
 }
 
@@ -158,24 +203,25 @@ __device__ __forceinline__ void fdist(const FTet &t, float4 p, float tol, float 
 // below, at least one strictly above) as one tetrahedron (nin == 1) or three,
 // each handed to put(tet, i); vertices are ordered below-first by a
 // compare-exchange network so that every index stays static
-template <class Put>
-__device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin, Put put)
+template <class R, class Put>
+__device__ __forceinline__ void fsplit(const RTet<R> &t, const R s[4], int nin, Put put)
 {
-    F3 P0 = t.v[0], P1 = t.v[1], P2 = t.v[2], P3 = t.v[3];
-    float S0 = s[0], S1 = s[1], S2 = s[2], S3 = s[3];
+    using V = R3<R>;
+    V P0 = t.v[0], P1 = t.v[1], P2 = t.v[2], P3 = t.v[3];
+    R S0 = s[0], S1 = s[1], S2 = s[2], S3 = s[3];
 #define MX_CX(a, b)                                                   \
-    if (!(S##a < 0.0f) && S##b < 0.0f) {                              \
-        F3 tp = P##a; P##a = P##b; P##b = tp;                         \
-        float ts = S##a; S##a = S##b; S##b = ts;                      \
+    if (!(S##a < R(0)) && S##b < R(0)) {                              \
+        V tp = P##a; P##a = P##b; P##b = tp;                          \
+        R ts = S##a; S##a = S##b; S##b = ts;                          \
     }
     MX_CX(0, 1) MX_CX(2, 3) MX_CX(0, 2) MX_CX(1, 3) MX_CX(1, 2)
 #undef MX_CX
-    auto ep = [](F3 a, float sa, F3 b, float sb) { return a + (b - a) * __fdividef(sa, sa - sb); };
+    auto ep = [](V a, R sa, V b, R sb) { return a + (b - a) * rdiv(sa, sa - sb); };
     if (nin == 1) {
-        put(FTet{{P0, ep(P0, S0, P1, S1), ep(P0, S0, P2, S2), ep(P0, S0, P3, S3)}}, 0);
+        put(RTet<R>{{P0, ep(P0, S0, P1, S1), ep(P0, S0, P2, S2), ep(P0, S0, P3, S3)}}, 0);
         return;
     }
-    F3 a0, a1, a2, b0, b1, b2;
+    V a0, a1, a2, b0, b1, b2;
     if (nin == 2) {
         a0 = P0; a1 = ep(P0, S0, P2, S2); a2 = ep(P0, S0, P3, S3);
         b0 = P1; b1 = ep(P1, S1, P2, S2); b2 = ep(P1, S1, P3, S3);
@@ -183,9 +229,9 @@ __device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin,
         a0 = P0; a1 = P1; a2 = P2;
         b0 = ep(P0, S0, P3, S3); b1 = ep(P1, S1, P3, S3); b2 = ep(P2, S2, P3, S3);
     }
-    put(FTet{{a0, a1, a2, b2}}, 0);
-    put(FTet{{a0, a1, b2, b1}}, 1);
-    put(FTet{{a0, b0, b1, b2}}, 2);
+    put(RTet<R>{{a0, a1, a2, b2}}, 0);
+    put(RTet<R>{{a0, a1, b2, b1}}, 1);
+    put(RTet<R>{{a0, b0, b1, b2}}, 2);
 }
 
 // The queued clip jobs, worked through by the whole warp, one piece per lane
@@ -203,8 +249,8 @@ __device__ __forceinline__ void fsplit(const FTet &t, const float s[4], int nin,
 // piece has at most 4 planes to go, so the split pieces keep i + 1 + 2 (r - 1)
 // <= MX_STACK for depth i and r planes to go: the top one alone always fits
 // once the leaves are gone, and the stacks cannot overflow.
-template <class Wk>
-__device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &accs, float &accc, Wk &wk)
+template <class R, class Wk>
+__device__ __forceinline__ void mx_clip(MXShared<R> &sh, int nq, R tol, R &accs, R &accc, Wk &wk)
 {
     const int lane = threadIdx.x & 31;
     const unsigned le = ((1u << lane) << 1) - 1u;
@@ -219,25 +265,25 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
             force_leaf = false;
             const int p = min(nl, 32);
             if (lane < p) {
-                const FTet t = ldT(sh.S[nl - 1 - lane]);
+                const RTet<R> t = ldT(sh.S[nl - 1 - lane]);
                 const unsigned meta = sh.Sm[nl - 1 - lane];
                 const int ti = meta & 31, k = (meta >> 5) & 31, j = __ffs(meta >> 10) - 1;
-                float sd[4];
+                R sd[4];
                 int nin, nup;
                 fdist(t, sh.Kp[k][j], tol, sd, nin, nup);
                 wk.add(WK_TEST, 1);
-                float v6 = 0.0f;
+                R v6 = R(0);
                 if (nin > 0) {
-                    v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    v6 = rabs(rvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
                     wk.add(WK_VOL, 1);
                     if (nup > 0) {
                         wk.add(WK_FRAC, 1);
-                        float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
-                        fsort4(h0, h1, h2, h3);
-                        v6 *= ffrac_below(h0, h1, h2, h3);
+                        R h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
+                        rsort4(h0, h1, h2, h3);
+                        v6 *= rfrac_below(h0, h1, h2, h3);
                     }
                 }
-                if (v6 != 0.0f) two_sum(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
+                if (v6 != R(0)) acc_add(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
             }
             nl -= p;
             __syncwarp();
@@ -246,7 +292,7 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
         // ---- split step
         const int p = min(nn, 32), r = min(32 - p, nq - qn);
         const bool act = lane < p + r;
-        FTet t;
+        RTet<R> t;
         unsigned meta = 0;
         if (lane < p) {
             t = ldT(sh.S[MX_STACK - nn + lane]);
@@ -258,7 +304,7 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
         __syncwarp();  // every piece read before the pushes reuse the slots
         int nch = 0, nin = 0, nup = 0, ti = 0, k = 0;
         unsigned rem = 0;
-        float sd[4], v6 = 0.0f;
+        R sd[4], v6 = R(0);
         bool cut = false;
         unsigned lw = 0;  // this lane's leaf work: 1 volume, 2 cut fraction
         if (act) {
@@ -272,13 +318,13 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
                 if (nup > 0) cut = true;
                 if (rem != 0) nch = nup == 0 || nin == 1 ? 1 : 3;
                 else {  // a job with one plane: its leaf here
-                    v6 = fabsf(fvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
+                    v6 = rabs(rvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
                     lw = 1;
                     if (nup > 0) {
                         lw = 3;
-                        float h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
-                        fsort4(h0, h1, h2, h3);
-                        v6 *= ffrac_below(h0, h1, h2, h3);
+                        R h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
+                        rsort4(h0, h1, h2, h3);
+                        v6 *= rfrac_below(h0, h1, h2, h3);
                     }
                 }
             }
@@ -303,13 +349,13 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
             wk.add(WK_VOL, lw & 1);
             wk.add(WK_FRAC, lw >> 1);
             if (cut && nch > 0) wk.add(WK_EDGE, nin == 2 ? 4 : 3);
-            if (v6 != 0.0f) two_sum(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
+            if (v6 != R(0)) acc_add(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
             if (nch > 0) {
                 const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
                 // parts of the lanes before this one that go the same way
                 const unsigned same = (toleaf ? bl : ~bl) & ((1u << lane) - 1u);
                 const int before = __popc(b0 & same) + 2 * __popc(b1 & same);
-                auto put = [&](const FTet &c, int i) {
+                auto put = [&](const RTet<R> &c, int i) {
                     const int at = toleaf ? nl + before + i : top - 1 - before - i;
                     stT(sh.S[at], c);
                     sh.Sm[at] = (unsigned short)cm;
@@ -332,21 +378,20 @@ __device__ __forceinline__ void mx_clip(MXShared &sh, int nq, float tol, float &
 // distances of the prism's six points to K's planes, from which each of its
 // three tetrahedra is classified: outside a plane, inside every plane (adds
 // |T| at once), or a clip job.
-template <class Wk>
-__device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float tol, float &accs, float &accc,
-                                         Wk &wk)
+template <class R, class Wk>
+__device__ __forceinline__ void mx_flush(MXShared<R> &sh, int nt, int ncand, R tol, R &accs, R &accc, Wk &wk)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int nprism = nt / 3;
     int total = 0;
     {
-        float kb[6];
+        R kb[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) kb[q] = lane < ncand ? sh.Kb[lane][q] : 0.0f;
+        for (int q = 0; q < 6; ++q) kb[q] = lane < ncand ? sh.Kb[lane][q] : R(0);
         for (int pr = 0; pr < nprism; ++pr) {
-            const float *tb = sh.Pb[pr];
-            const bool live = sh.Tsg[3 * pr] != 0.0f || sh.Tsg[3 * pr + 1] != 0.0f || sh.Tsg[3 * pr + 2] != 0.0f;
+            const R *tb = sh.Pb[pr];
+            const bool live = sh.Tsg[3 * pr] != R(0) || sh.Tsg[3 * pr + 1] != R(0) || sh.Tsg[3 * pr + 2] != R(0);
             const bool ov = lane < ncand && live &&
                             !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] || tb[5] < kb[2] ||
                               kb[5] < tb[2]);
@@ -364,10 +409,10 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
         if (pi < total) {
             const unsigned pc = sh.PQ[pi];
             const int pr = pc & 7, k = pc >> 3;
-            float v[20];
+            R v[20];
 #pragma unroll
             for (int i = 0; i < 5; ++i) {
-                const float4 q = sh.P6[pr][i];
+                const R4<R> q = sh.P6[pr][i];
                 v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
             }
             const int npl = sh.KuseH[k] ? 5 : 4;
@@ -379,16 +424,16 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
             // it only when its points lie clearly on both sides
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
-                const float4 pl = sh.Kp[k][q];
-                float d[6];
+                const R4<R> pl = sh.Kp[k][q];
+                R d[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i)
-                    d[i] = fmaf(pl.x, v[3 * i], fmaf(pl.y, v[3 * i + 1], fmaf(pl.z, v[3 * i + 2], -pl.w)));
+                    d[i] = rfma(pl.x, v[3 * i], rfma(pl.y, v[3 * i + 1], rfma(pl.z, v[3 * i + 2], -pl.w)));
                 // T0 = a0 a1 a2 b2, T1 = a0 a1 b2 b1, T2 = a0 b0 b1 b2
-                const float l01 = fminf(d[0], d[1]), h01 = fmaxf(d[0], d[1]);
-                const float lo0 = fminf(l01, fminf(d[2], d[5])), hi0 = fmaxf(h01, fmaxf(d[2], d[5]));
-                const float lo1 = fminf(l01, fminf(d[5], d[4])), hi1 = fmaxf(h01, fmaxf(d[5], d[4]));
-                const float lo2 = fminf(fminf(d[0], d[3]), fminf(d[4], d[5])), hi2 = fmaxf(fmaxf(d[0], d[3]), fmaxf(d[4], d[5]));
+                const R l01 = rmin(d[0], d[1]), h01 = rmax(d[0], d[1]);
+                const R lo0 = rmin(l01, rmin(d[2], d[5])), hi0 = rmax(h01, rmax(d[2], d[5]));
+                const R lo1 = rmin(l01, rmin(d[5], d[4])), hi1 = rmax(h01, rmax(d[5], d[4]));
+                const R lo2 = rmin(rmin(d[0], d[3]), rmin(d[4], d[5])), hi2 = rmax(rmax(d[0], d[3]), rmax(d[4], d[5]));
                 if (q < npl) {
                     outside[0] |= lo0 >= -tol; outside[1] |= lo1 >= -tol; outside[2] |= lo2 >= -tol;
                     if (hi0 > tol) mask[0] |= 1u << q;
@@ -399,9 +444,9 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
                 const int t = 3 * pr + j;
-                const float sg = sh.Tsg[t];
-                if (sg != 0.0f && !outside[j]) {
-                    if (mask[j] == 0) two_sum(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
+                const R sg = sh.Tsg[t];
+                if (sg != R(0) && !outside[j]) {
+                    if (mask[j] == 0) acc_add(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
                     else { job[j] = true; code[j] = (unsigned)t | ((unsigned)k << 5) | (mask[j] << 10); }
                 }
             }
@@ -417,15 +462,20 @@ __device__ __forceinline__ void mx_flush(MXShared &sh, int nt, int ncand, float 
     __syncwarp();
 }
 
-// W warps (faces) per block; blocks per SM as shared memory allows
-constexpr int mx_resident(int w) { return w == 1 ? 15 : w == 2 ? 8 : 5; }
+// W warps (faces) per block; blocks per SM as shared memory allows (the FP64
+// form's per-warp buffers are twice as large)
+template <class R> constexpr int mx_resident(int w) { return w == 1 ? 15 : w == 2 ? 8 : 5; }
+template <> constexpr int mx_resident<double>(int w) { return w == 1 ? 8 : 4; }
 
-template <bool LIST, int W, class Wk>
-__global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(DevMesh m, MXArgs a)
+template <class R> __device__ __forceinline__ R rconv(double v) { return (R)v; }
+
+template <class R, bool LIST, class Wk>
+__device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &a, MXShared<R> &sh)
 {
-    __shared__ MXShared shm[W];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    MXShared &sh = shm[wib];
+    using V = R3<R>;
+    const R4<R> *fpl = static_cast<const R4<R> *>(a.fpl), *cbl = static_cast<const R4<R> *>(a.cbl);
+    const R4<R> *ktl = static_cast<const R4<R> *>(a.ktl);
+    const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int total = LIST ? *a.count : m.nf;
@@ -471,24 +521,25 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
         // pieces and take V_alpha = F dt - void (equal in exact arithmetic since
         // the corrected polyhedron holds F dt and the stencil covers it); a
         // polyhedron inside full cells then carries exactly F dt, one inside
-        // empty cells exactly 0, and FP32 rounding stays with mixed cells.  Not
-        // where the polyhedron can leave the domain (the normal-sweep fallback at
-        // walls; a face touching an open boundary), since the part outside is
-        // empty and the stencil does not cover it.
+        // empty cells exactly 0, and the rounding of the clipping stays with
+        // mixed cells.  Not where the polyhedron can leave the domain (the
+        // normal-sweep fallback at walls; a face touching an open boundary),
+        // since the part outside is empty and the stencil does not cover it.
         const double Ff = a.F[f];
         const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
         const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
         const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0 && !__ldg(m.fopen + f);
         const int nt = n == 3 ? 3 : 3 * n;
-        // signed distances (to unit-normal planes) within 2e-6 of the face size are
-        // taken as zero: points shared by the polyhedron and the cell tetrahedra
-        // come out of different FP32 roundings and would otherwise look like cuts
-        const float tol = __ldg(a.fpl + b).w;
+        // signed distances (to unit-normal planes) within the on-plane band of
+        // the face (FP32: 2e-6 of the face size, FP64: 1e-14) are taken as zero:
+        // points shared by the polyhedron and the cell tetrahedra come out of
+        // different roundings and would otherwise look like cuts
+        const R tol = ldg4(fpl, b).w;
         // ---- flux polyhedron tetrahedra in the face frame
-        float bx[6] = {3e38f, 3e38f, 3e38f, -3e38f, -3e38f, -3e38f};
+        R bx[6] = {R(3e38), R(3e38), R(3e38), R(-3e38), R(-3e38), R(-3e38)};
         if (lane < nt) {
             int pr = lane / 3, j = lane % 3;
-            auto disp = [&](int i) -> F3 {  // i < 0: face centre
+            auto disp = [&](int i) -> V {  // i < 0: face centre
                 V3 w;
                 if (LIST) {
                     const double *q = a.disp + (size_t)item * DISP_STRIDE + (i < 0 ? 0 : 3 + 3 * i);
@@ -506,68 +557,68 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
                         w = w * (1.0 / n);
                     }
                 }
-                return f3((float)w.x, (float)w.y, (float)w.z);
+                return r3(rconv<R>(w.x), rconv<R>(w.y), rconv<R>(w.z));
             };
-            F3 a0, a1, a2, w0, w1, w2;
+            V a0, a1, a2, w0, w1, w2;
             long k0, k1, k2;
             if (n == 3) {
                 k0 = __ldg(m.fpts + b); k1 = __ldg(m.fpts + b + 1); k2 = __ldg(m.fpts + b + 2);
-                a0 = ld4(a.fpl, b); a1 = ld4(a.fpl, b + 1); a2 = ld4(a.fpl, b + 2);
+                a0 = ld43<R>(fpl, b); a1 = ld43<R>(fpl, b + 1); a2 = ld43<R>(fpl, b + 2);
                 w0 = disp(0); w1 = disp(1); w2 = disp(2);
             } else {
                 int u = pr + 1 == n ? 0 : pr + 1;
                 k0 = -1; k1 = __ldg(m.fpts + b + pr); k2 = __ldg(m.fpts + b + u);
-                a0 = f3(0.f, 0.f, 0.f); a1 = ld4(a.fpl, b + pr); a2 = ld4(a.fpl, b + u);
+                a0 = r3(R(0), R(0), R(0)); a1 = ld43<R>(fpl, b + pr); a2 = ld43<R>(fpl, b + u);
                 w0 = disp(-1); w1 = disp(pr); w2 = disp(u);
             }
             int par = 1;
-            if (k1 < k0) { F3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
-            if (k2 < k1) { F3 t = a1; a1 = a2; a2 = t; t = w1; w1 = w2; w2 = t; long q = k1; k1 = k2; k2 = q; par = -par; }
-            if (k1 < k0) { F3 t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
-            F3 b0 = a0 - w0, b1 = a1 - w1, b2 = a2 - w2;
-            FTet T;
-            if (j == 0) T = FTet{{a0, a1, a2, b2}};
-            else if (j == 1) T = FTet{{a0, a1, b2, b1}};
-            else T = FTet{{a0, b0, b1, b2}};
-            float v6 = fvol6(T.v[0], T.v[1], T.v[2], T.v[3]);
-            float sv = -par * v6;
+            if (k1 < k0) { V t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
+            if (k2 < k1) { V t = a1; a1 = a2; a2 = t; t = w1; w1 = w2; w2 = t; long q = k1; k1 = k2; k2 = q; par = -par; }
+            if (k1 < k0) { V t = a0; a0 = a1; a1 = t; t = w0; w0 = w1; w1 = t; long q = k0; k0 = k1; k1 = q; par = -par; }
+            V b0 = a0 - w0, b1 = a1 - w1, b2 = a2 - w2;
+            RTet<R> T;
+            if (j == 0) T = RTet<R>{{a0, a1, a2, b2}};
+            else if (j == 1) T = RTet<R>{{a0, a1, b2, b1}};
+            else T = RTet<R>{{a0, b0, b1, b2}};
+            R v6 = rvol6(T.v[0], T.v[1], T.v[2], T.v[3]);
+            R sv = R(-par) * v6;
             stT(sh.T[lane], T);
-            sh.Tsg[lane] = sv > 0.0f ? 1.0f : (sv < 0.0f ? -1.0f : 0.0f);
-            sh.Tv6[lane] = fabsf(v6);
-            bx[0] = fminf(fminf(T.v[0].x, T.v[1].x), fminf(T.v[2].x, T.v[3].x));
-            bx[1] = fminf(fminf(T.v[0].y, T.v[1].y), fminf(T.v[2].y, T.v[3].y));
-            bx[2] = fminf(fminf(T.v[0].z, T.v[1].z), fminf(T.v[2].z, T.v[3].z));
-            bx[3] = fmaxf(fmaxf(T.v[0].x, T.v[1].x), fmaxf(T.v[2].x, T.v[3].x));
-            bx[4] = fmaxf(fmaxf(T.v[0].y, T.v[1].y), fmaxf(T.v[2].y, T.v[3].y));
-            bx[5] = fmaxf(fmaxf(T.v[0].z, T.v[1].z), fmaxf(T.v[2].z, T.v[3].z));
+            sh.Tsg[lane] = sv > R(0) ? R(1) : (sv < R(0) ? R(-1) : R(0));
+            sh.Tv6[lane] = rabs(v6);
+            bx[0] = rmin(rmin(T.v[0].x, T.v[1].x), rmin(T.v[2].x, T.v[3].x));
+            bx[1] = rmin(rmin(T.v[0].y, T.v[1].y), rmin(T.v[2].y, T.v[3].y));
+            bx[2] = rmin(rmin(T.v[0].z, T.v[1].z), rmin(T.v[2].z, T.v[3].z));
+            bx[3] = rmax(rmax(T.v[0].x, T.v[1].x), rmax(T.v[2].x, T.v[3].x));
+            bx[4] = rmax(rmax(T.v[0].y, T.v[1].y), rmax(T.v[2].y, T.v[3].y));
+            bx[5] = rmax(rmax(T.v[0].z, T.v[1].z), rmax(T.v[2].z, T.v[3].z));
             if (j == 0) {
-                float *q = reinterpret_cast<float *>(sh.P6[pr]);
-                const F3 pv[6] = {a0, a1, a2, b0, b1, b2};
+                R *q = reinterpret_cast<R *>(sh.P6[pr]);
+                const V pv[6] = {a0, a1, a2, b0, b1, b2};
 #pragma unroll
                 for (int i = 0; i < 6; ++i) { q[3 * i] = pv[i].x; q[3 * i + 1] = pv[i].y; q[3 * i + 2] = pv[i].z; }
-                float lo3[3] = {3e38f, 3e38f, 3e38f}, hi3[3] = {-3e38f, -3e38f, -3e38f};
+                R lo3[3] = {R(3e38), R(3e38), R(3e38)}, hi3[3] = {R(-3e38), R(-3e38), R(-3e38)};
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
-                    lo3[0] = fminf(lo3[0], pv[i].x); lo3[1] = fminf(lo3[1], pv[i].y); lo3[2] = fminf(lo3[2], pv[i].z);
-                    hi3[0] = fmaxf(hi3[0], pv[i].x); hi3[1] = fmaxf(hi3[1], pv[i].y); hi3[2] = fmaxf(hi3[2], pv[i].z);
+                    lo3[0] = rmin(lo3[0], pv[i].x); lo3[1] = rmin(lo3[1], pv[i].y); lo3[2] = rmin(lo3[2], pv[i].z);
+                    hi3[0] = rmax(hi3[0], pv[i].x); hi3[1] = rmax(hi3[1], pv[i].y); hi3[2] = rmax(hi3[2], pv[i].z);
                 }
                 for (int i = 0; i < 3; ++i) { sh.Pb[pr][i] = lo3[i]; sh.Pb[pr][3 + i] = hi3[i]; }
             }
         }
         // bounding box of the whole polyhedron
-        float pb[6];
+        R pb[6];
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            float v = bx[i];
+            R v = bx[i];
 #pragma unroll
             for (int o2 = 16; o2 > 0; o2 >>= 1) {
-                float w = __shfl_xor_sync(0xffffffffu, v, o2);
-                v = i < 3 ? fminf(v, w) : fmaxf(v, w);
+                R w = __shfl_xor_sync(0xffffffffu, v, o2);
+                v = i < 3 ? rmin(v, w) : rmax(v, w);
             }
             pb[i] = v;
         }
         __syncwarp();
-        float accs = 0.0f, accc = 0.0f;
+        R accs = R(0), accc = R(0);
         wk.add(WK_VOL, lane < nt);  // the flux polyhedron's tetrahedra
         wk.face();
         int ncand = 0;
@@ -589,23 +640,23 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
                     bool pass = false;
                     int c = 0;
                     double al = 0.0;
-                    F3 dc = f3(0.f, 0.f, 0.f);
+                    V dc = r3(R(0), R(0), R(0));
                     if (s < s1) {
                         c = __ldg(m.scell + s);
                         al = a.alpha[c];
                         // an empty cell carries no phase, a full cell no void
                         if (!((!comp && al <= eps) || (comp && al >= 1.0 - eps))) {
                             const V3 cc = ld3(m.cc, m.nc, c);
-                            dc = f3((float)(cc.x - o.x), (float)(cc.y - o.y), (float)(cc.z - o.z));
-                            const float4 cb0 = __ldg(a.cbl + 2 * (size_t)c), cb1 = __ldg(a.cbl + 2 * (size_t)c + 1);
+                            dc = r3(rconv<R>(cc.x - o.x), rconv<R>(cc.y - o.y), rconv<R>(cc.z - o.z));
+                            const R4<R> cb0 = ldg4(cbl, 2 * (long)c), cb1 = ldg4(cbl, 2 * (long)c + 1);
                             pass = !(cb1.x + dc.x < pb[0] || pb[3] < cb0.x + dc.x || cb1.y + dc.y < pb[1] ||
                                      pb[4] < cb0.y + dc.y || cb1.z + dc.z < pb[2] || pb[5] < cb0.z + dc.z);
                         }
                     }
                     int nkt = 0, t0 = 0;
-                    float wgt = 1.0f;
+                    R wgt = R(1);
                     bool useH = false;
-                    float4 H = make_float4(0.f, 0.f, 0.f, 0.f);
+                    R4<R> H = mk4<R>(R(0), R(0), R(0), R(0));
                     if (pass) {
                         t0 = __ldg(a.ctptr + c);
                         nkt = __ldg(a.ctptr + c + 1) - t0;
@@ -614,10 +665,11 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
                                 V3 hn = ld3(a.n, m.nc, c);
                                 double hd = a.d[c] - dot(hn, o);
                                 // phase side n.x <= d; the void side is -n.x <= -d
-                                float sg = comp ? -1.0f : 1.0f;
-                                H = make_float4(sg * (float)hn.x, sg * (float)hn.y, sg * (float)hn.z, sg * (float)hd);
+                                R sg = comp ? R(-1) : R(1);
+                                H = mk4<R>(sg * rconv<R>(hn.x), sg * rconv<R>(hn.y), sg * rconv<R>(hn.z),
+                                           sg * rconv<R>(hd));
                                 useH = true;
-                            } else wgt = comp ? (float)(1.0 - al) : (float)al;
+                            } else wgt = comp ? rconv<R>(1.0 - al) : rconv<R>(al);
                         }
                     }
                     int inc = nkt;
@@ -645,8 +697,8 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
             const bool fin = sc >= s1;
             bool cand = false;
             int ci = 0;
-            float4 kp[4];
-            float kbx[6];
+            R4<R> kp[4];
+            R kbx[6];
             if (!fin) {
                 // the cell of tetrahedron tb + lane: the cells that end at or
                 // before tb, plus one for each cell that ends inside the batch at
@@ -660,9 +712,9 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
                 // to the face frame by the shift dc
                 const int g = tb + lane;
                 const int j = sh.Ct0[ci] + g - (ci ? sh.Cend[ci - 1] : 0);
-                const F3 dc = f3(sh.Cdc[ci][0], sh.Cdc[ci][1], sh.Cdc[ci][2]);
-                const float4 *q = a.ktl + 6 * (size_t)j;
-                const float4 b0 = __ldg(q + 4), b1 = __ldg(q + 5);
+                const V dc = r3(sh.Cdc[ci][0], sh.Cdc[ci][1], sh.Cdc[ci][2]);
+                const R4<R> *q = ktl + 6 * (size_t)j;
+                const R4<R> b0 = ldg4(q, 4), b1 = ldg4(q, 5);
                 kbx[0] = b0.x + dc.x; kbx[1] = b0.y + dc.y; kbx[2] = b0.z + dc.z;
                 kbx[3] = b1.x + dc.x; kbx[4] = b1.y + dc.y; kbx[5] = b1.z + dc.z;
                 cand = !(kbx[3] < pb[0] || pb[3] < kbx[0] || kbx[4] < pb[1] || pb[4] < kbx[1] ||
@@ -671,8 +723,8 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
                     wk.add(WK_SHIFT, 4);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const float4 pl = __ldg(q + i);
-                        kp[i] = make_float4(pl.x, pl.y, pl.z, pl.w + (pl.x * dc.x + pl.y * dc.y + pl.z * dc.z));
+                        const R4<R> pl = ldg4(q, i);
+                        kp[i] = mk4<R>(pl.x, pl.y, pl.z, pl.w + (pl.x * dc.x + pl.y * dc.y + pl.z * dc.z));
                     }
                 }
             }
@@ -695,13 +747,13 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
             tb += 32;
             __syncwarp();
         }
-        // lane sums and compensations merged across the warp by TwoSum, then the
+        // lane sums (and their compensations) merged across the warp, then the
         // 1/6 of the volumes in FP64
-        float rs = accs, rc = accc;
+        R rs = accs, rc = accc;
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
-            const float xs = __shfl_xor_sync(0xffffffffu, rs, o2), xc = __shfl_xor_sync(0xffffffffu, rc, o2);
-            two_sum(rs, rc, xs);
+            const R xs = __shfl_xor_sync(0xffffffffu, rs, o2), xc = __shfl_xor_sync(0xffffffffu, rc, o2);
+            acc_add(rs, rc, xs);
             rc += xc;
         }
         double acc = ((double)rs + (double)rc) / 6.0;
@@ -712,8 +764,25 @@ __global__ void __launch_bounds__(W * 32, mx_resident(W)) k_phase_flux_mixed(Dev
     wk.flush(a.work, lane);
 }
 
-// FP32 geometry of every cell relative to its centre (context creation)
-__global__ void k_local_geom(DevMesh m, const int *cfpptr, float4 *cfl, float4 *cfpl, float4 *cbl)
+template <bool LIST, int W, class Wk>
+__global__ void __launch_bounds__(W * 32, mx_resident<float>(W)) k_phase_flux_mixed(DevMesh m, MXArgs a)
+{
+    __shared__ MXShared<float> shm[W];
+    phase_flux_body<float, LIST, Wk>(m, a, shm[threadIdx.x >> 5]);
+}
+
+template <bool LIST, int W, class Wk>
+__global__ void __launch_bounds__(W * 32, mx_resident<double>(W)) k_phase_flux(DevMesh m, MXArgs a)
+{
+    __shared__ MXShared<double> shm[W];
+    phase_flux_body<double, LIST, Wk>(m, a, shm[threadIdx.x >> 5]);
+}
+
+// geometry of every cell relative to its centre (context creation): face
+// centres and face points, and the cell's box widened by one rounding of R so
+// that the boxes stay conservative
+template <class R>
+__global__ void k_local_geom(DevMesh m, const int *cfpptr, R4<R> *cfl, R4<R> *cfpl, R4<R> *cbl)
 {
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m.nc) return;
@@ -722,82 +791,108 @@ __global__ void k_local_geom(DevMesh m, const int *cfpptr, float4 *cfl, float4 *
     for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
         int g = m.cface[k] >> 1;
         V3 q = ld3(m.cf, m.nf, g) - cc;
-        cfl[k] = make_float4((float)q.x, (float)q.y, (float)q.z, 0.f);
+        cfl[k] = mk4<R>((R)q.x, (R)q.y, (R)q.z, R(0));
         for (int j = m.fptr[g]; j < m.fptr[g + 1]; ++j) {
             V3 p = ldP(m, m.fpts[j]) - cc;
-            cfpl[o++] = make_float4((float)p.x, (float)p.y, (float)p.z, 0.f);
+            cfpl[o++] = mk4<R>((R)p.x, (R)p.y, (R)p.z, R(0));
         }
     }
     const double *b = m.cbox + 6 * (size_t)c;
-    // widened by one FP32 rounding so that FP32 boxes stay conservative
-    auto lo = [](double v) { float f = (float)v; return f > v ? nextafterf(f, -3e38f) : f; };
-    auto hi = [](double v) { float f = (float)v; return f < v ? nextafterf(f, 3e38f) : f; };
-    cbl[2 * c] = make_float4(lo(b[0] - cc.x), lo(b[1] - cc.y), lo(b[2] - cc.z), 0.f);
-    cbl[2 * c + 1] = make_float4(hi(b[3] - cc.x), hi(b[4] - cc.y), hi(b[5] - cc.z), 0.f);
+    auto lo = [](double v) {
+        R f = (R)v;
+        return (double)f > v ? rnext(f, R(-3e38)) : f;
+    };
+    auto hi = [](double v) {
+        R f = (R)v;
+        return (double)f < v ? rnext(f, R(3e38)) : f;
+    };
+    cbl[2 * c] = mk4<R>(lo(b[0] - cc.x), lo(b[1] - cc.y), lo(b[2] - cc.z), R(0));
+    cbl[2 * c + 1] = mk4<R>(hi(b[3] - cc.x), hi(b[4] - cc.y), hi(b[5] - cc.z), R(0));
 }
+
+__device__ __forceinline__ float rrsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rrsqrt(double x) { return rsqrt(x); }
 
 // the tetrahedra of every cell (cell centre + fan triangle of a face, in the
 // order of the cell's faces and of the face's points) as 4 outward unit-normal
 // planes and a box, in the cell frame (context creation)
-__global__ void k_cell_tets(DevMesh m, const int *cfpptr, const float4 *cfl, const float4 *cfpl, const int *ctptr,
-                            float4 *ktl)
+template <class R>
+__global__ void k_cell_tets(DevMesh m, const int *cfpptr, const R4<R> *cfl, const R4<R> *cfpl, const int *ctptr,
+                            R4<R> *ktl)
 {
+    using V = R3<R>;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= m.nc) return;
     int o = cfpptr[c], j = ctptr[c];
     for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) {
         const int code = m.cface[k], g = code >> 1, gn = m.fptr[g + 1] - m.fptr[g];
         for (int i = 0; i < (gn == 3 ? 1 : gn); ++i, ++j) {
-            F3 k0 = f3(0.f, 0.f, 0.f), k1, k2, k3;
+            V k0 = r3(R(0), R(0), R(0)), k1, k2, k3;
             if (gn == 3) {
-                k1 = ld4(cfpl, o); k2 = ld4(cfpl, o + 1); k3 = ld4(cfpl, o + 2);
+                k1 = ld43<R>(cfpl, o); k2 = ld43<R>(cfpl, o + 1); k3 = ld43<R>(cfpl, o + 2);
             } else {
-                k1 = ld4(cfl, k); k2 = ld4(cfpl, o + i); k3 = ld4(cfpl, o + (i + 1 == gn ? 0 : i + 1));
+                k1 = ld43<R>(cfl, k); k2 = ld43<R>(cfpl, o + i); k3 = ld43<R>(cfpl, o + (i + 1 == gn ? 0 : i + 1));
             }
-            if (code & 1) { F3 t = k2; k2 = k3; k3 = t; }
-            F3 n0 = fcross(k2 - k0, k1 - k0), n1 = fcross(k1 - k0, k3 - k0);
-            F3 n2 = fcross(k3 - k0, k2 - k0), n3 = fcross(k2 - k1, k3 - k1);
-            n0 = n0 * rsqrtf(fdot(n0, n0) + 1e-37f); n1 = n1 * rsqrtf(fdot(n1, n1) + 1e-37f);
-            n2 = n2 * rsqrtf(fdot(n2, n2) + 1e-37f); n3 = n3 * rsqrtf(fdot(n3, n3) + 1e-37f);
-            float4 *q = ktl + 6 * (size_t)j;
-            q[0] = make_float4(n0.x, n0.y, n0.z, 0.f);
-            q[1] = make_float4(n1.x, n1.y, n1.z, 0.f);
-            q[2] = make_float4(n2.x, n2.y, n2.z, 0.f);
-            q[3] = make_float4(n3.x, n3.y, n3.z, fdot(n3, k1));
-            q[4] = make_float4(fminf(fminf(k0.x, k1.x), fminf(k2.x, k3.x)), fminf(fminf(k0.y, k1.y), fminf(k2.y, k3.y)),
-                               fminf(fminf(k0.z, k1.z), fminf(k2.z, k3.z)), 0.f);
-            q[5] = make_float4(fmaxf(fmaxf(k0.x, k1.x), fmaxf(k2.x, k3.x)), fmaxf(fmaxf(k0.y, k1.y), fmaxf(k2.y, k3.y)),
-                               fmaxf(fmaxf(k0.z, k1.z), fmaxf(k2.z, k3.z)), 0.f);
+            if (code & 1) { V t = k2; k2 = k3; k3 = t; }
+            V n0 = rcross(k2 - k0, k1 - k0), n1 = rcross(k1 - k0, k3 - k0);
+            V n2 = rcross(k3 - k0, k2 - k0), n3 = rcross(k2 - k1, k3 - k1);
+            const R tiny = sizeof(R) == 4 ? R(1e-37) : R(1e-300);
+            n0 = n0 * rrsqrt(rdot(n0, n0) + tiny); n1 = n1 * rrsqrt(rdot(n1, n1) + tiny);
+            n2 = n2 * rrsqrt(rdot(n2, n2) + tiny); n3 = n3 * rrsqrt(rdot(n3, n3) + tiny);
+            R4<R> *q = ktl + 6 * (size_t)j;
+            q[0] = mk4<R>(n0.x, n0.y, n0.z, R(0));
+            q[1] = mk4<R>(n1.x, n1.y, n1.z, R(0));
+            q[2] = mk4<R>(n2.x, n2.y, n2.z, R(0));
+            q[3] = mk4<R>(n3.x, n3.y, n3.z, rdot(n3, k1));
+            q[4] = mk4<R>(rmin(rmin(k0.x, k1.x), rmin(k2.x, k3.x)), rmin(rmin(k0.y, k1.y), rmin(k2.y, k3.y)),
+                          rmin(rmin(k0.z, k1.z), rmin(k2.z, k3.z)), R(0));
+            q[5] = mk4<R>(rmax(rmax(k0.x, k1.x), rmax(k2.x, k3.x)), rmax(rmax(k0.y, k1.y), rmax(k2.y, k3.y)),
+                          rmax(rmax(k0.z, k1.z), rmax(k2.z, k3.z)), R(0));
         }
         o += gn;
     }
 }
 
-__global__ void k_face_local(DevMesh m, float4 *fpl)
+// face points relative to the face centre; the w of the face's first point
+// holds the on-plane band of the clipping: 2e-6 of the face size in FP32
+// (reading R13), 1e-14 of it in FP64
+template <class R>
+__global__ void k_face_local(DevMesh m, R4<R> *fpl)
 {
     int f = blockIdx.x * blockDim.x + threadIdx.x;
     if (f >= m.nf) return;
     V3 c = ld3(m.cf, m.nf, f), S = ld3(m.sf, m.nf, f);
-    // w of the face's first point: the on-plane band of the clipping, 2e-6 of
-    // the face size
-    const float tol = (float)(2e-6 * sqrt(sqrt(dot(S, S))));
+    const double band = sizeof(R) == 4 ? 2e-6 : 1e-14;
+    const R tol = (R)(band * sqrt(sqrt(dot(S, S))));
     for (int j = m.fptr[f]; j < m.fptr[f + 1]; ++j) {
         V3 p = ldP(m, m.fpts[j]) - c;
-        fpl[j] = make_float4((float)p.x, (float)p.y, (float)p.z, j == m.fptr[f] ? tol : 0.f);
+        fpl[j] = mk4<R>((R)p.x, (R)p.y, (R)p.z, j == m.fptr[f] ? tol : R(0));
     }
 }
 
 inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
+template <class R>
+int setup_tables(vof_ctx *c, cudaStream_t s)
+{
+    R4<R> *cfl = static_cast<R4<R> *>(c->cfl), *cfpl = static_cast<R4<R> *>(c->cfpl);
+    k_local_geom<R><<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, cfl, cfpl, static_cast<R4<R> *>(c->cbl));
+    k_face_local<R><<<cdiv(c->nf, 256), 256, 0, s>>>(c->m, static_cast<R4<R> *>(c->fpl));
+    k_cell_tets<R><<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, cfl, cfpl, c->m.ctptr,
+                                                    static_cast<R4<R> *>(c->ktl));
+    return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
+}
+
 }  // namespace
+
+size_t phase_flux_table_entry_bytes(int precision)
+{
+    return precision == VOF_MIXED ? sizeof(float4) : sizeof(D4);
+}
 
 int launch_setup_mixed(vof_ctx *c, cudaStream_t s)
 {
-    k_local_geom<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->cbl);
-    k_face_local<<<cdiv(c->nf, 256), 256, 0, s>>>(c->m, c->fpl);
-    if (c->ktl)
-        k_cell_tets<<<cdiv(c->nc, 256), 256, 0, s>>>(c->m, c->cfpptr, c->cfl, c->cfpl, c->m.ctptr, c->ktl);
-    return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
+    return c->precision == VOF_MIXED ? setup_tables<float>(c, s) : setup_tables<double>(c, s);
 }
 
 static MXArgs mx_args(vof_ctx *c, const double *alpha, const double *n, const double *d, const uint8_t *flags,
@@ -808,33 +903,45 @@ static MXArgs mx_args(vof_ctx *c, const double *alpha, const double *n, const do
                   c->fpl, c->cbl, c->ktl, c->m.ctptr, nullptr};
 }
 
-int launch_phase_flux_mixed_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
+int launch_pf_all(vof_ctx *c, const double *alpha, const double *n, const double *d,
                                 const uint8_t *flags, const double *Up, const double *F, const double *lambda,
                                 double dt, double *Va, cudaStream_t s)
 {
-    MXArgs a = mx_args(c, alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr, nullptr);
-    if (c->work_on) k_phase_flux_mixed<false, 2, WkOn><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
-    else k_phase_flux_mixed<false, 2, WkOff><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+    MXArgs a = mx_args(c, alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr,
+                       c->work_on ? c->work : nullptr);
+    if (c->precision == VOF_MIXED) {
+        if (c->work_on) k_phase_flux_mixed<false, 2, WkOn><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+        else k_phase_flux_mixed<false, 2, WkOff><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+    } else {
+        if (c->work_on) k_phase_flux<false, 1, WkOn><<<cdiv((long)c->nf * 32, 32), 32, 0, s>>>(c->m, a);
+        else k_phase_flux<false, 1, WkOff><<<cdiv((long)c->nf * 32, 32), 32, 0, s>>>(c->m, a);
+    }
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 
-int launch_phase_flux_mixed_list(vof_ctx *c, const double *alpha, const double *F, double dt, int sms,
+int launch_pf_list(vof_ctx *c, const double *alpha, const double *F, double dt, int sms,
                                  cudaStream_t s)
 {
     MXArgs a = mx_args(c, alpha, c->n, c->d, c->flags, nullptr, F, nullptr, dt, c->Va, c->band,
-                       c->counters + CNT_BAND, c->disp_b, c->work);
+                       c->counters + CNT_BAND, c->disp_b, c->work_on ? c->work : nullptr);
     a.next = c->counters + CNT_PFNEXT;  // zeroed with the step's counters
+    if (c->precision != VOF_MIXED) {
+        // the FP64 form: one warp per block, as many blocks as shared memory allows
+        if (c->work_on) k_phase_flux<true, 1, WkOn><<<sms * mx_resident<double>(1), 32, 0, s>>>(c->m, a);
+        else k_phase_flux<true, 1, WkOff><<<sms * mx_resident<double>(1), 32, 0, s>>>(c->m, a);
+        return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
+    }
     // launch configuration (vof_batch_tune): warps per block, and grid = SMs x
     // resident blocks x multiplier
     const int w = c->pf_warps >= 1 && c->pf_warps <= 3 ? c->pf_warps : 2;
     const int mult = c->pf_mult >= 1 ? c->pf_mult : 1;
     if (c->work_on)  // instrumented variant (vof_count_work), the 2-warp shape
-        k_phase_flux_mixed<true, 2, WkOn><<<sms * mx_resident(2) * mult, 64, 0, s>>>(c->m, a);
+        k_phase_flux_mixed<true, 2, WkOn><<<sms * mx_resident<float>(2) * mult, 64, 0, s>>>(c->m, a);
     else if (w == 1)
-        k_phase_flux_mixed<true, 1, WkOff><<<sms * mx_resident(1) * mult, 32, 0, s>>>(c->m, a);
+        k_phase_flux_mixed<true, 1, WkOff><<<sms * mx_resident<float>(1) * mult, 32, 0, s>>>(c->m, a);
     else if (w == 2)
-        k_phase_flux_mixed<true, 2, WkOff><<<sms * mx_resident(2) * mult, 64, 0, s>>>(c->m, a);
+        k_phase_flux_mixed<true, 2, WkOff><<<sms * mx_resident<float>(2) * mult, 64, 0, s>>>(c->m, a);
     else
-        k_phase_flux_mixed<true, 3, WkOff><<<sms * mx_resident(3) * mult, 96, 0, s>>>(c->m, a);
+        k_phase_flux_mixed<true, 3, WkOff><<<sms * mx_resident<float>(3) * mult, 96, 0, s>>>(c->m, a);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }

@@ -157,10 +157,10 @@ def test_remap_matches_oracle(torch, oracle_lib, meshes):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_amr_deformation_run(torch, precision):
     """The deformation case on an octree re-refined around the interface every
-    4 steps to t = T = 3 (8^3 base, two levels): the volume is conserved
-    across every step and every remap, alpha stays in [0, 1], and the shape
-    error at t = T against the sphere's fractions on the final mesh is
-    reported."""
+    4 steps to t = T = 3 (8^3 base, two levels, finest h = 1/32): the volume is
+    conserved across every step and every remap, alpha stays in [0, 1], and
+    the shape error at t = T against the sphere's fractions on the final mesh
+    is that of a uniform mesh of the finest size."""
     from paper_1305_3417_gb300 import vof
     case = amr.AmrCase(n0=8, levels=2, band=3.0, precision=precision, every=4)
     v0 = case.volume()
@@ -185,5 +185,8 @@ def test_amr_deformation_run(torch, precision):
     print(f"AMR deformation ({'mixed' if precision else 'fp64'}): {case.steps} steps, {case.remaps} remaps, "
           f"{case.mesh.n_cells} cells at t = T, L1 {l1:.4e} ({l1 / (vc * ex).sum():.3e} of the volume), "
           f"worst remap volume change {max(abs(x) for x in case.mass_change):.1e}")
-    assert l1 < 0.3 * (vc * ex).sum()
+    # the finest cells are those of a uniform 32^3 mesh: the error stays within
+    # the paper's E_g for the uniform 32^3 deformation case at Co 0.5
+    # (tests/golden/paper_deformation_eg.txt)
+    assert l1 <= 8.15757e-3
     case.ctx.close()
