@@ -298,19 +298,20 @@ def config(args, w):
 
 
 def train_guess(device, workload="deform3d"):
-    """The initial-guess network trained on seeded sphere/plane fields of a
-    48^3 jittered hexahedral mesh, or for the octree workload of a 24^3-based
-    two-level octree (cells like the workload's: boxes of three sizes with
-    hanging points); targets from the FP64 reconstruction."""
+    """The initial-guess network trained on seeded sphere/plane fields (volume
+    fractions computed on the device) of a 96^3 jittered hexahedral mesh,
+    about 10^6 interface cells over 180 fields, or for the octree workload of
+    a 32^3-based two-level octree (cells like the workload's: boxes of three
+    sizes with hanging points); targets from the FP64 reconstruction."""
     import torch
     from paper_1305_3417_gb300 import inputs as I, mlp, vof
     t0 = time.perf_counter()
     if workload == "octree":
-        m = I.octree_mesh(24, 2)
+        m, nf = I.octree_mesh(32, 2), 120
     else:
-        m = I.hex_mesh((48, 48, 48), jitter=0.2, seed=21)
+        m, nf = I.hex_mesh((96, 96, 96), jitter=0.2, seed=21), 180
     c64 = vof.VofContext(m, precision=vof.FP64, device=device)
-    X, Y = mlp.samples(c64, m, mlp.random_fields(m, 40, seed=22))
+    X, Y = mlp.samples(c64, m, mlp.random_fields_device(c64, m, nf, seed=22))
     net = vof.Mlp(mlp.init_params(1306), max_batch=1 << 17, device=device)
     hist = mlp.train(net, X, Y, epochs=30, batch=4096, lr=3e-3)
     torch.cuda.synchronize()

@@ -45,6 +45,32 @@ def random_fields(mesh, n_fields: int, seed: int = 1306):
     return out
 
 
+def random_fields_device(ctx, mesh, n_fields: int, seed: int = 1306, levels: int = 3):
+    """As random_fields, with the volume fractions computed on the device by
+    vof_evsd (the ball's volume in each cell, R19): spheres directly, planes
+    as the boundary of a ball of radius 1e3 whose surface passes through the
+    plane's point (its pieces are cut by the tangent plane there)."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    vc = ctx.geometry()[1]
+    out = []
+    buf = torch.zeros(mesh.n_cells, dtype=torch.float64, device=vc.device)
+    for _ in range(n_fields):
+        if rng.random() < 0.6:
+            R = float(rng.uniform(0.08, 0.3))
+            c = rng.uniform(0.2, 0.8, 3)
+            ball = (float(c[0]), float(c[1]), float(c[2]), R)
+        else:
+            nrm = rng.normal(size=3)
+            nrm /= np.linalg.norm(nrm)
+            x0 = rng.uniform(0.3, 0.7, 3)
+            c = x0 - 1e3 * nrm
+            ball = (float(c[0]), float(c[1]), float(c[2]), 1e3)
+        vof.vof_evsd(ctx.h, None, None, None, ball, levels, buf)
+        out.append(torch.clamp(buf / vc, 0.0, 1.0).cpu().numpy())
+    return out
+
+
 def samples(ctx, mesh, fields):
     """(features [n x 33], targets [n x 4]) on the device for the oriented
     interface cells of every field, targets from the context's reconstruction."""
