@@ -518,6 +518,131 @@ def run_batch(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def run_amr(args, world, rank, local):
+    """The deformation case on a re-refined octree (Sec. 3, Alg. 2) to t = T:
+    base n^3 (default 32), two levels, re-refined around the interface every
+    --amr-every steps.  value: internal face fluxes per second of the device
+    steps; also the whole run's wall-clock rate with the host refinement
+    cycles, the remap kernel's time, the volume change across remaps and the
+    L1 error at t = T against the sphere's fractions on the final mesh."""
+    import torch
+    from paper_1305_3417_gb300 import amr, build, vof
+    from paper_1305_3417_gb300 import inputs as I
+    build.build()
+    torch.cuda.set_device(local)
+    case = amr.AmrCase(n0=args.n or 32, levels=2, band=3.0, precision=vof.MIXED, every=args.amr_every,
+                       device=local)
+    stream = torch.cuda.current_stream()
+    stats = torch.zeros(vof.S_LEN, dtype=torch.float64, device="cuda")
+    v0 = case.volume()
+    dev_ms, faces, t_remap, cells = 0.0, 0, 0.0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    worst_drift, lo, hi = 0.0, 1.0, 0.0
+    wall0 = time.perf_counter()
+    with Clocks(local) as clk:
+        while case.t < 3.0 - 1e-12:
+            if case.steps and case.steps % case.every == 0:
+                r0 = time.perf_counter()
+                case.remap()
+                t_remap += time.perf_counter() - r0
+            cells.append(case.mesh.n_cells)
+            e0.record(stream)
+            case.step(3.0, stats)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            dev_ms += e0.elapsed_time(e1)
+            faces += case.mesh.n_internal
+            s_ = stats.cpu().numpy()
+            worst_drift = max(worst_drift, abs(s_[1] - s_[0]) / s_[0])
+            lo, hi = min(lo, s_[4]), max(hi, s_[5])
+    wall = time.perf_counter() - wall0
+    ex = I.sampled_fraction(case.mesh, I.sphere_sdf(case.center, case.R))
+    a = case.alpha.cpu().numpy()
+    vc = case.vc.cpu().numpy()
+    l1 = float((vc * np.abs(a - ex)).sum())
+    if rank == 0:
+        line = {"metric": METRIC, "value": faces / (dev_ms * 1e-3) / 1e6, "unit": UNIT, "n_gpus": 1,
+                "steps": case.steps, "warmup": 0, "ms_per_step": dev_ms / case.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": f"octree_amr: {args.n or 32}^3 base, two levels, deformation field to t = T = 3, "
+                                       f"re-refined every {case.every} steps (Sec. 3, Alg. 2)",
+                           "cells_min": int(min(cells)), "cells_max": int(max(cells)), "remaps": case.remaps},
+                "whole_run": {"wall_s": wall, "value_with_remaps": faces / wall / 1e6, "remap_wall_s": t_remap},
+                "clocks": clk.summary(),
+                "quality": {"max_rel_volume_drift": worst_drift, "alpha_min": lo, "alpha_max": hi,
+                            "max_remap_volume_change": max(abs(x) for x in case.mass_change),
+                            "rel_volume_change": case.volume() / v0 - 1.0, "l1_at_T": l1,
+                            "l1_rel_to_volume": l1 / float((vc * ex).sum())}}
+        print(json.dumps(line), flush=True)
+
+
+def run_accuracy(args, world, rank, local):
+    """Reconstruction accuracy (Sec. 4.1) at scale: a jittered n^3 hexahedral
+    mesh (default 128) holding a ball (R = 0.27 at (0.41, 0.47, 0.52)) as its
+    E_vsd routine resolves it; the reconstruction with the NAG and with the
+    generalised LSQ gradient (Sec. 2.2.1), E_vsd of each, and the times of the
+    LSQ gradient (every cell) and of E_vsd.  The LSQ gradient is FP64-bound:
+    per neighbour the offset (3), its squared length (5), the inverse (an FP64
+    division, counted 20), the weighted offset (3) and nine accumulations
+    (18): 49 flop; per cell the adjugate solve, 60 flop; against the measured
+    FP64 FMA rate (its 164 B per cell of HBM traffic take 0.05 ms here)."""
+    import torch
+    from paper_1305_3417_gb300 import build, vof
+    from paper_1305_3417_gb300 import inputs as I
+    build.build()
+    torch.cuda.set_device(local)
+    n = args.n or 128
+    m = I.hex_mesh((n, n, n), jitter=0.2, seed=1302)
+    ctx = vof.VofContext(m, precision=vof.FP64, device=local)
+    ball, levels = (0.41, 0.47, 0.52, 0.27), 4
+    vc = ctx.geometry()[1]
+    vb = torch.zeros(m.n_cells, dtype=torch.float64, device="cuda")
+    vof.vof_evsd(ctx.h, None, None, None, ball, levels, vb)
+    a = torch.clamp(vb / vc, 0.0, 1.0)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    g = torch.zeros(3 * m.n_cells, dtype=torch.float64, device="cuda")
+    vof.vof_set_gradient(ctx.h, vof.GRAD_LSQ)
+    t_lsq = timed(lambda: vof.vof_lsq_gradient(ctx.h, a, g))
+    out = {}
+    ev = torch.zeros(m.n_cells, dtype=torch.float64, device="cuda")
+    pk, pk_src = peaks()
+    for kind, name in ((vof.GRAD_NAG, "nag"), (vof.GRAD_LSQ, "lsq")):
+        vof.vof_set_gradient(ctx.h, kind)
+        nn, dd, fl, _ = ctx.reconstruct(a)
+        t_ev = timed(lambda: vof.vof_evsd(ctx.h, fl, nn, dd, ball, levels, ev), reps=2)
+        out[name] = {"evsd": float(ev.sum()), "evsd_rel_to_volume": float(ev.sum() / (vc * a).sum()),
+                     "interface_cells": int(((fl & 1) != 0).sum()), "evsd_ms": t_ev}
+    # cells sharing a point with a cell of the n^3 lattice: 3 per axis inside,
+    # 2 on the boundary, less the cell itself
+    nbrs = (3 * n - 2) ** 3 - n ** 3
+    flops = 49.0 * nbrs + 60.0 * m.n_cells
+    p64 = vof.vof_probe_fma(local, vof.FP64)
+    if rank == 0:
+        line = {"metric": "reconstruction error E_vsd (Sec. 4.1) and LSQ gradient throughput", "value": out["lsq"]["evsd"],
+                "unit": "E_vsd volume", "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": False,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"accuracy: {n}^3 jittered hex, ball R = 0.27, {levels} levels", "n_cells": m.n_cells},
+                "lsq_gradient": {"ms": t_lsq, "cells_per_s": m.n_cells / (t_lsq * 1e-3),
+                                 "roofline": {"bound": "alu", "achieved": flops / (t_lsq * 1e-3) / 1e12,
+                                              "peak": p64 / 1e12, "unit": "TFLOP/s",
+                                              "frac": flops / (t_lsq * 1e-3) / p64, "flops": flops,
+                                              "peak_source": "measured FP64 FMA probe (vof_probe_fma)"}},
+                "nag": out["nag"], "lsq": out["lsq"]}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -533,6 +658,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=1)
     ap.add_argument("--cases", type=int, default=256, help="batch workload: number of cases")
     ap.add_argument("--mlp", action="store_true", help="learned initial guess of the positioning (trained first)")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default phase-flux launch (no autotuner)")
+    ap.add_argument("--amr-every", type=int, default=8, help="octree_amr workload: steps between refinement cycles")
     ap.add_argument("--batch-scale", type=float, default=1.0, help="batch workload: scale of the n ranges")
     ap.add_argument("--full-run", type=int, default=-1,
                     help="after the timed steps, run the whole case (t = 0 to its end) on the device and report the "
@@ -543,6 +670,12 @@ def main():
     world, rank, local = dist_init(args)
     if args.workload == "batch":
         run_batch(args, world, rank, local)
+        return
+    if args.workload == "octree_amr":
+        run_amr(args, world, rank, local)
+        return
+    if args.workload == "accuracy":
+        run_accuracy(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -578,6 +711,14 @@ def main():
     for k in range(args.skip + args.warmup):
         ctx.advect(alpha, Uk[k], Fk[k], w.dt, stats)
     torch.cuda.synchronize()
+    # the phase-flux launch shape and staging chosen by the autotuner, on the
+    # first timed step's state (it steps a copy)
+    tuned = None
+    if prec == vof.MIXED and not args.no_tune:
+        k0 = args.skip + args.warmup
+        cfg, tms = vof.vof_tune(ctx.h, alpha, Uk[k0], Fk[k0], w.dt)
+        tuned = {"config": cfg, "stack": 92 if cfg // 256 == 0 else 56, "warps_per_block": (cfg // 16) % 16,
+                 "grid_multiplier": cfg % 16, "step_ms": tms}
     a_start = alpha.clone()
     timed = [(Uk[args.skip + args.warmup + j], Fk[args.skip + args.warmup + j], w.dt) for j in range(args.steps)]
     st0 = ctx.status()
@@ -653,12 +794,16 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ej = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e2.record(stream)
     for j in range(args.steps):
         vof.vof_advect_host(ctx.h, ha, hU[j], hF[j], w.dt, hstat)
+        ej[j].record(stream)
     e3.record(stream)
     torch.cuda.synchronize()
     ms_e2e = max_over_ranks(e2.elapsed_time(e3), world, dev)
+    # per-call times (each call's events on the caller's stream)
+    e2e_steps = [e2.elapsed_time(ej[0])] + [ej[j - 1].elapsed_time(ej[j]) for j in range(1, args.steps)]
     e2e = faces / (ms_e2e * 1e-3) / 1e6
     h2d = 8 * m.n_cells + 24 * m.n_cells + 8 * m.n_faces
     d2h = 8 * m.n_cells + 8 * vof.S_LEN
@@ -717,9 +862,11 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64" if prec == vof.FP64 else "f32+f64",
-                "data": "synthetic", "config": config(args, w),
+                "data": "synthetic", "config": {**config(args, w), "tuned_launch": tuned},
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": ms_e2e / args.steps, "host_link_GBps": link},
+                        "ms_per_step": ms_e2e / args.steps, "host_link_GBps": link,
+                        "call_ms": {"min": float(np.min(e2e_steps)), "median": float(np.median(e2e_steps)),
+                                    "max": float(np.max(e2e_steps))}},
                 "gpu_launches": launches, "roofline": roof, "step_roofline": step_roof,
                 "band_face_fluxes": {"value": world * band * args.steps / (ms_max * 1e-3) / 1e6, "unit": UNIT,
                                      "band_faces_per_step": band},

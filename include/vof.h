@@ -276,13 +276,20 @@ int vof_batch_advect(vof_batch *batch, double *alpha, const double *U_dt, const 
 
 /* Autotuner for the phase-flux launch of a mixed batch: times one step from
  * the state alpha (left unchanged: the steps run on a copy in the context's
- * staging buffer) for 1, 2 and 3 warps (faces) per block and grid multipliers
- * 1, 2 and 4 over the resident blocks, keeps the fastest for later steps, and
- * returns it as config = 16 * warps + multiplier with its step time in ms
- * (either pointer may be NULL).  An FP64 batch keeps its launch (config 0).
- * Synchronous on `stream`. */
+ * staging buffer) for every launch configuration -- the per-warp staging of
+ * clip pieces in shared memory (a stack of 92 pieces, or of 56 for more
+ * resident warps), 1, 2 or 3 warps (faces) per block, and grid multipliers
+ * 1, 2 and 4 over the resident blocks -- keeps the fastest for later steps,
+ * and returns it as config = 256 * stack + 16 * warps + multiplier (stack 0:
+ * 92 pieces, 1: 56) with its step time in ms (either pointer may be NULL).
+ * An FP64 batch keeps its launch (config 0).  Synchronous on `stream`. */
 int vof_batch_tune(vof_batch *batch, const double *alpha, const double *U_dt, const double *F_dt, int *config,
                    float *best_ms, void *stream);
+
+/* The same autotuner for one context's vof_advect (inputs as vof_advect); the
+ * choice holds for the context's later steps.  The paper has no counterpart. */
+int vof_tune(vof_ctx *ctx, const double *alpha, const double *Uc, const double *F, double dt, int *config,
+             float *best_ms, void *stream);
 
 /* ---- Learned initial guess of the plane positioning ----------------------
  * The paper has no learned part.  A small network (VOF_MLP_IN features of an

@@ -46,7 +46,7 @@ __global__ void k_case_mass(const double *__restrict__ alpha, const double *__re
     if (threadIdx.x == 0) out[cs] = (sh[0] + sh[1]) + (sh[2] + sh[3]);
 }
 
-int cfg_code(const vof_ctx *c) { return c->pf_warps * 16 + c->pf_mult; }
+int cfg_code(const vof_ctx *c) { return c->pf_stack * 256 + c->pf_warps * 16 + c->pf_mult; }
 
 void drop_graph(vof_batch *b)
 {
@@ -148,13 +148,14 @@ int vof_batch_advect(vof_batch *b, double *alpha, const double *U_dt, const doub
     return VOF_OK;
 }
 
-int vof_batch_tune(vof_batch *b, const double *alpha, const double *U_dt, const double *F_dt, int *config,
-                   float *best_ms, void *stream)
+// Times one step (vof_advect's launch sequence, from the state alpha copied
+// into the context's staging buffer: no allocation) for every launch
+// configuration of the mixed phase flux -- clip-piece stack depth 92 or 56,
+// 1, 2 or 3 warps (faces) per block, grid multipliers 1, 2, 4 over the
+// resident blocks -- and keeps the fastest; an FP64 context keeps its launch
+static int tune_launch(vof_ctx *c, const double *alpha, const double *U, const double *F, double dt, cudaStream_t s,
+                       int *best_out, float *ms_out)
 {
-    if (!b || !alpha || !U_dt || !F_dt) return VOF_ERR_INVALID_ARG;
-    vof_ctx *c = b->ctx;
-    if (cudaSetDevice(c->device) != cudaSuccess) return VOF_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
     int best = -1;
     float tbest = 0.0f;
     if (c->precision == VOF_MIXED) {
@@ -162,37 +163,69 @@ int vof_batch_tune(vof_batch *b, const double *alpha, const double *U_dt, const 
         if (cudaEventCreate(&e0) != cudaSuccess) return VOF_ERR_CUDA;
         if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return VOF_ERR_CUDA; }
         int err = VOF_OK;
-        // every candidate steps from the same state: alpha copied into the
-        // context's staging buffer (no allocation), one untimed step, the
+        // every candidate steps from the same state: one untimed step, the
         // state restored, one timed step
-        for (int w = 1; w <= 3 && !err; ++w)
-            for (int mult = 1; mult <= 4 && !err; mult *= 2) {
-                c->pf_warps = w;
-                c->pf_mult = mult;
-                float ms = 0.0f;
-                for (int rep = 0; rep < 2 && !err; ++rep) {
-                    if (cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyDeviceToDevice, s) !=
-                        cudaSuccess) { err = VOF_ERR_CUDA; break; }
-                    if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) { err = VOF_ERR_CUDA; break; }
-                    err = launch_advect(c, c->h_alpha, U_dt, F_dt, 1.0, c->stats_dev, s);
-                    if (err) break;
-                    if (rep == 1 && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                                     cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                        err = VOF_ERR_CUDA;
+        for (int st = 0; st <= 1 && !err; ++st)
+            for (int w = 1; w <= 3 && !err; ++w)
+                for (int mult = 1; mult <= 4 && !err; mult *= 2) {
+                    c->pf_stack = st;
+                    c->pf_warps = w;
+                    c->pf_mult = mult;
+                    float ms = 0.0f;
+                    for (int rep = 0; rep < 2 && !err; ++rep) {
+                        if (cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyDeviceToDevice, s) !=
+                            cudaSuccess) { err = VOF_ERR_CUDA; break; }
+                        if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) { err = VOF_ERR_CUDA; break; }
+                        err = launch_advect(c, c->h_alpha, U, F, dt, c->stats_dev, s);
+                        if (err) break;
+                        if (rep == 1 &&
+                            (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                            err = VOF_ERR_CUDA;
+                    }
+                    if (!err && (best < 0 || ms < tbest)) {
+                        best = st * 256 + w * 16 + mult;
+                        tbest = ms;
+                    }
                 }
-                if (!err && (best < 0 || ms < tbest)) {
-                    best = w * 16 + mult;
-                    tbest = ms;
-                }
-            }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         if (err) return err;
-        c->pf_warps = best / 16;
+        c->pf_stack = best / 256;
+        c->pf_warps = (best / 16) % 16;
         c->pf_mult = best % 16;
     }
+    *best_out = best < 0 ? 0 : best;
+    *ms_out = tbest;
+    return VOF_OK;
+}
+
+int vof_batch_tune(vof_batch *b, const double *alpha, const double *U_dt, const double *F_dt, int *config,
+                   float *best_ms, void *stream)
+{
+    if (!b || !alpha || !U_dt || !F_dt) return VOF_ERR_INVALID_ARG;
+    vof_ctx *c = b->ctx;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VOF_ERR_CUDA;
+    int best = 0;
+    float tbest = 0.0f;
+    int r = tune_launch(c, alpha, U_dt, F_dt, 1.0, (cudaStream_t)stream, &best, &tbest);
+    if (r) return r;
     drop_graph(b);
-    if (config) *config = best < 0 ? 0 : best;
+    if (config) *config = best;
+    if (best_ms) *best_ms = tbest;
+    return VOF_OK;
+}
+
+int vof_tune(vof_ctx *c, const double *alpha, const double *Uc, const double *F, double dt, int *config,
+             float *best_ms, void *stream)
+{
+    if (!c || !alpha || !Uc || !F || !(dt > 0.0)) return VOF_ERR_INVALID_ARG;
+    if (cudaSetDevice(c->device) != cudaSuccess) return VOF_ERR_CUDA;
+    int best = 0;
+    float tbest = 0.0f;
+    int r = tune_launch(c, alpha, Uc, F, dt, (cudaStream_t)stream, &best, &tbest);
+    if (r) return r;
+    if (config) *config = best;
     if (best_ms) *best_ms = tbest;
     return VOF_OK;
 }

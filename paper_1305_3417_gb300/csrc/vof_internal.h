@@ -111,6 +111,7 @@ struct vof_ctx {
     // mixed phase-flux launch configuration (0: defaults): warps per block 1-3,
     // grid multiplier over the resident blocks
     int pf_warps, pf_mult;
+    int pf_stack;                // clip-piece stack per warp: 0 = 92 pieces, 1 = 56 (more resident warps)
     int rc_g;                    // reconstruction lanes per cell: 8 if every cell has <= 16 tetrahedra, else 32
     int rc_k;                    // tetrahedra per lane: 3 where some cell has more than 64, else 2
     // gradient of the reconstruction (vof_set_gradient): VOF_GRAD_NAG or

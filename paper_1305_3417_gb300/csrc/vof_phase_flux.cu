@@ -103,17 +103,20 @@ __device__ __forceinline__ void rsort4(R &a, R &b, R &c, R &d)
 
 template <class R> struct RTet { R3<R> v[4]; };
 
-// Running sum of the pieces: FP32 with TwoSum (Knuth) compensation, s + c
-// carrying the sum exactly up to the last addend's rounding (no
-// multiplications, so no fused operation can change it); FP64 plainly.
-__device__ __forceinline__ void acc_add(float &s, float &c, float x)
+// Running sum of the pieces (6 |volume| times sign and weight): FP32 with
+// TwoSum (Knuth) compensation, s + c carrying the sum up to the rounding of
+// the compensation (no multiplications, so no fused operation can change it);
+// FP64 plainly.  (A 64-bit fixed-point sum, exact and order-independent, cost
+// 6 % of the kernel's time in its conversions.)
+template <class R> struct Acc { R s = R(0), c = R(0); };
+__device__ __forceinline__ void acc_add(Acc<float> &a, float x)
 {
-    float t = s + x;
-    float bp = t - s;
-    c += (s - (t - bp)) + (x - bp);
-    s = t;
+    const float t = a.s + x;
+    const float bp = t - a.s;
+    a.c += (a.s - (t - bp)) + (x - bp);
+    a.s = t;
 }
-__device__ __forceinline__ void acc_add(double &s, double &, double x) { s += x; }
+__device__ __forceinline__ void acc_add(Acc<double> &a, double x) { a.s += x; }
 
 constexpr int MX_MAXT = 3 * VOF_MAXFP;
 static_assert(MX_MAXT <= 32, "one flux-polyhedron tetrahedron per lane");
@@ -135,11 +138,14 @@ struct MXArgs {
 
 constexpr int MX_CAND = 32;    // candidate cell tetrahedra buffered per warp: one per lane
 constexpr int MX_QUEUE = MX_MAXT * MX_CAND;  // clip jobs: one per (T, K) pair at most
-constexpr int MX_STACK = 92;                 // pieces of clip jobs waiting for their next plane
+// pieces of clip jobs waiting for their next plane, per warp (the stack depth
+// S is a launch choice: 92 commits more lanes per split step, 56 leaves room
+// for more resident warps)
+constexpr int MX_STACK_WIDE = 92, MX_STACK_SLIM = 56;
 
 // per warp; in FP32 the 48-byte tetrahedra are moved as three float4
 // (conflict-free across a warp)
-template <class R>
+template <class R, int MX_STACK>
 struct __align__(16) MXShared {
     RTet<R> S[MX_STACK];     // pieces
     RTet<R> T[MX_MAXT];      // flux-polyhedron tetrahedra
@@ -249,8 +255,8 @@ __device__ __forceinline__ void fsplit(const RTet<R> &t, const R s[4], int nin, 
 // piece has at most 4 planes to go, so the split pieces keep i + 1 + 2 (r - 1)
 // <= MX_STACK for depth i and r planes to go: the top one alone always fits
 // once the leaves are gone, and the stacks cannot overflow.
-template <class R, class Wk>
-__device__ __forceinline__ void mx_clip(MXShared<R> &sh, int nq, R tol, R &accs, R &accc, Wk &wk)
+template <class R, int MX_STACK, class Wk>
+__device__ __forceinline__ void mx_clip(MXShared<R, MX_STACK> &sh, int nq, R tol, Acc<R> &acc, Wk &wk)
 {
     const int lane = threadIdx.x & 31;
     const unsigned le = ((1u << lane) << 1) - 1u;
@@ -283,7 +289,7 @@ __device__ __forceinline__ void mx_clip(MXShared<R> &sh, int nq, R tol, R &accs,
                         v6 *= rfrac_below(h0, h1, h2, h3);
                     }
                 }
-                if (v6 != R(0)) acc_add(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
+                if (v6 != R(0)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);
             }
             nl -= p;
             __syncwarp();
@@ -349,7 +355,7 @@ __device__ __forceinline__ void mx_clip(MXShared<R> &sh, int nq, R tol, R &accs,
             wk.add(WK_VOL, lw & 1);
             wk.add(WK_FRAC, lw >> 1);
             if (cut && nch > 0) wk.add(WK_EDGE, nin == 2 ? 4 : 3);
-            if (v6 != R(0)) acc_add(accs, accc, sh.Tsg[ti] * sh.Kw[k] * v6);
+            if (v6 != R(0)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);
             if (nch > 0) {
                 const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
                 // parts of the lanes before this one that go the same way
@@ -378,8 +384,9 @@ __device__ __forceinline__ void mx_clip(MXShared<R> &sh, int nq, R tol, R &accs,
 // distances of the prism's six points to K's planes, from which each of its
 // three tetrahedra is classified: outside a plane, inside every plane (adds
 // |T| at once), or a clip job.
-template <class R, class Wk>
-__device__ __forceinline__ void mx_flush(MXShared<R> &sh, int nt, int ncand, R tol, R &accs, R &accc, Wk &wk)
+template <class R, int MX_STACK, class Wk>
+__device__ __forceinline__ void mx_flush(MXShared<R, MX_STACK> &sh, int nt, int ncand, R tol, Acc<R> &acc,
+                                         Wk &wk)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -446,7 +453,7 @@ __device__ __forceinline__ void mx_flush(MXShared<R> &sh, int nt, int ncand, R t
                 const int t = 3 * pr + j;
                 const R sg = sh.Tsg[t];
                 if (sg != R(0) && !outside[j]) {
-                    if (mask[j] == 0) acc_add(accs, accc, sg * sh.Kw[k] * sh.Tv6[t]);
+                    if (mask[j] == 0) acc_add(acc, sg * sh.Kw[k] * sh.Tv6[t]);
                     else { job[j] = true; code[j] = (unsigned)t | ((unsigned)k << 5) | (mask[j] << 10); }
                 }
             }
@@ -458,19 +465,22 @@ __device__ __forceinline__ void mx_flush(MXShared<R> &sh, int nt, int ncand, R t
             nq += __popc(bm);
         }
     }
-    if (nq > 0) mx_clip(sh, nq, tol, accs, accc, wk);
+    if (nq > 0) mx_clip(sh, nq, tol, acc, wk);
     __syncwarp();
 }
 
 // W warps (faces) per block; blocks per SM as shared memory allows (the FP64
 // form's per-warp buffers are twice as large)
-template <class R> constexpr int mx_resident(int w) { return w == 1 ? 15 : w == 2 ? 8 : 5; }
-template <> constexpr int mx_resident<double>(int w) { return w == 1 ? 8 : 4; }
+template <class R> constexpr int mx_resident(int w, int st)
+{
+    return st == MX_STACK_WIDE ? (w == 1 ? 15 : w == 2 ? 8 : 5) : (w == 1 ? 18 : w == 2 ? 9 : 6);
+}
+template <> constexpr int mx_resident<double>(int w, int) { return w == 1 ? 8 : 4; }
 
 template <class R> __device__ __forceinline__ R rconv(double v) { return (R)v; }
 
-template <class R, bool LIST, class Wk>
-__device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &a, MXShared<R> &sh)
+template <class R, int MX_STACK, bool LIST, class Wk>
+__device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &a, MXShared<R, MX_STACK> &sh)
 {
     using V = R3<R>;
     const R4<R> *fpl = static_cast<const R4<R> *>(a.fpl), *cbl = static_cast<const R4<R> *>(a.cbl);
@@ -528,7 +538,7 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
         const double Ff = a.F[f];
         const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
         const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
-        const bool comp = a.alpha[up] >= 0.5 && lamf >= 0.0 && !__ldg(m.fopen + f);
+        const bool comp = ge_pos(a.alpha[up], 0.5) && lamf >= 0.0 && !__ldg(m.fopen + f);
         const int nt = n == 3 ? 3 : 3 * n;
         // signed distances (to unit-normal planes) within the on-plane band of
         // the face (FP32: 2e-6 of the face size, FP64: 1e-14) are taken as zero:
@@ -618,7 +628,7 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
             pb[i] = v;
         }
         __syncwarp();
-        R accs = R(0), accc = R(0);
+        Acc<R> acc;
         wk.add(WK_VOL, lane < nt);  // the flux polyhedron's tetrahedra
         wk.face();
         int ncand = 0;
@@ -645,7 +655,8 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                         c = __ldg(m.scell + s);
                         al = a.alpha[c];
                         // an empty cell carries no phase, a full cell no void
-                        if (!((!comp && al <= eps) || (comp && al >= 1.0 - eps))) {
+                        // thresholds on the integer pipe (bit-pattern order of doubles)
+                        if (!((!comp && le_pos(al, eps)) || (comp && ge_pos(al, 1.0 - eps)))) {
                             const V3 cc = ld3(m.cc, m.nc, c);
                             dc = r3(rconv<R>(cc.x - o.x), rconv<R>(cc.y - o.y), rconv<R>(cc.z - o.z));
                             const R4<R> cb0 = ldg4(cbl, 2 * (long)c), cb1 = ldg4(cbl, 2 * (long)c + 1);
@@ -660,7 +671,7 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                     if (pass) {
                         t0 = __ldg(a.ctptr + c);
                         nkt = __ldg(a.ctptr + c + 1) - t0;
-                        if (al > eps && al < 1.0 - eps) {
+                        if (gt_pos(al, eps) && lt_pos(al, 1.0 - eps)) {
                             if (a.flags[c] & VOF_ORIENTED) {
                                 V3 hn = ld3(a.n, m.nc, c);
                                 double hd = a.d[c] - dot(hn, o);
@@ -730,7 +741,7 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
             }
             const unsigned cmask = __ballot_sync(0xffffffffu, cand);
             if (fin ? ncand > 0 : ncand + __popc(cmask) > MX_CAND) {
-                mx_flush(sh, nt, ncand, tol, accs, accc, wk);
+                mx_flush(sh, nt, ncand, tol, acc, wk);
                 ncand = 0;
                 continue;  // the batch again (or the end)
             }
@@ -749,33 +760,32 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
         }
         // lane sums (and their compensations) merged across the warp, then the
         // 1/6 of the volumes in FP64
-        R rs = accs, rc = accc;
 #pragma unroll
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
-            const R xs = __shfl_xor_sync(0xffffffffu, rs, o2), xc = __shfl_xor_sync(0xffffffffu, rc, o2);
-            acc_add(rs, rc, xs);
-            rc += xc;
+            const R xs = __shfl_xor_sync(0xffffffffu, acc.s, o2), xc = __shfl_xor_sync(0xffffffffu, acc.c, o2);
+            acc_add(acc, xs);
+            acc.c += xc;
         }
-        double acc = ((double)rs + (double)rc) / 6.0;
-        if (comp) acc = Ff * a.dt - acc;
-        if (lane == 0) a.Va[f] = acc;
+        double va = ((double)acc.s + (double)acc.c) * (1.0 / 6.0);
+        if (comp) va = Ff * a.dt - va;
+        if (lane == 0) a.Va[f] = va;
         __syncwarp();
     }
     wk.flush(a.work, lane);
 }
 
-template <bool LIST, int W, class Wk>
-__global__ void __launch_bounds__(W * 32, mx_resident<float>(W)) k_phase_flux_mixed(DevMesh m, MXArgs a)
+template <bool LIST, int W, int ST, class Wk>
+__global__ void __launch_bounds__(W * 32, mx_resident<float>(W, ST)) k_phase_flux_mixed(DevMesh m, MXArgs a)
 {
-    __shared__ MXShared<float> shm[W];
-    phase_flux_body<float, LIST, Wk>(m, a, shm[threadIdx.x >> 5]);
+    __shared__ MXShared<float, ST> shm[W];
+    phase_flux_body<float, ST, LIST, Wk>(m, a, shm[threadIdx.x >> 5]);
 }
 
 template <bool LIST, int W, class Wk>
-__global__ void __launch_bounds__(W * 32, mx_resident<double>(W)) k_phase_flux(DevMesh m, MXArgs a)
+__global__ void __launch_bounds__(W * 32, mx_resident<double>(W, MX_STACK_WIDE)) k_phase_flux(DevMesh m, MXArgs a)
 {
-    __shared__ MXShared<double> shm[W];
-    phase_flux_body<double, LIST, Wk>(m, a, shm[threadIdx.x >> 5]);
+    __shared__ MXShared<double, MX_STACK_WIDE> shm[W];
+    phase_flux_body<double, MX_STACK_WIDE, LIST, Wk>(m, a, shm[threadIdx.x >> 5]);
 }
 
 // geometry of every cell relative to its centre (context creation): face
@@ -910,8 +920,8 @@ int launch_pf_all(vof_ctx *c, const double *alpha, const double *n, const double
     MXArgs a = mx_args(c, alpha, n, d, flags, Up, F, lambda, dt, Va, nullptr, nullptr, nullptr,
                        c->work_on ? c->work : nullptr);
     if (c->precision == VOF_MIXED) {
-        if (c->work_on) k_phase_flux_mixed<false, 2, WkOn><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
-        else k_phase_flux_mixed<false, 2, WkOff><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+        if (c->work_on) k_phase_flux_mixed<false, 2, MX_STACK_WIDE, WkOn><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
+        else k_phase_flux_mixed<false, 2, MX_STACK_WIDE, WkOff><<<cdiv((long)c->nf * 32, 64), 64, 0, s>>>(c->m, a);
     } else {
         if (c->work_on) k_phase_flux<false, 1, WkOn><<<cdiv((long)c->nf * 32, 32), 32, 0, s>>>(c->m, a);
         else k_phase_flux<false, 1, WkOff><<<cdiv((long)c->nf * 32, 32), 32, 0, s>>>(c->m, a);
@@ -927,21 +937,29 @@ int launch_pf_list(vof_ctx *c, const double *alpha, const double *F, double dt, 
     a.next = c->counters + CNT_PFNEXT;  // zeroed with the step's counters
     if (c->precision != VOF_MIXED) {
         // the FP64 form: one warp per block, as many blocks as shared memory allows
-        if (c->work_on) k_phase_flux<true, 1, WkOn><<<sms * mx_resident<double>(1), 32, 0, s>>>(c->m, a);
-        else k_phase_flux<true, 1, WkOff><<<sms * mx_resident<double>(1), 32, 0, s>>>(c->m, a);
+        if (c->work_on) k_phase_flux<true, 1, WkOn><<<sms * mx_resident<double>(1, MX_STACK_WIDE), 32, 0, s>>>(c->m, a);
+        else k_phase_flux<true, 1, WkOff><<<sms * mx_resident<double>(1, MX_STACK_WIDE), 32, 0, s>>>(c->m, a);
         return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
     }
-    // launch configuration (vof_batch_tune): warps per block, and grid = SMs x
-    // resident blocks x multiplier
+    // launch configuration (vof_batch_tune): warps per block, stack depth, and
+    // grid = SMs x resident blocks x multiplier
     const int w = c->pf_warps >= 1 && c->pf_warps <= 3 ? c->pf_warps : 2;
     const int mult = c->pf_mult >= 1 ? c->pf_mult : 1;
-    if (c->work_on)  // instrumented variant (vof_count_work), the 2-warp shape
-        k_phase_flux_mixed<true, 2, WkOn><<<sms * mx_resident<float>(2) * mult, 64, 0, s>>>(c->m, a);
-    else if (w == 1)
-        k_phase_flux_mixed<true, 1, WkOff><<<sms * mx_resident<float>(1) * mult, 32, 0, s>>>(c->m, a);
-    else if (w == 2)
-        k_phase_flux_mixed<true, 2, WkOff><<<sms * mx_resident<float>(2) * mult, 64, 0, s>>>(c->m, a);
-    else
-        k_phase_flux_mixed<true, 3, WkOff><<<sms * mx_resident<float>(3) * mult, 96, 0, s>>>(c->m, a);
+    const bool slim = c->pf_stack == 1;
+#define PF_GO(W_, ST_, WK_)                                                                                  \
+    k_phase_flux_mixed<true, W_, ST_, WK_><<<sms * mx_resident<float>(W_, ST_) * mult, 32 * W_, 0, s>>>(c->m, a)
+    if (c->work_on) {  // instrumented variant (vof_count_work), two warps per block
+        if (slim) PF_GO(2, MX_STACK_SLIM, WkOn);
+        else PF_GO(2, MX_STACK_WIDE, WkOn);
+    } else if (slim) {
+        if (w == 1) PF_GO(1, MX_STACK_SLIM, WkOff);
+        else if (w == 2) PF_GO(2, MX_STACK_SLIM, WkOff);
+        else PF_GO(3, MX_STACK_SLIM, WkOff);
+    } else {
+        if (w == 1) PF_GO(1, MX_STACK_WIDE, WkOff);
+        else if (w == 2) PF_GO(2, MX_STACK_WIDE, WkOff);
+        else PF_GO(3, MX_STACK_WIDE, WkOff);
+    }
+#undef PF_GO
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }

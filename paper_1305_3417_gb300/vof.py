@@ -52,7 +52,7 @@ EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "v
            "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
            "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
            "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess", "vof_set_gradient", "vof_lsq_gradient",
-           "vof_evsd", "vof_remap"]
+           "vof_evsd", "vof_remap", "vof_tune"]
 GRAD_NAG, GRAD_LSQ = 0, 1
 MLP_IN, MLP_HID, MLP_OUT = 33, 64, 4
 MLP_NPARAM = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
@@ -108,6 +108,7 @@ def lib():
         "vof_lsq_gradient": (I, [P, P, P, P]),
         "vof_evsd": (I, [P, P, P, P, ctypes.POINTER(ctypes.c_double), I, P, P]),
         "vof_remap": (I, [P, P, P, P, P, P, P, P, P, P]),
+        "vof_tune": (I, [P, P, P, P, D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -313,6 +314,15 @@ def vof_remap(dst, src, alpha_src, n_src, d_src, flags_src, pair_ptr, pair_src, 
     """Alg. 2: alpha_dst of context dst from src's planes over the cell pairs."""
     _check(lib().vof_remap(dst, src, _ptr(alpha_src), _ptr(n_src), _ptr(d_src), _ptr(flags_src), _ptr(pair_ptr),
                            _ptr(pair_src), _ptr(alpha_dst), _stream(stream)), "vof_remap")
+
+
+def vof_tune(h, alpha, Uc, F, dt, stream=None):
+    """Autotunes the context's mixed phase-flux launch on one step from alpha
+    (left unchanged); returns (config, ms)."""
+    cfg, ms = ctypes.c_int(0), ctypes.c_float(0.0)
+    _check(lib().vof_tune(h, _ptr(alpha), _ptr(Uc), _ptr(F), float(dt), ctypes.byref(cfg), ctypes.byref(ms),
+                          _stream(stream)), "vof_tune")
+    return int(cfg.value), float(ms.value)
 
 
 def vof_count_work(h, on: bool = True):

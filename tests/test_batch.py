@@ -102,11 +102,14 @@ def test_batch_tuner(torch, batch):
     cfg, ms = b.tune(a0, U, F)
     torch.cuda.synchronize()
     assert torch.equal(a0, keep)            # the tuner steps on a copy
-    assert cfg in {16 * w + m for w in (1, 2, 3) for m in (1, 2, 4)} and ms > 0
+    assert cfg in {256 * st + 16 * w + m for st in (0, 1) for w in (1, 2, 3) for m in (1, 2, 4)} and ms > 0
     tuned = a0.clone()
     b.advect(tuned, U, F)                   # tuned launch shape (new graph)
     torch.cuda.synchronize()
-    assert torch.equal(tuned, ref)
+    if cfg // 256 == 0:                     # the default staging depth: bit for bit
+        assert torch.equal(tuned, ref)
+    else:                                   # the other depth: to the sums' rounding
+        assert (tuned - ref).abs().max().item() < 1e-13
 
 
 @pytest.mark.gpu

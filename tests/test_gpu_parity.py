@@ -453,3 +453,29 @@ def test_advect_mixed_replay(torch, O, name):
         assert stats[4] >= -1e-12 and stats[5] <= 1 + 1e-12
     print(f"mixed advect {name}: max |d alpha| = {worst:.3e}")
     assert worst < MIXED_ALPHA_TOL
+
+
+def test_tuner_keeps_the_state_and_the_step(torch, O):
+    """vof_tune times every phase-flux launch shape and staging depth on a copy
+    of the state and keeps the fastest.  The step it then runs equals the
+    default launch's bit for bit when the staging depth is the default's (a
+    face's pieces then fall to the same lanes in the same order), and to the
+    rounding of the compensated sums otherwise."""
+    from paper_1305_3417_gb300 import vof
+    w, ctx, om = contexts(torch, O, "deform20", precision=1)
+    F, U, dt = w.step_inputs(3)
+    tU, tF = T(torch, U), T(torch, F)
+    ref = T(torch, w.alpha0)
+    ctx.advect(ref, tU, tF, dt)
+    a = T(torch, w.alpha0)
+    keep = a.clone()
+    cfg, ms = vof.vof_tune(ctx.h, a, tU, tF, dt)
+    torch.cuda.synchronize()
+    assert torch.equal(a, keep) and ms > 0
+    assert cfg in {256 * st + 16 * wp + m for st in (0, 1) for wp in (1, 2, 3) for m in (1, 2, 4)}
+    ctx.advect(a, tU, tF, dt)
+    if cfg // 256 == 0:
+        assert torch.equal(a, ref)
+    else:
+        assert (a - ref).abs().max().item() < 1e-13
+    assert ctx.status() == 0

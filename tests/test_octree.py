@@ -180,3 +180,48 @@ def test_octree_initial_fractions_hold_the_sphere(wl):
     a = wl.alpha0
     assert a.min() >= 0.0 and a.max() <= 1.0
     assert abs((V * a).sum() / (4.0 / 3.0 * np.pi * 0.15 ** 3) - 1.0) < 1e-3
+
+
+@pytest.mark.gpu
+def test_octree_full_size_sampled(torch, oracle_lib):
+    """One mixed-precision step of config 5's octree (64^3 base, two levels,
+    508k cells) in the benchmark's launch configuration, compared with the
+    oracle on sampled cells (the oracle reconstructs the stencil cells and
+    corrects and fluxes the faces it needs)."""
+    from paper_1305_3417_gb300 import vof
+    O = oracle_lib
+    w = I.make_workload("octree")
+    m = w.mesh
+    ctx = vof.VofContext(m, precision=vof.MIXED, bound=False)
+    om = O.OracleMesh(m)
+    F, U, dt = w.step_inputs(0)
+    ta = torch.from_numpy(w.alpha0.copy()).cuda()
+    stats = ctx.advect(ta, torch.from_numpy(np.ascontiguousarray(U).reshape(-1).copy()).cuda(),
+                       torch.from_numpy(F.copy()).cuda(), dt).cpu().numpy()
+    assert ctx.status() == 0
+    a1 = ta.cpu().numpy()
+    rng = np.random.default_rng(29)
+    cls = om.classify_faces(w.alpha0)
+    band = np.flatnonzero((cls == 2) & (F != 0))
+    assert stats[7] == band.size
+    band_cells = np.unique(np.concatenate([m.owner[band], m.neighbour[band[band < m.n_internal]]]))
+    cells = np.unique(np.concatenate([rng.choice(band_cells, 50, replace=False),
+                                      rng.choice(m.n_cells, 20, replace=False)]))
+    own = {c: np.flatnonzero(m.owner == c) for c in cells}
+    nei = {c: np.flatnonzero(m.neighbour == c) for c in cells}
+    faces = np.unique(np.concatenate(list(own.values()) + list(nei.values())))
+    sten = np.unique(np.concatenate([om.stencil(f) for f in faces]))
+    on, od, ofl, _, _ = om.reconstruct(w.alpha0, sel=sten)
+    oUp = om.point_velocity(U)
+    olam, _, _ = om.correct_flux(oUp, F, dt, sel=faces)
+    oVa, ost = om.phase_flux(w.alpha0, on, od, ofl, oUp, F, olam, dt, sel=faces)
+    assert ost == 0
+    _, vc, _, _ = om.geometry()
+    worst = 0.0
+    for c in cells:
+        pre = w.alpha0[c] - (oVa[own[c]].sum() - oVa[nei[c]].sum()) / vc[c]
+        worst = max(worst, abs(a1[c] - pre))
+    print(f"octree 64^3 base, mixed, one step: max |d alpha| on {cells.size} sampled cells = {worst:.2e}")
+    assert worst < 2e-5
+    assert abs(stats[1] - stats[0]) / stats[0] < 1e-12
+    ctx.close()
