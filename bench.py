@@ -58,9 +58,11 @@ BYTES_PER_FACE = 72.0
 # dram__bytes_write.sum, mean of three launches of one ncu capture of the
 # default command (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,
 # gpu__time_duration.sum -k regex:k_phase_flux_mixed -s 3 -c 3 python bench.py
-# --steps 2 --warmup 3 --no-cpu-baseline --fp64-steps 0 --full-run 0);
+# --steps 2 --warmup 3 --no-tune --no-cpu-baseline --fp64-steps 0 --full-run 0);
 # valid while the kernel's sources hash to the captured digest, else null.
-TRAFFIC = {}
+TRAFFIC = {
+    ("deform3d", 128, "mixed"): {"bytes": 68.50e6, "sources_sha256": "477cc77e2a33c77b56176b4fed93decde628915ba78be1ab4f6b67e1990dfbd4"},
+}
 TRAFFIC_SOURCES = ["paper_1305_3417_gb300/csrc/vof_phase_flux.cu", "paper_1305_3417_gb300/csrc/vof_device.cuh"]
 
 
@@ -197,6 +199,40 @@ def host_link_gbps(stream, host):
         torch.cuda.synchronize()
         out[name] = 3 * host.numel() * host.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
     del dev
+    return out
+
+
+def host_buffers_diag(stream, bufs, device):
+    """Where the end-to-end copies' time goes: H2D rate of each pinned buffer
+    copied alone (GB/s: min, median, max), whether all are pinned, and the
+    GPU's NUMA node and local CPUs as the kernel reports them."""
+    import torch
+    rates = []
+    for b in bufs:
+        dst = torch.empty_like(b, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dst.copy_(b, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rates.append(b.numel() * b.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+        del dst
+    out = {"h2d_GBps_per_buffer": {"min": float(np.min(rates)), "median": float(np.median(rates)),
+                                   "max": float(np.max(rates)), "buffers": len(rates)},
+           "pinned": bool(all(b.is_pinned() for b in bufs))}
+    try:
+        bus = torch.cuda.get_device_properties(device).pci_bus_id.lower()
+        base = f"/sys/bus/pci/devices/{bus}"
+        with open(base + "/numa_node") as f:
+            out["gpu_numa_node"] = int(f.read().strip())
+        with open(base + "/local_cpulist") as f:
+            out["gpu_local_cpus"] = f.read().strip()
+    except Exception:
+        pass
+    try:
+        out["process_cpus"] = len(os.sched_getaffinity(0))
+    except Exception:
+        pass
     return out
 
 
@@ -487,19 +523,29 @@ def run_batch(args, world, rank, local):
             "unit": "TFLOP/s", "frac": achieved * 1e12 / alu, "traffic": None,
             "peak_source": "measured FP32 FMA probe (vof_probe_fma)", "group_ms_per_step": per_launch,
             "work_per_launch": work, "flops_per_launch": pf}
-    # end to end with host buffers (context's host-buffer step, dt = 1)
+    # end to end through the batched call itself: every step copies alpha, U
+    # and F from pinned host memory, replays the step and reads alpha back
     ha = torch.from_numpy(b.alpha0.copy()).pin_memory()
     hU, hF = U.cpu().pin_memory(), F.cpu().pin_memory()
-    hstat = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
-    vof.vof_advect_host(ctx, ha, hU, hF, 1.0, hstat)
+    da, dU, dF = torch.empty_like(alpha), torch.empty_like(U), torch.empty_like(F)
+
+    def host_step():
+        da.copy_(ha, non_blocking=True)
+        dU.copy_(hU, non_blocking=True)
+        dF.copy_(hF, non_blocking=True)
+        bt.advect(da, dU, dF, stats, mass)
+        ha.copy_(da, non_blocking=True)
+
+    host_step()
     torch.cuda.synchronize()
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for _ in range(args.steps):
-        vof.vof_advect_host(ctx, ha, hU, hF, 1.0, hstat)
+        host_step()
     e3.record(stream)
     torch.cuda.synchronize()
-    e2e = faces / (max_over_ranks(e2.elapsed_time(e3), world, dev) * 1e-3) / 1e6
+    e2e_ms = max_over_ranks(e2.elapsed_time(e3), world, dev) / args.steps
+    e2e = faces / (e2e_ms * args.steps * 1e-3) / 1e6
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = batch_cpu_baseline(b, ncase=args.cpu_steps * 4)
@@ -508,8 +554,9 @@ def run_batch(args, world, rank, local):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
                 "config": batch_config(args, b, hr, tr, {"config": tune, "ms": tune_ms}),
-                "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * m.n_cells + 24 * m.n_cells + 8 * m.n_faces,
-                        "d2h_bytes_per_step": 8 * m.n_cells + 8 * vof.S_LEN},
+                "e2e": {"value": e2e, "unit": UNIT, "ms_per_step": e2e_ms,
+                        "h2d_bytes_per_step": ha.numel() * 8 + hU.numel() * 8 + hF.numel() * 8,
+                        "d2h_bytes_per_step": ha.numel() * 8},
                 "gpu_launches": launches, "roofline": roof, "cpu_baseline": base, "clocks": clk.summary(),
                 "quality": {"rel_volume_drift_last_step": float(abs(S[1] + S[10] - S[0]) / S[0]),
                             "case_mass_min": float(m1.min()),
@@ -808,6 +855,7 @@ def main():
     h2d = 8 * m.n_cells + 24 * m.n_cells + 8 * m.n_faces
     d2h = 8 * m.n_cells + 8 * vof.S_LEN
     link = host_link_gbps(stream, hU[0])
+    diag = host_buffers_diag(stream, [ha] + hU + hF, dev)
 
     full = None
     do_full = args.full_run if args.full_run >= 0 else int(args.workload in ("deform3d", "vortex_tet")
@@ -864,7 +912,7 @@ def main():
                 "dtype": "f64" if prec == vof.FP64 else "f32+f64",
                 "data": "synthetic", "config": {**config(args, w), "tuned_launch": tuned},
                 "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": ms_e2e / args.steps, "host_link_GBps": link,
+                        "ms_per_step": ms_e2e / args.steps, "host_link_GBps": link, "host_buffers": diag,
                         "call_ms": {"min": float(np.min(e2e_steps)), "median": float(np.median(e2e_steps)),
                                     "max": float(np.max(e2e_steps))}},
                 "gpu_launches": launches, "roofline": roof, "step_roofline": step_roof,

@@ -386,7 +386,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->flags = dev_alloc<uint8_t>(c, nc, &err);
     c->pit = dev_alloc<int>(c, nc, &err);
     c->Va = dev_alloc<double>(c, nf, &err);
-    c->bscr = dev_alloc<double>(c, 4 * (size_t)nc, &err);
+    c->bscr = dev_alloc<double>(c, 3 * (size_t)nc, &err);
     c->partial = dev_alloc<double>(c, 10 * 1024, &err);
     c->stats_dev = dev_alloc<double>(c, VOF_S_LEN, &err);
     c->status = dev_alloc<unsigned>(c, 1, &err);
@@ -409,7 +409,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->ktl = dev_alloc<unsigned char>(c, e4 * 6 * (size_t)ctptr[nc], &err);
     if (err) { vof_destroy(c); return err; }
     cudaMemset(c->work, 0, WK_LEN * sizeof(unsigned long long));
-    cudaMemset(c->bscr, 0, sizeof(double) * 4 * nc);
+    cudaMemset(c->bscr, 0, sizeof(double) * 3 * nc);
     cudaMemset(c->counters, 0, sizeof(int) * CNT_ALLOC);
     cudaMemset(c->status, 0, sizeof(unsigned));
     cudaMemset(c->n, 0, sizeof(double) * 3 * nc);

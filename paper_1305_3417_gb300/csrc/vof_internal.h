@@ -74,7 +74,7 @@ struct vof_ctx {
     uint8_t *flags;
     int *pit;
     double *Va;
-    double *bscr;                // redistribution scratch, 4 doubles per cell
+    double *bscr;                // redistribution scratch, 3 doubles per cell
     double *gpartial;            // global bounding partial sums, 4 per segment
     // regions of the global bounding step (whole mesh, or the cases of a
     // batch): segments {region, first cell, end cell, -} and, per region, its

@@ -1002,8 +1002,8 @@ __device__ __forceinline__ double recv_w(double a, double V)
 }
 
 // scratch per cell: [1/W (0 where the source has no receiver), receiver
-// scales sp, sm, amount the source placed]
-enum { BS_RW = 0, BS_SP, BS_SM, BS_REL, BS_N = 4 };
+// scales sp, sm]
+enum { BS_RW = 0, BS_SP, BS_SM, BS_N = 3 };
 
 struct BoundBufs {
     int *la;             // source list (from the update kernel), capacity nc
@@ -1032,9 +1032,10 @@ __device__ __forceinline__ int first_source(const DevMesh &m, const double *alph
     return first;
 }
 
-// One pass as four phases over the source list (count on the device): the
-// receiver weight around each source, receiver scales, placement, new values
-// (then apply); t0 / nt: this thread's index and the thread count of the grid.
+// One pass as three phases over the source list (count on the device): the
+// receiver weight around each source, receiver scales, new values (a source's
+// own placement summed where its new value is formed), then apply; t0 / nt:
+// this thread's index and the thread count of the grid.
 // A source with something left and a receiver is counted in *act.
 __device__ __forceinline__ void bp_room(const DevMesh &m, const double *alpha, const BoundBufs &b, int *act, long t0, long nt)
 {
@@ -1081,27 +1082,6 @@ __device__ __forceinline__ void bp_scale(const DevMesh &m, const double *alpha, 
     }
 }
 
-__device__ __forceinline__ void bp_place(const DevMesh &m, const double *alpha, const BoundBufs &b, long t0, long nt)
-{
-    const int n = min(*b.n0, b.cap);
-    double *bs = b.bs;
-    for (long i = t0; i < n; i += nt) {
-        int c = b.la[i];
-        double *q = bs + BS_N * (size_t)c;
-        const double a = alpha[c], V = m.vc[c], rW = q[BS_RW];
-        double g = 0.0;
-        if (rW > 0.0) {
-            const bool xe = is_exc(a);
-            const double e = xe ? (a - 1.0) * V : -a * V;
-            for_nbrs(m, c, [&](int nb, int) {
-                const double w = recv_w(alpha[nb], m.vc[nb]);
-                if (w > 0.0) g += e * (w * rW) * bs[BS_N * (size_t)nb + (xe ? BS_SP : BS_SM)];
-            });
-        }
-        q[BS_REL] = g;
-    }
-}
-
 // new values of the sources and their neighbours, each cell once: by the
 // lowest-index source in its closed face neighbourhood
 __device__ __forceinline__ void bp_new(const DevMesh &m, const double *alpha, const BoundBufs &b, int *npend, unsigned *status,
@@ -1117,9 +1097,21 @@ __device__ __forceinline__ void bp_new(const DevMesh &m, const double *alpha, co
             if (x < 0 || first_source(m, alpha, x, true) != c) continue;
             const double ax = alpha[x], V = m.vc[x], wx = recv_w(ax, V);
             double dV = 0.0;
-            if (is_exc(ax)) dV -= bs[BS_N * (size_t)x + BS_REL];
-            else if (is_def(ax)) dV += bs[BS_N * (size_t)x + BS_REL];
-            if (wx > 0.0) {
+            const bool xe = is_exc(ax);
+            if (xe || is_def(ax)) {
+                // a source: what it places in its receivers (each scaled to fit)
+                const double rWx = bs[BS_N * (size_t)x + BS_RW];
+                if (rWx > 0.0) {
+                    const double e = xe ? (ax - 1.0) * V : -ax * V;
+                    double g = 0.0;
+                    for_nbrs(m, x, [&](int nb, int) {
+                        const double w = recv_w(alpha[nb], m.vc[nb]);
+                        if (w > 0.0) g += e * (w * rWx) * bs[BS_N * (size_t)nb + (xe ? BS_SP : BS_SM)];
+                    });
+                    dV += xe ? -g : g;
+                }
+            } else if (wx > 0.0) {
+                // a receiver: what its source neighbours place in it
                 const double SPx = bs[BS_N * (size_t)x + BS_SP], SMx = bs[BS_N * (size_t)x + BS_SM];
                 for_nbrs(m, x, [&](int s, int) {
                     const double as = alpha[s], rW = bs[BS_N * (size_t)s + BS_RW];
@@ -1293,7 +1285,7 @@ __device__ bool grid_sync(unsigned *count, unsigned *generation, unsigned *statu
 
 // The whole redistribution, the post-bounding mass and the step statistics in
 // one cooperative launch, a grid barrier between the phases: passes of the
-// local redistribution (weights, scales, placement, new values, apply) while
+// local redistribution (weights, scales, new values, apply) while
 // some source has something left and a receiver, segment sums, region totals,
 // global fallback with the mass partials, statistics (block 0).
 struct BoundStep {
@@ -1343,8 +1335,6 @@ __global__ void __launch_bounds__(BA_THREADS, 4) k_bound_step(DevMesh m, BoundSt
         if (*(volatile int *)act == 0) break;
         if (lead) *a.b.npass = p + 1;
         bp_scale(m, a.alpha, a.b, tl, nt);
-        if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
-        bp_place(m, a.alpha, a.b, tl, nt);
         if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
         bp_new(m, a.alpha, a.b, a.npend, a.status, tl, nt);
         if (!grid_sync(a.bar_count, a.bar_gen, a.status)) return;
