@@ -76,6 +76,27 @@ typedef struct {
     const int32_t *neighbour;    /* [n_internal] */
     const uint8_t *wall;         /* [n_faces - n_internal]: 1 = wall (no normal
                                     flow), 0 = open; NULL makes all walls */
+    /* Periodic meshes (the paper's translation case runs on a periodic box,
+     * Sec. 4.2); all NULL for other meshes.
+     *   period       [9]: period vectors L0, L1, L2 as rows (unused rows zero);
+     *   point_master [n_points]: the master point each point is an image of
+     *                (itself for a master); the images of one master are one
+     *                point of the periodic domain;
+     *   point_image  [3*n_points], each in {-1, 0, 1}: P = P_master + sum_i k_i L_i;
+     *   face_image   [n_faces - n_internal]: for the boundary face that is a
+     *                periodic internal face's copy on its neighbour's side, that
+     *                internal face; -1 for other boundary faces.
+     * A periodic internal face is listed with its points on its owner's side;
+     * its neighbour is built from the copy (same points, one translation
+     * away), which carries no flux: the internal face's phase flux leaves the
+     * owner and enters the neighbour.  The cells around a point are those
+     * around all its images, each moved next to it; face stencils and
+     * inverse-distance weights use the moved cells.  Flux polyhedra order
+     * their points by master index. */
+    const double *period;
+    const int32_t *point_master;
+    const int8_t *point_image;
+    const int32_t *face_image;
 } vof_mesh;
 
 typedef struct {
@@ -107,9 +128,12 @@ typedef struct vof_ctx vof_ctx;
  * of Eq. w_pc, NAG face weights of Sec. 2.2.1) in kernels, and allocates all
  * per-step scratch.  Synchronous.  Fails with VOF_ERR_BAD_MESH on an index out
  * of range, a cell tetrahedron of non-positive volume, a face of fewer than 3
- * or more than 8 points, or a cell of more than 96 tetrahedra (a face of n > 3
- * points gives n; 2:1 octree cells have up to 78).  *out receives a context the
- * caller releases with vof_destroy. */
+ * or more than 8 points, a cell of more than 96 tetrahedra (a face of n > 3
+ * points gives n; 2:1 octree cells have up to 78), or periodic data that do
+ * not fit together (a copy not owned by its face's neighbour or not the same
+ * points one translation away, images more than one period apart, a cell
+ * touching two images of one point).  *out receives a context the caller
+ * releases with vof_destroy. */
 int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out);
 void vof_destroy(vof_ctx *ctx);
 
@@ -253,7 +277,7 @@ int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double 
  * case_cell_ptr[ncases + 1] (host) the first cell of each case (0 first,
  * n_cells last, strictly increasing).  Synchronous; *out receives a batch the
  * caller releases with vof_batch_destroy.  Errors as vof_create, and
- * VOF_ERR_INVALID_ARG for bad case offsets. */
+ * VOF_ERR_INVALID_ARG for bad case offsets or a periodic mesh. */
 typedef struct vof_batch vof_batch;
 int vof_batch_create(const vof_mesh *mesh, const int32_t *case_cell_ptr, int ncases, const vof_options *opt,
                      vof_batch **out);
@@ -427,6 +451,10 @@ int vof_status(vof_ctx *ctx, uint32_t *bits, void *stream);
 int vof_last_launch_count(vof_ctx *ctx);
 
 const char *vof_error_string(int code);
+/* Why the last vof_create (or vof_batch_create) on the calling thread returned
+ * VOF_ERR_BAD_MESH: a static string naming the failed check ("" when the last
+ * call did not fail that way).  Owned by the library. */
+const char *vof_create_error(void);
 
 #ifdef __cplusplus
 }

@@ -45,6 +45,8 @@ def lib():
         P, I, D, V = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, None
         sig = {
             "vo_mesh_create": (P, [I, I, I, I, P, P, P, P, P, P, P, P]),
+            "vo_mesh_create_periodic": (P, [I, I, I, I, P, P, P, P, P, P, P, P, P, P, P, P]),
+            "vo_stencil_codes": (I, [P, I, P, P, I]),
             "vo_mesh_destroy": (V, [P]),
             "vo_set_threads": (I, [I]),
             "vo_geometry": (V, [P, P, P, P, P]),
@@ -116,8 +118,18 @@ class OracleMesh:
         self._keep = [px, py, pz, _i32(mesh.face_ptr), _i32(mesh.face_pts), _i32(mesh.owner),
                       _i32(mesh.neighbour), np.ascontiguousarray(mesh.wall_flags(), np.uint8)]
         k = self._keep
-        self.h = L.vo_mesh_create(self.np_, self.nf, self.ni, self.nc, _p(k[0]), _p(k[1]), _p(k[2]),
-                                  _p(k[3]), _p(k[4]), _p(k[5]), _p(k[6]), _p(k[7]))
+        if getattr(mesh, "point_master", None) is not None:
+            per = np.ascontiguousarray(mesh.period, np.float64).reshape(9)
+            pm = _i32(mesh.point_master)
+            pi = np.ascontiguousarray(mesh.point_image, np.int8).reshape(-1)
+            fi = _i32(mesh.face_image)
+            self._keep += [per, pm, pi, fi]
+            self.h = L.vo_mesh_create_periodic(self.np_, self.nf, self.ni, self.nc, _p(k[0]), _p(k[1]), _p(k[2]),
+                                               _p(k[3]), _p(k[4]), _p(k[5]), _p(k[6]), _p(k[7]), _p(per),
+                                               _p(pm), _p(pi), _p(fi))
+        else:
+            self.h = L.vo_mesh_create(self.np_, self.nf, self.ni, self.nc, _p(k[0]), _p(k[1]), _p(k[2]),
+                                      _p(k[3]), _p(k[4]), _p(k[5]), _p(k[6]), _p(k[7]))
         if not self.h:
             raise RuntimeError("oracle mesh creation failed")
 
@@ -140,6 +152,13 @@ class OracleMesh:
         out = np.zeros(2048, np.int32)
         n = lib().vo_stencil(self.h, int(f), _p(out), 2048)
         return out[:n].copy()
+
+    def stencil_codes(self, f):
+        """(cells, translation codes) of the face stencil (periodic meshes)."""
+        out = np.zeros(2048, np.int32)
+        cod = np.zeros(2048, np.int32)
+        n = lib().vo_stencil_codes(self.h, int(f), _p(out), _p(cod), 2048)
+        return out[:n].copy(), cod[:n].copy()
 
     # A1 --------------------------------------------------------------------
     def point_interp(self, phi_c):

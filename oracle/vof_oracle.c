@@ -61,11 +61,26 @@ struct vo_mesh {
     unsigned char *wall; /* per boundary face: 1 = wall */
     int *pwn;            /* per point: number of distinct wall normals (0..3) */
     v3 *pwv;             /* per point: up to two wall normals */
+    /* periodic meshes (R21); for others pmaster[p] = p and every code is T0 */
+    v3 L[3];             /* period vectors */
+    int *pmaster;        /* per point: the master point it is an image of */
+    int *fimg;           /* per boundary face: the internal face it copies, or -1 */
+    unsigned char *pcode;/* per (point, cell) entry: translation of the cell to the point */
 };
+
+/* A translation by i L0 + j L1 + k L2, i, j, k in {-1, 0, 1}, is coded
+ * (i+1) + 3 (j+1) + 9 (k+1); T0 is no translation. */
+#define T0 13
+static v3 tvec(const vo_mesh *m, int code);
 
 static int cmp_int(const void *a, const void *b)
 {
     int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+static int cmp_long(const void *a, const void *b)
+{
+    long long x = *(const long long *)a, y = *(const long long *)b;
     return (x > y) - (x < y);
 }
 
@@ -93,13 +108,107 @@ static void face_tri(const vo_mesh *m, int f, int t, v3 o[3])
     else { o[0] = m->cf[f]; o[1] = fp(m, f, t); o[2] = fp(m, f, (t + 1) % n); }
 }
 
+static v3 tvec(const vo_mesh *m, int code)
+{
+    int i = code % 3 - 1, j = (code / 3) % 3 - 1, k = code / 9 - 1;
+    return add(add(scl(m->L[0], (double)i), scl(m->L[1], (double)j)), scl(m->L[2], (double)k));
+}
+
+/* R21: the cells around every image of each point, translated to it: per
+ * point the union of its images' cells with code k(p) - k(q) (q the image that
+ * lists the cell), sorted by (cell, code).  Fails when images differ by more
+ * than one period or a cell lists two images of one point. */
+static int periodic_rings(vo_mesh *m, const int *pm, const signed char *pimg)
+{
+    const int np = m->np;
+    int i, total = 0, rc = 0;
+    int *mptr = (int *)calloc((size_t)np + 1, sizeof(int));
+    int *mem = (int *)malloc(sizeof(int) * (size_t)(np > 0 ? np : 1));
+    int *fill = (int *)calloc((size_t)(np > 0 ? np : 1), sizeof(int));
+    int *pptr2 = (int *)calloc((size_t)np + 1, sizeof(int)), *pcell2 = NULL;
+    unsigned char *pcode2 = NULL;
+    for (i = 0; i < np; i++) {
+        if (pm[i] < 0 || pm[i] >= np || pm[pm[i]] != pm[i]) { rc = -1; goto out; }
+        mptr[pm[i] + 1]++;
+    }
+    for (i = 0; i < np; i++) mptr[i + 1] += mptr[i];
+    for (i = 0; i < np; i++) mem[mptr[pm[i]] + fill[pm[i]]++] = i;
+    for (i = 0; i < np; i++) {
+        int j, k = 0;
+        for (j = mptr[pm[i]]; j < mptr[pm[i] + 1]; j++) k += m->pptr[mem[j] + 1] - m->pptr[mem[j]];
+        pptr2[i + 1] = pptr2[i] + k;
+    }
+    total = pptr2[np];
+    pcell2 = (int *)malloc(sizeof(int) * (size_t)(total > 0 ? total : 1));
+    pcode2 = (unsigned char *)malloc((size_t)(total > 0 ? total : 1));
+    for (i = 0; i < np; i++) {
+        int j, k = pptr2[i], a, b;
+        for (j = mptr[pm[i]]; j < mptr[pm[i] + 1]; j++) {
+            int r = mem[j], e, d[3];
+            for (e = 0; e < 3; e++) {
+                d[e] = pimg[3 * i + e] - pimg[3 * r + e];
+                if (d[e] < -1 || d[e] > 1) { rc = -1; goto out; }
+            }
+            for (e = m->pptr[r]; e < m->pptr[r + 1]; e++, k++) {
+                pcell2[k] = m->pcell[e];
+                pcode2[k] = (unsigned char)((d[0] + 1) + 3 * (d[1] + 1) + 9 * (d[2] + 1));
+            }
+        }
+        for (a = pptr2[i] + 1; a < pptr2[i + 1]; a++) /* insertion sort by (cell, code) */
+            for (b = a; b > pptr2[i] && (pcell2[b] < pcell2[b - 1] ||
+                                         (pcell2[b] == pcell2[b - 1] && pcode2[b] < pcode2[b - 1])); b--) {
+                int t = pcell2[b];
+                unsigned char u = pcode2[b];
+                pcell2[b] = pcell2[b - 1]; pcode2[b] = pcode2[b - 1];
+                pcell2[b - 1] = t; pcode2[b - 1] = u;
+            }
+        for (a = pptr2[i] + 1; a < pptr2[i + 1]; a++)
+            if (pcell2[a] == pcell2[a - 1]) { rc = -1; goto out; }
+    }
+    free(m->pptr); free(m->pcell); free(m->pcode);
+    m->pptr = pptr2; m->pcell = pcell2; m->pcode = pcode2;
+    pptr2 = NULL; pcell2 = NULL; pcode2 = NULL;
+out:
+    free(mptr); free(mem); free(fill); free(pptr2); free(pcell2); free(pcode2);
+    return rc;
+}
+
 vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
                         const double *px, const double *py, const double *pz,
                         const int *face_ptr, const int *face_pts, const int *owner,
                         const int *neighbour, const unsigned char *wall)
 {
+    return vo_mesh_create_periodic(n_points, n_faces, n_internal, n_cells, px, py, pz, face_ptr, face_pts,
+                                   owner, neighbour, wall, NULL, NULL, NULL, NULL);
+}
+
+/* Reading R21, periodic meshes (the paper's translation case runs on a
+ * periodic box, Sec. 4.2; the paper does not say how the sides are joined).
+ * Every point is an image of a master point, P[p] = P[m] + sum_i k_i L_i with
+ * m = point_master[p], k = point_image[3p..3p+2] in {-1, 0, 1}; the images of
+ * one master are one point of the periodic domain.  A face of a periodic side,
+ * given with its points on its owner's side, is an internal face whose
+ * neighbour lies across the period; the neighbour's own copy of the face (its
+ * points on the other side) is a boundary face with face_image[b - n_internal]
+ * = that internal face.  A cell is built from its own faces: the neighbour
+ * takes the copy, not the internal face.  The copy carries no flux: the
+ * internal face's phase flux leaves its owner and enters the copy's owner,
+ * who is the face's neighbour.  The cells around a point are the cells around
+ * every image of it, each translated to this image; face stencils, inverse-
+ * distance weights and the LSQ stencil take the translated cells.  Sweep keys
+ * (R5) are master indices, so that a side quad of two prisms across the
+ * period is split the same way in both. */
+vo_mesh *vo_mesh_create_periodic(int n_points, int n_faces, int n_internal, int n_cells,
+                                 const double *px, const double *py, const double *pz,
+                                 const int *face_ptr, const int *face_pts, const int *owner,
+                                 const int *neighbour, const unsigned char *wall, const double *period,
+                                 const int *point_master, const signed char *point_image,
+                                 const int *face_image)
+{
     vo_mesh *m = (vo_mesh *)calloc(1, sizeof(vo_mesh));
     int i, f, c;
+    const int nb = n_faces - n_internal;
+    int *imaged = (int *)calloc((size_t)(n_internal > 0 ? n_internal : 1), sizeof(int));
     m->np = n_points; m->nf = n_faces; m->ni = n_internal; m->nc = n_cells;
     m->P = (v3 *)malloc(sizeof(v3) * (size_t)n_points);
     for (i = 0; i < n_points; i++) m->P[i] = mk(px[i], py[i], pz[i]);
@@ -112,11 +221,40 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
     m->nei = (int *)malloc(sizeof(int) * (size_t)(n_internal > 0 ? n_internal : 1));
     if (n_internal > 0) memcpy(m->nei, neighbour, sizeof(int) * (size_t)n_internal);
 
-    /* cell -> faces */
+    /* R21 data */
+    m->pmaster = (int *)malloc(sizeof(int) * (size_t)(n_points > 0 ? n_points : 1));
+    m->fimg = (int *)malloc(sizeof(int) * (size_t)(nb > 0 ? nb : 1));
+    for (i = 0; i < n_points; i++) m->pmaster[i] = point_master ? point_master[i] : i;
+    for (i = 0; i < nb; i++) m->fimg[i] = face_image ? face_image[i] : -1;
+    for (i = 0; i < 3; i++) m->L[i] = period ? mk(period[3 * i], period[3 * i + 1], period[3 * i + 2]) : mk(0, 0, 0);
+    if (point_master && !point_image) goto bad;
+    for (i = 0; i < nb; i++)
+        if (m->fimg[i] >= 0) {
+            /* the copy: owned by the internal face's neighbour, the same points
+             * up to one translation */
+            int a = m->fimg[i], b = n_internal + i, j, k, e, d0[3] = {0, 0, 0};
+            if (a >= n_internal || imaged[a] || neighbour[a] != owner[b] || !point_master) goto bad;
+            if (face_ptr[a + 1] - face_ptr[a] != face_ptr[b + 1] - face_ptr[b]) goto bad;
+            for (j = face_ptr[a]; j < face_ptr[a + 1]; j++) {
+                int pa = face_pts[j], pb = -1;
+                for (k = face_ptr[b]; k < face_ptr[b + 1]; k++)
+                    if (point_master[face_pts[k]] == point_master[pa]) pb = face_pts[k];
+                if (pb < 0) goto bad;
+                for (e = 0; e < 3; e++) {
+                    int d = point_image[3 * pa + e] - point_image[3 * pb + e];
+                    if (j == face_ptr[a]) d0[e] = d;
+                    else if (d != d0[e]) goto bad;
+                }
+            }
+            imaged[a] = 1;
+        }
+
+    /* cell -> faces (its own faces: an imaged internal face belongs to its owner
+     * only, its neighbour has the copy) */
     m->cptr = (int *)calloc((size_t)n_cells + 1, sizeof(int));
     for (f = 0; f < n_faces; f++) {
         m->cptr[owner[f] + 1]++;
-        if (f < n_internal) m->cptr[neighbour[f] + 1]++;
+        if (f < n_internal && !imaged[f]) m->cptr[neighbour[f] + 1]++;
     }
     for (c = 0; c < n_cells; c++) m->cptr[c + 1] += m->cptr[c];
     m->cface = (int *)malloc(sizeof(int) * (size_t)m->cptr[n_cells]);
@@ -124,7 +262,7 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
         int *fill = (int *)calloc((size_t)n_cells, sizeof(int));
         for (f = 0; f < n_faces; f++) {
             c = owner[f]; m->cface[m->cptr[c] + fill[c]++] = f;
-            if (f < n_internal) { c = neighbour[f]; m->cface[m->cptr[c] + fill[c]++] = f; }
+            if (f < n_internal && !imaged[f]) { c = neighbour[f]; m->cface[m->cptr[c] + fill[c]++] = f; }
         }
         free(fill);
     }
@@ -155,7 +293,7 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
         }
         free(tmp);
     }
-    /* point -> cells */
+    /* point -> cells: the cells that list the point */
     m->pptr = (int *)calloc((size_t)n_points + 1, sizeof(int));
     for (i = 0; i < m->cpptr[n_cells]; i++) m->pptr[m->cpt[i] + 1]++;
     for (i = 0; i < n_points; i++) m->pptr[i + 1] += m->pptr[i];
@@ -169,6 +307,9 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
             }
         free(fill);
     }
+    m->pcode = (unsigned char *)malloc((size_t)(m->pptr[n_points] > 0 ? m->pptr[n_points] : 1));
+    memset(m->pcode, T0, (size_t)(m->pptr[n_points] > 0 ? m->pptr[n_points] : 1));
+    if (point_master && periodic_rings(m, point_master, point_image)) goto bad;
     /* R1 geometry */
     m->cf = (v3 *)malloc(sizeof(v3) * (size_t)n_faces);
     m->sf = (v3 *)malloc(sizeof(v3) * (size_t)n_faces);
@@ -212,7 +353,7 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
     m->pwv = (v3 *)calloc(2 * (size_t)n_points, sizeof(v3));
     for (f = n_internal; f < n_faces; f++) {
         v3 u;
-        if (!m->wall[f - n_internal]) continue;
+        if (!m->wall[f - n_internal] || m->fimg[f - n_internal] >= 0) continue; /* a copy is no wall */
         u = scl(m->sf[f], 1.0 / norm(m->sf[f]));
         for (i = m->fptr[f]; i < m->fptr[f + 1]; i++) {
             int p = m->fpts[i], k, dup = 0;
@@ -228,11 +369,17 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
     for (i = 0; i < n_points; i++) {
         double s = 0.0;
         int j;
-        for (j = m->pptr[i]; j < m->pptr[i + 1]; j++) s += 1.0 / norm(sub(m->P[i], m->cc[m->pcell[j]]));
         for (j = m->pptr[i]; j < m->pptr[i + 1]; j++)
-            m->w[j] = (1.0 / norm(sub(m->P[i], m->cc[m->pcell[j]]))) / s;
+            s += 1.0 / norm(sub(m->P[i], add(m->cc[m->pcell[j]], tvec(m, m->pcode[j]))));
+        for (j = m->pptr[i]; j < m->pptr[i + 1]; j++)
+            m->w[j] = (1.0 / norm(sub(m->P[i], add(m->cc[m->pcell[j]], tvec(m, m->pcode[j]))))) / s;
     }
+    free(imaged);
     return m;
+bad:
+    free(imaged);
+    vo_mesh_destroy(m);
+    return NULL;
 }
 
 void vo_mesh_destroy(vo_mesh *m)
@@ -241,7 +388,7 @@ void vo_mesh_destroy(vo_mesh *m)
     free(m->P); free(m->fptr); free(m->fpts); free(m->own); free(m->nei);
     free(m->cptr); free(m->cface); free(m->cpptr); free(m->cpt); free(m->pptr);
     free(m->pcell); free(m->w); free(m->cf); free(m->sf); free(m->cc); free(m->vc);
-    free(m->wall); free(m->pwn); free(m->pwv);
+    free(m->wall); free(m->pwn); free(m->pwv); free(m->pmaster); free(m->fimg); free(m->pcode);
     free(m);
 }
 
@@ -259,24 +406,31 @@ void vo_geometry(const vo_mesh *m, double *cc, double *vc, double *cf, double *s
 }
 
 /* R7: the flux stencil of a face is every cell that shares a point with it
- * (point and edge neighbours, Sec. 2.3), listed in ascending order. */
-int vo_stencil(const vo_mesh *m, int f, int *out, int cap)
+ * (point and edge neighbours, Sec. 2.3), listed in ascending order; on a
+ * periodic mesh (R21) each with the translation that brings it next to the
+ * face (a cell can appear at two translations), ordered by (cell, code). */
+int vo_stencil_codes(const vo_mesh *m, int f, int *out, int *codes, int cap)
 {
     int k = 0, i, j, u = 0;
-    int buf[1024];
+    long long buf[1024];
     for (i = m->fptr[f]; i < m->fptr[f + 1]; i++) {
         int p = m->fpts[i];
         for (j = m->pptr[p]; j < m->pptr[p + 1]; j++)
-            if (k < 1024) buf[k++] = m->pcell[j];
+            if (k < 1024) buf[k++] = (long long)m->pcell[j] * 32 + m->pcode[j];
     }
-    qsort(buf, (size_t)k, sizeof(int), cmp_int);
+    qsort(buf, (size_t)k, sizeof(long long), cmp_long);
     for (i = 0; i < k; i++)
         if (i == 0 || buf[i] != buf[i - 1]) {
-            if (u < cap) out[u] = buf[i];
+            if (u < cap) {
+                out[u] = (int)(buf[i] / 32);
+                if (codes) codes[u] = (int)(buf[i] % 32);
+            }
             u++;
         }
     return u;
 }
+
+int vo_stencil(const vo_mesh *m, int f, int *out, int cap) { return vo_stencil_codes(m, f, out, NULL, cap); }
 
 /* ---------------------------------------------------- A1: NAG gradient */
 static double point_value(const vo_mesh *m, int p, const double *phi_c)
@@ -623,19 +777,22 @@ int vo_reconstruct_grad(const vo_mesh *m, const double *alpha, const double *gra
 
 /* ------------------------------ generalised LSQ gradient (Sec. 2.2.1) */
 /* The cell's stencil: every other cell that shares a point with it. */
-static int point_nbrs(const vo_mesh *m, int c, int *out, int cap)
+/* (On a periodic mesh, R21: each with the translation that brings it next to
+ * the cell, coded as in the face stencils; the cell's own images other than
+ * itself count as neighbours.) */
+static int point_nbrs(const vo_mesh *m, int c, int *out, int *codes, int cap)
 {
     int k = 0, i, j, u = 0;
-    int buf[4096];
+    long long buf[4096];
     for (i = m->cpptr[c]; i < m->cpptr[c + 1]; i++) {
         int p = m->cpt[i];
         for (j = m->pptr[p]; j < m->pptr[p + 1]; j++)
-            if (m->pcell[j] != c && k < 4096) buf[k++] = m->pcell[j];
+            if ((m->pcell[j] != c || m->pcode[j] != T0) && k < 4096) buf[k++] = (long long)m->pcell[j] * 32 + m->pcode[j];
     }
-    qsort(buf, (size_t)k, sizeof(int), cmp_int);
+    qsort(buf, (size_t)k, sizeof(long long), cmp_long);
     for (i = 0; i < k; i++)
         if (i == 0 || buf[i] != buf[i - 1]) {
-            if (u < cap) out[u] = buf[i];
+            if (u < cap) { out[u] = (int)(buf[i] / 32); codes[u] = buf[i] % 32; }
             u++;
         }
     return u;
@@ -647,11 +804,11 @@ static int point_nbrs(const vo_mesh *m, int c, int *out, int cap)
  * phi_c), d = x_k - x_c, solved by Cramer's rule (g = 0 for a singular system). */
 static v3 lsq_gradient_cell(const vo_mesh *m, int c, const double *phi)
 {
-    int nb[1024], k, nk = point_nbrs(m, c, nb, 1024);
+    int nb[1024], code[1024], k, nk = point_nbrs(m, c, nb, code, 1024);
     double A[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, b[3] = {0, 0, 0}, det, x[3];
     int i, j, col;
     for (k = 0; k < nk && k < 1024; k++) {
-        v3 d = sub(m->cc[nb[k]], m->cc[c]);
+        v3 d = sub(add(m->cc[nb[k]], tvec(m, code[k])), m->cc[c]);
         double dv[3] = {d.x, d.y, d.z}, w2 = 1.0 / dot(d, d), dphi = phi[nb[k]] - phi[c];
         for (i = 0; i < 3; i++) {
             b[i] += w2 * dv[i] * dphi;
@@ -835,7 +992,8 @@ void vo_point_velocity(const vo_mesh *m, const double *Uc, double *Up)
  * normal-sweep fallback: every point moves by w = -lambda*(F_f/|S_f|^2) S_f dt,
  * a uniform translation whose swept volume is exactly -lambda*F_f*dt.
  * The triangular prism is split into three tetrahedra after ordering its
- * vertices by key (face centre first, then global point index), so that a side
+ * vertices by key (face centre first, then global point index; its master on
+ * a periodic mesh, R21), so that a side
  * quad shared by two prisms is split along the same diagonal in both.  Each
  * tetrahedron carries the sign that makes the sum the signed swept volume,
  * positive for a sweep against S_f (flux from owner to neighbour). */
@@ -864,13 +1022,13 @@ static int face_prism_tets(const vo_mesh *m, int f, const double *Up, double F, 
             for (j = 0; j < 3; j++) {
                 a[j] = m->P[p[j]];
                 w[j] = point_disp(m, p[j], Up, dt, lambda, wn);
-                key[j] = p[j];
+                key[j] = m->pmaster[p[j]];
             }
         } else {
             int j0 = p[t], j1 = p[(t + 1) % n];
             a[0] = m->cf[f]; w[0] = wc; key[0] = -1;
-            a[1] = m->P[j0]; w[1] = point_disp(m, j0, Up, dt, lambda, wn); key[1] = j0;
-            a[2] = m->P[j1]; w[2] = point_disp(m, j1, Up, dt, lambda, wn); key[2] = j1;
+            a[1] = m->P[j0]; w[1] = point_disp(m, j0, Up, dt, lambda, wn); key[1] = m->pmaster[j0];
+            a[2] = m->P[j1]; w[2] = point_disp(m, j1, Up, dt, lambda, wn); key[2] = m->pmaster[j1];
         }
         for (j = 0; j < 3; j++) b[j] = sub(a[j], w[j]);
         for (j = 1; j < 3; j++) /* sort vertex ids by key, tracking permutation parity */
@@ -1007,6 +1165,7 @@ void vo_classify_faces(const vo_mesh *m, const double *alpha, double eps, unsign
 #pragma omp parallel for schedule(dynamic, 1024)
     for (f = 0; f < m->nf; f++) {
         int all_e = 1, all_f = 1, i, j;
+        if (f >= m->ni && m->fimg[f - m->ni] >= 0) { cls[f] = 0; continue; } /* R21: a copy carries no flux */
         for (i = m->fptr[f]; i < m->fptr[f + 1]; i++) {
             int p = m->fpts[i];
             for (j = m->pptr[p]; j < m->pptr[p + 1]; j++) {
@@ -1026,10 +1185,10 @@ static double face_phase_volume(const vo_mesh *m, int f, const double *alpha, do
                                 int *st)
 {
     stet T[3 * 64];
-    int sten[1024];
+    int sten[1024], code[1024];
     v3 K[MAXK][4];
     int q = face_prism_tets(m, f, Up, F, dt, lambda, T);
-    int ns = vo_stencil(m, f, sten, 1024), t, s, k;
+    int ns = vo_stencil_codes(m, f, sten, code, 1024), t, s, k;
     double acc = 0.0;
     for (t = 0; t < q; t++) {
         v3 tlo, thi;
@@ -1038,10 +1197,10 @@ static double face_phase_volume(const vo_mesh *m, int f, const double *alpha, do
         sg = T[t].s > 0 ? 1.0 : -1.0;
         aabb_tet(T[t].v, &tlo, &thi);
         for (s = 0; s < ns; s++) {
-            int c = sten[s], nk;
+            int c = sten[s], nk, j;
             double a = coverage ? 1.0 : alpha[c], wgt = 1.0;
             int use_h = 0;
-            v3 hn = mk(0, 0, 0);
+            v3 hn = mk(0, 0, 0), tr = tvec(m, code[s]);
             double hd = 0.0;
             if (!coverage) {
                 if (a <= eps) continue; /* empty cell carries no phase */
@@ -1049,11 +1208,14 @@ static double face_phase_volume(const vo_mesh *m, int f, const double *alpha, do
                     if (flags[c] & VO_ORIENTED) {
                         use_h = 1;
                         hn = mk(nrm[c], nrm[m->nc + c], nrm[2 * m->nc + c]);
-                        hd = dd[c];
+                        hd = dd[c] + dot(hn, tr); /* the plane moves with the cell (R21) */
                     } else wgt = a; /* R4: unoriented mixed cell is homogeneous */
                 }
             }
             nk = cell_tets(m, c, K, MAXK);
+            if (code[s] != T0)
+                for (k = 0; k < nk; k++)
+                    for (j = 0; j < 4; j++) K[k][j] = add(K[k][j], tr);
             for (k = 0; k < nk; k++) {
                 v3 klo, khi, pn[5];
                 double pd[5], v;
@@ -1134,7 +1296,7 @@ int vo_phase_flux(const vo_mesh *m, const double *alpha, double eps, const doubl
 static int face_nbr(const vo_mesh *m, int c, int i)
 {
     int f = m->cface[i];
-    if (f >= m->ni) return -1;
+    if (f >= m->ni) return m->fimg[f - m->ni] >= 0 ? m->own[m->fimg[f - m->ni]] : -1; /* R21 copy */
     return m->own[f] == c ? m->nei[f] : m->own[f];
 }
 
@@ -1250,7 +1412,9 @@ int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, doub
         int i;
         for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
             int g = m->cface[i];
-            if (m->own[g] == c) s += Va[g]; else s -= Va[g];
+            if (g >= m->ni && m->fimg[g - m->ni] >= 0) s -= Va[m->fimg[g - m->ni]]; /* R21: c is its neighbour */
+            else if (m->own[g] == c) s += Va[g];
+            else s -= Va[g];
         }
         alpha[c] = alpha[c] - s / m->vc[c];
     }

@@ -46,6 +46,19 @@ vo_mesh *vo_mesh_create(int n_points, int n_faces, int n_internal, int n_cells,
                         const double *px, const double *py, const double *pz,
                         const int *face_ptr, const int *face_pts, const int *owner,
                         const int *neighbour, const unsigned char *wall);
+/* Periodic meshes (reading R21): period[9] holds the period vectors L0, L1,
+ * L2 (rows); point_master[p] is the point p is an image of and
+ * point_image[3p..3p+2] in {-1, 0, 1} the periods between them,
+ * P[p] = P[master] + sum_i k_i L_i; face_image[b - n_internal] is, for a
+ * boundary face that is the neighbour's copy of a periodic internal face, that
+ * internal face (else -1).  NULL on failure (malformed periodic data, a cell
+ * touching two images of one point). */
+vo_mesh *vo_mesh_create_periodic(int n_points, int n_faces, int n_internal, int n_cells,
+                                 const double *px, const double *py, const double *pz,
+                                 const int *face_ptr, const int *face_pts, const int *owner,
+                                 const int *neighbour, const unsigned char *wall, const double *period,
+                                 const int *point_master, const signed char *point_image,
+                                 const int *face_image);
 void vo_mesh_destroy(vo_mesh *m);
 int vo_set_threads(int n);
 
@@ -55,6 +68,9 @@ void vo_geometry(const vo_mesh *m, double *cell_centre, double *cell_vol,
                  double *face_centre, double *face_area);
 /* number of cells in the face stencil (cells sharing a point with the face) */
 int vo_stencil(const vo_mesh *m, int face, int *out, int cap);
+/* the same with each cell's translation code (i+1) + 3(j+1) + 9(k+1) for
+ * i L0 + j L1 + k L2 (13: none) */
+int vo_stencil_codes(const vo_mesh *m, int face, int *out, int *codes, int cap);
 
 /* Eq. idwpointphi: cell -> point inverse-distance interpolation of one scalar */
 void vo_point_interp(const vo_mesh *m, const double *phi_c, double *phi_p);

@@ -87,6 +87,16 @@ int set_bound_regions(vof_ctx *c, const int *reg_cell, int nreg)
 
 extern "C" {
 
+// the reason of the last VOF_ERR_BAD_MESH of vof_create on this thread
+static thread_local const char *g_bad_mesh = "";
+static int bad_mesh(const char *why)
+{
+    g_bad_mesh = why;
+    return VOF_ERR_BAD_MESH;
+}
+
+const char *vof_create_error(void) { return g_bad_mesh; }
+
 const char *vof_error_string(int code)
 {
     switch (code) {
@@ -135,6 +145,7 @@ void vof_destroy(vof_ctx *c)
 
 int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
 {
+    g_bad_mesh = "";
     if (!mesh || !out) return VOF_ERR_INVALID_ARG;
     *out = nullptr;
     const int np = mesh->n_points, nf = mesh->n_faces, ni = mesh->n_internal, nc = mesh->n_cells;
@@ -152,22 +163,57 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
 
     // ---------------------------------------------------------- validation
     const int *fptr = mesh->face_ptr, *fpts = mesh->face_pts, *own = mesh->owner, *nei = mesh->neighbour;
-    if (fptr[0] != 0) return VOF_ERR_BAD_MESH;
+    if (fptr[0] != 0) return bad_mesh("face_ptr[0] is not 0");
     for (int f = 0; f < nf; ++f) {
         int n = fptr[f + 1] - fptr[f];
-        if (n < 3 || n > VOF_MAXFP) return VOF_ERR_BAD_MESH;
-        if (own[f] < 0 || own[f] >= nc) return VOF_ERR_BAD_MESH;
-        if (f < ni && (nei[f] < 0 || nei[f] >= nc || nei[f] == own[f])) return VOF_ERR_BAD_MESH;
+        if (n < 3 || n > VOF_MAXFP) return bad_mesh("a face has fewer than 3 or more than 8 points");
+        if (own[f] < 0 || own[f] >= nc) return bad_mesh("an owner index is out of range");
+        if (f < ni && (nei[f] < 0 || nei[f] >= nc || nei[f] == own[f])) return bad_mesh("a neighbour index is out of range or equals the owner");
     }
     const long nfp = fptr[nf];
     for (long k = 0; k < nfp; ++k)
-        if (fpts[k] < 0 || fpts[k] >= np) return VOF_ERR_BAD_MESH;
+        if (fpts[k] < 0 || fpts[k] >= np) return bad_mesh("a face point index is out of range");
+    // periodic data: each copy is owned by its face's neighbour and lists the
+    // same points (by master) one translation away
+    const bool periodic = mesh->point_master != nullptr;
+    const int *pmas = mesh->point_master, *fimg = mesh->face_image;
+    const int8_t *pimg = mesh->point_image;
+    if (periodic && (!pimg || !mesh->period || !fimg)) return VOF_ERR_INVALID_ARG;
+    std::vector<uint8_t> imaged(std::max(ni, 1), 0);
+    if (periodic) {
+        for (int p = 0; p < np; ++p) {
+            if (pmas[p] < 0 || pmas[p] >= np || pmas[pmas[p]] != pmas[p]) return bad_mesh("a point master is out of range or not its own master");
+            for (int e = 0; e < 3; ++e)
+                if (pimg[3 * p + e] < -1 || pimg[3 * p + e] > 1) return bad_mesh("a point image is not in {-1, 0, 1}");
+        }
+        for (int b = ni; b < nf; ++b) {
+            const int a = fimg[b - ni];
+            if (a < 0) continue;
+            if (a >= ni || imaged[a] || nei[a] != own[b] || fptr[a + 1] - fptr[a] != fptr[b + 1] - fptr[b])
+                return bad_mesh("a periodic copy is not owned by its face's neighbour, copies an internal face twice, or differs in point count");
+            int d0[3] = {0, 0, 0};
+            for (int j = fptr[a]; j < fptr[a + 1]; ++j) {
+                int pb = -1;
+                for (int k = fptr[b]; k < fptr[b + 1]; ++k)
+                    if (pmas[fpts[k]] == pmas[fpts[j]]) pb = fpts[k];
+                if (pb < 0) return bad_mesh("a periodic copy lacks an image of one of its face's points");
+                for (int e = 0; e < 3; ++e) {
+                    const int d = pimg[3 * fpts[j] + e] - pimg[3 * pb + e];
+                    if (j == fptr[a]) d0[e] = d;
+                    else if (d != d0[e]) return bad_mesh("a periodic copy is not one translation away from its face");
+                }
+            }
+            imaged[a] = 1;
+        }
+    }
 
     // ------------------------------------------------------ host topology
+    // cell -> faces: a cell's own faces (a periodic face belongs to its owner;
+    // its neighbour has the copy)
     std::vector<int> cptr(nc + 1, 0), cface;
     for (int f = 0; f < nf; ++f) {
         cptr[own[f] + 1]++;
-        if (f < ni) cptr[nei[f] + 1]++;
+        if (f < ni && !imaged[f]) cptr[nei[f] + 1]++;
     }
     for (int c = 0; c < nc; ++c) cptr[c + 1] += cptr[c];
     cface.resize(cptr[nc]);
@@ -175,13 +221,21 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         std::vector<int> fill(nc, 0);
         for (int f = 0; f < nf; ++f) {
             cface[cptr[own[f]] + fill[own[f]]++] = 2 * f;
-            if (f < ni) cface[cptr[nei[f]] + fill[nei[f]]++] = 2 * f + 1;
+            if (f < ni && !imaged[f]) cface[cptr[nei[f]] + fill[nei[f]]++] = 2 * f + 1;
         }
     }
-    std::vector<int> cnb(cface.size());
+    std::vector<int> cnb(cface.size()), cflux;
     for (size_t k = 0; k < cface.size(); ++k) {
         const int f = cface[k] >> 1;
-        cnb[k] = f >= ni ? -1 : (cface[k] & 1) ? own[f] : nei[f];
+        if (f >= ni) cnb[k] = (periodic && fimg[f - ni] >= 0) ? own[fimg[f - ni]] : -1;
+        else cnb[k] = (cface[k] & 1) ? own[f] : nei[f];
+    }
+    if (periodic) {  // the update reads a copy's entry as its periodic face, seen from the neighbour
+        cflux = cface;
+        for (size_t k = 0; k < cface.size(); ++k) {
+            const int f = cface[k] >> 1;
+            if (f >= ni && fimg[f - ni] >= 0) cflux[k] = 2 * fimg[f - ni] + 1;
+        }
     }
     // cell -> distinct points, and the tetrahedron count per cell
     std::vector<int> cpcount(nc);
@@ -197,7 +251,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         ktet[c] = kt;
     });
     for (int c = 0; c < nc; ++c)
-        if (ktet[c] > 32 * VOF_MAXK_LANE || ktet[c] < 4) return VOF_ERR_BAD_MESH;
+        if (ktet[c] > 32 * VOF_MAXK_LANE || ktet[c] < 4) return bad_mesh("a cell has fewer than 4 or more than 96 tetrahedra");
     std::vector<int> cpptr(nc + 1, 0);
     {
         std::vector<int> uniq(nc);
@@ -238,7 +292,52 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
             }
     }
     for (int p = 0; p < np; ++p)
-        if (pptr[p + 1] == pptr[p]) return VOF_ERR_BAD_MESH;  // point used by no cell
+        if (pptr[p + 1] == pptr[p]) return bad_mesh("a point is used by no cell");  // point used by no cell
+    // periodic: the cells around every image of a point, moved next to it
+    // (code k(p) - k(q), q the image the cell lists), sorted by (cell, code)
+    std::vector<uint8_t> pcode;
+    if (periodic) {
+        std::vector<int> mptr(np + 1, 0), mem(np);
+        for (int p = 0; p < np; ++p) mptr[pmas[p] + 1]++;
+        for (int p = 0; p < np; ++p) mptr[p + 1] += mptr[p];
+        {
+            std::vector<int> fill(np, 0);
+            for (int p = 0; p < np; ++p) mem[mptr[pmas[p]] + fill[pmas[p]]++] = p;
+        }
+        std::vector<int> pptr2(np + 1, 0);
+        for (int p = 0; p < np; ++p) {
+            long k = 0;
+            for (int j = mptr[pmas[p]]; j < mptr[pmas[p] + 1]; ++j) k += pptr[mem[j] + 1] - pptr[mem[j]];
+            if (pptr2[p] + k > 0x7fffffffL) return bad_mesh("too many (point, cell) entries");
+            pptr2[p + 1] = pptr2[p] + (int)k;
+        }
+        std::vector<long long> key(pptr2[np]);
+        std::atomic<int> bad{0};
+        parallel_for(np, [&](long p) {
+            long o = pptr2[p];
+            for (int j = mptr[pmas[p]]; j < mptr[pmas[p] + 1]; ++j) {
+                const int q = mem[j];
+                int code = 0;
+                for (int e = 2; e >= 0; --e) {
+                    const int d = pimg[3 * p + e] - pimg[3 * q + e];
+                    if (d < -1 || d > 1) bad = 1;
+                    code = 3 * code + (d + 1);
+                }
+                for (int i = pptr[q]; i < pptr[q + 1]; ++i) key[o++] = (long long)pcell[i] * 32 + code;
+            }
+            std::sort(key.begin() + pptr2[p], key.begin() + pptr2[p + 1]);
+            for (long i = pptr2[p] + 1; i < pptr2[p + 1]; ++i)
+                if (key[i] / 32 == key[i - 1] / 32) bad = 1;  // a cell at two images of one point
+        });
+        if (bad) return bad_mesh("periodic images more than one period apart, or a cell touching two images of one point");
+        pcell.resize(key.size());
+        pcode.resize(key.size());
+        for (size_t i = 0; i < key.size(); ++i) {
+            pcell[i] = (int)(key[i] / 32);
+            pcode[i] = (uint8_t)(key[i] % 32);
+        }
+        pptr.swap(pptr2);
+    }
     // face stencils: every cell sharing a point with the face, ascending
     std::vector<int> scount(nf);
     std::vector<long> soff(nf + 1, 0);
@@ -248,30 +347,50 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         soff[f + 1] = soff[f] + k;
     }
     std::vector<int> stmp(soff[nf]);
+    std::vector<uint8_t> sctmp(periodic ? soff[nf] : 0);
     parallel_for(nf, [&](long f) {
         long o = soff[f];
         int k = 0;
-        for (int j = fptr[f]; j < fptr[f + 1]; ++j)
-            for (int q = pptr[fpts[j]]; q < pptr[fpts[j] + 1]; ++q) stmp[o + k++] = pcell[q];
-        std::sort(stmp.begin() + o, stmp.begin() + o + k);
-        scount[f] = (int)(std::unique(stmp.begin() + o, stmp.begin() + o + k) - (stmp.begin() + o));
+        if (!periodic) {
+            for (int j = fptr[f]; j < fptr[f + 1]; ++j)
+                for (int q = pptr[fpts[j]]; q < pptr[fpts[j] + 1]; ++q) stmp[o + k++] = pcell[q];
+            std::sort(stmp.begin() + o, stmp.begin() + o + k);
+            scount[f] = (int)(std::unique(stmp.begin() + o, stmp.begin() + o + k) - (stmp.begin() + o));
+        } else {  // (cell, code) pairs: a cell may sit next to the face at two translations
+            std::vector<long long> kk;
+            for (int j = fptr[f]; j < fptr[f + 1]; ++j)
+                for (int q = pptr[fpts[j]]; q < pptr[fpts[j] + 1]; ++q) kk.push_back((long long)pcell[q] * 32 + pcode[q]);
+            std::sort(kk.begin(), kk.end());
+            kk.erase(std::unique(kk.begin(), kk.end()), kk.end());
+            for (long long v : kk) {
+                stmp[o + k] = (int)(v / 32);
+                sctmp[o + k] = (uint8_t)(v % 32);
+                ++k;
+            }
+            scount[f] = k;
+        }
     });
     // 64-bit offsets: a large batch of tetrahedral cases holds billions of entries
     std::vector<long long> sptr(nf + 1, 0);
     for (int f = 0; f < nf; ++f) sptr[f + 1] = sptr[f] + scount[f];
     std::vector<int> scell(sptr[nf]);
+    std::vector<uint8_t> scode(periodic ? sptr[nf] : 0);
     parallel_for(nf, [&](long f) {
         std::copy(stmp.begin() + soff[f], stmp.begin() + soff[f] + scount[f], scell.begin() + sptr[f]);
+        if (periodic)
+            std::copy(sctmp.begin() + soff[f], sctmp.begin() + soff[f] + scount[f], scode.begin() + sptr[f]);
     });
     stmp.clear();
     stmp.shrink_to_fit();
+    sctmp.clear();
+    sctmp.shrink_to_fit();
     // wall points and the wall faces through them (reading R2)
     std::vector<int> pwall(np, -1), wptr(1, 0), wface;
     {
         std::vector<std::vector<int>> lists;
         for (int f = ni; f < nf; ++f) {
             bool w = mesh->wall ? mesh->wall[f - ni] != 0 : true;
-            if (!w) continue;
+            if (!w || (periodic && fimg[f - ni] >= 0)) continue;  // a copy is no wall
             for (int j = fptr[f]; j < fptr[f + 1]; ++j) {
                 int p = fpts[j];
                 if (pwall[p] < 0) { pwall[p] = (int)lists.size(); lists.emplace_back(); }
@@ -288,7 +407,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     // reach outside the domain, where the stencil does not cover them
     std::vector<uint8_t> popen(np, 0), fopen(nf, 0);
     for (int f = ni; f < nf; ++f)
-        if (mesh->wall && mesh->wall[f - ni] == 0)
+        if (mesh->wall && mesh->wall[f - ni] == 0 && !(periodic && fimg[f - ni] >= 0))
             for (int j = fptr[f]; j < fptr[f + 1]; ++j) popen[fpts[j]] = 1;
     parallel_for(nf, [&](long f) {
         for (int j = fptr[f]; j < fptr[f + 1]; ++j)
@@ -302,7 +421,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
             int f = cface[i] >> 1;
             v += fptr[f + 1] - fptr[f];
         }
-        if (v > 0x7fffffffL) return VOF_ERR_BAD_MESH;
+        if (v > 0x7fffffffL) return bad_mesh("too many (face, point) entries");
         cfpptr[c + 1] = (int)v;
     }
     std::vector<int> ctptr(nc + 1, 0);
@@ -370,6 +489,21 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     m.cent = dev_copy(c, cent.data(), cent.size(), &err);
     m.ctptr = dev_copy(c, ctptr.data(), ctptr.size(), &err);
     m.ctet = dev_copy(c, ctet.data(), ctet.size(), &err);
+    m.pcode = nullptr; m.scode = nullptr; m.fimg = nullptr;
+    m.fkey = m.fpts;
+    m.cflux = m.cface;
+    for (int i = 0; i < 9; ++i) m.L[i] = periodic ? mesh->period[i] : 0.0;
+    if (periodic) {
+        std::vector<int> fkey(nfp);
+        for (long k = 0; k < nfp; ++k) fkey[k] = pmas[fpts[k]];
+        m.pcode = dev_copy(c, pcode.data(), pcode.size(), &err);
+        m.scode = dev_copy(c, scode.data(), scode.size(), &err);
+        m.fkey = dev_copy(c, fkey.data(), fkey.size(), &err);
+        m.cflux = dev_copy(c, cflux.data(), cflux.size(), &err);
+        std::vector<int> fi(fimg, fimg + (nf - ni));
+        fi.push_back(-1);  // (never empty)
+        m.fimg = dev_copy(c, fi.data(), fi.size(), &err);
+    }
     // per-step scratch
     c->pstate = dev_alloc<uint8_t>(c, np, &err);
     c->band = dev_alloc<int>(c, nf, &err);
@@ -435,7 +569,7 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
         vof_destroy(c);
         return VOF_ERR_CUDA;
     }
-    if (bad) { vof_destroy(c); return VOF_ERR_BAD_MESH; }
+    if (bad) { vof_destroy(c); return bad_mesh("a cell tetrahedron of non-positive volume"); }
     *out = c;
     return VOF_OK;
 }
@@ -473,13 +607,16 @@ static int build_lsq(vof_ctx *c)
 {
     if (c->lptr) return VOF_OK;
     const int nc = c->nc, np = c->np;
+    const bool periodic = c->m.pcode != nullptr;
     std::vector<int> cpptr(nc + 1), pptr(np + 1);
     if (cudaMemcpy(cpptr.data(), c->m.cpptr, sizeof(int) * (nc + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(pptr.data(), c->m.pptr, sizeof(int) * (np + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
         return VOF_ERR_CUDA;
     std::vector<int> cpts(cpptr[nc]), pcell(pptr[np]);
+    std::vector<uint8_t> pcode(periodic ? pptr[np] : 0);
     if (cudaMemcpy(cpts.data(), c->m.cpts, sizeof(int) * cpts.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(pcell.data(), c->m.pcell, sizeof(int) * pcell.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+        cudaMemcpy(pcell.data(), c->m.pcell, sizeof(int) * pcell.size(), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (periodic && cudaMemcpy(pcode.data(), c->m.pcode, pcode.size(), cudaMemcpyDeviceToHost) != cudaSuccess))
         return VOF_ERR_CUDA;
     std::vector<long> off(nc + 1, 0);
     for (int x = 0; x < nc; ++x) {
@@ -487,13 +624,18 @@ static int build_lsq(vof_ctx *c)
         for (int i = cpptr[x]; i < cpptr[x + 1]; ++i) k += pptr[cpts[i] + 1] - pptr[cpts[i]];
         off[x + 1] = off[x] + k;
     }
-    std::vector<int> tmp(off[nc]), cnt(nc);
+    // (cell, translation code) keys; without periods every code is 13, so the
+    // keys sort as the cells do; the cell itself unmoved is not its neighbour
+    std::vector<long long> tmp(off[nc]);
+    std::vector<int> cnt(nc);
     parallel_for(nc, [&](long x) {
         long o = off[x];
         int k = 0;
         for (int i = cpptr[x]; i < cpptr[x + 1]; ++i)
-            for (int q = pptr[cpts[i]]; q < pptr[cpts[i] + 1]; ++q)
-                if (pcell[q] != x) tmp[o + k++] = pcell[q];
+            for (int q = pptr[cpts[i]]; q < pptr[cpts[i] + 1]; ++q) {
+                const int code = periodic ? pcode[q] : 13;
+                if (pcell[q] != x || code != 13) tmp[o + k++] = (long long)pcell[q] * 32 + code;
+            }
         std::sort(tmp.begin() + o, tmp.begin() + o + k);
         cnt[x] = (int)(std::unique(tmp.begin() + o, tmp.begin() + o + k) - (tmp.begin() + o));
     });
@@ -503,14 +645,22 @@ static int build_lsq(vof_ctx *c)
         lptr[x + 1] = lptr[x] + cnt[x];
     }
     std::vector<int> lcell(lptr[nc]);
-    parallel_for(nc, [&](long x) { std::copy(tmp.begin() + off[x], tmp.begin() + off[x] + cnt[x], lcell.begin() + lptr[x]); });
+    std::vector<uint8_t> lcode(periodic ? lptr[nc] : 0);
+    parallel_for(nc, [&](long x) {
+        for (int i = 0; i < cnt[x]; ++i) {
+            lcell[lptr[x] + i] = (int)(tmp[off[x] + i] / 32);
+            if (periodic) lcode[lptr[x] + i] = (uint8_t)(tmp[off[x] + i] % 32);
+        }
+    });
     int err = 0;
     int *dp = dev_copy(c, lptr.data(), lptr.size(), &err);
     int *dc = dev_copy(c, lcell.data(), lcell.size(), &err);
+    uint8_t *dk = periodic ? dev_copy(c, lcode.data(), lcode.size(), &err) : nullptr;
     double *g = dev_alloc<double>(c, 3 * (size_t)nc, &err);
     if (err) return err;
     c->lptr = dp;
     c->lcell = dc;
+    c->lcode = dk;
     c->grad = g;
     return VOF_OK;
 }

@@ -76,6 +76,7 @@ int vof_batch_create(const vof_mesh *mesh, const int32_t *case_cell_ptr, int nca
 {
     if (!mesh || !case_cell_ptr || ncases < 1 || !out) return VOF_ERR_INVALID_ARG;
     *out = nullptr;
+    if (mesh->point_master) return VOF_ERR_INVALID_ARG;  // one set of periods cannot serve cases of any size
     if (case_cell_ptr[0] != 0 || case_cell_ptr[ncases] != mesh->n_cells) return VOF_ERR_INVALID_ARG;
     for (int i = 0; i < ncases; ++i)
         if (case_cell_ptr[i + 1] <= case_cell_ptr[i]) return VOF_ERR_INVALID_ARG;

@@ -89,6 +89,14 @@ __device__ __forceinline__ void st3(double *a, int n, int i, V3 v)
 {
     a[i] = v.x; a[n + i] = v.y; a[2 * n + i] = v.z;
 }
+// the translation of a periodic code, (i L0 + j L1) + k L2 (exact products)
+constexpr int T_NONE = 13;
+__device__ __forceinline__ V3 tshift(const DevMesh &m, int code)
+{
+    const double i = code % 3 - 1, j = (code / 3) % 3 - 1, k = code / 9 - 1;
+    return mk(i * m.L[0], i * m.L[1], i * m.L[2]) + mk(j * m.L[3], j * m.L[4], j * m.L[5]) +
+           mk(k * m.L[6], k * m.L[7], k * m.L[8]);
+}
 
 // Comparisons of a double with a threshold t > 0 through the order of the bit
 // patterns as signed 64-bit integers: monotone on the non-negative doubles, and

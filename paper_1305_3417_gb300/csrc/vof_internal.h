@@ -37,6 +37,17 @@ struct DevMesh {
     const int2 *cent;
     const int *ctptr;
     const int4 *ctet;
+    // Periodic meshes (null otherwise, with fkey == fpts and cflux == cface):
+    // translation code per (point, cell) entry and per stencil entry, (i+1) +
+    // 3(j+1) + 9(k+1) for i L0 + j L1 + k L2 (13: none); the period vectors; the
+    // sweep key of each face-point slot (its point's master); the flux code of
+    // each cell-face entry (a copy's entry is its periodic face's, as
+    // neighbour); the periodic face each boundary face copies (-1: none)
+    const uint8_t *pcode, *scode;
+    double L[9];
+    const int *fkey;
+    const int *cflux;
+    const int *fimg;
 };
 
 // the context's counter buffer: per-step counters (the first CNT_LEN ints),
@@ -119,6 +130,7 @@ struct vof_ctx {
     // and the gradient buffer are made at the first selection of LSQ
     int grad_kind;
     int *lptr, *lcell;
+    uint8_t *lcode;  // periodic meshes: translation code of each LSQ neighbour (else null)
     double *grad;
     // learned guess of the positioning (vof_set_guess): the network, offsets by
     // interface-list position, features

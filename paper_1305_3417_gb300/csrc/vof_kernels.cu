@@ -78,16 +78,20 @@ __global__ void k_cell_geom(DevMesh m, double *cc, double *vc, double *cbox, uns
     cbox[6 * c + 3] = hi.x; cbox[6 * c + 4] = hi.y; cbox[6 * c + 5] = hi.z;
 }
 
-// Eq. w_pc: inverse distance from the point to each point-cell centre, normalised
+// Eq. w_pc: inverse distance from the point to each point-cell centre (on a
+// periodic mesh the cell moved next to the point), normalised
 __global__ void k_point_weights(DevMesh m, double *pw)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= m.np) return;
     V3 x = ldP(m, p);
+    auto centre = [&](int j) {
+        V3 c = ld3(m.cc, m.nc, m.pcell[j]);
+        return m.pcode ? c + tshift(m, m.pcode[j]) : c;
+    };
     double s = 0.0;
-    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) s += 1.0 / norm3(x - ld3(m.cc, m.nc, m.pcell[j]));
-    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j)
-        pw[j] = (1.0 / norm3(x - ld3(m.cc, m.nc, m.pcell[j]))) / s;
+    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) s += 1.0 / norm3(x - centre(j));
+    for (int j = m.pptr[p]; j < m.pptr[p + 1]; ++j) pw[j] = (1.0 / norm3(x - centre(j))) / s;
 }
 
 // wall table: distinct unit normals of the wall faces through each wall point
@@ -494,7 +498,7 @@ __device__ __forceinline__ int face_points(const DevMesh &m, int f, const double
     int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
     for (int i = 0; i < n; ++i) {
         int p = __ldg(m.fpts + b + i);
-        id[i] = p;
+        id[i] = __ldg(m.fkey + b + i);  // the point's index (its master's on a periodic mesh)
         A[i] = ldP(m, p);
         V3 u = IDW ? point_velocity(m, p, U) : ld3(U, m.np, p);
         W[i] = u * dt;
@@ -647,7 +651,7 @@ __device__ __forceinline__ void correct_face(const DevMesh &m, int f, int b, int
     for (int i = 0; i < N; ++i) {
         if (i < nn) {
             int p = __ldg(m.fpts + b + i);
-            id[i] = p;
+            id[i] = __ldg(m.fkey + b + i);  // the point's index (its master's on a periodic mesh)
             A[i] = ldP(m, p);
             W[i] = ld3(U, m.np, p) * dt;
         }
@@ -869,14 +873,16 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
             // flux is not zero, so warps of such cells issue no FP64 adds.
             const int k0 = m.cptr[c], k1 = m.cptr[c + 1];
             unsigned nz = 0;
+            // (cflux: the cell's faces, a periodic copy read as its face seen
+            // from the neighbour; the cell's own faces on other meshes)
             for (int k = k0; k < k1; ++k) {
-                DBits b = dbits(Va[m.cface[k] >> 1]);
+                DBits b = dbits(Va[m.cflux[k] >> 1]);
                 nz |= (unsigned)(b.hi & 0x7fffffff) | b.lo;
             }
             double s = 0.0;
             if (nz)
                 for (int k = k0; k < k1; ++k) {
-                    int code = m.cface[k];
+                    int code = m.cflux[k];
                     double x = Va[code >> 1];
                     s += (code & 1) ? -x : x;
                 }
@@ -1436,7 +1442,8 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
         if (i < m.nf) {
             double Ff = F[i];
             double v = 0.0;
-            if (!is_zero(Ff) && !(i >= m.ni && dbits(Ff).hi < 0)) {
+            // (a periodic face's copy carries no flux)
+            if (!is_zero(Ff) && !(i >= m.ni && (dbits(Ff).hi < 0 || (m.fimg && m.fimg[i - m.ni] >= 0)))) {
                 unsigned st = 3u;
                 for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) st &= state[m.fpts[k]];
                 if (st & 1u) v = 0.0;
@@ -1531,7 +1538,8 @@ int launch_point_velocity(vof_ctx *c, const double *Uc, double *Up, cudaStream_t
 // the adjugate of their symmetric matrix (g = 0 where it is singular).
 template <bool LIST>
 __global__ void k_lsq_gradient(DevMesh m, const double *__restrict__ alpha, const int *list, const int *count,
-                               const int *__restrict__ lptr, const int *__restrict__ lcell, double *grad)
+                               const int *__restrict__ lptr, const int *__restrict__ lcell,
+                               const uint8_t *__restrict__ lcode, double *grad)
 {
     const int total = LIST ? *count : m.nc;
     for (int item = blockIdx.x * blockDim.x + threadIdx.x; item < total; item += gridDim.x * blockDim.x) {
@@ -1541,7 +1549,7 @@ __global__ void k_lsq_gradient(DevMesh m, const double *__restrict__ alpha, cons
         double a00 = 0, a01 = 0, a02 = 0, a11 = 0, a12 = 0, a22 = 0, b0 = 0, b1 = 0, b2 = 0;
         for (int k = __ldg(lptr + c), k1 = __ldg(lptr + c + 1); k < k1; ++k) {
             const int q = __ldg(lcell + k);
-            const V3 dd = ld3(m.cc, m.nc, q) - xc;
+            const V3 dd = (lcode ? ld3(m.cc, m.nc, q) + tshift(m, __ldg(lcode + k)) : ld3(m.cc, m.nc, q)) - xc;
             const double w2 = 1.0 / dot(dd, dd), dp = (alpha[q] - pc) * w2;
             const V3 wd = dd * w2;
             a00 += wd.x * dd.x; a01 += wd.x * dd.y; a02 += wd.x * dd.z;
@@ -1565,9 +1573,11 @@ int launch_lsq_gradient(vof_ctx *c, const double *alpha, const int *list, const 
                         cudaStream_t s)
 {
     if (list)
-        k_lsq_gradient<true><<<num_sms(c->device) * 8, 128, 0, s>>>(c->m, alpha, list, count, c->lptr, c->lcell, grad);
+        k_lsq_gradient<true><<<num_sms(c->device) * 8, 128, 0, s>>>(c->m, alpha, list, count, c->lptr, c->lcell,
+                                                                    c->lcode, grad);
     else
-        k_lsq_gradient<false><<<cdiv(c->nc, 128), 128, 0, s>>>(c->m, alpha, nullptr, nullptr, c->lptr, c->lcell, grad);
+        k_lsq_gradient<false><<<cdiv(c->nc, 128), 128, 0, s>>>(c->m, alpha, nullptr, nullptr, c->lptr, c->lcell,
+                                                                c->lcode, grad);
     return cudaGetLastError() == cudaSuccess ? VOF_OK : VOF_ERR_CUDA;
 }
 

@@ -57,7 +57,8 @@ __device__ void mlp_features_one(const DevMesh &m, const double *__restrict__ al
         const int p = m.cpts[j];
         for (int q = m.pptr[p]; q < m.pptr[p + 1]; ++q) {
             const int nb = m.pcell[q];
-            const vofd::V3 d = vofd::ld3(m.cc, m.nc, nb) - cc;
+            vofd::V3 d = vofd::ld3(m.cc, m.nc, nb) - cc;
+            if (m.pcode) d = d + vofd::tshift(m, m.pcode[q]);  // periodic: the cell next to c
             const int sx = (d.x > 0.5 * h) - (d.x < -0.5 * h), sy = (d.y > 0.5 * h) - (d.y < -0.5 * h),
                       sz = (d.z > 0.5 * h) - (d.z < -0.5 * h);
             f[(sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)] = (float)alpha[nb];
@@ -306,7 +307,8 @@ __global__ void k_mlp_tables(DevMesh m, int *nbr, float *geo)
         const int p = m.cpts[j];
         for (int q = m.pptr[p]; q < m.pptr[p + 1]; ++q) {
             const int nb = m.pcell[q];
-            const vofd::V3 d = vofd::ld3(m.cc, m.nc, nb) - cc;
+            vofd::V3 d = vofd::ld3(m.cc, m.nc, nb) - cc;
+            if (m.pcode) d = d + vofd::tshift(m, m.pcode[q]);  // periodic: the cell next to c
             const int sx = (d.x > 0.5 * h) - (d.x < -0.5 * h), sy = (d.y > 0.5 * h) - (d.y < -0.5 * h),
                       sz = (d.z > 0.5 * h) - (d.z < -0.5 * h);
             t[(sx + 1) + 3 * (sy + 1) + 9 * (sz + 1)] = nb;

@@ -517,7 +517,9 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
             all_f = __all_sync(0xffffffffu, all_f);
             double triv = 0.0;
             bool done = true;
-            if (Ff == 0.0 || (f >= m.ni && Ff < 0.0) || all_e) triv = 0.0;
+            // (inflow through a boundary face brings nothing; a periodic face's
+            // copy carries no flux)
+            if (Ff == 0.0 || (f >= m.ni && (Ff < 0.0 || (m.fimg && m.fimg[f - m.ni] >= 0))) || all_e) triv = 0.0;
             else if (all_f) triv = Ff * a.dt;
             else done = false;
             if (done) {
@@ -572,12 +574,12 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
             V a0, a1, a2, w0, w1, w2;
             long k0, k1, k2;
             if (n == 3) {
-                k0 = __ldg(m.fpts + b); k1 = __ldg(m.fpts + b + 1); k2 = __ldg(m.fpts + b + 2);
+                k0 = __ldg(m.fkey + b); k1 = __ldg(m.fkey + b + 1); k2 = __ldg(m.fkey + b + 2);
                 a0 = ld43<R>(fpl, b); a1 = ld43<R>(fpl, b + 1); a2 = ld43<R>(fpl, b + 2);
                 w0 = disp(0); w1 = disp(1); w2 = disp(2);
             } else {
                 int u = pr + 1 == n ? 0 : pr + 1;
-                k0 = -1; k1 = __ldg(m.fpts + b + pr); k2 = __ldg(m.fpts + b + u);
+                k0 = -1; k1 = __ldg(m.fkey + b + pr); k2 = __ldg(m.fkey + b + u);
                 a0 = r3(R(0), R(0), R(0)); a1 = ld43<R>(fpl, b + pr); a2 = ld43<R>(fpl, b + u);
                 w0 = disp(-1); w1 = disp(pr); w2 = disp(u);
             }
@@ -651,14 +653,20 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                     int c = 0;
                     double al = 0.0;
                     V dc = r3(R(0), R(0), R(0));
+                    // the face centre in the cell's frame: on a periodic mesh
+                    // the cell sits next to the face moved by its stencil
+                    // translation t, and the cell, its tetrahedra and its
+                    // plane are taken relative to o - t
+                    V3 oc = o;
                     if (s < s1) {
                         c = __ldg(m.scell + s);
                         al = a.alpha[c];
+                        if (m.scode) oc = o - tshift(m, __ldg(m.scode + s));
                         // an empty cell carries no phase, a full cell no void
                         // thresholds on the integer pipe (bit-pattern order of doubles)
                         if (!((!comp && le_pos(al, eps)) || (comp && ge_pos(al, 1.0 - eps)))) {
                             const V3 cc = ld3(m.cc, m.nc, c);
-                            dc = r3(rconv<R>(cc.x - o.x), rconv<R>(cc.y - o.y), rconv<R>(cc.z - o.z));
+                            dc = r3(rconv<R>(cc.x - oc.x), rconv<R>(cc.y - oc.y), rconv<R>(cc.z - oc.z));
                             const R4<R> cb0 = ldg4(cbl, 2 * (long)c), cb1 = ldg4(cbl, 2 * (long)c + 1);
                             pass = !(cb1.x + dc.x < pb[0] || pb[3] < cb0.x + dc.x || cb1.y + dc.y < pb[1] ||
                                      pb[4] < cb0.y + dc.y || cb1.z + dc.z < pb[2] || pb[5] < cb0.z + dc.z);
@@ -674,7 +682,7 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                         if (gt_pos(al, eps) && lt_pos(al, 1.0 - eps)) {
                             if (a.flags[c] & VOF_ORIENTED) {
                                 V3 hn = ld3(a.n, m.nc, c);
-                                double hd = a.d[c] - dot(hn, o);
+                                double hd = a.d[c] - dot(hn, oc);
                                 // phase side n.x <= d; the void side is -n.x <= -d
                                 R sg = comp ? R(-1) : R(1);
                                 H = mk4<R>(sg * rconv<R>(hn.x), sg * rconv<R>(hn.y), sg * rconv<R>(hn.z),

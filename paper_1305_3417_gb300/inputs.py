@@ -34,7 +34,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "hex_mesh", "kuhn_tet_mesh", "disc_rect_area", "disc_fraction_2d",
-    "sampled_fraction", "sphere_sdf", "cylinder_sdf", "Field", "translation_field",
+    "sampled_fraction", "sphere_sdf", "cylinder_sdf", "Field", "translation_field", "diagonal_shuttle_field", "periodic_shear_field",
     "deformation_field", "single_vortex_field", "rotation_field",
     "face_flux_stokes", "cell_velocity", "Workload", "make_workload",
     "concat_meshes", "BatchCase", "Batch", "make_batch",
@@ -57,6 +57,14 @@ class Mesh:
     wall: np.ndarray | None = None   # (n_faces - n_internal,) uint8: 1 = wall (no normal flow)
     octree: dict | None = None       # octree meshes: lattice size N, levels, per cell level / origin /
                                      # size in finest units, and the finest-lattice cell map
+    # periodic meshes: period vectors (3, 3) as rows; per point the master point
+    # it is an image of and the periods between them (P = P_master + image @
+    # period); per boundary face the periodic internal face it is the
+    # neighbour's copy of, or -1
+    period: np.ndarray | None = None
+    point_master: np.ndarray | None = None   # (n_points,) int32
+    point_image: np.ndarray | None = None    # (n_points, 3) int8
+    face_image: np.ndarray | None = None     # (n_faces - n_internal,) int32
 
     @property
     def n_points(self) -> int:
@@ -85,16 +93,24 @@ class Mesh:
 # --------------------------------------------------------------------------
 
 def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = None,
-             dim: int = 3, open_sides: tuple = ()) -> Mesh:
+             dim: int = 3, open_sides: tuple = (), periodic: str = "") -> Mesh:
     """Box [0,lx]x[0,ly]x[0,lz] split into nx*ny*nz hexahedra.
 
     Boundary faces are walls (no normal flow) except on the sides listed in
     ``open_sides`` (any of "x-", "x+", "y-", "y+", "z-", "z+").
 
+    ``periodic`` (any of "x", "y", "z") joins the two sides normal to each
+    listed axis: the points of the high side are images of the low side's
+    (one period along the axis), a face of the high side becomes an internal
+    face from its owner to the low side's cell across the period, and the low
+    side's face is that cell's copy of it (``face_image``).
+
     ``jitter`` moves every point that lies on no boundary plane by an
     independent uniform offset in [-jitter*h, jitter*h] per coordinate
-    (h = lx/nx), drawn from PCG64(seed).  With dim=2 the mesh is one cell
-    thick and only x, y of points off the x/y boundary planes are moved.
+    (h = lx/nx), drawn from PCG64(seed); on a periodic axis the low side's
+    points are moved too and the high side's images follow them.  With dim=2
+    the mesh is one cell thick and only x, y of points off the x/y boundary
+    planes are moved.
     """
     nx, ny, nz = (int(v) for v in n)
     lx, ly, lz = (float(v) for v in length)
@@ -110,16 +126,33 @@ def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = 
     pts[pid.ravel(), 0] = xs[I.ravel()]
     pts[pid.ravel(), 1] = ys[J.ravel()]
     pts[pid.ravel(), 2] = zs[K.ravel()]
+    per = [ax in periodic for ax in "xyz"]
+    if dim == 2 and per[2]:
+        raise ValueError("a one-cell-thick mesh is not periodic across its thickness")
     if jitter > 0.0:
         rng = np.random.Generator(np.random.PCG64(seed))
+
+        def free(L, n_, p_):
+            return (L < n_) if p_ else ((L > 0) & (L < n_))
         if dim == 3:
-            inner = (I > 0) & (I < nx) & (J > 0) & (J < ny) & (K > 0) & (K < nz)
+            inner = free(I, nx, per[0]) & free(J, ny, per[1]) & free(K, nz, per[2])
             ids = np.sort(pid[inner])
             pts[ids] += rng.uniform(-jitter * h, jitter * h, size=(ids.size, 3))
         else:
-            inner = (I > 0) & (I < nx) & (J > 0) & (J < ny)
+            inner = free(I, nx, per[0]) & free(J, ny, per[1])
             ids = np.sort(pid[inner])
             pts[ids, :2] += rng.uniform(-jitter * h, jitter * h, size=(ids.size, 2))
+    period = np.diag([lx, ly, lz]) * np.array(per, float)[:, None]
+    img = np.stack([(I == nx) & per[0], (J == ny) & per[1], (K == nz) & per[2]], -1).astype(np.int8)
+    mI, mJ, mK = np.where(img[..., 0] > 0, 0, I), np.where(img[..., 1] > 0, 0, J), np.where(img[..., 2] > 0, 0, K)
+    master = (mI + (nx + 1) * (mJ + (ny + 1) * mK)).astype(np.int64)
+    point_master = np.empty(npts, np.int32)
+    point_image = np.zeros((npts, 3), np.int8)
+    point_master[pid.ravel()] = master.ravel()
+    point_image[pid.ravel()] = img.reshape(-1, 3)
+    if any(per):
+        # images sit one period from their masters (jitter included)
+        pts[:] = pts[point_master] + point_image.astype(float) @ period
 
     def P(i, j, k):
         return (i + (nx + 1) * (j + (ny + 1) * k)).astype(np.int64)
@@ -152,6 +185,26 @@ def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = 
     own_i = np.concatenate(own); nei_i = np.concatenate(nei); fp_i = np.concatenate(fps)
     order = np.lexsort((nei_i, own_i))          # upper-triangular (owner, neighbour) order
     own_i, nei_i, fp_i = own_i[order], nei_i[order], fp_i[order]
+    # periodic internal faces: each high side face, from its owner to the low
+    # side's cell across the period, after the others (owner order per axis)
+    per_block = {}
+    pown, pnei, pfp = [], [], []
+    nxt = own_i.size
+    for ax in range(3):
+        if not per[ax]:
+            continue
+        m = (ci, cj, ck)[ax] == (nx, ny, nz)[ax] - 1
+        lo = [ci[m], cj[m], ck[m]]
+        lo[ax] = np.zeros_like(lo[ax])
+        hi_idx = [ci[m], cj[m], ck[m]]
+        hi_idx[ax] = hi_idx[ax] + 1
+        pown.append(C(ci[m], cj[m], ck[m])); pnei.append(C(*lo))
+        pfp.append((xface, yface, zface)[ax](*hi_idx))
+        per_block[ax] = (nxt, pnei[-1])           # first face index, neighbours in order
+        nxt += int(m.sum())
+    if pown:
+        own_i = np.concatenate([own_i] + pown); nei_i = np.concatenate([nei_i] + pnei)
+        fp_i = np.concatenate([fp_i] + pfp)
 
     bown, bfp = [], []
     # x-, x+, y-, y+, z-, z+ ; reversed point order gives the outward normal on the low side
@@ -169,10 +222,23 @@ def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = 
     bown.append(C(ci[m], cj[m], ck[m])); bfp.append(zface(ci[m], cj[m], ck[m] + 1))
     bsorted = []
     wall = []
+    fimg = []
     for side, o, f in zip(("x-", "x+", "y-", "y+", "z-", "z+"), bown, bfp):
+        ax = "xyz".index(side[0])
+        if per[ax] and side[1] == "+":
+            continue                              # now the periodic internal faces
         s = np.argsort(o, kind="stable")
         bsorted.append((o[s], f[s]))
-        wall.append(np.full(o.size, 0 if side in open_sides else 1, np.uint8))
+        wall.append(np.full(o.size, 0 if (side in open_sides or per[ax]) else 1, np.uint8))
+        if per[ax]:
+            # the low side's face of cell o is the neighbour's copy of the
+            # periodic face whose neighbour is o
+            f0, nb = per_block[ax]
+            where = np.full(nx * ny * nz, -1, np.int64)
+            where[nb] = f0 + np.arange(nb.size)
+            fimg.append(where[o[s]])
+        else:
+            fimg.append(np.full(o.size, -1, np.int64))
     b_own = np.concatenate([b[0] for b in bsorted])
     b_fp = np.concatenate([b[1] for b in bsorted])
 
@@ -184,8 +250,14 @@ def hex_mesh(n, length=(1.0, 1.0, 1.0), jitter: float = 0.0, seed: int | None = 
     for t, (a, b, c) in enumerate([(0, 0, 0), (1, 0, 0), (1, 1, 0), (0, 1, 0),
                                    (0, 0, 1), (1, 0, 1), (1, 1, 1), (0, 1, 1)]):
         cv[cell_ids, t] = P(ci + a, cj + b, ck + c)
-    return Mesh(pts, face_ptr, face_pts, owner, nei_i.astype(np.int32), nx * ny * nz,
+    mesh = Mesh(pts, face_ptr, face_pts, owner, nei_i.astype(np.int32), nx * ny * nz,
                 cv.astype(np.int32), h, dim, "hex", (nx, ny, nz), np.concatenate(wall))
+    if any(per):
+        mesh.period = period
+        mesh.point_master = point_master
+        mesh.point_image = point_image
+        mesh.face_image = np.concatenate(fimg).astype(np.int32)
+    return mesh
 
 
 # --------------------------------------------------------------------------
@@ -502,14 +574,34 @@ def disc_rect_area(cx, cy, R, x0, x1, y0, y1):
 
 
 def disc_fraction_2d(mesh: Mesh, cx: float, cy: float, R: float) -> np.ndarray:
-    """Exact cell fractions of a disc on a uniform one-cell-thick hex mesh."""
+    """Exact cell fractions of a disc on a uniform one-cell-thick hex mesh; on a
+    mesh periodic in x and y the disc is wrapped (the sum over its images one
+    period away; a disc narrower than the box meets each cell in at most one)."""
     nx, ny, _ = mesh.shape
     h = mesh.h
     out = np.zeros(mesh.n_cells)
+    if mesh.period is not None:
+        Lx, Ly = mesh.period[0, 0], mesh.period[1, 1]
+        cx, cy = cx % Lx if Lx else cx, cy % Ly if Ly else cy
+        shifts = [(a * Lx, b * Ly) for a in ((-1, 0, 1) if Lx else (0,)) for b in ((-1, 0, 1) if Ly else (0,))]
+    else:
+        shifts = [(0.0, 0.0)]
     for j in range(ny):
         for i in range(nx):
-            out[i + nx * j] = disc_rect_area(cx, cy, R, i * h, (i + 1) * h, j * h, (j + 1) * h) / (h * h)
+            out[i + nx * j] = sum(disc_rect_area(cx + sx, cy + sy, R, i * h, (i + 1) * h, j * h, (j + 1) * h)
+                                  for sx, sy in shifts) / (h * h)
     return out
+
+
+def _wrapped_sphere_sdf(c, R):
+    """Signed distance to a sphere on the periodic unit box (nearest image)."""
+    c = np.asarray(c, float)
+
+    def f(x):
+        d = x - c
+        d -= np.round(d)
+        return np.sqrt((d ** 2).sum(-1)) - R
+    return f
 
 
 def sphere_sdf(c, R):
@@ -632,6 +724,41 @@ def single_vortex_field(T: float = 8.0):
                  lambda t: (T / pi) * math.sin(pi * t / T))
 
 
+def diagonal_shuttle_field():
+    """Uniform velocity (1,1,1) s(t) with s = +1 on [0, 1/2), -1 on [1/2, 3/2),
+    +1 from 3/2: over [0, 2] a body at the centre of the unit box goes to the
+    corner (1,1,1), back through the centre to (0,0,0) and returns to the
+    centre (reading R21 of the paper's periodic translation case)."""
+    U = np.array([1.0, 1.0, 1.0])
+
+    def tau(t):
+        return 1.0 if (t < 0.5 or t >= 1.5) else -1.0
+
+    def tau_int(t):
+        return t if t < 0.5 else (1.0 - t if t < 1.5 else t - 2.0)
+
+    return Field("diagonal_shuttle", lambda x: np.broadcast_to(U, x.shape).copy(),
+                 lambda x: 0.5 * np.cross(np.broadcast_to(U, x.shape), x), tau, tau_int)
+
+
+def periodic_shear_field(T: float = 2.0):
+    """u = (sin 2 pi y, sin 2 pi z, sin 2 pi x) cos(pi t / T): divergence-free
+    and periodic on the unit box, with the periodic potential
+    A = -(cos 2 pi z, cos 2 pi x, cos 2 pi y) / (2 pi)."""
+    pi = math.pi
+
+    def u(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return np.stack([np.sin(2 * pi * Y), np.sin(2 * pi * Z), np.sin(2 * pi * X)], -1)
+
+    def A(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        return -np.stack([np.cos(2 * pi * Z), np.cos(2 * pi * X), np.cos(2 * pi * Y)], -1) / (2 * pi)
+
+    return Field("periodic_shear", u, A, lambda t: math.cos(pi * t / T),
+                 lambda t: (T / pi) * math.sin(pi * t / T))
+
+
 def rotation_field(omega, x0=(0.5, 0.5, 0.5)):
     om = np.asarray(omega, float)
     c = np.asarray(x0, float)
@@ -712,8 +839,19 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
     """Named workloads.
 
     disc2d:       uniform 32x32x1 hex on [0,1]^2 x [0,1/32], disc R=0.15 at (0.5,0.75),
-                  exact fractions, translation (1,1,0), Co 0.5, 20 steps; the four
-                  sides are open (empty inflow, geometric outflow), front/back walls.
+                  exact fractions, translation (1,1,0), Co 0.5, 20 steps; periodic in
+                  x and y (the disc crosses y = 1 and comes back at y = 0), front/back
+                  walls.
+    disc2d_open:  the same with the four sides open (empty inflow, geometric outflow).
+    shear_periodic: jittered (+-0.2h, seed 1304) n^3 hex (n=12) periodic in x, y, z,
+                  a sphere R=0.25 at (0.9,0.15,0.5) wrapped across two seams, the
+                  periodic shear field (sin 2 pi y, sin 2 pi z, sin 2 pi x)
+                  cos(pi t / 2), Co 0.5 to t=2 (the field reverses).
+    translate3d:  periodic uniform n^3 hex (n=16), sphere R=0.15 at the centre,
+                  translation along the diagonal (1,1,1) reversed at t = 1/2 and
+                  3/2, to t = 2: the sphere reaches the corner (1,1,1), then
+                  (0,0,0), then comes back (the paper's periodic translation case,
+                  R21); Co 0.5.
     deform3d:     jittered (+-0.2h, seed 1302) n^3 hex (n=128), sphere R=0.15 at
                   (0.35,0.35,0.35), deformation field T=3, Co 0.5 to t=3.
     vortex_tet:   jittered (+-0.15h, seed 1303) Kuhn split of n^3 (n=96), cylinder
@@ -723,12 +861,27 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
                   2:1 face-balanced; deformation field T=3, Co 0.5 on the finest
                   cells, to t=0.5 (the interface leaves the refined band later).
     """
-    if name == "disc2d":
+    if name in ("disc2d", "disc2d_open"):
         n = 32 if n is None else n
-        mesh = hex_mesh((n, n, 1), (1.0, 1.0, 1.0 / n), dim=2, open_sides=("x-", "x+", "y-", "y+"))
+        if name == "disc2d":
+            mesh = hex_mesh((n, n, 1), (1.0, 1.0, 1.0 / n), dim=2, periodic="xy")
+        else:
+            mesh = hex_mesh((n, n, 1), (1.0, 1.0, 1.0 / n), dim=2, open_sides=("x-", "x+", "y-", "y+"))
         a0 = disc_fraction_2d(mesh, 0.5, 0.75, 0.15)
         fld = translation_field((1.0, 1.0, 0.0))
         steps = 20
+    elif name == "translate3d":
+        n = 16 if n is None else n
+        mesh = hex_mesh((n, n, n), periodic="xyz")
+        a0 = sampled_fraction(mesh, sphere_sdf((0.5, 0.5, 0.5), 0.15))
+        fld = diagonal_shuttle_field()
+        steps = None
+    elif name == "shear_periodic":
+        n = 12 if n is None else n
+        mesh = hex_mesh((n, n, n), jitter=0.2, seed=1304 if seed is None else seed, periodic="xyz")
+        a0 = sampled_fraction(mesh, _wrapped_sphere_sdf((0.9, 0.15, 0.5), 0.25))
+        fld = periodic_shear_field(2.0)
+        steps = None
     elif name == "deform3d":
         n = 128 if n is None else n
         mesh = hex_mesh((n, n, n), jitter=0.2, seed=1302 if seed is None else seed)
@@ -757,11 +910,12 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
     hc = mesh.h if mesh.kind in ("hex", "octree") else mesh.h / 6.0 ** (1.0 / 3.0)
     dt = co * hc / umax
     Fs = face_flux_stokes(mesh, fld.A)
-    t_end = {"disc2d": steps * dt if steps else None, "deform3d": 3.0, "vortex_tet": 8.0, "octree": 0.5}[name]
+    t_end = {"disc2d": steps * dt if steps else None, "disc2d_open": steps * dt if steps else None,
+             "translate3d": 2.0, "shear_periodic": 2.0, "deform3d": 3.0, "vortex_tet": 8.0, "octree": 0.5}[name]
     if steps is None:
         steps = int(math.ceil(t_end / dt - 1e-12))
     exact = None
-    if name == "disc2d":
+    if name in ("disc2d", "disc2d_open"):
         def exact(t, _m=mesh):
             return disc_fraction_2d(_m, 0.5 + t, 0.75 + t, 0.15)
     return Workload(name, mesh, a0, fld, Fs, Us, dt, steps, t_end, exact)

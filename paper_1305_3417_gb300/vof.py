@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvof.so")
 
 VOF_OK = 0
+VOF_ERR_BAD_MESH = -3
 FP64, MIXED = 0, 1
 INTERFACE, ORIENTED, FULL = 1, 2, 4
 STATUS_BITS = {1: "POS_NOT_CONVERGED", 2: "CORR_NOT_CONVERGED", 4: "CLIP_OVERFLOW",
@@ -37,7 +38,8 @@ class _Mesh(ctypes.Structure):
                 ("px", ctypes.c_void_p), ("py", ctypes.c_void_p), ("pz", ctypes.c_void_p),
                 ("face_ptr", ctypes.c_void_p), ("face_pts", ctypes.c_void_p),
                 ("owner", ctypes.c_void_p), ("neighbour", ctypes.c_void_p),
-                ("wall", ctypes.c_void_p)]
+                ("wall", ctypes.c_void_p), ("period", ctypes.c_void_p), ("point_master", ctypes.c_void_p),
+                ("point_image", ctypes.c_void_p), ("face_image", ctypes.c_void_p)]
 
 
 class _Options(ctypes.Structure):
@@ -52,7 +54,7 @@ EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "v
            "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
            "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
            "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess", "vof_set_gradient", "vof_lsq_gradient",
-           "vof_evsd", "vof_remap", "vof_tune"]
+           "vof_evsd", "vof_remap", "vof_tune", "vof_create_error"]
 GRAD_NAG, GRAD_LSQ = 0, 1
 MLP_IN, MLP_HID, MLP_OUT = 33, 64, 4
 MLP_NPARAM = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
@@ -85,6 +87,7 @@ def lib():
         "vof_status": (I, [P, ctypes.POINTER(ctypes.c_uint32), P]),
         "vof_last_launch_count": (I, [P]),
         "vof_error_string": (ctypes.c_char_p, [I]),
+        "vof_create_error": (ctypes.c_char_p, []),
         "vof_profile_begin": (I, [P, I]),
         "vof_profile_end": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "vof_work_counts": (I, [P, P, I, P]),
@@ -120,7 +123,10 @@ def lib():
 
 def _check(code: int, what: str):
     if code != VOF_OK:
-        raise VofError(f"{what}: {lib().vof_error_string(code).decode()} ({code})")
+        why = ""
+        if code == VOF_ERR_BAD_MESH and what in ("vof_create", "vof_batch_create"):
+            why = ": " + lib().vof_create_error().decode()
+        raise VofError(f"{what}: {lib().vof_error_string(code).decode()}{why} ({code})")
 
 
 def _ptr(t):
@@ -157,10 +163,20 @@ def _mesh_struct(mesh):
     own = np.ascontiguousarray(mesh.owner, np.int32)
     nei = np.ascontiguousarray(mesh.neighbour, np.int32)
     wall = np.ascontiguousarray(mesh.wall_flags(), np.uint8)
+    keep = [px, py, pz, fptr, fpts, own, nei, wall]
+    per = [None] * 4
+    if getattr(mesh, "point_master", None) is not None:
+        arrs = (np.ascontiguousarray(mesh.period, np.float64).reshape(9),
+                np.ascontiguousarray(mesh.point_master, np.int32),
+                np.ascontiguousarray(mesh.point_image, np.int8).reshape(-1),
+                np.ascontiguousarray(np.append(mesh.face_image, -1), np.int32))  # (never empty)
+        keep += list(arrs)
+        per = [a.ctypes.data for a in arrs]
     m = _Mesh(mesh.n_points, mesh.n_faces, mesh.n_internal, mesh.n_cells,
               px.ctypes.data, py.ctypes.data, pz.ctypes.data, fptr.ctypes.data, fpts.ctypes.data,
-              own.ctypes.data, nei.ctypes.data if nei.size else None, wall.ctypes.data if wall.size else None)
-    return m, (px, py, pz, fptr, fpts, own, nei, wall)
+              own.ctypes.data, nei.ctypes.data if nei.size else None, wall.ctypes.data if wall.size else None,
+              *per)
+    return m, tuple(keep)
 
 
 def vof_batch_create(mesh, case_cell_ptr, precision: int = MIXED, eps: float = 1e-9, bound: bool = True,
@@ -199,15 +215,7 @@ def vof_batch_tune(h, alpha, U_dt, F_dt, stream=None):
 
 def vof_create(mesh, precision: int = FP64, eps: float = 1e-9, bound: bool = True, device: int = 0):
     """mesh: paper_1305_3417_gb300.inputs.Mesh (host arrays).  Returns a handle."""
-    px, py, pz = (np.ascontiguousarray(v, np.float64) for v in mesh.soa_points())
-    fptr = np.ascontiguousarray(mesh.face_ptr, np.int32)
-    fpts = np.ascontiguousarray(mesh.face_pts, np.int32)
-    own = np.ascontiguousarray(mesh.owner, np.int32)
-    nei = np.ascontiguousarray(mesh.neighbour, np.int32)
-    wall = np.ascontiguousarray(mesh.wall_flags(), np.uint8)
-    m = _Mesh(mesh.n_points, mesh.n_faces, mesh.n_internal, mesh.n_cells,
-              px.ctypes.data, py.ctypes.data, pz.ctypes.data, fptr.ctypes.data, fpts.ctypes.data,
-              own.ctypes.data, nei.ctypes.data if nei.size else None, wall.ctypes.data if wall.size else None)
+    m, keep = _mesh_struct(mesh)
     o = _Options(eps, int(precision), int(bool(bound)), int(device))
     h = ctypes.c_void_p()
     _check(lib().vof_create(ctypes.byref(m), ctypes.byref(o), ctypes.byref(h)), "vof_create")

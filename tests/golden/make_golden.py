@@ -3,8 +3,9 @@
 Calls only the seeded input generator and the CPU oracle.  The paper prints no
 worked example with reproducible numbers (its error tables depend on meshes,
 time-step control and tolerances it does not give), so these fixtures record
-the oracle's own results on the 2D disc translation workload; a change to the
-oracle's arithmetic shows up here and must cite the passage that justifies it.
+the oracle's own results on the 2D disc translation workload (periodic in x and
+y, the first test case); a change to the oracle's arithmetic shows up here and
+must cite the passage that justifies it.
 """
 import os
 import sys
@@ -37,14 +38,14 @@ def disc2d_history():
 def main():
     rows, l1, a = disc2d_history()
     with open(os.path.join(HERE, "disc2d_oracle.txt"), "w") as f:
-        f.write("# oracle regression: 2D disc R=0.15 at (0.5,0.75), 32x32x1, U=(1,1,0), Co 0.5\n")
+        f.write("# oracle regression: 2D disc R=0.15 at (0.5,0.75), 32x32x1 periodic in x and y, U=(1,1,0), Co 0.5\n")
         f.write("# written by tests/golden/make_golden.py (oracle + input generator only)\n")
         f.write(f"# L1 = sum V|alpha - exact| after 20 steps: {l1:.17e}\n")
         f.write("# step mass boundary_out min_pre max_pre n_interface n_band\n")
         for r in rows:
             f.write(f"{r[0]} {r[1]:.17e} {r[2]:.17e} {r[3]:.17e} {r[4]:.17e} {r[5]} {r[6]}\n")
     np.savetxt(os.path.join(HERE, "disc2d_oracle_alpha20.txt"), a, fmt="%.17e",
-               header="oracle alpha after 20 steps of the 2D disc translation (cell order)")
+               header="oracle alpha after 20 steps of the periodic 2D disc translation (cell order)")
 
 
 if __name__ == "__main__":

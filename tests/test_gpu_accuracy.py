@@ -38,6 +38,7 @@ MESHES = {
     "hex": lambda: I.hex_mesh((14, 13, 12), jitter=0.2, seed=81),
     "tet": lambda: I.kuhn_tet_mesh((7, 7, 6), jitter=0.15, seed=82),
     "octree": lambda: I.octree_mesh(8, 2, BALL[:3], BALL[3]),
+    "periodic": lambda: I.hex_mesh((11, 12, 10), jitter=0.2, seed=83, periodic="xyz"),
 }
 _cache = {}
 

@@ -44,9 +44,11 @@ def H(t):
 
 
 WORKLOADS = {
-    "disc2d": lambda: I.make_workload("disc2d"),
+    "disc2d": lambda: I.make_workload("disc2d"),              # periodic in x and y
+    "disc2d_open": lambda: I.make_workload("disc2d_open"),
     "deform20": lambda: I.make_workload("deform3d", n=20),
     "tet7": lambda: I.make_workload("vortex_tet", n=7),
+    "shear_per": lambda: I.make_workload("shear_periodic", n=12),  # jittered, periodic in x, y, z
 }
 _cache = {}
 
@@ -212,6 +214,57 @@ def test_exact_shift_gpu(torch, O):
     assert np.abs(A1[:, :, 0]).max() < 1e-12
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_exact_shift_across_the_period_gpu(torch, O, axis, precision):
+    """Periodic in x, y, z, U along one axis, dt = h: alpha rolls by one cell,
+    across the seam too; a whole period of steps brings it back."""
+    from paper_1305_3417_gb300 import vof
+    shape = (5, 4, 3)
+    m = I.hex_mesh(shape, (1.0, 0.8, 0.6), periodic="xyz")
+    rng = np.random.default_rng(40 + axis)
+    a = rng.uniform(0, 1, m.n_cells)
+    a[rng.uniform(size=m.n_cells) < 0.2] = 0.0
+    a[rng.uniform(size=m.n_cells) < 0.2] = 1.0
+    U = np.zeros(3)
+    U[axis] = 1.0
+    fld = I.translation_field(U)
+    F = I.face_flux_stokes(m, fld.A)
+    Uc = I.cell_velocity(m, fld.u)
+    ctx = vof.VofContext(m, precision=precision, bound=False)
+    ta = T(torch, a)
+    stats = H(ctx.advect(ta, T(torch, Uc), T(torch, F), m.h))
+    A0, A1 = a.reshape(shape[::-1]), H(ta).reshape(shape[::-1])
+    tol = 1e-12 if precision == 0 else 2e-5
+    assert np.abs(A1 - np.roll(A0, 1, axis=2 - axis)).max() < tol
+    assert stats[10] == 0.0  # nothing leaves: no boundary flux
+    for _ in range(shape[axis] - 1):
+        ctx.advect(ta, T(torch, Uc), T(torch, F), m.h)
+    assert np.abs(H(ta) - a).max() < 10 * tol
+    assert ctx.status() == 0
+    ctx.close()
+
+
+def test_periodic_mesh_errors(torch, O):
+    """Periodic data that do not fit are rejected; a batch takes no periodic mesh."""
+    from paper_1305_3417_gb300 import vof
+    import copy
+    m = I.hex_mesh((4, 4, 3), periodic="xy")
+    bad = copy.deepcopy(m)
+    bad.face_image[np.flatnonzero(bad.face_image >= 0)[0]] = 0       # a copy of the wrong face
+    with pytest.raises(vof.VofError):
+        vof.VofContext(bad)
+    bad = copy.deepcopy(m)
+    bad.point_image[np.flatnonzero(bad.point_image[:, 0])[0], 0] = 2  # two periods away
+    with pytest.raises(vof.VofError):
+        vof.VofContext(bad)
+    one = I.hex_mesh((1, 4, 3), periodic="x")                        # a cell at two images of a point
+    with pytest.raises(vof.VofError):
+        vof.VofContext(one)
+    with pytest.raises(vof.VofError):
+        vof.vof_batch_create(m, np.array([0, m.n_cells], np.int32))
+
+
 def test_edge_cases(torch, O):
     w, ctx, om = contexts(torch, O, "deform20")
     F, U, dt = w.step_inputs(0)
@@ -238,7 +291,7 @@ def test_edge_cases(torch, O):
 
 def test_invalid_arguments(torch, O):
     from paper_1305_3417_gb300 import vof
-    w, ctx, om = contexts(torch, O, "disc2d")
+    w, ctx, om = contexts(torch, O, "disc2d_open")
     L = vof.lib()
     F, U, dt = w.step_inputs(0)
     tF, tU, ta = T(torch, F), T(torch, U), T(torch, w.alpha0)
@@ -249,7 +302,7 @@ def test_invalid_arguments(torch, O):
     assert L.vof_advect(ctx.h, vof._ptr(ta), vof._ptr(tU), vof._ptr(tF), float("nan"), None, s) == -1
     assert L.vof_advect(None, vof._ptr(ta), vof._ptr(tU), vof._ptr(tF), dt, None, s) == -1
     # a mesh with an out-of-range point index is rejected
-    m = workload("disc2d").mesh
+    m = workload("disc2d_open").mesh
     bad = I.Mesh(m.points, m.face_ptr, m.face_pts.copy(), m.owner, m.neighbour, m.n_cells, m.cell_verts,
                  m.h, m.dim, m.kind, m.shape, m.wall)
     bad.face_pts[5] = m.n_points + 3

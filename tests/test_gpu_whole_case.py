@@ -4,9 +4,10 @@ Every form (plain FP64, mixed precision, mixed with the learned initial
 guess) runs a whole case through vof_advect; the oracle runs the same inputs
 on the host.  The L1 shape error is Sec. 5's E_g read as
 L1 = sum_c V_c |alpha_c(T) - alpha_c^exact(T)| (reading R12), the exact state
-being the translated disc (2D disc, open sides: the disc clipped to the
-domain) or the initial field (the deformation and single-vortex fields
-reverse at t = T).  The target: |L1_gpu - L1_oracle| <= 1e-6, conservation
+being the translated disc (2D disc: periodic, the wrapped disc; open sides:
+the disc clipped to the domain) or the initial field (the deformation and
+single-vortex fields reverse at t = T, the periodic diagonal translation
+returns the sphere to the centre).  The target: |L1_gpu - L1_oracle| <= 1e-6, conservation
 per step, alpha within [0, 1] to 1e-12.
 
 Also here: the redistribution of over/undershoots (reading R10) through
@@ -39,6 +40,9 @@ def T(torch, x):
 
 CASES = {
     "disc2d": lambda: I.make_workload("disc2d"),
+    "disc2d_open": lambda: I.make_workload("disc2d_open"),
+    "translate3d_16": lambda: I.make_workload("translate3d", n=16),
+    "shear_periodic_12": lambda: I.make_workload("shear_periodic", n=12),
     "deform3d_24": lambda: I.make_workload("deform3d", n=24),
     "vortex_tet_10": lambda: I.make_workload("vortex_tet", n=10),
 }
@@ -53,7 +57,7 @@ def case(name):
 
 def schedule(w):
     """(step index, dt) of the whole case; the last step is trimmed to t_end."""
-    if w.name == "disc2d":
+    if w.name.startswith("disc2d"):
         return [(k, w.dt) for k in range(w.n_steps)]
     out, t, k = [], 0.0, 0
     while t < w.t_end - 1e-12:
@@ -65,7 +69,7 @@ def schedule(w):
 
 
 def exact(w):
-    if w.name == "disc2d":
+    if w.name.startswith("disc2d"):
         return w.exact(w.n_steps * w.dt)
     return w.alpha0
 

@@ -715,7 +715,7 @@ def test_conservation_and_boundedness_deformation(oracle_lib):
 
 
 def test_disc_translation_l1_and_outflow(oracle_lib):
-    w = I.make_workload("disc2d")
+    w = I.make_workload("disc2d_open")
     om = oracle_lib.OracleMesh(w.mesh)
     _, vc, _, _ = om.geometry()
     a = w.alpha0.copy()
