@@ -254,18 +254,21 @@ int vof_update(vof_ctx *ctx, double *alpha, const double *Valpha, double *stats,
 int vof_advect(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                double *stats, void *stream);
 
-/* vof_advect with HOST arrays (pinned memory gives full copy speed): copies
- * alpha, Uc, F to the context's device buffers, runs the step, copies alpha
- * (and stats, VOF_S_LEN doubles, if not NULL) back.  Asynchronous on `stream`;
- * the host arrays must stay valid until the stream reaches the end of it.
- * alpha is copied in order on `stream`.  Uc and F are copied on an internal
- * stream (created, with its events, at the first call) into one of two device
- * buffer pairs, alternating by call, as soon as the step two calls back is
- * done and the previous call's alpha copy is in (so that the alpha copy, on
- * the step's critical path, never waits in the copy engine behind them).  The
- * copies of consecutive calls thus overlap the previous step's kernels, and Uc
- * and F must hold this step's values when the call is made: they are not
- * ordered after earlier work on `stream`. */
+/* vof_advect with HOST arrays: alpha is copied to the context's device buffer
+ * in order on `stream`, the step runs, alpha (and stats, VOF_S_LEN doubles, if
+ * not NULL) is copied back.  Asynchronous on `stream`; the host arrays must
+ * stay valid, and Uc and F hold this step's values, from the call until the
+ * stream reaches the end of it.
+ * Uc in pinned host memory that the device can address (the driver reports a
+ * device pointer for it: cudaHostAlloc or cudaHostRegister memory on this
+ * system) is read in place by the step's kernels over the CPU-GPU link: only
+ * the band kernels read it, at the cells around band points.  F (read in full
+ * by the classification) and pageable Uc are copied on an internal stream
+ * (created, with its events, at the first call) into one of two device buffer
+ * pairs, alternating by call, as soon as the step two calls back is done and
+ * the previous call's alpha copy is in, so that those copies overlap the
+ * previous step's kernels; they are not ordered after earlier work on
+ * `stream`. */
 int vof_advect_host(vof_ctx *ctx, double *alpha, const double *Uc, const double *F, double dt,
                     double *stats, void *stream);
 

@@ -754,11 +754,23 @@ int vof_advect_host(vof_ctx *c, double *alpha, const double *Uc, const double *F
     if (!c || !alpha || !Uc || !F || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
     cudaSetDevice(c->device);
     cudaStream_t s = (cudaStream_t)stream;
-    // F and U go to the staging pair of this call's parity on the copy stream,
-    // once the step that last read that pair (two calls back) is done and the
-    // previous call's alpha is in: they overlap the previous step's kernels.  alpha (in place, so ordered after
-    // the previous step's read-back) goes on `stream`; the classification
-    // waits for F, the flux correction (inside the step) for U.
+    // Uc in host memory the device can address (pinned: the driver gives a
+    // device pointer for it) is read in place by the step: only the band
+    // kernels read it, at the cells around band points, so the link carries
+    // a small part of it.  F, which the classification reads in full, and
+    // pageable Uc go to the staging pair of this call's parity on the copy
+    // stream, once the step that last read that pair (two calls back) is done
+    // and the previous call's alpha is in: they overlap the previous step's
+    // kernels.  alpha (in place, so ordered after the previous step's
+    // read-back) goes on `stream`; the classification waits for F, the flux
+    // correction (inside the step) for a copied Uc.
+    const double *dU = nullptr;
+    {
+        cudaPointerAttributes pa;
+        if (cudaPointerGetAttributes(&pa, Uc) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer)
+            dU = static_cast<const double *>(pa.devicePointer);
+        cudaGetLastError();  // (an unknown pointer leaves an error behind)
+    }
     if (!c->s_copy && (cudaStreamCreateWithFlags(&c->s_copy, cudaStreamNonBlocking) ||
                        cudaEventCreateWithFlags(&c->ev_f, cudaEventDisableTiming) ||
                        cudaEventCreateWithFlags(&c->ev_u, cudaEventDisableTiming) ||
@@ -772,13 +784,14 @@ int vof_advect_host(vof_ctx *c, double *alpha, const double *Uc, const double *F
     if (cudaStreamWaitEvent(c->s_copy, c->ev_free[p], 0) || cudaStreamWaitEvent(c->s_copy, c->ev_ain, 0) ||
         cudaMemcpyAsync(c->h_F[p], F, sizeof(double) * c->nf, cudaMemcpyHostToDevice, c->s_copy) ||
         cudaEventRecord(c->ev_f, c->s_copy) ||
-        cudaMemcpyAsync(c->h_Uc[p], Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->s_copy) ||
-        cudaEventRecord(c->ev_u, c->s_copy) ||
+        (!dU && (cudaMemcpyAsync(c->h_Uc[p], Uc, 3 * sizeof(double) * c->nc, cudaMemcpyHostToDevice, c->s_copy) ||
+                 cudaEventRecord(c->ev_u, c->s_copy))) ||
         cudaMemcpyAsync(c->h_alpha, alpha, sizeof(double) * c->nc, cudaMemcpyHostToDevice, s) ||
         cudaEventRecord(c->ev_ain, s) || cudaStreamWaitEvent(s, c->ev_f, 0))
         return VOF_ERR_CUDA;
     c->h_par ^= 1;
-    int r = launch_advect(c, c->h_alpha, c->h_Uc[p], c->h_F[p], dt, c->stats_dev, s, c->ev_u);
+    int r = dU ? launch_advect(c, c->h_alpha, dU, c->h_F[p], dt, c->stats_dev, s)
+               : launch_advect(c, c->h_alpha, c->h_Uc[p], c->h_F[p], dt, c->stats_dev, s, c->ev_u);
     if (r) return r;
     if (cudaEventRecord(c->ev_free[p], s)) return VOF_ERR_CUDA;
     if (cudaMemcpyAsync(alpha, c->h_alpha, sizeof(double) * c->nc, cudaMemcpyDeviceToHost, s)) return VOF_ERR_CUDA;

@@ -11,6 +11,8 @@
 // offsets to the cell centre computed once at context creation, so the
 // rounding of a coordinate is relative to the cell size, not to its position.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <math.h>
 #include <stdint.h>
 
@@ -73,17 +75,42 @@ template <class R> __device__ __forceinline__ R3<R> ld43(const R4<R> *p, long i)
     return r3<R>(v.x, v.y, v.z);
 }
 
+// Threshold, sign and order tests of distances (tol >= 0).  FP32: the native
+// compares.  FP64: integer compares of the bit patterns (dbits), the same
+// decisions for every value that is not NaN: this part's FP64 pipe runs at
+// 1/64 of the FP32 rate, and an FP64 compare or min/max holds it as long as
+// an FMA.
+__device__ __forceinline__ bool rabove(float v, float t) { return v > t; }   // v > t
+__device__ __forceinline__ bool rbelow(float v, float t) { return v < -t; }  // v < -t
+__device__ __forceinline__ bool rpos(float v) { return v > 0.0f; }
+__device__ __forceinline__ bool rneg(float v) { return v < 0.0f; }
+__device__ __forceinline__ bool rgt(float a, float b) { return a > b; }
+__device__ __forceinline__ bool rabove(double v, double t) { return gt_pos(v, t); }
+__device__ __forceinline__ bool rbelow(double v, double t) { return lt_neg(v, t); }
+__device__ __forceinline__ bool rpos(double v) { return gt_pos(v, 0.0); }
+__device__ __forceinline__ bool rneg(double v) { return lt_neg(v, 0.0); }
+// a > b for any signs: the bit patterns made monotone by flipping the
+// magnitude bits of negative values (-0 then orders just below +0)
+__device__ __forceinline__ bool rgt(double a, double b)
+{
+    DBits x = dbits(a), y = dbits(b);
+    const int sx = x.hi >> 31, sy = y.hi >> 31;
+    x.hi ^= sx & 0x7fffffff; x.lo ^= (unsigned)sx;
+    y.hi ^= sy & 0x7fffffff; y.lo ^= (unsigned)sy;
+    return !bits_le(x, y);
+}
+
 // fraction of a tetrahedron below level 0 for sorted vertex values h0..h3
 template <class R>
 __device__ __forceinline__ R rfrac_below(R h0, R h1, R h2, R h3)
 {
-    if (R(0) <= h0) return R(0);
-    if (R(0) >= h3) return R(1);
-    if (R(0) <= h1) {
+    if (!rneg(h0)) return R(0);
+    if (!rpos(h3)) return R(1);
+    if (!rneg(h1)) {
         const R x = -h0;
         return rdiv(x, h1 - h0) * rdiv(x, h2 - h0) * rdiv(x, h3 - h0);
     }
-    if (R(0) >= h2) {
+    if (!rpos(h2)) {
         const R y = h3;
         return R(1) - rdiv(y, h3 - h0) * rdiv(y, h3 - h1) * rdiv(y, h3 - h2);
     }
@@ -96,7 +123,7 @@ template <class R>
 __device__ __forceinline__ void rsort4(R &a, R &b, R &c, R &d)
 {
     R t;
-#define CS(p, q) if (p > q) { t = p; p = q; q = t; }
+#define CS(p, q) if (rgt(p, q)) { t = p; p = q; q = t; }
     CS(a, b) CS(c, d) CS(a, c) CS(b, d) CS(b, c)
 #undef CS
 }
@@ -198,10 +225,17 @@ __device__ __forceinline__ void fdist(const RTet<R> &t, R4<R> p, R tol, R s[4], 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         R v = p.x * t.v[i].x + p.y * t.v[i].y + p.z * t.v[i].z - p.w;
-        if (rabs(v) <= tol) v = R(0);
-        s[i] = v;
-        nin += v < R(0);
-        nup += v > R(0);
+        if constexpr (std::is_same<R, double>::value) {  // integer tests
+            const bool up = rabove(v, tol), dn = rbelow(v, tol);
+            s[i] = (up || dn) ? v : R(0);
+            nin += dn;
+            nup += up;
+        } else {
+            if (rabs(v) <= tol) v = R(0);
+            s[i] = v;
+            nin += v < R(0);
+            nup += v > R(0);
+        }
     }
 }
 
@@ -216,7 +250,7 @@ __device__ __forceinline__ void fsplit(const RTet<R> &t, const R s[4], int nin, 
     V P0 = t.v[0], P1 = t.v[1], P2 = t.v[2], P3 = t.v[3];
     R S0 = s[0], S1 = s[1], S2 = s[2], S3 = s[3];
 #define MX_CX(a, b)                                                   \
-    if (!(S##a < R(0)) && S##b < R(0)) {                              \
+    if (!rneg(S##a) && rneg(S##b)) {                                  \
         V tp = P##a; P##a = P##b; P##b = tp;                          \
         R ts = S##a; S##a = S##b; S##b = ts;                          \
     }
@@ -289,7 +323,7 @@ __device__ __forceinline__ void mx_clip(MXShared<R, MX_STACK> &sh, int nq, R tol
                         v6 *= rfrac_below(h0, h1, h2, h3);
                     }
                 }
-                if (v6 != R(0)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);
+                if (rpos(v6)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);  // (v6 >= 0)
             }
             nl -= p;
             __syncwarp();
@@ -355,7 +389,7 @@ __device__ __forceinline__ void mx_clip(MXShared<R, MX_STACK> &sh, int nq, R tol
             wk.add(WK_VOL, lw & 1);
             wk.add(WK_FRAC, lw >> 1);
             if (cut && nch > 0) wk.add(WK_EDGE, nin == 2 ? 4 : 3);
-            if (v6 != R(0)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);
+            if (rpos(v6)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);
             if (nch > 0) {
                 const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
                 // parts of the lanes before this one that go the same way
@@ -400,8 +434,8 @@ __device__ __forceinline__ void mx_flush(MXShared<R, MX_STACK> &sh, int nt, int 
             const R *tb = sh.Pb[pr];
             const bool live = sh.Tsg[3 * pr] != R(0) || sh.Tsg[3 * pr + 1] != R(0) || sh.Tsg[3 * pr + 2] != R(0);
             const bool ov = lane < ncand && live &&
-                            !(tb[3] < kb[0] || kb[3] < tb[0] || tb[4] < kb[1] || kb[4] < tb[1] || tb[5] < kb[2] ||
-                              kb[5] < tb[2]);
+                            !(rgt(kb[0], tb[3]) || rgt(tb[0], kb[3]) || rgt(kb[1], tb[4]) || rgt(tb[1], kb[4]) ||
+                              rgt(kb[2], tb[5]) || rgt(tb[2], kb[5]));
             const unsigned bm = __ballot_sync(0xffffffffu, ov);
             if (ov) sh.PQ[total + __popc(bm & lt)] = (unsigned short)(pr | lane << 3);
             total += __popc(bm);
@@ -437,15 +471,34 @@ __device__ __forceinline__ void mx_flush(MXShared<R, MX_STACK> &sh, int nt, int 
                 for (int i = 0; i < 6; ++i)
                     d[i] = rfma(pl.x, v[3 * i], rfma(pl.y, v[3 * i + 1], rfma(pl.z, v[3 * i + 2], -pl.w)));
                 // T0 = a0 a1 a2 b2, T1 = a0 a1 b2 b1, T2 = a0 b0 b1 b2
-                const R l01 = rmin(d[0], d[1]), h01 = rmax(d[0], d[1]);
-                const R lo0 = rmin(l01, rmin(d[2], d[5])), hi0 = rmax(h01, rmax(d[2], d[5]));
-                const R lo1 = rmin(l01, rmin(d[5], d[4])), hi1 = rmax(h01, rmax(d[5], d[4]));
-                const R lo2 = rmin(rmin(d[0], d[3]), rmin(d[4], d[5])), hi2 = rmax(rmax(d[0], d[3]), rmax(d[4], d[5]));
-                if (q < npl) {
-                    outside[0] |= lo0 >= -tol; outside[1] |= lo1 >= -tol; outside[2] |= lo2 >= -tol;
-                    if (hi0 > tol) mask[0] |= 1u << q;
-                    if (hi1 > tol) mask[1] |= 1u << q;
-                    if (hi2 > tol) mask[2] |= 1u << q;
+                if constexpr (std::is_same<R, double>::value) {
+                    // the points not clearly inside the plane (ge) and those
+                    // clearly outside it (gt) as bits 0..5 = a0 a1 a2 b0 b1 b2,
+                    // from integer tests (no FP64 compare or min/max)
+                    unsigned ge = 0u, gt = 0u;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) {
+                        ge |= (unsigned)!rbelow(d[i], tol) << i;
+                        gt |= (unsigned)rabove(d[i], tol) << i;
+                    }
+                    constexpr unsigned M0 = 0x27u, M1 = 0x33u, M2 = 0x39u;
+                    if (q < npl) {
+                        outside[0] |= (ge & M0) == M0; outside[1] |= (ge & M1) == M1; outside[2] |= (ge & M2) == M2;
+                        if (gt & M0) mask[0] |= 1u << q;
+                        if (gt & M1) mask[1] |= 1u << q;
+                        if (gt & M2) mask[2] |= 1u << q;
+                    }
+                } else {
+                    const R l01 = rmin(d[0], d[1]), h01 = rmax(d[0], d[1]);
+                    const R lo0 = rmin(l01, rmin(d[2], d[5])), hi0 = rmax(h01, rmax(d[2], d[5]));
+                    const R lo1 = rmin(l01, rmin(d[5], d[4])), hi1 = rmax(h01, rmax(d[5], d[4]));
+                    const R lo2 = rmin(rmin(d[0], d[3]), rmin(d[4], d[5])), hi2 = rmax(rmax(d[0], d[3]), rmax(d[4], d[5]));
+                    if (q < npl) {
+                        outside[0] |= lo0 >= -tol; outside[1] |= lo1 >= -tol; outside[2] |= lo2 >= -tol;
+                        if (hi0 > tol) mask[0] |= 1u << q;
+                        if (hi1 > tol) mask[1] |= 1u << q;
+                        if (hi2 > tol) mask[2] |= 1u << q;
+                    }
                 }
             }
 #pragma unroll
@@ -668,8 +721,8 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                             const V3 cc = ld3(m.cc, m.nc, c);
                             dc = r3(rconv<R>(cc.x - oc.x), rconv<R>(cc.y - oc.y), rconv<R>(cc.z - oc.z));
                             const R4<R> cb0 = ldg4(cbl, 2 * (long)c), cb1 = ldg4(cbl, 2 * (long)c + 1);
-                            pass = !(cb1.x + dc.x < pb[0] || pb[3] < cb0.x + dc.x || cb1.y + dc.y < pb[1] ||
-                                     pb[4] < cb0.y + dc.y || cb1.z + dc.z < pb[2] || pb[5] < cb0.z + dc.z);
+                            pass = !(rgt(pb[0], cb1.x + dc.x) || rgt(cb0.x + dc.x, pb[3]) || rgt(pb[1], cb1.y + dc.y) ||
+                                     rgt(cb0.y + dc.y, pb[4]) || rgt(pb[2], cb1.z + dc.z) || rgt(cb0.z + dc.z, pb[5]));
                         }
                     }
                     int nkt = 0, t0 = 0;
@@ -736,8 +789,8 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                 const R4<R> b0 = ldg4(q, 4), b1 = ldg4(q, 5);
                 kbx[0] = b0.x + dc.x; kbx[1] = b0.y + dc.y; kbx[2] = b0.z + dc.z;
                 kbx[3] = b1.x + dc.x; kbx[4] = b1.y + dc.y; kbx[5] = b1.z + dc.z;
-                cand = !(kbx[3] < pb[0] || pb[3] < kbx[0] || kbx[4] < pb[1] || pb[4] < kbx[1] ||
-                         kbx[5] < pb[2] || pb[5] < kbx[2]);
+                cand = !(rgt(pb[0], kbx[3]) || rgt(kbx[0], pb[3]) || rgt(pb[1], kbx[4]) || rgt(kbx[1], pb[4]) ||
+                         rgt(pb[2], kbx[5]) || rgt(kbx[2], pb[5]));
                 if (cand) {
                     wk.add(WK_SHIFT, 4);
 #pragma unroll

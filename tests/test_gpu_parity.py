@@ -384,10 +384,11 @@ def test_advect_host_pageable_buffers(torch, O):
 
 
 def test_advect_host_steps_queued(torch, O):
-    """Five host-buffer steps queued back to back (the velocity and flux copies
-    of a call overlap the previous step, alternating between two device
-    buffer pairs) give the same fields and statistics, bit for bit, as the
-    device-buffer steps one by one."""
+    """Five host-buffer steps queued back to back (pinned U read in place by the
+    kernels over the host link, F and pageable U copied through two
+    alternating device buffer pairs that overlap the previous step) give the
+    same fields and statistics, bit for bit, as the device-buffer steps one by
+    one."""
     from paper_1305_3417_gb300 import vof
     w, ctx, om = contexts(torch, O, "deform20")
     steps = [w.step_inputs(k) for k in range(5)]
@@ -400,6 +401,16 @@ def test_advect_host_steps_queued(torch, O):
     hs = torch.zeros(vof.S_LEN, dtype=torch.float64).pin_memory()
     for k, (_, _, dt) in enumerate(steps):
         vof.vof_advect_host(ctx.h, ha, hU[k], hF[k], dt, hs)
+    torch.cuda.synchronize()
+    assert np.array_equal(ha.numpy(), H(ta))
+    assert np.array_equal(hs.numpy(), H(st))
+    # pageable U and F (the copy path), alpha pinned, queued the same way
+    ha = torch.from_numpy(w.alpha0.copy()).pin_memory()
+    pU = [u.clone() for u in hU]
+    pF = [f.clone() for f in hF]
+    assert not pU[0].is_pinned()
+    for k, (_, _, dt) in enumerate(steps):
+        vof.vof_advect_host(ctx.h, ha, pU[k], pF[k], dt, hs)
     torch.cuda.synchronize()
     assert np.array_equal(ha.numpy(), H(ta))
     assert np.array_equal(hs.numpy(), H(st))
