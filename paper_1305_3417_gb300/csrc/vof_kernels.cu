@@ -208,7 +208,7 @@ __device__ __forceinline__ R frac_below_dd(R h0, R h1, R h2, R h3, R d, R &df)
 // G lanes per cell: 32, or 8 where every cell has at most 16 tetrahedra (a
 // tetrahedral mesh: four cells per warp); reductions over the cell's lanes
 template <bool LIST, bool MIXED, int G, int KL, bool COUNT>
-__global__ void __launch_bounds__(128, 5) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
+__global__ void __launch_bounds__(128, KL == 3 ? 4 : 5) k_reconstruct(DevMesh m, const double *__restrict__ alpha,
                                                      const double *__restrict__ palpha, const int *list,
                                                      const int *count, double *nout, double *dout,
                                                      uint8_t *fout, int *itout, int *maxit, unsigned *status,
@@ -1781,8 +1781,9 @@ static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const do
         gin = c->grad;
     }
     // lanes per cell and tetrahedra per lane: 8 x 2 (cells of <= 16 tetrahedra),
-    // 32 x 2 (<= 64), 32 x 3 (<= 96: octree cells next to finer ones); the
-    // instrumented variant while work counting is on (vof_count_work)
+    // 8 x 3 (<= 24: hexahedra, four cells per warp), 32 x 2 (<= 64), 32 x 3
+    // (<= 96: octree cells next to finer ones); the instrumented variant while
+    // work counting is on (vof_count_work)
 #define RC_GO(G_, K_, BL)                                                                                    \
     do {                                                                                                     \
         if (c->work_on)                                                                                      \
@@ -1792,9 +1793,12 @@ static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const do
             k_reconstruct<LIST, MIXED, G_, K_, false><<<BL, 128, 0, s>>>(c->m, alpha, palpha, list, count, n,   \
                 d, flags, iters, maxit, c->status, c->mlp_s0, mlp_cap(c), next, nullptr, gin);                \
     } while (0)
-    if (c->rc_g == 8) {
+    if (c->rc_g == 8 && c->rc_k <= 2) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
         RC_GO(8, 2, blocks);
+    } else if (c->rc_g == 8) {
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
+        RC_GO(8, 3, blocks);
     } else if (c->rc_k <= 2) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 32, 128);
         RC_GO(32, 2, blocks);
