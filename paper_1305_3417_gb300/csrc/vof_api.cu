@@ -450,8 +450,8 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->precision = opt ? opt->precision : VOF_FP64;
     {
         const int kmax = *std::max_element(ktet.begin(), ktet.end());
-        c->rc_g = kmax <= 24 ? 8 : 32;
-        c->rc_k = kmax <= 16 ? 2 : kmax <= 24 ? 3 : kmax <= 64 ? 2 : 3;
+        c->rc_g = kmax <= 4 ? 4 : kmax <= 24 ? 8 : 32;
+        c->rc_k = kmax <= 4 ? 1 : kmax <= 16 ? 2 : kmax <= 24 ? 3 : kmax <= 64 ? 2 : 3;
     }
     c->bound = opt ? (opt->bound != 0) : 1;
     int err = 0;

@@ -1780,7 +1780,8 @@ static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const do
         launch_lsq_gradient(c, alpha, list, count, c->grad, s);
         gin = c->grad;
     }
-    // lanes per cell and tetrahedra per lane: 8 x 2 (cells of <= 16 tetrahedra),
+    // lanes per cell and tetrahedra per lane: 4 x 1 (tetrahedral cells, eight
+    // per warp), 8 x 2 (cells of <= 16 tetrahedra),
     // 8 x 3 (<= 24: hexahedra, four cells per warp), 32 x 2 (<= 64), 32 x 3
     // (<= 96: octree cells next to finer ones); the instrumented variant while
     // work counting is on (vof_count_work)
@@ -1793,7 +1794,10 @@ static void rc_launch(vof_ctx *c, int list_blocks, const double *alpha, const do
             k_reconstruct<LIST, MIXED, G_, K_, false><<<BL, 128, 0, s>>>(c->m, alpha, palpha, list, count, n,   \
                 d, flags, iters, maxit, c->status, c->mlp_s0, mlp_cap(c), next, nullptr, gin);                \
     } while (0)
-    if (c->rc_g == 8 && c->rc_k <= 2) {
+    if (c->rc_g == 4) {
+        const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 4, 128);
+        RC_GO(4, 1, blocks);
+    } else if (c->rc_g == 8 && c->rc_k <= 2) {
         const int blocks = LIST ? list_blocks : cdiv((long)c->nc * 8, 128);
         RC_GO(8, 2, blocks);
     } else if (c->rc_g == 8) {
