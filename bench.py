@@ -61,7 +61,7 @@ BYTES_PER_FACE = 72.0
 # --steps 2 --warmup 3 --no-tune --no-cpu-baseline --fp64-steps 0 --full-run 0);
 # valid while the kernel's sources hash to the captured digest, else null.
 TRAFFIC = {
-    ("deform3d", 128, "mixed"): {"bytes": 68.59e6, "sources_sha256": "27e7cfc64f21fd0d9c675a3216386057967267a92a91c7b2a324f1632b1f9ef8"},
+    ("deform3d", 128, "mixed"): {"bytes": 68.55e6, "sources_sha256": "0a356b2b35120c5b195587a2b391fb96761d6d1f0c71f93ec36af247c375b05b"},
 }
 TRAFFIC_SOURCES = ["paper_1305_3417_gb300/csrc/vof_phase_flux.cu", "paper_1305_3417_gb300/csrc/vof_device.cuh"]
 
@@ -480,6 +480,7 @@ def run_batch(args, world, rank, local):
     for _ in range(args.warmup):
         bt.advect(alpha, U, F, stats, mass0)
     torch.cuda.synchronize()
+    a_start = alpha.clone()  # the end-to-end steps start from the same state
     st0 = vof.vof_status(ctx)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -525,7 +526,7 @@ def run_batch(args, world, rank, local):
             "work_per_launch": work, "flops_per_launch": pf}
     # end to end through the batched call itself: every step copies alpha, U
     # and F from pinned host memory, replays the step and reads alpha back
-    ha = torch.from_numpy(b.alpha0.copy()).pin_memory()
+    ha = a_start.cpu().pin_memory()
     hU, hF = U.cpu().pin_memory(), F.cpu().pin_memory()
     da, dU, dF = torch.empty_like(alpha), torch.empty_like(U), torch.empty_like(F)
 
@@ -536,8 +537,9 @@ def run_batch(args, world, rank, local):
         bt.advect(da, dU, dF, stats, mass)
         ha.copy_(da, non_blocking=True)
 
-    host_step()
+    host_step()  # (the graph is captured again for these buffers)
     torch.cuda.synchronize()
+    ha.copy_(a_start.cpu())
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record(stream)
     for _ in range(args.steps):

@@ -450,8 +450,17 @@ int vof_create(const vof_mesh *mesh, const vof_options *opt, vof_ctx **out)
     c->precision = opt ? opt->precision : VOF_FP64;
     {
         const int kmax = *std::max_element(ktet.begin(), ktet.end());
-        c->rc_g = kmax <= 4 ? 4 : kmax <= 24 ? 8 : 32;
-        c->rc_k = kmax <= 4 ? 1 : kmax <= 16 ? 2 : kmax <= 24 ? 3 : kmax <= 64 ? 2 : 3;
+        // lanes per cell in the reconstruction: narrow groups (several cells
+        // a warp) for the mixed form's few, short FP32 iterations; in the FP64
+        // form the groups of a warp would run their long Alg. 1 iterations
+        // one after another, so hexahedra keep a warp each there
+        if (c->precision == VOF_MIXED) {
+            c->rc_g = kmax <= 4 ? 4 : kmax <= 24 ? 8 : 32;
+            c->rc_k = kmax <= 4 ? 1 : kmax <= 16 ? 2 : kmax <= 24 ? 3 : kmax <= 64 ? 2 : 3;
+        } else {
+            c->rc_g = kmax <= 16 ? 8 : 32;
+            c->rc_k = kmax <= 64 ? 2 : 3;
+        }
     }
     c->bound = opt ? (opt->bound != 0) : 1;
     int err = 0;

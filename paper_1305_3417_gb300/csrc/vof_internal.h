@@ -123,8 +123,8 @@ struct vof_ctx {
     // grid multiplier over the resident blocks
     int pf_warps, pf_mult;
     int pf_stack;                // clip-piece stack per warp: 0 = 92 pieces, 1 = 56 (more resident warps)
-    int rc_g;                    // reconstruction lanes per cell: 4 (<= 4 tetrahedra per cell), 8 (<= 24), else 32
-    int rc_k;                    // tetrahedra per lane: 1 (<= 4), 2 (<= 16 or <= 64), else 3
+    int rc_g;                    // reconstruction lanes per cell (4, 8 or 32; by form and cell size)
+    int rc_k;                    // tetrahedra per lane (1, 2 or 3)
     // gradient of the reconstruction (vof_set_gradient): VOF_GRAD_NAG or
     // VOF_GRAD_LSQ; the LSQ stencil (cells sharing a point with each cell, CSR)
     // and the gradient buffer are made at the first selection of LSQ
