@@ -106,32 +106,19 @@ __device__ __forceinline__ R rfrac_below(R h0, R h1, R h2, R h3)
 {
     if (!rneg(h0)) return R(0);
     if (!rpos(h3)) return R(1);
-    if constexpr (std::is_same<R, double>::value) {
-        // FP64: one division per case (the FP64 pipe's costliest step)
-        if (!rneg(h1)) {
-            const R x = -h0;
-            return (x * x * x) / ((h1 - h0) * (h2 - h0) * (h3 - h0));
-        }
-        if (!rpos(h2)) {
-            const R y = h3;
-            return R(1) - (y * y * y) / ((h3 - h0) * (h3 - h1) * (h3 - h2));
-        }
-        const R d1 = h2 - h0, d2 = h3 - h0, d3 = h2 - h1, d4 = h3 - h1;
-        const R p12 = d1 * d2, p123 = p12 * d3, q = R(1) / (p123 * d4);
-        const R r4 = q * p123, q3 = q * d4, r3 = q3 * p12, q2 = q3 * d3, r1 = q2 * d2, r2 = q2 * d1;
-        const R a = -h0 * r1, b = -h0 * r2, c = -h1 * r3, e = -h1 * r4;
-        return a * b + a * (R(1) - b) * e + (R(1) - a) * c * e;
-    }
+    // one division per case
     if (!rneg(h1)) {
         const R x = -h0;
-        return rdiv(x, h1 - h0) * rdiv(x, h2 - h0) * rdiv(x, h3 - h0);
+        return rdiv(x * x * x, (h1 - h0) * (h2 - h0) * (h3 - h0));
     }
     if (!rpos(h2)) {
         const R y = h3;
-        return R(1) - rdiv(y, h3 - h0) * rdiv(y, h3 - h1) * rdiv(y, h3 - h2);
+        return R(1) - rdiv(y * y * y, (h3 - h0) * (h3 - h1) * (h3 - h2));
     }
-    const R a = rdiv(-h0, h2 - h0), b = rdiv(-h0, h3 - h0);
-    const R c = rdiv(-h1, h2 - h1), e = rdiv(-h1, h3 - h1);
+    const R d1 = h2 - h0, d2 = h3 - h0, d3 = h2 - h1, d4 = h3 - h1;
+    const R p12 = d1 * d2, p123 = p12 * d3, q = rdiv(R(1), p123 * d4);
+    const R r4 = q * p123, q3 = q * d4, r3 = q3 * p12, q2 = q3 * d3, r1 = q2 * d2, r2 = q2 * d1;
+    const R a = -h0 * r1, b = -h0 * r2, c = -h1 * r3, e = -h1 * r4;
     return a * b + a * (R(1) - b) * e + (R(1) - a) * c * e;
 }
 
@@ -272,47 +259,28 @@ __device__ __forceinline__ void fsplit(const RTet<R> &t, const R s[4], int nin, 
     }
     MX_CX(0, 1) MX_CX(2, 3) MX_CX(0, 2) MX_CX(1, 3) MX_CX(1, 2)
 #undef MX_CX
-    if constexpr (std::is_same<R, double>::value) {
-        // FP64: the three or four edge parameters sa / (sa - sb) from one
-        // division (the reciprocal of the denominators' product, then
-        // products), as the divisions hold this part's FP64 pipe longest
-        auto ept = [](V a, V b, R t) { return a + (b - a) * t; };
-        if (nin == 1) {
-            const R d1 = S0 - S1, d2 = S0 - S2, d3 = S0 - S3, p12 = d1 * d2, q = R(1) / (p12 * d3);
-            const R r3 = q * p12, q3 = q * d3, r1 = q3 * d2, r2 = q3 * d1;
-            put(RTet<R>{{P0, ept(P0, P1, S0 * r1), ept(P0, P2, S0 * r2), ept(P0, P3, S0 * r3)}}, 0);
-            return;
-        }
-        V a0, a1, a2, b0, b1, b2;
-        if (nin == 2) {
-            const R d1 = S0 - S2, d2 = S0 - S3, d3 = S1 - S2, d4 = S1 - S3;
-            const R p12 = d1 * d2, p123 = p12 * d3, q = R(1) / (p123 * d4);
-            const R r4 = q * p123, q3 = q * d4, r3 = q3 * p12, q2 = q3 * d3, r1 = q2 * d2, r2 = q2 * d1;
-            a0 = P0; a1 = ept(P0, P2, S0 * r1); a2 = ept(P0, P3, S0 * r2);
-            b0 = P1; b1 = ept(P1, P2, S1 * r3); b2 = ept(P1, P3, S1 * r4);
-        } else {
-            const R d1 = S0 - S3, d2 = S1 - S3, d3 = S2 - S3, p12 = d1 * d2, q = R(1) / (p12 * d3);
-            const R r3 = q * p12, q3 = q * d3, r1 = q3 * d2, r2 = q3 * d1;
-            a0 = P0; a1 = P1; a2 = P2;
-            b0 = ept(P0, P3, S0 * r1); b1 = ept(P1, P3, S1 * r2); b2 = ept(P2, P3, S2 * r3);
-        }
-        put(RTet<R>{{a0, a1, a2, b2}}, 0);
-        put(RTet<R>{{a0, a1, b2, b1}}, 1);
-        put(RTet<R>{{a0, b0, b1, b2}}, 2);
-        return;
-    }
-    auto ep = [](V a, R sa, V b, R sb) { return a + (b - a) * rdiv(sa, sa - sb); };
+    // the three or four edge parameters sa / (sa - sb) from one division
+    // (the reciprocal of the denominators' product, then products): the
+    // divisions hold the FP64 pipe longest, and FP32 saves issue slots
+    auto ept = [](V a, V b, R t) { return a + (b - a) * t; };
     if (nin == 1) {
-        put(RTet<R>{{P0, ep(P0, S0, P1, S1), ep(P0, S0, P2, S2), ep(P0, S0, P3, S3)}}, 0);
+        const R d1 = S0 - S1, d2 = S0 - S2, d3 = S0 - S3, p12 = d1 * d2, q = rdiv(R(1), p12 * d3);
+        const R r3 = q * p12, q3 = q * d3, r1 = q3 * d2, r2 = q3 * d1;
+        put(RTet<R>{{P0, ept(P0, P1, S0 * r1), ept(P0, P2, S0 * r2), ept(P0, P3, S0 * r3)}}, 0);
         return;
     }
     V a0, a1, a2, b0, b1, b2;
     if (nin == 2) {
-        a0 = P0; a1 = ep(P0, S0, P2, S2); a2 = ep(P0, S0, P3, S3);
-        b0 = P1; b1 = ep(P1, S1, P2, S2); b2 = ep(P1, S1, P3, S3);
+        const R d1 = S0 - S2, d2 = S0 - S3, d3 = S1 - S2, d4 = S1 - S3;
+        const R p12 = d1 * d2, p123 = p12 * d3, q = rdiv(R(1), p123 * d4);
+        const R r4 = q * p123, q3 = q * d4, r3 = q3 * p12, q2 = q3 * d3, r1 = q2 * d2, r2 = q2 * d1;
+        a0 = P0; a1 = ept(P0, P2, S0 * r1); a2 = ept(P0, P3, S0 * r2);
+        b0 = P1; b1 = ept(P1, P2, S1 * r3); b2 = ept(P1, P3, S1 * r4);
     } else {
+        const R d1 = S0 - S3, d2 = S1 - S3, d3 = S2 - S3, p12 = d1 * d2, q = rdiv(R(1), p12 * d3);
+        const R r3 = q * p12, q3 = q * d3, r1 = q3 * d2, r2 = q3 * d1;
         a0 = P0; a1 = P1; a2 = P2;
-        b0 = ep(P0, S0, P3, S3); b1 = ep(P1, S1, P3, S3); b2 = ep(P2, S2, P3, S3);
+        b0 = ept(P0, P3, S0 * r1); b1 = ept(P1, P3, S1 * r2); b2 = ept(P2, P3, S2 * r3);
     }
     put(RTet<R>{{a0, a1, a2, b2}}, 0);
     put(RTet<R>{{a0, a1, b2, b1}}, 1);
