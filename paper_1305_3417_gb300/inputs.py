@@ -34,7 +34,7 @@ import numpy as np
 
 __all__ = [
     "Mesh", "hex_mesh", "kuhn_tet_mesh", "disc_rect_area", "disc_fraction_2d",
-    "sampled_fraction", "sphere_sdf", "cylinder_sdf", "Field", "translation_field", "diagonal_shuttle_field", "periodic_shear_field",
+    "sampled_fraction", "sphere_sdf", "cylinder_sdf", "Field", "translation_field", "diagonal_shuttle_field", "periodic_shear_field", "shear_field",
     "deformation_field", "single_vortex_field", "rotation_field",
     "face_flux_stokes", "cell_velocity", "Workload", "make_workload",
     "concat_meshes", "BatchCase", "Batch", "make_batch",
@@ -759,6 +759,39 @@ def periodic_shear_field(T: float = 2.0):
                  lambda t: (T / pi) * math.sin(pi * t / T))
 
 
+def shear_field(T: float = 3.0, umax: float = 1.0, R: float = 0.5):
+    """The shear test case (Sec. 4.2, Eq. shear-test-case, after Liovic et al.):
+    the single vortex in x, y reversed, sin(2 pi y) sin^2(pi x) and
+    -sin(2 pi x) sin^2(pi y), with the axial component umax (1 - r/R)^2 about
+    the box's vertical axis (r the distance from x = y = 1/2), all times
+    cos(pi t / T) (reading R22 of the garbled time factor of the third
+    component).  Potential: A_z = sin^2(pi x) sin^2(pi y) / pi for the x, y
+    part; A_x = -int_{1/2}^{y} umax (1 - r/R)^2 dy' in closed form for the
+    axial part (with sqrt(a^2 + t^2) integrated as (t s + a^2 asinh(t/|a|))/2)."""
+    pi = math.pi
+
+    def u(x):
+        X, Y = x[..., 0], x[..., 1]
+        r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+        return np.stack([np.sin(2 * pi * Y) * np.sin(pi * X) ** 2,
+                         -np.sin(2 * pi * X) * np.sin(pi * Y) ** 2,
+                         umax * (1.0 - r / R) ** 2], -1)
+
+    def A(x):
+        X, Y = x[..., 0], x[..., 1]
+        a, t = X - 0.5, Y - 0.5
+        sq = np.sqrt(a * a + t * t)
+        aa = np.abs(a)
+        lg = np.where(aa > 0.0, a * a * np.arcsinh(t / np.where(aa > 0.0, aa, 1.0)), 0.0)
+        G = 0.5 * (t * sq + lg)                       # int_0^t sqrt(a^2 + s^2) ds
+        Iw = t - (2.0 / R) * G + (a * a * t + t ** 3 / 3.0) / (R * R)
+        return np.stack([-umax * Iw, np.zeros_like(X),
+                         (1 / pi) * np.sin(pi * X) ** 2 * np.sin(pi * Y) ** 2], -1)
+
+    return Field("shear", u, A, lambda t: math.cos(pi * t / T),
+                 lambda t: (T / pi) * math.sin(pi * t / T))
+
+
 def rotation_field(omega, x0=(0.5, 0.5, 0.5)):
     om = np.asarray(omega, float)
     c = np.asarray(x0, float)
@@ -843,6 +876,10 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
                   x and y (the disc crosses y = 1 and comes back at y = 0), front/back
                   walls.
     disc2d_open:  the same with the four sides open (empty inflow, geometric outflow).
+    shear3d:      uniform n^3 hex (n=16) periodic in z (the axial flow leaves
+                  through z = 1 and comes back at z = 0), walls in x, y; sphere
+                  R=0.15 at (0.5,0.75,0.25); the shear field (T=3, umax=1,
+                  R=0.5, R22), Co 0.5 on the speed, to t=3.
     shear_periodic: jittered (+-0.2h, seed 1304) n^3 hex (n=12) periodic in x, y, z,
                   a sphere R=0.25 at (0.9,0.15,0.5) wrapped across two seams, the
                   periodic shear field (sin 2 pi y, sin 2 pi z, sin 2 pi x)
@@ -875,6 +912,12 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
         mesh = hex_mesh((n, n, n), periodic="xyz")
         a0 = sampled_fraction(mesh, sphere_sdf((0.5, 0.5, 0.5), 0.15))
         fld = diagonal_shuttle_field()
+        steps = None
+    elif name == "shear3d":
+        n = 16 if n is None else n
+        mesh = hex_mesh((n, n, n), periodic="z")
+        a0 = sampled_fraction(mesh, sphere_sdf((0.5, 0.75, 0.25), 0.15))
+        fld = shear_field(3.0)
         steps = None
     elif name == "shear_periodic":
         n = 12 if n is None else n
@@ -911,7 +954,7 @@ def make_workload(name: str, n: int | None = None, co: float = 0.5, seed: int | 
     dt = co * hc / umax
     Fs = face_flux_stokes(mesh, fld.A)
     t_end = {"disc2d": steps * dt if steps else None, "disc2d_open": steps * dt if steps else None,
-             "translate3d": 2.0, "shear_periodic": 2.0, "deform3d": 3.0, "vortex_tet": 8.0, "octree": 0.5}[name]
+             "translate3d": 2.0, "shear3d": 3.0, "shear_periodic": 2.0, "deform3d": 3.0, "vortex_tet": 8.0, "octree": 0.5}[name]
     if steps is None:
         steps = int(math.ceil(t_end / dt - 1e-12))
     exact = None

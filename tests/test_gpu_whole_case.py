@@ -43,6 +43,7 @@ CASES = {
     "disc2d_open": lambda: I.make_workload("disc2d_open"),
     "translate3d_16": lambda: I.make_workload("translate3d", n=16),
     "shear_periodic_12": lambda: I.make_workload("shear_periodic", n=12),
+    "shear3d_16": lambda: I.make_workload("shear3d", n=16),
     "deform3d_24": lambda: I.make_workload("deform3d", n=24),
     "vortex_tet_10": lambda: I.make_workload("vortex_tet", n=10),
 }
