@@ -243,6 +243,17 @@ int vof_phase_flux(vof_ctx *ctx, const double *alpha, const double *n, const dou
  * conservative bounding pass; stats (device, VOF_S_LEN doubles) or NULL. */
 int vof_update(vof_ctx *ctx, double *alpha, const double *Valpha, double *stats, void *stream);
 
+/* Courant number of a step (the paper sets each time step from the Courant
+ * number of the current velocity, Sec. 4.2): Co = max over cells of
+ * (1/2) sum over the cell's faces |F_f| dt / |C_c|, which is (|u|+|v|+|w|)
+ * dt / h for a uniform velocity on a uniform hexahedral mesh.  F [n_faces]
+ * (device) as for vof_advect (a periodic face counts for both its cells, its
+ * copy for none); co: one double (device), written.  Asynchronous on
+ * `stream`.  A caller keeping a target Courant number takes the next
+ * dt = dt * Co_target / Co.  VOF_ERR_INVALID_ARG for a null pointer or a
+ * dt that is not finite and positive. */
+int vof_courant(vof_ctx *ctx, const double *F, double dt, double *co, void *stream);
+
 /* One full advection step A1-A7 over the narrow band: band classification,
  * reconstruction of interface cells, point velocities and flux correction of
  * band faces, phase fluxes, update.  alpha [n_cells] in/out, Uc [3*n_cells]

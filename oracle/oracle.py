@@ -47,6 +47,7 @@ def lib():
             "vo_mesh_create": (P, [I, I, I, I, P, P, P, P, P, P, P, P]),
             "vo_mesh_create_periodic": (P, [I, I, I, I, P, P, P, P, P, P, P, P, P, P, P, P]),
             "vo_stencil_codes": (I, [P, I, P, P, I]),
+            "vo_courant": (D, [P, P, D]),
             "vo_mesh_destroy": (V, [P]),
             "vo_set_threads": (I, [I]),
             "vo_geometry": (V, [P, P, P, P, P]),
@@ -152,6 +153,10 @@ class OracleMesh:
         out = np.zeros(2048, np.int32)
         n = lib().vo_stencil(self.h, int(f), _p(out), 2048)
         return out[:n].copy()
+
+    def courant(self, F, dt):
+        F = _f64(F)
+        return lib().vo_courant(self.h, _p(F), float(dt))
 
     def stencil_codes(self, f):
         """(cells, translation codes) of the face stencil (periodic meshes)."""

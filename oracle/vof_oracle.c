@@ -1401,6 +1401,26 @@ static double bound_global(const vo_mesh *m, double *alpha)
     return Ep + Em;
 }
 
+/* The Courant number of a step (Sec. 4.2 sets the time step from it): the
+ * largest (1/2) sum over a cell's faces |F_f| dt / V_c; a cell takes a
+ * periodic face through its copy (R21). */
+double vo_courant(const vo_mesh *m, const double *F, double dt)
+{
+    double co = 0.0;
+    int c, i;
+    for (c = 0; c < m->nc; c++) {
+        double s = 0.0;
+        for (i = m->cptr[c]; i < m->cptr[c + 1]; i++) {
+            int g = m->cface[i];
+            if (g >= m->ni && m->fimg[g - m->ni] >= 0) g = m->fimg[g - m->ni];
+            s += fabs(F[g]);
+        }
+        s = 0.5 * s * dt / m->vc[c];
+        if (s > co) co = s;
+    }
+    return co;
+}
+
 int vo_update(const vo_mesh *m, double *alpha, const double *Va, int bound, double *stats)
 {
     int c, st = 0, f;

@@ -66,6 +66,8 @@ int vo_set_threads(int n);
  * the cell's points), cell volume (sum of its centre-apex tetrahedra). */
 void vo_geometry(const vo_mesh *m, double *cell_centre, double *cell_vol,
                  double *face_centre, double *face_area);
+/* Courant number: max over cells of (1/2) sum_f |F_f| dt / V_c */
+double vo_courant(const vo_mesh *m, const double *F, double dt);
 /* number of cells in the face stencil (cells sharing a point with the face) */
 int vo_stencil(const vo_mesh *m, int face, int *out, int cap);
 /* the same with each cell's translation code (i+1) + 3(j+1) + 9(k+1) for

@@ -749,6 +749,13 @@ int vof_update(vof_ctx *c, double *alpha, const double *Va, double *stats, void 
     return launch_update(c, alpha, Va, stats, (cudaStream_t)stream);
 }
 
+int vof_courant(vof_ctx *c, const double *F, double dt, double *co, void *stream)
+{
+    if (!c || !F || !co || !finite_pos(dt)) return VOF_ERR_INVALID_ARG;
+    cudaSetDevice(c->device);
+    return launch_courant(c, F, dt, co, (cudaStream_t)stream);
+}
+
 int vof_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt, double *stats,
                void *stream)
 {

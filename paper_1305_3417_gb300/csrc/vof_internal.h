@@ -164,6 +164,7 @@ int launch_phase_flux_all(vof_ctx *c, const double *alpha, const double *n, cons
                           const uint8_t *flags, const double *Up, const double *F,
                           const double *lambda, double dt, double *Va, cudaStream_t s);
 int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cudaStream_t s);
+int launch_courant(vof_ctx *c, const double *F, double dt, double *co, cudaStream_t s);
 int launch_advect(vof_ctx *c, double *alpha, const double *Uc, const double *F, double dt,
                   double *stats, cudaStream_t s,
                   cudaEvent_t wait_before_correct = nullptr);

@@ -1940,6 +1940,35 @@ int launch_barrier_probe(vof_ctx *c, int skip, cudaStream_t s)
     return VOF_OK;
 }
 
+// Courant number: the largest (1/2) sum |F_f| dt / V_c over the cells, the
+// block maxima combined by an atomic max on the bit patterns (non-negative
+// doubles order as their 64-bit integers)
+__global__ void k_courant(DevMesh m, const double *__restrict__ F, double dt, unsigned long long *co)
+{
+    __shared__ double red[8];
+    double v = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < m.nc; c += gridDim.x * blockDim.x) {
+        double sum = 0.0;
+        for (int k = m.cptr[c]; k < m.cptr[c + 1]; ++k) sum += fabs(F[m.cflux[k] >> 1]);
+        v = fmax(v, 0.5 * sum * dt / m.vc[c]);
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = fmax(v, red[w]);
+        atomicMax(co, (unsigned long long)__double_as_longlong(v));
+    }
+}
+
+int launch_courant(vof_ctx *c, const double *F, double dt, double *co, cudaStream_t s)
+{
+    if (cudaMemsetAsync(co, 0, sizeof(double), s) != cudaSuccess) return VOF_ERR_CUDA;
+    k_courant<<<num_sms(c->device) * 4, 256, 0, s>>>(c->m, F, dt, reinterpret_cast<unsigned long long *>(co));
+    LAUNCH_CHECK();
+    return VOF_OK;
+}
+
 int launch_update(vof_ctx *c, double *alpha, const double *Va, double *stats, cudaStream_t s)
 {
     int *cnt = c->counters;

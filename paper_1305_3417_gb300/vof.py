@@ -54,7 +54,7 @@ EXPORTS = ["vof_create", "vof_destroy", "vof_geometry", "vof_point_velocity", "v
            "vof_batch_create", "vof_batch_destroy", "vof_batch_context", "vof_batch_advect", "vof_batch_tune",
            "vof_mlp_create", "vof_mlp_destroy", "vof_mlp_params", "vof_mlp_features", "vof_mlp_forward",
            "vof_mlp_gradient", "vof_mlp_train_step", "vof_set_guess", "vof_set_gradient", "vof_lsq_gradient",
-           "vof_evsd", "vof_remap", "vof_tune", "vof_create_error"]
+           "vof_evsd", "vof_remap", "vof_tune", "vof_create_error", "vof_courant"]
 GRAD_NAG, GRAD_LSQ = 0, 1
 MLP_IN, MLP_HID, MLP_OUT = 33, 64, 4
 MLP_NPARAM = MLP_IN * MLP_HID + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID * MLP_OUT + MLP_OUT
@@ -112,6 +112,7 @@ def lib():
         "vof_evsd": (I, [P, P, P, P, ctypes.POINTER(ctypes.c_double), I, P, P]),
         "vof_remap": (I, [P, P, P, P, P, P, P, P, P, P]),
         "vof_tune": (I, [P, P, P, P, D, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), P]),
+        "vof_courant": (I, [P, P, D, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -264,6 +265,11 @@ def vof_advect(h, alpha, Uc, F, dt, stats=None, stream=None):
            "vof_advect")
 
 
+def vof_courant(h, F, dt, co, stream=None):
+    """co: one-element float64 device tensor, written with the step's Courant number."""
+    _check(lib().vof_courant(h, _ptr(F), float(dt), _ptr(co), _stream(stream)), "vof_courant")
+
+
 def vof_advect_host(h, alpha, Uc, F, dt, stats=None, stream=None):
     """Host (preferably pinned) CPU tensors; copies happen inside the call."""
     _check(lib().vof_advect_host(h, _ptr(alpha), _ptr(Uc), _ptr(F), float(dt), _ptr(stats), _stream(stream)),
@@ -383,6 +389,12 @@ class VofContext:
     def _z(self, n, dtype=None):
         import torch
         return torch.zeros(n, dtype=dtype or torch.float64, device=self.device)
+
+    def courant(self, F, dt) -> float:
+        """The step's Courant number (synchronises to read it back)."""
+        co = self._z(1)
+        vof_courant(self.h, F, dt, co)
+        return float(co.item())
 
     def geometry(self):
         cc, vc, cf, sf = self._z(3 * self.nc), self._z(self.nc), self._z(3 * self.nf), self._z(3 * self.nf)

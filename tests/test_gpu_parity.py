@@ -265,6 +265,16 @@ def test_periodic_mesh_errors(torch, O):
         vof.vof_batch_create(m, np.array([0, m.n_cells], np.int32))
 
 
+@pytest.mark.parametrize("name", list(WORKLOADS))
+def test_courant(torch, O, name):
+    """The step's Courant number on the device equals the oracle's."""
+    w, ctx, om = contexts(torch, O, name)
+    F, U, dt = w.step_inputs(1)
+    co = ctx.courant(T(torch, F), dt)
+    assert co > 0.0
+    assert co == pytest.approx(om.courant(F, dt), rel=1e-13)
+
+
 def test_edge_cases(torch, O):
     w, ctx, om = contexts(torch, O, "deform20")
     F, U, dt = w.step_inputs(0)

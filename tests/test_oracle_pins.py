@@ -848,3 +848,18 @@ def test_shear_error_near_paper_table(oracle_lib):
     print(f"oracle L1 {l1:.5e}, paper E_g {paper:.5e}")
     assert abs(float((vc * (a - w.alpha0)).sum())) < 1e-15
     assert 0.75 * paper <= l1 <= 1.1 * paper
+
+
+@pytest.mark.parametrize("U", [(1.0, 0.0, 0.0), (0.3, -0.7, 0.2)])
+def test_courant_number_of_a_uniform_velocity(oracle_lib, U):
+    """On a uniform hexahedral mesh a uniform velocity gives, in every cell,
+    (1/2) sum |F_f| dt / V = (|u| + |v| + |w|) dt / h; periodic or not."""
+    for periodic in ("", "xyz"):
+        m = I.hex_mesh((6, 5, 4), (1.0, 5 / 6, 4 / 6), periodic=periodic)
+        om = oracle_lib.OracleMesh(m)
+        fld = I.translation_field(U)
+        F = I.face_flux_stokes(m, fld.A)
+        dt = 0.037
+        co = om.courant(F, dt)
+        assert co == pytest.approx(sum(abs(u) for u in U) * dt / m.h, rel=1e-12)
+        assert om.courant(2.0 * F, dt) == pytest.approx(2.0 * co, rel=1e-15)
