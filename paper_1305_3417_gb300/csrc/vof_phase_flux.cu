@@ -595,18 +595,24 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
         }
         const V3 o = ld3(m.cf, m.nf, f);
         const int b = __ldg(m.fptr + f), n = __ldg(m.fptr + f + 1) - b;
-        // Complement form: when the upwind cell is mostly phase, sum the void
-        // pieces and take V_alpha = F dt - void (equal in exact arithmetic since
-        // the corrected polyhedron holds F dt and the stencil covers it); a
-        // polyhedron inside full cells then carries exactly F dt, one inside
-        // empty cells exactly 0, and the rounding of the clipping stays with
-        // mixed cells.  Not where the polyhedron can leave the domain (the
-        // normal-sweep fallback at walls; a face touching an open boundary),
-        // since the part outside is empty and the stencil does not cover it.
+        // Complement form: sum the void pieces and take V_alpha = F dt - void
+        // (equal in exact arithmetic since the corrected polyhedron holds F dt
+        // and the stencil covers it).  Full cells then need no clipping, where
+        // the plain form clips them and skips empty ones; the form is chosen by
+        // which of the two leaves fewer cells reaching the polyhedron's box
+        // (stencils of one chunk; ties, and longer stencils, by whether the
+        // upwind cell is mostly phase).  A polyhedron inside full cells carries
+        // exactly F dt, one inside empty cells exactly 0, and the rounding of
+        // the clipping stays with mixed cells.  Not where the polyhedron can
+        // leave the domain (the normal-sweep fallback at walls; a face touching
+        // an open boundary), since the part outside is empty and the stencil
+        // does not cover it.
         const double Ff = a.F[f];
         const int up = Ff > 0.0 ? __ldg(m.own + f) : (f < m.ni ? __ldg(m.nei + f) : __ldg(m.own + f));
         const double lamf = LIST ? a.lam_b[item] : a.lambda[f];
-        const bool comp = ge_pos(a.alpha[up], 0.5) && lamf >= 0.0 && !__ldg(m.fopen + f);
+        const bool comp_ok = lamf >= 0.0 && !__ldg(m.fopen + f);
+        const bool decide = comp_ok && s1 - s0 <= 32;  // warp-uniform
+        bool comp = comp_ok && ge_pos(a.alpha[up], 0.5);
         const int nt = n == 3 ? 3 : 3 * n;
         // signed distances (to unit-normal planes) within the on-plane band of
         // the face (FP32: 2e-6 of the face size, FP64: 1e-14) are taken as zero:
@@ -724,13 +730,16 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                     // translation t, and the cell, its tetrahedra and its
                     // plane are taken relative to o - t
                     V3 oc = o;
+                    bool emp = false, ful = false;
                     if (s < s1) {
                         c = __ldg(m.scell + s);
                         al = a.alpha[c];
                         if (m.scode) oc = o - tshift(m, __ldg(m.scode + s));
                         // an empty cell carries no phase, a full cell no void
                         // thresholds on the integer pipe (bit-pattern order of doubles)
-                        if (!((!comp && le_pos(al, eps)) || (comp && ge_pos(al, 1.0 - eps)))) {
+                        emp = le_pos(al, eps);
+                        ful = ge_pos(al, 1.0 - eps);
+                        if (decide || !(comp ? ful : emp)) {
                             const V3 cc = ld3(m.cc, m.nc, c);
                             dc = r3(rconv<R>(cc.x - oc.x), rconv<R>(cc.y - oc.y), rconv<R>(cc.z - oc.z));
                             const R4<R> cb0 = ldg4(cbl, 2 * (long)c), cb1 = ldg4(cbl, 2 * (long)c + 1);
@@ -738,6 +747,12 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                                      rgt(cb0.y + dc.y, pb[4]) || rgt(pb[2], cb1.z + dc.z) || rgt(cb0.z + dc.z, pb[5]));
                         }
                     }
+                    if (decide) {  // the whole stencil is this chunk
+                        const int nful = __popc(__ballot_sync(0xffffffffu, pass && ful));
+                        const int nemp = __popc(__ballot_sync(0xffffffffu, pass && emp));
+                        if (nful != nemp) comp = nful > nemp;
+                    }
+                    pass = pass && !(comp ? ful : emp);
                     int nkt = 0, t0 = 0;
                     R wgt = R(1);
                     bool useH = false;
