@@ -293,7 +293,8 @@ __device__ __forceinline__ void fsplit(const RTet<R> &t, const R s[4], int nin, 
 //    fraction);
 //  - split step: a piece from the other stack (else a new job) is cut by its
 //    next plane and the parts below are pushed, to the leaves if one plane is
-//    left.
+//    left; a new job with one plane goes to the leaves whole (no leaf work in
+//    a split step: a step's lanes never mix the two kinds of work).
 // A split step commits the longest prefix of lanes that leaves the two stacks
 // at most MX_STACK - 6 full; if none does, the top piece alone when it fits,
 // else a leaf step runs first (leaves need no room).  Every part of a split
@@ -355,32 +356,25 @@ __device__ __forceinline__ void mx_clip(MXShared<R, MX_STACK> &sh, int nq, R tol
         __syncwarp();  // every piece read before the pushes reuse the slots
         int nch = 0, nin = 0, nup = 0, ti = 0, k = 0;
         unsigned rem = 0;
-        R sd[4], v6 = R(0);
-        bool cut = false;
-        unsigned lw = 0;  // this lane's leaf work: 1 volume, 2 cut fraction
+        R sd[4];
+        bool cut = false, single = false;
         if (act) {
             ti = meta & 31;
             k = (meta >> 5) & 31;
             rem = meta >> 10;
-            const int j = __ffs(rem) - 1;
-            rem &= rem - 1;
-            fdist(t, sh.Kp[k][j], tol, sd, nin, nup);
-            if (nin > 0) {
-                if (nup > 0) cut = true;
-                if (rem != 0) nch = nup == 0 || nin == 1 ? 1 : 3;
-                else {  // a job with one plane: its leaf here
-                    v6 = rabs(rvol6(t.v[0], t.v[1], t.v[2], t.v[3]));
-                    lw = 1;
-                    if (nup > 0) {
-                        lw = 3;
-                        R h0 = sd[0], h1 = sd[1], h2 = sd[2], h3 = sd[3];
-                        rsort4(h0, h1, h2, h3);
-                        v6 *= rfrac_below(h0, h1, h2, h3);
-                    }
+            single = (rem & (rem - 1)) == 0;
+            if (single) nch = 1;  // a job with one plane goes to the leaves whole
+            else {
+                const int j = __ffs(rem) - 1;
+                rem &= rem - 1;
+                fdist(t, sh.Kp[k][j], tol, sd, nin, nup);
+                if (nin > 0) {
+                    if (nup > 0) cut = true;
+                    nch = nup == 0 || nin == 1 ? 1 : 3;
                 }
             }
         }
-        const bool toleaf = (rem & (rem - 1)) == 0;  // one plane left after this one
+        const bool toleaf = single || (rem & (rem - 1)) == 0;  // one plane left after this one
         const unsigned b0 = __ballot_sync(0xffffffffu, nch & 1), b1 = __ballot_sync(0xffffffffu, nch & 2);
         const unsigned bl = __ballot_sync(0xffffffffu, toleaf);
         const int inc = __popc(b0 & le) + 2 * __popc(b1 & le);
@@ -396,11 +390,8 @@ __device__ __forceinline__ void mx_clip(MXShared<R, MX_STACK> &sh, int nq, R tol
         const int top = MX_STACK - nn + min(L, p);  // the split stack's top after the pops
         if (lane < L) {
             // work of the committed lanes (the others redo theirs later)
-            wk.add(WK_TEST, 1);
-            wk.add(WK_VOL, lw & 1);
-            wk.add(WK_FRAC, lw >> 1);
+            wk.add(WK_TEST, !single);
             if (cut && nch > 0) wk.add(WK_EDGE, nin == 2 ? 4 : 3);
-            if (rpos(v6)) acc_add(acc, sh.Tsg[ti] * sh.Kw[k] * v6);
             if (nch > 0) {
                 const unsigned cm = (unsigned)ti | ((unsigned)k << 5) | (rem << 10);
                 // parts of the lanes before this one that go the same way
