@@ -875,6 +875,7 @@ __global__ void __launch_bounds__(UPD_THREADS) k_update(DevMesh m, double *alpha
             unsigned nz = 0;
             // (cflux: the cell's faces, a periodic copy read as its face seen
             // from the neighbour; the cell's own faces on other meshes)
+#pragma unroll 4
             for (int k = k0; k < k1; ++k) {
                 DBits b = dbits(Va[m.cflux[k] >> 1]);
                 nz |= (unsigned)(b.hi & 0x7fffffff) | b.lo;
@@ -1418,6 +1419,7 @@ __global__ void k_point_state(DevMesh m, const double *__restrict__ alpha, uint8
     bool all_e = true, all_f = true;
     const double full = 1.0 - m.eps;
     const int j0 = m.pptr[p], j1 = m.pptr[p + 1];
+#pragma unroll 4
     for (int j = j0; j < j1; ++j) {
         double a = __ldg(alpha + m.pcell[j]);
         all_e &= le_pos(a, m.eps);
@@ -1445,6 +1447,7 @@ __global__ void k_classify(DevMesh m, const double *__restrict__ alpha, const do
             // (a periodic face's copy carries no flux)
             if (!is_zero(Ff) && !(i >= m.ni && (dbits(Ff).hi < 0 || (m.fimg && m.fimg[i - m.ni] >= 0)))) {
                 unsigned st = 3u;
+#pragma unroll 4
                 for (int k = m.fptr[i]; k < m.fptr[i + 1]; ++k) st &= state[m.fpts[k]];
                 if (st & 1u) v = 0.0;
                 else if (st & 2u) v = Ff * dt;
