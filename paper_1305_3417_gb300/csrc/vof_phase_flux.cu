@@ -806,7 +806,11 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                 const int j = sh.Ct0[ci] + g - (ci ? sh.Cend[ci - 1] : 0);
                 const V dc = r3(sh.Cdc[ci][0], sh.Cdc[ci][1], sh.Cdc[ci][2]);
                 const R4<R> *q = ktl + 6 * (size_t)j;
+                // box and planes in one round trip to L2 (the planes of the
+                // tetrahedra the box test drops are read for nothing)
                 const R4<R> b0 = ldg4(q, 4), b1 = ldg4(q, 5);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) kp[i] = ldg4(q, i);
                 kbx[0] = b0.x + dc.x; kbx[1] = b0.y + dc.y; kbx[2] = b0.z + dc.z;
                 kbx[3] = b1.x + dc.x; kbx[4] = b1.y + dc.y; kbx[5] = b1.z + dc.z;
                 cand = !(rgt(pb[0], kbx[3]) || rgt(kbx[0], pb[3]) || rgt(pb[1], kbx[4]) || rgt(kbx[1], pb[4]) ||
@@ -815,7 +819,7 @@ __device__ __forceinline__ void phase_flux_body(const DevMesh &m, const MXArgs &
                     wk.add(WK_SHIFT, 4);
 #pragma unroll
                     for (int i = 0; i < 4; ++i) {
-                        const R4<R> pl = ldg4(q, i);
+                        const R4<R> pl = kp[i];
                         kp[i] = mk4<R>(pl.x, pl.y, pl.z, pl.w + (pl.x * dc.x + pl.y * dc.y + pl.z * dc.z));
                     }
                 }
